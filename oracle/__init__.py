@@ -1,0 +1,252 @@
+"""CPU oracle for the dense N x N FP64 product C = A.B (test infrastructure).
+
+Only the tests, ``__graft_entry__.smoke()`` and the benchmark's CPU-baseline
+leg may import this package.  The product path (the CUDA library and its
+Python binding) never imports, links or runs it, and it shares no code with
+that path.
+
+The arithmetic lives in ``oracle.c`` (plain C, FP64, no FMA contraction);
+this module compiles it with gcc on first use and binds it with ctypes.
+
+Parity status of each function (what pins it, in ``tests/test_oracle_pins.py``):
+  gemm / gemm_alg1 / gemm_rows -- identity, permutation, all-ones, small
+      integers (exact), hand-expanded 1x1..4x4, textbook 2x2, loop-order
+      and thread-count invariance, exact rational product within gamma_n.
+  absgemm -- exact integer case, bound against the exact rational value.
+  gemm_dot2 -- exact rational product (Python fractions) on small cases.
+  freivalds -- accepts exact products, rejects planted errors.
+  emu_* -- digits reconstruct D exactly; D equals the exact rounding of
+      a 2^(8s-1-e) (Python fractions); level sums equal brute force with
+      Python integers; RN of 128-bit integers equals Python's correctly
+      rounded int -> float; the full model is exact on small-integer inputs
+      and within the error bound of the exact product on random ones.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_OUT_DIR = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_OUT_DIR, "liboracle.so")
+CFLAGS = ["-O2", "-ffp-contract=off", "-fno-fast-math", "-fopenmp", "-fPIC", "-shared"]
+
+_lock = threading.Lock()
+_lib = None
+
+MAX_SLICES = 8
+
+
+def build(force: bool = False) -> str:
+    """Compiles oracle.c into oracle/_build/liboracle.so; returns its path."""
+    os.makedirs(_OUT_DIR, exist_ok=True)
+    fresh = os.path.exists(_LIB_PATH) and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)
+    if force or not fresh:
+        tmp = _LIB_PATH + f".tmp{os.getpid()}"
+        subprocess.run(["gcc", *CFLAGS, "-o", tmp, _SRC, "-lm"], check=True)
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+_D = ctypes.POINTER(ctypes.c_double)
+_I = ctypes.POINTER(ctypes.c_int)
+_I16 = ctypes.POINTER(ctypes.c_int16)
+_I64 = ctypes.POINTER(ctypes.c_int64)
+
+
+def lib() -> ctypes.CDLL:
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = build()
+            L = ctypes.CDLL(path)
+            c_int, c_double = ctypes.c_int, ctypes.c_double
+            L.or_gemm_alg1.argtypes = [c_int, _D, _D, _D]
+            L.or_gemm.argtypes = [c_int, _D, _D, _D, c_int]
+            L.or_gemm_rows.argtypes = [c_int, _D, _D, _I, c_int, _D, c_int]
+            L.or_absgemm.argtypes = [c_int, _D, _D, _D, c_int]
+            L.or_gemm_dot2.argtypes = [c_int, _D, _D, _D, c_int]
+            L.or_freivalds.argtypes = [c_int, _D, _D, _D, _D, c_double, _D, _D]
+            L.or_freivalds.restype = c_int
+            L.or_emu_row_exponents.argtypes = [c_int, _D, _I]
+            L.or_emu_col_exponents.argtypes = [c_int, _D, _I]
+            L.or_emu_fixed.argtypes = [c_double, c_int, c_int]
+            L.or_emu_fixed.restype = ctypes.c_int64
+            L.or_emu_digits_of.argtypes = [ctypes.c_int64, c_int, _I]
+            L.or_emu_digit_planes.argtypes = [c_int, c_int, _D, _I, c_int, _I16]
+            L.or_emu_level_sums.argtypes = [c_int, c_int, _I16, _I16, _I64, c_int]
+            L.or_emu_combine.argtypes = [_I64, c_int, c_int, c_int]
+            L.or_emu_combine.restype = c_double
+            L.or_emu_gemm.argtypes = [c_int, c_int, _D, _D, _D, c_int]
+            L.or_emu_gemm.restype = c_int
+            L.or_emu_gemm_rows.argtypes = [c_int, c_int, _D, _D, _I, c_int, _D, c_int]
+            L.or_emu_gemm_rows.restype = c_int
+            L.or_max_threads.restype = c_int
+            L.or_int128_to_double.argtypes = [ctypes.c_int64, ctypes.c_uint64]
+            L.or_int128_to_double.restype = c_double
+            _lib = L
+    return _lib
+
+
+def _dp(a: np.ndarray):
+    return a.ctypes.data_as(_D)
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _square(A, B):
+    A, B = _f64(A), _f64(B)
+    n = A.shape[0]
+    if A.shape != (n, n) or B.shape != (n, n):
+        raise ValueError("oracle: A and B must be square and of the same size")
+    return A, B, n
+
+
+def threads(nthreads: int | None) -> int:
+    return lib().or_max_threads() if nthreads is None else int(nthreads)
+
+
+def gemm(A, B, nthreads: int | None = None) -> np.ndarray:
+    """C = A.B with the paper's arithmetic (Alg. 1 / Alg. 4)."""
+    A, B, n = _square(A, B)
+    C = np.empty((n, n), np.float64)
+    lib().or_gemm(n, _dp(A), _dp(B), _dp(C), threads(nthreads))
+    return C
+
+
+def gemm_alg1(A, B) -> np.ndarray:
+    """C = A.B by the literal i, k, j loop of Alg. 1 (single thread)."""
+    A, B, n = _square(A, B)
+    C = np.empty((n, n), np.float64)
+    lib().or_gemm_alg1(n, _dp(A), _dp(B), _dp(C))
+    return C
+
+
+def gemm_rows(A, B, rows, nthreads: int | None = None) -> np.ndarray:
+    """Rows ``rows`` of A.B (same arithmetic as :func:`gemm`)."""
+    A, B, n = _square(A, B)
+    r = np.ascontiguousarray(rows, dtype=np.int32)
+    out = np.empty((len(r), n), np.float64)
+    lib().or_gemm_rows(n, _dp(A), _dp(B), r.ctypes.data_as(_I), len(r), _dp(out), threads(nthreads))
+    return out
+
+
+def absgemm(A, B, nthreads: int | None = None) -> np.ndarray:
+    """|A||B|, the denominator of the componentwise error."""
+    A, B, n = _square(A, B)
+    C = np.empty((n, n), np.float64)
+    lib().or_absgemm(n, _dp(A), _dp(B), _dp(C), threads(nthreads))
+    return C
+
+
+def gemm_dot2(A, B, nthreads: int | None = None) -> np.ndarray:
+    """A.B with compensated (Dot2) dot products: nearly the exact product."""
+    A, B, n = _square(A, B)
+    C = np.empty((n, n), np.float64)
+    lib().or_gemm_dot2(n, _dp(A), _dp(B), _dp(C), threads(nthreads))
+    return C
+
+
+def freivalds(A, B, C, x, slack: float = 4.0):
+    """Freivalds' check with probe x; returns (bad_rows, y, tol)."""
+    A, B, n = _square(A, B)
+    C, x = _f64(C), _f64(x)
+    y = np.empty(n, np.float64)
+    tol = np.empty(n, np.float64)
+    bad = lib().or_freivalds(n, _dp(A), _dp(B), _dp(C), _dp(x), float(slack), _dp(y), _dp(tol))
+    if bad < 0:
+        raise MemoryError("oracle: freivalds allocation failed")
+    return bad, y, tol
+
+
+# ---- model of the split-precision emulation ---------------------------------
+
+def emu_row_exponents(A) -> np.ndarray:
+    A = _f64(A)
+    n = A.shape[0]
+    e = np.empty(n, np.int32)
+    lib().or_emu_row_exponents(n, _dp(A), e.ctypes.data_as(_I))
+    return e
+
+
+def emu_col_exponents(B) -> np.ndarray:
+    B = _f64(B)
+    n = B.shape[0]
+    f = np.empty(n, np.int32)
+    lib().or_emu_col_exponents(n, _dp(B), f.ctypes.data_as(_I))
+    return f
+
+
+def emu_fixed(v: float, e: int, s: int) -> int:
+    return int(lib().or_emu_fixed(float(v), int(e), int(s)))
+
+
+def emu_digits_of(D: int, s: int) -> list[int]:
+    d = (ctypes.c_int * s)()
+    lib().or_emu_digits_of(int(D), int(s), d)
+    return list(d)
+
+
+def emu_digit_planes(M, ex, s: int, col_major: bool) -> np.ndarray:
+    """Digit planes [s][n][n] (int16) of an operand; see oracle.c."""
+    M = _f64(M)
+    n = M.shape[0]
+    ex = np.ascontiguousarray(ex, dtype=np.int32)
+    out = np.empty((s, n, n), np.int16)
+    lib().or_emu_digit_planes(n, s, _dp(M), ex.ctypes.data_as(_I), int(col_major),
+                              out.ctypes.data_as(_I16))
+    return out
+
+
+def emu_level_sums(dA, dB, nthreads: int | None = None) -> np.ndarray:
+    """Exact level sums S_L, L = 2..s+1, as int64 [s][n][n]."""
+    dA = np.ascontiguousarray(dA, dtype=np.int16)
+    dB = np.ascontiguousarray(dB, dtype=np.int16)
+    s, n, _ = dA.shape
+    S = np.empty((s, n, n), np.int64)
+    lib().or_emu_level_sums(n, s, dA.ctypes.data_as(_I16), dB.ctypes.data_as(_I16),
+                            S.ctypes.data_as(_I64), threads(nthreads))
+    return S
+
+
+def emu_combine(levels, s: int, e: int, f: int) -> float:
+    lv = np.ascontiguousarray(levels, dtype=np.int64)
+    return float(lib().or_emu_combine(lv.ctypes.data_as(_I64), int(s), int(e), int(f)))
+
+
+def emu_gemm(A, B, s: int, nthreads: int | None = None) -> np.ndarray:
+    """The emulated product with s slices, from the model's definitions."""
+    A, B, n = _square(A, B)
+    C = np.empty((n, n), np.float64)
+    rc = lib().or_emu_gemm(n, int(s), _dp(A), _dp(B), _dp(C), threads(nthreads))
+    if rc != 0:
+        raise ValueError(f"oracle: emu_gemm failed ({rc})")
+    return C
+
+
+def emu_gemm_rows(A, B, s: int, rows, nthreads: int | None = None) -> np.ndarray:
+    A, B, n = _square(A, B)
+    r = np.ascontiguousarray(rows, dtype=np.int32)
+    out = np.empty((len(r), n), np.float64)
+    rc = lib().or_emu_gemm_rows(n, int(s), _dp(A), _dp(B), r.ctypes.data_as(_I), len(r), _dp(out),
+                                threads(nthreads))
+    if rc != 0:
+        raise ValueError(f"oracle: emu_gemm_rows failed ({rc})")
+    return out
+
+
+def int128_to_double(T: int) -> float:
+    hi = T >> 64
+    lo = T & ((1 << 64) - 1)
+    return float(lib().or_int128_to_double(hi, lo))
+
+
+def max_threads() -> int:
+    return int(lib().or_max_threads())

@@ -1,0 +1,316 @@
+"""Pins of the CPU oracle against facts that do not come from the oracle.
+
+Each test names what fixes the expected value: the paper's printed tables, a
+closed form, an exact rational computation, a textbook example or a
+mathematical invariant.  A dropped term, a wrong index or a transposed
+operand in oracle.c fails at least one of them.
+"""
+import json
+import math
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import oracle
+import workload
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+U = 2.0 ** -53
+
+
+def exact_product(A, B):
+    """Exact rational product of two float matrices (Python fractions)."""
+    n = A.shape[0]
+    FA = [[Fraction(float(x)) for x in row] for row in A]
+    FB = [[Fraction(float(x)) for x in row] for row in B]
+    return [[sum((FA[i][j] * FB[j][k] for j in range(n)), Fraction(0)) for k in range(n)]
+            for i in range(n)]
+
+
+# ---- the paper's metric (Sec. 3.1, Alg. 2, Tables 1-3) -----------------------
+
+def test_flop_count_closed_form():
+    # N^2 (2N - 1) operations (Sec. 3.1); e.g. N = 100 -> 1,990,000.
+    assert workload.flops(100) == 1_990_000
+    for n in (1, 2, 10, 2000):
+        assert workload.flops(n) == n * n * (2 * n - 1)
+
+
+def test_paper_tables_are_consistent_with_the_metric():
+    g = json.load(open(os.path.join(GOLDEN, "paper_tables.json")))
+    Ns = g["N"]
+    for prog in ("sequential", "openmp", "mpi"):
+        for idx, n in enumerate(Ns):
+            t = g["table1_runtime_s"][prog][idx]
+            mflops = g["table2_mflops"][prog][idx]
+            rate = workload.flops(n) / t / 1e6
+            if n == 100 or (n == 2000 and prog in ("sequential", "openmp")):
+                continue  # 1-2 significant digits, or the two inconsistent cells
+            assert abs(rate - mflops) / mflops < 0.01, (prog, n, rate, mflops)
+    # The two flagged cells really are inconsistent (8.91 vs about 66.4).
+    assert workload.flops(2000) / 240.97 / 1e6 == pytest.approx(66.38, rel=1e-3)
+    # Speedup = t_seq / t_par (Table 3).
+    for prog in ("openmp", "mpi"):
+        for idx, n in enumerate(Ns):
+            sp = g["table1_runtime_s"]["sequential"][idx] / g["table1_runtime_s"][prog][idx]
+            assert abs(sp - g["table3_speedup"][prog][idx]) < 0.051, (prog, n, sp)
+
+
+# ---- the product (Alg. 1, 3, 4) -----------------------------------------------
+
+def test_textbook_2x2():
+    A = np.array([[1.0, 2.0], [3.0, 4.0]])
+    B = np.array([[5.0, 6.0], [7.0, 8.0]])
+    np.testing.assert_array_equal(oracle.gemm(A, B), [[19.0, 22.0], [43.0, 50.0]])
+    np.testing.assert_array_equal(oracle.gemm_alg1(A, B), [[19.0, 22.0], [43.0, 50.0]])
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 4])
+def test_tiny_sizes_by_brute_force_enumeration(n):
+    # Entries that are small powers of two times small odd integers make every
+    # partial sum exact, so the result must equal the exact rational product.
+    rng = np.random.default_rng(100 + n)
+    A = rng.integers(-9, 10, (n, n)) * 2.0 ** rng.integers(-3, 4, (n, n))
+    B = rng.integers(-9, 10, (n, n)) * 2.0 ** rng.integers(-3, 4, (n, n))
+    ex = exact_product(A, B)
+    C = oracle.gemm(A, B)
+    for i in range(n):
+        for k in range(n):
+            assert Fraction(float(C[i, k])) == ex[i][k]
+
+
+def test_identity_and_permutation_are_exact():
+    n = 37
+    A, B = workload.pair("uniform01", 3, n)
+    I = np.eye(n)
+    np.testing.assert_array_equal(oracle.gemm(I, B), B)
+    np.testing.assert_array_equal(oracle.gemm(A, I), A)
+    perm = np.random.default_rng(1).permutation(n)
+    P = np.eye(n)[perm]  # row i of P selects row perm[i]
+    np.testing.assert_array_equal(oracle.gemm(P, B), B[perm])
+    np.testing.assert_array_equal(oracle.gemm(A, P.T), A[:, perm])
+
+
+@pytest.mark.parametrize("n", [1, 7, 64, 129])
+def test_all_ones_gives_n(n):
+    J = np.ones((n, n))
+    np.testing.assert_array_equal(oracle.gemm(J, J), np.full((n, n), float(n)))
+
+
+@pytest.mark.parametrize("n", [5, 33, 100])
+def test_small_integers_are_exact(n):
+    # Entries in {-8..8}: every partial sum is an integer below 2^53, so any
+    # summation order gives the exact integer product (numpy int64 matmul).
+    A, B = workload.pair("int8", 7, n)
+    ref = (A.astype(np.int64) @ B.astype(np.int64)).astype(np.float64)
+    np.testing.assert_array_equal(oracle.gemm(A, B), ref)
+    np.testing.assert_array_equal(oracle.gemm_alg1(A, B), ref)
+    # (AB)^T = B^T A^T exactly for integer inputs: catches a transposed operand.
+    np.testing.assert_array_equal(oracle.gemm(B.T.copy(), A.T.copy()), ref.T)
+    np.testing.assert_array_equal(oracle.absgemm(A, B),
+                                  (np.abs(A).astype(np.int64) @ np.abs(B).astype(np.int64)))
+
+
+def test_loop_order_and_thread_count_do_not_change_bits():
+    n = 150
+    A, B = workload.pair("uniform11", 11, n)
+    ref = oracle.gemm_alg1(A, B)
+    for t in (1, 2, 3, 8):
+        np.testing.assert_array_equal(oracle.gemm(A, B, nthreads=t), ref)
+    rows = [0, 5, 149, 77]
+    np.testing.assert_array_equal(oracle.gemm_rows(A, B, rows), ref[rows])
+
+
+@pytest.mark.parametrize("dist", ["uniform01", "uniform11", "loguniform20"])
+def test_within_recursive_summation_bound_of_exact(dist):
+    # Higham, Accuracy and Stability, Sec. 3.1: |fl(x.y) - x.y| <= gamma_n |x|.|y|.
+    n = 9
+    A, B = workload.pair(dist, 21, n)
+    ex = exact_product(A, B)
+    C = oracle.gemm(A, B)
+    absAB = np.abs(A) @ np.abs(B)
+    gamma = n * U / (1 - n * U)
+    worst = 0.0
+    for i in range(n):
+        for k in range(n):
+            err = abs(Fraction(float(C[i, k])) - ex[i][k])
+            assert err <= Fraction(gamma) * Fraction(float(absAB[i, k])) * (1 + 1e-12)
+            worst = max(worst, float(err))
+    assert worst > 0.0  # rounding did occur, so the bound was exercised
+
+
+def test_dot2_is_nearly_exact():
+    # Ogita-Rump-Oishi: |res - x.y| <= u |x.y| + gamma_n^2 |x|.|y|.
+    n = 12
+    A, B = workload.pair("loguniform20", 5, n)
+    ex = exact_product(A, B)
+    D = oracle.gemm_dot2(A, B)
+    absAB = np.abs(A) @ np.abs(B)
+    gamma = n * U / (1 - n * U)
+    for i in range(n):
+        for k in range(n):
+            bound = Fraction(U) * abs(ex[i][k]) + Fraction(gamma * gamma) * Fraction(float(absAB[i, k])) * 2
+            assert abs(Fraction(float(D[i, k])) - ex[i][k]) <= bound
+
+
+def test_freivalds_accepts_exact_and_rejects_planted_errors():
+    n = 80
+    A, B = workload.pair("uniform11", 2, n)
+    C = oracle.gemm(A, B)
+    rng = np.random.default_rng(0)
+    for _ in range(4):
+        x = rng.choice([-1.0, 1.0], n)
+        bad, _, _ = oracle.freivalds(A, B, C, x)
+        assert bad == 0
+    # A single wrong entry far above the rounding level is caught by +-1 probes.
+    Cw = C.copy()
+    Cw[17, 33] += 1e-6
+    caught = 0
+    for _ in range(8):
+        x = rng.choice([-1.0, 1.0], n)
+        bad, _, _ = oracle.freivalds(A, B, Cw, x)
+        caught += bad > 0
+    assert caught == 8  # with +-1 probes a single-entry error is never cancelled
+    # The transposed product is rejected.
+    bad, _, _ = oracle.freivalds(A, B, oracle.gemm(B, A), rng.choice([-1.0, 1.0], n))
+    assert bad > 0
+
+
+# ---- model of the split-precision emulation -----------------------------------
+
+def test_row_and_column_exponents_bracket_the_maximum():
+    n = 50
+    A = workload.matrix("loguniform20", 4, n)
+    A[3] = 0.0
+    e = oracle.emu_row_exponents(A)
+    f = oracle.emu_col_exponents(A)
+    for i in range(n):
+        m = np.abs(A[i]).max()
+        if m == 0:
+            assert e[i] == 0
+        else:
+            assert m < 2.0 ** e[i] and m >= 2.0 ** (e[i] - 1)
+    for k in range(n):
+        m = np.abs(A[:, k]).max()
+        assert m < 2.0 ** f[k] and m >= 2.0 ** (f[k] - 1)
+
+
+def test_fixed_point_value_is_the_exact_rounding():
+    rng = np.random.default_rng(9)
+    vals = list(workload.values("loguniform20", 1, 200)) + [0.0, -0.0, 1 - 2 ** -53, -(1 - 2 ** -53),
+                                                             0.5, 2 ** -60, 3 * 2 ** -56]
+    for s in (1, 2, 5, 7, 8):
+        for v in vals:
+            e = 1 if abs(v) < 1 else math.frexp(abs(v))[1]
+            if abs(v) >= 2.0 ** e:
+                continue
+            exact = Fraction(float(v)) * Fraction(2) ** (8 * s - 1 - e)
+            assert oracle.emu_fixed(v, e, s) == round(exact)  # round() on Fraction: half to even
+    # Ties go to even.
+    assert oracle.emu_fixed(3 * 2.0 ** -8, 0, 1) == 2  # 1.5 -> 2
+    assert oracle.emu_fixed(5 * 2.0 ** -8, 0, 1) == 2  # 2.5 -> 2
+    assert oracle.emu_fixed(-5 * 2.0 ** -8, 0, 1) == -2
+    _ = rng
+
+
+def test_digits_reconstruct_and_respect_ranges():
+    rng = np.random.default_rng(3)
+    for s in range(1, 9):
+        top = 2 ** (8 * s - 1)
+        cases = [0, 1, -1, 127, 128, -128, 255, top, -top, top - 1, -(top - 1)]
+        cases += [int(x) for x in rng.integers(-top if s < 8 else -(2 ** 62), top if s < 8 else 2 ** 62, 50)]
+        for D in cases:
+            if abs(D) > min(top, 2 ** 63 - 2 ** 10):
+                continue  # |D| <= 2^(8s-1), and <= 2^63 - 2^10 at s = 8 since |x| <= 1 - 2^-53
+            d = oracle.emu_digits_of(D, s)
+            assert sum(dt * 256 ** (s - 1 - t) for t, dt in enumerate(d)) == D
+            assert all(-128 <= x <= 127 for x in d[1:])
+            assert -128 <= d[0] <= 128
+
+
+@pytest.mark.parametrize("s", [1, 2, 3])
+def test_level_sums_by_brute_force(s):
+    n = 6
+    A, B = workload.pair("uniform11", 8, n)
+    e = oracle.emu_row_exponents(A)
+    f = oracle.emu_col_exponents(B)
+    dA = oracle.emu_digit_planes(A, e, s, False)
+    dB = oracle.emu_digit_planes(B, f, s, True)
+    # digits taken one value at a time agree with the planes
+    for i in range(n):
+        for j in range(n):
+            assert list(dA[:, i, j]) == oracle.emu_digits_of(oracle.emu_fixed(A[i, j], e[i], s), s)
+            assert list(dB[:, i, j]) == oracle.emu_digits_of(oracle.emu_fixed(B[i, j], f[j], s), s)
+    S = oracle.emu_level_sums(dA, dB)
+    for i in range(n):
+        for k in range(n):
+            for L in range(2, s + 2):
+                want = sum(int(dA[t - 1, i, j]) * int(dB[L - t - 1, j, k])
+                           for j in range(n) for t in range(1, s + 1) if 1 <= L - t <= s)
+                assert S[L - 2, i, k] == want
+
+
+def test_int128_rounding_matches_exact_conversion():
+    rng = np.random.default_rng(12)
+    cases = [0, 1, -1, 2 ** 53 + 1, 2 ** 53 + 3, -(2 ** 53 + 1), 2 ** 95 + 2 ** 42, 2 ** 95 + 2 ** 42 + 1,
+             (2 ** 54 + 2) * 2 ** 30, (2 ** 54 + 6) * 2 ** 30, 2 ** 126 - 1]
+    for _ in range(300):
+        bits = int(rng.integers(1, 126))
+        cases.append(int(rng.integers(0, 2 ** 62)) << max(0, bits - 62) | int(rng.integers(0, 2 ** 31)))
+        cases.append(-cases[-1])
+    for T in cases:
+        assert oracle.int128_to_double(T) == float(T), T  # Python int -> float rounds half to even
+
+
+def test_combine_is_the_rounded_exact_sum():
+    rng = np.random.default_rng(5)
+    for s in (1, 4, 8):
+        for _ in range(50):
+            lv = [int(x) for x in rng.integers(-2 ** 31, 2 ** 31, s)]
+            e, f = int(rng.integers(-20, 21)), int(rng.integers(-20, 21))
+            T = sum(S * 256 ** (s + 1 - L) for L, S in zip(range(2, s + 2), lv))
+            want = float(Fraction(T) * Fraction(2) ** (e + f - 8 * s - 6))
+            # float(Fraction) is correctly rounded; here T fits the exponent range,
+            # so one rounding of T then exact scaling equals rounding the scaled value.
+            assert oracle.emu_combine(lv, s, e, f) == want
+
+
+@pytest.mark.parametrize("s", [1, 3, 7])
+def test_emulation_is_exact_on_small_integers(s):
+    n = 40
+    A, B = workload.pair("int8", 13, n)
+    ref = (A.astype(np.int64) @ B.astype(np.int64)).astype(np.float64)
+    np.testing.assert_array_equal(oracle.emu_gemm(A, B, s), ref)
+
+
+def test_emulation_of_identity_is_exact():
+    n = 24
+    B = 0.5 + 0.5 * workload.matrix("uniform01", 6, n)  # one binade: 54 bits suffice
+    I = np.eye(n)
+    np.testing.assert_array_equal(oracle.emu_gemm(I, B, 7), B)
+    np.testing.assert_array_equal(oracle.emu_gemm(B, I, 7), B)
+
+
+def test_emulation_error_shrinks_with_slices_and_meets_bound():
+    n = 32
+    A, B = workload.pair("uniform11", 17, n)
+    ex = np.array([[float(x) for x in row] for row in exact_product(A, B)])  # exact to 1/2 ulp
+    absAB = np.abs(A) @ np.abs(B)
+    errs = []
+    for s in range(2, 9):
+        C = oracle.emu_gemm(A, B, s)
+        errs.append(np.max(np.abs(C - ex) / absAB))
+    assert all(b <= a * 1.0001 or b < 1e-17 for a, b in zip(errs, errs[1:])), errs
+    assert errs[0] > 2 * n * U  # two slices are far from FP64 accuracy
+    assert errs[-2] <= 2 * n * U  # seven slices meet the componentwise bound
+    assert errs[-1] <= 2 * n * U
+
+
+def test_emulated_rows_match_full_model():
+    n = 70
+    A, B = workload.pair("loguniform20", 23, n)
+    C = oracle.emu_gemm(A, B, 5)
+    rows = [0, 69, 31]
+    np.testing.assert_array_equal(oracle.emu_gemm_rows(A, B, 5, rows), C[rows])

@@ -1,0 +1,98 @@
+"""Seeded synthetic inputs for the dense N x N FP64 product C = A.B.
+
+This module is the only code shared by the oracle tests and the GPU path.
+It holds random-number generation and nothing of the product's arithmetic.
+
+The paper fills its matrices with an unspecified ``RAND()`` (Alg. 2 and
+Alg. 4, Sec. 3.1).  The distributions here are the synthetic stand-ins for
+that: uniform [0, 1), uniform [-1, 1), log-uniform magnitude with a random
+sign, and small integers in {-8..8} whose products are exact in FP64.
+
+The generator is counter based: draw ``i`` of stream ``seed`` is
+SplitMix64 (Steele, Lea, Flood 2014) evaluated at ``seed + (i + 1) * gamma``,
+so any element can be reproduced without generating the ones before it.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+GOLDEN_GAMMA = np.uint64(0x9E3779B97F4A7C15)
+_M1 = np.uint64(0xBF58476D1CE4E5B9)
+_M2 = np.uint64(0x94D049BB133111EB)
+# Stream offset separating B from A for the same seed.
+B_STREAM_OFFSET = 0x5851F42D4C957F2D
+# Stream offset for the sign bits of log-uniform entries.
+SIGN_STREAM_OFFSET = 0x2545F4914F6CDD1D
+
+DISTRIBUTIONS = ("uniform01", "uniform11", "loguniform20", "int8")
+
+
+def splitmix64(seed: int, count: int, start: int = 0) -> np.ndarray:
+    """Draws ``start .. start+count-1`` of the SplitMix64 stream ``seed``."""
+    with np.errstate(over="ignore"):
+        idx = np.arange(start + 1, start + count + 1, dtype=np.uint64)
+        z = np.uint64(seed & 0xFFFFFFFFFFFFFFFF) + idx * GOLDEN_GAMMA
+        z = (z ^ (z >> np.uint64(30))) * _M1
+        z = (z ^ (z >> np.uint64(27))) * _M2
+        z = z ^ (z >> np.uint64(31))
+    return z
+
+
+def uniform01(seed: int, count: int) -> np.ndarray:
+    """Uniform doubles in [0, 1): the top 53 bits of each draw times 2^-53."""
+    z = splitmix64(seed, count)
+    return (z >> np.uint64(11)).astype(np.float64) * (2.0 ** -53)
+
+
+def values(dist: str, seed: int, count: int) -> np.ndarray:
+    """``count`` FP64 values of distribution ``dist`` from stream ``seed``."""
+    if dist == "uniform01":
+        return uniform01(seed, count)
+    if dist == "uniform11":
+        return 2.0 * uniform01(seed, count) - 1.0
+    if dist == "loguniform20":
+        u = uniform01(seed, count)
+        mag = np.exp2(-20.0 + 40.0 * u)
+        sign = (splitmix64(seed + SIGN_STREAM_OFFSET, count) >> np.uint64(63)).astype(np.int64)
+        return np.where(sign == 1, -mag, mag)
+    if dist == "int8":
+        z = splitmix64(seed, count)
+        return ((z % np.uint64(17)).astype(np.int64) - 8).astype(np.float64)
+    raise ValueError(f"unknown distribution {dist!r}; expected one of {DISTRIBUTIONS}")
+
+
+def matrix(dist: str, seed: int, n: int, which: str = "A") -> np.ndarray:
+    """Row-major n x n FP64 matrix; ``which`` = "A" or "B" selects the stream."""
+    s = seed if which == "A" else seed + B_STREAM_OFFSET
+    return np.ascontiguousarray(values(dist, s, n * n).reshape(n, n))
+
+
+def pair(dist: str, seed: int, n: int) -> tuple[np.ndarray, np.ndarray]:
+    """The (A, B) operand pair of one product."""
+    return matrix(dist, seed, n, "A"), matrix(dist, seed, n, "B")
+
+
+def loguniform_sizes(count: int, lo: int, hi: int, seed: int) -> list[int]:
+    """``count`` sizes N log-uniform over the integers [lo, hi].
+
+    N = clamp(floor(exp(ln lo + u (ln(hi + 1) - ln lo))), lo, hi), u uniform [0, 1).
+    """
+    u = uniform01(seed, count)
+    n = np.floor(np.exp(np.log(lo) + u * (np.log(hi + 1.0) - np.log(lo)))).astype(np.int64)
+    return [int(x) for x in np.clip(n, lo, hi)]
+
+
+def batch(dist: str, seed: int, sizes: list[int]) -> list[tuple[np.ndarray, np.ndarray]]:
+    """Operand pairs for a batch; problem p uses stream ``seed * 1000003 + p``."""
+    return [pair(dist, seed * 1000003 + p, n) for p, n in enumerate(sizes)]
+
+
+# Workloads by name.  Sizes follow the paper's sweep (N from 10 to 2000,
+# Sec. 1.1 and Tables 1-3) and its larger extensions.
+SWEEP_SIZES = (10, 100, 500, 1000, 1500, 2000)
+PRECISION_SIZES = (2000, 4096, 8192)
+
+
+def flops(n: int) -> int:
+    """The paper's operation count for one N x N product: N^2 (2N - 1) = 2N^3 - N^2."""
+    return 2 * n ** 3 - n ** 2
