@@ -1,0 +1,146 @@
+/*
+ * mm.h -- C ABI of the GB300 (sm_103a) dense FP64 matrix-product library.
+ *
+ * The operation is the square product C = A.B in double precision, as
+ * defined by the sequential triple loop of Hasta and Mutiara (2010), Alg. 1
+ * in Sec. 3.1: c(i,k) = sum over j of a(i,j) * b(j,k), accumulated from 0.0
+ * (Alg. 3 and Alg. 4 reset c to 0.0 the same way).  The paper times it for
+ * N from 10 to 2000 (Sec. 1.1, Sec. 4.1) and counts N^2 (2N - 1) operations
+ * per product (Sec. 3.1, Alg. 2).
+ *
+ * Two forms compute it on the GPU:
+ *   MM_NATIVE_FP64  FP64 tensor-core MMA (mma.sync f64), one rounding per
+ *                   fused multiply-add, in an order other than the paper's.
+ *   MM_EMU_BF16     split-precision emulation: A is scaled per row and B per
+ *                   column by powers of two, each value is split into s
+ *                   base-2^8 integer digits held exactly in bf16, the digit
+ *                   products run on the tcgen05 tensor cores with exact
+ *                   integer accumulation, and the exact sum is rounded once
+ *                   to FP64.  Nothing in the paper corresponds to it.
+ * MM_AUTO picks one per problem (see mm_config).
+ *
+ * Conventions for every call:
+ *   - Matrices are square, row-major, leading dimension N, FP64, 16-byte
+ *     aligned device pointers, owned by the caller.  C is overwritten
+ *     (beta = 0) and must not overlap A or B.
+ *   - Calls are asynchronous on `stream` (a cudaStream_t passed as void*;
+ *     NULL is the legacy default stream).  The return value covers argument
+ *     checks and launch errors only; errors found on the device (a timed-out
+ *     wait, non-finite input to the emulation) are kept in a status word
+ *     read by mm_status_get, which synchronises the stream.
+ *   - A handle is not thread safe: use one per host thread.  It owns a
+ *     device workspace that grows on demand and is freed by mm_destroy.
+ *   - Failed calls leave a message for mm_last_error.
+ */
+#ifndef MM_H_
+#define MM_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mm_handle_s* mm_handle;
+
+typedef enum {
+  MM_OK = 0,
+  MM_ERR_INVALID = 1,      /* bad argument: NULL, negative size, misaligned pointer */
+  MM_ERR_CUDA = 2,         /* a CUDA runtime or driver call failed */
+  MM_ERR_NOMEM = 3,        /* workspace allocation failed */
+  MM_ERR_UNSUPPORTED = 4,  /* size or slice count outside what the kernels support */
+  MM_ERR_TIMEOUT = 5,      /* a device-side wait ran out of time (kernel wound down) */
+  MM_ERR_NONFINITE = 6     /* emulation met an Inf or NaN input */
+} mm_status;
+
+typedef enum {
+  MM_NATIVE_FP64 = 0,
+  MM_EMU_BF16 = 1,
+  MM_AUTO = 3
+} mm_mode;
+
+/* Flags of mm_config.flags. */
+#define MM_FLAG_NO_GRAPH 1u /* grouped calls launch directly instead of replaying a CUDA graph */
+
+typedef struct {
+  mm_mode mode;          /* default MM_AUTO */
+  int slices;            /* emulation digit count s in 1..8; 0 = chosen per problem */
+  unsigned flags;        /* MM_FLAG_* */
+  const char* tune_path; /* optional autotune table (text file); NULL = built-in table */
+} mm_config;
+
+/* Creates a handle on the current CUDA device.  cfg may be NULL (MM_AUTO,
+ * automatic slice count).  *out receives the handle. */
+mm_status mm_create(mm_handle* out, const mm_config* cfg);
+
+/* Releases the handle and its workspace.  Waits for the device first. */
+mm_status mm_destroy(mm_handle h);
+
+/* C = A.B for one N x N problem (Alg. 1).  N = 0 is a no-op.
+ * A, B, C: device pointers (see conventions). */
+mm_status mm_gemm(mm_handle h, int N, const double* A, const double* B, double* C, void* stream);
+
+/* `count` independent products C_p = A_p.B_p of uneven sizes Ns[p] in one
+ * grouped launch per kernel.  Ns, As, Bs, Cs are HOST arrays of length
+ * count, read during the call; the matrices they point to are device
+ * memory.  Problems with N = 0 are skipped.  The first call with a given
+ * (count, Ns, pointers) signature builds a CUDA graph; later identical calls
+ * replay it (unless MM_FLAG_NO_GRAPH). */
+mm_status mm_gemm_grouped(mm_handle h, int count, const int* Ns, const double* const* As,
+                          const double* const* Bs, double* const* Cs, void* stream);
+
+/* End-to-end form of mm_gemm on HOST buffers: copies A and B to the device,
+ * computes, copies C back, and returns when C is on the host (the span the
+ * paper times with MPI_Wtime, Alg. 2).  Host buffers are best pinned. */
+mm_status mm_gemm_host(mm_handle h, int N, const double* A_host, const double* B_host, double* C_host,
+                       void* stream);
+
+/* Synchronises `stream` and returns the first error recorded on the device
+ * since the last call (and clears it), else MM_OK. */
+mm_status mm_status_get(mm_handle h, void* stream);
+
+/* Message of the last failed call on this handle (never NULL). */
+const char* mm_last_error(mm_handle h);
+
+/* Digit count the handle would use for an N x N problem (after AUTO), and
+ * the form: 0 = native FP64, 1 = emulation. */
+mm_status mm_plan(mm_handle h, int N, int* form, int* slices);
+
+/* ---------------------------------------------------------------------
+ * Steps of the emulation, exposed for testing each one on its own.
+ * They use caller-provided device buffers with the layouts stated here.
+ * --------------------------------------------------------------------- */
+
+/* Scale and split (row/column scaling, then integer digits).
+ * by_columns = 0: operand A, exponent e_i of row i; by_columns = 1: operand
+ * B, exponent f_k of column k.  e_i is the smallest integer with
+ * max_j |a_ij| < 2^e_i (0 for a zero row).  Each value v is turned into the
+ * integer D = round-half-even(v * 2^(8s - 1 - e)) and D is written as s
+ * balanced base-256 digits D = sum_t d_t 2^(8(s-t)), d_2..d_s in [-128,127],
+ * d_1 in [-128,128] (Ozaki, Ogita, Oishi, Rump 2012 split, fixed-point form).
+ * Outputs (device): exps[N] int32; digits: bf16 bit patterns, s planes of
+ * rows x ld elements, plane t at digits + t*rows*ld.  For A, element (i,j)
+ * sits at row i, column j; for B, (j,k) sits at row k, column j (B^T).
+ * rows >= N and ld >= N, ld a multiple of 8; the padding is written with 0. */
+mm_status mm_split(mm_handle h, int N, const double* M, int by_columns, int slices, int* exps,
+                   uint16_t* digits, int rows, int ld, void* stream);
+
+/* Exact level sums of digit products: for L = 2..s+1,
+ *   S_L(i,k) = sum_j sum_{t+u=L} d_t(a_ij) d_u(b_jk)
+ * written as int32 to levels[(L-2)*N*N + i*N + k].  Inputs are the digit
+ * planes of mm_split (A: rows = a_rows; B: rows = b_rows; both with ld).
+ * Requires (s) * N * 2^14 < 2^31. */
+mm_status mm_level_sums(mm_handle h, int N, int slices, const uint16_t* a_digits, int a_rows,
+                        const uint16_t* b_digits, int b_rows, int ld, int32_t* levels, void* stream);
+
+/* Recombination: c_ik = RN( sum_L S_L(i,k) 2^(8(s+1-L)) ) * 2^(e_i + f_k - 8s - 6),
+ * one round-to-nearest-even of the exact integer sum, then exact scaling. */
+mm_status mm_recombine(mm_handle h, int N, int slices, const int32_t* levels, const int* a_exps,
+                       const int* b_exps, double* C, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MM_H_ */

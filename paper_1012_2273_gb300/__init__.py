@@ -1,0 +1,235 @@
+"""Python binding of the GB300 dense FP64 product library (include/mm.h).
+
+Argument marshalling only: every step of the product runs in the CUDA
+kernels of libmm.so.  PyTorch supplies device memory and streams; tensors are
+passed to the C ABI as raw device pointers.  There is no CPU fallback: if the
+library cannot be built or loaded, importing a function that needs it raises.
+
+    import torch, paper_1012_2273_gb300 as mm
+    h = mm.Handle()                       # MM_AUTO
+    C = h.gemm(A, B)                      # A, B: (N, N) float64 CUDA tensors
+    Cs = h.gemm_grouped([A1, A2], [B1, B2])
+    h.check()                             # device-side errors (timeouts, Inf/NaN)
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from typing import Sequence
+
+from . import build as _build
+
+NATIVE_FP64 = 0
+EMU_BF16 = 1
+AUTO = 3
+FLAG_NO_GRAPH = 1
+
+STATUS_NAMES = {
+    0: "MM_OK", 1: "MM_ERR_INVALID", 2: "MM_ERR_CUDA", 3: "MM_ERR_NOMEM",
+    4: "MM_ERR_UNSUPPORTED", 5: "MM_ERR_TIMEOUT", 6: "MM_ERR_NONFINITE",
+}
+
+_MODES = {"native": NATIVE_FP64, "emulated": EMU_BF16, "emu": EMU_BF16, "auto": AUTO}
+
+_lock = threading.Lock()
+_lib = None
+
+
+class MMError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class _Config(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int), ("slices", ctypes.c_int), ("flags", ctypes.c_uint),
+                ("tune_path", ctypes.c_char_p)]
+
+
+SYMBOLS = ("mm_create", "mm_destroy", "mm_gemm", "mm_gemm_grouped", "mm_gemm_host", "mm_status_get",
+           "mm_last_error", "mm_plan", "mm_split", "mm_level_sums", "mm_recombine")
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib(build_if_needed: bool = True) -> ctypes.CDLL:
+    """Loads libmm.so (building it first if sources changed)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build() if build_if_needed else _build.LIB
+            if not os.path.exists(path):
+                raise ImportError(f"libmm.so not found at {path}; run __graft_entry__.build()")
+            L = ctypes.CDLL(path)
+            vp, ci, cd = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+            L.mm_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(_Config)]
+            L.mm_destroy.argtypes = [vp]
+            L.mm_gemm.argtypes = [vp, ci, vp, vp, vp, vp]
+            L.mm_gemm_grouped.argtypes = [vp, ci, ctypes.POINTER(ci), ctypes.POINTER(vp), ctypes.POINTER(vp),
+                                          ctypes.POINTER(vp), vp]
+            L.mm_gemm_host.argtypes = [vp, ci, vp, vp, vp, vp]
+            L.mm_status_get.argtypes = [vp, vp]
+            L.mm_last_error.argtypes = [vp]
+            L.mm_last_error.restype = ctypes.c_char_p
+            L.mm_plan.argtypes = [vp, ci, ctypes.POINTER(ci), ctypes.POINTER(ci)]
+            L.mm_split.argtypes = [vp, ci, vp, ci, ci, vp, vp, ci, ci, vp]
+            L.mm_level_sums.argtypes = [vp, ci, ci, vp, ci, vp, ci, ci, vp, vp]
+            L.mm_recombine.argtypes = [vp, ci, ci, vp, vp, vp, vp, vp]
+            for name in SYMBOLS:
+                if name != "mm_last_error":
+                    getattr(L, name).restype = ci
+            _ = cd
+            _lib = L
+    return _lib
+
+
+def _stream_ptr(stream) -> int:
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream) if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def _check_tensor(t, name: str, n: int | None = None):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != torch.float64:
+        raise TypeError(f"{name} must be float64")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous (row-major)")
+    if t.dim() != 2 or t.shape[0] != t.shape[1] or (n is not None and t.shape[0] != n):
+        raise ValueError(f"{name} must be square" + (f" of size {n}" if n is not None else ""))
+
+
+class Handle:
+    """One library handle (see mm_create).  Not thread safe."""
+
+    def __init__(self, mode: str | int = "auto", slices: int = 0, flags: int = 0, tune_path: str | None = None):
+        self._lib = lib()
+        m = _MODES[mode] if isinstance(mode, str) else int(mode)
+        self._tune = tune_path.encode() if tune_path else None
+        cfg = _Config(m, int(slices), int(flags), self._tune)
+        h = ctypes.c_void_p()
+        rc = self._lib.mm_create(ctypes.byref(h), ctypes.byref(cfg))
+        if rc != 0:
+            raise MMError(rc, "mm_create failed")
+        self._h = h
+
+    # -- helpers ---------------------------------------------------------------
+    def _raise(self, rc: int):
+        if rc != 0:
+            msg = self._lib.mm_last_error(self._h)
+            raise MMError(rc, msg.decode() if msg else "")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.mm_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- the product -----------------------------------------------------------
+    def gemm(self, A, B, C=None, stream=None):
+        """C = A.B on the device (asynchronous on `stream`)."""
+        import torch
+        _check_tensor(A, "A")
+        n = A.shape[0]
+        _check_tensor(B, "B", n)
+        if C is None:
+            C = torch.empty_like(A)
+        _check_tensor(C, "C", n)
+        self._raise(self._lib.mm_gemm(self._h, n, A.data_ptr(), B.data_ptr(), C.data_ptr(), _stream_ptr(stream)))
+        return C
+
+    def gemm_grouped(self, As: Sequence, Bs: Sequence, Cs: Sequence | None = None, stream=None):
+        import torch
+        count = len(As)
+        if len(Bs) != count or (Cs is not None and len(Cs) != count):
+            raise ValueError("As, Bs, Cs must have the same length")
+        if Cs is None:
+            Cs = [torch.empty_like(a) for a in As]
+        ns = (ctypes.c_int * count)()
+        pa = (ctypes.c_void_p * count)()
+        pb = (ctypes.c_void_p * count)()
+        pc = (ctypes.c_void_p * count)()
+        for i, (a, b, c) in enumerate(zip(As, Bs, Cs)):
+            _check_tensor(a, f"As[{i}]")
+            n = a.shape[0]
+            _check_tensor(b, f"Bs[{i}]", n)
+            _check_tensor(c, f"Cs[{i}]", n)
+            ns[i], pa[i], pb[i], pc[i] = n, a.data_ptr(), b.data_ptr(), c.data_ptr()
+        self._raise(self._lib.mm_gemm_grouped(self._h, count, ns, pa, pb, pc, _stream_ptr(stream)))
+        return Cs
+
+    def gemm_host(self, A, B, C=None, stream=None):
+        """End-to-end product on host (numpy) arrays: copy in, compute, copy out."""
+        import numpy as np
+        A = np.ascontiguousarray(A, dtype=np.float64)
+        B = np.ascontiguousarray(B, dtype=np.float64)
+        n = A.shape[0]
+        if A.shape != (n, n) or B.shape != (n, n):
+            raise ValueError("A and B must be square and of equal size")
+        if C is None:
+            C = np.empty((n, n), np.float64)
+        self._raise(self._lib.mm_gemm_host(self._h, n, A.ctypes.data, B.ctypes.data, C.ctypes.data,
+                                           _stream_ptr(stream)))
+        return C
+
+    def gemm_host_ptr(self, n: int, a_ptr: int, b_ptr: int, c_ptr: int, stream=None):
+        """mm_gemm_host on raw host pointers (e.g. pinned torch tensors)."""
+        self._raise(self._lib.mm_gemm_host(self._h, n, a_ptr, b_ptr, c_ptr, _stream_ptr(stream)))
+
+    def check(self, stream=None):
+        """Synchronises and raises MMError for any device-side error."""
+        self._raise(self._lib.mm_status_get(self._h, _stream_ptr(stream)))
+
+    def plan(self, n: int) -> tuple[int, int]:
+        form, s = ctypes.c_int(), ctypes.c_int()
+        self._raise(self._lib.mm_plan(self._h, n, ctypes.byref(form), ctypes.byref(s)))
+        return form.value, s.value
+
+    # -- steps of the emulation ------------------------------------------------
+    def split(self, M, by_columns: bool, slices: int, rows: int | None = None, ld: int | None = None, stream=None):
+        """Exponents (int32 [N]) and digit planes (int16 view of bf16, [s][rows][ld])."""
+        import torch
+        _check_tensor(M, "M")
+        n = M.shape[0]
+        rows = rows or -(-n // 128) * 128
+        ld = ld or -(-n // 64) * 64
+        exps = torch.empty(n, dtype=torch.int32, device=M.device)
+        digits = torch.empty((slices, rows, ld), dtype=torch.int16, device=M.device)
+        self._raise(self._lib.mm_split(self._h, n, M.data_ptr(), int(bool(by_columns)), slices, exps.data_ptr(),
+                                       digits.data_ptr(), rows, ld, _stream_ptr(stream)))
+        return exps, digits
+
+    def level_sums(self, n: int, slices: int, a_digits, b_digits, stream=None):
+        import torch
+        s, a_rows, ld = a_digits.shape
+        _, b_rows, ld2 = b_digits.shape
+        if ld != ld2 or s != slices or b_digits.shape[0] != slices:
+            raise ValueError("digit planes disagree")
+        levels = torch.empty((slices, n, n), dtype=torch.int32, device=a_digits.device)
+        self._raise(self._lib.mm_level_sums(self._h, n, slices, a_digits.data_ptr(), a_rows, b_digits.data_ptr(),
+                                            b_rows, ld, levels.data_ptr(), _stream_ptr(stream)))
+        return levels
+
+    def recombine(self, n: int, slices: int, levels, a_exps, b_exps, stream=None):
+        import torch
+        C = torch.empty((n, n), dtype=torch.float64, device=levels.device)
+        self._raise(self._lib.mm_recombine(self._h, n, slices, levels.data_ptr(), a_exps.data_ptr(),
+                                           b_exps.data_ptr(), C.data_ptr(), _stream_ptr(stream)))
+        return C

@@ -1,0 +1,747 @@
+// mm_api.cu -- host runtime and C ABI (see include/mm.h).
+//
+// The handle owns: a device status word, a grow-only device arena for the
+// emulation workspace (digit planes, exponents, per-CTA scratch, problem
+// tables, tensor maps), device buffers for the host-to-host entry point, a
+// private stream for CUDA-graph capture, and a cache of instantiated graphs
+// for grouped calls keyed by their full signature.
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <fstream>
+#include <map>
+#include <sstream>
+#include <string>
+#include <vector>
+
+#include "launch.cuh"
+
+using mmk::Problem;
+
+namespace {
+
+constexpr size_t kAlign = 256;
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+int round_up(int x, int a) { return (x + a - 1) / a * a; }
+
+// ---- driver entry point for tensor-map encoding (no -lcuda link needed) ----
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn get_encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  }
+  return fn;
+}
+
+// 2-D map over `rows` rows of `ld` bf16 elements, box = 64 x box_rows, 128-byte swizzle.
+bool make_plane_map(CUtensorMap* map, const void* base, int ld, long rows, int box_rows) {
+  EncodeTiledFn enc = get_encode_fn();
+  if (!enc) return false;
+  cuuint64_t dims[2] = {static_cast<cuuint64_t>(ld), static_cast<cuuint64_t>(rows)};
+  cuuint64_t strides[1] = {static_cast<cuuint64_t>(ld) * 2};
+  cuuint32_t box[2] = {64, static_cast<cuuint32_t>(box_rows)};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+struct Plan {
+  int form;    // 0 native, 1 emulation
+  int slices;  // emulation digit count
+  int bn;      // emulation tile width (128 or 256)
+};
+
+struct GraphEntry {
+  cudaGraphExec_t exec = nullptr;
+  void* table_mem = nullptr;  // device memory owned by this entry (problem tables, maps)
+};
+
+}  // namespace
+
+struct mm_handle_s {
+  int device = 0;
+  int num_sms = 148;
+  mm_config cfg{};
+  std::string tune_path;
+  std::string last_error;
+  uint64_t timeout_ns = 2000000000ull;
+  int* d_status = nullptr;
+  // grow-only arena for the emulation workspace
+  void* arena = nullptr;
+  size_t arena_cap = 0;
+  // host-to-host entry point buffers
+  double* e2e = nullptr;
+  size_t e2e_cap = 0;
+  // grouped calls
+  cudaStream_t cap_stream = nullptr;
+  std::map<std::vector<long long>, GraphEntry> graphs;
+  void* grp_table = nullptr;  // non-graph grouped path: device table
+  size_t grp_table_cap = 0;
+  void* grp_pinned = nullptr;
+  size_t grp_pinned_cap = 0;
+  cudaEvent_t grp_event = nullptr;
+  // autotune table: N upper bound -> plan
+  std::vector<std::pair<int, Plan>> tune;
+};
+
+namespace {
+
+mm_status fail(mm_handle h, mm_status st, const std::string& msg) {
+  if (h) h->last_error = msg;
+  return st;
+}
+
+mm_status cuda_fail(mm_handle h, cudaError_t e, const char* what) {
+  return fail(h, MM_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define MM_CUDA(h, call)                                   \
+  do {                                                     \
+    cudaError_t e_ = (call);                               \
+    if (e_ != cudaSuccess) return cuda_fail((h), e_, #call); \
+  } while (0)
+
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+// Built-in plan table (overridden by a tune file): below the crossover the
+// native path is as fast and exact enough, above it the emulation wins.
+void default_tune(mm_handle h) {
+  h->tune.clear();
+  h->tune.push_back({255, Plan{0, 7, 128}});
+  h->tune.push_back({1024, Plan{1, 7, 128}});
+  h->tune.push_back({1 << 30, Plan{1, 7, 256}});
+}
+
+// Tune file: lines "max_n form slices bn" ('#' starts a comment).
+bool load_tune(mm_handle h, const std::string& path) {
+  std::ifstream in(path);
+  if (!in) return false;
+  std::vector<std::pair<int, Plan>> rows;
+  std::string line;
+  while (std::getline(in, line)) {
+    const size_t hash = line.find('#');
+    if (hash != std::string::npos) line.resize(hash);
+    std::istringstream ss(line);
+    long maxn;
+    Plan p;
+    if (!(ss >> maxn >> p.form >> p.slices >> p.bn)) continue;
+    if ((p.form != 0 && p.form != 1) || p.slices < 1 || p.slices > 8 || (p.bn != 128 && p.bn != 256)) return false;
+    rows.push_back({static_cast<int>(std::min<long>(maxn, 1 << 30)), p});
+  }
+  if (rows.empty()) return false;
+  std::sort(rows.begin(), rows.end(), [](const auto& a, const auto& b) { return a.first < b.first; });
+  h->tune = rows;
+  return true;
+}
+
+Plan plan_for(mm_handle h, int n) {
+  Plan p = h->tune.back().second;
+  for (const auto& r : h->tune)
+    if (n <= r.first) {
+      p = r.second;
+      break;
+    }
+  if (h->cfg.mode == MM_NATIVE_FP64) p.form = 0;
+  if (h->cfg.mode == MM_EMU_BF16) {
+    p.form = 1;
+    if (p.bn != 128 && p.bn != 256) p.bn = 128;
+  }
+  if (h->cfg.slices > 0) p.slices = h->cfg.slices;
+  if (p.form == 1 && n < 256) p.bn = 128;
+  return p;
+}
+
+int emu_grid(mm_handle h, int total_tiles) { return std::max(1, std::min(total_tiles, h->num_sms)); }
+
+// Largest number of digit pairs whose products can share one int32 sum.
+int max_pairs_for(int n) {
+  const long long per_pair = static_cast<long long>(n) * (1 << 14);  // |sum_j d d| <= n 2^14
+  if (per_pair <= 0) return 64;
+  const long long m = (2147483647LL) / per_pair;
+  return static_cast<int>(std::min<long long>(m, 64));
+}
+
+// ---- workspace layout for a list of emulated problems -----------------------
+struct Arena {
+  size_t off = 0;
+  size_t take(size_t bytes) {
+    const size_t at = off;
+    off = align_up(off + bytes, kAlign);
+    return at;
+  }
+};
+
+mm_status ensure_arena(mm_handle h, size_t bytes) {
+  if (bytes <= h->arena_cap) return MM_OK;
+  // Replayed graphs point into the old arena: drop them first.
+  for (auto& kv : h->graphs) {
+    if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+    if (kv.second.table_mem) cudaFree(kv.second.table_mem);
+  }
+  h->graphs.clear();
+  if (h->arena) cudaFree(h->arena);  // implicit device synchronisation
+  h->arena = nullptr;
+  h->arena_cap = 0;
+  const size_t cap = align_up(bytes + bytes / 8, 1 << 20);
+  if (cudaMalloc(&h->arena, cap) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(h, MM_ERR_NOMEM, "workspace allocation of " + std::to_string(cap) + " bytes failed");
+  }
+  h->arena_cap = cap;
+  return MM_OK;
+}
+
+// One launch group of the emulation: problems sharing (s, bn).
+struct EmuGroup {
+  int s = 7, bn = 128, grid = 1;
+  mmk::SegTable seg{};
+  std::vector<Problem> ps;
+  std::vector<int> max_off;        // offset of problem p in the maxbits arrays
+  std::vector<CUtensorMap> maps;   // 2 per problem
+  int total_tiles = 0, total_split = 0, max_rows = 0;
+  // byte offsets inside the group's region of the arena
+  size_t amax = 0, bmax = 0, scratch = 0, bytes = 0;
+  char* base = nullptr;
+};
+
+// Sizes the group's workspace; with `base` set, also points the problems into it.
+mm_status layout_group(mm_handle h, EmuGroup& g, char* base) {
+  Arena ar;
+  g.total_tiles = g.total_split = g.max_rows = 0;
+  int maxn = 0;
+  g.max_off.assign(g.ps.size(), 0);
+  for (size_t i = 0; i < g.ps.size(); ++i) {
+    Problem& p = g.ps[i];
+    const int n = p.n;
+    maxn = std::max(maxn, n);
+    p.m_pad = round_up(n, 128);
+    p.n_pad = round_up(n, g.bn);
+    p.k_pad = round_up(n, 64);
+    p.tiles_m = p.m_pad / 128;
+    p.tiles_n = p.n_pad / g.bn;
+    p.tile_begin = g.total_tiles;
+    g.total_tiles += p.tiles_m * p.tiles_n;
+    p.split_begin = g.total_split;
+    g.total_split += mmk::split_tiles(p);
+    const size_t a_sl = ar.take(static_cast<size_t>(g.s) * p.m_pad * p.k_pad * 2);
+    const size_t b_sl = ar.take(static_cast<size_t>(g.s) * p.n_pad * p.k_pad * 2);
+    const size_t ae = ar.take(sizeof(int) * n);
+    const size_t be = ar.take(sizeof(int) * n);
+    if (base) {
+      p.a_slices = reinterpret_cast<uint16_t*>(base + a_sl);
+      p.b_slices = reinterpret_cast<uint16_t*>(base + b_sl);
+      p.a_exp = reinterpret_cast<int*>(base + ae);
+      p.b_exp = reinterpret_cast<int*>(base + be);
+    }
+    g.max_off[i] = g.max_rows;
+    g.max_rows += n;
+  }
+  if (!mmk::emu_build_segments(g.s, max_pairs_for(maxn), &g.seg))
+    return fail(h, MM_ERR_UNSUPPORTED, "too many accumulation segments for this size");
+  g.grid = emu_grid(h, g.total_tiles);
+  g.amax = ar.take(sizeof(uint64_t) * g.max_rows);
+  g.bmax = ar.take(sizeof(uint64_t) * g.max_rows);
+  g.scratch = ar.take(static_cast<size_t>(g.grid) * g.seg.nseg * 128 * g.bn * sizeof(int32_t));
+  g.bytes = ar.off;
+  g.base = base;
+  if (base) {
+    g.maps.resize(2 * g.ps.size());
+    for (size_t i = 0; i < g.ps.size(); ++i) {
+      const Problem& p = g.ps[i];
+      if (!make_plane_map(&g.maps[2 * i], p.a_slices, p.k_pad, static_cast<long>(g.s) * p.m_pad, 128) ||
+          !make_plane_map(&g.maps[2 * i + 1], p.b_slices, p.k_pad, static_cast<long>(g.s) * p.n_pad, g.bn))
+        return fail(h, MM_ERR_CUDA, "cuTensorMapEncodeTiled failed");
+    }
+  }
+  return MM_OK;
+}
+
+// Enqueues the emulated path of group g: zero the maxima, scale+split, slice
+// products with fused recombination.  With d_table == nullptr the group must
+// hold one problem, passed by value; otherwise d_table/d_maps/d_max_off are
+// device copies of g.ps, g.maps and g.max_off.
+mm_status run_group(mm_handle h, const EmuGroup& g, const Problem* d_table, const CUtensorMap* d_maps,
+                    const int* d_max_off, cudaStream_t stream) {
+  if (g.total_tiles == 0) return MM_OK;
+  uint64_t* amax = reinterpret_cast<uint64_t*>(g.base + g.amax);
+  uint64_t* bmax = reinterpret_cast<uint64_t*>(g.base + g.bmax);
+  MM_CUDA(h, cudaMemsetAsync(amax, 0, sizeof(uint64_t) * g.max_rows, stream));
+  MM_CUDA(h, cudaMemsetAsync(bmax, 0, sizeof(uint64_t) * g.max_rows, stream));
+  const bool single = d_table == nullptr;
+  MM_CUDA(h, mmk::split_launch(d_table, single ? &g.ps[0] : nullptr, static_cast<int>(g.ps.size()), g.total_split,
+                               g.s, amax, bmax, single ? nullptr : d_max_off, h->d_status, stream));
+  mmk::EmuArgs a{};
+  a.table = d_table;
+  if (single) a.single = g.ps[0];
+  a.maps = d_maps;
+  a.count = static_cast<int>(g.ps.size());
+  a.total_tiles = g.total_tiles;
+  a.s = g.s;
+  a.seg = g.seg;
+  a.scratch = reinterpret_cast<int32_t*>(g.base + g.scratch);
+  a.levels_out = nullptr;
+  a.status = h->d_status;
+  a.timeout_ns = h->timeout_ns;
+  const cudaError_t le = mmk::emu_gemm_launch(g.bn, &g.maps[0], &g.maps[1], a, g.grid, stream);
+  if (le != cudaSuccess) {
+    char info[512];
+    mmk::emu_kernel_info(g.bn, info, sizeof(info));
+    return fail(h, MM_ERR_CUDA, std::string("slice-product launch: ") + cudaGetErrorString(le) + " " + info);
+  }
+  return MM_OK;
+}
+
+mm_status check_emu_size(mm_handle h, int n, int s) {
+  if (s < 1 || s > 8) return fail(h, MM_ERR_UNSUPPORTED, "slices must be in 1..8");
+  if (n > 131071) return fail(h, MM_ERR_UNSUPPORTED, "emulation supports N <= 131071 (one pair per int32 sum)");
+  return MM_OK;
+}
+
+// Single emulated problem: workspace, maps, launches (no device table).
+mm_status emu_single(mm_handle h, const Problem& p, int s, int bn, cudaStream_t stream) {
+  mm_status st = check_emu_size(h, p.n, s);
+  if (st != MM_OK) return st;
+  EmuGroup g;
+  g.s = s;
+  g.bn = bn;
+  g.ps.push_back(p);
+  st = layout_group(h, g, nullptr);
+  if (st != MM_OK) return st;
+  st = ensure_arena(h, g.bytes);
+  if (st != MM_OK) return st;
+  st = layout_group(h, g, static_cast<char*>(h->arena));
+  if (st != MM_OK) return st;
+  return run_group(h, g, nullptr, nullptr, nullptr, stream);
+}
+
+mm_status native_single(mm_handle h, Problem p, cudaStream_t stream) {
+  mmk::native_fill_tiles(p);
+  p.tile_begin = 0;
+  MM_CUDA(h, mmk::native_launch(nullptr, &p, 1, p.tiles_m * p.tiles_n, stream));
+  return MM_OK;
+}
+
+}  // namespace
+
+// ============================================================================
+// C ABI
+// ============================================================================
+extern "C" {
+
+mm_status mm_create(mm_handle* out, const mm_config* cfg) {
+  if (!out) return MM_ERR_INVALID;
+  *out = nullptr;
+  mm_handle h = new (std::nothrow) mm_handle_s();
+  if (!h) return MM_ERR_NOMEM;
+  h->cfg.mode = MM_AUTO;
+  h->cfg.slices = 0;
+  h->cfg.flags = 0;
+  h->cfg.tune_path = nullptr;
+  if (cfg) {
+    h->cfg = *cfg;
+    if (cfg->tune_path) h->tune_path = cfg->tune_path;
+    h->cfg.tune_path = nullptr;
+  }
+  if (h->cfg.mode != MM_NATIVE_FP64 && h->cfg.mode != MM_EMU_BF16 && h->cfg.mode != MM_AUTO) {
+    delete h;
+    return MM_ERR_INVALID;
+  }
+  if (h->cfg.slices < 0 || h->cfg.slices > 8) {
+    delete h;
+    return MM_ERR_UNSUPPORTED;
+  }
+  if (const char* t = std::getenv("MM_TIMEOUT_MS")) {
+    const long ms = std::atol(t);
+    if (ms > 0) h->timeout_ns = static_cast<uint64_t>(ms) * 1000000ull;
+  }
+  default_tune(h);
+  if (!h->tune_path.empty() && !load_tune(h, h->tune_path)) {
+    delete h;
+    return MM_ERR_INVALID;
+  }
+  if (cudaGetDevice(&h->device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess ||
+      cudaMalloc(&h->d_status, sizeof(int)) != cudaSuccess || cudaMemset(h->d_status, 0, sizeof(int)) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->grp_event, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    if (h->d_status) cudaFree(h->d_status);
+    if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+    delete h;
+    return MM_ERR_CUDA;
+  }
+  *out = h;
+  return MM_OK;
+}
+
+mm_status mm_destroy(mm_handle h) {
+  if (!h) return MM_ERR_INVALID;
+  cudaDeviceSynchronize();
+  for (auto& kv : h->graphs) {
+    if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+    if (kv.second.table_mem) cudaFree(kv.second.table_mem);
+  }
+  if (h->arena) cudaFree(h->arena);
+  if (h->e2e) cudaFree(h->e2e);
+  if (h->grp_table) cudaFree(h->grp_table);
+  if (h->grp_pinned) cudaFreeHost(h->grp_pinned);
+  if (h->grp_event) cudaEventDestroy(h->grp_event);
+  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  if (h->d_status) cudaFree(h->d_status);
+  delete h;
+  return MM_OK;
+}
+
+const char* mm_last_error(mm_handle h) { return h ? h->last_error.c_str() : "invalid handle"; }
+
+mm_status mm_plan(mm_handle h, int N, int* form, int* slices) {
+  if (!h || N < 0) return MM_ERR_INVALID;
+  const Plan p = plan_for(h, N);
+  if (form) *form = p.form;
+  if (slices) *slices = p.slices;
+  return MM_OK;
+}
+
+mm_status mm_status_get(mm_handle h, void* stream) {
+  if (!h) return MM_ERR_INVALID;
+  MM_CUDA(h, cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
+  int st = 0;
+  MM_CUDA(h, cudaMemcpy(&st, h->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+  if (st != 0) {
+    MM_CUDA(h, cudaMemset(h->d_status, 0, sizeof(int)));
+    return fail(h, static_cast<mm_status>(st), st == MM_ERR_TIMEOUT ? "a device-side wait timed out"
+                                             : st == MM_ERR_NONFINITE ? "non-finite input to the emulation"
+                                                                      : "device error");
+  }
+  return MM_OK;
+}
+
+mm_status mm_gemm(mm_handle h, int N, const double* A, const double* B, double* C, void* stream) {
+  if (!h) return MM_ERR_INVALID;
+  if (N < 0) return fail(h, MM_ERR_INVALID, "N must be >= 0");
+  if (N == 0) return MM_OK;
+  if (!A || !B || !C) return fail(h, MM_ERR_INVALID, "null matrix pointer");
+  if (!aligned16(A) || !aligned16(B) || !aligned16(C)) return fail(h, MM_ERR_INVALID, "pointers must be 16-byte aligned");
+  const size_t bytes = static_cast<size_t>(N) * N * sizeof(double);
+  auto overlap = [bytes](const void* x, const void* y) {
+    const char* a = static_cast<const char*>(x);
+    const char* b = static_cast<const char*>(y);
+    return a < b + bytes && b < a + bytes;
+  };
+  if (overlap(C, A) || overlap(C, B)) return fail(h, MM_ERR_INVALID, "C must not overlap A or B");
+  Problem p{};
+  p.A = A;
+  p.B = B;
+  p.C = C;
+  p.n = N;
+  const Plan plan = plan_for(h, N);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (plan.form == 0) return native_single(h, p, s);
+  return emu_single(h, p, plan.slices, plan.bn, s);
+}
+
+mm_status mm_gemm_host(mm_handle h, int N, const double* A_host, const double* B_host, double* C_host,
+                       void* stream) {
+  if (!h) return MM_ERR_INVALID;
+  if (N < 0 || (N > 0 && (!A_host || !B_host || !C_host))) return fail(h, MM_ERR_INVALID, "bad arguments");
+  if (N == 0) return MM_OK;
+  const size_t elems = static_cast<size_t>(N) * N;
+  const size_t need = 3 * align_up(elems * sizeof(double), kAlign);
+  if (need > h->e2e_cap) {
+    if (h->e2e) cudaFree(h->e2e);
+    h->e2e = nullptr;
+    h->e2e_cap = 0;
+    if (cudaMalloc(&h->e2e, need) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(h, MM_ERR_NOMEM, "device buffers for the host entry point");
+    }
+    h->e2e_cap = need;
+  }
+  const size_t stride = align_up(elems * sizeof(double), kAlign) / sizeof(double);
+  double* dA = h->e2e;
+  double* dB = h->e2e + stride;
+  double* dC = h->e2e + 2 * stride;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  MM_CUDA(h, cudaMemcpyAsync(dA, A_host, elems * sizeof(double), cudaMemcpyHostToDevice, s));
+  MM_CUDA(h, cudaMemcpyAsync(dB, B_host, elems * sizeof(double), cudaMemcpyHostToDevice, s));
+  mm_status st = mm_gemm(h, N, dA, dB, dC, stream);
+  if (st != MM_OK) return st;
+  MM_CUDA(h, cudaMemcpyAsync(C_host, dC, elems * sizeof(double), cudaMemcpyDeviceToHost, s));
+  MM_CUDA(h, cudaStreamSynchronize(s));
+  return MM_OK;
+}
+
+mm_status mm_gemm_grouped(mm_handle h, int count, const int* Ns, const double* const* As, const double* const* Bs,
+                          double* const* Cs, void* stream) {
+  if (!h) return MM_ERR_INVALID;
+  if (count < 0) return fail(h, MM_ERR_INVALID, "count must be >= 0");
+  if (count == 0) return MM_OK;
+  if (!Ns || !As || !Bs || !Cs) return fail(h, MM_ERR_INVALID, "null array");
+  for (int i = 0; i < count; ++i) {
+    if (Ns[i] < 0) return fail(h, MM_ERR_INVALID, "negative N in group");
+    if (Ns[i] > 0 && (!As[i] || !Bs[i] || !Cs[i])) return fail(h, MM_ERR_INVALID, "null matrix in group");
+    if (Ns[i] > 0 && (!aligned16(As[i]) || !aligned16(Bs[i]) || !aligned16(Cs[i])))
+      return fail(h, MM_ERR_INVALID, "group pointers must be 16-byte aligned");
+  }
+  cudaStream_t user = static_cast<cudaStream_t>(stream);
+
+  // Partition: native problems, and emulated problems by (slices, bn).
+  std::vector<Problem> nat;
+  std::map<std::pair<int, int>, std::vector<Problem>> emu;
+  for (int i = 0; i < count; ++i) {
+    if (Ns[i] == 0) continue;
+    Problem p{};
+    p.A = As[i];
+    p.B = Bs[i];
+    p.C = Cs[i];
+    p.n = Ns[i];
+    const Plan pl = plan_for(h, p.n);
+    if (pl.form == 0) {
+      nat.push_back(p);
+    } else {
+      mm_status st = check_emu_size(h, p.n, pl.slices);
+      if (st != MM_OK) return st;
+      emu[{pl.slices, pl.bn}].push_back(p);
+    }
+  }
+  int nat_tiles = 0;
+  for (Problem& p : nat) {
+    mmk::native_fill_tiles(p);
+    p.tile_begin = nat_tiles;
+    nat_tiles += p.tiles_m * p.tiles_n;
+  }
+
+  // Workspace: the emulation groups are laid out one after another in the arena.
+  std::vector<EmuGroup> groups;
+  std::vector<size_t> group_off;
+  size_t arena_need = 0;
+  for (auto& kv : emu) {
+    EmuGroup g;
+    g.s = kv.first.first;
+    g.bn = kv.first.second;
+    g.ps = kv.second;
+    mm_status st = layout_group(h, g, nullptr);
+    if (st != MM_OK) return st;
+    group_off.push_back(arena_need);
+    arena_need = align_up(arena_need + g.bytes, kAlign);
+    groups.push_back(std::move(g));
+  }
+  if (arena_need) {
+    mm_status st = ensure_arena(h, arena_need);
+    if (st != MM_OK) return st;
+  }
+  for (size_t gi = 0; gi < groups.size(); ++gi) {
+    mm_status st = layout_group(h, groups[gi], static_cast<char*>(h->arena) + group_off[gi]);
+    if (st != MM_OK) return st;
+  }
+
+  // Device-side tables: [native problems][per group: problems, maps, max offsets].
+  Arena tab;
+  const size_t off_nat = tab.take(sizeof(Problem) * std::max<size_t>(nat.size(), 1));
+  std::vector<size_t> off_tab, off_maps, off_mo;
+  for (const EmuGroup& g : groups) {
+    off_tab.push_back(tab.take(sizeof(Problem) * g.ps.size()));
+    off_maps.push_back(tab.take(sizeof(CUtensorMap) * g.maps.size()));
+    off_mo.push_back(tab.take(sizeof(int) * g.max_off.size()));
+  }
+  const size_t tab_bytes = tab.off;
+  std::vector<char> host_tab(tab_bytes, 0);
+  if (!nat.empty()) std::memcpy(host_tab.data() + off_nat, nat.data(), sizeof(Problem) * nat.size());
+  for (size_t gi = 0; gi < groups.size(); ++gi) {
+    const EmuGroup& g = groups[gi];
+    std::memcpy(host_tab.data() + off_tab[gi], g.ps.data(), sizeof(Problem) * g.ps.size());
+    std::memcpy(host_tab.data() + off_maps[gi], g.maps.data(), sizeof(CUtensorMap) * g.maps.size());
+    std::memcpy(host_tab.data() + off_mo[gi], g.max_off.data(), sizeof(int) * g.max_off.size());
+  }
+
+  auto launch_all = [&](char* dtab, cudaStream_t s) -> mm_status {
+    if (!nat.empty()) {
+      MM_CUDA(h, mmk::native_launch(reinterpret_cast<Problem*>(dtab + off_nat), nullptr,
+                                    static_cast<int>(nat.size()), nat_tiles, s));
+    }
+    for (size_t gi = 0; gi < groups.size(); ++gi) {
+      mm_status st = run_group(h, groups[gi], reinterpret_cast<Problem*>(dtab + off_tab[gi]),
+                               reinterpret_cast<CUtensorMap*>(dtab + off_maps[gi]),
+                               reinterpret_cast<int*>(dtab + off_mo[gi]), s);
+      if (st != MM_OK) return st;
+    }
+    return MM_OK;
+  };
+
+  const bool use_graph = (h->cfg.flags & MM_FLAG_NO_GRAPH) == 0;
+  if (!use_graph) {
+    if (tab_bytes > h->grp_table_cap) {
+      if (h->grp_table) cudaFree(h->grp_table);
+      if (h->grp_pinned) cudaFreeHost(h->grp_pinned);
+      h->grp_table = nullptr;
+      h->grp_pinned = nullptr;
+      h->grp_table_cap = 0;
+      if (cudaMalloc(&h->grp_table, tab_bytes) != cudaSuccess ||
+          cudaMallocHost(&h->grp_pinned, tab_bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(h, MM_ERR_NOMEM, "grouped table buffers");
+      }
+      h->grp_table_cap = tab_bytes;
+    }
+    MM_CUDA(h, cudaEventSynchronize(h->grp_event));  // previous upload done with the staging buffer
+    std::memcpy(h->grp_pinned, host_tab.data(), tab_bytes);
+    MM_CUDA(h, cudaMemcpyAsync(h->grp_table, h->grp_pinned, tab_bytes, cudaMemcpyHostToDevice, user));
+    MM_CUDA(h, cudaEventRecord(h->grp_event, user));
+    return launch_all(static_cast<char*>(h->grp_table), user);
+  }
+
+  std::vector<long long> key;
+  key.reserve(4 * count + 4);
+  key.push_back(count);
+  key.push_back(h->cfg.mode);
+  key.push_back(h->cfg.slices);
+  key.push_back(static_cast<long long>(reinterpret_cast<uintptr_t>(h->arena)));
+  for (int i = 0; i < count; ++i) {
+    key.push_back(Ns[i]);
+    key.push_back(static_cast<long long>(reinterpret_cast<uintptr_t>(As[i])));
+    key.push_back(static_cast<long long>(reinterpret_cast<uintptr_t>(Bs[i])));
+    key.push_back(static_cast<long long>(reinterpret_cast<uintptr_t>(Cs[i])));
+  }
+  auto it = h->graphs.find(key);
+  if (it == h->graphs.end()) {
+    if (h->graphs.size() >= 32) {
+      for (auto& kv : h->graphs) {
+        if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+        if (kv.second.table_mem) cudaFree(kv.second.table_mem);
+      }
+      h->graphs.clear();
+    }
+    GraphEntry ge;
+    if (cudaMalloc(&ge.table_mem, std::max<size_t>(tab_bytes, 256)) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(h, MM_ERR_NOMEM, "grouped table");
+    }
+    if (cudaMemcpy(ge.table_mem, host_tab.data(), tab_bytes, cudaMemcpyHostToDevice) != cudaSuccess) {
+      cudaFree(ge.table_mem);
+      return fail(h, MM_ERR_CUDA, "grouped table upload");
+    }
+    cudaGraph_t graph = nullptr;
+    MM_CUDA(h, cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+    mm_status st = launch_all(static_cast<char*>(ge.table_mem), h->cap_stream);
+    cudaError_t ce = cudaStreamEndCapture(h->cap_stream, &graph);
+    if (st != MM_OK || ce != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      cudaFree(ge.table_mem);
+      cudaGetLastError();
+      return st != MM_OK ? st : cuda_fail(h, ce, "graph capture");
+    }
+    ce = cudaGraphInstantiate(&ge.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ce != cudaSuccess) {
+      cudaFree(ge.table_mem);
+      return cuda_fail(h, ce, "graph instantiate");
+    }
+    it = h->graphs.emplace(key, ge).first;
+  }
+  MM_CUDA(h, cudaGraphLaunch(it->second.exec, user));
+  return MM_OK;
+}
+
+mm_status mm_split(mm_handle h, int N, const double* M, int by_columns, int slices, int* exps, uint16_t* digits,
+                   int rows, int ld, void* stream) {
+  if (!h) return MM_ERR_INVALID;
+  if (N <= 0 || !M || !exps || !digits || rows < N || ld < N || rows % 128 || ld % 64 || !aligned16(digits))
+    return fail(h, MM_ERR_INVALID, "mm_split: bad arguments (rows % 128, ld % 64, 16-byte aligned digits)");
+  if (slices < 1 || slices > 8) return fail(h, MM_ERR_UNSUPPORTED, "slices must be in 1..8");
+  Problem p{};
+  p.n = N;
+  p.k_pad = ld;
+  if (by_columns) {
+    p.B = M;
+    p.b_slices = digits;
+    p.b_exp = exps;
+    p.n_pad = rows;
+    p.m_pad = 0;
+  } else {
+    p.A = M;
+    p.a_slices = digits;
+    p.a_exp = exps;
+    p.m_pad = rows;
+    p.n_pad = 0;
+  }
+  const size_t need = 2 * align_up(sizeof(uint64_t) * N, kAlign);
+  mm_status st = ensure_arena(h, need);
+  if (st != MM_OK) return st;
+  uint64_t* mx = static_cast<uint64_t*>(h->arena);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  MM_CUDA(h, cudaMemsetAsync(mx, 0, sizeof(uint64_t) * N, s));
+  MM_CUDA(h, mmk::split_launch(nullptr, &p, 1, mmk::split_tiles(p), slices, mx, mx, nullptr, h->d_status, s));
+  return MM_OK;
+}
+
+mm_status mm_level_sums(mm_handle h, int N, int slices, const uint16_t* a_digits, int a_rows,
+                        const uint16_t* b_digits, int b_rows, int ld, int32_t* levels, void* stream) {
+  if (!h) return MM_ERR_INVALID;
+  if (N <= 0 || !a_digits || !b_digits || !levels || a_rows < N || b_rows < N || ld < N || a_rows % 128 ||
+      b_rows % 128 || ld % 64)
+    return fail(h, MM_ERR_INVALID, "mm_level_sums: bad arguments");
+  if (slices < 1 || slices > 8) return fail(h, MM_ERR_UNSUPPORTED, "slices must be in 1..8");
+  if (static_cast<long long>(slices) * N * (1 << 14) >= (1LL << 31))
+    return fail(h, MM_ERR_UNSUPPORTED, "level sums would not fit int32");
+  const int bn = (b_rows % 256 == 0 && N > 128) ? 256 : 128;
+  Problem p{};
+  p.n = N;
+  p.a_slices = const_cast<uint16_t*>(a_digits);
+  p.b_slices = const_cast<uint16_t*>(b_digits);
+  p.m_pad = a_rows;
+  p.n_pad = b_rows;
+  p.k_pad = ld;
+  p.tiles_m = (N + 127) / 128;
+  p.tiles_n = (N + bn - 1) / bn;
+  p.tile_begin = 0;
+  std::vector<CUtensorMap> maps(2);
+  if (!make_plane_map(&maps[0], a_digits, ld, static_cast<long>(slices) * a_rows, 128) ||
+      !make_plane_map(&maps[1], b_digits, ld, static_cast<long>(slices) * b_rows, bn))
+    return fail(h, MM_ERR_CUDA, "cuTensorMapEncodeTiled failed");
+  mmk::EmuArgs a{};
+  a.single = p;
+  a.count = 1;
+  a.total_tiles = p.tiles_m * p.tiles_n;
+  a.s = slices;
+  if (!mmk::emu_build_segments(slices, slices, &a.seg)) return fail(h, MM_ERR_UNSUPPORTED, "segments");
+  a.scratch = nullptr;
+  a.levels_out = levels;
+  a.status = h->d_status;
+  a.timeout_ns = h->timeout_ns;
+  const cudaError_t le = mmk::emu_gemm_launch(bn, &maps[0], &maps[1], a, emu_grid(h, a.total_tiles),
+                                              static_cast<cudaStream_t>(stream));
+  if (le != cudaSuccess) {
+    char info[512];
+    mmk::emu_kernel_info(bn, info, sizeof(info));
+    return fail(h, MM_ERR_CUDA, std::string("slice-product launch: ") + cudaGetErrorString(le) + " " + info);
+  }
+  return MM_OK;
+}
+
+mm_status mm_recombine(mm_handle h, int N, int slices, const int32_t* levels, const int* a_exps, const int* b_exps,
+                       double* C, void* stream) {
+  if (!h) return MM_ERR_INVALID;
+  if (N <= 0 || !levels || !a_exps || !b_exps || !C) return fail(h, MM_ERR_INVALID, "mm_recombine: bad arguments");
+  if (slices < 1 || slices > 8) return fail(h, MM_ERR_UNSUPPORTED, "slices must be in 1..8");
+  MM_CUDA(h, mmk::recombine_launch(N, slices, levels, a_exps, b_exps, C, static_cast<cudaStream_t>(stream)));
+  return MM_OK;
+}
+
+}  // extern "C"

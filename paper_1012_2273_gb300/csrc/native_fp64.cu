@@ -1,0 +1,172 @@
+// native_fp64.cu -- the plain form: C = A.B in FP64 on the FP64 tensor path.
+//
+// The product is the one Alg. 1 (Sec. 3.1) defines: c(i,k) = sum_j a(i,j) b(j,k),
+// starting from 0.0.  The paper splits the rows of A among workers (Alg. 2-4);
+// here the split is into 64 x 64 tiles of C, one CTA each, over all problems
+// of a grouped call.  Each CTA streams 64 x 16 panels of A and 16 x 64 panels
+// of B through a double-buffered shared-memory ring (cp.async, 8-byte copies,
+// so any N works: rows of an odd-N matrix are not 16-byte aligned, which rules
+// out TMA tiles), and four warps run mma.sync m16n8k4 f64 on 32 x 32 sub-tiles.
+// Each output is a chain of FP64 fused multiply-adds; the order differs from
+// the paper's left-to-right sum, so results agree with it to within
+// gamma_N |A||B| rather than bit for bit (exactly, when all partial sums are
+// exact, e.g. for small-integer inputs).
+#include "launch.cuh"
+
+namespace mmk {
+
+constexpr int NT_BM = 64;
+constexpr int NT_BN = 64;
+constexpr int NT_BK = 16;
+constexpr int NT_LD = 68;  // padded stride (doubles): conflict-free fragment loads
+constexpr int NT_THREADS = 128;
+
+struct NativeArgs {
+  const Problem* table;  // device problem table (grouped) or nullptr
+  Problem single;        // used when table == nullptr
+  int count;
+};
+
+__device__ __forceinline__ void cp_async_8(void* smem, const void* gmem, bool valid) {
+  const unsigned src_bytes = valid ? 8u : 0u;  // 0 bytes read -> zero fill
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(smem_u32(smem)), "l"(gmem), "r"(src_bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+__device__ __forceinline__ void dmma_16x8x4(double (&c)[4], double a0, double a1, double b0) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k4.row.col.f64.f64.f64.f64 {%0,%1,%2,%3}, {%4,%5}, {%6}, {%0,%1,%2,%3};"
+      : "+d"(c[0]), "+d"(c[1]), "+d"(c[2]), "+d"(c[3])
+      : "d"(a0), "d"(a1), "d"(b0));
+}
+
+__global__ void __launch_bounds__(NT_THREADS) native_fp64_kernel(const __grid_constant__ NativeArgs args) {
+  __shared__ __align__(16) double As[2][NT_BK][NT_LD];  // [k][m]
+  __shared__ __align__(16) double Bs[2][NT_BK][NT_LD];  // [k][n]
+
+  const int tile = blockIdx.x;
+  const Problem* P;
+  if (args.table) {
+    P = &args.table[find_problem(args.table, args.count, tile)];
+  } else {
+    P = &args.single;
+  }
+  const int n = P->n;
+  const int local = tile - P->tile_begin;
+  if (n <= 0 || local < 0 || local >= P->tiles_m * P->tiles_n) return;
+  const int m0 = (local / P->tiles_n) * NT_BM;
+  const int n0 = (local % P->tiles_n) * NT_BN;
+  const double* __restrict__ A = P->A;
+  const double* __restrict__ B = P->B;
+  double* __restrict__ C = P->C;
+
+  const int tid = threadIdx.x;
+  const int warp = tid >> 5, lane = tid & 31;
+  const int g = lane >> 2, t = lane & 3;
+  const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
+
+  auto load_stage = [&](int buf, int k0) {
+#pragma unroll
+    for (int it = 0; it < (NT_BM * NT_BK) / NT_THREADS; ++it) {
+      const int idx = tid + it * NT_THREADS;
+      const int r = idx / NT_BK, c = idx % NT_BK;  // A: row r of the tile, column c
+      const int gi = m0 + r, gk = k0 + c;
+      const bool ok = gi < n && gk < n;
+      cp_async_8(&As[buf][c][r], ok ? A + (size_t)gi * n + gk : A, ok);
+    }
+#pragma unroll
+    for (int it = 0; it < (NT_BK * NT_BN) / NT_THREADS; ++it) {
+      const int idx = tid + it * NT_THREADS;
+      const int r = idx / NT_BN, c = idx % NT_BN;  // B: row r (k), column c
+      const int gk = k0 + r, gj = n0 + c;
+      const bool ok = gk < n && gj < n;
+      cp_async_8(&Bs[buf][r][c], ok ? B + (size_t)gk * n + gj : B, ok);
+    }
+    cp_async_commit();
+  };
+
+  double acc[2][4][4];
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.0;
+
+  const int ktiles = (n + NT_BK - 1) / NT_BK;
+  load_stage(0, 0);
+  for (int kt = 0; kt < ktiles; ++kt) {
+    const int buf = kt & 1;
+    if (kt + 1 < ktiles) {
+      load_stage(buf ^ 1, (kt + 1) * NT_BK);
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < NT_BK; kk += 4) {
+      double a[2][2], b[4];
+#pragma unroll
+      for (int mi = 0; mi < 2; ++mi) {
+        a[mi][0] = As[buf][kk + t][wm + mi * 16 + g];
+        a[mi][1] = As[buf][kk + t][wm + mi * 16 + g + 8];
+      }
+#pragma unroll
+      for (int ni = 0; ni < 4; ++ni) b[ni] = Bs[buf][kk + t][wn + ni * 8 + g];
+#pragma unroll
+      for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+        for (int ni = 0; ni < 4; ++ni) dmma_16x8x4(acc[mi][ni], a[mi][0], a[mi][1], b[ni]);
+    }
+    __syncthreads();
+  }
+
+#pragma unroll
+  for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+    for (int ni = 0; ni < 4; ++ni) {
+      const int r0 = m0 + wm + mi * 16 + g;
+      const int c0 = n0 + wn + ni * 8 + 2 * t;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int r = r0 + 8 * h;
+        if (r < n) {
+          if (c0 < n) C[(size_t)r * n + c0] = acc[mi][ni][2 * h];
+          if (c0 + 1 < n) C[(size_t)r * n + c0 + 1] = acc[mi][ni][2 * h + 1];
+        }
+      }
+    }
+}
+
+// Host-side helpers --------------------------------------------------------
+
+int native_tiles(int n) {
+  if (n <= 0) return 0;
+  const int tm = (n + NT_BM - 1) / NT_BM;
+  return tm * tm;
+}
+
+void native_fill_tiles(Problem& p) {
+  const int tm = p.n > 0 ? (p.n + NT_BM - 1) / NT_BM : 0;
+  p.tiles_m = tm;
+  p.tiles_n = tm;
+}
+
+cudaError_t native_launch(const Problem* table, const Problem* single, int count, int total_tiles,
+                          cudaStream_t stream) {
+  if (total_tiles <= 0) return cudaSuccess;
+  NativeArgs args{};
+  args.table = table;
+  if (single) args.single = *single;
+  args.count = count;
+  native_fp64_kernel<<<total_tiles, NT_THREADS, 0, stream>>>(args);
+  return cudaGetLastError();
+}
+
+}  // namespace mmk

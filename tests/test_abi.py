@@ -1,0 +1,72 @@
+"""The C-ABI library builds, loads without a GPU and exports every declared symbol.
+
+No compute call is made here; only argument checks that return before any
+CUDA work.
+"""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+import paper_1012_2273_gb300 as mm
+from paper_1012_2273_gb300 import build as mmbuild
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "mm.h")
+
+
+def declared_symbols():
+    text = open(HEADER).read()
+    return sorted(set(re.findall(r"^\s*(?:mm_status|const char\*)\s+(mm_\w+)\s*\(", text, re.M)))
+
+
+def test_header_declares_the_boundary():
+    syms = declared_symbols()
+    for name in ("mm_create", "mm_gemm", "mm_gemm_grouped", "mm_destroy", "mm_status_get", "mm_last_error"):
+        assert name in syms
+    assert set(syms) == set(mm.SYMBOLS)
+
+
+def test_library_exports_every_declared_symbol():
+    path = mmbuild.build()
+    out = subprocess.run(["nm", "-D", "--defined-only", path], capture_output=True, text=True, check=True).stdout
+    exported = set(re.findall(r"\bT (mm_\w+)$", out, re.M))
+    missing = set(declared_symbols()) - exported
+    assert not missing, missing
+    L = ctypes.CDLL(path)
+    for name in declared_symbols():
+        assert hasattr(L, name)
+
+
+def test_argument_checks_without_gpu():
+    L = mm.lib()
+    assert L.mm_create(None, None) == 1  # MM_ERR_INVALID
+    assert L.mm_gemm(None, 10, None, None, None, None) == 1
+    assert L.mm_destroy(None) == 1
+    assert L.mm_last_error(None) == b"invalid handle"
+    assert L.mm_gemm_grouped(None, 1, None, None, None, None, None) == 1
+
+
+def test_header_cites_the_paper_and_states_conventions():
+    text = open(HEADER).read()
+    assert "Alg. 1" in text and "Sec. 3.1" in text
+    assert "row-major" in text and "16-byte" in text and "owned by the caller" in text
+
+
+def test_sources_have_no_cpu_fallback_or_oracle_use():
+    pkg = os.path.join(ROOT, "paper_1012_2273_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        if "_build" in dirpath:
+            continue
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh")):
+                src = open(os.path.join(dirpath, f)).read()
+                assert "import oracle" not in src and "from oracle" not in src, f
+                assert "oracle.c" not in src, f
+
+
+@pytest.mark.parametrize("flag", ["-gencode", "arch=compute_103a,code=sm_103a"])
+def test_build_targets_sm103a_only(flag):
+    assert flag in mmbuild.NVCC_FLAGS
