@@ -1,0 +1,493 @@
+#!/usr/bin/env python3
+"""Benchmark: FP64-accurate GEMM throughput on the paper's size sweep, one GB300.
+
+Workload (the sweep the paper times, Sec. 4.1 and Tables 1-3, N from 10 to
+2000): one square FP64 product C = A.B at each N in (10, 100, 500, 1000, 1500,
+2000), entries uniform [0, 1) from seed 0 (synthetic stand-in for the paper's
+unspecified RAND()).  One step = one grouped call of the library over the
+six problems (mm_gemm_grouped, automatic plan: native FP64 for the small
+sizes, split-precision emulation for the large ones, replayed from a CUDA
+graph).  Flops are counted the paper's way, N^2 (2N - 1) per product.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line on rank 0.  `--impl reference` times the CPU oracle (the
+plain triple loop of Alg. 1 on all host cores) on a bounded sample of the same
+workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import workload  # noqa: E402
+
+SWEEP = workload.SWEEP_SIZES
+DIST = "uniform01"
+SEED = 0
+METRIC = "FP64-accurate GEMM TFLOP/s vs N, emulated vs native FP64, % of peak, 1 GB300"
+UNIT = "TFLOP/s"
+L2_FLUSH_BYTES = 512 << 20
+
+
+def parse_args():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing on the host")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target length of the CPU-baseline sample")
+    return ap.parse_args()
+
+
+def sweep_flops(sizes=SWEEP) -> int:
+    return sum(workload.flops(n) for n in sizes)
+
+
+def load_peaks() -> dict:
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        d["source"] = "measured"
+        return d
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "source": "fallback"}
+
+
+# ---------------------------------------------------------------------------
+# distributed plumbing (one process per GPU; the sweep is replicated per rank)
+# ---------------------------------------------------------------------------
+class Dist:
+    def __init__(self):
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.local = int(os.environ.get("LOCAL_RANK", "0"))
+        self.pg = None
+        if self.world > 1:
+            import torch.distributed as td
+            td.init_process_group("nccl" if self._cuda() else "gloo")
+            self.pg = td
+
+    @staticmethod
+    def _cuda():
+        import torch
+        return torch.cuda.is_available()
+
+    def barrier(self):
+        if self.pg:
+            self.pg.barrier()
+
+    def max(self, x: float) -> float:
+        if not self.pg:
+            return x
+        import torch
+        t = torch.tensor([x], dtype=torch.float64, device="cuda" if self._cuda() else "cpu")
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.MAX)
+        return float(t.item())
+
+    def close(self):
+        if self.pg:
+            self.pg.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------
+# SM clock sampling through NVML (ctypes), nvidia-smi as a fallback
+# ---------------------------------------------------------------------------
+REASON_BITS = {0x1: "gpu_idle", 0x2: "applications_clocks_setting", 0x4: "sw_power_cap", 0x8: "hw_slowdown",
+               0x10: "sync_boost", 0x20: "sw_thermal_slowdown", 0x40: "hw_thermal_slowdown",
+               0x80: "hw_power_brake_slowdown", 0x100: "display_clock_setting"}
+
+
+class ClockSampler:
+    def __init__(self, cuda_index: int, period_s: float = 0.002):
+        self.period = period_s
+        self.samples: list[tuple[int, int]] = []
+        self.max_mhz = None
+        self._stop = threading.Event()
+        self._thread = None
+        self._nvml = None
+        self._handle = None
+        self._smi_proc = None
+        self._smi_file = None
+        try:
+            import torch
+            props = torch.cuda.get_device_properties(cuda_index)
+            nv = ctypes.CDLL("libnvidia-ml.so.1")
+            if nv.nvmlInit_v2() != 0:
+                raise OSError("nvmlInit failed")
+            h = ctypes.c_void_p()
+            bus = f"{getattr(props, 'pci_domain_id', 0):08X}:{props.pci_bus_id:02X}:{props.pci_device_id:02X}.0"
+            if nv.nvmlDeviceGetHandleByPciBusId_v2(bus.encode(), ctypes.byref(h)) != 0:
+                raise OSError("nvml handle")
+            mx = ctypes.c_uint()
+            if nv.nvmlDeviceGetMaxClockInfo(h, 1, ctypes.byref(mx)) == 0:
+                self.max_mhz = int(mx.value)
+            self._reason_fn = getattr(nv, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+                getattr(nv, "nvmlDeviceGetCurrentClocksThrottleReasons")
+            self._nvml, self._handle = nv, h
+        except Exception:
+            self._nvml = None
+
+    def _poll(self):
+        nv, h = self._nvml, self._handle
+        clk = ctypes.c_uint()
+        rs = ctypes.c_ulonglong()
+        while not self._stop.is_set():
+            if nv.nvmlDeviceGetClockInfo(h, 1, ctypes.byref(clk)) == 0 and self._reason_fn(h, ctypes.byref(rs)) == 0:
+                self.samples.append((int(clk.value), int(rs.value)))
+            time.sleep(self.period)
+
+    def start(self):
+        self.samples = []
+        self._stop.clear()
+        if self._nvml is not None:
+            self._thread = threading.Thread(target=self._poll, daemon=True)
+            self._thread.start()
+        else:
+            self._smi_file = open(os.path.join(ROOT, ".bench_clocks.csv"), "w")
+            self._smi_proc = subprocess.Popen(
+                ["nvidia-smi", "--query-gpu=clocks.sm,clocks.max.sm,clocks_event_reasons.active", "--format=csv,noheader,nounits",
+                 "-lms", "50", "-i", os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0]],
+                stdout=self._smi_file, stderr=subprocess.DEVNULL)
+
+    def stop(self) -> dict:
+        self._stop.set()
+        if self._thread:
+            self._thread.join()
+        if self._smi_proc:
+            self._smi_proc.terminate()
+            self._smi_proc.wait()
+            self._smi_file.close()
+            path = os.path.join(ROOT, ".bench_clocks.csv")
+            for line in open(path):
+                parts = [p.strip() for p in line.split(",")]
+                try:
+                    self.samples.append((int(float(parts[0])), int(parts[2], 16)))
+                    self.max_mhz = int(float(parts[1]))
+                except (ValueError, IndexError):
+                    pass
+            os.remove(path)
+        mhz = [s[0] for s in self.samples]
+        reasons = 0
+        for _, r in self.samples:
+            reasons |= r
+        names = [n for b, n in REASON_BITS.items() if reasons & b and b != 0x1]
+        return {"sm_mhz": statistics.median(mhz) if mhz else None, "sm_max_mhz": self.max_mhz,
+                "reasons": names, "samples": len(mhz),
+                "source": "nvml" if self._nvml is not None else "nvidia-smi"}
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def source_digest() -> str:
+    h = hashlib.sha256()
+    path = os.path.join(ROOT, "paper_1012_2273_gb300", "csrc", "emu_gemm.cu")
+    with open(path, "rb") as f:
+        h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(kernel_digest: str):
+    """DRAM bytes per launch of the slice-product kernel from a committed ncu summary, if current."""
+    path = os.path.join(ROOT, "profiles", "emu_gemm_traffic.json")
+    if not os.path.exists(path):
+        return None, None
+    with open(path) as f:
+        d = json.load(f)
+    if d.get("kernel_sha256_16") != kernel_digest:
+        return None, d
+    return d.get("dram_bytes_per_launch_full_workload"), d
+
+
+def run_ours(args, dist: Dist):
+    import torch
+    import paper_1012_2273_gb300 as mm
+
+    torch.cuda.set_device(dist.local)
+    dev = torch.device("cuda", dist.local)
+    peaks = load_peaks()
+    rank_seed = SEED + dist.rank * 7919  # per-rank inputs (weak scaling)
+    host = [workload.pair(DIST, rank_seed, n) for n in SWEEP]
+    As = [torch.from_numpy(a).to(dev) for a, _ in host]
+    Bs = [torch.from_numpy(b).to(dev) for _, b in host]
+    Cs = [torch.empty_like(a) for a in As]
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    h = mm.Handle("auto")
+    plan = {n: h.plan(n) for n in SWEEP}
+
+    def step(handle):
+        handle.gemm_grouped(As, Bs, Cs)
+
+    # warm-up (builds and caches the CUDA graph)
+    for _ in range(max(args.warmup, 3)):
+        step(h)
+    h.check()
+    check = verify(As, Bs, Cs)
+
+    # timed region: K steps, L2 flushed before each, device time by CUDA events
+    sampler = ClockSampler(dist.local)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        ev[i][0].record(stream)
+        step(h)
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    dist.barrier()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_s = dist.max(sum(step_ms) / 1e3)
+    h.check()
+    flops_step = sweep_flops()
+    value = dist.world * args.steps * flops_step / total_s / 1e12
+
+    # roofline pass: same steps with per-kernel events on the launch stream
+    hp = mm.Handle("auto", flags=mm.FLAG_PROFILE)
+    prof_steps = min(args.steps, 50)
+    kinds = {k: [] for k in mm.KERNEL_KINDS}
+    launches_per_step = 0
+    for i in range(prof_steps + 2):
+        flush.fill_(float(i))
+        step(hp)
+        p = hp.profile()
+        if i >= 2:
+            for k in kinds:
+                kinds[k].append(p[k][0])
+            launches_per_step = sum(v[1] for v in p.values())
+    hp.check()
+    emu_sizes = [n for n in SWEEP if plan[n][0] == 1]
+    s_emu = plan[emu_sizes[0]][1] if emu_sizes else 0
+    pairs = s_emu * (s_emu + 1) // 2
+    tensor_flops = pairs * sum(2 * n ** 3 for n in emu_sizes)
+    gemm_ms = statistics.mean(kinds["slice_products"]) if emu_sizes else None
+    digest = source_digest()
+    traffic, traffic_meta = profiled_traffic(digest)
+    roofline = None
+    if gemm_ms:
+        achieved = tensor_flops / (gemm_ms / 1e3) / 1e12
+        peak = peaks["bf16_tflops"]
+        roofline = {"kernel": "emu_gemm_kernel (tcgen05 bf16 digit products, fused exact recombination)",
+                    "bound": "tensor", "achieved": round(achieved, 2), "peak": peak, "unit": "TFLOP/s",
+                    "frac": round(achieved / peak, 4),
+                    "peak_source": f"{peaks['source']} bf16 dense burst (MEASURED_PEAKS.json bf16_tflops)",
+                    "traffic": traffic,
+                    "algorithmic_flops_per_launch": tensor_flops,
+                    "avg_launch_ms": round(gemm_ms, 4),
+                    "note": f"{pairs} digit-pair products of 2N^3 flops each for N in {emu_sizes}, s = {s_emu}"}
+
+    # per-N comparison of the two forms (single calls, L2 flushed)
+    per_n = per_size(mm, As, Bs, Cs, flush, stream)
+    hn = mm.Handle("native")
+    dmma_peak, dfma_peak = hn.probe_fp64_peak()
+    for n, d in per_n.items():
+        d["native_frac_of_dmma_peak"] = round(d["native_tflops"] / dmma_peak, 4)
+
+    # end to end through the public API on host buffers (pinned), per step:
+    # H2D of A and B, compute, D2H of C for every problem of the sweep
+    e2e = end_to_end(mm, host, dev, steps=min(args.steps, 20))
+    e2e_s = dist.max(e2e["seconds"])
+    e2e_value = dist.world * e2e["steps"] * flops_step / e2e_s / 1e12
+
+    cpu = None
+    if dist.world == 1 and dist.rank == 0 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(args.cpu_seconds)
+
+    line = {
+        "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": dist.world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(total_s * 1e3 / args.steps, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic: uniform [0,1) FP64 from SplitMix64 seed 0 (stand-in for the paper's RAND())",
+        "config": {"workload": "paper size sweep: one square FP64 product at each N in "
+                               f"{list(SWEEP)}, one grouped library call per step (plan: "
+                               + ", ".join(f"N={n}:{'native' if plan[n][0] == 0 else f'emulated s={plan[n][1]}'}"
+                                           for n in SWEEP) + ")",
+                   "flops_per_step": flops_step, "flop_count": "N^2 (2N - 1) per product (paper, Sec. 3.1)",
+                   "l2": f"flushed before every timed step ({L2_FLUSH_BYTES >> 20} MiB write)",
+                   "timing": "CUDA events on the launching stream around each step; max over ranks"},
+        "e2e": {"value": round(e2e_value, 4), "unit": UNIT, "h2d_bytes_per_step": e2e["h2d"],
+                "d2h_bytes_per_step": e2e["d2h"],
+                "how": "mm_gemm_host on pinned host buffers, every problem of the sweep, wall clock per step"},
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": clocks,
+        "roofline": roofline,
+        "kernel_times_ms_per_step": {k: round(statistics.mean(v), 4) for k, v in kinds.items() if v},
+        "per_n": per_n,
+        "fp64_peak_measured": {"dmma_tflops": round(dmma_peak, 4), "dfma_tflops": round(dfma_peak, 4)},
+        "check": check,
+        "cpu_baseline": cpu,
+    }
+    for hh in (h, hp, hn):
+        hh.close()
+    return line
+
+
+def verify(As, Bs, Cs) -> dict:
+    """Freivalds-style residual check of the step's output on the device (not timed)."""
+    import torch
+    worst = 0.0
+    for A, B, C in zip(As, Bs, Cs):
+        n = A.shape[0]
+        x = torch.sign(torch.randn(n, dtype=torch.float64, device=A.device, generator=None))
+        y = A @ (B @ x) - C @ x
+        tol = (A.abs() @ (B.abs() @ x.abs()) + C.abs() @ x.abs()) * n * 2.0 ** -53
+        worst = max(worst, float((y.abs() / tol.clamp_min(1e-300)).max()))
+    return {"freivalds_worst_ratio": round(worst, 4), "passed": worst <= 4.0}
+
+
+def per_size(mm, As, Bs, Cs, flush, stream, reps: int = 5) -> dict:
+    import torch
+    out = {}
+    hn = mm.Handle("native")
+    he = mm.Handle("emulated")
+    for A, B, C in zip(As, Bs, Cs):
+        n = A.shape[0]
+        row = {}
+        for name, hh in (("native", hn), ("emulated", he)):
+            hh.gemm(A, B, C)  # warm
+            ts = []
+            for r in range(reps):
+                flush.fill_(float(r))
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                hh.gemm(A, B, C)
+                e1.record(stream)
+                e1.synchronize()
+                ts.append(e0.elapsed_time(e1))
+            ms = statistics.median(ts)
+            row[f"{name}_ms"] = round(ms, 4)
+            row[f"{name}_tflops"] = round(workload.flops(n) / (ms / 1e3) / 1e12, 4)
+        row["emulated_slices"] = he.plan(n)[1]
+        row["speedup_emulated_over_native"] = round(row["native_ms"] / row["emulated_ms"], 2)
+        out[str(n)] = row
+    hn.check()
+    he.check()
+    hn.close()
+    he.close()
+    return out
+
+
+def end_to_end(mm, host_pairs, dev, steps: int) -> dict:
+    import torch
+    h = mm.Handle("auto")
+    pinned = []
+    for a, b in host_pairs:
+        pa = torch.from_numpy(a).pin_memory()
+        pb = torch.from_numpy(b).pin_memory()
+        pc = torch.empty_like(pa).pin_memory()
+        pinned.append((a.shape[0], pa, pb, pc))
+    for n, pa, pb, pc in pinned:  # warm
+        h.gemm_host_ptr(n, pa.data_ptr(), pb.data_ptr(), pc.data_ptr())
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        for n, pa, pb, pc in pinned:
+            h.gemm_host_ptr(n, pa.data_ptr(), pb.data_ptr(), pc.data_ptr())
+    secs = time.perf_counter() - t0
+    h.check()
+    h.close()
+    h2d = sum(2 * n * n * 8 for n, *_ in pinned)
+    d2h = sum(n * n * 8 for n, *_ in pinned)
+    return {"seconds": secs, "steps": steps, "h2d": h2d, "d2h": d2h}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timings (baseline and reference arm)
+# ---------------------------------------------------------------------------
+def _oracle_sample(budget_s: float):
+    """Sizes of the sweep (ascending) whose oracle run fits `budget_s`, and the inputs."""
+    import oracle
+    oracle.build()
+    threads = oracle.max_threads()
+    a, b = workload.pair(DIST, SEED, 200)
+    t0 = time.perf_counter()
+    oracle.gemm(a, b, nthreads=threads)
+    rate = workload.flops(200) / max(time.perf_counter() - t0, 1e-6)  # flop/s, rough
+    sizes, est = [], 0.0
+    for n in SWEEP:
+        t = workload.flops(n) / rate
+        if est + t > budget_s and sizes:
+            break
+        sizes.append(n)
+        est += t
+    pairs = [workload.pair(DIST, SEED, n) for n in sizes]
+    return oracle, threads, sizes, pairs
+
+
+def cpu_baseline(target_s: float) -> dict:
+    oracle, threads, sizes, pairs = _oracle_sample(min(target_s, 30.0))
+    flops, reps = 0, 0
+    t0 = time.perf_counter()
+    while True:
+        for a, b in pairs:
+            oracle.gemm(a, b, nthreads=threads)
+        flops += sum(workload.flops(n) for n in sizes)
+        reps += 1
+        if time.perf_counter() - t0 >= min(target_s, 30.0) or reps >= 200:
+            break
+    secs = time.perf_counter() - t0
+    return {"value": flops / secs / 1e12, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"oracle (Alg. 1 triple loop, OpenMP over rows) on N={sizes} x {reps} repetitions, "
+                      f"{secs:.1f} s on {threads} host threads"}
+
+
+def run_reference(args, dist: Dist):
+    if dist.rank != 0:
+        return None
+    per_step_budget = max(0.05, min(5.0, 150.0 / max(1, args.steps + args.warmup)))
+    oracle, threads, sizes, pairs = _oracle_sample(per_step_budget)
+    flops_step = sum(workload.flops(n) for n in sizes)
+    for _ in range(args.warmup):
+        for a, b in pairs:
+            oracle.gemm(a, b, nthreads=threads)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        for a, b in pairs:
+            oracle.gemm(a, b, nthreads=threads)
+    secs = time.perf_counter() - t0
+    value = args.steps * flops_step / secs / 1e12
+    sample = f"oracle (Alg. 1 triple loop, OpenMP over rows) on N={sizes} of the sweep per step"
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic: uniform [0,1) FP64 from SplitMix64 seed 0",
+            "config": {"workload": f"paper size sweep, bounded sample N={sizes}", "flops_per_step": flops_step},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse_args()
+    dist = Dist()
+    try:
+        if args.impl == "reference":
+            line = run_reference(args, dist)
+        else:
+            line = run_ours(args, dist)
+        if dist.rank == 0 and line is not None:
+            print(json.dumps(line), flush=True)
+    finally:
+        dist.close()
+
+
+if __name__ == "__main__":
+    main()

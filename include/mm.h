@@ -62,6 +62,7 @@ typedef enum {
 
 /* Flags of mm_config.flags. */
 #define MM_FLAG_NO_GRAPH 1u /* grouped calls launch directly instead of replaying a CUDA graph */
+#define MM_FLAG_PROFILE 2u  /* bracket every kernel with CUDA events (implies MM_FLAG_NO_GRAPH) */
 
 typedef struct {
   mm_mode mode;          /* default MM_AUTO */
@@ -107,6 +108,21 @@ const char* mm_last_error(mm_handle h);
  * the form: 0 = native FP64, 1 = emulation. */
 mm_status mm_plan(mm_handle h, int N, int* form, int* slices);
 
+/* Device time of the last call made on this handle with MM_FLAG_PROFILE set,
+ * in milliseconds, by kernel kind (events recorded on the call's stream):
+ *   out_ms[0] scale and split (including zeroing of the row/column maxima)
+ *   out_ms[1] slice products with fused recombination
+ *   out_ms[2] native FP64 kernel
+ *   out_ms[3] standalone recombination (mm_recombine)
+ * and launches[0..3] the number of kernel launches of each kind (may be
+ * NULL).  Synchronises on the recorded events.  MM_ERR_INVALID without the flag. */
+mm_status mm_profile_read(mm_handle h, double out_ms[4], int launches[4]);
+
+/* Measures the FP64 throughput of this GPU with two calibration kernels
+ * (independent chains of mma.sync m16n8k4 f64, and of scalar FP64 FMA),
+ * in TFLOP/s: the roof of the native form.  Blocks for a few milliseconds. */
+mm_status mm_probe_fp64_peak(mm_handle h, double* dmma_tflops, double* dfma_tflops);
+
 /* ---------------------------------------------------------------------
  * Steps of the emulation, exposed for testing each one on its own.
  * They use caller-provided device buffers with the layouts stated here.
@@ -122,15 +138,16 @@ mm_status mm_plan(mm_handle h, int N, int* form, int* slices);
  * Outputs (device): exps[N] int32; digits: bf16 bit patterns, s planes of
  * rows x ld elements, plane t at digits + t*rows*ld.  For A, element (i,j)
  * sits at row i, column j; for B, (j,k) sits at row k, column j (B^T).
- * rows >= N and ld >= N, ld a multiple of 8; the padding is written with 0. */
+ * rows >= N a multiple of 128, ld >= N a multiple of 64, digits 16-byte
+ * aligned; the padding is written with 0. */
 mm_status mm_split(mm_handle h, int N, const double* M, int by_columns, int slices, int* exps,
                    uint16_t* digits, int rows, int ld, void* stream);
 
 /* Exact level sums of digit products: for L = 2..s+1,
  *   S_L(i,k) = sum_j sum_{t+u=L} d_t(a_ij) d_u(b_jk)
  * written as int32 to levels[(L-2)*N*N + i*N + k].  Inputs are the digit
- * planes of mm_split (A: rows = a_rows; B: rows = b_rows; both with ld).
- * Requires (s) * N * 2^14 < 2^31. */
+ * planes of mm_split (A: rows = a_rows; B: rows = b_rows, multiples of 128;
+ * both with ld).  Requires s * N * 2^14 < 2^31. */
 mm_status mm_level_sums(mm_handle h, int N, int slices, const uint16_t* a_digits, int a_rows,
                         const uint16_t* b_digits, int b_rows, int ld, int32_t* levels, void* stream);
 

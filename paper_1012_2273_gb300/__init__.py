@@ -24,6 +24,7 @@ NATIVE_FP64 = 0
 EMU_BF16 = 1
 AUTO = 3
 FLAG_NO_GRAPH = 1
+FLAG_PROFILE = 2
 
 STATUS_NAMES = {
     0: "MM_OK", 1: "MM_ERR_INVALID", 2: "MM_ERR_CUDA", 3: "MM_ERR_NOMEM",
@@ -48,7 +49,9 @@ class _Config(ctypes.Structure):
 
 
 SYMBOLS = ("mm_create", "mm_destroy", "mm_gemm", "mm_gemm_grouped", "mm_gemm_host", "mm_status_get",
-           "mm_last_error", "mm_plan", "mm_split", "mm_level_sums", "mm_recombine")
+           "mm_last_error", "mm_plan", "mm_profile_read", "mm_probe_fp64_peak", "mm_split", "mm_level_sums",
+           "mm_recombine")
+KERNEL_KINDS = ("split", "slice_products", "native_fp64", "recombine")
 
 
 def library_path() -> str:
@@ -78,6 +81,8 @@ def lib(build_if_needed: bool = True) -> ctypes.CDLL:
             L.mm_split.argtypes = [vp, ci, vp, ci, ci, vp, vp, ci, ci, vp]
             L.mm_level_sums.argtypes = [vp, ci, ci, vp, ci, vp, ci, ci, vp, vp]
             L.mm_recombine.argtypes = [vp, ci, ci, vp, vp, vp, vp, vp]
+            L.mm_profile_read.argtypes = [vp, ctypes.POINTER(cd), ctypes.POINTER(ci)]
+            L.mm_probe_fp64_peak.argtypes = [vp, ctypes.POINTER(cd), ctypes.POINTER(cd)]
             for name in SYMBOLS:
                 if name != "mm_last_error":
                     getattr(L, name).restype = ci
@@ -196,6 +201,19 @@ class Handle:
     def check(self, stream=None):
         """Synchronises and raises MMError for any device-side error."""
         self._raise(self._lib.mm_status_get(self._h, _stream_ptr(stream)))
+
+    def profile(self) -> dict:
+        """Per-kernel-kind device time (ms) and launch counts of the last call (MM_FLAG_PROFILE)."""
+        ms = (ctypes.c_double * 4)()
+        n = (ctypes.c_int * 4)()
+        self._raise(self._lib.mm_profile_read(self._h, ms, n))
+        return {k: (ms[i], n[i]) for i, k in enumerate(KERNEL_KINDS)}
+
+    def probe_fp64_peak(self) -> tuple[float, float]:
+        """Measured FP64 roof of this GPU: (DMMA TFLOP/s, DFMA TFLOP/s)."""
+        a, b = ctypes.c_double(), ctypes.c_double()
+        self._raise(self._lib.mm_probe_fp64_peak(self._h, ctypes.byref(a), ctypes.byref(b)))
+        return a.value, b.value
 
     def plan(self, n: int) -> tuple[int, int]:
         form, s = ctypes.c_int(), ctypes.c_int()

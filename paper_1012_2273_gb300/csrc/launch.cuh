@@ -51,4 +51,7 @@ void emu_kernel_info(int bn, char* buf, size_t len);
 cudaError_t recombine_launch(int n, int s, const int32_t* levels, const int* e, const int* f, double* C,
                              cudaStream_t stream);
 
+// probe.cu
+cudaError_t probe_fp64(int num_sms, double* sink, cudaStream_t stream, double* dmma, double* dfma);
+
 }  // namespace mmk

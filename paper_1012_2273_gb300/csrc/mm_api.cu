@@ -99,6 +99,12 @@ struct mm_handle_s {
   cudaEvent_t grp_event = nullptr;
   // autotune table: N upper bound -> plan
   std::vector<std::pair<int, Plan>> tune;
+  // MM_FLAG_PROFILE: events around every kernel of the last call
+  bool profile = false;
+  std::vector<cudaEvent_t> ev_pool;
+  size_t ev_used = 0;
+  std::vector<std::pair<int, size_t>> marks;  // (kind, index of start event; end = start + 1)
+  double* probe_sink = nullptr;
 };
 
 namespace {
@@ -119,6 +125,33 @@ mm_status cuda_fail(mm_handle h, cudaError_t e, const char* what) {
   } while (0)
 
 bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+// ---- MM_FLAG_PROFILE --------------------------------------------------------
+enum { KIND_SPLIT = 0, KIND_SLICE_GEMM = 1, KIND_NATIVE = 2, KIND_RECOMBINE = 3 };
+
+void prof_reset(mm_handle h) {
+  h->ev_used = 0;
+  h->marks.clear();
+}
+
+// Records the start event of a kernel of `kind`; returns its mark or -1.
+long prof_start(mm_handle h, cudaStream_t s, int kind) {
+  if (!h->profile) return -1;
+  while (h->ev_pool.size() < h->ev_used + 2) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return -1;
+    h->ev_pool.push_back(e);
+  }
+  const size_t at = h->ev_used;
+  h->ev_used += 2;
+  cudaEventRecord(h->ev_pool[at], s);
+  h->marks.push_back({kind, at});
+  return static_cast<long>(at);
+}
+
+void prof_end(mm_handle h, cudaStream_t s, long mark) {
+  if (mark >= 0) cudaEventRecord(h->ev_pool[static_cast<size_t>(mark) + 1], s);
+}
 
 // Built-in plan table (overridden by a tune file): below the crossover the
 // native path is as fast and exact enough, above it the emulation wins.
@@ -282,11 +315,13 @@ mm_status run_group(mm_handle h, const EmuGroup& g, const Problem* d_table, cons
   if (g.total_tiles == 0) return MM_OK;
   uint64_t* amax = reinterpret_cast<uint64_t*>(g.base + g.amax);
   uint64_t* bmax = reinterpret_cast<uint64_t*>(g.base + g.bmax);
+  const bool single = d_table == nullptr;
+  const long m_split = prof_start(h, stream, KIND_SPLIT);
   MM_CUDA(h, cudaMemsetAsync(amax, 0, sizeof(uint64_t) * g.max_rows, stream));
   MM_CUDA(h, cudaMemsetAsync(bmax, 0, sizeof(uint64_t) * g.max_rows, stream));
-  const bool single = d_table == nullptr;
   MM_CUDA(h, mmk::split_launch(d_table, single ? &g.ps[0] : nullptr, static_cast<int>(g.ps.size()), g.total_split,
                                g.s, amax, bmax, single ? nullptr : d_max_off, h->d_status, stream));
+  prof_end(h, stream, m_split);
   mmk::EmuArgs a{};
   a.table = d_table;
   if (single) a.single = g.ps[0];
@@ -299,7 +334,9 @@ mm_status run_group(mm_handle h, const EmuGroup& g, const Problem* d_table, cons
   a.levels_out = nullptr;
   a.status = h->d_status;
   a.timeout_ns = h->timeout_ns;
+  const long m_gemm = prof_start(h, stream, KIND_SLICE_GEMM);
   const cudaError_t le = mmk::emu_gemm_launch(g.bn, &g.maps[0], &g.maps[1], a, g.grid, stream);
+  prof_end(h, stream, m_gemm);
   if (le != cudaSuccess) {
     char info[512];
     mmk::emu_kernel_info(g.bn, info, sizeof(info));
@@ -334,7 +371,9 @@ mm_status emu_single(mm_handle h, const Problem& p, int s, int bn, cudaStream_t 
 mm_status native_single(mm_handle h, Problem p, cudaStream_t stream) {
   mmk::native_fill_tiles(p);
   p.tile_begin = 0;
+  const long m = prof_start(h, stream, KIND_NATIVE);
   MM_CUDA(h, mmk::native_launch(nullptr, &p, 1, p.tiles_m * p.tiles_n, stream));
+  prof_end(h, stream, m);
   return MM_OK;
 }
 
@@ -371,6 +410,7 @@ mm_status mm_create(mm_handle* out, const mm_config* cfg) {
     const long ms = std::atol(t);
     if (ms > 0) h->timeout_ns = static_cast<uint64_t>(ms) * 1000000ull;
   }
+  h->profile = (h->cfg.flags & MM_FLAG_PROFILE) != 0;
   default_tune(h);
   if (!h->tune_path.empty() && !load_tune(h, h->tune_path)) {
     delete h;
@@ -405,7 +445,34 @@ mm_status mm_destroy(mm_handle h) {
   if (h->grp_event) cudaEventDestroy(h->grp_event);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   if (h->d_status) cudaFree(h->d_status);
+  for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
+  if (h->probe_sink) cudaFree(h->probe_sink);
   delete h;
+  return MM_OK;
+}
+
+mm_status mm_profile_read(mm_handle h, double out_ms[4], int launches[4]) {
+  if (!h || !out_ms) return MM_ERR_INVALID;
+  if (!h->profile) return fail(h, MM_ERR_INVALID, "handle was created without MM_FLAG_PROFILE");
+  for (int k = 0; k < 4; ++k) {
+    out_ms[k] = 0.0;
+    if (launches) launches[k] = 0;
+  }
+  for (const auto& m : h->marks) {
+    cudaEvent_t e0 = h->ev_pool[m.second], e1 = h->ev_pool[m.second + 1];
+    MM_CUDA(h, cudaEventSynchronize(e1));
+    float ms = 0.f;
+    MM_CUDA(h, cudaEventElapsedTime(&ms, e0, e1));
+    out_ms[m.first] += ms;
+    if (launches) launches[m.first] += (m.first == KIND_SPLIT) ? 2 : 1;  // split = absmax + split kernels
+  }
+  return MM_OK;
+}
+
+mm_status mm_probe_fp64_peak(mm_handle h, double* dmma_tflops, double* dfma_tflops) {
+  if (!h || !dmma_tflops || !dfma_tflops) return MM_ERR_INVALID;
+  if (!h->probe_sink) MM_CUDA(h, cudaMalloc(&h->probe_sink, 64));
+  MM_CUDA(h, mmk::probe_fp64(h->num_sms, h->probe_sink, h->cap_stream, dmma_tflops, dfma_tflops));
   return MM_OK;
 }
 
@@ -446,6 +513,7 @@ mm_status mm_gemm(mm_handle h, int N, const double* A, const double* B, double* 
     return a < b + bytes && b < a + bytes;
   };
   if (overlap(C, A) || overlap(C, B)) return fail(h, MM_ERR_INVALID, "C must not overlap A or B");
+  prof_reset(h);
   Problem p{};
   p.A = A;
   p.B = B;
@@ -501,6 +569,7 @@ mm_status mm_gemm_grouped(mm_handle h, int count, const int* Ns, const double* c
       return fail(h, MM_ERR_INVALID, "group pointers must be 16-byte aligned");
   }
   cudaStream_t user = static_cast<cudaStream_t>(stream);
+  prof_reset(h);
 
   // Partition: native problems, and emulated problems by (slices, bn).
   std::vector<Problem> nat;
@@ -573,8 +642,10 @@ mm_status mm_gemm_grouped(mm_handle h, int count, const int* Ns, const double* c
 
   auto launch_all = [&](char* dtab, cudaStream_t s) -> mm_status {
     if (!nat.empty()) {
+      const long m = prof_start(h, s, KIND_NATIVE);
       MM_CUDA(h, mmk::native_launch(reinterpret_cast<Problem*>(dtab + off_nat), nullptr,
                                     static_cast<int>(nat.size()), nat_tiles, s));
+      prof_end(h, s, m);
     }
     for (size_t gi = 0; gi < groups.size(); ++gi) {
       mm_status st = run_group(h, groups[gi], reinterpret_cast<Problem*>(dtab + off_tab[gi]),
@@ -585,7 +656,7 @@ mm_status mm_gemm_grouped(mm_handle h, int count, const int* Ns, const double* c
     return MM_OK;
   };
 
-  const bool use_graph = (h->cfg.flags & MM_FLAG_NO_GRAPH) == 0;
+  const bool use_graph = (h->cfg.flags & (MM_FLAG_NO_GRAPH | MM_FLAG_PROFILE)) == 0;
   if (!use_graph) {
     if (tab_bytes > h->grp_table_cap) {
       if (h->grp_table) cudaFree(h->grp_table);
@@ -740,7 +811,10 @@ mm_status mm_recombine(mm_handle h, int N, int slices, const int32_t* levels, co
   if (!h) return MM_ERR_INVALID;
   if (N <= 0 || !levels || !a_exps || !b_exps || !C) return fail(h, MM_ERR_INVALID, "mm_recombine: bad arguments");
   if (slices < 1 || slices > 8) return fail(h, MM_ERR_UNSUPPORTED, "slices must be in 1..8");
+  prof_reset(h);
+  const long m = prof_start(h, static_cast<cudaStream_t>(stream), KIND_RECOMBINE);
   MM_CUDA(h, mmk::recombine_launch(N, slices, levels, a_exps, b_exps, C, static_cast<cudaStream_t>(stream)));
+  prof_end(h, static_cast<cudaStream_t>(stream), m);
   return MM_OK;
 }
 
