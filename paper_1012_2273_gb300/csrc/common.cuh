@@ -34,7 +34,10 @@ struct Problem {
   int m_pad;           // rows of an A plane (multiple of 128)
   int n_pad;           // rows of a B^T plane (multiple of the tile width)
   int k_pad;           // columns of a plane (multiple of 64)
-  int split_begin;  // first split tile of this problem (scale/split kernels)
+  int split_begin;     // first split tile of this problem (scale/split kernels)
+  int groups;          // digit-pair groups per tile: work units per tile of the slice-product kernel
+  int nslots;          // segment sums per tile (all groups together)
+  long long slot_base; // int32 offset of this problem's tile 0 in the per-tile slot buffer (groups > 1)
 };
 
 // Device status word.  0 = fine; otherwise the first mm_status recorded.

@@ -17,12 +17,20 @@
 // and its FP32 bit pattern is 0x4B400000 + x, so adding bit patterns in int32
 // accumulates the chunk sums exactly (the bias is removed once per segment).
 // An int32 segment sum stays below 2^31 because the host limits the pairs per
-// segment to floor((2^31 - 1) / (N 2^14)).  Segments are written to per-CTA
-// scratch (L2 resident), and the recombination reads them back in 128-bit
-// integer arithmetic and rounds once -- no FP64 instruction on the way, which
-// matters on GB300 where the FP64 pipe is a small fraction of the others.
+// segment to floor((2^31 - 1) / (N 2^14)).  The recombination reads the
+// segment sums back in 128-bit integer arithmetic and rounds once -- no FP64
+// instruction on the way, which matters on GB300 where the FP64 pipe is a
+// small fraction of the others.
 //
-// Pipeline (one persistent CTA per SM, tiles strided by gridDim.x):
+// Work units.  Integer sums are exact in any order, so the digit pairs of one
+// tile may be split into G groups computed by different CTAs (G chosen by the
+// host so that small problems still fill every SM).  A unit = one tile and one
+// group.  With G = 1 the segment sums go to per-CTA scratch and the same CTA
+// recombines; with G > 1 they go to per-tile slots and, for each 32-row x BN/2
+// region, the epilogue warp that completes the region last (an atomic count,
+// no waiting) recombines it.
+//
+// Pipeline (one persistent CTA per SM, units strided by gridDim.x):
 //   warp 0      TMA producer: A and B^T k-blocks (64 deep, 128-byte swizzle)
 //               into a STAGES-deep shared-memory ring (mbarrier full/empty)
 //   warp 1      allocates TMEM; one lane issues tcgen05.mma (M=128, N=BN,
@@ -44,6 +52,11 @@ constexpr int EM_BM = 128;
 constexpr int EM_BK = 64;          // elements per k-block: one 128-byte swizzle row
 constexpr int EM_CHUNK_KB = 4;     // k-blocks per exact chunk: 256 digit products
 constexpr int EM_THREADS = 384;    // 12 warps: registers are budgeted per 4-warp group
+constexpr int EM_REGS_LAUNCH = 168;  // 65536 / 384, rounded down to a multiple of 8
+constexpr int EM_REGS_CTRL = 56;     // warpgroup 0 after setmaxnreg.dec
+constexpr int EM_REGS_EPI = 224;     // warpgroups 1-2 after setmaxnreg.inc
+static_assert(128 * EM_REGS_CTRL + 256 * EM_REGS_EPI == EM_THREADS * EM_REGS_LAUNCH,
+              "register split must add up to the launch allocation");
 constexpr uint32_t EM_MAGIC = 0x4B400000u;
 
 template <int BN>
@@ -53,7 +66,7 @@ struct EmuCfg {
   static constexpr int B_BYTES = BN * EM_BK * 2;
   static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
   static constexpr int TMEM_COLS = 2 * BN;
-  static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
+  static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers, flags*/;
 };
 
 // ---------------------------------------------------------------------------
@@ -120,13 +133,98 @@ __device__ __forceinline__ void i128_shift_add(int64_t& hi, uint64_t& lo, int sh
   lo = nlo;
 }
 
-__device__ __forceinline__ const Problem* emu_problem(const EmuArgs& a, int tile, int* pi) {
-  if (!a.table) {
-    *pi = 0;
-    return &a.single;
+struct UnitRef {
+  const Problem* P;
+  int pi;          // problem index (map selection)
+  int tile_local;  // tile within the problem
+  int g;           // pair group
+  int G;           // pair groups of this problem
+};
+
+__device__ __forceinline__ UnitRef emu_unit(const EmuArgs& a, int u) {
+  UnitRef r;
+  if (!a.units) {
+    r.P = &a.single;
+    r.pi = 0;
+    r.G = a.single.groups;
+    const int tiles = a.single.tiles_m * a.single.tiles_n;
+    r.g = u / tiles;  // group-major: concurrent CTAs share the same digit slices
+    r.tile_local = u - r.g * tiles;
+  } else {
+    const int4 e = a.units[u];
+    r.pi = e.x;
+    r.P = &a.table[e.x];
+    r.tile_local = e.y;
+    r.g = e.z;
+    r.G = r.P->groups;
   }
-  *pi = find_problem(a.table, a.count, tile);
-  return &a.table[*pi];
+  return r;
+}
+
+// Segment-sum slots hold a 128 x BN int32 tile as [col / 4][row][col % 4]:
+// one thread's four consecutive columns are one 16-byte vector and the 32
+// lanes of a warp (consecutive rows) touch 512 contiguous bytes.
+__device__ __forceinline__ size_t slot_index(int row, int col) {
+  return static_cast<size_t>(col >> 2) * (EM_BM * 4) + static_cast<size_t>(row) * 4 + (col & 3);
+}
+
+template <bool kCacheGlobal>
+__device__ __forceinline__ int4 load_slot4(const int32_t* p) {
+  const int4* q = reinterpret_cast<const int4*>(p);
+  return kCacheGlobal ? __ldcg(q) : *q;
+}
+
+// Sum of the segment slots of one tile in 128-bit integers (levels ascending),
+// rounded once: writes the outputs of one row, columns [col0, col0 + BN/2) of
+// the tile, 16 at a time with four independent vector loads per slot.
+template <int BN, bool kCacheGlobal>
+__device__ __forceinline__ void recombine_row(const int32_t* tile_slots, int s, int G, int max_pairs, int r_in_tile,
+                                              int col0, int n0, int n, int base_scale, const int* b_exp,
+                                              double* crow) {
+  constexpr int HALF = BN / 2;
+  constexpr size_t SLOT = static_cast<size_t>(EM_BM) * BN;
+  for (int c16 = 0; c16 < HALF; c16 += 16) {
+    const int tcol = col0 + c16;  // column within the tile
+    if (n0 + tcol >= n) break;
+    int64_t th[16];
+    uint64_t tl[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      th[j] = 0;
+      tl[j] = 0;
+    }
+    int curL = 2, slot = 0;
+    for (int g = 0; g < G; ++g) {
+      int p0, p1;
+      emu_group_range(s, G, g, &p0, &p1);
+      int L, t0;
+      for (int p = p0; p < p1; ++slot) {
+        p += emu_segment(p, p1, max_pairs, &L, &t0);
+        const int32_t* at = tile_slots + static_cast<size_t>(slot) * SLOT + slot_index(r_in_tile, tcol);
+        int4 v[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) v[k] = load_slot4<kCacheGlobal>(at + k * (EM_BM * 4));
+        const int sh = 8 * (L - curL);
+        curL = L;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          i128_shift_add(th[4 * k + 0], tl[4 * k + 0], sh, v[k].x);
+          i128_shift_add(th[4 * k + 1], tl[4 * k + 1], sh, v[k].y);
+          i128_shift_add(th[4 * k + 2], tl[4 * k + 2], sh, v[k].z);
+          i128_shift_add(th[4 * k + 3], tl[4 * k + 3], sh, v[k].w);
+        }
+      }
+    }
+    const int tail = 8 * (s + 1 - curL);
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      const int col = n0 + tcol + j;
+      if (col < n) {
+        i128_shift_add(th[j], tl[j], tail, 0);
+        crow[col] = round_i128_scaled(th[j], tl[j], base_scale + b_exp[col]);
+      }
+    }
+  }
 }
 
 template <int BN>
@@ -169,14 +267,20 @@ __global__ void __launch_bounds__(EM_THREADS, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
-
-  const int nseg = args.seg.nseg;
   const uint64_t tmo = args.timeout_ns;
+  const int s = args.s;
+  const int maxp = args.max_pairs;
 
+  // Register split: the launch gives every thread EM_REGS_LAUNCH; warpgroup 0
+  // (TMA, MMA, two idle warps) hands registers back and the two epilogue
+  // warpgroups take them: 128 * 56 + 256 * 224 = 384 * 168 exactly.  Each
+  // warpgroup executes its setmaxnreg at the top of its own branch.
+  if (warp < 4) {
+  asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(EM_REGS_CTRL));
   if (warp == 0) {
     // ------------------------------ TMA producer ------------------------------
     if (lane == 0) {
-      if (!args.table) {
+      if (!args.units) {
         tma_prefetch_desc(&mapA);
         tma_prefetch_desc(&mapB);
       }
@@ -184,22 +288,21 @@ __global__ void __launch_bounds__(EM_THREADS, 1)
       uint32_t phase = 0;
       long issued = 0;
       bool ok = true;
-      for (int tile = blockIdx.x; tile < args.total_tiles && ok; tile += gridDim.x) {
-        int pi;
-        const Problem* P = emu_problem(args, tile, &pi);
-        const int local = tile - P->tile_begin;
-        const int m0 = (local / P->tiles_n) * EM_BM;
-        const int n0 = (local % P->tiles_n) * BN;
+      for (int u = blockIdx.x; u < args.total_units && ok; u += gridDim.x) {
+        const UnitRef U = emu_unit(args, u);
+        const Problem* P = U.P;
+        const int m0 = (U.tile_local / P->tiles_n) * EM_BM;
+        const int n0 = (U.tile_local % P->tiles_n) * BN;
         const int KB = P->k_pad / EM_BK;
-        const CUtensorMap* ma = args.table ? &args.maps[2 * pi] : &mapA;
-        const CUtensorMap* mb = args.table ? &args.maps[2 * pi + 1] : &mapB;
-        for (int sg = 0; sg < nseg && ok; ++sg) {
-          const int L = args.seg.L[sg], t0 = args.seg.t0[sg];
-          const int nb = args.seg.np[sg] * KB;
-          for (int b = 0; b < nb; ++b) {
-            const int t = t0 + b / KB;
-            const int u = L - t;
-            const int kb = b - (b / KB) * KB;
+        const CUtensorMap* ma = args.units ? &args.maps[2 * U.pi] : &mapA;
+        const CUtensorMap* mb = args.units ? &args.maps[2 * U.pi + 1] : &mapB;
+        int p0, p1;
+        emu_group_range(s, U.G, U.g, &p0, &p1);
+        for (int p = p0; p < p1 && ok; ++p) {
+          int L, t;
+          emu_pair_of(p, &L, &t);
+          const int uu = L - t;
+          for (int kb = 0; kb < KB; ++kb) {
             if (!mbar_wait(&empty[stage], phase ^ 1, tmo, args.status)) {
               ok = false;
               break;
@@ -207,7 +310,7 @@ __global__ void __launch_bounds__(EM_THREADS, 1)
             uint8_t* sa = smem + stage * Cfg::STAGE_BYTES;
             mbar_arrive_expect_tx(&full[stage], Cfg::STAGE_BYTES);
             tma_load_2d(sa, ma, &full[stage], kb * EM_BK, (t - 1) * P->m_pad + m0);
-            tma_load_2d(sa + Cfg::A_BYTES, mb, &full[stage], kb * EM_BK, (u - 1) * P->n_pad + n0);
+            tma_load_2d(sa + Cfg::A_BYTES, mb, &full[stage], kb * EM_BK, (uu - 1) * P->n_pad + n0);
             ++issued;
             if (++stage == Cfg::STAGES) {
               stage = 0;
@@ -238,12 +341,16 @@ __global__ void __launch_bounds__(EM_THREADS, 1)
       int abuf = 0;
       uint32_t aphase = 0;
       bool ok = true;
-      for (int tile = blockIdx.x; tile < args.total_tiles && ok; tile += gridDim.x) {
-        int pi;
-        const Problem* P = emu_problem(args, tile, &pi);
-        const int KB = P->k_pad / EM_BK;
-        for (int sg = 0; sg < nseg && ok; ++sg) {
-          const int nb = args.seg.np[sg] * KB;
+      for (int u = blockIdx.x; u < args.total_units && ok; u += gridDim.x) {
+        const UnitRef U = emu_unit(args, u);
+        const int KB = U.P->k_pad / EM_BK;
+        int p0, p1;
+        emu_group_range(s, U.G, U.g, &p0, &p1);
+        int L, t0;
+        for (int p = p0; p < p1 && ok;) {
+          const int np = emu_segment(p, p1, maxp, &L, &t0);
+          p += np;
+          const int nb = np * KB;
           for (int c0 = 0; c0 < nb && ok; c0 += EM_CHUNK_KB) {
             if (!mbar_wait(&acc_empty[abuf], aphase ^ 1, tmo, args.status)) {
               ok = false;
@@ -283,27 +390,43 @@ __global__ void __launch_bounds__(EM_THREADS, 1)
       mbar_wait(mma_done, 0, tmo, args.status);
     }
     __syncwarp();
-  } else if (warp >= 4) {
+  }
+  } else {
+    asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(EM_REGS_EPI));
     // ------------------------------ epilogue ----------------------------------
     const int q = warp & 3;           // TMEM lanes 32q .. 32q + 31 (hardware rule)
     const int h = (warp - 4) >> 2;    // column half of the tile
     const int r_in_tile = 32 * q + lane;
     constexpr int HALF = BN / 2;
-    int32_t* my_scratch = args.scratch + static_cast<size_t>(blockIdx.x) * nseg * EM_BM * BN;
+    constexpr size_t SLOT = static_cast<size_t>(EM_BM) * BN;  // int32 elements per slot
+    int32_t* my_scratch = args.scratch + static_cast<size_t>(blockIdx.x) * args.scratch_slots * SLOT;
     int abuf = 0;
     uint32_t aphase = 0;
     bool ok = true;
-    for (int tile = blockIdx.x; tile < args.total_tiles && ok; tile += gridDim.x) {
-      int pi;
-      const Problem* P = emu_problem(args, tile, &pi);
+    for (int u = blockIdx.x; u < args.total_units && ok; u += gridDim.x) {
+      const UnitRef U = emu_unit(args, u);
+      const Problem* P = U.P;
       const int n = P->n;
-      const int local = tile - P->tile_begin;
-      const int m0 = (local / P->tiles_n) * EM_BM;
-      const int n0 = (local % P->tiles_n) * BN;
+      const int m0 = (U.tile_local / P->tiles_n) * EM_BM;
+      const int n0 = (U.tile_local % P->tiles_n) * BN;
       const int KB = P->k_pad / EM_BK;
       const int row = m0 + r_in_tile;
-      for (int sg = 0; sg < nseg && ok; ++sg) {
-        const int nb = args.seg.np[sg] * KB;
+      int p0, p1;
+      emu_group_range(s, U.G, U.g, &p0, &p1);
+      // slot of this unit's first segment, and where the tile's slots live
+      int slot = 0;
+      for (int g = 0; g < U.g; ++g) {
+        int q0, q1;
+        emu_group_range(s, U.G, g, &q0, &q1);
+        slot += emu_count_segments(q0, q1, maxp);
+      }
+      int32_t* tile_slots = U.G > 1 ? args.tilebuf + P->slot_base + static_cast<long long>(U.tile_local) * P->nslots * SLOT
+                                    : my_scratch;
+      int L, t0;
+      for (int p = p0; p < p1 && ok; ++slot) {
+        const int np = emu_segment(p, p1, maxp, &L, &t0);
+        p += np;
+        const int nb = np * KB;
         const int nchunks = (nb + EM_CHUNK_KB - 1) / EM_CHUNK_KB;
         uint32_t acc[HALF];
 #pragma unroll
@@ -334,11 +457,10 @@ __global__ void __launch_bounds__(EM_THREADS, 1)
         if (!ok) break;
         const uint32_t bias = static_cast<uint32_t>(nchunks) * EM_MAGIC;
         if (args.levels_out) {
-          // step API: accumulate this segment into level L of levels_out
+          // step API (one group per tile): accumulate this segment into level L
           if (row < n) {
-            const int L = args.seg.L[sg];
             int32_t* dst = args.levels_out + static_cast<size_t>(L - 2) * n * n + static_cast<size_t>(row) * n;
-            const bool first = args.seg.t0[sg] == 1;
+            const bool first = t0 == 1;
 #pragma unroll
             for (int i = 0; i < HALF; ++i) {
               const int col = n0 + h * HALF + i;
@@ -349,7 +471,7 @@ __global__ void __launch_bounds__(EM_THREADS, 1)
             }
           }
         } else {
-          int32_t* dst = my_scratch + (static_cast<size_t>(sg) * EM_BM + r_in_tile) * BN + h * HALF;
+          int32_t* dst = tile_slots + static_cast<size_t>(slot) * SLOT + slot_index(r_in_tile, h * HALF);
 #pragma unroll
           for (int i = 0; i < HALF; i += 4) {
             int4 v;
@@ -357,41 +479,32 @@ __global__ void __launch_bounds__(EM_THREADS, 1)
             v.y = static_cast<int32_t>(acc[i + 1] - bias);
             v.z = static_cast<int32_t>(acc[i + 2] - bias);
             v.w = static_cast<int32_t>(acc[i + 3] - bias);
-            *reinterpret_cast<int4*>(dst + i) = v;
+            *reinterpret_cast<int4*>(dst + (i >> 2) * (EM_BM * 4)) = v;
           }
         }
       }
-      if (!ok || args.levels_out || row >= n) continue;
-      // Recombination: T = sum_L S_L 256^(s+1-L) in 128-bit integers, one rounding.
-      const int e_row = P->a_exp[row];
-      const int base_scale = e_row - 8 * args.s - 6;
-      const int32_t* src = my_scratch + static_cast<size_t>(r_in_tile) * BN + h * HALF;
+      if (!ok || args.levels_out) continue;
+      bool mine = true;
+      if (U.G > 1) {
+        // Each epilogue warp owns the same 32 x BN/2 region in every unit of
+        // the tile.  The warp that finishes its region last (counted per
+        // tile and region, no waiting) recombines it from all units' slots.
+        __threadfence();
+        __syncwarp();
+        int before = 0;
+        if (lane == 0)
+          before = atomicAdd(&args.tile_counters[(P->tile_begin + U.tile_local) * 8 + (warp - 4)], 1);
+        before = __shfl_sync(0xffffffffu, before, 0);
+        mine = before == U.G - 1;
+        if (mine) __threadfence();
+      }
+      if (!mine || row >= n) continue;
+      const int base_scale = P->a_exp[row] - 8 * s - 6;
       double* crow = P->C + static_cast<size_t>(row) * n;
-      for (int i = 0; i < HALF; i += 4) {
-        const int col = n0 + h * HALF + i;
-        if (col >= n) break;
-        int64_t th[4] = {0, 0, 0, 0};
-        uint64_t tl[4] = {0, 0, 0, 0};
-        int curL = 2;
-        for (int sg = 0; sg < nseg; ++sg) {
-          const int L = args.seg.L[sg];
-          const int4 v = *reinterpret_cast<const int4*>(src + static_cast<size_t>(sg) * EM_BM * BN + i);
-          const int sh = 8 * (L - curL);
-          curL = L;
-          i128_shift_add(th[0], tl[0], sh, v.x);
-          i128_shift_add(th[1], tl[1], sh, v.y);
-          i128_shift_add(th[2], tl[2], sh, v.z);
-          i128_shift_add(th[3], tl[3], sh, v.w);
-        }
-        const int tail = 8 * (args.s + 1 - curL);
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          if (col + j < n) {
-            i128_shift_add(th[j], tl[j], tail, 0);
-            crow[col + j] = round_i128_scaled(th[j], tl[j], base_scale + P->b_exp[col + j]);
-          }
-        }
-      }
+      if (U.G > 1)
+        recombine_row<BN, true>(tile_slots, s, U.G, maxp, r_in_tile, h * HALF, n0, n, base_scale, P->b_exp, crow);
+      else
+        recombine_row<BN, false>(tile_slots, s, 1, maxp, r_in_tile, h * HALF, n0, n, base_scale, P->b_exp, crow);
     }
   }
 
@@ -420,24 +533,6 @@ __global__ void recombine_kernel(int n, int s, const int32_t* __restrict__ level
 // Host side
 // ---------------------------------------------------------------------------
 
-// Segments: levels L = 2..s+1 in order, each cut into runs of at most
-// max_pairs pairs (t, L - t), t = 1..L-1.
-bool emu_build_segments(int s, int max_pairs, SegTable* out) {
-  int ns = 0;
-  for (int L = 2; L <= s + 1; ++L) {
-    for (int t0 = 1; t0 <= L - 1; t0 += max_pairs) {
-      if (ns >= EM_MAX_SEG) return false;
-      const int np = (L - 1) - t0 + 1 < max_pairs ? (L - 1) - t0 + 1 : max_pairs;
-      out->L[ns] = static_cast<int8_t>(L);
-      out->t0[ns] = static_cast<int8_t>(t0);
-      out->np[ns] = static_cast<int8_t>(np);
-      ++ns;
-    }
-  }
-  out->nseg = ns;
-  return true;
-}
-
 int emu_smem_bytes(int bn) { return bn == 256 ? EmuCfg<256>::SMEM_BYTES : EmuCfg<128>::SMEM_BYTES; }
 
 template <int BN>
@@ -452,7 +547,7 @@ static cudaError_t launch_bn(const CUtensorMap* mapA, const CUtensorMap* mapB, c
 
 cudaError_t emu_gemm_launch(int bn, const CUtensorMap* mapA, const CUtensorMap* mapB, const EmuArgs& args, int grid,
                             cudaStream_t stream) {
-  if (args.total_tiles <= 0) return cudaSuccess;
+  if (args.total_units <= 0) return cudaSuccess;
   return bn == 256 ? launch_bn<256>(mapA, mapB, args, grid, stream) : launch_bn<128>(mapA, mapB, args, grid, stream);
 }
 

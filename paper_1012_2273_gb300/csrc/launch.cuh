@@ -6,26 +6,73 @@
 
 namespace mmk {
 
-constexpr int EM_MAX_SEG = 48;
+// ---------------------------------------------------------------------------
+// Digit pairs of the emulation.  The products kept are the pairs (t, u),
+// t, u >= 1, t + u = L for the levels L = 2..s+1; they are numbered level by
+// level, p = (L-2)(L-1)/2 + (t-1), so p runs over [0, s(s+1)/2).  A work unit
+// of the slice-product kernel is one tile of C and a contiguous range of pair
+// numbers ("group"); its pairs are cut into segments -- runs of one level,
+// at most max_pairs long -- each summed exactly in one int32 accumulator.
+// Host and device share these helpers so that both cut the same segments.
+// ---------------------------------------------------------------------------
+__host__ __device__ inline int emu_pairs(int s) { return s * (s + 1) / 2; }
 
-// Accumulation segments of the emulation: levels L = 2..s+1 in order, each cut
-// into runs of digit pairs (t, L - t) short enough for an int32 sum.
-struct SegTable {
-  int nseg;
-  int8_t L[EM_MAX_SEG];   // level t + u of the segment
-  int8_t t0[EM_MAX_SEG];  // first t of the segment (1-based)
-  int8_t np[EM_MAX_SEG];  // pairs in the segment: (t0, L - t0), (t0 + 1, L - t0 - 1), ...
-};
+__host__ __device__ inline void emu_pair_of(int p, int* L, int* t) {
+  int level = 2, count = 1;
+  while (p >= count) {
+    p -= count;
+    ++level;
+    ++count;
+  }
+  *L = level;
+  *t = p + 1;
+}
+
+__host__ __device__ inline void emu_group_range(int s, int G, int g, int* p0, int* p1) {
+  const int P = emu_pairs(s);
+  *p0 = g * P / G;
+  *p1 = (g + 1) * P / G;
+}
+
+// Segment starting at pair p (< p1): its level *L, first t *t0; returns its pair count.
+__host__ __device__ inline int emu_segment(int p, int p1, int max_pairs, int* L, int* t0) {
+  emu_pair_of(p, L, t0);
+  int np = (*L - 1) - (*t0 - 1);  // pairs left in this level
+  if (np > max_pairs) np = max_pairs;
+  if (np > p1 - p) np = p1 - p;
+  return np;
+}
+
+__host__ __device__ inline int emu_count_segments(int p0, int p1, int max_pairs) {
+  int n = 0, L, t0;
+  for (int p = p0; p < p1; p += emu_segment(p, p1, max_pairs, &L, &t0)) ++n;
+  return n;
+}
+
+// Segment slots of a whole tile split into G groups (groups are cut apart too).
+__host__ __device__ inline int emu_tile_slots(int s, int G, int max_pairs) {
+  int n = 0;
+  for (int g = 0; g < G; ++g) {
+    int p0, p1;
+    emu_group_range(s, G, g, &p0, &p1);
+    n += emu_count_segments(p0, p1, max_pairs);
+  }
+  return n;
+}
 
 struct EmuArgs {
   const Problem* table;      // grouped: device problem table (else nullptr)
   Problem single;            // used when table == nullptr
   const CUtensorMap* maps;   // grouped: 2 maps per problem (A planes, B^T planes)
+  const int4* units;         // grouped: {problem, tile within problem, group, 0}; nullptr: single, group-major
   int count;
-  int total_tiles;
+  int total_units;
   int s;
-  SegTable seg;
-  int32_t* scratch;          // [gridDim.x][nseg][128][BN] int32 segment sums
+  int max_pairs;             // longest run of pairs whose products share an int32 sum
+  int32_t* scratch;          // per-CTA slots [gridDim.x][scratch_slots][128][BN] (problems with groups == 1)
+  int scratch_slots;
+  int32_t* tilebuf;          // per-tile slots (problems with groups > 1), see Problem::slot_base
+  int* tile_counters;        // [global tile][8 epilogue regions]: units finished, zero at launch
   int32_t* levels_out;       // step API: level sums [s][n][n] instead of C (else nullptr)
   int* status;
   uint64_t timeout_ns;
@@ -43,7 +90,6 @@ cudaError_t split_launch(const Problem* table, const Problem* single, int count,
                          cudaStream_t stream);
 
 // emu_gemm.cu
-bool emu_build_segments(int s, int max_pairs, SegTable* out);
 int emu_smem_bytes(int bn);
 cudaError_t emu_gemm_launch(int bn, const CUtensorMap* mapA, const CUtensorMap* mapB, const EmuArgs& args, int grid,
                             cudaStream_t stream);

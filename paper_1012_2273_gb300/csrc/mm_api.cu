@@ -16,6 +16,7 @@
 #include <map>
 #include <sstream>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "launch.cuh"
@@ -66,6 +67,7 @@ struct Plan {
   int form;    // 0 native, 1 emulation
   int slices;  // emulation digit count
   int bn;      // emulation tile width (128 or 256)
+  int groups;  // digit-pair groups per tile (0 = chosen from the SM count)
 };
 
 struct GraphEntry {
@@ -157,12 +159,12 @@ void prof_end(mm_handle h, cudaStream_t s, long mark) {
 // native path is as fast and exact enough, above it the emulation wins.
 void default_tune(mm_handle h) {
   h->tune.clear();
-  h->tune.push_back({255, Plan{0, 7, 128}});
-  h->tune.push_back({1024, Plan{1, 7, 128}});
-  h->tune.push_back({1 << 30, Plan{1, 7, 256}});
+  h->tune.push_back({255, Plan{0, 7, 256, 0}});
+  h->tune.push_back({1 << 30, Plan{1, 7, 256, 0}});
 }
 
-// Tune file: lines "max_n form slices bn" ('#' starts a comment).
+// Tune file: lines "max_n form slices bn [groups]" ('#' starts a comment):
+// problems with N <= max_n (first matching line) use that plan.
 bool load_tune(mm_handle h, const std::string& path) {
   std::ifstream in(path);
   if (!in) return false;
@@ -173,9 +175,12 @@ bool load_tune(mm_handle h, const std::string& path) {
     if (hash != std::string::npos) line.resize(hash);
     std::istringstream ss(line);
     long maxn;
-    Plan p;
+    Plan p{0, 7, 256, 0};
     if (!(ss >> maxn >> p.form >> p.slices >> p.bn)) continue;
-    if ((p.form != 0 && p.form != 1) || p.slices < 1 || p.slices > 8 || (p.bn != 128 && p.bn != 256)) return false;
+    if (!(ss >> p.groups)) p.groups = 0;
+    if ((p.form != 0 && p.form != 1) || p.slices < 1 || p.slices > 8 || (p.bn != 128 && p.bn != 256) ||
+        p.groups < 0 || p.groups > 36)
+      return false;
     rows.push_back({static_cast<int>(std::min<long>(maxn, 1 << 30)), p});
   }
   if (rows.empty()) return false;
@@ -243,27 +248,55 @@ mm_status ensure_arena(mm_handle h, size_t bytes) {
 
 // One launch group of the emulation: problems sharing (s, bn).
 struct EmuGroup {
-  int s = 7, bn = 128, grid = 1;
-  mmk::SegTable seg{};
+  bool tabled = false;  // launched with a device problem/unit table (grouped calls)
+  int groups = 0;       // forced pair groups per tile (0 = automatic)
+  int s = 7, bn = 256, grid = 1, max_pairs = 1;
   std::vector<Problem> ps;
   std::vector<int> max_off;        // offset of problem p in the maxbits arrays
   std::vector<CUtensorMap> maps;   // 2 per problem
-  int total_tiles = 0, total_split = 0, max_rows = 0;
+  std::vector<int4> units;         // grouped launches: {problem, tile, group, cost}
+  int total_tiles = 0, total_split = 0, total_units = 0, max_rows = 0, scratch_slots = 1;
+  long long tilebuf_elems = 0;
   // byte offsets inside the group's region of the arena
-  size_t amax = 0, bmax = 0, scratch = 0, bytes = 0;
+  size_t amax = 0, bmax = 0, scratch = 0, tilebuf = 0, counters = 0, bytes = 0;
   char* base = nullptr;
 };
 
-// Sizes the group's workspace; with `base` set, also points the problems into it.
+// Pair groups per tile for a problem launched alone: the count whose units
+// fill the SMs best, with a small preference for fewer groups (each extra
+// group adds one round trip of segment sums through memory).
+int choose_groups_single(int tiles, int s, int kb, int sms) {
+  const int P = mmk::emu_pairs(s);
+  int best = 1;
+  double best_score = -1.0;
+  for (int G = 1; G <= P; ++G) {
+    if (G > 1 && P * kb / G < 8) break;  // keep units at least 8 k-blocks long
+    const long long units = static_cast<long long>(tiles) * G;
+    const long long waves = (units + sms - 1) / sms;
+    const double eff = static_cast<double>(units) / static_cast<double>(waves * sms);
+    const double score = eff - 0.01 * (G - 1);
+    if (score > best_score + 1e-9) {
+      best_score = score;
+      best = G;
+    }
+  }
+  return best;
+}
+
+// Sizes the group's workspace and work units; with `base` set, also points
+// the problems into it and encodes the tensor maps.
 mm_status layout_group(mm_handle h, EmuGroup& g, char* base) {
   Arena ar;
   g.total_tiles = g.total_split = g.max_rows = 0;
   int maxn = 0;
   g.max_off.assign(g.ps.size(), 0);
+  for (Problem& p : g.ps) maxn = std::max(maxn, p.n);
+  g.max_pairs = max_pairs_for(maxn);
+  const int P = mmk::emu_pairs(g.s);
+  long long work = 0;
   for (size_t i = 0; i < g.ps.size(); ++i) {
     Problem& p = g.ps[i];
     const int n = p.n;
-    maxn = std::max(maxn, n);
     p.m_pad = round_up(n, 128);
     p.n_pad = round_up(n, g.bn);
     p.k_pad = round_up(n, 64);
@@ -273,6 +306,7 @@ mm_status layout_group(mm_handle h, EmuGroup& g, char* base) {
     g.total_tiles += p.tiles_m * p.tiles_n;
     p.split_begin = g.total_split;
     g.total_split += mmk::split_tiles(p);
+    work += static_cast<long long>(p.tiles_m) * p.tiles_n * P * (p.k_pad / 64);
     const size_t a_sl = ar.take(static_cast<size_t>(g.s) * p.m_pad * p.k_pad * 2);
     const size_t b_sl = ar.take(static_cast<size_t>(g.s) * p.n_pad * p.k_pad * 2);
     const size_t ae = ar.take(sizeof(int) * n);
@@ -286,12 +320,61 @@ mm_status layout_group(mm_handle h, EmuGroup& g, char* base) {
     g.max_off[i] = g.max_rows;
     g.max_rows += n;
   }
-  if (!mmk::emu_build_segments(g.s, max_pairs_for(maxn), &g.seg))
-    return fail(h, MM_ERR_UNSUPPORTED, "too many accumulation segments for this size");
-  g.grid = emu_grid(h, g.total_tiles);
+  // Work units: pair groups per tile, then slot storage.
+  const double target = static_cast<double>(work) / (4.0 * h->num_sms);
+  g.units.clear();
+  g.tilebuf_elems = 0;
+  g.scratch_slots = 1;
+  const long long slot = 128LL * g.bn;
+  for (size_t i = 0; i < g.ps.size(); ++i) {
+    Problem& p = g.ps[i];
+    const int tiles = p.tiles_m * p.tiles_n;
+    const int kb = p.k_pad / 64;
+    int G;
+    if (g.groups > 0) {
+      G = std::min(g.groups, P);
+    } else if (g.ps.size() == 1) {
+      G = choose_groups_single(tiles, g.s, kb, h->num_sms);
+    } else {
+      G = static_cast<int>(std::lround(P * kb / std::max(target, 1.0)));
+      G = std::max(1, std::min(G, P));
+    }
+    p.groups = G;
+    p.nslots = mmk::emu_tile_slots(g.s, G, g.max_pairs);
+    if (G > 1) {
+      p.slot_base = g.tilebuf_elems;
+      g.tilebuf_elems += static_cast<long long>(tiles) * p.nslots * slot;
+    } else {
+      p.slot_base = 0;
+      g.scratch_slots = std::max(g.scratch_slots, p.nslots);
+    }
+    if (g.tabled) {
+      for (int gi = 0; gi < G; ++gi) {
+        int p0, p1;
+        mmk::emu_group_range(g.s, G, gi, &p0, &p1);
+        const int cost = (p1 - p0) * kb;
+        for (int t = 0; t < tiles; ++t) g.units.push_back(make_int4(static_cast<int>(i), t, gi, cost));
+      }
+    }
+  }
+  if (g.tabled) {
+    // Longest units first, then group-major so concurrent CTAs share slices.
+    std::stable_sort(g.units.begin(), g.units.end(), [](const int4& a, const int4& b) {
+      if (a.w != b.w) return a.w > b.w;
+      if (a.x != b.x) return a.x < b.x;
+      if (a.z != b.z) return a.z < b.z;
+      return a.y < b.y;
+    });
+    g.total_units = static_cast<int>(g.units.size());
+  } else {
+    g.total_units = g.ps[0].tiles_m * g.ps[0].tiles_n * g.ps[0].groups;
+  }
+  g.grid = emu_grid(h, g.total_units);
   g.amax = ar.take(sizeof(uint64_t) * g.max_rows);
   g.bmax = ar.take(sizeof(uint64_t) * g.max_rows);
-  g.scratch = ar.take(static_cast<size_t>(g.grid) * g.seg.nseg * 128 * g.bn * sizeof(int32_t));
+  g.scratch = ar.take(static_cast<size_t>(g.grid) * g.scratch_slots * slot * sizeof(int32_t));
+  g.tilebuf = ar.take(static_cast<size_t>(std::max<long long>(g.tilebuf_elems, 4)) * sizeof(int32_t));
+  g.counters = ar.take(sizeof(int) * 8 * std::max(g.total_tiles, 1));
   g.bytes = ar.off;
   g.base = base;
   if (base) {
@@ -308,11 +391,11 @@ mm_status layout_group(mm_handle h, EmuGroup& g, char* base) {
 
 // Enqueues the emulated path of group g: zero the maxima, scale+split, slice
 // products with fused recombination.  With d_table == nullptr the group must
-// hold one problem, passed by value; otherwise d_table/d_maps/d_max_off are
-// device copies of g.ps, g.maps and g.max_off.
+// hold one problem, passed by value; otherwise d_table/d_maps/d_max_off/d_units
+// are device copies of g.ps, g.maps, g.max_off and g.units.
 mm_status run_group(mm_handle h, const EmuGroup& g, const Problem* d_table, const CUtensorMap* d_maps,
-                    const int* d_max_off, cudaStream_t stream) {
-  if (g.total_tiles == 0) return MM_OK;
+                    const int* d_max_off, const int4* d_units, cudaStream_t stream) {
+  if (g.total_units == 0) return MM_OK;
   uint64_t* amax = reinterpret_cast<uint64_t*>(g.base + g.amax);
   uint64_t* bmax = reinterpret_cast<uint64_t*>(g.base + g.bmax);
   const bool single = d_table == nullptr;
@@ -322,15 +405,23 @@ mm_status run_group(mm_handle h, const EmuGroup& g, const Problem* d_table, cons
   MM_CUDA(h, mmk::split_launch(d_table, single ? &g.ps[0] : nullptr, static_cast<int>(g.ps.size()), g.total_split,
                                g.s, amax, bmax, single ? nullptr : d_max_off, h->d_status, stream));
   prof_end(h, stream, m_split);
+  bool any_split = false;
+  for (const Problem& p : g.ps) any_split |= p.groups > 1;
+  int* counters = reinterpret_cast<int*>(g.base + g.counters);
+  if (any_split) MM_CUDA(h, cudaMemsetAsync(counters, 0, sizeof(int) * 8 * g.total_tiles, stream));
   mmk::EmuArgs a{};
   a.table = d_table;
   if (single) a.single = g.ps[0];
   a.maps = d_maps;
+  a.units = single ? nullptr : d_units;
   a.count = static_cast<int>(g.ps.size());
-  a.total_tiles = g.total_tiles;
+  a.total_units = g.total_units;
   a.s = g.s;
-  a.seg = g.seg;
+  a.max_pairs = g.max_pairs;
   a.scratch = reinterpret_cast<int32_t*>(g.base + g.scratch);
+  a.scratch_slots = g.scratch_slots;
+  a.tilebuf = reinterpret_cast<int32_t*>(g.base + g.tilebuf);
+  a.tile_counters = counters;
   a.levels_out = nullptr;
   a.status = h->d_status;
   a.timeout_ns = h->timeout_ns;
@@ -352,12 +443,13 @@ mm_status check_emu_size(mm_handle h, int n, int s) {
 }
 
 // Single emulated problem: workspace, maps, launches (no device table).
-mm_status emu_single(mm_handle h, const Problem& p, int s, int bn, cudaStream_t stream) {
+mm_status emu_single(mm_handle h, const Problem& p, int s, int bn, int groups, cudaStream_t stream) {
   mm_status st = check_emu_size(h, p.n, s);
   if (st != MM_OK) return st;
   EmuGroup g;
   g.s = s;
   g.bn = bn;
+  g.groups = groups;
   g.ps.push_back(p);
   st = layout_group(h, g, nullptr);
   if (st != MM_OK) return st;
@@ -365,7 +457,7 @@ mm_status emu_single(mm_handle h, const Problem& p, int s, int bn, cudaStream_t 
   if (st != MM_OK) return st;
   st = layout_group(h, g, static_cast<char*>(h->arena));
   if (st != MM_OK) return st;
-  return run_group(h, g, nullptr, nullptr, nullptr, stream);
+  return run_group(h, g, nullptr, nullptr, nullptr, nullptr, stream);
 }
 
 mm_status native_single(mm_handle h, Problem p, cudaStream_t stream) {
@@ -522,7 +614,7 @@ mm_status mm_gemm(mm_handle h, int N, const double* A, const double* B, double* 
   const Plan plan = plan_for(h, N);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (plan.form == 0) return native_single(h, p, s);
-  return emu_single(h, p, plan.slices, plan.bn, s);
+  return emu_single(h, p, plan.slices, plan.bn, plan.groups, s);
 }
 
 mm_status mm_gemm_host(mm_handle h, int N, const double* A_host, const double* B_host, double* C_host,
@@ -573,7 +665,7 @@ mm_status mm_gemm_grouped(mm_handle h, int count, const int* Ns, const double* c
 
   // Partition: native problems, and emulated problems by (slices, bn).
   std::vector<Problem> nat;
-  std::map<std::pair<int, int>, std::vector<Problem>> emu;
+  std::map<std::tuple<int, int, int>, std::vector<Problem>> emu;
   for (int i = 0; i < count; ++i) {
     if (Ns[i] == 0) continue;
     Problem p{};
@@ -587,7 +679,7 @@ mm_status mm_gemm_grouped(mm_handle h, int count, const int* Ns, const double* c
     } else {
       mm_status st = check_emu_size(h, p.n, pl.slices);
       if (st != MM_OK) return st;
-      emu[{pl.slices, pl.bn}].push_back(p);
+      emu[{pl.slices, pl.bn, pl.groups}].push_back(p);
     }
   }
   int nat_tiles = 0;
@@ -603,8 +695,10 @@ mm_status mm_gemm_grouped(mm_handle h, int count, const int* Ns, const double* c
   size_t arena_need = 0;
   for (auto& kv : emu) {
     EmuGroup g;
-    g.s = kv.first.first;
-    g.bn = kv.first.second;
+    g.tabled = true;
+    g.s = std::get<0>(kv.first);
+    g.bn = std::get<1>(kv.first);
+    g.groups = std::get<2>(kv.first);
     g.ps = kv.second;
     mm_status st = layout_group(h, g, nullptr);
     if (st != MM_OK) return st;
@@ -624,11 +718,12 @@ mm_status mm_gemm_grouped(mm_handle h, int count, const int* Ns, const double* c
   // Device-side tables: [native problems][per group: problems, maps, max offsets].
   Arena tab;
   const size_t off_nat = tab.take(sizeof(Problem) * std::max<size_t>(nat.size(), 1));
-  std::vector<size_t> off_tab, off_maps, off_mo;
+  std::vector<size_t> off_tab, off_maps, off_mo, off_units;
   for (const EmuGroup& g : groups) {
     off_tab.push_back(tab.take(sizeof(Problem) * g.ps.size()));
     off_maps.push_back(tab.take(sizeof(CUtensorMap) * g.maps.size()));
     off_mo.push_back(tab.take(sizeof(int) * g.max_off.size()));
+    off_units.push_back(tab.take(sizeof(int4) * std::max<size_t>(g.units.size(), 1)));
   }
   const size_t tab_bytes = tab.off;
   std::vector<char> host_tab(tab_bytes, 0);
@@ -638,6 +733,7 @@ mm_status mm_gemm_grouped(mm_handle h, int count, const int* Ns, const double* c
     std::memcpy(host_tab.data() + off_tab[gi], g.ps.data(), sizeof(Problem) * g.ps.size());
     std::memcpy(host_tab.data() + off_maps[gi], g.maps.data(), sizeof(CUtensorMap) * g.maps.size());
     std::memcpy(host_tab.data() + off_mo[gi], g.max_off.data(), sizeof(int) * g.max_off.size());
+    if (!g.units.empty()) std::memcpy(host_tab.data() + off_units[gi], g.units.data(), sizeof(int4) * g.units.size());
   }
 
   auto launch_all = [&](char* dtab, cudaStream_t s) -> mm_status {
@@ -650,7 +746,8 @@ mm_status mm_gemm_grouped(mm_handle h, int count, const int* Ns, const double* c
     for (size_t gi = 0; gi < groups.size(); ++gi) {
       mm_status st = run_group(h, groups[gi], reinterpret_cast<Problem*>(dtab + off_tab[gi]),
                                reinterpret_cast<CUtensorMap*>(dtab + off_maps[gi]),
-                               reinterpret_cast<int*>(dtab + off_mo[gi]), s);
+                               reinterpret_cast<int*>(dtab + off_mo[gi]),
+                               reinterpret_cast<int4*>(dtab + off_units[gi]), s);
       if (st != MM_OK) return st;
     }
     return MM_OK;
@@ -782,6 +879,8 @@ mm_status mm_level_sums(mm_handle h, int N, int slices, const uint16_t* a_digits
   p.tiles_m = (N + 127) / 128;
   p.tiles_n = (N + bn - 1) / bn;
   p.tile_begin = 0;
+  p.groups = 1;
+  p.nslots = slices;
   std::vector<CUtensorMap> maps(2);
   if (!make_plane_map(&maps[0], a_digits, ld, static_cast<long>(slices) * a_rows, 128) ||
       !make_plane_map(&maps[1], b_digits, ld, static_cast<long>(slices) * b_rows, bn))
@@ -789,14 +888,15 @@ mm_status mm_level_sums(mm_handle h, int N, int slices, const uint16_t* a_digits
   mmk::EmuArgs a{};
   a.single = p;
   a.count = 1;
-  a.total_tiles = p.tiles_m * p.tiles_n;
+  a.total_units = p.tiles_m * p.tiles_n;
   a.s = slices;
-  if (!mmk::emu_build_segments(slices, slices, &a.seg)) return fail(h, MM_ERR_UNSUPPORTED, "segments");
+  a.max_pairs = slices;  // every level in one segment: level sums fit int32 (checked above)
   a.scratch = nullptr;
+  a.scratch_slots = 0;
   a.levels_out = levels;
   a.status = h->d_status;
   a.timeout_ns = h->timeout_ns;
-  const cudaError_t le = mmk::emu_gemm_launch(bn, &maps[0], &maps[1], a, emu_grid(h, a.total_tiles),
+  const cudaError_t le = mmk::emu_gemm_launch(bn, &maps[0], &maps[1], a, emu_grid(h, a.total_units),
                                               static_cast<cudaStream_t>(stream));
   if (le != cudaSuccess) {
     char info[512];

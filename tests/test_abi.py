@@ -70,3 +70,16 @@ def test_sources_have_no_cpu_fallback_or_oracle_use():
 @pytest.mark.parametrize("flag", ["-gencode", "arch=compute_103a,code=sm_103a"])
 def test_build_targets_sm103a_only(flag):
     assert flag in mmbuild.NVCC_FLAGS
+
+
+def test_tune_file_is_validated_before_any_device_work(tmp_path):
+    bad = tmp_path / "bad.txt"
+    bad.write_text("1000 1 9 256\n")  # 9 slices: out of range
+    L = mm.lib()
+    cfg = mm._Config(mm.AUTO, 0, 0, str(bad).encode())
+    h = ctypes.c_void_p()
+    assert L.mm_create(ctypes.byref(h), ctypes.byref(cfg)) == 1  # MM_ERR_INVALID
+    bad.write_text("1000 1 7 192\n")  # tile width must be 128 or 256
+    assert L.mm_create(ctypes.byref(h), ctypes.byref(cfg)) == 1
+    missing = mm._Config(mm.AUTO, 0, 0, str(tmp_path / "none.txt").encode())
+    assert L.mm_create(ctypes.byref(h), ctypes.byref(missing)) == 1

@@ -217,3 +217,24 @@ def test_auto_plan_picks_native_for_small_and_emulation_for_large():
     with mm.Handle("auto") as h:
         assert h.plan(10)[0] == 0
         assert h.plan(4096)[0] == 1
+
+
+@pytest.mark.parametrize("groups", [1, 2, 5, 13, 28])
+def test_forced_pair_groups_are_bit_exact(tmp_path, groups):
+    # Units = (tile, pair group); any split of the 28 digit pairs (s = 7) must
+    # give the same bits: the partial sums are integers, added exactly.
+    import paper_1012_2273_gb300 as mm
+    tune = tmp_path / "tune.txt"
+    tune.write_text(f"# max_n form slices bn groups\n100000 1 7 256 {groups}\n")
+    n = 300
+    A, B = workload.pair("uniform11", 7, n)
+    with mm.Handle("emulated", slices=7, tune_path=str(tune)) as h:
+        C = host(h.gemm(dev(A), dev(B)))
+        sizes = [300, 64, 513]
+        pairs = [workload.pair("uniform01", 20 + i, m) for i, m in enumerate(sizes)]
+        Cs = h.gemm_grouped([dev(a) for a, _ in pairs], [dev(b) for _, b in pairs])
+        h.check()
+    want = oracle.emu_gemm(A, B, 7)
+    np.testing.assert_array_equal(C.view(np.int64), want.view(np.int64))
+    for (a, b), c in zip(pairs, Cs):
+        np.testing.assert_array_equal(host(c).view(np.int64), oracle.emu_gemm(a, b, 7).view(np.int64))
