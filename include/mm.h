@@ -143,6 +143,30 @@ mm_status mm_probe_fp64_peak(mm_handle h, double* dmma_tflops, double* dfma_tflo
 mm_status mm_split(mm_handle h, int N, const double* M, int by_columns, int slices, int* exps,
                    uint16_t* digits, int rows, int ld, void* stream);
 
+/* Scale and split without allocating: the same computation and output
+ * layout as mm_split, for callers that may not allocate device memory at all
+ * (code living inside another framework's memory pool, services that forbid
+ * allocation after start-up, code that must avoid the device-wide
+ * synchronisation of cudaFree).  It needs no handle.  The paper has no
+ * counterpart; this is an interface convenience of the library.
+ *   - Its only scratch (one 64-bit maximum per row or column) is a static
+ *     device array of MM_SPLIT_NOALLOC_MAX_N entries (512 KiB) that exists on
+ *     every GPU that loads the library, until the process exits.
+ *   - N > MM_SPLIT_NOALLOC_MAX_N returns MM_ERR_UNSUPPORTED; bad arguments
+ *     return MM_ERR_INVALID; nothing is launched in either case.
+ *   - The first call on each device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture.
+ *   - Every call uses the same array: calls that overlap on the GPU (on
+ *     different streams, or from several threads) race and corrupt each
+ *     other's exponents.  Serialise them on one stream.
+ *   - status: optional device int (may be NULL); the first error found on the
+ *     device (MM_ERR_NONFINITE for an Inf or NaN input) is stored there if it
+ *     holds 0.  Returns after enqueueing the work on `stream`. */
+#define MM_SPLIT_NOALLOC_MAX_N 65536
+mm_status mm_split_noalloc(int N, const double* M, int by_columns, int slices, int* exps, uint16_t* digits,
+                           int rows, int ld, int* status, void* stream);
+
 /* Exact level sums of digit products: for L = 2..s+1,
  *   S_L(i,k) = sum_j sum_{t+u=L} d_t(a_ij) d_u(b_jk)
  * written as int32 to levels[(L-2)*N*N + i*N + k].  Inputs are the digit

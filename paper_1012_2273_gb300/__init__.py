@@ -49,8 +49,9 @@ class _Config(ctypes.Structure):
 
 
 SYMBOLS = ("mm_create", "mm_destroy", "mm_gemm", "mm_gemm_grouped", "mm_gemm_host", "mm_status_get",
-           "mm_last_error", "mm_plan", "mm_profile_read", "mm_probe_fp64_peak", "mm_split", "mm_level_sums",
-           "mm_recombine")
+           "mm_last_error", "mm_plan", "mm_profile_read", "mm_probe_fp64_peak", "mm_split", "mm_split_noalloc",
+           "mm_level_sums", "mm_recombine")
+SPLIT_NOALLOC_MAX_N = 65536
 KERNEL_KINDS = ("split", "slice_products", "native_fp64", "recombine")
 
 
@@ -79,6 +80,7 @@ def lib(build_if_needed: bool = True) -> ctypes.CDLL:
             L.mm_last_error.restype = ctypes.c_char_p
             L.mm_plan.argtypes = [vp, ci, ctypes.POINTER(ci), ctypes.POINTER(ci)]
             L.mm_split.argtypes = [vp, ci, vp, ci, ci, vp, vp, ci, ci, vp]
+            L.mm_split_noalloc.argtypes = [ci, vp, ci, ci, vp, vp, ci, ci, vp, vp]
             L.mm_level_sums.argtypes = [vp, ci, ci, vp, ci, vp, ci, ci, vp, vp]
             L.mm_recombine.argtypes = [vp, ci, ci, vp, vp, vp, vp, vp]
             L.mm_profile_read.argtypes = [vp, ctypes.POINTER(cd), ctypes.POINTER(ci)]
@@ -108,6 +110,24 @@ def _check_tensor(t, name: str, n: int | None = None):
         raise ValueError(f"{name} must be contiguous (row-major)")
     if t.dim() != 2 or t.shape[0] != t.shape[1] or (n is not None and t.shape[0] != n):
         raise ValueError(f"{name} must be square" + (f" of size {n}" if n is not None else ""))
+
+
+def split_noalloc(M, by_columns: bool, slices: int, exps, digits, status=None, stream=None) -> int:
+    """mm_split_noalloc: scale and split into caller-provided buffers, allocating nothing.
+
+    For callers that may not allocate device memory: the library's only
+    scratch for this step is a fixed static device array (N <= 65536).
+    `exps` (int32 [N]) and `digits` (int16 [s][rows][ld], bf16 bit patterns)
+    are CUDA tensors the caller owns; `status` an optional int32 CUDA tensor.
+    Calls sharing the device must not overlap on the GPU.  Returns the
+    mm_status code (0 = enqueued).
+    """
+    _check_tensor(M, "M")
+    n = M.shape[0]
+    s_, rows, ld = digits.shape
+    return int(lib().mm_split_noalloc(n, M.data_ptr(), int(bool(by_columns)), int(slices), exps.data_ptr(),
+                                      digits.data_ptr(), rows, ld, status.data_ptr() if status is not None else None,
+                                      _stream_ptr(stream)))
 
 
 class Handle:
