@@ -1,6 +1,11 @@
 """One small, self-contained product for kernel profiling (e.g. under ncu).
 
     python -m paper_1012_2273_gb300.profile_case --n 2048 --form emulated --reps 3
+    python -m paper_1012_2273_gb300.profile_case --sweep --reps 2
+
+--sweep runs the benchmark's step instead: one grouped call over the paper's
+size sweep (N = 10, 100, 500, 1000, 1500, 2000, automatic plan), the exact
+launches bench.py times.
 
 Generates seeded inputs (uniform [0, 1), seed 0), runs the product `reps`
 times through the C ABI and exits 0 if every call succeeded.  The operands of
@@ -23,6 +28,7 @@ def main() -> int:
     ap.add_argument("--slices", type=int, default=0)
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--dist", default="uniform01")
+    ap.add_argument("--sweep", action="store_true", help="run the benchmark's grouped sweep step")
     args = ap.parse_args()
 
     import torch
@@ -30,6 +36,17 @@ def main() -> int:
     import paper_1012_2273_gb300 as mm
     import workload
 
+    if args.sweep:
+        pairs = [workload.pair("uniform01", 0, n) for n in workload.SWEEP_SIZES]
+        As = [torch.from_numpy(a).cuda() for a, _ in pairs]
+        Bs = [torch.from_numpy(b).cuda() for _, b in pairs]
+        with mm.Handle("auto") as h:
+            for _ in range(args.reps):
+                h.gemm_grouped(As, Bs)
+            h.check()
+        torch.cuda.synchronize()
+        print(f"profile_case: sweep {list(workload.SWEEP_SIZES)} reps={args.reps} ok")
+        return 0
     A, B = workload.pair(args.dist, 0, args.n)
     dA = torch.from_numpy(A).cuda()
     dB = torch.from_numpy(B).cuda()
