@@ -168,10 +168,12 @@ __device__ __forceinline__ size_t slot_index(int row, int col) {
   return static_cast<size_t>(col >> 2) * (EM_BM * 4) + static_cast<size_t>(row) * 4 + (col & 3);
 }
 
+// Slots written by other CTAs are read from L2 (bypassing L1, which is not
+// coherent with them); a CTA's own scratch is read as streaming data.
 template <bool kCacheGlobal>
 __device__ __forceinline__ int4 load_slot4(const int32_t* p) {
   const int4* q = reinterpret_cast<const int4*>(p);
-  return kCacheGlobal ? __ldcg(q) : *q;
+  return kCacheGlobal ? __ldcg(q) : __ldcs(q);
 }
 
 // Sum of the segment slots of one tile in 128-bit integers (levels ascending),
@@ -221,7 +223,7 @@ __device__ __forceinline__ void recombine_row(const int32_t* tile_slots, int s, 
       const int col = n0 + tcol + j;
       if (col < n) {
         i128_shift_add(th[j], tl[j], tail, 0);
-        crow[col] = round_i128_scaled(th[j], tl[j], base_scale + b_exp[col]);
+        __stcs(crow + col, round_i128_scaled(th[j], tl[j], base_scale + b_exp[col]));
       }
     }
   }
@@ -288,11 +290,16 @@ __global__ void __launch_bounds__(EM_THREADS, 1)
       uint32_t phase = 0;
       long issued = 0;
       bool ok = true;
+      // Digit planes are re-read by the other tiles of the band and by later
+      // digit pairs: keep them in L2 ahead of streaming data.
+      const uint64_t keep = l2_policy_evict_last();
       for (int u = blockIdx.x; u < args.total_units && ok; u += gridDim.x) {
         const UnitRef U = emu_unit(args, u);
         const Problem* P = U.P;
-        const int m0 = (U.tile_local / P->tiles_n) * EM_BM;
-        const int n0 = (U.tile_local % P->tiles_n) * BN;
+        int tm, tn;
+        emu_tile_coords(U.tile_local, P->tiles_m, P->tiles_n, &tm, &tn);
+        const int m0 = tm * EM_BM;
+        const int n0 = tn * BN;
         const int KB = P->k_pad / EM_BK;
         const CUtensorMap* ma = args.units ? &args.maps[2 * U.pi] : &mapA;
         const CUtensorMap* mb = args.units ? &args.maps[2 * U.pi + 1] : &mapB;
@@ -309,8 +316,8 @@ __global__ void __launch_bounds__(EM_THREADS, 1)
             }
             uint8_t* sa = smem + stage * Cfg::STAGE_BYTES;
             mbar_arrive_expect_tx(&full[stage], Cfg::STAGE_BYTES);
-            tma_load_2d(sa, ma, &full[stage], kb * EM_BK, (t - 1) * P->m_pad + m0);
-            tma_load_2d(sa + Cfg::A_BYTES, mb, &full[stage], kb * EM_BK, (uu - 1) * P->n_pad + n0);
+            tma_load_2d_hint(sa, ma, &full[stage], kb * EM_BK, (t - 1) * P->m_pad + m0, keep);
+            tma_load_2d_hint(sa + Cfg::A_BYTES, mb, &full[stage], kb * EM_BK, (uu - 1) * P->n_pad + n0, keep);
             ++issued;
             if (++stage == Cfg::STAGES) {
               stage = 0;
@@ -407,8 +414,10 @@ __global__ void __launch_bounds__(EM_THREADS, 1)
       const UnitRef U = emu_unit(args, u);
       const Problem* P = U.P;
       const int n = P->n;
-      const int m0 = (U.tile_local / P->tiles_n) * EM_BM;
-      const int n0 = (U.tile_local % P->tiles_n) * BN;
+      int tm, tn;
+      emu_tile_coords(U.tile_local, P->tiles_m, P->tiles_n, &tm, &tn);
+      const int m0 = tm * EM_BM;
+      const int n0 = tn * BN;
       const int KB = P->k_pad / EM_BK;
       const int row = m0 + r_in_tile;
       int p0, p1;
@@ -479,7 +488,7 @@ __global__ void __launch_bounds__(EM_THREADS, 1)
             v.y = static_cast<int32_t>(acc[i + 1] - bias);
             v.z = static_cast<int32_t>(acc[i + 2] - bias);
             v.w = static_cast<int32_t>(acc[i + 3] - bias);
-            *reinterpret_cast<int4*>(dst + (i >> 2) * (EM_BM * 4)) = v;
+            __stcs(reinterpret_cast<int4*>(dst + (i >> 2) * (EM_BM * 4)), v);  // read once, by the recombination
           }
         }
       }

@@ -60,6 +60,18 @@ __host__ __device__ inline int emu_tile_slots(int s, int G, int max_pairs) {
   return n;
 }
 
+// Tile order: bands of EMU_BAND tile-columns, row-major inside a band, so the
+// ~150 tiles in flight at once share few A row-panels and few B column-panels.
+constexpr int EMU_BAND = 8;
+__host__ __device__ inline void emu_tile_coords(int tile, int tiles_m, int tiles_n, int* tm, int* tn) {
+  const int band_tiles = tiles_m * EMU_BAND;
+  const int band = tile / band_tiles;
+  const int in_band = tile - band * band_tiles;
+  const int width = (tiles_n - band * EMU_BAND) < EMU_BAND ? (tiles_n - band * EMU_BAND) : EMU_BAND;
+  *tm = in_band / width;
+  *tn = band * EMU_BAND + (in_band - (in_band / width) * width);
+}
+
 struct EmuArgs {
   const Problem* table;      // grouped: device problem table (else nullptr)
   Problem single;            // used when table == nullptr

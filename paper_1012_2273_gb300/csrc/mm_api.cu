@@ -262,21 +262,25 @@ struct EmuGroup {
   char* base = nullptr;
 };
 
-// Pair groups per tile for a problem launched alone: the count whose units
-// fill the SMs best, with a small preference for fewer groups (each extra
-// group adds one round trip of segment sums through memory).
-int choose_groups_single(int tiles, int s, int kb, int sms) {
+// Pair groups per tile for a problem launched alone.  Estimated time =
+// waves of units x the longest unit's k-blocks x the time of one k-block on
+// the tensor cores, plus, when G > 1, one write and one read of every tile's
+// segment slots through memory.  The constants are GB300 measurements: about
+// 0.35 us per 128 x 256 x 64 k-block of digit products in steady state, and
+// about 6 TB/s for streaming slot traffic.
+int choose_groups_single(int tiles, int s, int kb, int sms, int max_pairs) {
   const int P = mmk::emu_pairs(s);
+  const double t_kb = 0.35e-6, bw = 6.0e12, slot_bytes = 128.0 * 256.0 * 4.0;
   int best = 1;
-  double best_score = -1.0;
+  double best_t = 1e30;
   for (int G = 1; G <= P; ++G) {
-    if (G > 1 && P * kb / G < 8) break;  // keep units at least 8 k-blocks long
     const long long units = static_cast<long long>(tiles) * G;
     const long long waves = (units + sms - 1) / sms;
-    const double eff = static_cast<double>(units) / static_cast<double>(waves * sms);
-    const double score = eff - 0.01 * (G - 1);
-    if (score > best_score + 1e-9) {
-      best_score = score;
+    const int longest = (P + G - 1) / G;
+    double t = static_cast<double>(waves) * longest * kb * t_kb;
+    if (G > 1) t += 2.0 * tiles * mmk::emu_tile_slots(s, G, max_pairs) * slot_bytes / bw;
+    if (t < best_t * 0.98) {  // a new group count must win by 2%
+      best_t = t;
       best = G;
     }
   }
@@ -334,7 +338,7 @@ mm_status layout_group(mm_handle h, EmuGroup& g, char* base) {
     if (g.groups > 0) {
       G = std::min(g.groups, P);
     } else if (g.ps.size() == 1) {
-      G = choose_groups_single(tiles, g.s, kb, h->num_sms);
+      G = choose_groups_single(tiles, g.s, kb, h->num_sms, g.max_pairs);
     } else {
       G = static_cast<int>(std::lround(P * kb / std::max(target, 1.0)));
       G = std::max(1, std::min(G, P));
