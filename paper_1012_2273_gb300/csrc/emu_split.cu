@@ -23,7 +23,6 @@ namespace mmk {
 
 constexpr int SP_TILE = 64;
 constexpr int SP_THREADS = 256;
-constexpr uint32_t kMagicF32 = 0x4B400000u;  // bits of 1.5 * 2^23
 
 struct SplitArgs {
   const Problem* table;
@@ -93,31 +92,50 @@ __device__ __forceinline__ int64_t fixed_point(uint64_t bits, int e, int s, bool
   return neg ? -static_cast<int64_t>(D) : static_cast<int64_t>(D);
 }
 
-// bf16 bit pattern of a small integer d (|d| <= 256): exact through an FP32
-// add on the 1.5 * 2^23 grid, then the top half of the FP32 pattern (the
-// low 16 bits are zero for at most 8 significant bits).
-__device__ __forceinline__ uint32_t bf16_of_small_int(int d) {
-  const float f = __int_as_float(static_cast<int>(kMagicF32) + d) - 12582912.0f;
-  return __float_as_uint(f) >> 16;
+// Digits d_1..d_s of D (balanced base 256: d_2..d_s in [-128, 127]).  With
+// M = sum_{k=0}^{s-2} 128 * 256^k, the low s-1 bytes of D + M are exactly
+// d_t + 128 (t = s, s-1, ..., 2, least significant first) and (D + M) >> 8(s-1)
+// is d_1: adding 128 to every lower position turns the balanced digits into
+// plain bytes.  D + M itself can exceed the int64 range at s = 8, so M is
+// added to the low 8(s-1) bits alone and their carry is added to d_1.  Each digit d
+// becomes a float exactly (0x4B400000 | (d + 128) is 2^23 + 2^22 + d + 128)
+// and pairs of them become bf16x2 with one round-to-nearest conversion, exact
+// for integers of at most 8 significant bits.  Output: packed bf16x2 words,
+// word w of element q holds digit planes (2w, 2w+1).
+__device__ __forceinline__ uint32_t bf16x2_of_digits(float lo, float hi) {
+  uint32_t r;
+  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+  return r;
 }
 
-// Digits d_1..d_s of D (bottom-up balanced base-256), as bf16 patterns.
+__device__ __forceinline__ float digit_float(uint32_t biased_byte) {
+  return __uint_as_float(0x4B400000u | biased_byte) - 12583040.0f;  // (2^23 + 2^22 + 128) -> d
+}
+
 template <int S>
-__device__ __forceinline__ void digits_of(int64_t D, uint32_t (&out)[S]) {
+__device__ __forceinline__ void digits_of(int64_t D, float (&out)[S]) {
+  constexpr int SH = 8 * (S - 1);
+  constexpr uint64_t M = (S > 1) ? (0x8080808080808080ull >> (8 * (9 - S))) : 0ull;
+  constexpr uint64_t MASK = (S > 1) ? ((1ull << SH) - 1) : 0ull;
+  // Lower digits from the low SH bits only: (D mod 2^SH) + M < 2^(SH+1), no overflow.
+  const uint64_t low = (static_cast<uint64_t>(D) & MASK) + M;
 #pragma unroll
   for (int t = S - 1; t >= 1; --t) {
-    const int r = static_cast<int>(D & 255);
-    const int d = r >= 128 ? r - 256 : r;
-    out[t] = bf16_of_small_int(d);
-    D = (D - d) >> 8;
+    const uint32_t b = static_cast<uint32_t>(low >> (8 * (S - 1 - t))) & 255u;
+    out[t] = digit_float(b);
   }
-  out[0] = bf16_of_small_int(static_cast<int>(D));
+  // d_1 = floor(D / 2^SH) plus the carry out of the low part; |d_1| <= 128.
+  const int d1 = static_cast<int>(D >> SH) + static_cast<int>(low >> SH);
+  out[0] = static_cast<float>(d1);
 }
 
 // Row maxima of |A| and column maxima of |B| (as bit patterns; for finite
-// values the unsigned order of |v|'s pattern is the order of |v|).
+// values the unsigned order of |v|'s pattern is the order of |v|).  One 64 x 64
+// tile per CTA; reads are coalesced along the rows of the source, partial
+// maxima are reduced in registers and warps, and one global atomicMax per
+// row (A) or column (B) per tile publishes them.
 __global__ void __launch_bounds__(SP_THREADS) absmax_kernel(const __grid_constant__ SplitArgs args) {
-  __shared__ unsigned long long smax[SP_TILE];
+  __shared__ unsigned long long part[SP_THREADS / SP_TILE][SP_TILE];
   const Problem* P;
   const int pi = split_find(args, blockIdx.x, &P);
   const int n = P->n;
@@ -130,45 +148,62 @@ __global__ void __launch_bounds__(SP_THREADS) absmax_kernel(const __grid_constan
   const int c0 = (local % kt) * SP_TILE;  // A: columns j; B^T: rows j of B
   if (r0 >= n || c0 >= n) return;          // tile lies in the padding
   const int off = args.max_offset ? args.max_offset[pi] : 0;
-  if (threadIdx.x < SP_TILE) smax[threadIdx.x] = 0ull;
-  __syncthreads();
-  const int c = threadIdx.x % SP_TILE;
   const uint64_t* src = reinterpret_cast<const uint64_t*>(is_a ? P->A : P->B);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (is_a) {
-    // thread handles column c0 + c of rows r0 + q (q = tid/64 + 4i): coalesced along j
-    const int j = c0 + c;
-    for (int q = threadIdx.x / SP_TILE; q < SP_TILE; q += SP_THREADS / SP_TILE) {
-      const int i = r0 + q;
-      if (i < n && j < n) {
-        const unsigned long long v = src[static_cast<size_t>(i) * n + j] & 0x7FFFFFFFFFFFFFFFull;
-        if (v) atomicMax(&smax[q], v);
+    // warp w: rows r0 + w, r0 + w + 8, ...; lanes cover the 64 columns twice
+    for (int r = warp; r < SP_TILE; r += SP_THREADS / 32) {
+      const int i = r0 + r;
+      unsigned long long m = 0;
+      if (i < n) {
+        const int j0 = c0 + lane, j1 = c0 + lane + 32;
+        if (j0 < n) m = src[static_cast<size_t>(i) * n + j0] & 0x7FFFFFFFFFFFFFFFull;
+        if (j1 < n) {
+          const unsigned long long v = src[static_cast<size_t>(i) * n + j1] & 0x7FFFFFFFFFFFFFFFull;
+          m = v > m ? v : m;
+        }
       }
-    }
-    __syncthreads();
-    if (threadIdx.x < SP_TILE && r0 + threadIdx.x < n && smax[threadIdx.x])
-      atomicMax(reinterpret_cast<unsigned long long*>(&args.a_maxbits[off + r0 + threadIdx.x]), smax[threadIdx.x]);
-  } else {
-    // thread handles column k = r0 + c of B over rows j = c0 + q
-    const int k = r0 + c;
-    unsigned long long m = 0;
-    for (int q = threadIdx.x / SP_TILE; q < SP_TILE; q += SP_THREADS / SP_TILE) {
-      const int j = c0 + q;
-      if (j < n && k < n) {
-        const unsigned long long v = src[static_cast<size_t>(j) * n + k] & 0x7FFFFFFFFFFFFFFFull;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long v = __shfl_xor_sync(0xffffffffu, m, o);
         m = v > m ? v : m;
       }
+      if (lane == 0 && i < n && m) atomicMax(reinterpret_cast<unsigned long long*>(&args.a_maxbits[off + i]), m);
     }
-    if (m) atomicMax(&smax[c], m);
+  } else {
+    // thread: column k = r0 + (tid % 64) of B over rows j = c0 + tid / 64 + 4q
+    const int c = threadIdx.x % SP_TILE, q0 = threadIdx.x / SP_TILE;
+    const int k = r0 + c;
+    unsigned long long m = 0;
+    if (k < n) {
+      for (int q = q0; q < SP_TILE; q += SP_THREADS / SP_TILE) {
+        const int j = c0 + q;
+        if (j < n) {
+          const unsigned long long v = src[static_cast<size_t>(j) * n + k] & 0x7FFFFFFFFFFFFFFFull;
+          m = v > m ? v : m;
+        }
+      }
+    }
+    part[q0][c] = m;
     __syncthreads();
-    if (threadIdx.x < SP_TILE && r0 + threadIdx.x < n && smax[threadIdx.x])
-      atomicMax(reinterpret_cast<unsigned long long*>(&args.b_maxbits[off + r0 + threadIdx.x]), smax[threadIdx.x]);
+    if (threadIdx.x < SP_TILE && r0 + threadIdx.x < n) {
+      unsigned long long mm = 0;
+#pragma unroll
+      for (int w = 0; w < SP_THREADS / SP_TILE; ++w) mm = part[w][threadIdx.x] > mm ? part[w][threadIdx.x] : mm;
+      if (mm) atomicMax(reinterpret_cast<unsigned long long*>(&args.b_maxbits[off + r0 + threadIdx.x]), mm);
+    }
   }
 }
 
-// Writes the digit planes.  Thread item = 8 consecutive j of one output row
-// (A: row i; B^T: row k), stored as one 16-byte vector per plane.
+// Writes the digit planes of one 64 x 64 tile.  Phase 1 reads the tile
+// coalesced along the source rows and stores each fixed-point value D in
+// shared memory, transposed for B^T; phase 2 turns 8 consecutive D of an
+// output row into one 16-byte vector per plane (8 threads write a row's 128
+// contiguous bytes).
 template <int S>
 __global__ void __launch_bounds__(SP_THREADS) split_kernel(const __grid_constant__ SplitArgs args) {
+  __shared__ long long Ds[SP_TILE][SP_TILE + 1];
+  __shared__ int any_nonfinite;
   const Problem* P;
   const int pi = split_find(args, blockIdx.x, &P);
   const int n = P->n;
@@ -177,8 +212,8 @@ __global__ void __launch_bounds__(SP_THREADS) split_kernel(const __grid_constant
   int local = blockIdx.x - (args.table ? P->split_begin : 0);
   const bool is_a = local < a_tiles;
   if (!is_a) local -= a_tiles;
-  const int r0 = (local / kt) * SP_TILE;
-  const int c0 = (local % kt) * SP_TILE;
+  const int r0 = (local / kt) * SP_TILE;  // output rows: A rows i / B columns k
+  const int c0 = (local % kt) * SP_TILE;  // output columns: j
   const int off = args.max_offset ? args.max_offset[pi] : 0;
   const int rows = is_a ? P->m_pad : P->n_pad;
   const size_t plane = static_cast<size_t>(rows) * P->k_pad;
@@ -186,47 +221,54 @@ __global__ void __launch_bounds__(SP_THREADS) split_kernel(const __grid_constant
   const uint64_t* src = reinterpret_cast<const uint64_t*>(is_a ? P->A : P->B);
   const uint64_t* maxbits = is_a ? args.a_maxbits + off : args.b_maxbits + off;
   int* exps = is_a ? P->a_exp : P->b_exp;
+  if (threadIdx.x == 0) any_nonfinite = 0;
   bool nonfinite = false;
 
-  // 64 rows x 8 groups of 8 columns = 512 items, 2 per thread.  Items are
-  // numbered so that a warp covers 32 consecutive output rows of one column
-  // group for B^T (coalesced reads of B along k) and 4 rows x 8 groups for A.
-  for (int item = threadIdx.x; item < SP_TILE * (SP_TILE / 8); item += SP_THREADS) {
-    int r, cg;
+  // Phase 1: source element (x, y) of the tile, x fastest (coalesced).
+  //   A:   source row i = r0 + y, column j = c0 + x -> Ds[y][x]  (output row y)
+  //   B^T: source row j = c0 + y, column k = r0 + x -> Ds[x][y]  (output row x)
+  for (int idx = threadIdx.x; idx < SP_TILE * SP_TILE; idx += SP_THREADS) {
+    const int x = idx % SP_TILE, y = idx / SP_TILE;
+    long long D = 0;
     if (is_a) {
-      r = item >> 3;
-      cg = item & 7;
-    } else {
-      r = item & 63;
-      cg = item >> 6;
-    }
-    const int row = r0 + r;       // A: i; B^T: k
-    const int col = c0 + cg * 8;  // first of 8 consecutive j
-    const int e = row < n ? exponent_from_maxbits(maxbits[row]) : 0;
-    if (row < n && col == 0 && exps) exps[row] = e;
-    uint32_t dig[8][S];
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      const int j = col + q;
-      int64_t D = 0;
-      if (row < n && j < n) {
-        const uint64_t bits = is_a ? src[static_cast<size_t>(row) * n + j] : src[static_cast<size_t>(j) * n + row];
-        D = fixed_point(bits, e, S, &nonfinite);
+      const int i = r0 + y, j = c0 + x;
+      if (i < n && j < n) {
+        const int e = exponent_from_maxbits(maxbits[i]);
+        if (j == 0 && exps) exps[i] = e;
+        D = fixed_point(src[static_cast<size_t>(i) * n + j], e, S, &nonfinite);
       }
-      digits_of<S>(D, dig[q]);
+      Ds[y][x] = D;
+    } else {
+      const int j = c0 + y, k = r0 + x;
+      if (j < n && k < n) {
+        const int f = exponent_from_maxbits(maxbits[k]);
+        if (j == 0 && exps) exps[k] = f;
+        D = fixed_point(src[static_cast<size_t>(j) * n + k], f, S, &nonfinite);
+      }
+      Ds[x][y] = D;
     }
-    uint16_t* out = dst + static_cast<size_t>(row) * P->k_pad + col;
+  }
+  if (nonfinite) any_nonfinite = 1;
+  __syncthreads();
+
+  // Phase 2: item = (output row r, group cg of 8 columns); 8 items per row.
+  for (int item = threadIdx.x; item < SP_TILE * (SP_TILE / 8); item += SP_THREADS) {
+    const int r = item >> 3, cg = item & 7;
+    float dig[8][S];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) digits_of<S>(Ds[r][cg * 8 + q], dig[q]);
+    uint16_t* out = dst + static_cast<size_t>(r0 + r) * P->k_pad + c0 + cg * 8;
 #pragma unroll
     for (int t = 0; t < S; ++t) {
       uint4 v;
-      v.x = dig[0][t] | (dig[1][t] << 16);
-      v.y = dig[2][t] | (dig[3][t] << 16);
-      v.z = dig[4][t] | (dig[5][t] << 16);
-      v.w = dig[6][t] | (dig[7][t] << 16);
+      v.x = bf16x2_of_digits(dig[0][t], dig[1][t]);
+      v.y = bf16x2_of_digits(dig[2][t], dig[3][t]);
+      v.z = bf16x2_of_digits(dig[4][t], dig[5][t]);
+      v.w = bf16x2_of_digits(dig[6][t], dig[7][t]);
       *reinterpret_cast<uint4*>(out + t * plane) = v;
     }
   }
-  if (nonfinite) set_status(args.status, MM_ERR_NONFINITE);
+  if (threadIdx.x == 0 && any_nonfinite) set_status(args.status, MM_ERR_NONFINITE);
 }
 
 // Host side -------------------------------------------------------------------
