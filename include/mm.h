@@ -123,6 +123,14 @@ mm_status mm_profile_read(mm_handle h, double out_ms[4], int launches[4]);
  * in TFLOP/s: the roof of the native form.  Blocks for a few milliseconds. */
 mm_status mm_probe_fp64_peak(mm_handle h, double* dmma_tflops, double* dfma_tflops);
 
+/* Failure-detection self-test: enqueues a kernel that waits on an mbarrier
+ * nothing ever arrives on, through the same time-bounded wait every pipeline
+ * of the library uses.  After timeout_ms (1..60000) the wait gives up, the
+ * kernel records MM_ERR_TIMEOUT in the handle's status word and returns; the
+ * CUDA context stays usable.  mm_status_get then reports MM_ERR_TIMEOUT.
+ * The paper has no counterpart (its programs have no failure detection). */
+mm_status mm_selftest_wait(mm_handle h, int timeout_ms, void* stream);
+
 /* ---------------------------------------------------------------------
  * Steps of the emulation, exposed for testing each one on its own.
  * They use caller-provided device buffers with the layouts stated here.

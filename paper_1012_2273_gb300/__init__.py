@@ -49,7 +49,8 @@ class _Config(ctypes.Structure):
 
 
 SYMBOLS = ("mm_create", "mm_destroy", "mm_gemm", "mm_gemm_grouped", "mm_gemm_host", "mm_status_get",
-           "mm_last_error", "mm_plan", "mm_profile_read", "mm_probe_fp64_peak", "mm_split", "mm_split_noalloc",
+           "mm_last_error", "mm_plan", "mm_profile_read", "mm_probe_fp64_peak", "mm_selftest_wait", "mm_split",
+           "mm_split_noalloc",
            "mm_level_sums", "mm_recombine")
 SPLIT_NOALLOC_MAX_N = 65536
 KERNEL_KINDS = ("split", "slice_products", "native_fp64", "recombine")
@@ -85,6 +86,7 @@ def lib(build_if_needed: bool = True) -> ctypes.CDLL:
             L.mm_recombine.argtypes = [vp, ci, ci, vp, vp, vp, vp, vp]
             L.mm_profile_read.argtypes = [vp, ctypes.POINTER(cd), ctypes.POINTER(ci)]
             L.mm_probe_fp64_peak.argtypes = [vp, ctypes.POINTER(cd), ctypes.POINTER(cd)]
+            L.mm_selftest_wait.argtypes = [vp, ci, vp]
             for name in SYMBOLS:
                 if name != "mm_last_error":
                     getattr(L, name).restype = ci
@@ -234,6 +236,10 @@ class Handle:
         a, b = ctypes.c_double(), ctypes.c_double()
         self._raise(self._lib.mm_probe_fp64_peak(self._h, ctypes.byref(a), ctypes.byref(b)))
         return a.value, b.value
+
+    def selftest_wait(self, timeout_ms: int = 200, stream=None):
+        """Enqueues the bounded-wait self-test (see mm_selftest_wait)."""
+        self._raise(self._lib.mm_selftest_wait(self._h, int(timeout_ms), _stream_ptr(stream)))
 
     def plan(self, n: int) -> tuple[int, int]:
         form, s = ctypes.c_int(), ctypes.c_int()

@@ -1,0 +1,122 @@
+"""Autotuner: per size bucket, the fastest plan that keeps FP64 accuracy.
+
+    python -m paper_1012_2273_gb300.autotune --out tune/gb300.tune
+
+For each bucket of N it times the native FP64 form and the emulated form for
+every slice count s in 6..8 and tile width in {128, 256} (pair groups chosen
+automatically) at one representative size, and keeps the fastest plan whose
+result stays close to native FP64 -- at the representative size and at the
+bucket's smallest size -- on two input classes: uniform [-1, 1) and log-uniform
+magnitudes 2^U(-20,20).  "Close" means
+max |C_plan - C_native| / (|A||B|) <= N 2^-53 / 2; the native result is itself
+within gamma_N |A||B| of the exact product, so an accepted plan is within
+(N/2 + N + small) 2^-53 |A||B| < 2 N 2^-53 |A||B|, the library's accuracy
+contract.  |A||B| is computed by the native form on |A| and |B|.
+
+The output is a tune file ("max_n form slices bn groups" per line) that
+mm_create accepts as mm_config.tune_path; the library's built-in table is
+the result of running this on a GB300.
+"""
+from __future__ import annotations
+
+import argparse
+import os
+import statistics
+import sys
+import time
+
+sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+
+# (largest N of the bucket, size timed) -- accuracy is checked at the timed
+# size and at the bucket's smallest size, where the bound is tightest.
+BUCKETS = ((31, 24), (63, 48), (127, 96), (255, 192), (511, 384), (767, 640), (1023, 896), (1535, 1280),
+           (2047, 1792), (3071, 2560), (4095, 3584), (6143, 5120), (1 << 30, 8192))
+U = 2.0 ** -53
+
+
+def _time_ms(fn, flush, reps):
+    import torch
+    stream = torch.cuda.current_stream()
+    fn()
+    ts = []
+    for r in range(reps):
+        flush.fill_(float(r))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return statistics.median(ts)
+
+
+def tune(buckets=BUCKETS, slices=(6, 7, 8), widths=(128, 256), reps=5, log=print):
+    import torch
+
+    import paper_1012_2273_gb300 as mm
+    import workload
+
+    flush = torch.empty(128 << 20, dtype=torch.float32, device="cuda")
+    tmp = os.path.join(os.environ.get("TMPDIR", "/tmp"), f"mm_autotune_{os.getpid()}.tune")
+    rows = []
+    native = mm.Handle("native")
+    lo = 1
+    for max_n, n in buckets:
+        classes = []  # (A, B, native C, |A||B|, size)
+        for size in sorted({n, max(lo, 8)}, reverse=True):
+            for dist in ("uniform11", "loguniform20"):
+                A, B = workload.pair(dist, 0, size)
+                dA, dB = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+                ref = native.gemm(dA, dB)
+                absab = native.gemm(dA.abs(), dB.abs())
+                classes.append((dA, dB, ref, absab, size))
+        lo = max_n + 1
+        native.check()
+        best = ("native", 0, 256, _time_ms(lambda: native.gemm(classes[0][0], classes[0][1]), flush, reps))
+        log(f"N={n:5d} native {best[3]:.3f} ms")
+        for s in slices:
+            for bn in widths:
+                with open(tmp, "w") as f:
+                    f.write(f"{1 << 30} 1 {s} {bn} 0\n")
+                h = mm.Handle("emulated", slices=s, tune_path=tmp)
+                worst = 0.0  # deviation relative to each size's allowance N u / 2
+                for dA, dB, ref, absab, size in classes:
+                    C = h.gemm(dA, dB)
+                    d = ((C - ref).abs() / absab.clamp_min(1e-300)).max().item()
+                    worst = max(worst, d / (size * U / 2))
+                h.check()
+                ok = worst <= 1.0
+                ms = _time_ms(lambda: h.gemm(classes[0][0], classes[0][1]), flush, reps)
+                h.close()
+                log(f"N={n:5d} s={s} bn={bn} {ms:.3f} ms  max dev / allowance {worst:.3g} ({'ok' if ok else 'too far'})")
+                if ok and ms < best[3]:
+                    best = ("emulated", s, bn, ms)
+        rows.append((max_n, best))
+        log(f"N<={max_n}: {best[0]} s={best[1]} bn={best[2]} ({best[3]:.3f} ms at N={n})")
+    native.close()
+    if os.path.exists(tmp):
+        os.remove(tmp)
+    return rows
+
+
+def write(rows, path):
+    os.makedirs(os.path.dirname(os.path.abspath(path)), exist_ok=True)
+    with open(path, "w") as f:
+        f.write("# max_n form slices bn groups   (form 0 = native FP64, 1 = emulation; groups 0 = automatic)\n")
+        f.write(f"# written by paper_1012_2273_gb300.autotune on {time.strftime('%Y-%m-%d %H:%M')}\n")
+        for max_n, (form, s, bn, ms) in rows:
+            f.write(f"{max_n} {0 if form == 'native' else 1} {s if s else 7} {bn} 0   # {ms:.3f} ms\n")
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--out", default="tune.txt")
+    ap.add_argument("--reps", type=int, default=5)
+    args = ap.parse_args()
+    rows = tune(reps=args.reps)
+    write(rows, args.out)
+    print(f"wrote {args.out}")
+
+
+if __name__ == "__main__":
+    main()

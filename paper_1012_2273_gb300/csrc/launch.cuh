@@ -111,5 +111,6 @@ cudaError_t recombine_launch(int n, int s, const int32_t* levels, const int* e, 
 
 // probe.cu
 cudaError_t probe_fp64(int num_sms, double* sink, cudaStream_t stream, double* dmma, double* dfma);
+cudaError_t selftest_wait(int* status, uint64_t timeout_ns, int* gave_up, cudaStream_t stream);
 
 }  // namespace mmk

@@ -155,12 +155,20 @@ void prof_end(mm_handle h, cudaStream_t s, long mark) {
   if (mark >= 0) cudaEventRecord(h->ev_pool[static_cast<size_t>(mark) + 1], s);
 }
 
-// Built-in plan table (overridden by a tune file): below the crossover the
-// native path is as fast and exact enough, above it the emulation wins.
+// Built-in plan table (a tune file overrides it): the output of
+// paper_1012_2273_gb300.autotune on a GB300 (tune/gb300.tune).  Below N = 256
+// native FP64 is as fast and is the only form that meets the componentwise
+// bound for wide-range inputs at the smallest N; from there the emulation with
+// the fewest digits that stays within the bound on uniform and log-uniform
+// (2^+-20) inputs: 8 digits up to N = 767, 7 up to 4095, 6 above (the bound
+// 2 N 2^-53 |A||B| grows with N).
 void default_tune(mm_handle h) {
   h->tune.clear();
   h->tune.push_back({255, Plan{0, 7, 256, 0}});
-  h->tune.push_back({1 << 30, Plan{1, 7, 256, 0}});
+  h->tune.push_back({767, Plan{1, 8, 128, 0}});
+  h->tune.push_back({1023, Plan{1, 7, 128, 0}});
+  h->tune.push_back({4095, Plan{1, 7, 256, 0}});
+  h->tune.push_back({1 << 30, Plan{1, 6, 256, 0}});
 }
 
 // Tune file: lines "max_n form slices bn [groups]" ('#' starts a comment):
@@ -565,6 +573,13 @@ mm_status mm_profile_read(mm_handle h, double out_ms[4], int launches[4]) {
   return MM_OK;
 }
 
+mm_status mm_selftest_wait(mm_handle h, int timeout_ms, void* stream) {
+  if (!h || timeout_ms <= 0 || timeout_ms > 60000) return MM_ERR_INVALID;
+  MM_CUDA(h, mmk::selftest_wait(h->d_status, static_cast<uint64_t>(timeout_ms) * 1000000ull, nullptr,
+                                static_cast<cudaStream_t>(stream)));
+  return MM_OK;
+}
+
 mm_status mm_probe_fp64_peak(mm_handle h, double* dmma_tflops, double* dfma_tflops) {
   if (!h || !dmma_tflops || !dfma_tflops) return MM_ERR_INVALID;
   if (!h->probe_sink) MM_CUDA(h, cudaMalloc(&h->probe_sink, 64));
@@ -666,6 +681,29 @@ mm_status mm_gemm_grouped(mm_handle h, int count, const int* Ns, const double* c
   }
   cudaStream_t user = static_cast<cudaStream_t>(stream);
   prof_reset(h);
+  const bool use_graph = (h->cfg.flags & (MM_FLAG_NO_GRAPH | MM_FLAG_PROFILE)) == 0;
+
+  // A call identical to an earlier one replays its graph without redoing the
+  // host-side planning.  (Graphs are dropped whenever the arena is regrown.)
+  std::vector<long long> key;
+  key.reserve(4 * static_cast<size_t>(count) + 3);
+  key.push_back(count);
+  key.push_back(h->cfg.mode);
+  key.push_back(h->cfg.slices);
+  for (int i = 0; i < count; ++i) {
+    key.push_back(Ns[i]);
+    key.push_back(static_cast<long long>(reinterpret_cast<uintptr_t>(As[i])));
+    key.push_back(static_cast<long long>(reinterpret_cast<uintptr_t>(Bs[i])));
+    key.push_back(static_cast<long long>(reinterpret_cast<uintptr_t>(Cs[i])));
+  }
+  auto it = h->graphs.end();
+  if (use_graph) {
+    it = h->graphs.find(key);
+    if (it != h->graphs.end()) {
+      MM_CUDA(h, cudaGraphLaunch(it->second.exec, user));
+      return MM_OK;
+    }
+  }
 
   // Partition: native problems, and emulated problems by (slices, bn).
   std::vector<Problem> nat;
@@ -693,29 +731,67 @@ mm_status mm_gemm_grouped(mm_handle h, int count, const int* Ns, const double* c
     nat_tiles += p.tiles_m * p.tiles_n;
   }
 
-  // Workspace: the emulation groups are laid out one after another in the arena.
+  // Workspace.  Emulation groups run one after another on the same stream, so
+  // they all start at offset 0 of the arena; a group whose workspace exceeds
+  // the limit is cut into waves (largest problems first), each run in turn.
+  size_t limit = 0;
+  {
+    size_t free_b = 0, total_b = 0;
+    if (const char* e = std::getenv("MM_WORKSPACE_LIMIT_MB")) limit = static_cast<size_t>(std::atoll(e)) << 20;
+    if (!limit && cudaMemGetInfo(&free_b, &total_b) == cudaSuccess) {
+      const size_t reserve = size_t(1) << 30;
+      limit = h->arena_cap + (free_b > reserve ? (free_b - reserve) / 10 * 9 : 0);
+    }
+    cudaGetLastError();
+    if (!limit) limit = size_t(64) << 30;
+  }
   std::vector<EmuGroup> groups;
-  std::vector<size_t> group_off;
   size_t arena_need = 0;
   for (auto& kv : emu) {
-    EmuGroup g;
-    g.tabled = true;
-    g.s = std::get<0>(kv.first);
-    g.bn = std::get<1>(kv.first);
-    g.groups = std::get<2>(kv.first);
-    g.ps = kv.second;
-    mm_status st = layout_group(h, g, nullptr);
-    if (st != MM_OK) return st;
-    group_off.push_back(arena_need);
-    arena_need = align_up(arena_need + g.bytes, kAlign);
-    groups.push_back(std::move(g));
+    std::vector<Problem> rest = kv.second;
+    std::stable_sort(rest.begin(), rest.end(), [](const Problem& a, const Problem& b) { return a.n > b.n; });
+    size_t at = 0;
+    while (at < rest.size()) {
+      // Largest prefix of the remaining problems whose workspace fits the
+      // limit (binary search; at least one problem).
+      auto make = [&](size_t end) {
+        EmuGroup t;
+        t.tabled = true;
+        t.s = std::get<0>(kv.first);
+        t.bn = std::get<1>(kv.first);
+        t.groups = std::get<2>(kv.first);
+        t.ps.assign(rest.begin() + at, rest.begin() + end);
+        return t;
+      };
+      EmuGroup g = make(rest.size());
+      mm_status st = layout_group(h, g, nullptr);
+      if (st != MM_OK) return st;
+      size_t end = rest.size();
+      if (g.bytes > limit && rest.size() - at > 1) {
+        size_t lo = at + 1, hi = rest.size() - 1;  // lo always fits or is the single-problem floor
+        while (lo < hi) {
+          const size_t mid = (lo + hi + 1) / 2;
+          EmuGroup t = make(mid);
+          st = layout_group(h, t, nullptr);
+          if (st != MM_OK) return st;
+          if (t.bytes <= limit) lo = mid; else hi = mid - 1;
+        }
+        end = lo;
+        g = make(end);
+        st = layout_group(h, g, nullptr);
+        if (st != MM_OK) return st;
+      }
+      at = end;
+      arena_need = std::max(arena_need, g.bytes);
+      groups.push_back(std::move(g));
+    }
   }
   if (arena_need) {
     mm_status st = ensure_arena(h, arena_need);
     if (st != MM_OK) return st;
   }
   for (size_t gi = 0; gi < groups.size(); ++gi) {
-    mm_status st = layout_group(h, groups[gi], static_cast<char*>(h->arena) + group_off[gi]);
+    mm_status st = layout_group(h, groups[gi], static_cast<char*>(h->arena));
     if (st != MM_OK) return st;
   }
 
@@ -757,7 +833,6 @@ mm_status mm_gemm_grouped(mm_handle h, int count, const int* Ns, const double* c
     return MM_OK;
   };
 
-  const bool use_graph = (h->cfg.flags & (MM_FLAG_NO_GRAPH | MM_FLAG_PROFILE)) == 0;
   if (!use_graph) {
     if (tab_bytes > h->grp_table_cap) {
       if (h->grp_table) cudaFree(h->grp_table);
@@ -779,19 +854,7 @@ mm_status mm_gemm_grouped(mm_handle h, int count, const int* Ns, const double* c
     return launch_all(static_cast<char*>(h->grp_table), user);
   }
 
-  std::vector<long long> key;
-  key.reserve(4 * count + 4);
-  key.push_back(count);
-  key.push_back(h->cfg.mode);
-  key.push_back(h->cfg.slices);
-  key.push_back(static_cast<long long>(reinterpret_cast<uintptr_t>(h->arena)));
-  for (int i = 0; i < count; ++i) {
-    key.push_back(Ns[i]);
-    key.push_back(static_cast<long long>(reinterpret_cast<uintptr_t>(As[i])));
-    key.push_back(static_cast<long long>(reinterpret_cast<uintptr_t>(Bs[i])));
-    key.push_back(static_cast<long long>(reinterpret_cast<uintptr_t>(Cs[i])));
-  }
-  auto it = h->graphs.find(key);
+  it = h->graphs.find(key);  // the arena may have been regrown above (cache cleared)
   if (it == h->graphs.end()) {
     if (h->graphs.size() >= 32) {
       for (auto& kv : h->graphs) {

@@ -41,6 +41,26 @@ __global__ void probe_dfma_kernel(double* sink, int iters) {
   if (s == 1234567.0) sink[0] = s;
 }
 
+// Failure-detection self-test: waits on an mbarrier that nothing ever arrives
+// on, through the bounded wait every pipeline of the library uses.  The wait
+// must give up after `timeout_ns`, record MM_ERR_TIMEOUT and let the kernel
+// return normally.
+__global__ void selftest_wait_kernel(int* status, uint64_t timeout_ns, int* gave_up) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  const bool completed = mbar_wait(&bar, 0, timeout_ns, status);
+  if (threadIdx.x == 0 && gave_up) *gave_up = completed ? 0 : 1;
+}
+
+cudaError_t selftest_wait(int* status, uint64_t timeout_ns, int* gave_up, cudaStream_t stream) {
+  selftest_wait_kernel<<<1, 32, 0, stream>>>(status, timeout_ns, gave_up);
+  return cudaGetLastError();
+}
+
 // Runs both probes on `stream`; returns TFLOP/s through dmma/dfma.
 cudaError_t probe_fp64(int num_sms, double* sink, cudaStream_t stream, double* dmma, double* dfma) {
   const int blocks = num_sms * 4, threads = 256, iters = 1500;
