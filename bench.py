@@ -276,9 +276,8 @@ def run_ours(args, dist: Dist):
             launches_per_step = sum(v[1] for v in p.values())
     hp.check()
     emu_sizes = [n for n in SWEEP if plan[n][0] == 1]
-    s_emu = plan[emu_sizes[0]][1] if emu_sizes else 0
-    pairs = s_emu * (s_emu + 1) // 2
-    tensor_flops = pairs * sum(2 * n ** 3 for n in emu_sizes)
+    pairs_of = {n: plan[n][1] * (plan[n][1] + 1) // 2 for n in emu_sizes}
+    tensor_flops = sum(pairs_of[n] * 2 * n ** 3 for n in emu_sizes)
     gemm_ms = statistics.mean(kinds["slice_products"]) if emu_sizes else None
     digest = source_digest()
     traffic, traffic_meta = profiled_traffic(digest)
@@ -293,7 +292,8 @@ def run_ours(args, dist: Dist):
                     "traffic": traffic,
                     "algorithmic_flops_per_launch": tensor_flops,
                     "avg_launch_ms": round(gemm_ms, 4),
-                    "note": f"{pairs} digit-pair products of 2N^3 flops each for N in {emu_sizes}, s = {s_emu}"}
+                    "note": "digit-pair products of 2N^3 flops each: " + ", ".join(
+                        f"N={n}: s={plan[n][1]}, {pairs_of[n]} pairs" for n in emu_sizes)}
 
     # per-N comparison of the two forms (single calls, L2 flushed)
     per_n = per_size(mm, As, Bs, Cs, flush, stream)

@@ -35,6 +35,7 @@ struct Problem {
   int n_pad;           // rows of a B^T plane (multiple of the tile width)
   int k_pad;           // columns of a plane (multiple of 64)
   int split_begin;     // first split tile of this problem (scale/split kernels)
+  int s;               // digits per value (emulation), 1..8
   int groups;          // digit-pair groups per tile: work units per tile of the slice-product kernel
   int nslots;          // segment sums per tile (all groups together)
   long long slot_base; // int32 offset of this problem's tile 0 in the per-tile slot buffer (groups > 1)

@@ -270,7 +270,6 @@ __global__ void __launch_bounds__(EM_THREADS, 1)
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
   const uint64_t tmo = args.timeout_ns;
-  const int s = args.s;
   const int maxp = args.max_pairs;
 
   // Register split: the launch gives every thread EM_REGS_LAUNCH; warpgroup 0
@@ -304,7 +303,7 @@ __global__ void __launch_bounds__(EM_THREADS, 1)
         const CUtensorMap* ma = args.units ? &args.maps[2 * U.pi] : &mapA;
         const CUtensorMap* mb = args.units ? &args.maps[2 * U.pi + 1] : &mapB;
         int p0, p1;
-        emu_group_range(s, U.G, U.g, &p0, &p1);
+        emu_group_range(P->s, U.G, U.g, &p0, &p1);
         for (int p = p0; p < p1 && ok; ++p) {
           int L, t;
           emu_pair_of(p, &L, &t);
@@ -352,7 +351,7 @@ __global__ void __launch_bounds__(EM_THREADS, 1)
         const UnitRef U = emu_unit(args, u);
         const int KB = U.P->k_pad / EM_BK;
         int p0, p1;
-        emu_group_range(s, U.G, U.g, &p0, &p1);
+        emu_group_range(U.P->s, U.G, U.g, &p0, &p1);
         int L, t0;
         for (int p = p0; p < p1 && ok;) {
           const int np = emu_segment(p, p1, maxp, &L, &t0);
@@ -420,6 +419,7 @@ __global__ void __launch_bounds__(EM_THREADS, 1)
       const int n0 = tn * BN;
       const int KB = P->k_pad / EM_BK;
       const int row = m0 + r_in_tile;
+      const int s = P->s;
       int p0, p1;
       emu_group_range(s, U.G, U.g, &p0, &p1);
       // slot of this unit's first segment, and where the tile's slots live

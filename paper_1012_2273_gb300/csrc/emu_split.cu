@@ -28,7 +28,6 @@ struct SplitArgs {
   const Problem* table;
   Problem single;
   int count;
-  int s;
   int total_tiles;
   uint64_t* a_maxbits;  // per problem: [n] row maxima of |A| (bit patterns), at p's offset
   uint64_t* b_maxbits;  // per problem: [n] column maxima of |B|
@@ -200,13 +199,41 @@ __global__ void __launch_bounds__(SP_THREADS) absmax_kernel(const __grid_constan
 // shared memory, transposed for B^T; phase 2 turns 8 consecutive D of an
 // output row into one 16-byte vector per plane (8 threads write a row's 128
 // contiguous bytes).
+// Phase 2 of split_kernel for S digits: item = (output row r, group cg of 8
+// columns), 8 items per row; one 16-byte vector per digit plane.
 template <int S>
+__device__ __forceinline__ void write_digit_planes(const long long (&Ds)[SP_TILE][SP_TILE + 1], uint16_t* dst,
+                                                   int r0, int c0, int k_pad, size_t plane) {
+  for (int item = threadIdx.x; item < SP_TILE * (SP_TILE / 8); item += SP_THREADS) {
+    const int r = item >> 3, cg = item & 7;
+    float dig[8][S];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) digits_of<S>(Ds[r][cg * 8 + q], dig[q]);
+    uint16_t* out = dst + static_cast<size_t>(r0 + r) * k_pad + c0 + cg * 8;
+#pragma unroll
+    for (int t = 0; t < S; ++t) {
+      uint4 v;
+      v.x = bf16x2_of_digits(dig[0][t], dig[1][t]);
+      v.y = bf16x2_of_digits(dig[2][t], dig[3][t]);
+      v.z = bf16x2_of_digits(dig[4][t], dig[5][t]);
+      v.w = bf16x2_of_digits(dig[6][t], dig[7][t]);
+      *reinterpret_cast<uint4*>(out + t * plane) = v;
+    }
+  }
+}
+
+// Writes the digit planes of one 64 x 64 tile (digit count from the problem).
+// Phase 1 reads the tile coalesced along the source rows and stores each
+// fixed-point value D in shared memory, transposed for B^T; phase 2 turns 8
+// consecutive D of an output row into one 16-byte vector per plane (8 threads
+// write a row's 128 contiguous bytes).
 __global__ void __launch_bounds__(SP_THREADS) split_kernel(const __grid_constant__ SplitArgs args) {
   __shared__ long long Ds[SP_TILE][SP_TILE + 1];
   __shared__ int any_nonfinite;
   const Problem* P;
   const int pi = split_find(args, blockIdx.x, &P);
   const int n = P->n;
+  const int S = P->s;
   const int kt = P->k_pad / SP_TILE;
   const int a_tiles = (P->m_pad / SP_TILE) * kt;
   int local = blockIdx.x - (args.table ? P->split_begin : 0);
@@ -251,22 +278,15 @@ __global__ void __launch_bounds__(SP_THREADS) split_kernel(const __grid_constant
   if (nonfinite) any_nonfinite = 1;
   __syncthreads();
 
-  // Phase 2: item = (output row r, group cg of 8 columns); 8 items per row.
-  for (int item = threadIdx.x; item < SP_TILE * (SP_TILE / 8); item += SP_THREADS) {
-    const int r = item >> 3, cg = item & 7;
-    float dig[8][S];
-#pragma unroll
-    for (int q = 0; q < 8; ++q) digits_of<S>(Ds[r][cg * 8 + q], dig[q]);
-    uint16_t* out = dst + static_cast<size_t>(r0 + r) * P->k_pad + c0 + cg * 8;
-#pragma unroll
-    for (int t = 0; t < S; ++t) {
-      uint4 v;
-      v.x = bf16x2_of_digits(dig[0][t], dig[1][t]);
-      v.y = bf16x2_of_digits(dig[2][t], dig[3][t]);
-      v.z = bf16x2_of_digits(dig[4][t], dig[5][t]);
-      v.w = bf16x2_of_digits(dig[6][t], dig[7][t]);
-      *reinterpret_cast<uint4*>(out + t * plane) = v;
-    }
+  switch (S) {
+    case 1: write_digit_planes<1>(Ds, dst, r0, c0, P->k_pad, plane); break;
+    case 2: write_digit_planes<2>(Ds, dst, r0, c0, P->k_pad, plane); break;
+    case 3: write_digit_planes<3>(Ds, dst, r0, c0, P->k_pad, plane); break;
+    case 4: write_digit_planes<4>(Ds, dst, r0, c0, P->k_pad, plane); break;
+    case 5: write_digit_planes<5>(Ds, dst, r0, c0, P->k_pad, plane); break;
+    case 6: write_digit_planes<6>(Ds, dst, r0, c0, P->k_pad, plane); break;
+    case 7: write_digit_planes<7>(Ds, dst, r0, c0, P->k_pad, plane); break;
+    default: write_digit_planes<8>(Ds, dst, r0, c0, P->k_pad, plane); break;
   }
   if (threadIdx.x == 0 && any_nonfinite) set_status(args.status, MM_ERR_NONFINITE);
 }
@@ -278,7 +298,7 @@ int split_tiles(const Problem& p) {
   return (p.m_pad / SP_TILE + p.n_pad / SP_TILE) * (p.k_pad / SP_TILE);
 }
 
-cudaError_t split_launch(const Problem* table, const Problem* single, int count, int total_tiles, int s,
+cudaError_t split_launch(const Problem* table, const Problem* single, int count, int total_tiles,
                          uint64_t* a_maxbits, uint64_t* b_maxbits, const int* max_offset, int* status,
                          cudaStream_t stream) {
   if (total_tiles <= 0) return cudaSuccess;
@@ -286,7 +306,6 @@ cudaError_t split_launch(const Problem* table, const Problem* single, int count,
   args.table = table;
   if (single) args.single = *single;
   args.count = count;
-  args.s = s;
   args.total_tiles = total_tiles;
   args.a_maxbits = a_maxbits;
   args.b_maxbits = b_maxbits;
@@ -295,17 +314,7 @@ cudaError_t split_launch(const Problem* table, const Problem* single, int count,
   absmax_kernel<<<total_tiles, SP_THREADS, 0, stream>>>(args);
   cudaError_t err = cudaGetLastError();
   if (err != cudaSuccess) return err;
-  switch (s) {
-    case 1: split_kernel<1><<<total_tiles, SP_THREADS, 0, stream>>>(args); break;
-    case 2: split_kernel<2><<<total_tiles, SP_THREADS, 0, stream>>>(args); break;
-    case 3: split_kernel<3><<<total_tiles, SP_THREADS, 0, stream>>>(args); break;
-    case 4: split_kernel<4><<<total_tiles, SP_THREADS, 0, stream>>>(args); break;
-    case 5: split_kernel<5><<<total_tiles, SP_THREADS, 0, stream>>>(args); break;
-    case 6: split_kernel<6><<<total_tiles, SP_THREADS, 0, stream>>>(args); break;
-    case 7: split_kernel<7><<<total_tiles, SP_THREADS, 0, stream>>>(args); break;
-    case 8: split_kernel<8><<<total_tiles, SP_THREADS, 0, stream>>>(args); break;
-    default: return cudaErrorInvalidValue;
-  }
+  split_kernel<<<total_tiles, SP_THREADS, 0, stream>>>(args);
   return cudaGetLastError();
 }
 

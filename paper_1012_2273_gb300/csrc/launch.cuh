@@ -79,7 +79,6 @@ struct EmuArgs {
   const int4* units;         // grouped: {problem, tile within problem, group, 0}; nullptr: single, group-major
   int count;
   int total_units;
-  int s;
   int max_pairs;             // longest run of pairs whose products share an int32 sum
   int32_t* scratch;          // per-CTA slots [gridDim.x][scratch_slots][128][BN] (problems with groups == 1)
   int scratch_slots;
@@ -91,13 +90,17 @@ struct EmuArgs {
 };
 
 // native_fp64.cu
+bool native_is_small(int n);
+void native_small_fill_tiles(Problem& p);
+cudaError_t native_small_launch(const Problem* table, const Problem* single, int count, int total_tiles,
+                                cudaStream_t stream);
 void native_fill_tiles(Problem& p);
 cudaError_t native_launch(const Problem* table, const Problem* single, int count, int total_tiles,
                           cudaStream_t stream);
 
 // emu_split.cu
 int split_tiles(const Problem& p);
-cudaError_t split_launch(const Problem* table, const Problem* single, int count, int total_tiles, int s,
+cudaError_t split_launch(const Problem* table, const Problem* single, int count, int total_tiles,
                          uint64_t* a_maxbits, uint64_t* b_maxbits, const int* max_offset, int* status,
                          cudaStream_t stream);
 

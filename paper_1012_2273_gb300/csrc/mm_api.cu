@@ -258,7 +258,7 @@ mm_status ensure_arena(mm_handle h, size_t bytes) {
 struct EmuGroup {
   bool tabled = false;  // launched with a device problem/unit table (grouped calls)
   int groups = 0;       // forced pair groups per tile (0 = automatic)
-  int s = 7, bn = 256, grid = 1, max_pairs = 1;
+  int bn = 256, grid = 1, max_pairs = 1;
   std::vector<Problem> ps;
   std::vector<int> max_off;        // offset of problem p in the maxbits arrays
   std::vector<CUtensorMap> maps;   // 2 per problem
@@ -304,7 +304,6 @@ mm_status layout_group(mm_handle h, EmuGroup& g, char* base) {
   g.max_off.assign(g.ps.size(), 0);
   for (Problem& p : g.ps) maxn = std::max(maxn, p.n);
   g.max_pairs = max_pairs_for(maxn);
-  const int P = mmk::emu_pairs(g.s);
   long long work = 0;
   for (size_t i = 0; i < g.ps.size(); ++i) {
     Problem& p = g.ps[i];
@@ -318,9 +317,9 @@ mm_status layout_group(mm_handle h, EmuGroup& g, char* base) {
     g.total_tiles += p.tiles_m * p.tiles_n;
     p.split_begin = g.total_split;
     g.total_split += mmk::split_tiles(p);
-    work += static_cast<long long>(p.tiles_m) * p.tiles_n * P * (p.k_pad / 64);
-    const size_t a_sl = ar.take(static_cast<size_t>(g.s) * p.m_pad * p.k_pad * 2);
-    const size_t b_sl = ar.take(static_cast<size_t>(g.s) * p.n_pad * p.k_pad * 2);
+    work += static_cast<long long>(p.tiles_m) * p.tiles_n * mmk::emu_pairs(p.s) * (p.k_pad / 64);
+    const size_t a_sl = ar.take(static_cast<size_t>(p.s) * p.m_pad * p.k_pad * 2);
+    const size_t b_sl = ar.take(static_cast<size_t>(p.s) * p.n_pad * p.k_pad * 2);
     const size_t ae = ar.take(sizeof(int) * n);
     const size_t be = ar.take(sizeof(int) * n);
     if (base) {
@@ -342,17 +341,18 @@ mm_status layout_group(mm_handle h, EmuGroup& g, char* base) {
     Problem& p = g.ps[i];
     const int tiles = p.tiles_m * p.tiles_n;
     const int kb = p.k_pad / 64;
+    const int P = mmk::emu_pairs(p.s);
     int G;
     if (g.groups > 0) {
       G = std::min(g.groups, P);
     } else if (g.ps.size() == 1) {
-      G = choose_groups_single(tiles, g.s, kb, h->num_sms, g.max_pairs);
+      G = choose_groups_single(tiles, p.s, kb, h->num_sms, g.max_pairs);
     } else {
       G = static_cast<int>(std::lround(P * kb / std::max(target, 1.0)));
       G = std::max(1, std::min(G, P));
     }
     p.groups = G;
-    p.nslots = mmk::emu_tile_slots(g.s, G, g.max_pairs);
+    p.nslots = mmk::emu_tile_slots(p.s, G, g.max_pairs);
     if (G > 1) {
       p.slot_base = g.tilebuf_elems;
       g.tilebuf_elems += static_cast<long long>(tiles) * p.nslots * slot;
@@ -363,7 +363,7 @@ mm_status layout_group(mm_handle h, EmuGroup& g, char* base) {
     if (g.tabled) {
       for (int gi = 0; gi < G; ++gi) {
         int p0, p1;
-        mmk::emu_group_range(g.s, G, gi, &p0, &p1);
+        mmk::emu_group_range(p.s, G, gi, &p0, &p1);
         const int cost = (p1 - p0) * kb;
         for (int t = 0; t < tiles; ++t) g.units.push_back(make_int4(static_cast<int>(i), t, gi, cost));
       }
@@ -393,8 +393,8 @@ mm_status layout_group(mm_handle h, EmuGroup& g, char* base) {
     g.maps.resize(2 * g.ps.size());
     for (size_t i = 0; i < g.ps.size(); ++i) {
       const Problem& p = g.ps[i];
-      if (!make_plane_map(&g.maps[2 * i], p.a_slices, p.k_pad, static_cast<long>(g.s) * p.m_pad, 128) ||
-          !make_plane_map(&g.maps[2 * i + 1], p.b_slices, p.k_pad, static_cast<long>(g.s) * p.n_pad, g.bn))
+      if (!make_plane_map(&g.maps[2 * i], p.a_slices, p.k_pad, static_cast<long>(p.s) * p.m_pad, 128) ||
+          !make_plane_map(&g.maps[2 * i + 1], p.b_slices, p.k_pad, static_cast<long>(p.s) * p.n_pad, g.bn))
         return fail(h, MM_ERR_CUDA, "cuTensorMapEncodeTiled failed");
     }
   }
@@ -415,7 +415,7 @@ mm_status run_group(mm_handle h, const EmuGroup& g, const Problem* d_table, cons
   MM_CUDA(h, cudaMemsetAsync(amax, 0, sizeof(uint64_t) * g.max_rows, stream));
   MM_CUDA(h, cudaMemsetAsync(bmax, 0, sizeof(uint64_t) * g.max_rows, stream));
   MM_CUDA(h, mmk::split_launch(d_table, single ? &g.ps[0] : nullptr, static_cast<int>(g.ps.size()), g.total_split,
-                               g.s, amax, bmax, single ? nullptr : d_max_off, h->d_status, stream));
+                               amax, bmax, single ? nullptr : d_max_off, h->d_status, stream));
   prof_end(h, stream, m_split);
   bool any_split = false;
   for (const Problem& p : g.ps) any_split |= p.groups > 1;
@@ -428,7 +428,6 @@ mm_status run_group(mm_handle h, const EmuGroup& g, const Problem* d_table, cons
   a.units = single ? nullptr : d_units;
   a.count = static_cast<int>(g.ps.size());
   a.total_units = g.total_units;
-  a.s = g.s;
   a.max_pairs = g.max_pairs;
   a.scratch = reinterpret_cast<int32_t*>(g.base + g.scratch);
   a.scratch_slots = g.scratch_slots;
@@ -459,10 +458,10 @@ mm_status emu_single(mm_handle h, const Problem& p, int s, int bn, int groups, c
   mm_status st = check_emu_size(h, p.n, s);
   if (st != MM_OK) return st;
   EmuGroup g;
-  g.s = s;
   g.bn = bn;
   g.groups = groups;
   g.ps.push_back(p);
+  g.ps[0].s = s;
   st = layout_group(h, g, nullptr);
   if (st != MM_OK) return st;
   st = ensure_arena(h, g.bytes);
@@ -473,10 +472,14 @@ mm_status emu_single(mm_handle h, const Problem& p, int s, int bn, int groups, c
 }
 
 mm_status native_single(mm_handle h, Problem p, cudaStream_t stream) {
-  mmk::native_fill_tiles(p);
+  const bool small = mmk::native_is_small(p.n);
+  if (small) mmk::native_small_fill_tiles(p); else mmk::native_fill_tiles(p);
   p.tile_begin = 0;
   const long m = prof_start(h, stream, KIND_NATIVE);
-  MM_CUDA(h, mmk::native_launch(nullptr, &p, 1, p.tiles_m * p.tiles_n, stream));
+  if (small)
+    MM_CUDA(h, mmk::native_small_launch(nullptr, &p, 1, p.tiles_m * p.tiles_n, stream));
+  else
+    MM_CUDA(h, mmk::native_launch(nullptr, &p, 1, p.tiles_m * p.tiles_n, stream));
   prof_end(h, stream, m);
   return MM_OK;
 }
@@ -707,7 +710,8 @@ mm_status mm_gemm_grouped(mm_handle h, int count, const int* Ns, const double* c
 
   // Partition: native problems, and emulated problems by (slices, bn).
   std::vector<Problem> nat;
-  std::map<std::tuple<int, int, int>, std::vector<Problem>> emu;
+  std::map<std::tuple<int, int>, std::vector<Problem>> emu;
+  std::vector<std::pair<Problem, Plan>> emu_plans;
   for (int i = 0; i < count; ++i) {
     if (Ns[i] == 0) continue;
     Problem p{};
@@ -721,14 +725,37 @@ mm_status mm_gemm_grouped(mm_handle h, int count, const int* Ns, const double* c
     } else {
       mm_status st = check_emu_size(h, p.n, pl.slices);
       if (st != MM_OK) return st;
-      emu[{pl.slices, pl.bn, pl.groups}].push_back(p);
+      p.s = pl.slices;
+      emu_plans.push_back({p, pl});
     }
   }
-  int nat_tiles = 0;
+  // All emulated problems of the call share one slice-product launch: the
+  // tile width is the one planned for the largest problem (digit counts may
+  // differ per problem).
+  if (!emu_plans.empty()) {
+    size_t big = 0;
+    for (size_t i = 1; i < emu_plans.size(); ++i)
+      if (emu_plans[i].first.n > emu_plans[big].first.n) big = i;
+    const int bn = emu_plans[big].second.bn;
+    for (auto& ep : emu_plans) emu[{bn, ep.second.groups}].push_back(ep.first);
+  }
+  // Native problems: 64 x 64 tiles, or 16 x 16 tiles below 512 (two launches).
+  std::vector<Problem> nat_small;
+  {
+    std::vector<Problem> big;
+    for (const Problem& p : nat) (mmk::native_is_small(p.n) ? nat_small : big).push_back(p);
+    nat.swap(big);
+  }
+  int nat_tiles = 0, nat_small_tiles = 0;
   for (Problem& p : nat) {
     mmk::native_fill_tiles(p);
     p.tile_begin = nat_tiles;
     nat_tiles += p.tiles_m * p.tiles_n;
+  }
+  for (Problem& p : nat_small) {
+    mmk::native_small_fill_tiles(p);
+    p.tile_begin = nat_small_tiles;
+    nat_small_tiles += p.tiles_m * p.tiles_n;
   }
 
   // Workspace.  Emulation groups run one after another on the same stream, so
@@ -757,9 +784,8 @@ mm_status mm_gemm_grouped(mm_handle h, int count, const int* Ns, const double* c
       auto make = [&](size_t end) {
         EmuGroup t;
         t.tabled = true;
-        t.s = std::get<0>(kv.first);
-        t.bn = std::get<1>(kv.first);
-        t.groups = std::get<2>(kv.first);
+        t.bn = std::get<0>(kv.first);
+        t.groups = std::get<1>(kv.first);
         t.ps.assign(rest.begin() + at, rest.begin() + end);
         return t;
       };
@@ -798,6 +824,7 @@ mm_status mm_gemm_grouped(mm_handle h, int count, const int* Ns, const double* c
   // Device-side tables: [native problems][per group: problems, maps, max offsets].
   Arena tab;
   const size_t off_nat = tab.take(sizeof(Problem) * std::max<size_t>(nat.size(), 1));
+  const size_t off_nat_small = tab.take(sizeof(Problem) * std::max<size_t>(nat_small.size(), 1));
   std::vector<size_t> off_tab, off_maps, off_mo, off_units;
   for (const EmuGroup& g : groups) {
     off_tab.push_back(tab.take(sizeof(Problem) * g.ps.size()));
@@ -808,6 +835,8 @@ mm_status mm_gemm_grouped(mm_handle h, int count, const int* Ns, const double* c
   const size_t tab_bytes = tab.off;
   std::vector<char> host_tab(tab_bytes, 0);
   if (!nat.empty()) std::memcpy(host_tab.data() + off_nat, nat.data(), sizeof(Problem) * nat.size());
+  if (!nat_small.empty())
+    std::memcpy(host_tab.data() + off_nat_small, nat_small.data(), sizeof(Problem) * nat_small.size());
   for (size_t gi = 0; gi < groups.size(); ++gi) {
     const EmuGroup& g = groups[gi];
     std::memcpy(host_tab.data() + off_tab[gi], g.ps.data(), sizeof(Problem) * g.ps.size());
@@ -817,10 +846,14 @@ mm_status mm_gemm_grouped(mm_handle h, int count, const int* Ns, const double* c
   }
 
   auto launch_all = [&](char* dtab, cudaStream_t s) -> mm_status {
-    if (!nat.empty()) {
+    if (!nat.empty() || !nat_small.empty()) {
       const long m = prof_start(h, s, KIND_NATIVE);
-      MM_CUDA(h, mmk::native_launch(reinterpret_cast<Problem*>(dtab + off_nat), nullptr,
-                                    static_cast<int>(nat.size()), nat_tiles, s));
+      if (!nat_small.empty())
+        MM_CUDA(h, mmk::native_small_launch(reinterpret_cast<Problem*>(dtab + off_nat_small), nullptr,
+                                            static_cast<int>(nat_small.size()), nat_small_tiles, s));
+      if (!nat.empty())
+        MM_CUDA(h, mmk::native_launch(reinterpret_cast<Problem*>(dtab + off_nat), nullptr,
+                                      static_cast<int>(nat.size()), nat_tiles, s));
       prof_end(h, s, m);
     }
     for (size_t gi = 0; gi < groups.size(); ++gi) {
@@ -902,6 +935,7 @@ mm_status mm_split(mm_handle h, int N, const double* M, int by_columns, int slic
   if (slices < 1 || slices > 8) return fail(h, MM_ERR_UNSUPPORTED, "slices must be in 1..8");
   Problem p{};
   p.n = N;
+  p.s = slices;
   p.k_pad = ld;
   if (by_columns) {
     p.B = M;
@@ -922,7 +956,7 @@ mm_status mm_split(mm_handle h, int N, const double* M, int by_columns, int slic
   uint64_t* mx = static_cast<uint64_t*>(h->arena);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   MM_CUDA(h, cudaMemsetAsync(mx, 0, sizeof(uint64_t) * N, s));
-  MM_CUDA(h, mmk::split_launch(nullptr, &p, 1, mmk::split_tiles(p), slices, mx, mx, nullptr, h->d_status, s));
+  MM_CUDA(h, mmk::split_launch(nullptr, &p, 1, mmk::split_tiles(p), mx, mx, nullptr, h->d_status, s));
   return MM_OK;
 }
 
@@ -938,6 +972,7 @@ mm_status mm_level_sums(mm_handle h, int N, int slices, const uint16_t* a_digits
   const int bn = (b_rows % 256 == 0 && N > 128) ? 256 : 128;
   Problem p{};
   p.n = N;
+  p.s = slices;
   p.a_slices = const_cast<uint16_t*>(a_digits);
   p.b_slices = const_cast<uint16_t*>(b_digits);
   p.m_pad = a_rows;
@@ -956,7 +991,6 @@ mm_status mm_level_sums(mm_handle h, int N, int slices, const uint16_t* a_digits
   a.single = p;
   a.count = 1;
   a.total_units = p.tiles_m * p.tiles_n;
-  a.s = slices;
   a.max_pairs = slices;  // every level in one segment: level sums fit int32 (checked above)
   a.scratch = nullptr;
   a.scratch_slots = 0;

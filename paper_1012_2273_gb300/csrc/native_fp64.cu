@@ -144,7 +144,82 @@ __global__ void __launch_bounds__(NT_THREADS) native_fp64_kernel(const __grid_co
     }
 }
 
+// Small problems: one warp per 16 x 16 tile of C, so that N ~ 100 still spreads
+// over many SMs (a 64 x 64 tile would leave all but a few idle, and the FP64
+// MMA rate of one SM is small).  Fragments are loaded straight from global
+// memory (L1/L2), 16 k at a time: two m16n8k4 per k step.
+constexpr int NS_TILE = 16;
+
+__global__ void __launch_bounds__(32) native_fp64_small_kernel(const __grid_constant__ NativeArgs args) {
+  const int tile = blockIdx.x;
+  const Problem* P = args.table ? &args.table[find_problem(args.table, args.count, tile)] : &args.single;
+  const int n = P->n;
+  const int local = tile - P->tile_begin;
+  if (n <= 0 || local < 0 || local >= P->tiles_m * P->tiles_n) return;
+  const int m0 = (local / P->tiles_n) * NS_TILE;
+  const int n0 = (local % P->tiles_n) * NS_TILE;
+  const double* __restrict__ A = P->A;
+  const double* __restrict__ B = P->B;
+  const int lane = threadIdx.x, g = lane >> 2, t = lane & 3;
+  const int ra = m0 + g, rb = m0 + g + 8;  // rows of the A fragment
+  double acc[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}};
+  for (int k0 = 0; k0 < n; k0 += 16) {
+    double a[4][2], b[4][2];
+#pragma unroll
+    for (int kk = 0; kk < 4; ++kk) {
+      const int k = k0 + 4 * kk + t;
+      const bool kin = k < n;
+      a[kk][0] = (kin && ra < n) ? A[static_cast<size_t>(ra) * n + k] : 0.0;
+      a[kk][1] = (kin && rb < n) ? A[static_cast<size_t>(rb) * n + k] : 0.0;
+#pragma unroll
+      for (int ni = 0; ni < 2; ++ni) {
+        const int col = n0 + ni * 8 + g;
+        b[kk][ni] = (kin && col < n) ? B[static_cast<size_t>(k) * n + col] : 0.0;
+      }
+    }
+#pragma unroll
+    for (int kk = 0; kk < 4; ++kk)
+#pragma unroll
+      for (int ni = 0; ni < 2; ++ni) dmma_16x8x4(acc[ni], a[kk][0], a[kk][1], b[kk][ni]);
+  }
+  double* __restrict__ C = P->C;
+#pragma unroll
+  for (int ni = 0; ni < 2; ++ni) {
+    const int c0 = n0 + ni * 8 + 2 * t;
+#pragma unroll
+    for (int hh = 0; hh < 2; ++hh) {
+      const int r = m0 + g + 8 * hh;
+      if (r < n) {
+        if (c0 < n) C[static_cast<size_t>(r) * n + c0] = acc[ni][2 * hh];
+        if (c0 + 1 < n) C[static_cast<size_t>(r) * n + c0 + 1] = acc[ni][2 * hh + 1];
+      }
+    }
+  }
+}
+
 // Host-side helpers --------------------------------------------------------
+
+// Problems below this size use the 16 x 16 kernel.
+constexpr int NATIVE_SMALL_MAX_N = 511;
+
+bool native_is_small(int n) { return n <= NATIVE_SMALL_MAX_N; }
+
+void native_small_fill_tiles(Problem& p) {
+  const int tm = p.n > 0 ? (p.n + NS_TILE - 1) / NS_TILE : 0;
+  p.tiles_m = tm;
+  p.tiles_n = tm;
+}
+
+cudaError_t native_small_launch(const Problem* table, const Problem* single, int count, int total_tiles,
+                                cudaStream_t stream) {
+  if (total_tiles <= 0) return cudaSuccess;
+  NativeArgs args{};
+  args.table = table;
+  if (single) args.single = *single;
+  args.count = count;
+  native_fp64_small_kernel<<<total_tiles, 32, 0, stream>>>(args);
+  return cudaGetLastError();
+}
 
 int native_tiles(int n) {
   if (n <= 0) return 0;
