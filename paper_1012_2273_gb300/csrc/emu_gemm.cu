@@ -30,7 +30,8 @@
 // region, the epilogue warp that completes the region last (an atomic count,
 // no waiting) recombines it.
 //
-// Pipeline (one persistent CTA per SM, units strided by gridDim.x):
+// Pipeline (one persistent CTA per SM; the producer claims units from a global
+// counter and passes their indices to the other warps through a small ring):
 //   warp 0      TMA producer: A and B^T k-blocks (64 deep, 128-byte swizzle)
 //               into a STAGES-deep shared-memory ring (mbarrier full/empty)
 //   warp 1      allocates TMEM; one lane issues tcgen05.mma (M=128, N=BN,
@@ -51,6 +52,7 @@ namespace mmk {
 constexpr int EM_BM = 128;
 constexpr int EM_BK = 64;          // elements per k-block: one 128-byte swizzle row
 constexpr int EM_CHUNK_KB = 4;     // k-blocks per exact chunk: 256 digit products
+constexpr int EM_UNIT_RING = 4;    // work units the producer may claim ahead of the consumers
 constexpr int EM_THREADS = 384;    // 12 warps: registers are budgeted per 4-warp group
 constexpr int EM_REGS_LAUNCH = 168;  // 65536 / 384, rounded down to a multiple of 8
 constexpr int EM_REGS_CTRL = 56;     // warpgroup 0 after setmaxnreg.dec
@@ -66,7 +68,7 @@ struct EmuCfg {
   static constexpr int B_BYTES = BN * EM_BK * 2;
   static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
   static constexpr int TMEM_COLS = 2 * BN;
-  static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers, flags*/;
+  static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*align*/ + 512 /*barriers, unit ring*/;
 };
 
 // ---------------------------------------------------------------------------
@@ -244,7 +246,10 @@ __global__ void __launch_bounds__(EM_THREADS, 1)
   uint64_t* acc_full = bars + 2 * Cfg::STAGES;
   uint64_t* acc_empty = acc_full + 2;
   uint64_t* mma_done = acc_empty + 2;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mma_done + 1);
+  uint64_t* ufull = mma_done + 1;             // unit ring: index published
+  uint64_t* uempty = ufull + EM_UNIT_RING;     // unit ring: slot read by all consumers
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(uempty + EM_UNIT_RING);
+  volatile int* ring = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
@@ -259,6 +264,10 @@ __global__ void __launch_bounds__(EM_THREADS, 1)
       mbar_init(&acc_empty[i], 8);
     }
     mbar_init(mma_done, 1);
+    for (int i = 0; i < EM_UNIT_RING; ++i) {
+      mbar_init(&ufull[i], 1);
+      mbar_init(&uempty[i], 9);  // the MMA thread and the 8 epilogue warps
+    }
     fence_mbar_init();
   }
   if (warp == 1) {
@@ -292,7 +301,24 @@ __global__ void __launch_bounds__(EM_THREADS, 1)
       // Digit planes are re-read by the other tiles of the band and by later
       // digit pairs: keep them in L2 ahead of streaming data.
       const uint64_t keep = l2_policy_evict_last();
-      for (int u = blockIdx.x; u < args.total_units && ok; u += gridDim.x) {
+      int uslot = 0;
+      uint32_t uphase = 0;
+      while (ok) {
+        // Claim the next unit (units are sorted longest first: greedy LPT) and
+        // publish it to the MMA and epilogue warps; -1 ends the loop.
+        int u = atomicAdd(args.unit_counter, 1);
+        if (u >= args.total_units) u = -1;
+        if (!mbar_wait(&uempty[uslot], uphase ^ 1, tmo, args.status)) {
+          ok = false;
+          break;
+        }
+        ring[uslot] = u;
+        mbar_arrive(&ufull[uslot]);
+        if (++uslot == EM_UNIT_RING) {
+          uslot = 0;
+          uphase ^= 1;
+        }
+        if (u < 0) break;
         const UnitRef U = emu_unit(args, u);
         const Problem* P = U.P;
         int tm, tn;
@@ -347,7 +373,20 @@ __global__ void __launch_bounds__(EM_THREADS, 1)
       int abuf = 0;
       uint32_t aphase = 0;
       bool ok = true;
-      for (int u = blockIdx.x; u < args.total_units && ok; u += gridDim.x) {
+      int uslot = 0;
+      uint32_t uphase = 0;
+      while (ok) {
+        if (!mbar_wait(&ufull[uslot], uphase, tmo, args.status)) {
+          ok = false;
+          break;
+        }
+        const int u = ring[uslot];
+        mbar_arrive(&uempty[uslot]);
+        if (++uslot == EM_UNIT_RING) {
+          uslot = 0;
+          uphase ^= 1;
+        }
+        if (u < 0) break;
         const UnitRef U = emu_unit(args, u);
         const int KB = U.P->k_pad / EM_BK;
         int p0, p1;
@@ -409,7 +448,21 @@ __global__ void __launch_bounds__(EM_THREADS, 1)
     int abuf = 0;
     uint32_t aphase = 0;
     bool ok = true;
-    for (int u = blockIdx.x; u < args.total_units && ok; u += gridDim.x) {
+    int uslot = 0;
+    uint32_t uphase = 0;
+    while (ok) {
+      if (!mbar_wait(&ufull[uslot], uphase, tmo, args.status)) {
+        ok = false;
+        break;
+      }
+      const int u = ring[uslot];
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&uempty[uslot]);
+      if (++uslot == EM_UNIT_RING) {
+        uslot = 0;
+        uphase ^= 1;
+      }
+      if (u < 0) break;
       const UnitRef U = emu_unit(args, u);
       const Problem* P = U.P;
       const int n = P->n;

@@ -84,6 +84,7 @@ struct EmuArgs {
   int scratch_slots;
   int32_t* tilebuf;          // per-tile slots (problems with groups > 1), see Problem::slot_base
   int* tile_counters;        // [global tile][8 epilogue regions]: units finished, zero at launch
+  int* unit_counter;         // next unit to claim, zero at launch
   int32_t* levels_out;       // step API: level sums [s][n][n] instead of C (else nullptr)
   int* status;
   uint64_t timeout_ns;

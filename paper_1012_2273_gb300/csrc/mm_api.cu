@@ -386,7 +386,7 @@ mm_status layout_group(mm_handle h, EmuGroup& g, char* base) {
   g.bmax = ar.take(sizeof(uint64_t) * g.max_rows);
   g.scratch = ar.take(static_cast<size_t>(g.grid) * g.scratch_slots * slot * sizeof(int32_t));
   g.tilebuf = ar.take(static_cast<size_t>(std::max<long long>(g.tilebuf_elems, 4)) * sizeof(int32_t));
-  g.counters = ar.take(sizeof(int) * 8 * std::max(g.total_tiles, 1));
+  g.counters = ar.take(sizeof(int) * (8 * static_cast<size_t>(g.total_tiles) + 1));  // + unit counter
   g.bytes = ar.off;
   g.base = base;
   if (base) {
@@ -417,10 +417,9 @@ mm_status run_group(mm_handle h, const EmuGroup& g, const Problem* d_table, cons
   MM_CUDA(h, mmk::split_launch(d_table, single ? &g.ps[0] : nullptr, static_cast<int>(g.ps.size()), g.total_split,
                                amax, bmax, single ? nullptr : d_max_off, h->d_status, stream));
   prof_end(h, stream, m_split);
-  bool any_split = false;
-  for (const Problem& p : g.ps) any_split |= p.groups > 1;
+  // Per-region completion counters (pair groups > 1) and the unit counter.
   int* counters = reinterpret_cast<int*>(g.base + g.counters);
-  if (any_split) MM_CUDA(h, cudaMemsetAsync(counters, 0, sizeof(int) * 8 * g.total_tiles, stream));
+  MM_CUDA(h, cudaMemsetAsync(counters, 0, sizeof(int) * (8 * static_cast<size_t>(g.total_tiles) + 1), stream));
   mmk::EmuArgs a{};
   a.table = d_table;
   if (single) a.single = g.ps[0];
@@ -433,6 +432,7 @@ mm_status run_group(mm_handle h, const EmuGroup& g, const Problem* d_table, cons
   a.scratch_slots = g.scratch_slots;
   a.tilebuf = reinterpret_cast<int32_t*>(g.base + g.tilebuf);
   a.tile_counters = counters;
+  a.unit_counter = counters + 8 * static_cast<size_t>(g.total_tiles);
   a.levels_out = nullptr;
   a.status = h->d_status;
   a.timeout_ns = h->timeout_ns;
@@ -525,7 +525,7 @@ mm_status mm_create(mm_handle* out, const mm_config* cfg) {
   }
   if (cudaGetDevice(&h->device) != cudaSuccess ||
       cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess ||
-      cudaMalloc(&h->d_status, sizeof(int)) != cudaSuccess || cudaMemset(h->d_status, 0, sizeof(int)) != cudaSuccess ||
+      cudaMalloc(&h->d_status, 128) != cudaSuccess || cudaMemset(h->d_status, 0, 128) != cudaSuccess ||
       cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&h->grp_event, cudaEventDisableTiming) != cudaSuccess) {
     cudaGetLastError();
@@ -994,6 +994,8 @@ mm_status mm_level_sums(mm_handle h, int N, int slices, const uint16_t* a_digits
   a.max_pairs = slices;  // every level in one segment: level sums fit int32 (checked above)
   a.scratch = nullptr;
   a.scratch_slots = 0;
+  a.unit_counter = h->d_status + 16;  // spare word of the status block
+  MM_CUDA(h, cudaMemsetAsync(a.unit_counter, 0, sizeof(int), static_cast<cudaStream_t>(stream)));
   a.levels_out = levels;
   a.status = h->d_status;
   a.timeout_ns = h->timeout_ns;
