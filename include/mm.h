@@ -113,7 +113,7 @@ mm_status mm_plan(mm_handle h, int N, int* form, int* slices);
  *   out_ms[0] scale and split (including zeroing of the row/column maxima)
  *   out_ms[1] slice products with fused recombination
  *   out_ms[2] native FP64 kernel
- *   out_ms[3] standalone recombination (mm_recombine)
+ *   out_ms[3] recombination run as its own pass (small problems, mm_recombine)
  * and launches[0..3] the number of kernel launches of each kind (may be
  * NULL).  Synchronises on the recorded events.  MM_ERR_INVALID without the flag. */
 mm_status mm_profile_read(mm_handle h, double out_ms[4], int launches[4]);

@@ -11,7 +11,7 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 
-#include "../../include/mm.h"
+#include "mm.h"
 
 namespace mmk {
 
@@ -38,6 +38,7 @@ struct Problem {
   int s;               // digits per value (emulation), 1..8
   int groups;          // digit-pair groups per tile: work units per tile of the slice-product kernel
   int nslots;          // segment sums per tile (all groups together)
+  int defer;           // 1: slots go to the per-tile buffer and a separate pass recombines them
   long long slot_base; // int32 offset of this problem's tile 0 in the per-tile slot buffer (groups > 1)
 };
 

@@ -482,8 +482,9 @@ __global__ void __launch_bounds__(EM_THREADS, 1)
         emu_group_range(s, U.G, g, &q0, &q1);
         slot += emu_count_segments(q0, q1, maxp);
       }
-      int32_t* tile_slots = U.G > 1 ? args.tilebuf + P->slot_base + static_cast<long long>(U.tile_local) * P->nslots * SLOT
-                                    : my_scratch;
+      int32_t* tile_slots = (U.G > 1 || P->defer)
+                                ? args.tilebuf + P->slot_base + static_cast<long long>(U.tile_local) * P->nslots * SLOT
+                                : my_scratch;
       int L, t0;
       for (int p = p0; p < p1 && ok; ++slot) {
         const int np = emu_segment(p, p1, maxp, &L, &t0);
@@ -545,7 +546,7 @@ __global__ void __launch_bounds__(EM_THREADS, 1)
           }
         }
       }
-      if (!ok || args.levels_out) continue;
+      if (!ok || args.levels_out || P->defer) continue;  // deferred: recombined by slots_recombine_kernel
       bool mine = true;
       if (U.G > 1) {
         // Each epilogue warp owns the same 32 x BN/2 region in every unit of
@@ -575,6 +576,58 @@ __global__ void __launch_bounds__(EM_THREADS, 1)
   if (warp == 1) {
     tc_fence_after();
     tmem_dealloc(tmem_base, Cfg::TMEM_COLS);
+  }
+}
+
+// Deferred recombination of whole tiles, after the slice-product kernel: one
+// thread per 4 consecutive outputs of a tile row.  Consecutive threads take
+// consecutive rows, so every slot read of a warp is 512 contiguous bytes; many
+// resident warps hide the latency that the in-kernel epilogue cannot.
+template <int BN>
+__global__ void __launch_bounds__(256) slots_recombine_kernel(const __grid_constant__ EmuArgs args) {
+  constexpr int PER_TILE = EM_BM * BN / 4;  // threads per tile
+  constexpr size_t SLOT = static_cast<size_t>(EM_BM) * BN;
+  const long long item = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+  const int tile = static_cast<int>(item / PER_TILE);
+  const int in_tile = static_cast<int>(item - static_cast<long long>(tile) * PER_TILE);
+  const Problem* P = args.table ? &args.table[find_problem(args.table, args.count, tile)] : &args.single;
+  const int tile_local = tile - P->tile_begin;
+  if (!P->defer || tile_local < 0 || tile_local >= P->tiles_m * P->tiles_n) return;
+  const int r = in_tile % EM_BM, c4 = in_tile / EM_BM;
+  int tm, tn;
+  emu_tile_coords(tile_local, P->tiles_m, P->tiles_n, &tm, &tn);
+  const int n = P->n, row = tm * EM_BM + r, col = tn * BN + 4 * c4;
+  if (row >= n || col >= n) return;
+  const int s = P->s, G = P->groups, maxp = args.max_pairs;
+  const int32_t* at = args.tilebuf + P->slot_base + static_cast<long long>(tile_local) * P->nslots * SLOT +
+                      slot_index(r, 4 * c4);
+  int64_t th[4] = {0, 0, 0, 0};
+  uint64_t tl[4] = {0, 0, 0, 0};
+  int curL = 2, slot = 0;
+  for (int g = 0; g < G; ++g) {
+    int p0, p1;
+    emu_group_range(s, G, g, &p0, &p1);
+    int L, t0;
+    for (int p = p0; p < p1; ++slot) {
+      p += emu_segment(p, p1, maxp, &L, &t0);
+      const int4 v = __ldcs(reinterpret_cast<const int4*>(at + static_cast<size_t>(slot) * SLOT));
+      const int sh = 8 * (L - curL);
+      curL = L;
+      i128_shift_add(th[0], tl[0], sh, v.x);
+      i128_shift_add(th[1], tl[1], sh, v.y);
+      i128_shift_add(th[2], tl[2], sh, v.z);
+      i128_shift_add(th[3], tl[3], sh, v.w);
+    }
+  }
+  const int tail = 8 * (s + 1 - curL);
+  const int base_scale = P->a_exp[row] - 8 * s - 6;
+  double* crow = P->C + static_cast<size_t>(row) * n;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    if (col + j < n) {
+      i128_shift_add(th[j], tl[j], tail, 0);
+      __stcs(crow + col + j, round_i128_scaled(th[j], tl[j], base_scale + P->b_exp[col + j]));
+    }
   }
 }
 
@@ -611,6 +664,18 @@ cudaError_t emu_gemm_launch(int bn, const CUtensorMap* mapA, const CUtensorMap* 
                             cudaStream_t stream) {
   if (args.total_units <= 0) return cudaSuccess;
   return bn == 256 ? launch_bn<256>(mapA, mapB, args, grid, stream) : launch_bn<128>(mapA, mapB, args, grid, stream);
+}
+
+cudaError_t slots_recombine_launch(int bn, const EmuArgs& args, int total_tiles, cudaStream_t stream) {
+  if (total_tiles <= 0) return cudaSuccess;
+  const int per_tile = EM_BM * bn / 4;
+  const long long threads = static_cast<long long>(total_tiles) * per_tile;
+  const unsigned blocks = static_cast<unsigned>((threads + 255) / 256);
+  if (bn == 256)
+    slots_recombine_kernel<256><<<blocks, 256, 0, stream>>>(args);
+  else
+    slots_recombine_kernel<128><<<blocks, 256, 0, stream>>>(args);
+  return cudaGetLastError();
 }
 
 // Registers, threads and shared memory of the slice-product kernel, for error messages.

@@ -110,6 +110,7 @@ int emu_smem_bytes(int bn);
 cudaError_t emu_gemm_launch(int bn, const CUtensorMap* mapA, const CUtensorMap* mapB, const EmuArgs& args, int grid,
                             cudaStream_t stream);
 void emu_kernel_info(int bn, char* buf, size_t len);
+cudaError_t slots_recombine_launch(int bn, const EmuArgs& args, int total_tiles, cudaStream_t stream);
 cudaError_t recombine_launch(int n, int s, const int32_t* levels, const int* e, const int* f, double* C,
                              cudaStream_t stream);
 

@@ -254,6 +254,10 @@ mm_status ensure_arena(mm_handle h, size_t bytes) {
   return MM_OK;
 }
 
+// Problems smaller than this recombine in a separate pass after the slice
+// products (see layout_group); larger ones in the slice-product epilogue.
+constexpr int kDeferBelowN = 3072;
+
 // One launch group of the emulation: problems sharing (s, bn).
 struct EmuGroup {
   bool tabled = false;  // launched with a device problem/unit table (grouped calls)
@@ -331,8 +335,12 @@ mm_status layout_group(mm_handle h, EmuGroup& g, char* base) {
     g.max_off[i] = g.max_rows;
     g.max_rows += n;
   }
-  // Work units: pair groups per tile, then slot storage.
-  const double target = static_cast<double>(work) / (4.0 * h->num_sms);
+  // Work units: pair groups per tile, then slot storage.  Grouped calls aim at
+  // about MM_UNITS_PER_SM units per SM (default 4) so the dynamic scheduler
+  // can balance uneven problems with a short tail.
+  double units_per_sm = 4.0;
+  if (const char* e = std::getenv("MM_UNITS_PER_SM")) units_per_sm = std::max(1.0, std::atof(e));
+  const double target = static_cast<double>(work) / (units_per_sm * h->num_sms);
   g.units.clear();
   g.tilebuf_elems = 0;
   g.scratch_slots = 1;
@@ -353,7 +361,10 @@ mm_status layout_group(mm_handle h, EmuGroup& g, char* base) {
     }
     p.groups = G;
     p.nslots = mmk::emu_tile_slots(p.s, G, g.max_pairs);
-    if (G > 1) {
+    // Short tiles (small N) leave the recombination to a separate pass: done
+    // in the epilogue it stalls the tensor pipe for a large share of the tile.
+    p.defer = p.n < kDeferBelowN ? 1 : 0;
+    if (G > 1 || p.defer) {
       p.slot_base = g.tilebuf_elems;
       g.tilebuf_elems += static_cast<long long>(tiles) * p.nslots * slot;
     } else {
@@ -443,6 +454,13 @@ mm_status run_group(mm_handle h, const EmuGroup& g, const Problem* d_table, cons
     char info[512];
     mmk::emu_kernel_info(g.bn, info, sizeof(info));
     return fail(h, MM_ERR_CUDA, std::string("slice-product launch: ") + cudaGetErrorString(le) + " " + info);
+  }
+  bool any_deferred = false;
+  for (const Problem& p : g.ps) any_deferred |= p.defer != 0;
+  if (any_deferred) {
+    const long m_rec = prof_start(h, stream, KIND_RECOMBINE);
+    MM_CUDA(h, mmk::slots_recombine_launch(g.bn, a, g.total_tiles, stream));
+    prof_end(h, stream, m_rec);
   }
   return MM_OK;
 }
