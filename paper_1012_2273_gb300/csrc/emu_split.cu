@@ -150,24 +150,28 @@ __global__ void __launch_bounds__(SP_THREADS) absmax_kernel(const __grid_constan
   const uint64_t* src = reinterpret_cast<const uint64_t*>(is_a ? P->A : P->B);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (is_a) {
-    // warp w: rows r0 + w, r0 + w + 8, ...; lanes cover the 64 columns twice
-    for (int r = warp; r < SP_TILE; r += SP_THREADS / 32) {
-      const int i = r0 + r;
-      unsigned long long m = 0;
-      if (i < n) {
-        const int j0 = c0 + lane, j1 = c0 + lane + 32;
-        if (j0 < n) m = src[static_cast<size_t>(i) * n + j0] & 0x7FFFFFFFFFFFFFFFull;
-        if (j1 < n) {
-          const unsigned long long v = src[static_cast<size_t>(i) * n + j1] & 0x7FFFFFFFFFFFFFFFull;
-          m = v > m ? v : m;
-        }
-      }
+    // warp w: rows r0 + w + 8q (q = 0..7); lanes cover the 64 columns twice.
+    // All 16 loads of a lane are issued before any reduction.
+    constexpr int RW = SP_TILE / (SP_THREADS / 32);  // rows per warp
+    unsigned long long m[RW];
+#pragma unroll
+    for (int q = 0; q < RW; ++q) {
+      const int i = r0 + warp + 8 * q;
+      const int j0 = c0 + lane, j1 = c0 + lane + 32;
+      unsigned long long a = 0, b = 0;
+      if (i < n && j0 < n) a = src[static_cast<size_t>(i) * n + j0] & 0x7FFFFFFFFFFFFFFFull;
+      if (i < n && j1 < n) b = src[static_cast<size_t>(i) * n + j1] & 0x7FFFFFFFFFFFFFFFull;
+      m[q] = a > b ? a : b;
+    }
+#pragma unroll
+    for (int q = 0; q < RW; ++q) {
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
-        const unsigned long long v = __shfl_xor_sync(0xffffffffu, m, o);
-        m = v > m ? v : m;
+        const unsigned long long v = __shfl_xor_sync(0xffffffffu, m[q], o);
+        m[q] = v > m[q] ? v : m[q];
       }
-      if (lane == 0 && i < n && m) atomicMax(reinterpret_cast<unsigned long long*>(&args.a_maxbits[off + i]), m);
+      const int i = r0 + warp + 8 * q;
+      if (lane == 0 && i < n && m[q]) atomicMax(reinterpret_cast<unsigned long long*>(&args.a_maxbits[off + i]), m[q]);
     }
   } else {
     // thread: column k = r0 + (tid % 64) of B over rows j = c0 + tid / 64 + 4q
@@ -175,12 +179,11 @@ __global__ void __launch_bounds__(SP_THREADS) absmax_kernel(const __grid_constan
     const int k = r0 + c;
     unsigned long long m = 0;
     if (k < n) {
+#pragma unroll
       for (int q = q0; q < SP_TILE; q += SP_THREADS / SP_TILE) {
         const int j = c0 + q;
-        if (j < n) {
-          const unsigned long long v = src[static_cast<size_t>(j) * n + k] & 0x7FFFFFFFFFFFFFFFull;
-          m = v > m ? v : m;
-        }
+        const unsigned long long v = j < n ? src[static_cast<size_t>(j) * n + k] & 0x7FFFFFFFFFFFFFFFull : 0ull;
+        m = v > m ? v : m;
       }
     }
     part[q0][c] = m;
@@ -254,25 +257,34 @@ __global__ void __launch_bounds__(SP_THREADS) split_kernel(const __grid_constant
   // Phase 1: source element (x, y) of the tile, x fastest (coalesced).
   //   A:   source row i = r0 + y, column j = c0 + x -> Ds[y][x]  (output row y)
   //   B^T: source row j = c0 + y, column k = r0 + x -> Ds[x][y]  (output row x)
-  for (int idx = threadIdx.x; idx < SP_TILE * SP_TILE; idx += SP_THREADS) {
-    const int x = idx % SP_TILE, y = idx / SP_TILE;
-    long long D = 0;
-    if (is_a) {
-      const int i = r0 + y, j = c0 + x;
+  // Each thread's 16 elements, 4 loads in flight at a time.
+  constexpr int PER = SP_TILE * SP_TILE / SP_THREADS;
+  constexpr int BATCH = 4;
+  const int x = threadIdx.x % SP_TILE;
+#pragma unroll
+  for (int q0 = 0; q0 < PER; q0 += BATCH) {
+    uint64_t bits[BATCH];
+    int ex[BATCH];
+#pragma unroll
+    for (int b = 0; b < BATCH; ++b) {
+      const int y = threadIdx.x / SP_TILE + (q0 + b) * (SP_THREADS / SP_TILE);
+      const int i = is_a ? r0 + y : c0 + y;  // source row
+      const int j = is_a ? c0 + x : r0 + x;  // source column
+      const int er = is_a ? i : j;           // row (A) or column (B) of the exponent
+      bits[b] = (i < n && j < n) ? src[static_cast<size_t>(i) * n + j] : 0ull;
+      ex[b] = er < n ? exponent_from_maxbits(maxbits[er]) : 0;
+    }
+#pragma unroll
+    for (int b = 0; b < BATCH; ++b) {
+      const int y = threadIdx.x / SP_TILE + (q0 + b) * (SP_THREADS / SP_TILE);
+      const int i = is_a ? r0 + y : c0 + y;
+      const int j = is_a ? c0 + x : r0 + x;
+      long long D = 0;
       if (i < n && j < n) {
-        const int e = exponent_from_maxbits(maxbits[i]);
-        if (j == 0 && exps) exps[i] = e;
-        D = fixed_point(src[static_cast<size_t>(i) * n + j], e, S, &nonfinite);
+        D = fixed_point(bits[b], ex[b], S, &nonfinite);
+        if (exps && (is_a ? j : i) == 0) exps[is_a ? i : j] = ex[b];
       }
-      Ds[y][x] = D;
-    } else {
-      const int j = c0 + y, k = r0 + x;
-      if (j < n && k < n) {
-        const int f = exponent_from_maxbits(maxbits[k]);
-        if (j == 0 && exps) exps[k] = f;
-        D = fixed_point(src[static_cast<size_t>(j) * n + k], f, S, &nonfinite);
-      }
-      Ds[x][y] = D;
+      if (is_a) Ds[y][x] = D; else Ds[x][y] = D;
     }
   }
   if (nonfinite) any_nonfinite = 1;
