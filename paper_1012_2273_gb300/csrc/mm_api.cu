@@ -99,6 +99,10 @@ struct mm_handle_s {
   void* grp_pinned = nullptr;
   size_t grp_pinned_cap = 0;
   cudaEvent_t grp_event = nullptr;
+  // grouped calls: the native problems run on a side stream, forked from and
+  // joined back into the call's stream (inside the captured graph)
+  cudaStream_t side_stream = nullptr;
+  cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
   // autotune table: N upper bound -> plan
   std::vector<std::pair<int, Plan>> tune;
   // MM_FLAG_PROFILE: events around every kernel of the last call
@@ -545,6 +549,9 @@ mm_status mm_create(mm_handle* out, const mm_config* cfg) {
       cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess ||
       cudaMalloc(&h->d_status, 128) != cudaSuccess || cudaMemset(h->d_status, 0, 128) != cudaSuccess ||
       cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&h->side_stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->fork_ev, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->join_ev, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&h->grp_event, cudaEventDisableTiming) != cudaSuccess) {
     cudaGetLastError();
     if (h->d_status) cudaFree(h->d_status);
@@ -569,6 +576,9 @@ mm_status mm_destroy(mm_handle h) {
   if (h->grp_pinned) cudaFreeHost(h->grp_pinned);
   if (h->grp_event) cudaEventDestroy(h->grp_event);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  if (h->side_stream) cudaStreamDestroy(h->side_stream);
+  if (h->fork_ev) cudaEventDestroy(h->fork_ev);
+  if (h->join_ev) cudaEventDestroy(h->join_ev);
   if (h->d_status) cudaFree(h->d_status);
   for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
   if (h->probe_sink) cudaFree(h->probe_sink);
@@ -864,7 +874,20 @@ mm_status mm_gemm_grouped(mm_handle h, int count, const int* Ns, const double* c
   }
 
   auto launch_all = [&](char* dtab, cudaStream_t s) -> mm_status {
-    if (!nat.empty() || !nat_small.empty()) {
+    // Native problems do not depend on the emulation's kernels: unless
+    // profiling (which wants one kernel at a time), they run on a side stream.
+    const bool fork = !h->profile && (!nat.empty() || !nat_small.empty()) && !groups.empty();
+    if (fork) {
+      MM_CUDA(h, cudaEventRecord(h->fork_ev, s));
+      MM_CUDA(h, cudaStreamWaitEvent(h->side_stream, h->fork_ev, 0));
+      if (!nat_small.empty())
+        MM_CUDA(h, mmk::native_small_launch(reinterpret_cast<Problem*>(dtab + off_nat_small), nullptr,
+                                            static_cast<int>(nat_small.size()), nat_small_tiles, h->side_stream));
+      if (!nat.empty())
+        MM_CUDA(h, mmk::native_launch(reinterpret_cast<Problem*>(dtab + off_nat), nullptr,
+                                      static_cast<int>(nat.size()), nat_tiles, h->side_stream));
+      MM_CUDA(h, cudaEventRecord(h->join_ev, h->side_stream));
+    } else if (!nat.empty() || !nat_small.empty()) {
       const long m = prof_start(h, s, KIND_NATIVE);
       if (!nat_small.empty())
         MM_CUDA(h, mmk::native_small_launch(reinterpret_cast<Problem*>(dtab + off_nat_small), nullptr,
@@ -881,6 +904,7 @@ mm_status mm_gemm_grouped(mm_handle h, int count, const int* Ns, const double* c
                                reinterpret_cast<int4*>(dtab + off_units[gi]), s);
       if (st != MM_OK) return st;
     }
+    if (fork) MM_CUDA(h, cudaStreamWaitEvent(s, h->join_ev, 0));
     return MM_OK;
   };
 
