@@ -40,6 +40,7 @@ struct Problem {
   int nslots;          // segment sums per tile (all groups together)
   int defer;           // 1: slots go to the per-tile buffer and a separate pass recombines them
   long long slot_base; // int32 offset of this problem's tile 0 in the per-tile slot buffer (groups > 1)
+  int8_t slot_level[64];  // level L of each segment slot of a tile, in slot order (nslots <= 64)
 };
 
 // Device status word.  0 = fine; otherwise the first mm_status recorded.

@@ -122,6 +122,18 @@ __device__ __forceinline__ double round_i128_scaled(int64_t hi_s, uint64_t lo, i
   return d * 0x1p-1000;
 }
 
+// T = T * 2^shift_bits + v for a signed 64-bit v, on (hi:lo).
+__device__ __forceinline__ void i128_shift_add64(int64_t& hi, uint64_t& lo, int shift_bits, int64_t v) {
+  if (shift_bits > 0) {
+    hi = static_cast<int64_t>((static_cast<uint64_t>(hi) << shift_bits) | (lo >> (64 - shift_bits)));
+    lo <<= shift_bits;
+  }
+  const uint64_t add = static_cast<uint64_t>(v);
+  const uint64_t nlo = lo + add;
+  hi = hi + (v < 0 ? -1 : 0) + static_cast<int64_t>(nlo < lo ? 1 : 0);
+  lo = nlo;
+}
+
 // T = T * 256^shift_bytes + v (v sign-extended), on (hi:lo).
 __device__ __forceinline__ void i128_shift_add(int64_t& hi, uint64_t& lo, int shift_bits, int32_t v) {
   if (shift_bits > 0) {
@@ -601,24 +613,32 @@ __global__ void __launch_bounds__(256) slots_recombine_kernel(const __grid_const
   const int s = P->s, G = P->groups, maxp = args.max_pairs;
   const int32_t* at = args.tilebuf + P->slot_base + static_cast<long long>(tile_local) * P->nslots * SLOT +
                       slot_index(r, 4 * c4);
+  // Slots of one level are summed in 64-bit integers (each is below 2^31 and
+  // there are at most 64), then folded into the 128-bit total with one shift.
+  const int nslots = P->nslots;
   int64_t th[4] = {0, 0, 0, 0};
   uint64_t tl[4] = {0, 0, 0, 0};
-  int curL = 2, slot = 0;
-  for (int g = 0; g < G; ++g) {
-    int p0, p1;
-    emu_group_range(s, G, g, &p0, &p1);
-    int L, t0;
-    for (int p = p0; p < p1; ++slot) {
-      p += emu_segment(p, p1, maxp, &L, &t0);
-      const int4 v = __ldcs(reinterpret_cast<const int4*>(at + static_cast<size_t>(slot) * SLOT));
-      const int sh = 8 * (L - curL);
+  int64_t lv[4] = {0, 0, 0, 0};
+  int curL = 2;
+  for (int j = 0; j < nslots; ++j) {
+    const int L = P->slot_level[j];
+    const int4 v = __ldcs(reinterpret_cast<const int4*>(at + static_cast<size_t>(j) * SLOT));
+    if (L != curL) {  // close level curL: T = (T + S_curL) * 256^(L - curL)
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        i128_shift_add64(th[k], tl[k], 0, lv[k]);
+        i128_shift_add64(th[k], tl[k], 8 * (L - curL), 0);
+        lv[k] = 0;
+      }
       curL = L;
-      i128_shift_add(th[0], tl[0], sh, v.x);
-      i128_shift_add(th[1], tl[1], sh, v.y);
-      i128_shift_add(th[2], tl[2], sh, v.z);
-      i128_shift_add(th[3], tl[3], sh, v.w);
     }
+    lv[0] += v.x;
+    lv[1] += v.y;
+    lv[2] += v.z;
+    lv[3] += v.w;
   }
+#pragma unroll
+  for (int k = 0; k < 4; ++k) i128_shift_add64(th[k], tl[k], 0, lv[k]);
   const int tail = 8 * (s + 1 - curL);
   const int base_scale = P->a_exp[row] - 8 * s - 6;
   double* crow = P->C + static_cast<size_t>(row) * n;

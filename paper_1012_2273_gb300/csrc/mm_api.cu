@@ -363,8 +363,22 @@ mm_status layout_group(mm_handle h, EmuGroup& g, char* base) {
       G = static_cast<int>(std::lround(P * kb / std::max(target, 1.0)));
       G = std::max(1, std::min(G, P));
     }
+    // A tile's segment slots are listed per problem (at most 64).
+    while (G > 1 && mmk::emu_tile_slots(p.s, G, g.max_pairs) > 64) --G;
     p.groups = G;
     p.nslots = mmk::emu_tile_slots(p.s, G, g.max_pairs);
+    if (p.nslots > 64) return fail(h, MM_ERR_UNSUPPORTED, "too many accumulation segments for this size");
+    {
+      int k = 0;
+      for (int gi = 0; gi < G; ++gi) {
+        int p0, p1, L, t0;
+        mmk::emu_group_range(p.s, G, gi, &p0, &p1);
+        for (int q = p0; q < p1; ++k) {
+          q += mmk::emu_segment(q, p1, g.max_pairs, &L, &t0);
+          p.slot_level[k] = static_cast<int8_t>(L);
+        }
+      }
+    }
     // Short tiles (small N) leave the recombination to a separate pass: done
     // in the epilogue it stalls the tensor pipe for a large share of the tile.
     p.defer = p.n < kDeferBelowN ? 1 : 0;
