@@ -610,7 +610,7 @@ __global__ void __launch_bounds__(256) slots_recombine_kernel(const __grid_const
   emu_tile_coords(tile_local, P->tiles_m, P->tiles_n, &tm, &tn);
   const int n = P->n, row = tm * EM_BM + r, col = tn * BN + 4 * c4;
   if (row >= n || col >= n) return;
-  const int s = P->s, G = P->groups, maxp = args.max_pairs;
+  const int s = P->s;
   const int32_t* at = args.tilebuf + P->slot_base + static_cast<long long>(tile_local) * P->nslots * SLOT +
                       slot_index(r, 4 * c4);
   // Slots of one level are summed in 64-bit integers (each is below 2^31 and
