@@ -15,6 +15,12 @@ Parity status of each function (what pins it, in ``tests/test_oracle_pins.py``):
   absgemm -- exact integer case, bound against the exact rational value.
   gemm_dot2 -- exact rational product (Python fractions) on small cases.
   freivalds -- accepts exact products, rejects planted errors.
+  fixed_gemm / fixed_gemm_rows / fix -- the exact product of the rounded
+      fixed-point operands, against Python integers and fractions on small
+      random cases (every step: exponents, rounding, exact sum, one final
+      rounding), exact on small-integer inputs, within the fixed-point error
+      bound of the exact product on random ones.
+  modular_beta -- the fixed-point width rule, against Python big integers.
   emu_* -- digits reconstruct D exactly; D equals the exact rounding of
       a 2^(8s-1-e) (Python fractions); level sums equal brute force with
       Python integers; RN of 128-bit integers equals Python's correctly
@@ -89,6 +95,12 @@ def lib() -> ctypes.CDLL:
             L.or_max_threads.restype = c_int
             L.or_int128_to_double.argtypes = [ctypes.c_int64, ctypes.c_uint64]
             L.or_int128_to_double.restype = c_double
+            L.or_fix.argtypes = [c_double, c_int, c_int]
+            L.or_fix.restype = ctypes.c_int64
+            L.or_fixed_gemm.argtypes = [c_int, c_int, _D, _D, _D, c_int]
+            L.or_fixed_gemm.restype = c_int
+            L.or_fixed_gemm_rows.argtypes = [c_int, c_int, _D, _D, _I, c_int, _D, c_int]
+            L.or_fixed_gemm_rows.restype = c_int
             _lib = L
     return _lib
 
@@ -250,3 +262,55 @@ def int128_to_double(T: int) -> float:
 
 def max_threads() -> int:
     return int(lib().or_max_threads())
+
+
+# ---- 4. the modular form: exact product of fixed-point operands -------------
+
+# The moduli of the modular emulation form, in the order the library uses
+# them: pairwise coprime, each at most 256 so that every symmetric residue
+# (|r| <= 128) is an exact bf16 value.  The first k are used with k moduli.
+MODULI = (256, 255, 253, 251, 247, 241, 239, 233, 229, 227, 223, 217, 211, 199, 197, 193)
+MAX_FIXED_BITS = 55
+
+
+def modular_beta(k: int, n: int) -> int:
+    """Fixed-point width used with the first k moduli at size n.
+
+    The largest beta <= 55 with 4 n 2^(2 beta) <= M_k (M_k the product of the
+    first k moduli): the exact product X of two beta-bit operands has
+    |X| <= n 2^(2 beta) <= M_k / 4, so X is recovered from its residues with
+    a quarter of the modulus to spare.  0 means k is too small for n.
+    """
+    M = 1
+    for m in MODULI[:k]:
+        M *= m
+    for beta in range(MAX_FIXED_BITS, 0, -1):
+        if 4 * n * (1 << (2 * beta)) <= M:
+            return beta
+    return 0
+
+
+def fix(v: float, e: int, beta: int) -> int:
+    """round-half-even(v 2^(beta - e))."""
+    return int(lib().or_fix(float(v), int(e), int(beta)))
+
+
+def fixed_gemm(A, B, beta: int, nthreads: int | None = None) -> np.ndarray:
+    """RN(sum_j A_int B_int) 2^(e_i + f_k - 2 beta): the modular form's result."""
+    A, B, n = _square(A, B)
+    C = np.empty((n, n), np.float64)
+    rc = lib().or_fixed_gemm(n, int(beta), _dp(A), _dp(B), _dp(C), threads(nthreads))
+    if rc != 0:
+        raise ValueError(f"oracle: fixed_gemm failed ({rc})")
+    return C
+
+
+def fixed_gemm_rows(A, B, beta: int, rows, nthreads: int | None = None) -> np.ndarray:
+    A, B, n = _square(A, B)
+    r = np.ascontiguousarray(rows, dtype=np.int32)
+    out = np.empty((len(r), n), np.float64)
+    rc = lib().or_fixed_gemm_rows(n, int(beta), _dp(A), _dp(B), r.ctypes.data_as(_I), len(r), _dp(out),
+                                  threads(nthreads))
+    if rc != 0:
+        raise ValueError(f"oracle: fixed_gemm_rows failed ({rc})")
+    return out

@@ -437,3 +437,99 @@ double or_int128_to_double(int64_t hi, uint64_t lo) {
   __int128 T = ((__int128)hi << 64) | (__int128)lo;
   return (double)T;
 }
+
+/* ------------------------------------------------------------------------ */
+/* 4. Exact product of fixed-point operands (model of the modular form)      */
+/* ------------------------------------------------------------------------ */
+/*
+ * The library's second emulation form (no counterpart in the paper, which
+ * computes in native FP64) rounds every operand to a fixed-point integer and
+ * recovers the exact integer product from its residues modulo several small
+ * moduli (Chinese remainder theorem), after Ozaki, Uchino and Imamura's
+ * "Ozaki scheme II" (2025).  The residues are only the means; what it
+ * computes has a plain definition, written out here without any modular
+ * arithmetic:
+ *   A_int(i,j) = round-half-even(a_ij 2^(beta - e_i)),  e_i as in section 3
+ *   B_int(j,k) = round-half-even(b_jk 2^(beta - f_k)),  f_k likewise
+ *   X(i,k)     = sum_j A_int(i,j) B_int(j,k)        (exact, 128-bit)
+ *   c_ik       = RN(X(i,k)) 2^(e_i + f_k - 2 beta)
+ * |A_int|, |B_int| <= 2^beta, so |X| <= n 2^(2 beta) < 2^127 for beta <= 55
+ * and n < 2^17.
+ */
+
+/* round-half-even(v 2^(beta - e)); exact scaling as in or_emu_fixed. */
+int64_t or_fix(double v, int e, int beta) { return (int64_t)nearbyint(ldexp(v, beta - e)); }
+
+static int fixed_args_ok(int n, int beta) { return n >= 0 && n < (1 << 17) && beta >= 1 && beta <= 55; }
+
+/* Row i of the product from A_int row `ai` and all of B_int (row-major [j][k]). */
+static void fixed_row(int n, int beta, const int64_t* ai, const int64_t* Bi, int e, const int* f,
+                      __int128* acc, double* out) {
+  for (int k = 0; k < n; ++k) acc[k] = 0;
+  for (int j = 0; j < n; ++j) {
+    const __int128 a = ai[j];
+    const int64_t* b = Bi + (size_t)j * n;
+    for (int k = 0; k < n; ++k) acc[k] += a * (__int128)b[k];
+  }
+  for (int k = 0; k < n; ++k) out[k] = ldexp((double)acc[k], e + f[k] - 2 * beta);
+}
+
+static int64_t* fixed_B(int n, int beta, const double* B, int* f) {
+  int64_t* Bi = (int64_t*)malloc(sizeof(int64_t) * (size_t)n * n);
+  if (!Bi) return NULL;
+  or_emu_col_exponents(n, B, f);
+  for (int j = 0; j < n; ++j)
+    for (int k = 0; k < n; ++k) Bi[(size_t)j * n + k] = or_fix(B[(size_t)j * n + k], f[k], beta);
+  return Bi;
+}
+
+/* Rows `rows[0..nrows)` of the fixed-point product into out[nrows][n].
+ * Returns 0 on success. */
+int or_fixed_gemm_rows(int n, int beta, const double* A, const double* B, const int* rows, int nrows,
+                       double* out, int nthreads) {
+  if (!fixed_args_ok(n, beta)) return -1;
+  if (n == 0 || nrows == 0) return 0;
+  int* f = (int*)malloc(sizeof(int) * (size_t)n);
+  int64_t* Bi = f ? fixed_B(n, beta, B, f) : NULL;
+  if (!f || !Bi) { free(f); free(Bi); return -2; }
+  int bad = 0;
+#ifdef _OPENMP
+  if (nthreads < 1) nthreads = 1;
+#pragma omp parallel num_threads(nthreads) reduction(+ : bad)
+#endif
+  {
+    int64_t* ai = (int64_t*)malloc(sizeof(int64_t) * (size_t)n);
+    __int128* acc = (__int128*)malloc(sizeof(__int128) * (size_t)n);
+    if (!ai || !acc) {
+      ++bad;
+    } else {
+#ifdef _OPENMP
+#pragma omp for schedule(dynamic)
+#endif
+      for (int r = 0; r < nrows; ++r) {
+        const double* a = A + (size_t)rows[r] * n;
+        const int e = exponent_of_max(a, n, 1);
+        for (int j = 0; j < n; ++j) ai[j] = or_fix(a[j], e, beta);
+        fixed_row(n, beta, ai, Bi, e, f, acc, out + (size_t)r * n);
+      }
+    }
+    free(ai);
+    free(acc);
+  }
+  (void)nthreads;
+  free(f);
+  free(Bi);
+  return bad ? -2 : 0;
+}
+
+/* The whole fixed-point product C (n x n).  Returns 0 on success. */
+int or_fixed_gemm(int n, int beta, const double* A, const double* B, double* C, int nthreads) {
+  if (!fixed_args_ok(n, beta)) return -1;
+  if (n == 0) return 0;
+  int* rows = (int*)malloc(sizeof(int) * (size_t)n);
+  if (!rows) return -2;
+  for (int i = 0; i < n; ++i) rows[i] = i;
+  const int r = or_fixed_gemm_rows(n, beta, A, B, rows, n, C, nthreads);
+  free(rows);
+  return r;
+}

@@ -314,3 +314,124 @@ def test_emulated_rows_match_full_model():
     C = oracle.emu_gemm(A, B, 5)
     rows = [0, 69, 31]
     np.testing.assert_array_equal(oracle.emu_gemm_rows(A, B, 5, rows), C[rows])
+
+
+# ---- the modular form's definition: exact product of fixed-point operands ----
+
+def _py_exponent(vals):
+    m = max(abs(float(v)) for v in vals)
+    return 0 if m == 0 else math.frexp(m)[1]  # m = f 2^e, f in [0.5, 1)
+
+
+def _py_fixed_product(A, B, beta):
+    """Every step with Python integers and fractions, independent of oracle.c."""
+    n = A.shape[0]
+    e = [_py_exponent(A[i, :]) for i in range(n)]
+    f = [_py_exponent(B[:, k]) for k in range(n)]
+    Ai = [[round(Fraction(float(A[i, j])) * Fraction(2) ** (beta - e[i])) for j in range(n)] for i in range(n)]
+    Bi = [[round(Fraction(float(B[j, k])) * Fraction(2) ** (beta - f[k])) for k in range(n)] for j in range(n)]
+    C = np.empty((n, n))
+    for i in range(n):
+        for k in range(n):
+            X = sum(Ai[i][j] * Bi[j][k] for j in range(n))
+            C[i, k] = float(Fraction(X) * Fraction(2) ** (e[i] + f[k] - 2 * beta))  # correctly rounded
+    return C
+
+
+def test_fix_is_the_exact_rounding():
+    vals = list(workload.values("loguniform20", 4, 200)) + [0.0, -0.0, 1 - 2 ** -53, -(1 - 2 ** -53), 0.5,
+                                                             2 ** -60, 3 * 2 ** -56]
+    for beta in (1, 7, 30, 47, 55):
+        for v in vals:
+            e = 1 if abs(v) < 1 else math.frexp(abs(v))[1]
+            assert oracle.fix(v, e, beta) == round(Fraction(float(v)) * Fraction(2) ** (beta - e))
+    assert oracle.fix(3 * 2.0 ** -3, 0, 2) == 2   # 1.5 -> 2 (ties to even)
+    assert oracle.fix(5 * 2.0 ** -3, 0, 2) == 2   # 2.5 -> 2
+    assert oracle.fix(-5 * 2.0 ** -3, 0, 2) == -2
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 5, 7])
+@pytest.mark.parametrize("dist", ["uniform11", "loguniform20"])
+def test_fixed_product_by_exact_integers(n, dist):
+    A, B = workload.pair(dist, 30 + n, n)
+    A[0, :] *= 2.0 ** 30  # rows and columns on different scales
+    B[:, -1] *= 2.0 ** -25
+    for beta in (3, 21, 40, 55):
+        np.testing.assert_array_equal(oracle.fixed_gemm(A, B, beta), _py_fixed_product(A, B, beta))
+
+
+def test_fixed_product_with_zero_rows_and_columns():
+    n = 6
+    A, B = workload.pair("uniform11", 41, n)
+    A[2, :] = 0.0
+    B[:, 4] = -0.0
+    C = oracle.fixed_gemm(A, B, 50)
+    np.testing.assert_array_equal(C, _py_fixed_product(A, B, 50))
+    assert np.all(C[2, :] == 0) and np.all(C[:, 4] == 0)
+
+
+@pytest.mark.parametrize("beta", [4, 20, 55])
+def test_fixed_product_is_exact_on_small_integers(beta):
+    n = 40  # entries in {-8..8}: a 2^(beta - e) is an integer once beta >= 4
+    A, B = workload.pair("int8", 13, n)
+    ref = (A.astype(np.int64) @ B.astype(np.int64)).astype(np.float64)
+    np.testing.assert_array_equal(oracle.fixed_gemm(A, B, beta), ref)
+
+
+@pytest.mark.parametrize("dist", ["uniform11", "loguniform20"])
+def test_fixed_product_error_bound(dist):
+    # a_ij 2^(beta - e_i) moves by at most 1/2 when rounded, so
+    # |X 2^(e+f-2beta) - (AB)_ik| <= 2^(-beta-1) (2^e_i sum_j |b_jk| + 2^f_k sum_j |a_ij|)
+    #                                 + n 2^(e_i + f_k - 2 beta - 2),
+    # and the final rounding adds at most 2^-53 of the result.
+    n = 32
+    A, B = workload.pair(dist, 17, n)
+    ex = exact_product(A, B)
+    e = np.array([_py_exponent(A[i, :]) for i in range(n)], dtype=np.float64)
+    f = np.array([_py_exponent(B[:, k]) for k in range(n)], dtype=np.float64)
+    rowsum = np.abs(A).sum(axis=1)
+    colsum = np.abs(B).sum(axis=0)
+    errs = []
+    for beta in (16, 30, 45, 55):
+        C = oracle.fixed_gemm(A, B, beta)
+        worst = 0.0
+        for i in range(n):
+            for k in range(n):
+                fix_err = (2.0 ** (e[i] - beta - 1) * colsum[k] + 2.0 ** (f[k] - beta - 1) * rowsum[i]
+                           + n * 2.0 ** (e[i] + f[k] - 2 * beta - 2))
+                bound = Fraction(fix_err) + Fraction(U) * (abs(ex[i][k]) + Fraction(fix_err))
+                err = abs(Fraction(float(C[i, k])) - ex[i][k])
+                assert err <= bound * Fraction(1001, 1000), (beta, i, k)
+                worst = max(worst, float(err / max(Fraction(float((np.abs(A) @ np.abs(B))[i, k])), Fraction(1, 2**1000))))
+        errs.append(worst)
+    assert all(b < a for a, b in zip(errs, errs[1:])), errs
+    if dist == "uniform11":
+        assert errs[0] > 2 * n * U >= errs[-1], errs  # 16 bits are not FP64, 55 bits meet the bound
+    # (wide-range entries: the width is relative to the row and column maxima,
+    # so at n = 32 a dot product of small entries keeps a larger relative error)
+
+
+def test_fixed_rows_match_full_product():
+    n = 70
+    A, B = workload.pair("loguniform20", 23, n)
+    C = oracle.fixed_gemm(A, B, 48)
+    rows = [0, 69, 31]
+    np.testing.assert_array_equal(oracle.fixed_gemm_rows(A, B, 48, rows), C[rows])
+
+
+def test_modular_width_rule():
+    M = oracle.MODULI
+    assert len(M) == 16 and list(M) == sorted(M, reverse=True) and max(M) <= 256
+    assert all(math.gcd(a, b) == 1 for i, a in enumerate(M) for b in M[i + 1:])
+    assert math.prod(M) < 2 ** 126  # recovered integers fit a signed 128-bit word
+    for k in range(2, 17):
+        Mk = math.prod(M[:k])
+        for n in (1, 100, 500, 2000, 4095, 8192, 16384, 32767):
+            beta = oracle.modular_beta(k, n)
+            if beta == 0:
+                assert 4 * n * 4 > Mk
+                continue
+            assert 4 * n * 2 ** (2 * beta) <= Mk
+            assert beta == oracle.MAX_FIXED_BITS or 4 * n * 2 ** (2 * beta + 2) > Mk
+    assert oracle.modular_beta(16, 2000) == 55 and oracle.modular_beta(16, 16384) == 54
+    assert oracle.modular_beta(14, 8192) == 47 and oracle.modular_beta(15, 2000) == 52
