@@ -8,7 +8,7 @@
  * N from 10 to 2000 (Sec. 1.1, Sec. 4.1) and counts N^2 (2N - 1) operations
  * per product (Sec. 3.1, Alg. 2).
  *
- * Two forms compute it on the GPU:
+ * Three forms compute it on the GPU:
  *   MM_NATIVE_FP64  FP64 tensor-core MMA (mma.sync f64), one rounding per
  *                   fused multiply-add, in an order other than the paper's.
  *   MM_EMU_BF16     split-precision emulation: A is scaled per row and B per
@@ -17,6 +17,15 @@
  *                   products run on the tcgen05 tensor cores with exact
  *                   integer accumulation, and the exact sum is rounded once
  *                   to FP64.  Nothing in the paper corresponds to it.
+ *   MM_EMU_MODULAR  modular emulation: A (per row) and B (per column) are
+ *                   rounded to beta-bit fixed-point integers, their residues
+ *                   modulo k pairwise coprime moduli <= 256 (held exactly in
+ *                   bf16) are multiplied on the tcgen05 tensor cores, the
+ *                   exact integer product is recovered by the Chinese
+ *                   remainder theorem and rounded once to FP64 (after Ozaki,
+ *                   Uchino and Imamura's "Ozaki scheme II", 2025): k products
+ *                   instead of the s(s+1)/2 of the digit form.  Nothing in
+ *                   the paper corresponds to it either.
  * MM_AUTO picks one per problem (see mm_config).
  *
  * Conventions for every call:
@@ -57,7 +66,8 @@ typedef enum {
 typedef enum {
   MM_NATIVE_FP64 = 0,
   MM_EMU_BF16 = 1,
-  MM_AUTO = 3
+  MM_AUTO = 3,
+  MM_EMU_MODULAR = 4
 } mm_mode;
 
 /* Flags of mm_config.flags. */
@@ -66,7 +76,8 @@ typedef enum {
 
 typedef struct {
   mm_mode mode;          /* default MM_AUTO */
-  int slices;            /* emulation digit count s in 1..8; 0 = chosen per problem */
+  int slices;            /* digit count s in 1..8 (MM_EMU_BF16), moduli k in 2..16
+                            (MM_EMU_MODULAR); 0 = chosen per problem */
   unsigned flags;        /* MM_FLAG_* */
   const char* tune_path; /* optional autotune table (text file); NULL = built-in table */
 } mm_config;
@@ -104,9 +115,19 @@ mm_status mm_status_get(mm_handle h, void* stream);
 /* Message of the last failed call on this handle (never NULL). */
 const char* mm_last_error(mm_handle h);
 
-/* Digit count the handle would use for an N x N problem (after AUTO), and
- * the form: 0 = native FP64, 1 = emulation. */
+/* Form and slice count the handle would use for an N x N problem (after
+ * AUTO): form 0 = native FP64, 1 = digit emulation (slices = digits s),
+ * 2 = modular emulation (slices = moduli k). */
 mm_status mm_plan(mm_handle h, int N, int* form, int* slices);
+
+/* Parameters of the modular form with k moduli at size N, computed on the
+ * host (no handle, no GPU): *beta receives the fixed-point width, the
+ * largest beta <= 55 with 4 N 2^(2 beta) <= m_1 m_2 ... m_k, so that the exact
+ * product of two beta-bit operands (at most N 2^(2 beta) in magnitude) is
+ * recovered from its residues with a quarter of the modulus to spare; 0 when
+ * k is too small for N.  moduli (may be NULL) receives m_1..m_k.
+ * MM_ERR_INVALID for k outside 1..16 or N < 1. */
+mm_status mm_modular_params(int k, int N, int* beta, int* moduli);
 
 /* Device time of the last call made on this handle with MM_FLAG_PROFILE set,
  * in milliseconds, by kernel kind (events recorded on the call's stream):

@@ -23,6 +23,7 @@ from . import build as _build
 NATIVE_FP64 = 0
 EMU_BF16 = 1
 AUTO = 3
+EMU_MODULAR = 4
 FLAG_NO_GRAPH = 1
 FLAG_PROFILE = 2
 
@@ -31,7 +32,10 @@ STATUS_NAMES = {
     4: "MM_ERR_UNSUPPORTED", 5: "MM_ERR_TIMEOUT", 6: "MM_ERR_NONFINITE",
 }
 
-_MODES = {"native": NATIVE_FP64, "emulated": EMU_BF16, "emu": EMU_BF16, "auto": AUTO}
+_MODES = {"native": NATIVE_FP64, "emulated": EMU_BF16, "emu": EMU_BF16, "auto": AUTO,
+          "modular": EMU_MODULAR}
+# forms reported by plan(): native FP64, digit emulation, modular emulation
+FORMS = ("native", "emulated", "modular")
 
 _lock = threading.Lock()
 _lib = None
@@ -51,7 +55,7 @@ class _Config(ctypes.Structure):
 SYMBOLS = ("mm_create", "mm_destroy", "mm_gemm", "mm_gemm_grouped", "mm_gemm_host", "mm_status_get",
            "mm_last_error", "mm_plan", "mm_profile_read", "mm_probe_fp64_peak", "mm_selftest_wait", "mm_split",
            "mm_split_noalloc",
-           "mm_level_sums", "mm_recombine")
+           "mm_level_sums", "mm_recombine", "mm_modular_params")
 SPLIT_NOALLOC_MAX_N = 65536
 KERNEL_KINDS = ("split", "slice_products", "native_fp64", "recombine")
 
@@ -87,6 +91,7 @@ def lib(build_if_needed: bool = True) -> ctypes.CDLL:
             L.mm_profile_read.argtypes = [vp, ctypes.POINTER(cd), ctypes.POINTER(ci)]
             L.mm_probe_fp64_peak.argtypes = [vp, ctypes.POINTER(cd), ctypes.POINTER(cd)]
             L.mm_selftest_wait.argtypes = [vp, ci, vp]
+            L.mm_modular_params.argtypes = [ci, ci, ctypes.POINTER(ci), ctypes.POINTER(ci)]
             for name in SYMBOLS:
                 if name != "mm_last_error":
                     getattr(L, name).restype = ci
@@ -130,6 +135,17 @@ def split_noalloc(M, by_columns: bool, slices: int, exps, digits, status=None, s
     return int(lib().mm_split_noalloc(n, M.data_ptr(), int(bool(by_columns)), int(slices), exps.data_ptr(),
                                       digits.data_ptr(), rows, ld, status.data_ptr() if status is not None else None,
                                       _stream_ptr(stream)))
+
+
+def modular_params(k: int, n: int) -> tuple[int, tuple[int, ...]]:
+    """mm_modular_params: (fixed-point width beta, moduli) of the modular form
+    with k moduli at size n.  Host-only; needs no GPU."""
+    beta = ctypes.c_int(0)
+    mods = (ctypes.c_int * 16)()
+    rc = int(lib().mm_modular_params(int(k), int(n), ctypes.byref(beta), mods))
+    if rc != 0:
+        raise MMError(rc, "mm_modular_params: k must be in 1..16 and n >= 1")
+    return beta.value, tuple(mods[:k])
 
 
 class Handle:

@@ -35,7 +35,8 @@ struct Problem {
   int n_pad;           // rows of a B^T plane (multiple of the tile width)
   int k_pad;           // columns of a plane (multiple of 64)
   int split_begin;     // first split tile of this problem (scale/split kernels)
-  int s;               // digits per value (emulation), 1..8
+  int s;               // digits per value (digit form, 1..8) or moduli (modular form, 2..16)
+  int beta;            // modular form: fixed-point width of the operands; 0 = digit form
   int groups;          // digit-pair groups per tile: work units per tile of the slice-product kernel
   int nslots;          // segment sums per tile (all groups together)
   int defer;           // 1: slots go to the per-tile buffer and a separate pass recombines them

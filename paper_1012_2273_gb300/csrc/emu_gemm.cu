@@ -46,8 +46,11 @@
 #include <cstdio>
 
 #include "launch.cuh"
+#include "modular.cuh"
 
 namespace mmk {
+
+static __constant__ ModTables c_mod = make_mod_tables();
 
 constexpr int EM_BM = 128;
 constexpr int EM_BK = 64;          // elements per k-block: one 128-byte swizzle row
@@ -243,7 +246,7 @@ __device__ __forceinline__ void recombine_row(const int32_t* tile_slots, int s, 
   }
 }
 
-template <int BN>
+template <int BN, bool kMod>
 __global__ void __launch_bounds__(EM_THREADS, 1)
     emu_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                     const __grid_constant__ EmuArgs args) {
@@ -341,11 +344,15 @@ __global__ void __launch_bounds__(EM_THREADS, 1)
         const CUtensorMap* ma = args.units ? &args.maps[2 * U.pi] : &mapA;
         const CUtensorMap* mb = args.units ? &args.maps[2 * U.pi + 1] : &mapB;
         int p0, p1;
-        emu_group_range(P->s, U.G, U.g, &p0, &p1);
+        unit_group_range<kMod>(P->s, U.G, U.g, &p0, &p1);
         for (int p = p0; p < p1 && ok; ++p) {
-          int L, t;
-          emu_pair_of(p, &L, &t);
-          const int uu = L - t;
+          int ta = p, tb = p;  // modular form: residue planes p of A and of B^T
+          if (!kMod) {         // digit pair (t, L - t): planes t - 1 and L - t - 1
+            int L, t;
+            emu_pair_of(p, &L, &t);
+            ta = t - 1;
+            tb = L - t - 1;
+          }
           for (int kb = 0; kb < KB; ++kb) {
             if (!mbar_wait(&empty[stage], phase ^ 1, tmo, args.status)) {
               ok = false;
@@ -353,8 +360,8 @@ __global__ void __launch_bounds__(EM_THREADS, 1)
             }
             uint8_t* sa = smem + stage * Cfg::STAGE_BYTES;
             mbar_arrive_expect_tx(&full[stage], Cfg::STAGE_BYTES);
-            tma_load_2d_hint(sa, ma, &full[stage], kb * EM_BK, (t - 1) * P->m_pad + m0, keep);
-            tma_load_2d_hint(sa + Cfg::A_BYTES, mb, &full[stage], kb * EM_BK, (uu - 1) * P->n_pad + n0, keep);
+            tma_load_2d_hint(sa, ma, &full[stage], kb * EM_BK, ta * P->m_pad + m0, keep);
+            tma_load_2d_hint(sa + Cfg::A_BYTES, mb, &full[stage], kb * EM_BK, tb * P->n_pad + n0, keep);
             ++issued;
             if (++stage == Cfg::STAGES) {
               stage = 0;
@@ -402,10 +409,10 @@ __global__ void __launch_bounds__(EM_THREADS, 1)
         const UnitRef U = emu_unit(args, u);
         const int KB = U.P->k_pad / EM_BK;
         int p0, p1;
-        emu_group_range(U.P->s, U.G, U.g, &p0, &p1);
+        unit_group_range<kMod>(U.P->s, U.G, U.g, &p0, &p1);
         int L, t0;
         for (int p = p0; p < p1 && ok;) {
-          const int np = emu_segment(p, p1, maxp, &L, &t0);
+          const int np = kMod ? 1 : emu_segment(p, p1, maxp, &L, &t0);
           p += np;
           const int nb = np * KB;
           for (int c0 = 0; c0 < nb && ok; c0 += EM_CHUNK_KB) {
@@ -486,20 +493,22 @@ __global__ void __launch_bounds__(EM_THREADS, 1)
       const int row = m0 + r_in_tile;
       const int s = P->s;
       int p0, p1;
-      emu_group_range(s, U.G, U.g, &p0, &p1);
+      unit_group_range<kMod>(s, U.G, U.g, &p0, &p1);
       // slot of this unit's first segment, and where the tile's slots live
-      int slot = 0;
-      for (int g = 0; g < U.g; ++g) {
-        int q0, q1;
-        emu_group_range(s, U.G, g, &q0, &q1);
-        slot += emu_count_segments(q0, q1, maxp);
+      int slot = kMod ? p0 : 0;
+      if (!kMod) {
+        for (int g = 0; g < U.g; ++g) {
+          int q0, q1;
+          emu_group_range(s, U.G, g, &q0, &q1);
+          slot += emu_count_segments(q0, q1, maxp);
+        }
       }
       int32_t* tile_slots = (U.G > 1 || P->defer)
                                 ? args.tilebuf + P->slot_base + static_cast<long long>(U.tile_local) * P->nslots * SLOT
                                 : my_scratch;
       int L, t0;
       for (int p = p0; p < p1 && ok; ++slot) {
-        const int np = emu_segment(p, p1, maxp, &L, &t0);
+        const int np = kMod ? 1 : emu_segment(p, p1, maxp, &L, &t0);
         p += np;
         const int nb = np * KB;
         const int nchunks = (nb + EM_CHUNK_KB - 1) / EM_CHUNK_KB;
@@ -531,6 +540,40 @@ __global__ void __launch_bounds__(EM_THREADS, 1)
         }
         if (!ok) break;
         const uint32_t bias = static_cast<uint32_t>(nchunks) * EM_MAGIC;
+        if (kMod) {
+          // The exact sum S = sum_j r_a r_b of this modulus m (|S| <= n 2^14
+          // <= 2^30) becomes t = (S mod m) y mod m in [0, m), one byte: x =
+          // S + (a multiple of m, at least 2^30) is non-negative and below
+          // 2^31 + 2^8, where floor(x / m) = umulhi(x, ceil(2^39 / m)) >> 7
+          // exactly; y = (M_k / m)^-1 mod m prepares the Chinese remainder
+          // sum.  Slot layout: [col / 16][row][16 bytes], one 16-byte vector
+          // per 16 columns, a warp's 32 rows contiguous.
+          const int j = slot;
+          const uint32_t m = c_mod.m_u[j], magic = c_mod.magic[j], y = c_mod.y[s][j];
+          const uint32_t shift_in = c_mod.bias[j] - bias;  // x = acc - bias + bias_j
+          uint8_t* dst = reinterpret_cast<uint8_t*>(args.tilebuf + P->slot_base) +
+                         (static_cast<size_t>(U.tile_local) * P->nslots + j) * (EM_BM * BN) +
+                         static_cast<size_t>(h * HALF / 16) * (EM_BM * 16) + r_in_tile * 16;
+#pragma unroll
+          for (int c = 0; c < HALF; c += 16) {
+            uint32_t w[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              uint32_t word = 0;
+#pragma unroll
+              for (int b = 0; b < 4; ++b) {
+                const uint32_t x = acc[c + 4 * q + b] + shift_in;
+                const uint32_t r = x - (__umulhi(x, magic) >> 7) * m;
+                const uint32_t pr = r * y;
+                const uint32_t t = pr - (__umulhi(pr, magic) >> 7) * m;
+                word |= t << (8 * b);
+              }
+              w[q] = word;
+            }
+            __stcs(reinterpret_cast<uint4*>(dst + (c / 16) * (EM_BM * 16)), make_uint4(w[0], w[1], w[2], w[3]));
+          }
+          continue;
+        }
         if (args.levels_out) {
           // step API (one group per tile): accumulate this segment into level L
           if (row < n) {
@@ -558,7 +601,8 @@ __global__ void __launch_bounds__(EM_THREADS, 1)
           }
         }
       }
-      if (!ok || args.levels_out || P->defer) continue;  // deferred: recombined by slots_recombine_kernel
+      // deferred (and every modular problem): recombined by a separate pass
+      if (!ok || args.levels_out || P->defer || kMod) continue;
       bool mine = true;
       if (U.G > 1) {
         // Each epilogue warp owns the same 32 x BN/2 region in every unit of
@@ -651,6 +695,75 @@ __global__ void __launch_bounds__(256) slots_recombine_kernel(const __grid_const
   }
 }
 
+// Recombination of the modular form with K moduli, after the slice-product
+// kernel: one thread per 16 consecutive outputs of a tile row (one 16-byte
+// vector per modulus).  With t_j = (X mod m_j) (M/m_j)^-1 mod m_j from the
+// epilogue, V = sum_j t_j (M/m_j) is congruent to X modulo M = m_1...m_K and
+// V / M = sum_j t_j / m_j < K.  Because |X| <= M/4 (the width rule),
+// X = V - round(V/M) M, and round(V/M) is found from a 24-bit estimate of V:
+// its relative error is a few 2^-24, far inside the quarter-modulus margin.
+// V is summed in four 64-bit accumulators of 32-bit limbs (each term below
+// 2^40, K of them), carried, and X is formed modulo 2^128, exact since
+// |X| < 2^126.  Then one rounding: c = RN(X) 2^(e_i + f_k - 2 beta).
+template <int K, int BN>
+__global__ void __launch_bounds__(256) mod_recombine_kernel(const __grid_constant__ EmuArgs args) {
+  constexpr int PER_TILE = EM_BM * BN / 16;  // threads per tile
+  constexpr size_t SLOT_BYTES = static_cast<size_t>(EM_BM) * BN;
+  constexpr int QS = limbs_bit_length(mod_product(K)) - 31;  // V 2^-QS < 2^35
+  const long long item = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+  const int tile = static_cast<int>(item / PER_TILE);
+  const int in_tile = static_cast<int>(item - static_cast<long long>(tile) * PER_TILE);
+  const Problem* P = args.table ? &args.table[find_problem(args.table, args.count, tile)] : &args.single;
+  const int tile_local = tile - P->tile_begin;
+  if (P->beta <= 0 || P->s != K || tile_local < 0 || tile_local >= P->tiles_m * P->tiles_n) return;
+  const int r = in_tile % EM_BM, c16 = in_tile / EM_BM;
+  int tm, tn;
+  emu_tile_coords(tile_local, P->tiles_m, P->tiles_n, &tm, &tn);
+  const int n = P->n, row = tm * EM_BM + r, col0 = tn * BN + 16 * c16;
+  if (row >= n || col0 >= n) return;
+  const uint8_t* at = reinterpret_cast<const uint8_t*>(args.tilebuf + P->slot_base) +
+                      static_cast<size_t>(tile_local) * K * SLOT_BYTES + static_cast<size_t>(c16) * (EM_BM * 16) +
+                      r * 16;
+  uint4 v[K];
+#pragma unroll
+  for (int j = 0; j < K; ++j) v[j] = __ldcs(reinterpret_cast<const uint4*>(at + j * SLOT_BYTES));
+  const int base_scale = P->a_exp[row] - 2 * P->beta;
+  const uint64_t m_lo = (static_cast<uint64_t>(c_mod.mk[K][1]) << 32) | c_mod.mk[K][0];
+  const uint64_t m_hi = (static_cast<uint64_t>(c_mod.mk[K][3]) << 32) | c_mod.mk[K][2];
+  double* crow = P->C + static_cast<size_t>(row) * n;
+#pragma unroll
+  for (int c = 0; c < 16; ++c) {
+    if (col0 + c < n) {
+      uint64_t a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+#pragma unroll
+      for (int j = 0; j < K; ++j) {
+        const uint32_t word = (c < 4) ? v[j].x : (c < 8) ? v[j].y : (c < 12) ? v[j].z : v[j].w;
+        const uint32_t t = (word >> (8 * (c & 3))) & 255u;
+        a0 += static_cast<uint64_t>(t) * c_mod.mj[K][j][0];
+        a1 += static_cast<uint64_t>(t) * c_mod.mj[K][j][1];
+        a2 += static_cast<uint64_t>(t) * c_mod.mj[K][j][2];
+        a3 += static_cast<uint64_t>(t) * c_mod.mj[K][j][3];
+      }
+      a1 += a0 >> 32;
+      a2 += a1 >> 32;
+      a3 += a2 >> 32;
+      const uint32_t w0 = static_cast<uint32_t>(a0), w1 = static_cast<uint32_t>(a1), w2 = static_cast<uint32_t>(a2);
+      // q = round(V / M) from V 2^-QS in FP32
+      const float vf = __ull2float_rn(a3) * pow2f(96 - QS) + __uint2float_rn(w2) * pow2f(64 - QS) +
+                       __uint2float_rn(w1) * pow2f(32 - QS) + __uint2float_rn(w0) * pow2f(-QS);
+      const uint64_t q = static_cast<uint64_t>(__float2int_rn(vf * c_mod.qscale[K]));
+      // X = V - q M modulo 2^128
+      const uint64_t lo = (static_cast<uint64_t>(w1) << 32) | w0;
+      const uint64_t hi = (a3 << 32) | w2;
+      const uint64_t qm_lo = q * m_lo;
+      const uint64_t qm_hi = __umul64hi(q, m_lo) + q * m_hi;
+      const uint64_t x_lo = lo - qm_lo;
+      const uint64_t x_hi = hi - qm_hi - (lo < qm_lo ? 1 : 0);
+      __stcs(crow + col0 + c, round_i128_scaled(static_cast<int64_t>(x_hi), x_lo, base_scale + P->b_exp[col0 + c]));
+    }
+  }
+}
+
 // Standalone recombination (step API): levels [s][n][n] int32 -> C.
 __global__ void recombine_kernel(int n, int s, const int32_t* __restrict__ levels, const int* __restrict__ e,
                                  const int* __restrict__ f, double* __restrict__ C) {
@@ -670,20 +783,24 @@ __global__ void recombine_kernel(int n, int s, const int32_t* __restrict__ level
 
 int emu_smem_bytes(int bn) { return bn == 256 ? EmuCfg<256>::SMEM_BYTES : EmuCfg<128>::SMEM_BYTES; }
 
-template <int BN>
+template <int BN, bool kMod>
 static cudaError_t launch_bn(const CUtensorMap* mapA, const CUtensorMap* mapB, const EmuArgs& args, int grid,
                              cudaStream_t stream) {
-  cudaError_t e = cudaFuncSetAttribute(emu_gemm_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t e = cudaFuncSetAttribute(emu_gemm_kernel<BN, kMod>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        EmuCfg<BN>::SMEM_BYTES);
   if (e != cudaSuccess) return e;
-  emu_gemm_kernel<BN><<<grid, EM_THREADS, EmuCfg<BN>::SMEM_BYTES, stream>>>(*mapA, *mapB, args);
+  emu_gemm_kernel<BN, kMod><<<grid, EM_THREADS, EmuCfg<BN>::SMEM_BYTES, stream>>>(*mapA, *mapB, args);
   return cudaGetLastError();
 }
 
-cudaError_t emu_gemm_launch(int bn, const CUtensorMap* mapA, const CUtensorMap* mapB, const EmuArgs& args, int grid,
-                            cudaStream_t stream) {
+cudaError_t emu_gemm_launch(int bn, bool modular, const CUtensorMap* mapA, const CUtensorMap* mapB,
+                            const EmuArgs& args, int grid, cudaStream_t stream) {
   if (args.total_units <= 0) return cudaSuccess;
-  return bn == 256 ? launch_bn<256>(mapA, mapB, args, grid, stream) : launch_bn<128>(mapA, mapB, args, grid, stream);
+  if (modular)
+    return bn == 256 ? launch_bn<256, true>(mapA, mapB, args, grid, stream)
+                     : launch_bn<128, true>(mapA, mapB, args, grid, stream);
+  return bn == 256 ? launch_bn<256, false>(mapA, mapB, args, grid, stream)
+                   : launch_bn<128, false>(mapA, mapB, args, grid, stream);
 }
 
 cudaError_t slots_recombine_launch(int bn, const EmuArgs& args, int total_tiles, cudaStream_t stream) {
@@ -698,11 +815,44 @@ cudaError_t slots_recombine_launch(int bn, const EmuArgs& args, int total_tiles,
   return cudaGetLastError();
 }
 
+template <int K>
+static void launch_mod_recombine(int bn, const EmuArgs& args, unsigned blocks, cudaStream_t stream) {
+  if (bn == 256)
+    mod_recombine_kernel<K, 256><<<blocks, 256, 0, stream>>>(args);
+  else
+    mod_recombine_kernel<K, 128><<<blocks, 256, 0, stream>>>(args);
+}
+
+cudaError_t mod_recombine_launch(int bn, int k, const EmuArgs& args, int total_tiles, cudaStream_t stream) {
+  if (total_tiles <= 0) return cudaSuccess;
+  const long long threads = static_cast<long long>(total_tiles) * (EM_BM * bn / 16);
+  const unsigned blocks = static_cast<unsigned>((threads + 255) / 256);
+  switch (k) {
+    case 2: launch_mod_recombine<2>(bn, args, blocks, stream); break;
+    case 3: launch_mod_recombine<3>(bn, args, blocks, stream); break;
+    case 4: launch_mod_recombine<4>(bn, args, blocks, stream); break;
+    case 5: launch_mod_recombine<5>(bn, args, blocks, stream); break;
+    case 6: launch_mod_recombine<6>(bn, args, blocks, stream); break;
+    case 7: launch_mod_recombine<7>(bn, args, blocks, stream); break;
+    case 8: launch_mod_recombine<8>(bn, args, blocks, stream); break;
+    case 9: launch_mod_recombine<9>(bn, args, blocks, stream); break;
+    case 10: launch_mod_recombine<10>(bn, args, blocks, stream); break;
+    case 11: launch_mod_recombine<11>(bn, args, blocks, stream); break;
+    case 12: launch_mod_recombine<12>(bn, args, blocks, stream); break;
+    case 13: launch_mod_recombine<13>(bn, args, blocks, stream); break;
+    case 14: launch_mod_recombine<14>(bn, args, blocks, stream); break;
+    case 15: launch_mod_recombine<15>(bn, args, blocks, stream); break;
+    case 16: launch_mod_recombine<16>(bn, args, blocks, stream); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
 // Registers, threads and shared memory of the slice-product kernel, for error messages.
 void emu_kernel_info(int bn, char* buf, size_t len) {
   cudaFuncAttributes fa{};
-  const cudaError_t e = bn == 256 ? cudaFuncGetAttributes(&fa, emu_gemm_kernel<256>)
-                                  : cudaFuncGetAttributes(&fa, emu_gemm_kernel<128>);
+  const cudaError_t e = bn == 256 ? cudaFuncGetAttributes(&fa, emu_gemm_kernel<256, false>)
+                                  : cudaFuncGetAttributes(&fa, emu_gemm_kernel<128, false>);
   int dev = 0, optin = 0, regs_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);

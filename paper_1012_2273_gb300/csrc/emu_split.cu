@@ -8,6 +8,9 @@
 // This is the error-free splitting of Ozaki et al. (2012) in fixed-point
 // form; the paper itself has no such step (it computes in native FP64).
 //
+// Modular form (Problem::beta > 0): D = round-half-even(v 2^(beta-e)) and
+// plane j holds the symmetric residue of D modulo m_j (modular.cuh), j = 0..k-1.
+//
 // All arithmetic is integer arithmetic on the IEEE-754 bit patterns: GB300's
 // FP64 pipe is a small fraction of its integer and FP32 throughput, so no
 // FP64 instruction appears here.  Both kernels stream memory; they are bound
@@ -18,8 +21,11 @@
 // n_pad/64) * (k_pad/64)), first the A tiles (rows i, columns j), then the
 // B^T tiles (rows k, columns j).
 #include "launch.cuh"
+#include "modular.cuh"
 
 namespace mmk {
+
+static __constant__ ModTables c_mod = make_mod_tables();
 
 constexpr int SP_TILE = 64;
 constexpr int SP_THREADS = 256;
@@ -57,9 +63,10 @@ __device__ __forceinline__ int exponent_from_maxbits(uint64_t mb) {
   return E - 1022;
 }
 
-// D = round-half-even(v * 2^(8s-1-e)) computed on the bit pattern of v.
+// D = round-half-even(v * 2^(width-e)) computed on the bit pattern of v
+// (width = 8s - 1 for s digits, beta for the modular form).
 // Requires |v| < 2^e (true for every entry of a row/column scaled by its max).
-__device__ __forceinline__ int64_t fixed_point(uint64_t bits, int e, int s, bool* nonfinite) {
+__device__ __forceinline__ int64_t fixed_point(uint64_t bits, int e, int width, bool* nonfinite) {
   const bool neg = (bits >> 63) != 0;
   int E = static_cast<int>((bits >> 52) & 0x7FF);
   uint64_t m = bits & ((1ull << 52) - 1);
@@ -73,10 +80,10 @@ __device__ __forceinline__ int64_t fixed_point(uint64_t bits, int e, int s, bool
     m |= 1ull << 52;
   }
   if (m == 0) return 0;
-  const int sh = (E - 1075) - e + 8 * s - 1;
+  const int sh = (E - 1075) - e + width;
   uint64_t D;
   if (sh >= 0) {
-    D = m << sh;  // < 2^(8s-1) because |v| < 2^e
+    D = m << sh;  // < 2^width because |v| < 2^e
   } else {
     const int n = -sh;
     if (n >= 54) {
@@ -225,6 +232,54 @@ __device__ __forceinline__ void write_digit_planes(const long long (&Ds)[SP_TILE
   }
 }
 
+// Phase 2 for the modular form with K moduli: the symmetric residues of D
+// modulo m_0..m_{K-1}, one 16-byte vector (8 values) per plane.  |D| <= 2^55
+// is cut into four 14-bit limbs x_l carrying D's sign, and
+//     S = x_0 + x_1 c_1 + x_2 c_2 + x_3 c_3,  c_l = 2^(14 l) mod m (symmetric),
+// is congruent to D with |S| < 2^14 + 3 2^14 128 < 2^23, so every step is an
+// exact FP32 integer operation.  r = S - m rint(S RN(1/m)): the product's
+// relative error is at most 2^-24, below 1 / (2 |S|), so rint picks the
+// nearest multiple of m exactly as exact division would and |r| <= m/2 <= 128
+// -- an exact bf16 value.  rint is the add-and-subtract of 1.5 2^23.
+template <int K>
+__device__ __forceinline__ void write_residue_planes(const long long (&Ds)[SP_TILE][SP_TILE + 1], uint16_t* dst,
+                                                     int r0, int c0, int k_pad, size_t plane) {
+  for (int item = threadIdx.x; item < SP_TILE * (SP_TILE / 8); item += SP_THREADS) {
+    const int r = item >> 3, cg = item & 7;
+    float x[8][4];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const long long D = Ds[r][cg * 8 + q];
+      const uint64_t X = D < 0 ? 0ull - static_cast<uint64_t>(D) : static_cast<uint64_t>(D);
+      const float sg = D < 0 ? -1.0f : 1.0f;
+#pragma unroll
+      for (int l = 0; l < 4; ++l) {
+        const uint32_t limb = static_cast<uint32_t>(X >> (14 * l)) & 0x3FFFu;
+        x[q][l] = sg * (__uint_as_float(0x4B000000u | limb) - 8388608.0f);  // exact: limb < 2^23
+      }
+    }
+    uint16_t* out = dst + static_cast<size_t>(r0 + r) * k_pad + c0 + cg * 8;
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+      const float c1 = c_mod.split_c[j][0], c2 = c_mod.split_c[j][1], c3 = c_mod.split_c[j][2];
+      const float m = c_mod.m_f[j], inv = c_mod.inv_f[j];
+      float res[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const float S = fmaf(x[q][3], c3, fmaf(x[q][2], c2, fmaf(x[q][1], c1, x[q][0])));
+        const float qt = fmaf(S, inv, 12582912.0f) - 12582912.0f;
+        res[q] = fmaf(-qt, m, S);
+      }
+      uint4 v;
+      v.x = bf16x2_of_digits(res[0], res[1]);
+      v.y = bf16x2_of_digits(res[2], res[3]);
+      v.z = bf16x2_of_digits(res[4], res[5]);
+      v.w = bf16x2_of_digits(res[6], res[7]);
+      *reinterpret_cast<uint4*>(out + j * plane) = v;
+    }
+  }
+}
+
 // Writes the digit planes of one 64 x 64 tile (digit count from the problem).
 // Phase 1 reads the tile coalesced along the source rows and stores each
 // fixed-point value D in shared memory, transposed for B^T; phase 2 turns 8
@@ -237,6 +292,8 @@ __global__ void __launch_bounds__(SP_THREADS) split_kernel(const __grid_constant
   const int pi = split_find(args, blockIdx.x, &P);
   const int n = P->n;
   const int S = P->s;
+  const int beta = P->beta;
+  const int width = beta > 0 ? beta : 8 * S - 1;
   const int kt = P->k_pad / SP_TILE;
   const int a_tiles = (P->m_pad / SP_TILE) * kt;
   int local = blockIdx.x - (args.table ? P->split_begin : 0);
@@ -281,7 +338,7 @@ __global__ void __launch_bounds__(SP_THREADS) split_kernel(const __grid_constant
       const int j = is_a ? c0 + x : r0 + x;
       long long D = 0;
       if (i < n && j < n) {
-        D = fixed_point(bits[b], ex[b], S, &nonfinite);
+        D = fixed_point(bits[b], ex[b], width, &nonfinite);
         if (exps && (is_a ? j : i) == 0) exps[is_a ? i : j] = ex[b];
       }
       if (is_a) Ds[y][x] = D; else Ds[x][y] = D;
@@ -290,6 +347,19 @@ __global__ void __launch_bounds__(SP_THREADS) split_kernel(const __grid_constant
   if (nonfinite) any_nonfinite = 1;
   __syncthreads();
 
+  if (beta > 0) {
+    switch (S) {
+#define MM_RESIDUE_CASE(K) \
+  case K: write_residue_planes<K>(Ds, dst, r0, c0, P->k_pad, plane); break;
+      MM_RESIDUE_CASE(2) MM_RESIDUE_CASE(3) MM_RESIDUE_CASE(4) MM_RESIDUE_CASE(5) MM_RESIDUE_CASE(6)
+      MM_RESIDUE_CASE(7) MM_RESIDUE_CASE(8) MM_RESIDUE_CASE(9) MM_RESIDUE_CASE(10) MM_RESIDUE_CASE(11)
+      MM_RESIDUE_CASE(12) MM_RESIDUE_CASE(13) MM_RESIDUE_CASE(14) MM_RESIDUE_CASE(15)
+      default: write_residue_planes<16>(Ds, dst, r0, c0, P->k_pad, plane); break;
+#undef MM_RESIDUE_CASE
+    }
+    if (threadIdx.x == 0 && any_nonfinite) set_status(args.status, MM_ERR_NONFINITE);
+    return;
+  }
   switch (S) {
     case 1: write_digit_planes<1>(Ds, dst, r0, c0, P->k_pad, plane); break;
     case 2: write_digit_planes<2>(Ds, dst, r0, c0, P->k_pad, plane); break;

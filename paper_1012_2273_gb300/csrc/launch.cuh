@@ -60,6 +60,24 @@ __host__ __device__ inline int emu_tile_slots(int s, int G, int max_pairs) {
   return n;
 }
 
+// Modular form: the pairs of a tile are its k moduli (one residue product
+// each, each its own segment), numbered 0..k-1 and cut into G contiguous groups.
+__host__ __device__ inline void mod_group_range(int k, int G, int g, int* p0, int* p1) {
+  *p0 = g * k / G;
+  *p1 = (g + 1) * k / G;
+}
+
+template <bool kMod>
+__host__ __device__ inline void unit_group_range(int s, int G, int g, int* p0, int* p1) {
+  if (kMod)
+    mod_group_range(s, G, g, p0, p1);
+  else
+    emu_group_range(s, G, g, p0, p1);
+}
+
+// Products per tile: digit pairs, or moduli of the modular form.
+__host__ __device__ inline int problem_pairs(const Problem& p) { return p.beta > 0 ? p.s : emu_pairs(p.s); }
+
 // Tile order: bands of EMU_BAND tile-columns, row-major inside a band, so the
 // ~150 tiles in flight at once share few A row-panels and few B column-panels.
 constexpr int EMU_BAND = 8;
@@ -82,7 +100,7 @@ struct EmuArgs {
   int max_pairs;             // longest run of pairs whose products share an int32 sum
   int32_t* scratch;          // per-CTA slots [gridDim.x][scratch_slots][128][BN] (problems with groups == 1)
   int scratch_slots;
-  int32_t* tilebuf;          // per-tile slots (problems with groups > 1), see Problem::slot_base
+  int32_t* tilebuf;          // per-tile slots (problems with groups > 1, deferred or modular), see Problem::slot_base
   int* tile_counters;        // [global tile][8 epilogue regions]: units finished, zero at launch
   int* unit_counter;         // next unit to claim, zero at launch
   int32_t* levels_out;       // step API: level sums [s][n][n] instead of C (else nullptr)
@@ -107,10 +125,11 @@ cudaError_t split_launch(const Problem* table, const Problem* single, int count,
 
 // emu_gemm.cu
 int emu_smem_bytes(int bn);
-cudaError_t emu_gemm_launch(int bn, const CUtensorMap* mapA, const CUtensorMap* mapB, const EmuArgs& args, int grid,
-                            cudaStream_t stream);
+cudaError_t emu_gemm_launch(int bn, bool modular, const CUtensorMap* mapA, const CUtensorMap* mapB,
+                            const EmuArgs& args, int grid, cudaStream_t stream);
 void emu_kernel_info(int bn, char* buf, size_t len);
 cudaError_t slots_recombine_launch(int bn, const EmuArgs& args, int total_tiles, cudaStream_t stream);
+cudaError_t mod_recombine_launch(int bn, int k, const EmuArgs& args, int total_tiles, cudaStream_t stream);
 cudaError_t recombine_launch(int n, int s, const int32_t* levels, const int* e, const int* f, double* C,
                              cudaStream_t stream);
 

@@ -20,6 +20,7 @@
 #include <vector>
 
 #include "launch.cuh"
+#include "modular.cuh"
 
 using mmk::Problem;
 
@@ -64,8 +65,8 @@ bool make_plane_map(CUtensorMap* map, const void* base, int ld, long rows, int b
 }
 
 struct Plan {
-  int form;    // 0 native, 1 emulation
-  int slices;  // emulation digit count
+  int form;    // 0 native, 1 digit emulation, 2 modular emulation
+  int slices;  // digit count (form 1) or moduli (form 2)
   int bn;      // emulation tile width (128 or 256)
   int groups;  // digit-pair groups per tile (0 = chosen from the SM count)
 };
@@ -190,8 +191,9 @@ bool load_tune(mm_handle h, const std::string& path) {
     Plan p{0, 7, 256, 0};
     if (!(ss >> maxn >> p.form >> p.slices >> p.bn)) continue;
     if (!(ss >> p.groups)) p.groups = 0;
-    if ((p.form != 0 && p.form != 1) || p.slices < 1 || p.slices > 8 || (p.bn != 128 && p.bn != 256) ||
-        p.groups < 0 || p.groups > 36)
+    const int max_slices = p.form == 2 ? mmk::MOD_COUNT : 8;
+    if (p.form < 0 || p.form > 2 || p.slices < (p.form == 2 ? 2 : 1) || p.slices > max_slices ||
+        (p.bn != 128 && p.bn != 256) || p.groups < 0 || p.groups > 36)
       return false;
     rows.push_back({static_cast<int>(std::min<long>(maxn, 1 << 30)), p});
   }
@@ -209,12 +211,19 @@ Plan plan_for(mm_handle h, int n) {
       break;
     }
   if (h->cfg.mode == MM_NATIVE_FP64) p.form = 0;
-  if (h->cfg.mode == MM_EMU_BF16) {
-    p.form = 1;
+  if (h->cfg.mode == MM_EMU_BF16 || h->cfg.mode == MM_EMU_MODULAR) {
+    const int want = h->cfg.mode == MM_EMU_BF16 ? 1 : 2;
+    if (p.form != want) {
+      // a table row of another form: keep its tile width, take this form's
+      // default count
+      p.slices = want == 1 ? 7 : 16;
+      p.groups = 0;
+    }
+    p.form = want;
     if (p.bn != 128 && p.bn != 256) p.bn = 128;
   }
   if (h->cfg.slices > 0) p.slices = h->cfg.slices;
-  if (p.form == 1 && n < 256) p.bn = 128;
+  if (p.form != 0 && n < 256) p.bn = 128;
   return p;
 }
 
@@ -262,8 +271,9 @@ mm_status ensure_arena(mm_handle h, size_t bytes) {
 // products (see layout_group); larger ones in the slice-product epilogue.
 constexpr int kDeferBelowN = 3072;
 
-// One launch group of the emulation: problems sharing (s, bn).
+// One launch group of the emulation: problems sharing (form, bn, groups).
 struct EmuGroup {
+  int form = 1;         // 1 digit form, 2 modular form
   bool tabled = false;  // launched with a device problem/unit table (grouped calls)
   int groups = 0;       // forced pair groups per tile (0 = automatic)
   int bn = 256, grid = 1, max_pairs = 1;
@@ -284,8 +294,10 @@ struct EmuGroup {
 // segment slots through memory.  The constants are GB300 measurements: about
 // 0.35 us per 128 x 256 x 64 k-block of digit products in steady state, and
 // about 6 TB/s for streaming slot traffic.
-int choose_groups_single(int tiles, int s, int kb, int sms, int max_pairs) {
-  const int P = mmk::emu_pairs(s);
+// (The modular form writes its residue slots whatever G is, so they cost
+// nothing extra there.)
+int choose_groups_single(int tiles, int s, bool modular, int kb, int sms, int max_pairs) {
+  const int P = modular ? s : mmk::emu_pairs(s);
   const double t_kb = 0.35e-6, bw = 6.0e12, slot_bytes = 128.0 * 256.0 * 4.0;
   int best = 1;
   double best_t = 1e30;
@@ -294,7 +306,7 @@ int choose_groups_single(int tiles, int s, int kb, int sms, int max_pairs) {
     const long long waves = (units + sms - 1) / sms;
     const int longest = (P + G - 1) / G;
     double t = static_cast<double>(waves) * longest * kb * t_kb;
-    if (G > 1) t += 2.0 * tiles * mmk::emu_tile_slots(s, G, max_pairs) * slot_bytes / bw;
+    if (G > 1 && !modular) t += 2.0 * tiles * mmk::emu_tile_slots(s, G, max_pairs) * slot_bytes / bw;
     if (t < best_t * 0.98) {  // a new group count must win by 2%
       best_t = t;
       best = G;
@@ -325,7 +337,8 @@ mm_status layout_group(mm_handle h, EmuGroup& g, char* base) {
     g.total_tiles += p.tiles_m * p.tiles_n;
     p.split_begin = g.total_split;
     g.total_split += mmk::split_tiles(p);
-    work += static_cast<long long>(p.tiles_m) * p.tiles_n * mmk::emu_pairs(p.s) * (p.k_pad / 64);
+    p.beta = g.form == 2 ? mmk::mod_beta(p.s, n) : 0;
+    work += static_cast<long long>(p.tiles_m) * p.tiles_n * mmk::problem_pairs(p) * (p.k_pad / 64);
     const size_t a_sl = ar.take(static_cast<size_t>(p.s) * p.m_pad * p.k_pad * 2);
     const size_t b_sl = ar.take(static_cast<size_t>(p.s) * p.n_pad * p.k_pad * 2);
     const size_t ae = ar.take(sizeof(int) * n);
@@ -349,19 +362,38 @@ mm_status layout_group(mm_handle h, EmuGroup& g, char* base) {
   g.tilebuf_elems = 0;
   g.scratch_slots = 1;
   const long long slot = 128LL * g.bn;
+  const bool modular = g.form == 2;
   for (size_t i = 0; i < g.ps.size(); ++i) {
     Problem& p = g.ps[i];
     const int tiles = p.tiles_m * p.tiles_n;
     const int kb = p.k_pad / 64;
-    const int P = mmk::emu_pairs(p.s);
+    const int P = mmk::problem_pairs(p);
     int G;
     if (g.groups > 0) {
       G = std::min(g.groups, P);
     } else if (g.ps.size() == 1) {
-      G = choose_groups_single(tiles, p.s, kb, h->num_sms, g.max_pairs);
+      G = choose_groups_single(tiles, p.s, modular, kb, h->num_sms, g.max_pairs);
     } else {
       G = static_cast<int>(std::lround(P * kb / std::max(target, 1.0)));
       G = std::max(1, std::min(G, P));
+    }
+    if (modular) {
+      // One byte per output and modulus: k slots of 128 x bn bytes per tile,
+      // always recombined by the separate pass.
+      p.groups = G;
+      p.nslots = p.s;
+      p.defer = 1;
+      p.slot_base = g.tilebuf_elems;
+      g.tilebuf_elems += static_cast<long long>(tiles) * p.nslots * (slot / 4);
+      if (g.tabled) {
+        for (int gi = 0; gi < G; ++gi) {
+          int p0, p1;
+          mmk::mod_group_range(p.s, G, gi, &p0, &p1);
+          const int cost = (p1 - p0) * kb;
+          for (int t = 0; t < tiles; ++t) g.units.push_back(make_int4(static_cast<int>(i), t, gi, cost));
+        }
+      }
+      continue;
     }
     // A tile's segment slots are listed per problem (at most 64).
     while (G > 1 && mmk::emu_tile_slots(p.s, G, g.max_pairs) > 64) --G;
@@ -466,12 +498,22 @@ mm_status run_group(mm_handle h, const EmuGroup& g, const Problem* d_table, cons
   a.status = h->d_status;
   a.timeout_ns = h->timeout_ns;
   const long m_gemm = prof_start(h, stream, KIND_SLICE_GEMM);
-  const cudaError_t le = mmk::emu_gemm_launch(g.bn, &g.maps[0], &g.maps[1], a, g.grid, stream);
+  const cudaError_t le = mmk::emu_gemm_launch(g.bn, g.form == 2, &g.maps[0], &g.maps[1], a, g.grid, stream);
   prof_end(h, stream, m_gemm);
   if (le != cudaSuccess) {
     char info[512];
     mmk::emu_kernel_info(g.bn, info, sizeof(info));
     return fail(h, MM_ERR_CUDA, std::string("slice-product launch: ") + cudaGetErrorString(le) + " " + info);
+  }
+  if (g.form == 2) {
+    // one recombination launch per moduli count present in the group
+    bool seen[mmk::MOD_COUNT + 1] = {};
+    for (const Problem& p : g.ps) seen[p.s] = true;
+    const long m_rec = prof_start(h, stream, KIND_RECOMBINE);
+    for (int k = 2; k <= mmk::MOD_COUNT; ++k)
+      if (seen[k]) MM_CUDA(h, mmk::mod_recombine_launch(g.bn, k, a, g.total_tiles, stream));
+    prof_end(h, stream, m_rec);
+    return MM_OK;
   }
   bool any_deferred = false;
   for (const Problem& p : g.ps) any_deferred |= p.defer != 0;
@@ -483,17 +525,25 @@ mm_status run_group(mm_handle h, const EmuGroup& g, const Problem* d_table, cons
   return MM_OK;
 }
 
-mm_status check_emu_size(mm_handle h, int n, int s) {
+mm_status check_emu_size(mm_handle h, int n, int s, int form) {
+  if (form == 2) {
+    if (s < 2 || s > mmk::MOD_COUNT) return fail(h, MM_ERR_UNSUPPORTED, "the modular form takes 2..16 moduli");
+    if (n > 65535) return fail(h, MM_ERR_UNSUPPORTED, "the modular form supports N <= 65535");
+    if (mmk::mod_beta(s, n) < 1)
+      return fail(h, MM_ERR_UNSUPPORTED, "too few moduli for this N (the fixed-point width would be 0)");
+    return MM_OK;
+  }
   if (s < 1 || s > 8) return fail(h, MM_ERR_UNSUPPORTED, "slices must be in 1..8");
   if (n > 131071) return fail(h, MM_ERR_UNSUPPORTED, "emulation supports N <= 131071 (one pair per int32 sum)");
   return MM_OK;
 }
 
 // Single emulated problem: workspace, maps, launches (no device table).
-mm_status emu_single(mm_handle h, const Problem& p, int s, int bn, int groups, cudaStream_t stream) {
-  mm_status st = check_emu_size(h, p.n, s);
+mm_status emu_single(mm_handle h, const Problem& p, int form, int s, int bn, int groups, cudaStream_t stream) {
+  mm_status st = check_emu_size(h, p.n, s, form);
   if (st != MM_OK) return st;
   EmuGroup g;
+  g.form = form;
   g.bn = bn;
   g.groups = groups;
   g.ps.push_back(p);
@@ -541,11 +591,13 @@ mm_status mm_create(mm_handle* out, const mm_config* cfg) {
     if (cfg->tune_path) h->tune_path = cfg->tune_path;
     h->cfg.tune_path = nullptr;
   }
-  if (h->cfg.mode != MM_NATIVE_FP64 && h->cfg.mode != MM_EMU_BF16 && h->cfg.mode != MM_AUTO) {
+  if (h->cfg.mode != MM_NATIVE_FP64 && h->cfg.mode != MM_EMU_BF16 && h->cfg.mode != MM_AUTO &&
+      h->cfg.mode != MM_EMU_MODULAR) {
     delete h;
     return MM_ERR_INVALID;
   }
-  if (h->cfg.slices < 0 || h->cfg.slices > 8) {
+  if (h->cfg.slices < 0 || h->cfg.slices > (h->cfg.mode == MM_EMU_MODULAR ? mmk::MOD_COUNT : 8) ||
+      (h->cfg.mode == MM_EMU_MODULAR && h->cfg.slices == 1)) {
     delete h;
     return MM_ERR_UNSUPPORTED;
   }
@@ -634,6 +686,14 @@ mm_status mm_probe_fp64_peak(mm_handle h, double* dmma_tflops, double* dfma_tflo
 
 const char* mm_last_error(mm_handle h) { return h ? h->last_error.c_str() : "invalid handle"; }
 
+mm_status mm_modular_params(int k, int N, int* beta, int* moduli) {
+  if (k < 1 || k > mmk::MOD_COUNT || N < 1 || !beta) return MM_ERR_INVALID;
+  *beta = mmk::mod_beta(k, N);
+  if (moduli)
+    for (int j = 0; j < k; ++j) moduli[j] = static_cast<int>(mmk::mod_value(j));
+  return MM_OK;
+}
+
 mm_status mm_plan(mm_handle h, int N, int* form, int* slices) {
   if (!h || N < 0) return MM_ERR_INVALID;
   const Plan p = plan_for(h, N);
@@ -678,7 +738,7 @@ mm_status mm_gemm(mm_handle h, int N, const double* A, const double* B, double* 
   const Plan plan = plan_for(h, N);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (plan.form == 0) return native_single(h, p, s);
-  return emu_single(h, p, plan.slices, plan.bn, plan.groups, s);
+  return emu_single(h, p, plan.form, plan.slices, plan.bn, plan.groups, s);
 }
 
 mm_status mm_gemm_host(mm_handle h, int N, const double* A_host, const double* B_host, double* C_host,
@@ -752,7 +812,7 @@ mm_status mm_gemm_grouped(mm_handle h, int count, const int* Ns, const double* c
 
   // Partition: native problems, and emulated problems by (slices, bn).
   std::vector<Problem> nat;
-  std::map<std::tuple<int, int>, std::vector<Problem>> emu;
+  std::map<std::tuple<int, int, int>, std::vector<Problem>> emu;  // (form, bn, groups)
   std::vector<std::pair<Problem, Plan>> emu_plans;
   for (int i = 0; i < count; ++i) {
     if (Ns[i] == 0) continue;
@@ -765,7 +825,7 @@ mm_status mm_gemm_grouped(mm_handle h, int count, const int* Ns, const double* c
     if (pl.form == 0) {
       nat.push_back(p);
     } else {
-      mm_status st = check_emu_size(h, p.n, pl.slices);
+      mm_status st = check_emu_size(h, p.n, pl.slices, pl.form);
       if (st != MM_OK) return st;
       p.s = pl.slices;
       emu_plans.push_back({p, pl});
@@ -779,7 +839,7 @@ mm_status mm_gemm_grouped(mm_handle h, int count, const int* Ns, const double* c
     for (size_t i = 1; i < emu_plans.size(); ++i)
       if (emu_plans[i].first.n > emu_plans[big].first.n) big = i;
     const int bn = emu_plans[big].second.bn;
-    for (auto& ep : emu_plans) emu[{bn, ep.second.groups}].push_back(ep.first);
+    for (auto& ep : emu_plans) emu[{ep.second.form, bn, ep.second.groups}].push_back(ep.first);
   }
   // Native problems: 64 x 64 tiles, or 16 x 16 tiles below 512 (two launches).
   std::vector<Problem> nat_small;
@@ -826,8 +886,9 @@ mm_status mm_gemm_grouped(mm_handle h, int count, const int* Ns, const double* c
       auto make = [&](size_t end) {
         EmuGroup t;
         t.tabled = true;
-        t.bn = std::get<0>(kv.first);
-        t.groups = std::get<1>(kv.first);
+        t.form = std::get<0>(kv.first);
+        t.bn = std::get<1>(kv.first);
+        t.groups = std::get<2>(kv.first);
         t.ps.assign(rest.begin() + at, rest.begin() + end);
         return t;
       };
@@ -1055,7 +1116,7 @@ mm_status mm_level_sums(mm_handle h, int N, int slices, const uint16_t* a_digits
   a.levels_out = levels;
   a.status = h->d_status;
   a.timeout_ns = h->timeout_ns;
-  const cudaError_t le = mmk::emu_gemm_launch(bn, &maps[0], &maps[1], a, emu_grid(h, a.total_units),
+  const cudaError_t le = mmk::emu_gemm_launch(bn, false, &maps[0], &maps[1], a, emu_grid(h, a.total_units),
                                               static_cast<cudaStream_t>(stream));
   if (le != cudaSuccess) {
     char info[512];

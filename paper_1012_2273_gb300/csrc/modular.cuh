@@ -1,0 +1,187 @@
+// modular.cuh -- constants of the modular emulation form.
+//
+// The modular form rounds A row by row and B column by column to beta-bit
+// fixed-point integers (|A_int|, |B_int| <= 2^beta), multiplies their
+// residues modulo k pairwise coprime moduli m_1..m_k <= 256 on the bf16
+// tensor cores, and recovers the exact integer product
+//     X(i,k) = sum_j A_int(i,j) B_int(j,k)
+// from its k residues by the Chinese remainder theorem, then rounds X once to
+// FP64.  It is the integer-modular scheme of Ozaki, Uchino and Imamura
+// ("Ozaki scheme II", 2025) with bf16 operands: a symmetric residue of a
+// modulus <= 256 has |r| <= 128, an exact bf16 value, and the product of two
+// is at most 2^14, so the chunked FP32 accumulation of the digit form stays
+// exact.  The paper itself computes in native FP64 and has no such step.
+//
+// Everything here is derived at compile time from the list of moduli.
+#pragma once
+
+#include <cstdint>
+
+namespace mmk {
+
+constexpr int MOD_COUNT = 16;     // moduli available; k = 2..16 are used
+constexpr int MOD_MAX_BITS = 55;  // fixed-point width limit: |A_int| <= 2^55 splits into 4 limbs of 14 bits
+
+// The moduli, largest first: pairwise coprime, each at most 256.
+__host__ __device__ constexpr uint32_t mod_value(int j) {
+  return j == 0 ? 256u : j == 1 ? 255u : j == 2 ? 253u : j == 3 ? 251u : j == 4 ? 247u : j == 5 ? 241u
+       : j == 6 ? 239u : j == 7 ? 233u : j == 8 ? 229u : j == 9 ? 227u : j == 10 ? 223u : j == 11 ? 217u
+       : j == 12 ? 211u : j == 13 ? 199u : j == 14 ? 197u : 193u;
+}
+
+// 128-bit unsigned integer as four 32-bit limbs, least significant first.
+struct Limbs4 {
+  uint32_t w[4];
+};
+
+__host__ __device__ constexpr Limbs4 limbs_mul_small(Limbs4 a, uint32_t m) {
+  Limbs4 r{};
+  uint64_t carry = 0;
+  for (int l = 0; l < 4; ++l) {
+    const uint64_t t = static_cast<uint64_t>(a.w[l]) * m + carry;
+    r.w[l] = static_cast<uint32_t>(t);
+    carry = t >> 32;
+  }
+  return r;
+}
+
+__host__ __device__ constexpr Limbs4 limbs_div_small(Limbs4 a, uint32_t m) {
+  Limbs4 r{};
+  uint64_t rem = 0;
+  for (int l = 3; l >= 0; --l) {
+    const uint64_t cur = (rem << 32) | a.w[l];
+    r.w[l] = static_cast<uint32_t>(cur / m);
+    rem = cur % m;
+  }
+  return r;
+}
+
+__host__ __device__ constexpr uint32_t limbs_mod_small(Limbs4 a, uint32_t m) {
+  uint64_t rem = 0;
+  for (int l = 3; l >= 0; --l) rem = ((rem << 32) | a.w[l]) % m;
+  return static_cast<uint32_t>(rem);
+}
+
+// Product of the first k moduli.
+__host__ __device__ constexpr Limbs4 mod_product(int k) {
+  Limbs4 M{{1u, 0u, 0u, 0u}};
+  for (int j = 0; j < k; ++j) M = limbs_mul_small(M, mod_value(j));
+  return M;
+}
+
+// Inverse of a modulo m (gcd(a, m) = 1), by the extended Euclidean algorithm.
+__host__ __device__ constexpr uint32_t inv_mod(uint32_t a, uint32_t m) {
+  int64_t r0 = m, r1 = a % m, s0 = 0, s1 = 1;
+  while (r1 != 0) {
+    const int64_t q = r0 / r1;
+    const int64_t r2 = r0 - q * r1, s2 = s0 - q * s1;
+    r0 = r1;
+    r1 = r2;
+    s0 = s1;
+    s1 = s2;
+  }
+  return static_cast<uint32_t>(((s0 % static_cast<int64_t>(m)) + m) % m);
+}
+
+__host__ __device__ constexpr int limbs_bit_length(Limbs4 a) {
+  for (int l = 3; l >= 0; --l)
+    if (a.w[l]) {
+      int b = 0;
+      for (uint32_t v = a.w[l]; v; v >>= 1) ++b;
+      return 32 * l + b;
+    }
+  return 0;
+}
+
+__host__ __device__ constexpr float pow2f(int e) {
+  float r = 1.0f;
+  for (; e > 0; --e) r *= 2.0f;
+  for (; e < 0; ++e) r *= 0.5f;
+  return r;
+}
+
+struct ModTables {
+  // split: the symmetric residue of 2^(14 l) modulo m_j (l = 1..3), m_j and
+  // RN(1/m_j) as floats
+  float split_c[MOD_COUNT][3];
+  uint32_t m_u[MOD_COUNT];
+  float m_f[MOD_COUNT];
+  float inv_f[MOD_COUNT];
+  // slice-product epilogue: ceil(2^39 / m_j) (so that floor(x / m_j) =
+  // umulhi(x, magic) >> 7 for 0 <= x < 2^31 + 2^8), a multiple of m_j at least
+  // 2^30 (added to make a sum of at most 2^30 in magnitude non-negative),
+  // and, per k, y = (M_k / m_j)^-1 mod m_j
+  uint32_t magic[MOD_COUNT];
+  uint32_t bias[MOD_COUNT];
+  uint32_t y[MOD_COUNT + 1][MOD_COUNT];
+  // recombination, per k: limbs of M_k / m_j and of M_k; V 2^-qshift is
+  // formed in FP32 and multiplied by qscale = 2^qshift / M_k to estimate
+  // round(V / M_k)
+  uint32_t mj[MOD_COUNT + 1][MOD_COUNT][4];
+  uint32_t mk[MOD_COUNT + 1][4];
+  int qshift[MOD_COUNT + 1];
+  float qscale[MOD_COUNT + 1];
+};
+
+__host__ __device__ constexpr ModTables make_mod_tables() {
+  ModTables t{};
+  for (int j = 0; j < MOD_COUNT; ++j) {
+    const uint32_t m = mod_value(j);
+    for (int l = 1; l <= 3; ++l) {
+      uint64_t p = 1;
+      for (int b = 0; b < 14 * l; ++b) p = (p * 2) % m;
+      const int64_t sym = (p > m / 2) ? static_cast<int64_t>(p) - m : static_cast<int64_t>(p);
+      t.split_c[j][l - 1] = static_cast<float>(sym);
+    }
+    t.m_u[j] = m;
+    t.m_f[j] = static_cast<float>(m);
+    t.inv_f[j] = 1.0f / static_cast<float>(m);
+    t.magic[j] = static_cast<uint32_t>(((1ull << 39) + m - 1) / m);
+    t.bias[j] = static_cast<uint32_t>(((1ull << 30) + m - 1) / m * m);
+  }
+  for (int k = 1; k <= MOD_COUNT; ++k) {
+    const Limbs4 M = mod_product(k);
+    for (int l = 0; l < 4; ++l) t.mk[k][l] = M.w[l];
+    for (int j = 0; j < k; ++j) {
+      const uint32_t m = mod_value(j);
+      const Limbs4 Mj = limbs_div_small(M, m);
+      for (int l = 0; l < 4; ++l) t.mj[k][j][l] = Mj.w[l];
+      t.y[k][j] = inv_mod(limbs_mod_small(Mj, m), m);
+    }
+    const int bits = limbs_bit_length(M);
+    t.qshift[k] = bits - 31;
+    double Md = 0.0;
+    for (int l = 3; l >= 0; --l) Md = Md * 4294967296.0 + static_cast<double>(M.w[l]);
+    double sc = 1.0;
+    for (int e = t.qshift[k]; e > 0; --e) sc *= 2.0;
+    for (int e = t.qshift[k]; e < 0; ++e) sc *= 0.5;
+    t.qscale[k] = static_cast<float>(sc / Md);
+  }
+  return t;
+}
+
+// Largest fixed-point width beta <= MOD_MAX_BITS with 4 n 2^(2 beta) <= M_k,
+// so that the exact product (|X| <= n 2^(2 beta)) lies within a quarter of
+// the modulus of zero; 0 if k moduli are too few for size n.
+inline int mod_beta(int k, int n) {
+  if (k < 1 || k > MOD_COUNT || n < 1) return 0;
+  const Limbs4 M = mod_product(k);
+  for (int beta = MOD_MAX_BITS; beta >= 1; --beta) {
+    // floor(M / 2^(2 beta)) >= 4 n  <=>  4 n 2^(2 beta) <= M
+    const int sh = 2 * beta;
+    uint64_t q_lo = 0, q_hi = 0;  // M >> sh as 128 bits
+    const uint64_t lo = (static_cast<uint64_t>(M.w[1]) << 32) | M.w[0];
+    const uint64_t hi = (static_cast<uint64_t>(M.w[3]) << 32) | M.w[2];
+    if (sh >= 64) {
+      q_lo = hi >> (sh - 64);
+      q_hi = 0;
+    } else {
+      q_lo = (lo >> sh) | (sh ? (hi << (64 - sh)) : 0);
+      q_hi = hi >> sh;
+    }
+    if (q_hi != 0 || q_lo >= 4ull * static_cast<uint64_t>(n)) return beta;
+  }
+  return 0;
+}
+
+}  // namespace mmk

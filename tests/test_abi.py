@@ -83,3 +83,22 @@ def test_tune_file_is_validated_before_any_device_work(tmp_path):
     assert L.mm_create(ctypes.byref(h), ctypes.byref(cfg)) == 1
     missing = mm._Config(mm.AUTO, 0, 0, str(tmp_path / "none.txt").encode())
     assert L.mm_create(ctypes.byref(h), ctypes.byref(missing)) == 1
+    bad.write_text("1000 2 17 256\n")  # modular form: at most 16 moduli
+    assert L.mm_create(ctypes.byref(h), ctypes.byref(cfg)) == 1
+    bad.write_text("1000 2 1 256\n")  # and at least 2
+    assert L.mm_create(ctypes.byref(h), ctypes.byref(cfg)) == 1
+
+
+def test_modular_width_rule_matches_the_oracle_statement():
+    # Host-side planning of the modular form (no GPU): the fixed-point width
+    # and the moduli agree with the oracle's own, independent statement.
+    import oracle
+    for k in range(1, 17):
+        for n in (1, 2, 10, 100, 255, 256, 500, 1000, 2000, 4095, 4096, 8192, 16384, 32767, 65535):
+            beta, mods = mm.modular_params(k, n)
+            assert beta == oracle.modular_beta(k, n), (k, n)
+            assert mods == oracle.MODULI[:k]
+    with pytest.raises(mm.MMError):
+        mm.modular_params(17, 100)
+    with pytest.raises(mm.MMError):
+        mm.modular_params(4, 0)
