@@ -275,8 +275,9 @@ def run_ours(args, dist: Dist):
                 kinds[k].append(p[k][0])
             launches_per_step = sum(v[1] for v in p.values())
     hp.check()
-    emu_sizes = [n for n in SWEEP if plan[n][0] == 1]
-    pairs_of = {n: plan[n][1] * (plan[n][1] + 1) // 2 for n in emu_sizes}
+    emu_sizes = [n for n in SWEEP if plan[n][0] != 0]
+    # tensor products per size: s(s+1)/2 digit pairs, or k residue products
+    pairs_of = {n: plan[n][1] * (plan[n][1] + 1) // 2 if plan[n][0] == 1 else plan[n][1] for n in emu_sizes}
     tensor_flops = sum(pairs_of[n] * 2 * n ** 3 for n in emu_sizes)
     gemm_ms = statistics.mean(kinds["slice_products"]) if emu_sizes else None
     digest = source_digest()
@@ -285,15 +286,18 @@ def run_ours(args, dist: Dist):
     if gemm_ms:
         achieved = tensor_flops / (gemm_ms / 1e3) / 1e12
         peak = peaks["bf16_tflops"]
-        roofline = {"kernel": "emu_gemm_kernel (tcgen05 bf16 digit products, fused exact recombination)",
+        roofline = {"kernel": "emu_gemm_kernel (tcgen05 bf16 digit or residue products with exact int32 "
+                              "accumulation; every instantiation the step launches)",
                     "bound": "tensor", "achieved": round(achieved, 2), "peak": peak, "unit": "TFLOP/s",
                     "frac": round(achieved / peak, 4),
                     "peak_source": f"{peaks['source']} bf16 dense burst (MEASURED_PEAKS.json bf16_tflops)",
                     "traffic": traffic,
                     "algorithmic_flops_per_launch": tensor_flops,
                     "avg_launch_ms": round(gemm_ms, 4),
-                    "note": "digit-pair products of 2N^3 flops each: " + ", ".join(
-                        f"N={n}: s={plan[n][1]}, {pairs_of[n]} pairs" for n in emu_sizes)}
+                    "note": "bf16 products of 2N^3 flops each: " + ", ".join(
+                        f"N={n}: " + (f"digits s={plan[n][1]}, {pairs_of[n]} pairs" if plan[n][0] == 1
+                                      else f"moduli k={plan[n][1]}, {pairs_of[n]} residue products")
+                        for n in emu_sizes)}
 
     # per-N comparison of the two forms (single calls, L2 flushed)
     per_n = per_size(mm, As, Bs, Cs, flush, stream)
@@ -319,7 +323,9 @@ def run_ours(args, dist: Dist):
         "data": "synthetic: uniform [0,1) FP64 from SplitMix64 seed 0 (stand-in for the paper's RAND())",
         "config": {"workload": "paper size sweep: one square FP64 product at each N in "
                                f"{list(SWEEP)}, one grouped library call per step (plan: "
-                               + ", ".join(f"N={n}:{'native' if plan[n][0] == 0 else f'emulated s={plan[n][1]}'}"
+                               + ", ".join(f"N={n}:" + ("native" if plan[n][0] == 0 else
+                                                         f"digits s={plan[n][1]}" if plan[n][0] == 1 else
+                                                         f"modular k={plan[n][1]}")
                                            for n in SWEEP) + ")",
                    "flops_per_step": flops_step, "flop_count": "N^2 (2N - 1) per product (paper, Sec. 3.1)",
                    "l2": f"flushed before every timed step ({L2_FLUSH_BYTES >> 20} MiB write)",
@@ -359,10 +365,15 @@ def per_size(mm, As, Bs, Cs, flush, stream, reps: int = 5) -> dict:
     out = {}
     hn = mm.Handle("native")
     he = mm.Handle("emulated")
+    hm = mm.Handle("modular")
+    ha = mm.Handle("auto")
     for A, B, C in zip(As, Bs, Cs):
         n = A.shape[0]
         row = {}
-        for name, hh in (("native", hn), ("emulated", he)):
+        forms = [("native", hn), ("emulated", he), ("auto", ha)]
+        if n >= 256:
+            forms.insert(2, ("modular", hm))
+        for name, hh in forms:
             hh.gemm(A, B, C)  # warm
             ts = []
             for r in range(reps):
@@ -377,12 +388,15 @@ def per_size(mm, As, Bs, Cs, flush, stream, reps: int = 5) -> dict:
             row[f"{name}_ms"] = round(ms, 4)
             row[f"{name}_tflops"] = round(workload.flops(n) / (ms / 1e3) / 1e12, 4)
         row["emulated_slices"] = he.plan(n)[1]
-        row["speedup_emulated_over_native"] = round(row["native_ms"] / row["emulated_ms"], 2)
+        if n >= 256:
+            row["modular_moduli"] = hm.plan(n)[1]
+        form, k = ha.plan(n)
+        row["auto_plan"] = ("native", f"digits s={k}", f"modular k={k}")[form]
+        row["speedup_auto_over_native"] = round(row["native_ms"] / row["auto_ms"], 2)
         out[str(n)] = row
-    hn.check()
-    he.check()
-    hn.close()
-    he.close()
+    for hh in (hn, he, hm, ha):
+        hh.check()
+        hh.close()
     return out
 
 

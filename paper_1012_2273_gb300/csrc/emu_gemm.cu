@@ -696,18 +696,20 @@ __global__ void __launch_bounds__(256) slots_recombine_kernel(const __grid_const
 }
 
 // Recombination of the modular form with K moduli, after the slice-product
-// kernel: one thread per 16 consecutive outputs of a tile row (one 16-byte
-// vector per modulus).  With t_j = (X mod m_j) (M/m_j)^-1 mod m_j from the
-// epilogue, V = sum_j t_j (M/m_j) is congruent to X modulo M = m_1...m_K and
+// kernel: one thread per 4 consecutive outputs of a tile row (one 4-byte word
+// per modulus; 4 lanes read a row's 16 contiguous bytes, a warp 8 rows).
+// With t_j = (X mod m_j) (M/m_j)^-1 mod m_j from the epilogue,
+// V = sum_j t_j (M/m_j) is congruent to X modulo M = m_1...m_K and
 // V / M = sum_j t_j / m_j < K.  Because |X| <= M/4 (the width rule),
 // X = V - round(V/M) M, and round(V/M) is found from a 24-bit estimate of V:
 // its relative error is a few 2^-24, far inside the quarter-modulus margin.
 // V is summed in four 64-bit accumulators of 32-bit limbs (each term below
 // 2^40, K of them), carried, and X is formed modulo 2^128, exact since
-// |X| < 2^126.  Then one rounding: c = RN(X) 2^(e_i + f_k - 2 beta).
+// |X| < 2^126.  Then one rounding: c = RN(X) 2^(e_i + f_k - 2 beta).  The
+// four outputs' multiply-add chains are interleaved.
 template <int K, int BN>
 __global__ void __launch_bounds__(256) mod_recombine_kernel(const __grid_constant__ EmuArgs args) {
-  constexpr int PER_TILE = EM_BM * BN / 16;  // threads per tile
+  constexpr int PER_TILE = EM_BM * BN / 4;  // threads per tile
   constexpr size_t SLOT_BYTES = static_cast<size_t>(EM_BM) * BN;
   constexpr int QS = limbs_bit_length(mod_product(K)) - 31;  // V 2^-QS < 2^35
   const long long item = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
@@ -716,47 +718,50 @@ __global__ void __launch_bounds__(256) mod_recombine_kernel(const __grid_constan
   const Problem* P = args.table ? &args.table[find_problem(args.table, args.count, tile)] : &args.single;
   const int tile_local = tile - P->tile_begin;
   if (P->beta <= 0 || P->s != K || tile_local < 0 || tile_local >= P->tiles_m * P->tiles_n) return;
-  const int r = in_tile % EM_BM, c16 = in_tile / EM_BM;
+  // in_tile = ((c16 * 16 + rblock) * 8 + r8) * 4 + q: 16-column group c16,
+  // row r = 8 rblock + r8, word q of the row's 16 bytes
+  const int q = in_tile & 3, r = (in_tile >> 2) & (EM_BM - 1), c16 = in_tile >> 9;
   int tm, tn;
   emu_tile_coords(tile_local, P->tiles_m, P->tiles_n, &tm, &tn);
-  const int n = P->n, row = tm * EM_BM + r, col0 = tn * BN + 16 * c16;
+  const int n = P->n, row = tm * EM_BM + r, col0 = tn * BN + 16 * c16 + 4 * q;
   if (row >= n || col0 >= n) return;
   const uint8_t* at = reinterpret_cast<const uint8_t*>(args.tilebuf + P->slot_base) +
                       static_cast<size_t>(tile_local) * K * SLOT_BYTES + static_cast<size_t>(c16) * (EM_BM * 16) +
-                      r * 16;
-  uint4 v[K];
+                      r * 16 + q * 4;
+  uint32_t w[K];
 #pragma unroll
-  for (int j = 0; j < K; ++j) v[j] = __ldcs(reinterpret_cast<const uint4*>(at + j * SLOT_BYTES));
-  const int base_scale = P->a_exp[row] - 2 * P->beta;
+  for (int j = 0; j < K; ++j) w[j] = __ldcs(reinterpret_cast<const unsigned int*>(at + j * SLOT_BYTES));
+  uint64_t a[4][4] = {};
+#pragma unroll
+  for (int j = 0; j < K; ++j) {
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const uint32_t t = __byte_perm(w[j], 0u, 0x4440u + c);
+#pragma unroll
+      for (int l = 0; l < 4; ++l) a[c][l] += static_cast<uint64_t>(t) * c_mod.mj[K][j][l];
+    }
+  }
   const uint64_t m_lo = (static_cast<uint64_t>(c_mod.mk[K][1]) << 32) | c_mod.mk[K][0];
   const uint64_t m_hi = (static_cast<uint64_t>(c_mod.mk[K][3]) << 32) | c_mod.mk[K][2];
+  const int base_scale = P->a_exp[row] - 2 * P->beta;
   double* crow = P->C + static_cast<size_t>(row) * n;
 #pragma unroll
-  for (int c = 0; c < 16; ++c) {
+  for (int c = 0; c < 4; ++c) {
     if (col0 + c < n) {
-      uint64_t a0 = 0, a1 = 0, a2 = 0, a3 = 0;
-#pragma unroll
-      for (int j = 0; j < K; ++j) {
-        const uint32_t word = (c < 4) ? v[j].x : (c < 8) ? v[j].y : (c < 12) ? v[j].z : v[j].w;
-        const uint32_t t = (word >> (8 * (c & 3))) & 255u;
-        a0 += static_cast<uint64_t>(t) * c_mod.mj[K][j][0];
-        a1 += static_cast<uint64_t>(t) * c_mod.mj[K][j][1];
-        a2 += static_cast<uint64_t>(t) * c_mod.mj[K][j][2];
-        a3 += static_cast<uint64_t>(t) * c_mod.mj[K][j][3];
-      }
-      a1 += a0 >> 32;
-      a2 += a1 >> 32;
-      a3 += a2 >> 32;
-      const uint32_t w0 = static_cast<uint32_t>(a0), w1 = static_cast<uint32_t>(a1), w2 = static_cast<uint32_t>(a2);
-      // q = round(V / M) from V 2^-QS in FP32
+      const uint64_t a1 = a[c][1] + (a[c][0] >> 32);
+      const uint64_t a2 = a[c][2] + (a1 >> 32);
+      const uint64_t a3 = a[c][3] + (a2 >> 32);
+      const uint32_t w0 = static_cast<uint32_t>(a[c][0]), w1 = static_cast<uint32_t>(a1),
+                     w2 = static_cast<uint32_t>(a2);
+      // qt = round(V / M) from V 2^-QS in FP32
       const float vf = __ull2float_rn(a3) * pow2f(96 - QS) + __uint2float_rn(w2) * pow2f(64 - QS) +
                        __uint2float_rn(w1) * pow2f(32 - QS) + __uint2float_rn(w0) * pow2f(-QS);
-      const uint64_t q = static_cast<uint64_t>(__float2int_rn(vf * c_mod.qscale[K]));
-      // X = V - q M modulo 2^128
+      const uint64_t qt = static_cast<uint64_t>(__float2int_rn(vf * c_mod.qscale[K]));
+      // X = V - qt M modulo 2^128
       const uint64_t lo = (static_cast<uint64_t>(w1) << 32) | w0;
       const uint64_t hi = (a3 << 32) | w2;
-      const uint64_t qm_lo = q * m_lo;
-      const uint64_t qm_hi = __umul64hi(q, m_lo) + q * m_hi;
+      const uint64_t qm_lo = qt * m_lo;
+      const uint64_t qm_hi = __umul64hi(qt, m_lo) + qt * m_hi;
       const uint64_t x_lo = lo - qm_lo;
       const uint64_t x_hi = hi - qm_hi - (lo < qm_lo ? 1 : 0);
       __stcs(crow + col0 + c, round_i128_scaled(static_cast<int64_t>(x_hi), x_lo, base_scale + P->b_exp[col0 + c]));
@@ -825,7 +830,7 @@ static void launch_mod_recombine(int bn, const EmuArgs& args, unsigned blocks, c
 
 cudaError_t mod_recombine_launch(int bn, int k, const EmuArgs& args, int total_tiles, cudaStream_t stream) {
   if (total_tiles <= 0) return cudaSuccess;
-  const long long threads = static_cast<long long>(total_tiles) * (EM_BM * bn / 16);
+  const long long threads = static_cast<long long>(total_tiles) * (EM_BM * bn / 4);
   const unsigned blocks = static_cast<unsigned>((threads + 255) / 256);
   switch (k) {
     case 2: launch_mod_recombine<2>(bn, args, blocks, stream); break;

@@ -163,16 +163,18 @@ void prof_end(mm_handle h, cudaStream_t s, long mark) {
 // Built-in plan table (a tune file overrides it): the output of
 // paper_1012_2273_gb300.autotune on a GB300 (tune/gb300.tune).  Below N = 256
 // native FP64 is as fast and is the only form that meets the componentwise
-// bound for wide-range inputs at the smallest N; from there the emulation with
-// the fewest digits that stays within the bound on uniform and log-uniform
-// (2^+-20) inputs: 8 digits up to N = 767, 7 up to 4095, 6 above (the bound
-// 2 N 2^-53 |A||B| grows with N).
+// bound for wide-range inputs at the smallest N; up to 767 the digit form
+// (8, then 7 digits); from 768 the modular form, with the fewest moduli that
+// stay within the bound on uniform and log-uniform (2^+-20) inputs: 15 up to
+// N = 2047, 14 above (the bound 2 N 2^-53 |A||B| grows with N).  Beyond the
+// modular form's size limit the digit form with 6 digits.
 void default_tune(mm_handle h) {
   h->tune.clear();
   h->tune.push_back({255, Plan{0, 7, 256, 0}});
-  h->tune.push_back({767, Plan{1, 8, 128, 0}});
-  h->tune.push_back({1023, Plan{1, 7, 128, 0}});
-  h->tune.push_back({4095, Plan{1, 7, 256, 0}});
+  h->tune.push_back({511, Plan{1, 8, 128, 0}});
+  h->tune.push_back({767, Plan{1, 7, 256, 0}});
+  h->tune.push_back({2047, Plan{2, 15, 256, 0}});
+  h->tune.push_back({65535, Plan{2, 14, 256, 0}});
   h->tune.push_back({1 << 30, Plan{1, 6, 256, 0}});
 }
 
@@ -258,10 +260,16 @@ mm_status ensure_arena(mm_handle h, size_t bytes) {
   if (h->arena) cudaFree(h->arena);  // implicit device synchronisation
   h->arena = nullptr;
   h->arena_cap = 0;
-  const size_t cap = align_up(bytes + bytes / 8, 1 << 20);
+  // An eighth to spare for the next call's growth, when the device has it.
+  size_t cap = align_up(bytes + bytes / 8, 1 << 20);
   if (cudaMalloc(&h->arena, cap) != cudaSuccess) {
     cudaGetLastError();
-    return fail(h, MM_ERR_NOMEM, "workspace allocation of " + std::to_string(cap) + " bytes failed");
+    cap = align_up(bytes, 1 << 20);
+    if (cudaMalloc(&h->arena, cap) != cudaSuccess) {
+      cudaGetLastError();
+      h->arena = nullptr;
+      return fail(h, MM_ERR_NOMEM, "workspace allocation of " + std::to_string(cap) + " bytes failed");
+    }
   }
   h->arena_cap = cap;
   return MM_OK;

@@ -1,6 +1,7 @@
 """One small, self-contained product for kernel profiling (e.g. under ncu).
 
     python -m paper_1012_2273_gb300.profile_case --n 2048 --form emulated --reps 3
+    python -m paper_1012_2273_gb300.profile_case --n 2048 --form modular --slices 16 --reps 3
     python -m paper_1012_2273_gb300.profile_case --sweep --reps 2
 
 --sweep runs the benchmark's step instead: one grouped call over the paper's
@@ -24,7 +25,7 @@ sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
 def main() -> int:
     ap = argparse.ArgumentParser()
     ap.add_argument("--n", type=int, default=2048)
-    ap.add_argument("--form", choices=("native", "emulated", "auto"), default="emulated")
+    ap.add_argument("--form", choices=("native", "emulated", "modular", "auto"), default="emulated")
     ap.add_argument("--slices", type=int, default=0)
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--dist", default="uniform01")

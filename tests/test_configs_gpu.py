@@ -41,7 +41,7 @@ def check_rows(C, A, B, n, factor=2.0):
 
 # ---- paper sweep: N = 10 .. 2000, uniform [0, 1) and integers {-8..8} ---------
 
-@pytest.mark.parametrize("form", ["native", "emulated", "auto"])
+@pytest.mark.parametrize("form", ["native", "emulated", "modular", "auto"])
 def test_paper_sweep_both_forms(form):
     import paper_1012_2273_gb300 as mm
     with mm.Handle(form) as h:
@@ -94,6 +94,34 @@ def test_precision_per_slice_count_n2000():
     report("precision_n2000.json", out)
 
 
+def test_precision_per_moduli_count_n2000():
+    # The modular form: error against the plain product per moduli count k
+    # (fixed-point width beta from the width rule).
+    import paper_1012_2273_gb300 as mm
+    n = 2000
+    out = {"N": n, "bound_2Nu": 2 * n * U, "rows": {}}
+    for dist in ("uniform11", "loguniform20"):
+        A, B = workload.pair(dist, 3, n)
+        r = rows_of(n, 10)
+        ref = oracle.gemm_rows(A, B, r)
+        absab = np.abs(A[r]) @ np.abs(B)
+        errs = {}
+        for k in range(8, 17):
+            with mm.Handle("modular", slices=k) as h:
+                C = host(h.gemm(dev(A), dev(B)))
+                h.check()
+            errs[f"k={k} beta={oracle.modular_beta(k, n)}"] = float(np.max(np.abs(C[r] - ref) / absab))
+            if k == 16:
+                np.testing.assert_array_equal(C[r[:2]].view(np.int64),
+                                              oracle.fixed_gemm_rows(A, B, oracle.modular_beta(k, n), r[:2]).view(np.int64))
+        out["rows"][dist] = errs
+        seq = list(errs.values())
+        assert all(b <= a * 1.01 + 2 * n * U for a, b in zip(seq, seq[1:])), seq
+        assert seq[-2] <= 2 * n * U and seq[-1] <= 2 * n * U  # 15 and 16 moduli
+        assert seq[0] > 2 * n * U  # 8 moduli: about 25 bits
+    report("precision_modular_n2000.json", out)
+
+
 @pytest.mark.parametrize("n", [4096, 8192])
 def test_precision_large_sizes_rows(n):
     import paper_1012_2273_gb300 as mm
@@ -125,7 +153,7 @@ def batch_1024():
     return sizes, pairs
 
 
-@pytest.mark.parametrize("form", ["native", "emulated", "auto"])
+@pytest.mark.parametrize("form", ["native", "emulated", "modular", "auto"])
 def test_grouped_batch_1024(batch_1024, form):
     import torch
     import paper_1012_2273_gb300 as mm
@@ -151,9 +179,12 @@ def test_grouped_batch_1024(batch_1024, form):
             worst = max(worst, float(np.max(np.abs(C - ref) / absab)) / (2 * n * U))
         elif p % 16 == 0:
             check_rows(C, A, B, n)
-        if plans[n][0] == 1 and p % 64 == 1:
+        if plans[n][0] != 0 and p % 64 == 1:
             r = rows_of(n, 2)[:3]
-            want = oracle.emu_gemm_rows(A, B, plans[n][1], r)
+            if plans[n][0] == 1:
+                want = oracle.emu_gemm_rows(A, B, plans[n][1], r)
+            else:
+                want = oracle.fixed_gemm_rows(A, B, oracle.modular_beta(plans[n][1], n), r)
             np.testing.assert_array_equal(C[r].view(np.int64), want.view(np.int64))
     report(f"grouped_1024_{form}.json", {"worst_error_over_bound_small_problems": worst})
 

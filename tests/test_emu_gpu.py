@@ -212,11 +212,12 @@ def test_nonfinite_input_is_reported():
         h.check()  # the status word was cleared
 
 
-def test_auto_plan_picks_native_for_small_and_emulation_for_large():
+def test_auto_plan_picks_native_small_digits_middle_modular_large():
     import paper_1012_2273_gb300 as mm
     with mm.Handle("auto") as h:
         assert h.plan(10)[0] == 0
-        assert h.plan(4096)[0] == 1
+        assert h.plan(600)[0] == 1   # digit form where the modular width is too narrow
+        assert h.plan(4096)[0] == 2  # modular form above
 
 
 @pytest.mark.parametrize("groups", [1, 2, 5, 13, 28])
