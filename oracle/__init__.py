@@ -270,13 +270,13 @@ def max_threads() -> int:
 # them: pairwise coprime, each at most 256 so that every symmetric residue
 # (|r| <= 128) is an exact bf16 value.  The first k are used with k moduli.
 MODULI = (256, 255, 253, 251, 247, 241, 239, 233, 229, 227, 223, 217, 211, 199, 197, 193)
-MAX_FIXED_BITS = 55
+MAX_FIXED_BITS = 62
 
 
 def modular_beta(k: int, n: int) -> int:
     """Fixed-point width used with the first k moduli at size n.
 
-    The largest beta <= 55 with 4 n 2^(2 beta) <= M_k (M_k the product of the
+    The largest beta <= 62 with 4 n 2^(2 beta) <= M_k (M_k the product of the
     first k moduli): the exact product X of two beta-bit operands has
     |X| <= n 2^(2 beta) <= M_k / 4, so X is recovered from its residues with
     a quarter of the modulus to spare.  0 means k is too small for n.

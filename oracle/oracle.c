@@ -453,14 +453,18 @@ double or_int128_to_double(int64_t hi, uint64_t lo) {
  *   B_int(j,k) = round-half-even(b_jk 2^(beta - f_k)),  f_k likewise
  *   X(i,k)     = sum_j A_int(i,j) B_int(j,k)        (exact, 128-bit)
  *   c_ik       = RN(X(i,k)) 2^(e_i + f_k - 2 beta)
- * |A_int|, |B_int| <= 2^beta, so |X| <= n 2^(2 beta) < 2^127 for beta <= 55
- * and n < 2^17.
+ * |A_int|, |B_int| <= 2^beta, so |X| <= n 2^(2 beta), below 2^126 whenever
+ * 2 beta plus the bit length of n is at most 126 (checked; beta <= 62).
  */
 
 /* round-half-even(v 2^(beta - e)); exact scaling as in or_emu_fixed. */
 int64_t or_fix(double v, int e, int beta) { return (int64_t)nearbyint(ldexp(v, beta - e)); }
 
-static int fixed_args_ok(int n, int beta) { return n >= 0 && n < (1 << 17) && beta >= 1 && beta <= 55; }
+static int fixed_args_ok(int n, int beta) {
+  int bits = 0;
+  for (int v = n; v > 0; v >>= 1) ++bits;
+  return n >= 0 && n < (1 << 17) && beta >= 1 && beta <= 62 && 2 * beta + bits <= 126;
+}
 
 /* Row i of the product from A_int row `ai` and all of B_int (row-major [j][k]). */
 static void fixed_row(int n, int beta, const int64_t* ai, const int64_t* Bi, int e, const int* f,

@@ -341,7 +341,7 @@ def _py_fixed_product(A, B, beta):
 def test_fix_is_the_exact_rounding():
     vals = list(workload.values("loguniform20", 4, 200)) + [0.0, -0.0, 1 - 2 ** -53, -(1 - 2 ** -53), 0.5,
                                                              2 ** -60, 3 * 2 ** -56]
-    for beta in (1, 7, 30, 47, 55):
+    for beta in (1, 7, 30, 47, 55, 62):
         for v in vals:
             e = 1 if abs(v) < 1 else math.frexp(abs(v))[1]
             assert oracle.fix(v, e, beta) == round(Fraction(float(v)) * Fraction(2) ** (beta - e))
@@ -356,7 +356,7 @@ def test_fixed_product_by_exact_integers(n, dist):
     A, B = workload.pair(dist, 30 + n, n)
     A[0, :] *= 2.0 ** 30  # rows and columns on different scales
     B[:, -1] *= 2.0 ** -25
-    for beta in (3, 21, 40, 55):
+    for beta in (3, 21, 40, 55, 60):
         np.testing.assert_array_equal(oracle.fixed_gemm(A, B, beta), _py_fixed_product(A, B, beta))
 
 
@@ -433,5 +433,6 @@ def test_modular_width_rule():
                 continue
             assert 4 * n * 2 ** (2 * beta) <= Mk
             assert beta == oracle.MAX_FIXED_BITS or 4 * n * 2 ** (2 * beta + 2) > Mk
-    assert oracle.modular_beta(16, 2000) == 55 and oracle.modular_beta(16, 16384) == 54
+    assert oracle.modular_beta(16, 100) == 58 and oracle.modular_beta(16, 500) == 57
+    assert oracle.modular_beta(16, 2000) == 56 and oracle.modular_beta(16, 16384) == 54
     assert oracle.modular_beta(14, 8192) == 47 and oracle.modular_beta(15, 2000) == 52
