@@ -753,9 +753,10 @@ __global__ void __launch_bounds__(256) mod_recombine_kernel(const __grid_constan
       const uint64_t a3 = a[c][3] + (a2 >> 32);
       const uint32_t w0 = static_cast<uint32_t>(a[c][0]), w1 = static_cast<uint32_t>(a1),
                      w2 = static_cast<uint32_t>(a2);
-      // qt = round(V / M) from V 2^-QS in FP32
-      const float vf = __ull2float_rn(a3) * pow2f(96 - QS) + __uint2float_rn(w2) * pow2f(64 - QS) +
-                       __uint2float_rn(w1) * pow2f(32 - QS) + __uint2float_rn(w0) * pow2f(-QS);
+      // qt = round(V / M) from V 2^-QS in FP32 (for M > 2^100 the low 64
+      // bits of V move V / M by less than 2^-36 and are left out)
+      float vf = __ull2float_rn(a3) * pow2f(96 - QS) + __uint2float_rn(w2) * pow2f(64 - QS);
+      if (QS < 100 - 31) vf += __uint2float_rn(w1) * pow2f(32 - QS) + __uint2float_rn(w0) * pow2f(-QS);
       const uint64_t qt = static_cast<uint64_t>(__float2int_rn(vf * c_mod.qscale[K]));
       // X = V - qt M modulo 2^128
       const uint64_t lo = (static_cast<uint64_t>(w1) << 32) | w0;

@@ -233,50 +233,90 @@ __device__ __forceinline__ void write_digit_planes(const long long (&Ds)[SP_TILE
 }
 
 // Phase 2 for the modular form with K moduli: the symmetric residues of D
-// modulo m_0..m_{K-1}, one 16-byte vector (8 values) per plane.  |D| <= 2^55
-// is cut into four 14-bit limbs x_l carrying D's sign, and
-//     S = x_0 + x_1 c_1 + x_2 c_2 + x_3 c_3,  c_l = 2^(14 l) mod m (symmetric),
-// is congruent to D with |S| < 2^14 + 3 2^14 128 < 2^23, so every step is an
+// modulo m_0..m_{K-1}, one 16-byte vector (8 values) per plane.  |D| <= 2^62
+// is cut into five 13-bit limbs x_l carrying D's sign, and
+//     S = x_0 + x_1 c_1 + ... + x_4 c_4,  c_l = 2^(13 l) mod m (symmetric),
+// is congruent to D with |S| < 2^13 (1 + 4 128) < 2^23, so every step is an
 // exact FP32 integer operation.  r = S - m rint(S RN(1/m)): the product's
 // relative error is at most 2^-24, below 1 / (2 |S|), so rint picks the
 // nearest multiple of m exactly as exact division would and |r| <= m/2 <= 128
 // -- an exact bf16 value.  rint is the add-and-subtract of 1.5 2^23.
 template <int K>
-__device__ __forceinline__ void write_residue_planes(const long long (&Ds)[SP_TILE][SP_TILE + 1], uint16_t* dst,
-                                                     int r0, int c0, int k_pad, size_t plane) {
-  for (int item = threadIdx.x; item < SP_TILE * (SP_TILE / 8); item += SP_THREADS) {
-    const int r = item >> 3, cg = item & 7;
-    float x[8][4];
+__device__ __forceinline__ void write_residue_item(const long long (&D)[8], uint16_t* out, size_t plane) {
+  float x[8][MOD_LIMBS];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const uint64_t X = D[q] < 0 ? 0ull - static_cast<uint64_t>(D[q]) : static_cast<uint64_t>(D[q]);
+    const float sg = D[q] < 0 ? -1.0f : 1.0f;
+#pragma unroll
+    for (int l = 0; l < MOD_LIMBS; ++l) {
+      const uint32_t limb = static_cast<uint32_t>(X >> (MOD_LIMB_BITS * l)) & ((1u << MOD_LIMB_BITS) - 1);
+      x[q][l] = sg * (__uint_as_float(0x4B000000u | limb) - 8388608.0f);  // exact: limb < 2^23
+    }
+  }
+  // (the moduli loop stays rolled: unrolled, its 4 K limb constants would
+  // all be held in registers)
+#pragma unroll 1
+  for (int j = 0; j < K; ++j) {
+    const float m = c_mod.m_f[j], inv = c_mod.inv_f[j];
+    float c[MOD_LIMBS - 1];
+#pragma unroll
+    for (int l = 1; l < MOD_LIMBS; ++l) c[l - 1] = c_mod.split_c[j][l - 1];
+    float res[8];
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
-      const long long D = Ds[r][cg * 8 + q];
-      const uint64_t X = D < 0 ? 0ull - static_cast<uint64_t>(D) : static_cast<uint64_t>(D);
-      const float sg = D < 0 ? -1.0f : 1.0f;
+      float S = x[q][0];
 #pragma unroll
-      for (int l = 0; l < 4; ++l) {
-        const uint32_t limb = static_cast<uint32_t>(X >> (14 * l)) & 0x3FFFu;
-        x[q][l] = sg * (__uint_as_float(0x4B000000u | limb) - 8388608.0f);  // exact: limb < 2^23
-      }
+      for (int l = 1; l < MOD_LIMBS; ++l) S = fmaf(x[q][l], c[l - 1], S);
+      const float qt = fmaf(S, inv, 12582912.0f) - 12582912.0f;
+      res[q] = fmaf(-qt, m, S);
     }
-    uint16_t* out = dst + static_cast<size_t>(r0 + r) * k_pad + c0 + cg * 8;
+    uint4 v;
+    v.x = bf16x2_of_digits(res[0], res[1]);
+    v.y = bf16x2_of_digits(res[2], res[3]);
+    v.z = bf16x2_of_digits(res[4], res[5]);
+    v.w = bf16x2_of_digits(res[6], res[7]);
+    *reinterpret_cast<uint4*>(out + j * plane) = v;
+  }
+}
+
+// Modular form, A tile: the planes are row-major like A, so no transpose is
+// needed -- each item (output row r, columns c0 + 8 cg ..) loads its 8 values
+// straight from A (a warp: 4 rows x 512 contiguous bytes) and writes one
+// 16-byte vector per plane (4 rows x 128 contiguous bytes).
+template <int K>
+__device__ __forceinline__ void residue_tile_a(const uint64_t* src, int n, int r0, int c0, const int* ex_s,
+                                               int width, uint16_t* dst, int k_pad, size_t plane,
+                                               bool* nonfinite) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll 1
+  for (int pass = 0; pass < 2; ++pass) {
+    const int r = (lane >> 3) + 4 * warp + 32 * pass, cg = lane & 7;
+    const int i = r0 + r, j0 = c0 + 8 * cg;
+    long long D[8];
+    uint64_t bits[8];
 #pragma unroll
-    for (int j = 0; j < K; ++j) {
-      const float c1 = c_mod.split_c[j][0], c2 = c_mod.split_c[j][1], c3 = c_mod.split_c[j][2];
-      const float m = c_mod.m_f[j], inv = c_mod.inv_f[j];
-      float res[8];
+    for (int q = 0; q < 8; ++q) bits[q] = (i < n && j0 + q < n) ? src[static_cast<size_t>(i) * n + j0 + q] : 0ull;
 #pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        const float S = fmaf(x[q][3], c3, fmaf(x[q][2], c2, fmaf(x[q][1], c1, x[q][0])));
-        const float qt = fmaf(S, inv, 12582912.0f) - 12582912.0f;
-        res[q] = fmaf(-qt, m, S);
-      }
-      uint4 v;
-      v.x = bf16x2_of_digits(res[0], res[1]);
-      v.y = bf16x2_of_digits(res[2], res[3]);
-      v.z = bf16x2_of_digits(res[4], res[5]);
-      v.w = bf16x2_of_digits(res[6], res[7]);
-      *reinterpret_cast<uint4*>(out + j * plane) = v;
-    }
+    for (int q = 0; q < 8; ++q) D[q] = (i < n && j0 + q < n) ? fixed_point(bits[q], ex_s[r], width, nonfinite) : 0;
+    write_residue_item<K>(D, dst + static_cast<size_t>(i) * k_pad + j0, plane);
+  }
+}
+
+// Modular form, B^T tile, after the transpose into Ds: item (r, cg) with two
+// lanes per row -- every 8-byte shared load of a half-warp hits 16 distinct
+// bank pairs, and each row's two vectors per plane fill one 32-byte sector.
+template <int K>
+__device__ __forceinline__ void residue_tile_from_smem(const long long (&Ds)[SP_TILE][SP_TILE + 1], uint16_t* dst,
+                                                       int r0, int c0, int k_pad, size_t plane) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll 1
+  for (int pass = 0; pass < 2; ++pass) {
+    const int r = 16 * (warp >> 2) + (lane >> 1) + 32 * pass, cg = 2 * (warp & 3) + (lane & 1);
+    long long D[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) D[q] = Ds[r][8 * cg + q];
+    write_residue_item<K>(D, dst + static_cast<size_t>(r0 + r) * k_pad + c0 + 8 * cg, plane);
   }
 }
 
@@ -285,8 +325,19 @@ __device__ __forceinline__ void write_residue_planes(const long long (&Ds)[SP_TI
 // fixed-point value D in shared memory, transposed for B^T; phase 2 turns 8
 // consecutive D of an output row into one 16-byte vector per plane (8 threads
 // write a row's 128 contiguous bytes).
+template <int K>
+__device__ __forceinline__ void residue_tile(bool is_a, const uint64_t* src, int n, int r0, int c0, const int* ex_s,
+                                             int width, const long long (&Ds)[SP_TILE][SP_TILE + 1], uint16_t* dst,
+                                             int k_pad, size_t plane, bool* nonfinite) {
+  if (is_a)
+    residue_tile_a<K>(src, n, r0, c0, ex_s, width, dst, k_pad, plane, nonfinite);
+  else
+    residue_tile_from_smem<K>(Ds, dst, r0, c0, k_pad, plane);
+}
+
 __global__ void __launch_bounds__(SP_THREADS) split_kernel(const __grid_constant__ SplitArgs args) {
   __shared__ long long Ds[SP_TILE][SP_TILE + 1];
+  __shared__ int ex_s[SP_TILE];  // exponent of each output row (A: row i; B^T: column k of B)
   __shared__ int any_nonfinite;
   const Problem* P;
   const int pi = split_find(args, blockIdx.x, &P);
@@ -309,67 +360,71 @@ __global__ void __launch_bounds__(SP_THREADS) split_kernel(const __grid_constant
   const uint64_t* maxbits = is_a ? args.a_maxbits + off : args.b_maxbits + off;
   int* exps = is_a ? P->a_exp : P->b_exp;
   if (threadIdx.x == 0) any_nonfinite = 0;
-  bool nonfinite = false;
-
-  // Phase 1: source element (x, y) of the tile, x fastest (coalesced).
-  //   A:   source row i = r0 + y, column j = c0 + x -> Ds[y][x]  (output row y)
-  //   B^T: source row j = c0 + y, column k = r0 + x -> Ds[x][y]  (output row x)
-  // Each thread's 16 elements, 4 loads in flight at a time.
-  constexpr int PER = SP_TILE * SP_TILE / SP_THREADS;
-  constexpr int BATCH = 4;
-  const int x = threadIdx.x % SP_TILE;
-#pragma unroll
-  for (int q0 = 0; q0 < PER; q0 += BATCH) {
-    uint64_t bits[BATCH];
-    int ex[BATCH];
-#pragma unroll
-    for (int b = 0; b < BATCH; ++b) {
-      const int y = threadIdx.x / SP_TILE + (q0 + b) * (SP_THREADS / SP_TILE);
-      const int i = is_a ? r0 + y : c0 + y;  // source row
-      const int j = is_a ? c0 + x : r0 + x;  // source column
-      const int er = is_a ? i : j;           // row (A) or column (B) of the exponent
-      bits[b] = (i < n && j < n) ? src[static_cast<size_t>(i) * n + j] : 0ull;
-      ex[b] = er < n ? exponent_from_maxbits(maxbits[er]) : 0;
-    }
-#pragma unroll
-    for (int b = 0; b < BATCH; ++b) {
-      const int y = threadIdx.x / SP_TILE + (q0 + b) * (SP_THREADS / SP_TILE);
-      const int i = is_a ? r0 + y : c0 + y;
-      const int j = is_a ? c0 + x : r0 + x;
-      long long D = 0;
-      if (i < n && j < n) {
-        D = fixed_point(bits[b], ex[b], width, &nonfinite);
-        if (exps && (is_a ? j : i) == 0) exps[is_a ? i : j] = ex[b];
-      }
-      if (is_a) Ds[y][x] = D; else Ds[x][y] = D;
-    }
+  if (threadIdx.x < SP_TILE) {
+    const int er = r0 + threadIdx.x;
+    const int e = er < n ? exponent_from_maxbits(maxbits[er]) : 0;
+    ex_s[threadIdx.x] = e;
+    if (exps && c0 == 0 && er < n) exps[er] = e;
   }
-  if (nonfinite) any_nonfinite = 1;
   __syncthreads();
+  bool nonfinite = false;
+  const bool direct = beta > 0 && is_a;  // modular A tiles skip the shared-memory pass
+
+  if (!direct) {
+    // Phase 1: source element (x, y) of the tile, x fastest (coalesced).
+    //   A:   source row i = r0 + y, column j = c0 + x -> Ds[y][x]  (output row y)
+    //   B^T: source row j = c0 + y, column k = r0 + x -> Ds[x][y]  (output row x)
+    // Each thread's 16 elements, 4 loads in flight at a time.
+    constexpr int PER = SP_TILE * SP_TILE / SP_THREADS;
+    constexpr int BATCH = 4;
+    const int x = threadIdx.x % SP_TILE;
+#pragma unroll
+    for (int q0 = 0; q0 < PER; q0 += BATCH) {
+      uint64_t bits[BATCH];
+#pragma unroll
+      for (int b = 0; b < BATCH; ++b) {
+        const int y = threadIdx.x / SP_TILE + (q0 + b) * (SP_THREADS / SP_TILE);
+        const int i = is_a ? r0 + y : c0 + y;  // source row
+        const int j = is_a ? c0 + x : r0 + x;  // source column
+        bits[b] = (i < n && j < n) ? src[static_cast<size_t>(i) * n + j] : 0ull;
+      }
+#pragma unroll
+      for (int b = 0; b < BATCH; ++b) {
+        const int y = threadIdx.x / SP_TILE + (q0 + b) * (SP_THREADS / SP_TILE);
+        const int i = is_a ? r0 + y : c0 + y;
+        const int j = is_a ? c0 + x : r0 + x;
+        long long D = 0;
+        if (i < n && j < n) D = fixed_point(bits[b], ex_s[is_a ? y : x], width, &nonfinite);
+        if (is_a) Ds[y][x] = D; else Ds[x][y] = D;
+      }
+    }
+    __syncthreads();
+  }
 
   if (beta > 0) {
     switch (S) {
 #define MM_RESIDUE_CASE(K) \
-  case K: write_residue_planes<K>(Ds, dst, r0, c0, P->k_pad, plane); break;
+  case K: residue_tile<K>(is_a, src, n, r0, c0, ex_s, width, Ds, dst, P->k_pad, plane, &nonfinite); break;
       MM_RESIDUE_CASE(2) MM_RESIDUE_CASE(3) MM_RESIDUE_CASE(4) MM_RESIDUE_CASE(5) MM_RESIDUE_CASE(6)
       MM_RESIDUE_CASE(7) MM_RESIDUE_CASE(8) MM_RESIDUE_CASE(9) MM_RESIDUE_CASE(10) MM_RESIDUE_CASE(11)
       MM_RESIDUE_CASE(12) MM_RESIDUE_CASE(13) MM_RESIDUE_CASE(14) MM_RESIDUE_CASE(15)
-      default: write_residue_planes<16>(Ds, dst, r0, c0, P->k_pad, plane); break;
+      default: residue_tile<16>(is_a, src, n, r0, c0, ex_s, width, Ds, dst, P->k_pad, plane, &nonfinite); break;
 #undef MM_RESIDUE_CASE
     }
-    if (threadIdx.x == 0 && any_nonfinite) set_status(args.status, MM_ERR_NONFINITE);
-    return;
+  } else {
+    switch (S) {
+      case 1: write_digit_planes<1>(Ds, dst, r0, c0, P->k_pad, plane); break;
+      case 2: write_digit_planes<2>(Ds, dst, r0, c0, P->k_pad, plane); break;
+      case 3: write_digit_planes<3>(Ds, dst, r0, c0, P->k_pad, plane); break;
+      case 4: write_digit_planes<4>(Ds, dst, r0, c0, P->k_pad, plane); break;
+      case 5: write_digit_planes<5>(Ds, dst, r0, c0, P->k_pad, plane); break;
+      case 6: write_digit_planes<6>(Ds, dst, r0, c0, P->k_pad, plane); break;
+      case 7: write_digit_planes<7>(Ds, dst, r0, c0, P->k_pad, plane); break;
+      default: write_digit_planes<8>(Ds, dst, r0, c0, P->k_pad, plane); break;
+    }
   }
-  switch (S) {
-    case 1: write_digit_planes<1>(Ds, dst, r0, c0, P->k_pad, plane); break;
-    case 2: write_digit_planes<2>(Ds, dst, r0, c0, P->k_pad, plane); break;
-    case 3: write_digit_planes<3>(Ds, dst, r0, c0, P->k_pad, plane); break;
-    case 4: write_digit_planes<4>(Ds, dst, r0, c0, P->k_pad, plane); break;
-    case 5: write_digit_planes<5>(Ds, dst, r0, c0, P->k_pad, plane); break;
-    case 6: write_digit_planes<6>(Ds, dst, r0, c0, P->k_pad, plane); break;
-    case 7: write_digit_planes<7>(Ds, dst, r0, c0, P->k_pad, plane); break;
-    default: write_digit_planes<8>(Ds, dst, r0, c0, P->k_pad, plane); break;
-  }
+  if (nonfinite) any_nonfinite = 1;
+  __syncthreads();
   if (threadIdx.x == 0 && any_nonfinite) set_status(args.status, MM_ERR_NONFINITE);
 }
 

