@@ -108,6 +108,17 @@ mm_status mm_gemm_grouped(mm_handle h, int count, const int* Ns, const double* c
 mm_status mm_gemm_host(mm_handle h, int N, const double* A_host, const double* B_host, double* C_host,
                        void* stream);
 
+/* End-to-end form of mm_gemm_grouped on HOST buffers: Ns, As, Bs, Cs as in
+ * mm_gemm_grouped but the matrices are host memory (best pinned).  Returns
+ * when every C_p is on the host.  The problems are cut into chunks (those
+ * below N = 768 together, the larger ones in up to four chunks by size,
+ * the smallest of those last); the copies of one chunk overlap the
+ * computation of its neighbours (inputs on an upload stream, results on a
+ * download stream, the products on `stream` as a grouped call).  The device
+ * copies live in a grow-only handle buffer. */
+mm_status mm_gemm_grouped_host(mm_handle h, int count, const int* Ns, const double* const* As_host,
+                               const double* const* Bs_host, double* const* Cs_host, void* stream);
+
 /* Synchronises `stream` and returns the first error recorded on the device
  * since the last call (and clears it), else MM_OK. */
 mm_status mm_status_get(mm_handle h, void* stream);

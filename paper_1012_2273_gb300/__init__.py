@@ -52,7 +52,8 @@ class _Config(ctypes.Structure):
                 ("tune_path", ctypes.c_char_p)]
 
 
-SYMBOLS = ("mm_create", "mm_destroy", "mm_gemm", "mm_gemm_grouped", "mm_gemm_host", "mm_status_get",
+SYMBOLS = ("mm_create", "mm_destroy", "mm_gemm", "mm_gemm_grouped", "mm_gemm_host", "mm_gemm_grouped_host",
+           "mm_status_get",
            "mm_last_error", "mm_plan", "mm_profile_read", "mm_probe_fp64_peak", "mm_selftest_wait", "mm_split",
            "mm_split_noalloc",
            "mm_level_sums", "mm_recombine", "mm_modular_params")
@@ -80,6 +81,8 @@ def lib(build_if_needed: bool = True) -> ctypes.CDLL:
             L.mm_gemm_grouped.argtypes = [vp, ci, ctypes.POINTER(ci), ctypes.POINTER(vp), ctypes.POINTER(vp),
                                           ctypes.POINTER(vp), vp]
             L.mm_gemm_host.argtypes = [vp, ci, vp, vp, vp, vp]
+            L.mm_gemm_grouped_host.argtypes = [vp, ci, ctypes.POINTER(ci), ctypes.POINTER(vp), ctypes.POINTER(vp),
+                                               ctypes.POINTER(vp), vp]
             L.mm_status_get.argtypes = [vp, vp]
             L.mm_last_error.argtypes = [vp]
             L.mm_last_error.restype = ctypes.c_char_p
@@ -231,6 +234,32 @@ class Handle:
         self._raise(self._lib.mm_gemm_host(self._h, n, A.ctypes.data, B.ctypes.data, C.ctypes.data,
                                            _stream_ptr(stream)))
         return C
+
+    def gemm_grouped_host(self, As, Bs, Cs=None, stream=None):
+        """mm_gemm_grouped_host: uneven products on host matrices (numpy arrays or
+        CPU tensors, best pinned); copies overlap the computation.  Returns Cs."""
+        import numpy as np
+        def ptr(x):
+            return x.data_ptr() if hasattr(x, "data_ptr") else x.ctypes.data
+        def n_of(x):
+            if len(x.shape) != 2 or x.shape[0] != x.shape[1]:
+                raise ValueError("matrices must be square")
+            return int(x.shape[0])
+        for x in list(As) + list(Bs):
+            if hasattr(x, "is_cuda") and x.is_cuda:
+                raise TypeError("gemm_grouped_host takes host matrices")
+            if hasattr(x, "dtype") and str(x.dtype) not in ("float64", "torch.float64"):
+                raise TypeError("matrices must be float64")
+        count = len(As)
+        Ns = [n_of(a) for a in As]
+        if Cs is None:
+            Cs = [np.empty((n, n), np.float64) for n in Ns]
+        arr_n = (ctypes.c_int * count)(*Ns)
+        arr_a = (ctypes.c_void_p * count)(*[ptr(a) for a in As])
+        arr_b = (ctypes.c_void_p * count)(*[ptr(b) for b in Bs])
+        arr_c = (ctypes.c_void_p * count)(*[ptr(c) for c in Cs])
+        self._raise(self._lib.mm_gemm_grouped_host(self._h, count, arr_n, arr_a, arr_b, arr_c, _stream_ptr(stream)))
+        return Cs
 
     def gemm_host_ptr(self, n: int, a_ptr: int, b_ptr: int, c_ptr: int, stream=None):
         """mm_gemm_host on raw host pointers (e.g. pinned torch tensors)."""

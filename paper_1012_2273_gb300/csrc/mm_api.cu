@@ -92,6 +92,12 @@ struct mm_handle_s {
   // host-to-host entry point buffers
   double* e2e = nullptr;
   size_t e2e_cap = 0;
+  // grouped host-to-host entry point: device copies of all problems, copy
+  // streams and per-chunk events
+  char* ge2e = nullptr;
+  size_t ge2e_cap = 0;
+  cudaStream_t up_stream = nullptr, down_stream = nullptr;
+  std::vector<cudaEvent_t> ge2e_events;
   // grouped calls
   cudaStream_t cap_stream = nullptr;
   std::map<std::vector<long long>, GraphEntry> graphs;
@@ -649,6 +655,10 @@ mm_status mm_destroy(mm_handle h) {
   }
   if (h->arena) cudaFree(h->arena);
   if (h->e2e) cudaFree(h->e2e);
+  if (h->ge2e) cudaFree(h->ge2e);
+  if (h->up_stream) cudaStreamDestroy(h->up_stream);
+  if (h->down_stream) cudaStreamDestroy(h->down_stream);
+  for (cudaEvent_t e : h->ge2e_events) cudaEventDestroy(e);
   if (h->grp_table) cudaFree(h->grp_table);
   if (h->grp_pinned) cudaFreeHost(h->grp_pinned);
   if (h->grp_event) cudaEventDestroy(h->grp_event);
@@ -779,6 +789,116 @@ mm_status mm_gemm_host(mm_handle h, int N, const double* A_host, const double* B
   mm_status st = mm_gemm(h, N, dA, dB, dC, stream);
   if (st != MM_OK) return st;
   MM_CUDA(h, cudaMemcpyAsync(C_host, dC, elems * sizeof(double), cudaMemcpyDeviceToHost, s));
+  MM_CUDA(h, cudaStreamSynchronize(s));
+  return MM_OK;
+}
+
+mm_status mm_gemm_grouped_host(mm_handle h, int count, const int* Ns, const double* const* As_host,
+                               const double* const* Bs_host, double* const* Cs_host, void* stream) {
+  if (!h) return MM_ERR_INVALID;
+  if (count < 0) return fail(h, MM_ERR_INVALID, "count must be >= 0");
+  if (count == 0) return MM_OK;
+  if (!Ns || !As_host || !Bs_host || !Cs_host) return fail(h, MM_ERR_INVALID, "null array");
+  for (int i = 0; i < count; ++i) {
+    if (Ns[i] < 0) return fail(h, MM_ERR_INVALID, "negative N in group");
+    if (Ns[i] > 0 && (!As_host[i] || !Bs_host[i] || !Cs_host[i])) return fail(h, MM_ERR_INVALID, "null matrix in group");
+  }
+  // Device copies: A, B, C of every problem, 256-byte aligned.
+  std::vector<size_t> off(count, 0);
+  size_t need = 0;
+  for (int i = 0; i < count; ++i) {
+    off[i] = need;
+    need += 3 * align_up(static_cast<size_t>(Ns[i]) * Ns[i] * sizeof(double), kAlign);
+  }
+  if (need > h->ge2e_cap) {
+    if (h->ge2e) cudaFree(h->ge2e);
+    h->ge2e = nullptr;
+    h->ge2e_cap = 0;
+    if (cudaMalloc(&h->ge2e, need) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(h, MM_ERR_NOMEM, "device buffers for the grouped host entry point");
+    }
+    h->ge2e_cap = need;
+  }
+  if (!h->up_stream) {
+    if (cudaStreamCreateWithFlags(&h->up_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&h->down_stream, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(h, MM_ERR_CUDA, "copy streams");
+    }
+  }
+  // Chunks: every problem below N = 768 in a first chunk (little to copy,
+  // quick to compute), then the larger ones in order of size, at most four
+  // chunks of them cut by running flop count; the smallest of those chunks
+  // goes last, so that both the first upload and the last download that
+  // nothing overlaps are short.
+  std::vector<int> small, big;
+  double total_big = 0.0;
+  for (int i = 0; i < count; ++i) {
+    if (Ns[i] <= 0) continue;
+    if (Ns[i] < 768) {
+      small.push_back(i);
+    } else {
+      big.push_back(i);
+      total_big += 2.0 * Ns[i] * static_cast<double>(Ns[i]) * Ns[i];
+    }
+  }
+  if (small.empty() && big.empty()) return MM_OK;
+  std::stable_sort(big.begin(), big.end(), [Ns](int a, int b) { return Ns[a] < Ns[b]; });
+  std::vector<std::vector<int>> bigc;
+  double acc = 0.0;
+  for (int i : big) {
+    if (bigc.empty() || (bigc.size() < 4 && acc >= total_big * bigc.size() / 4.0)) bigc.emplace_back();
+    bigc.back().push_back(i);
+    acc += 2.0 * Ns[i] * static_cast<double>(Ns[i]) * Ns[i];
+  }
+  std::vector<std::vector<int>> chunks;
+  if (!small.empty()) chunks.push_back(small);
+  for (size_t c = 1; c < bigc.size(); ++c) chunks.push_back(bigc[c]);
+  if (!bigc.empty()) chunks.push_back(bigc[0]);
+  while (h->ge2e_events.size() < 2 * chunks.size() + 1) {
+    cudaEvent_t e;
+    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(h, MM_ERR_CUDA, "events");
+    }
+    h->ge2e_events.push_back(e);
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaEvent_t start = h->ge2e_events[2 * chunks.size()];
+  MM_CUDA(h, cudaEventRecord(start, s));  // earlier work on the caller's stream comes first
+  MM_CUDA(h, cudaStreamWaitEvent(h->up_stream, start, 0));
+  auto dptr = [&](int i, int which) {
+    const size_t bytes = align_up(static_cast<size_t>(Ns[i]) * Ns[i] * sizeof(double), kAlign);
+    return reinterpret_cast<double*>(h->ge2e + off[i] + which * bytes);
+  };
+  for (size_t c = 0; c < chunks.size(); ++c) {
+    cudaEvent_t in = h->ge2e_events[2 * c], done = h->ge2e_events[2 * c + 1];
+    std::vector<int> cn;
+    std::vector<const double*> ca, cb;
+    std::vector<double*> cc;
+    for (int i : chunks[c]) {
+      const size_t bytes = static_cast<size_t>(Ns[i]) * Ns[i] * sizeof(double);
+      MM_CUDA(h, cudaMemcpyAsync(dptr(i, 0), As_host[i], bytes, cudaMemcpyHostToDevice, h->up_stream));
+      MM_CUDA(h, cudaMemcpyAsync(dptr(i, 1), Bs_host[i], bytes, cudaMemcpyHostToDevice, h->up_stream));
+      cn.push_back(Ns[i]);
+      ca.push_back(dptr(i, 0));
+      cb.push_back(dptr(i, 1));
+      cc.push_back(dptr(i, 2));
+    }
+    MM_CUDA(h, cudaEventRecord(in, h->up_stream));
+    MM_CUDA(h, cudaStreamWaitEvent(s, in, 0));
+    const mm_status st = mm_gemm_grouped(h, static_cast<int>(cn.size()), cn.data(), ca.data(), cb.data(), cc.data(), s);
+    if (st != MM_OK) return st;
+    MM_CUDA(h, cudaEventRecord(done, s));
+    MM_CUDA(h, cudaStreamWaitEvent(h->down_stream, done, 0));
+    for (size_t q = 0; q < chunks[c].size(); ++q) {
+      const int i = chunks[c][q];
+      MM_CUDA(h, cudaMemcpyAsync(Cs_host[i], cc[q], static_cast<size_t>(Ns[i]) * Ns[i] * sizeof(double),
+                                 cudaMemcpyDeviceToHost, h->down_stream));
+    }
+  }
+  MM_CUDA(h, cudaStreamSynchronize(h->down_stream));
   MM_CUDA(h, cudaStreamSynchronize(s));
   return MM_OK;
 }
