@@ -194,11 +194,15 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
+KERNEL_SOURCES = ("emu_gemm.cu", "common.cuh", "launch.cuh", "modular.cuh", "recombine.cuh")
+
+
 def source_digest() -> str:
+    """Digest of the sources the slice-product kernel is built from."""
     h = hashlib.sha256()
-    path = os.path.join(ROOT, "paper_1012_2273_gb300", "csrc", "emu_gemm.cu")
-    with open(path, "rb") as f:
-        h.update(f.read())
+    for name in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_1012_2273_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
     return h.hexdigest()[:16]
 
 
