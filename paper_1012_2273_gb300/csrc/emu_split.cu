@@ -234,24 +234,27 @@ __device__ __forceinline__ void write_digit_planes(const long long (&Ds)[SP_TILE
 
 // Phase 2 for the modular form with K moduli: the symmetric residues of D
 // modulo m_0..m_{K-1}, one 16-byte vector (8 values) per plane.  |D| <= 2^62
-// is cut into five 13-bit limbs x_l carrying D's sign, and
-//     S = x_0 + x_1 c_1 + ... + x_4 c_4,  c_l = 2^(13 l) mod m (symmetric),
-// is congruent to D with |S| < 2^13 (1 + 4 128) < 2^23, so every step is an
-// exact FP32 integer operation.  r = S - m rint(S RN(1/m)): the product's
+// is cut into LIMBS limbs x_l of b bits carrying D's sign (five of 13 bits,
+// or four of 14 bits when the width is at most 55), and
+//     S = x_0 + x_1 c_1 + ... ,  c_l = 2^(b l) mod m (symmetric),
+// is congruent to D with |S| < 2^b (1 + (LIMBS - 1) 128) < 2^23, so every step
+// is an exact FP32 integer operation.  r = S - m rint(S RN(1/m)): the product's
 // relative error is at most 2^-24, below 1 / (2 |S|), so rint picks the
 // nearest multiple of m exactly as exact division would and |r| <= m/2 <= 128
 // -- an exact bf16 value.  rint is the add-and-subtract of 1.5 2^23.
-template <int K>
+template <int K, int LIMBS>
 __device__ __forceinline__ void write_residue_item(const long long (&D)[8], uint16_t* out, size_t plane) {
-  float x[8][MOD_LIMBS];
+  constexpr int LB = mod_limb_bits(LIMBS);
+  float x[8][LIMBS];
 #pragma unroll
   for (int q = 0; q < 8; ++q) {
     const uint64_t X = D[q] < 0 ? 0ull - static_cast<uint64_t>(D[q]) : static_cast<uint64_t>(D[q]);
-    const float sg = D[q] < 0 ? -1.0f : 1.0f;
+    // sg (2^23 + limb) - sg 2^23 = sg limb, exactly, in one FMA
+    const float sg = D[q] < 0 ? -1.0f : 1.0f, bias = D[q] < 0 ? 8388608.0f : -8388608.0f;
 #pragma unroll
-    for (int l = 0; l < MOD_LIMBS; ++l) {
-      const uint32_t limb = static_cast<uint32_t>(X >> (MOD_LIMB_BITS * l)) & ((1u << MOD_LIMB_BITS) - 1);
-      x[q][l] = sg * (__uint_as_float(0x4B000000u | limb) - 8388608.0f);  // exact: limb < 2^23
+    for (int l = 0; l < LIMBS; ++l) {
+      const uint32_t limb = static_cast<uint32_t>(X >> (LB * l)) & ((1u << LB) - 1);
+      x[q][l] = fmaf(sg, __uint_as_float(0x4B000000u | limb), bias);
     }
   }
   // (the moduli loop stays rolled: unrolled, its 4 K limb constants would
@@ -259,15 +262,15 @@ __device__ __forceinline__ void write_residue_item(const long long (&D)[8], uint
 #pragma unroll 1
   for (int j = 0; j < K; ++j) {
     const float m = c_mod.m_f[j], inv = c_mod.inv_f[j];
-    float c[MOD_LIMBS - 1];
+    float c[LIMBS - 1];
 #pragma unroll
-    for (int l = 1; l < MOD_LIMBS; ++l) c[l - 1] = c_mod.split_c[j][l - 1];
+    for (int l = 1; l < LIMBS; ++l) c[l - 1] = LIMBS == 4 ? c_mod.split_c14[j][l - 1] : c_mod.split_c13[j][l - 1];
     float res[8];
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
       float S = x[q][0];
 #pragma unroll
-      for (int l = 1; l < MOD_LIMBS; ++l) S = fmaf(x[q][l], c[l - 1], S);
+      for (int l = 1; l < LIMBS; ++l) S = fmaf(x[q][l], c[l - 1], S);
       const float qt = fmaf(S, inv, 12582912.0f) - 12582912.0f;
       res[q] = fmaf(-qt, m, S);
     }
@@ -284,7 +287,7 @@ __device__ __forceinline__ void write_residue_item(const long long (&D)[8], uint
 // needed -- each item (output row r, columns c0 + 8 cg ..) loads its 8 values
 // straight from A (a warp: 4 rows x 512 contiguous bytes) and writes one
 // 16-byte vector per plane (4 rows x 128 contiguous bytes).
-template <int K>
+template <int K, int LIMBS>
 __device__ __forceinline__ void residue_tile_a(const uint64_t* src, int n, int r0, int c0, const int* ex_s,
                                                int width, uint16_t* dst, int k_pad, size_t plane,
                                                bool* nonfinite) {
@@ -299,14 +302,14 @@ __device__ __forceinline__ void residue_tile_a(const uint64_t* src, int n, int r
     for (int q = 0; q < 8; ++q) bits[q] = (i < n && j0 + q < n) ? src[static_cast<size_t>(i) * n + j0 + q] : 0ull;
 #pragma unroll
     for (int q = 0; q < 8; ++q) D[q] = (i < n && j0 + q < n) ? fixed_point(bits[q], ex_s[r], width, nonfinite) : 0;
-    write_residue_item<K>(D, dst + static_cast<size_t>(i) * k_pad + j0, plane);
+    write_residue_item<K, LIMBS>(D, dst + static_cast<size_t>(i) * k_pad + j0, plane);
   }
 }
 
 // Modular form, B^T tile, after the transpose into Ds: item (r, cg) with two
 // lanes per row -- every 8-byte shared load of a half-warp hits 16 distinct
 // bank pairs, and each row's two vectors per plane fill one 32-byte sector.
-template <int K>
+template <int K, int LIMBS>
 __device__ __forceinline__ void residue_tile_from_smem(const long long (&Ds)[SP_TILE][SP_TILE + 1], uint16_t* dst,
                                                        int r0, int c0, int k_pad, size_t plane) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -316,7 +319,7 @@ __device__ __forceinline__ void residue_tile_from_smem(const long long (&Ds)[SP_
     long long D[8];
 #pragma unroll
     for (int q = 0; q < 8; ++q) D[q] = Ds[r][8 * cg + q];
-    write_residue_item<K>(D, dst + static_cast<size_t>(r0 + r) * k_pad + c0 + 8 * cg, plane);
+    write_residue_item<K, LIMBS>(D, dst + static_cast<size_t>(r0 + r) * k_pad + c0 + 8 * cg, plane);
   }
 }
 
@@ -329,10 +332,17 @@ template <int K>
 __device__ __forceinline__ void residue_tile(bool is_a, const uint64_t* src, int n, int r0, int c0, const int* ex_s,
                                              int width, const long long (&Ds)[SP_TILE][SP_TILE + 1], uint16_t* dst,
                                              int k_pad, size_t plane, bool* nonfinite) {
-  if (is_a)
-    residue_tile_a<K>(src, n, r0, c0, ex_s, width, dst, k_pad, plane, nonfinite);
-  else
-    residue_tile_from_smem<K>(Ds, dst, r0, c0, k_pad, plane);
+  if (width <= 55) {  // |D| <= 2^55 < 2^56: four 14-bit limbs
+    if (is_a)
+      residue_tile_a<K, 4>(src, n, r0, c0, ex_s, width, dst, k_pad, plane, nonfinite);
+    else
+      residue_tile_from_smem<K, 4>(Ds, dst, r0, c0, k_pad, plane);
+  } else {
+    if (is_a)
+      residue_tile_a<K, 5>(src, n, r0, c0, ex_s, width, dst, k_pad, plane, nonfinite);
+    else
+      residue_tile_from_smem<K, 5>(Ds, dst, r0, c0, k_pad, plane);
+  }
 }
 
 __global__ void __launch_bounds__(SP_THREADS) split_kernel(const __grid_constant__ SplitArgs args) {

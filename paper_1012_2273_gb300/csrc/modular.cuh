@@ -21,8 +21,10 @@ namespace mmk {
 
 constexpr int MOD_COUNT = 16;     // moduli available; k = 2..16 are used
 constexpr int MOD_MAX_BITS = 62;  // fixed-point width limit: |A_int| <= 2^62 splits into 5 limbs of 13 bits
-constexpr int MOD_LIMBS = 5;
-constexpr int MOD_LIMB_BITS = 13;
+// The split cuts |D| into L limbs of 13 (L = 5, any width) or 14 bits (L = 4,
+// widths up to 55): with symmetric c_l = 2^(b l) mod m, |sum x_l c_l| stays
+// below 2^b (1 + (L - 1) 128) < 2^23 either way.
+__host__ __device__ constexpr int mod_limb_bits(int limbs) { return limbs == 4 ? 14 : 13; }
 
 // The moduli, largest first: pairwise coprime, each at most 256.
 __host__ __device__ constexpr uint32_t mod_value(int j) {
@@ -103,9 +105,10 @@ __host__ __device__ constexpr float pow2f(int e) {
 }
 
 struct ModTables {
-  // split: the symmetric residue of 2^(13 l) modulo m_j (l = 1..4), m_j and
-  // RN(1/m_j) as floats
-  float split_c[MOD_COUNT][MOD_LIMBS - 1];
+  // split: the symmetric residue of 2^(13 l) (l = 1..4) and of 2^(14 l)
+  // (l = 1..3) modulo m_j, m_j and RN(1/m_j) as floats
+  float split_c13[MOD_COUNT][4];
+  float split_c14[MOD_COUNT][3];
   uint32_t m_u[MOD_COUNT];
   float m_f[MOD_COUNT];
   float inv_f[MOD_COUNT];
@@ -129,11 +132,17 @@ __host__ __device__ constexpr ModTables make_mod_tables() {
   ModTables t{};
   for (int j = 0; j < MOD_COUNT; ++j) {
     const uint32_t m = mod_value(j);
-    for (int l = 1; l < MOD_LIMBS; ++l) {
-      uint64_t p = 1;
-      for (int b = 0; b < MOD_LIMB_BITS * l; ++b) p = (p * 2) % m;
-      const int64_t sym = (p > m / 2) ? static_cast<int64_t>(p) - m : static_cast<int64_t>(p);
-      t.split_c[j][l - 1] = static_cast<float>(sym);
+    for (int l = 1; l <= 4; ++l) {
+      for (int bits = 13; bits <= 14; ++bits) {
+        if (bits == 14 && l == 4) continue;
+        uint64_t p = 1;
+        for (int b = 0; b < bits * l; ++b) p = (p * 2) % m;
+        const int64_t sym = (p > m / 2) ? static_cast<int64_t>(p) - m : static_cast<int64_t>(p);
+        if (bits == 13)
+          t.split_c13[j][l - 1] = static_cast<float>(sym);
+        else
+          t.split_c14[j][l - 1] = static_cast<float>(sym);
+      }
     }
     t.m_u[j] = m;
     t.m_f[j] = static_cast<float>(m);
