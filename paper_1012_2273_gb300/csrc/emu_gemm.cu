@@ -424,6 +424,7 @@ __global__ void __launch_bounds__(EM_THREADS, 1)
                                 ? args.tilebuf + P->slot_base + static_cast<long long>(U.tile_local) * P->nslots * SLOT
                                 : my_scratch;
       int L, t0;
+      uint32_t pend[kMod ? HALF / 4 : 1];  // modular form: residues of a pair's first modulus
       for (int p = p0; p < p1 && ok; ++slot) {
         const int np = kMod ? 1 : emu_segment(p, p1, maxp, &L, &t0);
         p += np;
@@ -458,36 +459,64 @@ __global__ void __launch_bounds__(EM_THREADS, 1)
         if (!ok) break;
         const uint32_t bias = static_cast<uint32_t>(nchunks) * EM_MAGIC;
         if (kMod) {
-          // The exact sum S = sum_j r_a r_b of this modulus m (|S| <= n 2^14
-          // <= 2^30) becomes t = (S mod m) y mod m in [0, m), one byte: x =
-          // S + (a multiple of m, at least 2^30) is non-negative and below
-          // 2^31 + 2^8, where floor(x / m) = umulhi(x, ceil(2^39 / m)) >> 7
-          // exactly; y = (M_k / m)^-1 mod m prepares the Chinese remainder
-          // sum.  Slot layout: [col / 16][row][16 bytes], one 16-byte vector
-          // per 16 columns, a warp's 32 rows contiguous.
+          // The exact sum S = sum_j r_a r_b of modulus m_j (|S| <= n 2^14 <=
+          // 2^30) becomes t = (S mod m) cy mod m in [0, m): x = S + (a
+          // multiple of m, at least 2^30) is non-negative and below 2^31 +
+          // 2^8, where floor(x / m) = umulhi(x, ceil(2^39 / m)) >> 7 exactly.
+          // The first modulus of a pair keeps its t (4 per word) until the
+          // second arrives; then the group residue T = t_a m_b + t_b m_a,
+          // reduced below m_a m_b < 2^16, is stored as 16 bits (a lone last
+          // modulus stores its t).  Slot layout: [col / 8][row][8 x 16 bits],
+          // one 16-byte vector per 8 columns, a warp's 32 rows contiguous.
           const int j = slot;
-          const uint32_t m = c_mod.m_u[j], magic = c_mod.magic[j], y = c_mod.y[s][j];
+          const uint32_t m = c_mod.m_u[j], magic = c_mod.magic[j], cy = c_mod.cy[s][j];
           const uint32_t shift_in = c_mod.bias[j] - bias;  // x = acc - bias + bias_j
-          uint8_t* dst = reinterpret_cast<uint8_t*>(args.tilebuf + P->slot_base) +
-                         (static_cast<size_t>(U.tile_local) * P->nslots + j) * (EM_BM * BN) +
-                         static_cast<size_t>(h * HALF / 16) * (EM_BM * 16) + r_in_tile * 16;
+          uint32_t tw[HALF / 4];
 #pragma unroll
-          for (int c = 0; c < HALF; c += 16) {
+          for (int c = 0; c < HALF; c += 4) {
+            uint32_t word = 0;
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+              const uint32_t x = acc[c + b] + shift_in;
+              const uint32_t r = x - (__umulhi(x, magic) >> 7) * m;
+              const uint32_t pr = r * cy;
+              const uint32_t t = pr - (__umulhi(pr, magic) >> 7) * m;
+              word |= t << (8 * b);
+            }
+            tw[c / 4] = word;
+          }
+          if ((j & 1) == 0 && j + 1 < s) {  // first of a pair
+#pragma unroll
+            for (int i = 0; i < HALF / 4; ++i) pend[i] = tw[i];
+            continue;
+          }
+          const bool paired = (j & 1) != 0;
+          const uint32_t ma = paired ? c_mod.m_u[j - 1] : 0u;
+          const uint32_t Mg = ma * m;
+          uint16_t* dst = reinterpret_cast<uint16_t*>(args.tilebuf + P->slot_base) +
+                          (static_cast<size_t>(U.tile_local) * P->nslots + (j >> 1)) * (EM_BM * BN) +
+                          static_cast<size_t>(h * HALF / 8) * (EM_BM * 8) + r_in_tile * 8;
+#pragma unroll
+          for (int c = 0; c < HALF; c += 8) {
             uint32_t w[4];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-              uint32_t word = 0;
+            for (int q2 = 0; q2 < 4; ++q2) {
+              uint32_t half16[2];
 #pragma unroll
-              for (int b = 0; b < 4; ++b) {
-                const uint32_t x = acc[c + 4 * q + b] + shift_in;
-                const uint32_t r = x - (__umulhi(x, magic) >> 7) * m;
-                const uint32_t pr = r * y;
-                const uint32_t t = pr - (__umulhi(pr, magic) >> 7) * m;
-                word |= t << (8 * b);
+              for (int b = 0; b < 2; ++b) {
+                const int col = c + 2 * q2 + b;
+                const uint32_t tb = (tw[col >> 2] >> (8 * (col & 3))) & 255u;
+                uint32_t T = tb;
+                if (paired) {
+                  const uint32_t ta = (pend[col >> 2] >> (8 * (col & 3))) & 255u;
+                  T = ta * m + tb * ma;
+                  if (T >= Mg) T -= Mg;
+                }
+                half16[b] = T;
               }
-              w[q] = word;
+              w[q2] = half16[0] | (half16[1] << 16);
             }
-            __stcs(reinterpret_cast<uint4*>(dst + (c / 16) * (EM_BM * 16)), make_uint4(w[0], w[1], w[2], w[3]));
+            __stcs(reinterpret_cast<uint4*>(dst + (c / 8) * (EM_BM * 8)), make_uint4(w[0], w[1], w[2], w[3]));
           }
           continue;
         }

@@ -60,11 +60,15 @@ __host__ __device__ inline int emu_tile_slots(int s, int G, int max_pairs) {
   return n;
 }
 
-// Modular form: the pairs of a tile are its k moduli (one residue product
-// each, each its own segment), numbered 0..k-1 and cut into G contiguous groups.
+// Modular form: the products of a tile are its k moduli (one residue
+// product each, each its own segment), numbered 0..k-1.  Units are cut at
+// residue-group boundaries (pairs of moduli, modular.cuh): group range g of G
+// holds groups [g ng / G, (g+1) ng / G) of the ng = ceil(k/2).
 __host__ __device__ inline void mod_group_range(int k, int G, int g, int* p0, int* p1) {
-  *p0 = g * k / G;
-  *p1 = (g + 1) * k / G;
+  const int ng = (k + 1) / 2;
+  const int g0 = g * ng / G, g1 = (g + 1) * ng / G;
+  *p0 = 2 * g0;
+  *p1 = 2 * g1 < k ? 2 * g1 : k;
 }
 
 template <bool kMod>

@@ -311,14 +311,14 @@ struct EmuGroup {
 // (The modular form writes its residue slots whatever G is, so they cost
 // nothing extra there.)
 int choose_groups_single(int tiles, int s, bool modular, int kb, int sms, int max_pairs) {
-  const int P = modular ? s : mmk::emu_pairs(s);
+  const int P = modular ? mmk::mod_groups(s) : mmk::emu_pairs(s);
   const double t_kb = 0.35e-6, bw = 6.0e12, slot_bytes = 128.0 * 256.0 * 4.0;
   int best = 1;
   double best_t = 1e30;
   for (int G = 1; G <= P; ++G) {
     const long long units = static_cast<long long>(tiles) * G;
     const long long waves = (units + sms - 1) / sms;
-    const int longest = (P + G - 1) / G;
+    const int longest = (P + G - 1) / G * (modular ? 2 : 1);  // products in the longest unit
     double t = static_cast<double>(waves) * longest * kb * t_kb;
     if (G > 1 && !modular) t += 2.0 * tiles * mmk::emu_tile_slots(s, G, max_pairs) * slot_bytes / bw;
     if (t < best_t * 0.98) {  // a new group count must win by 2%
@@ -392,16 +392,19 @@ mm_status layout_group(mm_handle h, EmuGroup& g, char* base) {
       G = std::max(1, std::min(G, P));
     }
     if (modular) {
-      // One byte per output and modulus: k slots of 128 x bn bytes per tile,
-      // always recombined by the separate pass.  The slots are written
-      // whatever the grouping, so grouped calls give every modulus its own
-      // unit: the most, equal, units for the dynamic scheduler.
-      if (g.groups == 0 && g.ps.size() > 1) G = P;
+      // Two bytes per output and residue group (pair of moduli): ceil(k/2)
+      // slots of 128 x bn 16-bit entries per tile, always recombined by the
+      // separate pass.  The slots are written whatever the grouping, so
+      // grouped calls give every residue group its own unit: the most,
+      // equal, units for the dynamic scheduler.
+      const int NG = mmk::mod_groups(p.s);
+      if (g.groups == 0 && g.ps.size() > 1) G = NG;
+      G = std::min(G, NG);
       p.groups = G;
-      p.nslots = p.s;
+      p.nslots = NG;
       p.defer = 1;
       p.slot_base = g.tilebuf_elems;
-      g.tilebuf_elems += static_cast<long long>(tiles) * p.nslots * (slot / 4);
+      g.tilebuf_elems += static_cast<long long>(tiles) * p.nslots * (slot / 2);
       if (g.tabled) {
         for (int gi = 0; gi < G; ++gi) {
           int p0, p1;

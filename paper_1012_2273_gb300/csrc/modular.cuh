@@ -104,6 +104,11 @@ __host__ __device__ constexpr float pow2f(int e) {
   return r;
 }
 
+// Residue groups: the moduli are taken in pairs (0,1), (2,3), ..., with the
+// last one alone when k is odd; group g has modulus M_g = m_2g m_2g+1 < 2^16.
+__host__ __device__ constexpr int mod_groups(int k) { return (k + 1) / 2; }
+constexpr int MOD_GROUPS = MOD_COUNT / 2;
+
 struct ModTables {
   // split: the symmetric residue of 2^(13 l) (l = 1..4) and of 2^(14 l)
   // (l = 1..3) modulo m_j, m_j and RN(1/m_j) as floats
@@ -115,14 +120,19 @@ struct ModTables {
   // slice-product epilogue: ceil(2^39 / m_j) (so that floor(x / m_j) =
   // umulhi(x, magic) >> 7 for 0 <= x < 2^31 + 2^8), a multiple of m_j at least
   // 2^30 (added to make a sum of at most 2^30 in magnitude non-negative),
-  // and, per k, y = (M_k / m_j)^-1 mod m_j
+  // and, per k, the multiplier cy of the residue: with W_g = M_k / M_g and
+  // w_g = W_g^-1 mod M_g for j's group g, the group residue
+  //     T_g = X w_g mod M_g
+  // is t_a m_b + t_b m_a (mod M_g) for a pair (a, b), t_j = (X mod m_j) cy_j
+  // mod m_j with cy_a = w_g m_b^-1 mod m_a (and symmetrically), and t_a itself
+  // with cy_a = w_g mod m_a for a lone modulus
   uint32_t magic[MOD_COUNT];
   uint32_t bias[MOD_COUNT];
-  uint32_t y[MOD_COUNT + 1][MOD_COUNT];
-  // recombination, per k: limbs of M_k / m_j and of M_k; V 2^-qshift is
-  // formed in FP32 and multiplied by qscale = 2^qshift / M_k to estimate
-  // round(V / M_k)
-  uint32_t mj[MOD_COUNT + 1][MOD_COUNT][4];
+  uint32_t cy[MOD_COUNT + 1][MOD_COUNT];
+  // recombination, per k: limbs of W_g = M_k / M_g and of M_k; V = sum_g
+  // T_g W_g is congruent to X modulo M_k; V 2^-qshift is formed in FP32 and
+  // multiplied by qscale = 2^qshift / M_k to estimate round(V / M_k)
+  uint32_t wg[MOD_COUNT + 1][MOD_GROUPS][4];
   uint32_t mk[MOD_COUNT + 1][4];
   int qshift[MOD_COUNT + 1];
   float qscale[MOD_COUNT + 1];
@@ -153,11 +163,19 @@ __host__ __device__ constexpr ModTables make_mod_tables() {
   for (int k = 1; k <= MOD_COUNT; ++k) {
     const Limbs4 M = mod_product(k);
     for (int l = 0; l < 4; ++l) t.mk[k][l] = M.w[l];
-    for (int j = 0; j < k; ++j) {
-      const uint32_t m = mod_value(j);
-      const Limbs4 Mj = limbs_div_small(M, m);
-      for (int l = 0; l < 4; ++l) t.mj[k][j][l] = Mj.w[l];
-      t.y[k][j] = inv_mod(limbs_mod_small(Mj, m), m);
+    for (int g = 0; g < mod_groups(k); ++g) {
+      const int a = 2 * g, b = 2 * g + 1;
+      const uint32_t ma = mod_value(a), mb = b < k ? mod_value(b) : 1u;
+      const uint32_t Mg = ma * mb;
+      const Limbs4 Wg = limbs_div_small(M, Mg);
+      for (int l = 0; l < 4; ++l) t.wg[k][g][l] = Wg.w[l];
+      const uint32_t w = inv_mod(limbs_mod_small(Wg, Mg), Mg);
+      if (b < k) {
+        t.cy[k][a] = static_cast<uint32_t>(static_cast<uint64_t>(w % ma) * inv_mod(mb % ma, ma) % ma);
+        t.cy[k][b] = static_cast<uint32_t>(static_cast<uint64_t>(w % mb) * inv_mod(ma % mb, mb) % mb);
+      } else {
+        t.cy[k][a] = w % ma;
+      }
     }
     const int bits = limbs_bit_length(M);
     t.qshift[k] = bits - 31;

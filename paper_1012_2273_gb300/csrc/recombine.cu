@@ -71,49 +71,51 @@ __global__ void __launch_bounds__(256) slots_recombine_kernel(const __grid_const
 }
 
 // Recombination of the modular form with K moduli, after the slice-product
-// kernel: one thread per 4 consecutive outputs of a tile row (one 4-byte word
-// per modulus; 4 lanes read a row's 16 contiguous bytes, a warp 8 rows).
-// With t_j = (X mod m_j) (M/m_j)^-1 mod m_j from the epilogue,
-// V = sum_j t_j (M/m_j) is congruent to X modulo M = m_1...m_K and
-// V / M = sum_j t_j / m_j < K.  Because |X| <= M/4 (the width rule),
-// X = V - round(V/M) M, and round(V/M) is found from a 24-bit estimate of V:
-// its relative error is a few 2^-24, far inside the quarter-modulus margin.
-// V is summed in four 64-bit accumulators of 32-bit limbs (each term below
-// 2^40, K of them), carried, and X is formed modulo 2^128, exact since
-// |X| < 2^126.  Then one rounding: c = RN(X) 2^(e_i + f_k - 2 beta).  The
-// four outputs' multiply-add chains are interleaved.
+// kernel: one thread per 4 consecutive outputs of a tile row (one 8-byte
+// word per residue group; 2 lanes read a row's 16 contiguous bytes, a warp 16
+// rows).  With T_g = X w_g mod M_g from the epilogue (w_g = (M/M_g)^-1 mod
+// M_g, M_g the product of group g's moduli), V = sum_g T_g (M/M_g) is
+// congruent to X modulo M = m_1...m_K and V / M = sum_g T_g / M_g < ceil(K/2).
+// Because |X| <= M/4 (the width rule), X = V - round(V/M) M, and round(V/M)
+// is found from a 24-bit estimate of V: its relative error is a few 2^-24,
+// far inside the quarter-modulus margin.  V is summed in four 64-bit
+// accumulators of 32-bit limbs (each term below 2^48, at most 8 of them),
+// carried, and X is formed modulo 2^128, exact since |X| < 2^126.  Then one
+// rounding: c = RN(X) 2^(e_i + f_k - 2 beta).  The four outputs' multiply-add
+// chains are interleaved.
 template <int K, int BN>
 __global__ void __launch_bounds__(256) mod_recombine_kernel(const __grid_constant__ EmuArgs args, int tile0) {
-  constexpr int PER_TILE = EM_BM * BN / 4;  // threads per tile
-  constexpr size_t SLOT_BYTES = static_cast<size_t>(EM_BM) * BN;
-  constexpr int QS = limbs_bit_length(mod_product(K)) - 31;  // V 2^-QS < 2^35
+  constexpr int NG = mod_groups(K);
+  constexpr int PER_TILE = EM_BM * BN / 4;          // threads per tile
+  constexpr size_t SLOT = static_cast<size_t>(EM_BM) * BN;  // 16-bit entries per slot
+  constexpr int QS = limbs_bit_length(mod_product(K)) - 31;  // V 2^-QS < 2^34
   const long long item = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
   const int tile = tile0 + static_cast<int>(item / PER_TILE);
   const int in_tile = static_cast<int>(item % PER_TILE);
   const Problem* P = args.table ? &args.table[find_problem(args.table, args.count, tile)] : &args.single;
   const int tile_local = tile - P->tile_begin;
   if (P->beta <= 0 || P->s != K || tile_local < 0 || tile_local >= P->tiles_m * P->tiles_n) return;
-  // in_tile = ((c16 * 16 + rblock) * 8 + r8) * 4 + q: 16-column group c16,
-  // row r = 8 rblock + r8, word q of the row's 16 bytes
-  const int q = in_tile & 3, r = (in_tile >> 2) & (EM_BM - 1), c16 = in_tile >> 9;
+  // in_tile = ((c8 * 128 + r) * 2 + q): 8-column group c8, row r, half q of
+  // the row's 16 bytes
+  const int q = in_tile & 1, r = (in_tile >> 1) & (EM_BM - 1), c8 = in_tile >> 8;
   int tm, tn;
   emu_tile_coords(tile_local, P->tiles_m, P->tiles_n, &tm, &tn);
-  const int n = P->n, row = tm * EM_BM + r, col0 = tn * BN + 16 * c16 + 4 * q;
+  const int n = P->n, row = tm * EM_BM + r, col0 = tn * BN + 8 * c8 + 4 * q;
   if (row >= n || col0 >= n) return;
-  const uint8_t* at = reinterpret_cast<const uint8_t*>(args.tilebuf + P->slot_base) +
-                      static_cast<size_t>(tile_local) * K * SLOT_BYTES + static_cast<size_t>(c16) * (EM_BM * 16) +
-                      r * 16 + q * 4;
-  uint32_t w[K];
+  const uint16_t* at = reinterpret_cast<const uint16_t*>(args.tilebuf + P->slot_base) +
+                       static_cast<size_t>(tile_local) * NG * SLOT + static_cast<size_t>(c8) * (EM_BM * 8) + r * 8 +
+                       q * 4;
+  uint2 v[NG];
 #pragma unroll
-  for (int j = 0; j < K; ++j) w[j] = __ldcs(reinterpret_cast<const unsigned int*>(at + j * SLOT_BYTES));
+  for (int g = 0; g < NG; ++g) v[g] = __ldcs(reinterpret_cast<const uint2*>(at + g * SLOT));
   uint64_t a[4][4] = {};
 #pragma unroll
-  for (int j = 0; j < K; ++j) {
+  for (int g = 0; g < NG; ++g) {
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
-      const uint32_t t = __byte_perm(w[j], 0u, 0x4440u + c);
+      const uint32_t T = ((c < 2 ? v[g].x : v[g].y) >> (16 * (c & 1))) & 0xFFFFu;
 #pragma unroll
-      for (int l = 0; l < 4; ++l) a[c][l] += static_cast<uint64_t>(t) * c_mod.mj[K][j][l];
+      for (int l = 0; l < 4; ++l) a[c][l] += static_cast<uint64_t>(T) * c_mod.wg[K][g][l];
     }
   }
   const uint64_t m_lo = (static_cast<uint64_t>(c_mod.mk[K][1]) << 32) | c_mod.mk[K][0];
