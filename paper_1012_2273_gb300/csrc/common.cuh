@@ -34,7 +34,8 @@ struct Problem {
   int m_pad;           // rows of an A plane (multiple of 128)
   int n_pad;           // rows of a B^T plane (multiple of the tile width)
   int k_pad;           // columns of a plane (multiple of 64)
-  int split_begin;     // first split tile of this problem (scale/split kernels)
+  int split_begin;     // first split tile of this problem (split kernel)
+  int absmax_begin;    // first block of this problem in the maxima kernel
   int s;               // digits per value (digit form, 1..8) or moduli (modular form, 2..16)
   int beta;            // modular form: fixed-point width of the operands; 0 = digit form
   int groups;          // digit-pair groups per tile: work units per tile of the slice-product kernel

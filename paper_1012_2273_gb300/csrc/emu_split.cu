@@ -136,71 +136,92 @@ __device__ __forceinline__ void digits_of(int64_t D, float (&out)[S]) {
 }
 
 // Row maxima of |A| and column maxima of |B| (as bit patterns; for finite
-// values the unsigned order of |v|'s pattern is the order of |v|).  One 64 x 64
-// tile per CTA; reads are coalesced along the rows of the source, partial
-// maxima are reduced in registers and warps, and one global atomicMax per
-// row (A) or column (B) per tile publishes them.
+// values the unsigned order of |v|'s pattern is the order of |v|).
+//   A: one warp per row, AM_ROWS rows per block; the lanes stride along the
+//      row (coalesced), 8 loads in flight each, and lane 0 stores the row's
+//      maximum (no atomics; every row of the problem is written).
+//   B: one block per AM_BCOLS columns x AM_BROWS rows; 4 row phases of 64
+//      columns (a warp reads 256 contiguous bytes of a row), reduced through
+//      shared memory, one atomicMax per column per block (the column maxima
+//      start at zero).
+constexpr int AM_ROWS = SP_THREADS / 32;
+constexpr int AM_BCOLS = 64;
+constexpr int AM_BROWS = 128;
+
+__device__ __forceinline__ int absmax_find(const SplitArgs& a, int block, const Problem** P) {
+  if (!a.table) {
+    *P = &a.single;
+    return 0;
+  }
+  int lo = 0, hi = a.count - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (a.table[mid].absmax_begin <= block) lo = mid; else hi = mid - 1;
+  }
+  *P = &a.table[lo];
+  return lo;
+}
+
 __global__ void __launch_bounds__(SP_THREADS) absmax_kernel(const __grid_constant__ SplitArgs args) {
-  __shared__ unsigned long long part[SP_THREADS / SP_TILE][SP_TILE];
+  __shared__ unsigned long long part[SP_THREADS / AM_BCOLS][AM_BCOLS];
   const Problem* P;
-  const int pi = split_find(args, blockIdx.x, &P);
+  const int pi = absmax_find(args, blockIdx.x, &P);
   const int n = P->n;
-  const int kt = P->k_pad / SP_TILE;
-  const int a_tiles = (P->m_pad / SP_TILE) * kt;
-  int local = blockIdx.x - (args.table ? P->split_begin : 0);
-  const bool is_a = local < a_tiles;
-  if (!is_a) local -= a_tiles;
-  const int r0 = (local / kt) * SP_TILE;  // A: rows i; B^T: columns k of B
-  const int c0 = (local % kt) * SP_TILE;  // A: columns j; B^T: rows j of B
-  if (r0 >= n || c0 >= n) return;          // tile lies in the padding
+  const int a_blocks = P->m_pad > 0 ? (n + AM_ROWS - 1) / AM_ROWS : 0;
+  int local = blockIdx.x - (args.table ? P->absmax_begin : 0);
   const int off = args.max_offset ? args.max_offset[pi] : 0;
-  const uint64_t* src = reinterpret_cast<const uint64_t*>(is_a ? P->A : P->B);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  if (is_a) {
-    // warp w: rows r0 + w + 8q (q = 0..7); lanes cover the 64 columns twice.
-    // All 16 loads of a lane are issued before any reduction.
-    constexpr int RW = SP_TILE / (SP_THREADS / 32);  // rows per warp
-    unsigned long long m[RW];
-#pragma unroll
-    for (int q = 0; q < RW; ++q) {
-      const int i = r0 + warp + 8 * q;
-      const int j0 = c0 + lane, j1 = c0 + lane + 32;
-      unsigned long long a = 0, b = 0;
-      if (i < n && j0 < n) a = src[static_cast<size_t>(i) * n + j0] & 0x7FFFFFFFFFFFFFFFull;
-      if (i < n && j1 < n) b = src[static_cast<size_t>(i) * n + j1] & 0x7FFFFFFFFFFFFFFFull;
-      m[q] = a > b ? a : b;
-    }
-#pragma unroll
-    for (int q = 0; q < RW; ++q) {
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        const unsigned long long v = __shfl_xor_sync(0xffffffffu, m[q], o);
-        m[q] = v > m[q] ? v : m[q];
-      }
-      const int i = r0 + warp + 8 * q;
-      if (lane == 0 && i < n && m[q]) atomicMax(reinterpret_cast<unsigned long long*>(&args.a_maxbits[off + i]), m[q]);
-    }
-  } else {
-    // thread: column k = r0 + (tid % 64) of B over rows j = c0 + tid / 64 + 4q
-    const int c = threadIdx.x % SP_TILE, q0 = threadIdx.x / SP_TILE;
-    const int k = r0 + c;
+  if (local < a_blocks) {
+    const int i = local * AM_ROWS + warp;
+    if (i >= n) return;
+    const uint64_t* row = reinterpret_cast<const uint64_t*>(P->A) + static_cast<size_t>(i) * n;
     unsigned long long m = 0;
-    if (k < n) {
+    for (int j0 = 0; j0 < n; j0 += 32 * 8) {
+      unsigned long long v[8];
 #pragma unroll
-      for (int q = q0; q < SP_TILE; q += SP_THREADS / SP_TILE) {
-        const int j = c0 + q;
-        const unsigned long long v = j < n ? src[static_cast<size_t>(j) * n + k] & 0x7FFFFFFFFFFFFFFFull : 0ull;
-        m = v > m ? v : m;
+      for (int q = 0; q < 8; ++q) {
+        const int j = j0 + 32 * q + lane;
+        v[q] = j < n ? row[j] & 0x7FFFFFFFFFFFFFFFull : 0ull;
       }
-    }
-    part[q0][c] = m;
-    __syncthreads();
-    if (threadIdx.x < SP_TILE && r0 + threadIdx.x < n) {
-      unsigned long long mm = 0;
 #pragma unroll
-      for (int w = 0; w < SP_THREADS / SP_TILE; ++w) mm = part[w][threadIdx.x] > mm ? part[w][threadIdx.x] : mm;
-      if (mm) atomicMax(reinterpret_cast<unsigned long long*>(&args.b_maxbits[off + r0 + threadIdx.x]), mm);
+      for (int q = 0; q < 8; ++q) m = v[q] > m ? v[q] : m;
     }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned long long v = __shfl_xor_sync(0xffffffffu, m, o);
+      m = v > m ? v : m;
+    }
+    if (lane == 0) args.a_maxbits[off + i] = m;
+    return;
+  }
+  local -= a_blocks;
+  const int nbc = (n + AM_BCOLS - 1) / AM_BCOLS;
+  const int k0 = (local % nbc) * AM_BCOLS, j0 = (local / nbc) * AM_BROWS;
+  const int c = threadIdx.x % AM_BCOLS, ph = threadIdx.x / AM_BCOLS;
+  constexpr int PHASES = SP_THREADS / AM_BCOLS;
+  const int k = k0 + c;
+  const uint64_t* src = reinterpret_cast<const uint64_t*>(P->B);
+  unsigned long long m = 0;
+  if (k < n) {
+    for (int jj = ph; jj < AM_BROWS; jj += PHASES * 8) {
+      unsigned long long v[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int j = j0 + jj + PHASES * q;
+        v[q] = (jj + PHASES * q < AM_BROWS && j < n) ? src[static_cast<size_t>(j) * n + k] & 0x7FFFFFFFFFFFFFFFull
+                                                      : 0ull;
+      }
+#pragma unroll
+      for (int q = 0; q < 8; ++q) m = v[q] > m ? v[q] : m;
+    }
+  }
+  part[ph][c] = m;
+  __syncthreads();
+  if (threadIdx.x < AM_BCOLS && k0 + threadIdx.x < n) {
+    unsigned long long mm = 0;
+#pragma unroll
+    for (int w = 0; w < PHASES; ++w) mm = part[w][threadIdx.x] > mm ? part[w][threadIdx.x] : mm;
+    if (mm) atomicMax(reinterpret_cast<unsigned long long*>(&args.b_maxbits[off + k0 + threadIdx.x]), mm);
   }
 }
 
@@ -445,7 +466,14 @@ int split_tiles(const Problem& p) {
   return (p.m_pad / SP_TILE + p.n_pad / SP_TILE) * (p.k_pad / SP_TILE);
 }
 
-cudaError_t split_launch(const Problem* table, const Problem* single, int count, int total_tiles,
+int absmax_blocks(const Problem& p) {
+  if (p.n <= 0) return 0;
+  const int a = p.m_pad > 0 ? (p.n + AM_ROWS - 1) / AM_ROWS : 0;
+  const int b = p.n_pad > 0 ? ((p.n + AM_BCOLS - 1) / AM_BCOLS) * ((p.n + AM_BROWS - 1) / AM_BROWS) : 0;
+  return a + b;
+}
+
+cudaError_t split_launch(const Problem* table, const Problem* single, int count, int total_tiles, int total_absmax,
                          uint64_t* a_maxbits, uint64_t* b_maxbits, const int* max_offset, int* status,
                          cudaStream_t stream) {
   if (total_tiles <= 0) return cudaSuccess;
@@ -458,7 +486,8 @@ cudaError_t split_launch(const Problem* table, const Problem* single, int count,
   args.b_maxbits = b_maxbits;
   args.max_offset = max_offset;
   args.status = status;
-  absmax_kernel<<<total_tiles, SP_THREADS, 0, stream>>>(args);
+  const int am_blocks = table ? total_absmax : absmax_blocks(*single);
+  if (am_blocks > 0) absmax_kernel<<<am_blocks, SP_THREADS, 0, stream>>>(args);
   cudaError_t err = cudaGetLastError();
   if (err != cudaSuccess) return err;
   split_kernel<<<total_tiles, SP_THREADS, 0, stream>>>(args);

@@ -123,7 +123,9 @@ cudaError_t native_launch(const Problem* table, const Problem* single, int count
 
 // emu_split.cu
 int split_tiles(const Problem& p);
-cudaError_t split_launch(const Problem* table, const Problem* single, int count, int total_tiles,
+int absmax_blocks(const Problem& p);
+// total_absmax: sum of absmax_blocks over the table (ignored for a single problem)
+cudaError_t split_launch(const Problem* table, const Problem* single, int count, int total_tiles, int total_absmax,
                          uint64_t* a_maxbits, uint64_t* b_maxbits, const int* max_offset, int* status,
                          cudaStream_t stream);
 

@@ -295,7 +295,7 @@ struct EmuGroup {
   std::vector<int> max_off;        // offset of problem p in the maxbits arrays
   std::vector<CUtensorMap> maps;   // 2 per problem
   std::vector<int4> units;         // grouped launches: {problem, tile, group, cost}
-  int total_tiles = 0, total_split = 0, total_units = 0, max_rows = 0, scratch_slots = 1;
+  int total_tiles = 0, total_split = 0, total_absmax = 0, total_units = 0, max_rows = 0, scratch_slots = 1;
   long long tilebuf_elems = 0;
   // byte offsets inside the group's region of the arena
   size_t amax = 0, bmax = 0, scratch = 0, tilebuf = 0, counters = 0, bytes = 0;
@@ -333,7 +333,7 @@ int choose_groups_single(int tiles, int s, bool modular, int kb, int sms, int ma
 // the problems into it and encodes the tensor maps.
 mm_status layout_group(mm_handle h, EmuGroup& g, char* base) {
   Arena ar;
-  g.total_tiles = g.total_split = g.max_rows = 0;
+  g.total_tiles = g.total_split = g.total_absmax = g.max_rows = 0;
   int maxn = 0;
   g.max_off.assign(g.ps.size(), 0);
   for (Problem& p : g.ps) maxn = std::max(maxn, p.n);
@@ -351,6 +351,8 @@ mm_status layout_group(mm_handle h, EmuGroup& g, char* base) {
     g.total_tiles += p.tiles_m * p.tiles_n;
     p.split_begin = g.total_split;
     g.total_split += mmk::split_tiles(p);
+    p.absmax_begin = g.total_absmax;
+    g.total_absmax += mmk::absmax_blocks(p);
     p.beta = g.form == 2 ? mmk::mod_beta(p.s, n) : 0;
     work += static_cast<long long>(p.tiles_m) * p.tiles_n * mmk::problem_pairs(p) * (p.k_pad / 64);
     const size_t a_sl = ar.take(static_cast<size_t>(p.s) * p.m_pad * p.k_pad * 2);
@@ -496,6 +498,7 @@ mm_status run_group(mm_handle h, const EmuGroup& g, const Problem* d_table, cons
   MM_CUDA(h, cudaMemsetAsync(amax, 0, sizeof(uint64_t) * g.max_rows, stream));
   MM_CUDA(h, cudaMemsetAsync(bmax, 0, sizeof(uint64_t) * g.max_rows, stream));
   MM_CUDA(h, mmk::split_launch(d_table, single ? &g.ps[0] : nullptr, static_cast<int>(g.ps.size()), g.total_split,
+                               g.total_absmax,
                                amax, bmax, single ? nullptr : d_max_off, h->d_status, stream));
   prof_end(h, stream, m_split);
   // Per-region completion counters (pair groups > 1) and the unit counter.
@@ -1215,7 +1218,7 @@ mm_status mm_split(mm_handle h, int N, const double* M, int by_columns, int slic
   uint64_t* mx = static_cast<uint64_t*>(h->arena);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   MM_CUDA(h, cudaMemsetAsync(mx, 0, sizeof(uint64_t) * N, s));
-  MM_CUDA(h, mmk::split_launch(nullptr, &p, 1, mmk::split_tiles(p), mx, mx, nullptr, h->d_status, s));
+  MM_CUDA(h, mmk::split_launch(nullptr, &p, 1, mmk::split_tiles(p), 0, mx, mx, nullptr, h->d_status, s));
   return MM_OK;
 }
 

@@ -86,7 +86,7 @@ extern "C" mm_status mm_split_noalloc(int N, const double* M, int by_columns, in
     p.m_pad = rows;
   }
   uint64_t* mx = reinterpret_cast<uint64_t*>(maxbits);
-  if (mmk::split_launch(nullptr, &p, 1, mmk::split_tiles(p), mx, mx, nullptr, status, s) != cudaSuccess) {
+  if (mmk::split_launch(nullptr, &p, 1, mmk::split_tiles(p), 0, mx, mx, nullptr, status, s) != cudaSuccess) {
     cudaGetLastError();
     return MM_ERR_CUDA;
   }
