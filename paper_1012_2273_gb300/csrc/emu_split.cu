@@ -64,37 +64,22 @@ __device__ __forceinline__ int exponent_from_maxbits(uint64_t mb) {
 }
 
 // D = round-half-even(v * 2^(width-e)) computed on the bit pattern of v
-// (width = 8s - 1 for s digits, beta for the modular form).
-// Requires |v| < 2^e (true for every entry of a row/column scaled by its max).
+// (width = 8s - 1 for s digits, beta for the modular form), without
+// branches.  Requires |v| < 2^e (true for every entry of a row/column scaled
+// by its max), so a left shift never exceeds width bits.  A right shift by
+// n >= 1 rounds half to even as floor((x + 2^(n-1) - 1 + lsb) / 2^n) with
+// lsb the lowest kept bit of x; for n >= 54 (x < 2^53 <= 2^(n-1)) that is 0.
 __device__ __forceinline__ int64_t fixed_point(uint64_t bits, int e, int width, bool* nonfinite) {
   const bool neg = (bits >> 63) != 0;
-  int E = static_cast<int>((bits >> 52) & 0x7FF);
-  uint64_t m = bits & ((1ull << 52) - 1);
-  if (E == 0x7FF) {
-    *nonfinite = true;
-    return 0;
-  }
-  if (E == 0) {
-    E = 1;  // subnormal: v = m 2^(1 - 1075)
-  } else {
-    m |= 1ull << 52;
-  }
-  if (m == 0) return 0;
-  const int sh = (E - 1075) - e + width;
-  uint64_t D;
-  if (sh >= 0) {
-    D = m << sh;  // < 2^width because |v| < 2^e
-  } else {
-    const int n = -sh;
-    if (n >= 54) {
-      D = 0;  // m < 2^53 <= 2^(n-1): below one half
-    } else {
-      const uint64_t q = m >> n;
-      const uint64_t rem = m & ((1ull << n) - 1);
-      const uint64_t half = 1ull << (n - 1);
-      D = q + ((rem > half || (rem == half && (q & 1))) ? 1 : 0);
-    }
-  }
+  const int E = static_cast<int>((bits >> 52) & 0x7FF);
+  const uint64_t frac = bits & ((1ull << 52) - 1);
+  const uint64_t x = E != 0 ? (frac | (1ull << 52)) : frac;  // subnormal: v = frac 2^(1 - 1075)
+  const int sh = ((E != 0 ? E : 1) - 1075) - e + width;
+  const int n = min(max(-sh, 1), 63);
+  const uint64_t right = (x + ((1ull << (n - 1)) - 1) + ((x >> n) & 1)) >> n;
+  uint64_t D = sh >= 0 ? (x << min(sh, 63)) : right;
+  if (E == 0x7FF) *nonfinite = true;
+  D = E == 0x7FF ? 0ull : D;
   return neg ? -static_cast<int64_t>(D) : static_cast<int64_t>(D);
 }
 
@@ -278,8 +263,8 @@ __device__ __forceinline__ void write_residue_item(const long long (&D)[8], uint
       x[q][l] = fmaf(sg, __uint_as_float(0x4B000000u | limb), bias);
     }
   }
-  // (the moduli loop stays rolled: unrolled, its 4 K limb constants would
-  // all be held in registers)
+  // (the moduli loop is unrolled only a little: fully unrolled, all its limb
+  // constants would be held in registers)
 #pragma unroll 1
   for (int j = 0; j < K; ++j) {
     const float m = c_mod.m_f[j], inv = c_mod.inv_f[j];
