@@ -276,16 +276,18 @@ MAX_FIXED_BITS = 62
 def modular_beta(k: int, n: int) -> int:
     """Fixed-point width used with the first k moduli at size n.
 
-    The largest beta <= 62 with 4 n 2^(2 beta) <= M_k (M_k the product of the
-    first k moduli): the exact product X of two beta-bit operands has
-    |X| <= n 2^(2 beta) <= M_k / 4, so X is recovered from its residues with
-    a quarter of the modulus to spare.  0 means k is too small for n.
+    The largest beta <= 62 with 514 n 2^(2 beta) <= 256 M_k (M_k the product
+    of the first k moduli): the exact product X of two beta-bit operands has
+    |X| <= n 2^(2 beta) <= (256/514) M_k / 2 < M_k / 2, so X is the unique
+    integer of its residue class within half the modulus of zero, and stays
+    a margin of M_k / 514 away from the ends of that range.  0 means k is too
+    small for n.
     """
     M = 1
     for m in MODULI[:k]:
         M *= m
     for beta in range(MAX_FIXED_BITS, 0, -1):
-        if 4 * n * (1 << (2 * beta)) <= M:
+        if 514 * n * (1 << (2 * beta)) <= 256 * M:
             return beta
     return 0
 

@@ -429,10 +429,12 @@ def test_modular_width_rule():
         for n in (1, 100, 500, 2000, 4095, 8192, 16384, 32767):
             beta = oracle.modular_beta(k, n)
             if beta == 0:
-                assert 4 * n * 4 > Mk
+                assert 514 * n * 4 > 256 * Mk
                 continue
-            assert 4 * n * 2 ** (2 * beta) <= Mk
-            assert beta == oracle.MAX_FIXED_BITS or 4 * n * 2 ** (2 * beta + 2) > Mk
+            # |X| <= n 2^(2 beta) is below M_k / 2 with a margin of M_k / 514
+            assert 2 * n * 2 ** (2 * beta) + Fraction(Mk, 257) <= Mk
+            assert beta == oracle.MAX_FIXED_BITS or 514 * n * 2 ** (2 * beta + 2) > 256 * Mk
     assert oracle.modular_beta(16, 100) == 58 and oracle.modular_beta(16, 500) == 57
-    assert oracle.modular_beta(16, 2000) == 56 and oracle.modular_beta(16, 16384) == 54
-    assert oracle.modular_beta(14, 8192) == 47 and oracle.modular_beta(15, 2000) == 52
+    assert oracle.modular_beta(16, 2000) == 56 and oracle.modular_beta(16, 16384) == 55
+    assert oracle.modular_beta(14, 8192) == 48 and oracle.modular_beta(14, 2000) == 49
+    assert oracle.modular_beta(15, 2000) == 52
