@@ -133,10 +133,11 @@ mm_status mm_plan(mm_handle h, int N, int* form, int* slices);
 
 /* Parameters of the modular form with k moduli at size N, computed on the
  * host (no handle, no GPU): *beta receives the fixed-point width, the
- * largest beta <= 62 with 4 N 2^(2 beta) <= m_1 m_2 ... m_k, so that the exact
- * product of two beta-bit operands (at most N 2^(2 beta) in magnitude) is
- * recovered from its residues with a quarter of the modulus to spare; 0 when
- * k is too small for N.  moduli (may be NULL) receives m_1..m_k.
+ * largest beta <= 62 with 514 N 2^(2 beta) <= 256 m_1 m_2 ... m_k, so that the
+ * exact product of two beta-bit operands (at most N 2^(2 beta) in magnitude)
+ * lies within half the modulus of zero with a margin of 1/514 of it and is
+ * recovered from its residues; 0 when k is too small for N.  moduli (may be
+ * NULL) receives m_1..m_k.
  * MM_ERR_INVALID for k outside 1..16 or N < 1. */
 mm_status mm_modular_params(int k, int N, int* beta, int* moduli);
 

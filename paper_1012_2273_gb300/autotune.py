@@ -14,6 +14,11 @@ within gamma_N |A||B| of the exact product, so an accepted plan is within
 (N/2 + N + small) 2^-53 |A||B| < 2 N 2^-53 |A||B|, the library's accuracy
 contract.  |A||B| is computed by the native form on |A| and |B|.
 
+Among accurate plans the modular form is preferred unless another is more
+than 5% faster: it serves every size above this range, and problems of
+different forms in one grouped call run as separate launch groups, one after
+another.
+
 The modular form's fixed-point width shrinks by half a bit per doubling of N
 while the allowance doubles, so within a bucket its worst case is the
 smallest size, which is checked.
@@ -40,6 +45,7 @@ BUCKETS = ((31, 24), (63, 48), (127, 96), (255, 192), (511, 384), (767, 640), (1
 FALLBACK = (1 << 30, ("emulated", 6, 256, 0.0))
 FORM_CODE = {"native": 0, "emulated": 1, "modular": 2}
 U = 2.0 ** -53
+MODULAR_PREFERENCE = 0.95  # a modular plan's time is compared after this factor
 
 
 def _time_ms(fn, flush, reps):
@@ -101,7 +107,9 @@ def tune(buckets=BUCKETS, slices=(6, 7, 8), moduli=(13, 14, 15, 16), widths=(128
             h.close()
             log(f"N={n:5d} {form} {'k' if form == 'modular' else 's'}={s} bn={bn} {ms:.3f} ms  "
                 f"max dev / allowance {worst:.3g} ({'ok' if ok else 'too far'})")
-            if ok and ms < best[3]:
+            score = ms * (MODULAR_PREFERENCE if form == "modular" else 1.0)
+            best_score = best[3] * (MODULAR_PREFERENCE if best[0] == "modular" else 1.0)
+            if ok and score < best_score:
                 best = (form, s, bn, ms)
         rows.append((max_n, best))
         log(f"N<={max_n}: {best[0]} s={best[1]} bn={best[2]} ({best[3]:.3f} ms at N={n})")

@@ -171,16 +171,17 @@ void prof_end(mm_handle h, cudaStream_t s, long mark) {
 // native FP64 is as fast and is the only form that meets the componentwise
 // bound for wide-range inputs at the smallest N; from there the modular form
 // with the fewest moduli that stay within the bound on uniform and
-// log-uniform (2^+-20) inputs: 16 up to N = 511, 15 up to 2047, 14 above
-// (the bound 2 N 2^-53 |A||B| grows with N).  Beyond the modular form's size
-// limit the digit form with 6 digits.
+// log-uniform (2^+-20) inputs: 16 up to N = 511, 15 up to 1535, 14 up to
+// 6143, 13 above (the bound 2 N 2^-53 |A||B| grows with N).  Beyond the
+// modular form's size limit the digit form with 6 digits.
 void default_tune(mm_handle h) {
   h->tune.clear();
   h->tune.push_back({255, Plan{0, 7, 256, 0}});
   h->tune.push_back({511, Plan{2, 16, 128, 0}});
   h->tune.push_back({767, Plan{2, 15, 128, 0}});
-  h->tune.push_back({2047, Plan{2, 15, 256, 0}});
-  h->tune.push_back({65535, Plan{2, 14, 256, 0}});
+  h->tune.push_back({1535, Plan{2, 15, 256, 0}});
+  h->tune.push_back({6143, Plan{2, 14, 256, 0}});
+  h->tune.push_back({65535, Plan{2, 13, 256, 0}});
   h->tune.push_back({1 << 30, Plan{1, 6, 256, 0}});
 }
 

@@ -189,26 +189,26 @@ __host__ __device__ constexpr ModTables make_mod_tables() {
   return t;
 }
 
-// Largest fixed-point width beta <= MOD_MAX_BITS with 4 n 2^(2 beta) <= M_k,
-// so that the exact product (|X| <= n 2^(2 beta)) lies within a quarter of
-// the modulus of zero; 0 if k moduli are too few for size n.
+// Largest fixed-point width beta <= MOD_MAX_BITS with 514 n 2^(2 beta) <=
+// 256 M_k: the exact product (|X| <= n 2^(2 beta)) then lies below M_k / 2
+// with a margin of M_k / 514, so it is the unique integer of its residue
+// class within half the modulus of zero, and the recombination's estimate of
+// round(V / M_k) (error a few 2^-20) cannot be pushed across a half.  0 if
+// k moduli are too few for size n.
 inline int mod_beta(int k, int n) {
   if (k < 1 || k > MOD_COUNT || n < 1) return 0;
-  const Limbs4 M = mod_product(k);
+  const Limbs4 Ml = mod_product(k);
+  unsigned __int128 M = 0;
+  for (int l = 3; l >= 0; --l) M = (M << 32) | Ml.w[l];
+  const unsigned __int128 need = static_cast<unsigned __int128>(514) * static_cast<unsigned>(n);
   for (int beta = MOD_MAX_BITS; beta >= 1; --beta) {
-    // floor(M / 2^(2 beta)) >= 4 n  <=>  4 n 2^(2 beta) <= M
-    const int sh = 2 * beta;
-    uint64_t q_lo = 0, q_hi = 0;  // M >> sh as 128 bits
-    const uint64_t lo = (static_cast<uint64_t>(M.w[1]) << 32) | M.w[0];
-    const uint64_t hi = (static_cast<uint64_t>(M.w[3]) << 32) | M.w[2];
-    if (sh >= 64) {
-      q_lo = hi >> (sh - 64);
-      q_hi = 0;
-    } else {
-      q_lo = (lo >> sh) | (sh ? (hi << (64 - sh)) : 0);
-      q_hi = hi >> sh;
-    }
-    if (q_hi != 0 || q_lo >= 4ull * static_cast<uint64_t>(n)) return beta;
+    const int sh = 2 * beta - 8;  // 514 n 2^(2 beta) <= 256 M  <=>  514 n <= M 2^-(2 beta - 8)
+    bool ok;
+    if (sh >= 0)
+      ok = (sh >= 128 ? 0 : (M >> sh)) >= need;
+    else
+      ok = (M >> 120) != 0 || (M << -sh) >= need;
+    if (ok) return beta;
   }
   return 0;
 }

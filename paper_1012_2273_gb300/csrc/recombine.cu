@@ -76,9 +76,9 @@ __global__ void __launch_bounds__(256) slots_recombine_kernel(const __grid_const
 // rows).  With T_g = X w_g mod M_g from the epilogue (w_g = (M/M_g)^-1 mod
 // M_g, M_g the product of group g's moduli), V = sum_g T_g (M/M_g) is
 // congruent to X modulo M = m_1...m_K and V / M = sum_g T_g / M_g < ceil(K/2).
-// Because |X| <= M/4 (the width rule), X = V - round(V/M) M, and round(V/M)
-// is found from a 24-bit estimate of V: its relative error is a few 2^-24,
-// far inside the quarter-modulus margin.  V is summed in four 64-bit
+// Because |X| < M/2 - M/514 (the width rule), X = V - round(V/M) M, and
+// round(V/M) is found from a 24-bit estimate of V: its error, a few 2^-20,
+// is far inside the margin of 1/514.  V is summed in four 64-bit
 // accumulators of 32-bit limbs (each term below 2^48, at most 8 of them),
 // carried, and X is formed modulo 2^128, exact since |X| < 2^126.  Then one
 // rounding: c = RN(X) 2^(e_i + f_k - 2 beta).  The four outputs' multiply-add

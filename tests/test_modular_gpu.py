@@ -199,9 +199,11 @@ def test_modular_rejects_too_few_moduli_and_bad_counts():
         mm.Handle("modular", slices=17)
     with pytest.raises(mm.MMError):
         mm.Handle("modular", slices=1)
-    n = 4096  # two moduli leave no fixed-point width at this size
-    A, B = workload.pair("uniform01", 1, n)
+    import torch
+    n = 8129  # the smallest size at which two moduli leave no fixed-point width
+    assert oracle.modular_beta(2, n) == 0 and oracle.modular_beta(2, n - 1) == 1
+    A = torch.zeros((n, n), dtype=torch.float64, device="cuda")
     with handle(2) as h:
         with pytest.raises(mm.MMError) as ei:
-            h.gemm(dev(A), dev(B))
+            h.gemm(A, A)
         assert ei.value.code == 4
