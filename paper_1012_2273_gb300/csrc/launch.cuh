@@ -137,7 +137,7 @@ void emu_kernel_info(int bn, char* buf, size_t len);
 
 // recombine.cu
 cudaError_t slots_recombine_launch(int bn, const EmuArgs& args, int total_tiles, cudaStream_t stream);
-cudaError_t mod_recombine_launch(int bn, int k, const EmuArgs& args, int tile0, int ntiles, cudaStream_t stream);
+cudaError_t mod_recombine_launch(int bn, const EmuArgs& args, int tile0, int ntiles, cudaStream_t stream);
 cudaError_t recombine_launch(int n, int s, const int32_t* levels, const int* e, const int* f, double* C,
                              cudaStream_t stream);
 

@@ -530,20 +530,9 @@ mm_status run_group(mm_handle h, const EmuGroup& g, const Problem* d_table, cons
     return fail(h, MM_ERR_CUDA, std::string("slice-product launch: ") + cudaGetErrorString(le) + " " + info);
   }
   if (g.form == 2) {
-    // one recombination launch per moduli count present in the group, over
-    // the range of tiles of the problems with that count
-    int lo[mmk::MOD_COUNT + 1], hi[mmk::MOD_COUNT + 1];
-    for (int k = 0; k <= mmk::MOD_COUNT; ++k) {
-      lo[k] = g.total_tiles;
-      hi[k] = 0;
-    }
-    for (const Problem& p : g.ps) {
-      lo[p.s] = std::min(lo[p.s], p.tile_begin);
-      hi[p.s] = std::max(hi[p.s], p.tile_begin + p.tiles_m * p.tiles_n);
-    }
+    // one recombination launch over the tiles of every modular problem
     const long m_rec = prof_start(h, stream, KIND_RECOMBINE);
-    for (int k = 2; k <= mmk::MOD_COUNT; ++k)
-      if (hi[k] > lo[k]) MM_CUDA(h, mmk::mod_recombine_launch(g.bn, k, a, lo[k], hi[k] - lo[k], stream));
+    MM_CUDA(h, mmk::mod_recombine_launch(g.bn, a, 0, g.total_tiles, stream));
     prof_end(h, stream, m_rec);
     return MM_OK;
   }

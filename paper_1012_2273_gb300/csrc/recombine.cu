@@ -84,17 +84,11 @@ __global__ void __launch_bounds__(256) slots_recombine_kernel(const __grid_const
 // rounding: c = RN(X) 2^(e_i + f_k - 2 beta).  The four outputs' multiply-add
 // chains are interleaved.
 template <int K, int BN>
-__global__ void __launch_bounds__(256) mod_recombine_kernel(const __grid_constant__ EmuArgs args, int tile0) {
+__device__ __forceinline__ void mod_recombine_tile(const EmuArgs& args, const Problem* P, int tile_local,
+                                                   int in_tile) {
   constexpr int NG = mod_groups(K);
-  constexpr int PER_TILE = EM_BM * BN / 4;          // threads per tile
   constexpr size_t SLOT = static_cast<size_t>(EM_BM) * BN;  // 16-bit entries per slot
   constexpr int QS = limbs_bit_length(mod_product(K)) - 31;  // V 2^-QS < 2^34
-  const long long item = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
-  const int tile = tile0 + static_cast<int>(item / PER_TILE);
-  const int in_tile = static_cast<int>(item % PER_TILE);
-  const Problem* P = args.table ? &args.table[find_problem(args.table, args.count, tile)] : &args.single;
-  const int tile_local = tile - P->tile_begin;
-  if (P->beta <= 0 || P->s != K || tile_local < 0 || tile_local >= P->tiles_m * P->tiles_n) return;
   // in_tile = ((c8 * 128 + r) * 2 + q): 8-column group c8, row r, half q of
   // the row's 16 bytes
   const int q = in_tile & 1, r = (in_tile >> 1) & (EM_BM - 1), c8 = in_tile >> 8;
@@ -147,6 +141,28 @@ __global__ void __launch_bounds__(256) mod_recombine_kernel(const __grid_constan
   }
 }
 
+// One launch for every modular problem of a group: each tile dispatches on
+// its problem's moduli count (uniform across the tile's threads).
+template <int BN>
+__global__ void __launch_bounds__(256) mod_recombine_kernel(const __grid_constant__ EmuArgs args, int tile0) {
+  constexpr int PER_TILE = EM_BM * BN / 4;  // threads per tile
+  const long long item = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+  const int tile = tile0 + static_cast<int>(item / PER_TILE);
+  const int in_tile = static_cast<int>(item % PER_TILE);
+  const Problem* P = args.table ? &args.table[find_problem(args.table, args.count, tile)] : &args.single;
+  const int tile_local = tile - P->tile_begin;
+  if (P->beta <= 0 || tile_local < 0 || tile_local >= P->tiles_m * P->tiles_n) return;
+  switch (P->s) {
+#define MM_RECOMBINE_CASE(K) \
+  case K: mod_recombine_tile<K, BN>(args, P, tile_local, in_tile); break;
+    MM_RECOMBINE_CASE(2) MM_RECOMBINE_CASE(3) MM_RECOMBINE_CASE(4) MM_RECOMBINE_CASE(5) MM_RECOMBINE_CASE(6)
+    MM_RECOMBINE_CASE(7) MM_RECOMBINE_CASE(8) MM_RECOMBINE_CASE(9) MM_RECOMBINE_CASE(10) MM_RECOMBINE_CASE(11)
+    MM_RECOMBINE_CASE(12) MM_RECOMBINE_CASE(13) MM_RECOMBINE_CASE(14) MM_RECOMBINE_CASE(15) MM_RECOMBINE_CASE(16)
+#undef MM_RECOMBINE_CASE
+    default: break;
+  }
+}
+
 // Standalone recombination (step API): levels [s][n][n] int32 -> C.
 __global__ void recombine_kernel(int n, int s, const int32_t* __restrict__ levels, const int* __restrict__ e,
                                  const int* __restrict__ f, double* __restrict__ C) {
@@ -176,36 +192,14 @@ cudaError_t slots_recombine_launch(int bn, const EmuArgs& args, int total_tiles,
   return cudaGetLastError();
 }
 
-template <int K>
-static void launch_mod_recombine(int bn, const EmuArgs& args, int tile0, unsigned blocks, cudaStream_t stream) {
-  if (bn == 256)
-    mod_recombine_kernel<K, 256><<<blocks, 256, 0, stream>>>(args, tile0);
-  else
-    mod_recombine_kernel<K, 128><<<blocks, 256, 0, stream>>>(args, tile0);
-}
-
-cudaError_t mod_recombine_launch(int bn, int k, const EmuArgs& args, int tile0, int ntiles, cudaStream_t stream) {
+cudaError_t mod_recombine_launch(int bn, const EmuArgs& args, int tile0, int ntiles, cudaStream_t stream) {
   if (ntiles <= 0) return cudaSuccess;
   const long long threads = static_cast<long long>(ntiles) * (EM_BM * bn / 4);
   const unsigned blocks = static_cast<unsigned>((threads + 255) / 256);
-  switch (k) {
-    case 2: launch_mod_recombine<2>(bn, args, tile0, blocks, stream); break;
-    case 3: launch_mod_recombine<3>(bn, args, tile0, blocks, stream); break;
-    case 4: launch_mod_recombine<4>(bn, args, tile0, blocks, stream); break;
-    case 5: launch_mod_recombine<5>(bn, args, tile0, blocks, stream); break;
-    case 6: launch_mod_recombine<6>(bn, args, tile0, blocks, stream); break;
-    case 7: launch_mod_recombine<7>(bn, args, tile0, blocks, stream); break;
-    case 8: launch_mod_recombine<8>(bn, args, tile0, blocks, stream); break;
-    case 9: launch_mod_recombine<9>(bn, args, tile0, blocks, stream); break;
-    case 10: launch_mod_recombine<10>(bn, args, tile0, blocks, stream); break;
-    case 11: launch_mod_recombine<11>(bn, args, tile0, blocks, stream); break;
-    case 12: launch_mod_recombine<12>(bn, args, tile0, blocks, stream); break;
-    case 13: launch_mod_recombine<13>(bn, args, tile0, blocks, stream); break;
-    case 14: launch_mod_recombine<14>(bn, args, tile0, blocks, stream); break;
-    case 15: launch_mod_recombine<15>(bn, args, tile0, blocks, stream); break;
-    case 16: launch_mod_recombine<16>(bn, args, tile0, blocks, stream); break;
-    default: return cudaErrorInvalidValue;
-  }
+  if (bn == 256)
+    mod_recombine_kernel<256><<<blocks, 256, 0, stream>>>(args, tile0);
+  else
+    mod_recombine_kernel<128><<<blocks, 256, 0, stream>>>(args, tile0);
   return cudaGetLastError();
 }
 
