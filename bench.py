@@ -308,7 +308,14 @@ def run_ours(args, dist: Dist):
     hn = mm.Handle("native")
     dmma_peak, dfma_peak = hn.probe_fp64_peak()
     for n, d in per_n.items():
+        N = int(n)
         d["native_frac_of_dmma_peak"] = round(d["native_tflops"] / dmma_peak, 4)
+        if N <= 100:  # HBM roofline: 24 N^2 bytes (A, B read, C written) per product
+            d["native_frac_of_hbm_peak"] = round(24 * N * N / (d["native_ms"] / 1e3) / 1e9 / peaks["hbm_gbs"], 6)
+        if "modular_moduli" in d:  # bf16 tensor work of the whole call (split and recombination included)
+            k = d["modular_moduli"]
+            d["modular_tensor_frac_whole_call"] = round(
+                k * 2 * N ** 3 / (d["modular_ms"] / 1e3) / 1e12 / peaks["bf16_tflops"], 4)
 
     # end to end through the public API on host buffers (pinned), per step:
     # H2D of A and B, compute, D2H of C for every problem of the sweep
