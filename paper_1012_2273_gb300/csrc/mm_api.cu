@@ -791,7 +791,11 @@ mm_status mm_gemm_host(mm_handle h, int N, const double* A_host, const double* B
   MM_CUDA(h, cudaMemcpyAsync(dA, A_host, elems * sizeof(double), cudaMemcpyHostToDevice, s));
   MM_CUDA(h, cudaMemcpyAsync(dB, B_host, elems * sizeof(double), cudaMemcpyHostToDevice, s));
   mm_status st = mm_gemm(h, N, dA, dB, dC, stream);
-  if (st != MM_OK) return st;
+  if (st != MM_OK) {
+    cudaStreamSynchronize(s);  // the uploads read the caller's buffers: let them finish
+    cudaGetLastError();
+    return st;
+  }
   MM_CUDA(h, cudaMemcpyAsync(C_host, dC, elems * sizeof(double), cudaMemcpyDeviceToHost, s));
   MM_CUDA(h, cudaStreamSynchronize(s));
   return MM_OK;
@@ -872,6 +876,20 @@ mm_status mm_gemm_grouped_host(mm_handle h, int count, const int* Ns, const doub
   cudaEvent_t start = h->ge2e_events[2 * chunks.size()];
   MM_CUDA(h, cudaEventRecord(start, s));  // earlier work on the caller's stream comes first
   MM_CUDA(h, cudaStreamWaitEvent(h->up_stream, start, 0));
+  // From here on, copies that touch the caller's host buffers may be in
+  // flight: every way out waits for them first.
+  auto drain = [&](mm_status st) {
+    cudaStreamSynchronize(h->up_stream);
+    cudaStreamSynchronize(h->down_stream);
+    cudaStreamSynchronize(s);
+    cudaGetLastError();
+    return st;
+  };
+#define MM_CUDA_DRAIN(call)                                              \
+  do {                                                                   \
+    cudaError_t e_ = (call);                                             \
+    if (e_ != cudaSuccess) return drain(cuda_fail(h, e_, #call));        \
+  } while (0)
   auto dptr = [&](int i, int which) {
     const size_t bytes = align_up(static_cast<size_t>(Ns[i]) * Ns[i] * sizeof(double), kAlign);
     return reinterpret_cast<double*>(h->ge2e + off[i] + which * bytes);
@@ -883,27 +901,28 @@ mm_status mm_gemm_grouped_host(mm_handle h, int count, const int* Ns, const doub
     std::vector<double*> cc;
     for (int i : chunks[c]) {
       const size_t bytes = static_cast<size_t>(Ns[i]) * Ns[i] * sizeof(double);
-      MM_CUDA(h, cudaMemcpyAsync(dptr(i, 0), As_host[i], bytes, cudaMemcpyHostToDevice, h->up_stream));
-      MM_CUDA(h, cudaMemcpyAsync(dptr(i, 1), Bs_host[i], bytes, cudaMemcpyHostToDevice, h->up_stream));
+      MM_CUDA_DRAIN(cudaMemcpyAsync(dptr(i, 0), As_host[i], bytes, cudaMemcpyHostToDevice, h->up_stream));
+      MM_CUDA_DRAIN(cudaMemcpyAsync(dptr(i, 1), Bs_host[i], bytes, cudaMemcpyHostToDevice, h->up_stream));
       cn.push_back(Ns[i]);
       ca.push_back(dptr(i, 0));
       cb.push_back(dptr(i, 1));
       cc.push_back(dptr(i, 2));
     }
-    MM_CUDA(h, cudaEventRecord(in, h->up_stream));
-    MM_CUDA(h, cudaStreamWaitEvent(s, in, 0));
+    MM_CUDA_DRAIN(cudaEventRecord(in, h->up_stream));
+    MM_CUDA_DRAIN(cudaStreamWaitEvent(s, in, 0));
     const mm_status st = mm_gemm_grouped(h, static_cast<int>(cn.size()), cn.data(), ca.data(), cb.data(), cc.data(), s);
-    if (st != MM_OK) return st;
-    MM_CUDA(h, cudaEventRecord(done, s));
-    MM_CUDA(h, cudaStreamWaitEvent(h->down_stream, done, 0));
+    if (st != MM_OK) return drain(st);
+    MM_CUDA_DRAIN(cudaEventRecord(done, s));
+    MM_CUDA_DRAIN(cudaStreamWaitEvent(h->down_stream, done, 0));
     for (size_t q = 0; q < chunks[c].size(); ++q) {
       const int i = chunks[c][q];
-      MM_CUDA(h, cudaMemcpyAsync(Cs_host[i], cc[q], static_cast<size_t>(Ns[i]) * Ns[i] * sizeof(double),
+      MM_CUDA_DRAIN(cudaMemcpyAsync(Cs_host[i], cc[q], static_cast<size_t>(Ns[i]) * Ns[i] * sizeof(double),
                                  cudaMemcpyDeviceToHost, h->down_stream));
     }
   }
-  MM_CUDA(h, cudaStreamSynchronize(h->down_stream));
-  MM_CUDA(h, cudaStreamSynchronize(s));
+  MM_CUDA_DRAIN(cudaStreamSynchronize(h->down_stream));
+  MM_CUDA_DRAIN(cudaStreamSynchronize(s));
+#undef MM_CUDA_DRAIN
   return MM_OK;
 }
 

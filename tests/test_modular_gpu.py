@@ -207,3 +207,31 @@ def test_modular_rejects_too_few_moduli_and_bad_counts():
         with pytest.raises(mm.MMError) as ei:
             h.gemm(A, A)
         assert ei.value.code == 4
+
+
+@pytest.mark.parametrize("use_graph", [True, False])
+def test_grouped_call_mixing_native_digit_and_modular_forms(tmp_path, use_graph):
+    # Three forms in one grouped call: native FP64, the digit form (its own
+    # launch group) and the modular form (another), one after another on the
+    # call's stream, each problem bit-exact against its form's model.
+    import paper_1012_2273_gb300 as mm
+    tune = tmp_path / "tune.txt"
+    tune.write_text("60 0 7 256 0\n300 1 7 256 0\n100000 2 15 256 0\n")
+    sizes = [700, 40, 250, 1, 129, 513, 300, 64]
+    pairs = [workload.pair("uniform11", 150 + i, n) for i, n in enumerate(sizes)]
+    flags = 0 if use_graph else mm.FLAG_NO_GRAPH
+    with mm.Handle("auto", flags=flags, tune_path=str(tune)) as h:
+        plans = {n: h.plan(n) for n in sizes}
+        for _ in range(2):
+            Cs = h.gemm_grouped([dev(a) for a, _ in pairs], [dev(b) for _, b in pairs])
+            h.check()
+            for (A, B), C, n in zip(pairs, Cs, sizes):
+                form, k = plans[n]
+                C = host(C)
+                if form == 0:
+                    assert_within_bound(C, oracle.gemm(A, B), oracle.absgemm(A, B), n)
+                elif form == 1:
+                    assert_bits(C, oracle.emu_gemm(A, B, k))
+                else:
+                    assert_bits(C, oracle.fixed_gemm(A, B, beta_of(k, n)))
+    assert {f for f, _ in plans.values()} == {0, 1, 2}
