@@ -204,6 +204,13 @@ __device__ __forceinline__ void tmem_ld_32x32b_x32(uint32_t taddr, uint32_t (&r)
 }
 __device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
+// Writes v into 4 consecutive 32-bit columns of the warp's 32 TMEM lanes
+// (lane 32 w + i from thread i of warp w).
+__device__ __forceinline__ void tmem_st_32x32b_x4(uint32_t taddr, uint32_t v) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %1, %1, %1};" ::"r"(taddr), "r"(v) : "memory");
+}
+__device__ __forceinline__ void tmem_st_wait() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
 // Shared-memory matrix descriptor for a K-major bf16 tile written by TMA with
 // 128-byte swizzle: rows of 128 B (64 elements), 8-row groups 1024 B apart.
 // Fields: start address >> 4 (bits 0-13), leading byte offset >> 4 (16-29,

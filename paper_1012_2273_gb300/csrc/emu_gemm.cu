@@ -11,11 +11,13 @@
 // this library's, the paper itself has no emulation).
 //
 // Exactness.  Digits satisfy |d| <= 128, so one digit product is at most 2^14
-// in magnitude and a sum of 256 of them at most 2^22: the tensor core's FP32
-// accumulator holds every partial sum of a 256-long chunk exactly.  After each
-// chunk the accumulator is drained: x + 1.5 * 2^23 is exact for |x| <= 2^22
-// and its FP32 bit pattern is 0x4B400000 + x, so adding bit patterns in int32
-// accumulates the chunk sums exactly (the bias is removed once per segment).
+// in magnitude and a sum of 256 of them at most 2^22.  Each chunk accumulates
+// onto 1.5 * 2^23 (the epilogue stores that constant into the TMEM buffer
+// before handing it back), so every partial sum is an integer in [2^23, 2^24],
+// held exactly by the tensor core's FP32 accumulator, and the FP32 bit
+// pattern of 1.5 * 2^23 + x is 0x4B400000 + x: adding the drained bit
+// patterns in int32 accumulates the chunk sums exactly (the bias is removed
+// once per segment).
 // An int32 segment sum stays below 2^31 because the host limits the pairs per
 // segment to floor((2^31 - 1) / (N 2^14)).  The recombination reads the
 // segment sums back in 128-bit integer arithmetic and rounds once -- no FP64
@@ -333,7 +335,8 @@ __global__ void __launch_bounds__(EM_THREADS, 1)
           p += np;
           const int nb = np * KB;
           for (int c0 = 0; c0 < nb && ok; c0 += EM_CHUNK_KB) {
-            if (!mbar_wait(&acc_empty[abuf], aphase ^ 1, tmo, args.status)) {
+            // phase 0 of each buffer is the epilogue's first bias store
+            if (!mbar_wait(&acc_empty[abuf], aphase, tmo, args.status)) {
               ok = false;
               break;
             }
@@ -352,7 +355,8 @@ __global__ void __launch_bounds__(EM_THREADS, 1)
 #pragma unroll
               for (int k = 0; k < EM_BK / 16; ++k) {
                 // advance 16 elements = 32 bytes = 2 units of the address field
-                tc_mma_bf16(d_tmem, adesc + 2 * k, bdesc + 2 * k, idesc, (b > c0 || k > 0) ? 1u : 0u);
+                // always accumulate: the buffer holds 1.5 * 2^23 at a chunk's start
+                tc_mma_bf16(d_tmem, adesc + 2 * k, bdesc + 2 * k, idesc, 1u);
               }
               tc_commit(&empty[stage]);
               if (++stage == Cfg::STAGES) {
@@ -386,6 +390,23 @@ __global__ void __launch_bounds__(EM_THREADS, 1)
     bool ok = true;
     int uslot = 0;
     uint32_t uphase = 0;
+    // Both accumulators start every chunk at 1.5 * 2^23 (stored here, and again
+    // after each drain), so the MMAs' FP32 sums stay exact integers in [2^23,
+    // 2^24] whose bit patterns are 0x4B400000 + x: draining is one int32 add.
+    {
+      const uint32_t t0 = tmem_base + (static_cast<uint32_t>(32 * q) << 16) + static_cast<uint32_t>(h * HALF);
+#pragma unroll
+      for (int b = 0; b < 2; ++b)
+#pragma unroll
+        for (int c = 0; c < HALF; c += 4) tmem_st_32x32b_x4(t0 + b * BN + c, EM_MAGIC);
+      tmem_st_wait();
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) {
+        mbar_arrive(&acc_empty[0]);
+        mbar_arrive(&acc_empty[1]);
+      }
+    }
     while (ok) {
       if (!mbar_wait(&ufull[uslot], uphase, tmo, args.status)) {
         ok = false;
@@ -424,7 +445,7 @@ __global__ void __launch_bounds__(EM_THREADS, 1)
                                 ? args.tilebuf + P->slot_base + static_cast<long long>(U.tile_local) * P->nslots * SLOT
                                 : my_scratch;
       int L, t0;
-      uint32_t pend[kMod ? HALF / 4 : 1];  // modular form: residues of a pair's first modulus
+      uint32_t pend[kMod ? HALF / 4 : 1] = {};  // modular form: residues of a pair's first modulus
       for (int p = p0; p < p1 && ok; ++slot) {
         const int np = kMod ? 1 : emu_segment(p, p1, maxp, &L, &t0);
         p += np;
@@ -447,9 +468,11 @@ __global__ void __launch_bounds__(EM_THREADS, 1)
             tmem_ld_32x32b_x32(taddr + part * 32, r);
             tmem_ld_wait();
 #pragma unroll
-            for (int i = 0; i < 32; ++i)
-              acc[part * 32 + i] += __float_as_uint(__uint_as_float(r[i]) + 12582912.0f);
+            for (int i = 0; i < 32; ++i) acc[part * 32 + i] += r[i];
           }
+#pragma unroll
+          for (int c4 = 0; c4 < HALF; c4 += 4) tmem_st_32x32b_x4(taddr + c4, EM_MAGIC);
+          tmem_st_wait();
           tc_fence_before();
           __syncwarp();
           if (lane == 0) mbar_arrive(&acc_empty[abuf]);
@@ -460,39 +483,39 @@ __global__ void __launch_bounds__(EM_THREADS, 1)
         const uint32_t bias = static_cast<uint32_t>(nchunks) * EM_MAGIC;
         if (kMod) {
           // The exact sum S = sum_j r_a r_b of modulus m_j (|S| <= n 2^14 <=
-          // 2^30) becomes t = (S mod m) cy mod m in [0, m): x = S + (a
-          // multiple of m, at least 2^30) is non-negative and below 2^31 +
-          // 2^8, where floor(x / m) = umulhi(x, ceil(2^39 / m)) >> 7 exactly.
-          // The first modulus of a pair keeps its t (4 per word) until the
-          // second arrives; then the group residue T = t_a m_b + t_b m_a,
-          // reduced below m_a m_b < 2^16, is stored as 16 bits (a lone last
-          // modulus stores its t).  Slot layout: [col / 8][row][8 x 16 bits],
-          // one 16-byte vector per 8 columns, a warp's 32 rows contiguous.
+          // 2^30) becomes r = S mod m in [0, m): x = S + (a multiple of m, at
+          // least 2^30) is non-negative and below 2^31 + 2^8, where
+          // floor(x / m) = umulhi(x, ceil(2^39 / m)) >> 7 exactly.  The first
+          // modulus of a pair keeps t = r cy mod m (4 per word) until the
+          // second arrives; then the group residue T = t_a m_b + t_b m_a mod
+          // M_g < 2^16, reduced once from t_a m_b + r_b cy_b m_a, is stored as
+          // 16 bits (a lone last modulus stores r cy mod m).  Slot layout:
+          // [col / 8][row][8 x 16 bits], one 16-byte vector per 8 columns, a
+          // warp's 32 rows contiguous.
           const int j = slot;
-          const uint32_t m = c_mod.m_u[j], magic = c_mod.magic[j], cy = c_mod.cy[s][j];
+          const uint32_t m = c_mod.m_u[j], magic = c_mod.magic[j];
           const uint32_t shift_in = c_mod.bias[j] - bias;  // x = acc - bias + bias_j
-          uint32_t tw[HALF / 4];
-#pragma unroll
-          for (int c = 0; c < HALF; c += 4) {
-            uint32_t word = 0;
-#pragma unroll
-            for (int b = 0; b < 4; ++b) {
-              const uint32_t x = acc[c + b] + shift_in;
-              const uint32_t r = x - (__umulhi(x, magic) >> 7) * m;
-              const uint32_t pr = r * cy;
-              const uint32_t t = pr - (__umulhi(pr, magic) >> 7) * m;
-              word |= t << (8 * b);
-            }
-            tw[c / 4] = word;
-          }
           if ((j & 1) == 0 && j + 1 < s) {  // first of a pair
+            const uint32_t cy = c_mod.cy[s][j], cq = c_mod.cyq[s][j];
 #pragma unroll
-            for (int i = 0; i < HALF / 4; ++i) pend[i] = tw[i];
+            for (int c = 0; c < HALF; c += 4) {
+              uint32_t t[4];
+#pragma unroll
+              for (int b = 0; b < 4; ++b) {
+                const uint32_t x = acc[c + b] + shift_in;
+                const uint32_t r = x - (__umulhi(x, magic) >> 7) * m;
+                t[b] = r * cy - __umulhi(r, cq) * m;
+              }
+              pend[c / 4] = __byte_perm(__byte_perm(t[0], t[1], 0x0040), __byte_perm(t[2], t[3], 0x0040), 0x5410);
+            }
             continue;
           }
           const bool paired = (j & 1) != 0;
-          const uint32_t ma = paired ? c_mod.m_u[j - 1] : 0u;
-          const uint32_t Mg = ma * m;
+          const uint32_t mt = paired ? m : 0u;  // weight of t_a
+          const uint32_t cm = c_mod.cym[s][j];
+          const uint32_t Mg = paired ? c_mod.m_u[j - 1] * m : m;
+          const uint32_t gm = c_mod.gmagic[s][j >> 1];
+          const int gs = paired ? 9 : 7;
           uint16_t* dst = reinterpret_cast<uint16_t*>(args.tilebuf + P->slot_base) +
                           (static_cast<size_t>(U.tile_local) * P->nslots + (j >> 1)) * (EM_BM * BN) +
                           static_cast<size_t>(h * HALF / 8) * (EM_BM * 8) + r_in_tile * 8;
@@ -501,20 +524,17 @@ __global__ void __launch_bounds__(EM_THREADS, 1)
             uint32_t w[4];
 #pragma unroll
             for (int q2 = 0; q2 < 4; ++q2) {
-              uint32_t half16[2];
+              uint32_t T[2];
 #pragma unroll
               for (int b = 0; b < 2; ++b) {
                 const int col = c + 2 * q2 + b;
-                const uint32_t tb = (tw[col >> 2] >> (8 * (col & 3))) & 255u;
-                uint32_t T = tb;
-                if (paired) {
-                  const uint32_t ta = (pend[col >> 2] >> (8 * (col & 3))) & 255u;
-                  T = ta * m + tb * ma;
-                  if (T >= Mg) T -= Mg;
-                }
-                half16[b] = T;
+                const uint32_t x = acc[col] + shift_in;
+                const uint32_t r = x - (__umulhi(x, magic) >> 7) * m;
+                const uint32_t ta = __byte_perm(pend[col >> 2], 0u, 0x4440u | static_cast<uint32_t>(col & 3));
+                const uint32_t Tp = ta * mt + r * cm;
+                T[b] = Tp - (__umulhi(Tp, gm) >> gs) * Mg;
               }
-              w[q2] = half16[0] | (half16[1] << 16);
+              w[q2] = __byte_perm(T[0], T[1], 0x5410);
             }
             __stcs(reinterpret_cast<uint4*>(dst + (c / 8) * (EM_BM * 8)), make_uint4(w[0], w[1], w[2], w[3]));
           }

@@ -129,6 +129,16 @@ struct ModTables {
   uint32_t magic[MOD_COUNT];
   uint32_t bias[MOD_COUNT];
   uint32_t cy[MOD_COUNT + 1][MOD_COUNT];
+  // how the epilogue applies cy, with r = X mod m_j: the first modulus a of
+  // a pair keeps t_a = r cy_a - umulhi(r, cyq_a) m_a (cyq = ceil(cy 2^32 / m),
+  // exact for r < 256); the second, b, forms T' = t_a m_b + r cym_b < 2^25
+  // with cym_b = cy_b m_a -- congruent to t_a m_b + t_b m_a modulo M_g -- and
+  // reduces it once: floor(T' / M_g) = umulhi(T', gmagic) >> 9 with gmagic =
+  // ceil(2^41 / M_g), exact for T' < 2^25 and M_g < 2^16; a lone modulus has
+  // cym = cy and reduces r cy < 2^16 with its own magic (shift 7)
+  uint32_t cyq[MOD_COUNT + 1][MOD_COUNT];
+  uint32_t cym[MOD_COUNT + 1][MOD_COUNT];
+  uint32_t gmagic[MOD_COUNT + 1][MOD_GROUPS];
   // recombination, per k: limbs of W_g = M_k / M_g and of M_k; V = sum_g
   // T_g W_g is congruent to X modulo M_k; V 2^-qshift is formed in FP32 and
   // multiplied by qscale = 2^qshift / M_k to estimate round(V / M_k)
@@ -173,9 +183,16 @@ __host__ __device__ constexpr ModTables make_mod_tables() {
       if (b < k) {
         t.cy[k][a] = static_cast<uint32_t>(static_cast<uint64_t>(w % ma) * inv_mod(mb % ma, ma) % ma);
         t.cy[k][b] = static_cast<uint32_t>(static_cast<uint64_t>(w % mb) * inv_mod(ma % mb, mb) % mb);
+        t.cym[k][a] = t.cy[k][a];
+        t.cym[k][b] = t.cy[k][b] * ma;
+        t.gmagic[k][g] = static_cast<uint32_t>(((1ull << 41) + Mg - 1) / Mg);
       } else {
         t.cy[k][a] = w % ma;
+        t.cym[k][a] = t.cy[k][a];
+        t.gmagic[k][g] = t.magic[a];
       }
+      t.cyq[k][a] = static_cast<uint32_t>(((static_cast<uint64_t>(t.cy[k][a]) << 32) + ma - 1) / ma);
+      if (b < k) t.cyq[k][b] = static_cast<uint32_t>(((static_cast<uint64_t>(t.cy[k][b]) << 32) + mb - 1) / mb);
     }
     const int bits = limbs_bit_length(M);
     t.qshift[k] = bits - 31;
