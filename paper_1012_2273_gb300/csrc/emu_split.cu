@@ -247,45 +247,74 @@ __device__ __forceinline__ void write_digit_planes(const long long (&Ds)[SP_TILE
 // is an exact FP32 integer operation.  r = S - m rint(S RN(1/m)): the product's
 // relative error is at most 2^-24, below 1 / (2 |S|), so rint picks the
 // nearest multiple of m exactly as exact division would and |r| <= m/2 <= 128
-// -- an exact bf16 value.  rint is the add-and-subtract of 1.5 2^23.
+// -- an exact bf16 value.  rint is the add-and-subtract of 1.5 2^23.  The
+// arithmetic runs on pairs of elements with the packed f32x2 instructions of
+// sm_100 and later: each rounds its two results exactly as two scalar
+// instructions would, for half the instructions issued.
+__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
+  float2 d;
+  asm("{\n\t.reg .b64 ra, rb, rc, rd;\n\t"
+      "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\tmov.b64 rc, {%6, %7};\n\t"
+      "fma.rn.f32x2 rd, ra, rb, rc;\n\t"
+      "mov.b64 {%0, %1}, rd;\n\t}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+  return d;
+}
+__device__ __forceinline__ float2 fadd2(float2 a, float2 b) {
+  float2 d;
+  asm("{\n\t.reg .b64 ra, rb, rd;\n\t"
+      "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+      "add.rn.f32x2 rd, ra, rb;\n\t"
+      "mov.b64 {%0, %1}, rd;\n\t}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return d;
+}
+
 template <int K, int LIMBS>
 __device__ __forceinline__ void write_residue_item(const long long (&D)[8], uint16_t* out, size_t plane) {
   constexpr int LB = mod_limb_bits(LIMBS);
-  float x[8][LIMBS];
+  float2 x[4][LIMBS];  // limbs of elements 2p (.x) and 2p + 1 (.y)
 #pragma unroll
-  for (int q = 0; q < 8; ++q) {
-    const uint64_t X = D[q] < 0 ? 0ull - static_cast<uint64_t>(D[q]) : static_cast<uint64_t>(D[q]);
+  for (int p = 0; p < 4; ++p) {
+    const long long d0 = D[2 * p], d1 = D[2 * p + 1];
+    const uint64_t X0 = d0 < 0 ? 0ull - static_cast<uint64_t>(d0) : static_cast<uint64_t>(d0);
+    const uint64_t X1 = d1 < 0 ? 0ull - static_cast<uint64_t>(d1) : static_cast<uint64_t>(d1);
     // sg (2^23 + limb) - sg 2^23 = sg limb, exactly, in one FMA
-    const float sg = D[q] < 0 ? -1.0f : 1.0f, bias = D[q] < 0 ? 8388608.0f : -8388608.0f;
+    const float2 sg = make_float2(d0 < 0 ? -1.0f : 1.0f, d1 < 0 ? -1.0f : 1.0f);
+    const float2 bias = make_float2(d0 < 0 ? 8388608.0f : -8388608.0f, d1 < 0 ? 8388608.0f : -8388608.0f);
 #pragma unroll
     for (int l = 0; l < LIMBS; ++l) {
-      const uint32_t limb = static_cast<uint32_t>(X >> (LB * l)) & ((1u << LB) - 1);
-      x[q][l] = fmaf(sg, __uint_as_float(0x4B000000u | limb), bias);
+      const uint32_t l0 = static_cast<uint32_t>(X0 >> (LB * l)) & ((1u << LB) - 1);
+      const uint32_t l1 = static_cast<uint32_t>(X1 >> (LB * l)) & ((1u << LB) - 1);
+      x[p][l] = ffma2(sg, make_float2(__uint_as_float(0x4B000000u | l0), __uint_as_float(0x4B000000u | l1)), bias);
     }
   }
+  const float2 magic = make_float2(12582912.0f, 12582912.0f), unmagic = make_float2(-12582912.0f, -12582912.0f);
   // (the moduli loop is unrolled only a little: fully unrolled, all its limb
   // constants would be held in registers)
 #pragma unroll 1
   for (int j = 0; j < K; ++j) {
     const float m = c_mod.m_f[j], inv = c_mod.inv_f[j];
-    float c[LIMBS - 1];
+    const float2 negm = make_float2(-m, -m), inv2 = make_float2(inv, inv);
+    float2 c[LIMBS - 1];
 #pragma unroll
-    for (int l = 1; l < LIMBS; ++l) c[l - 1] = LIMBS == 4 ? c_mod.split_c14[j][l - 1] : c_mod.split_c13[j][l - 1];
-    float res[8];
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      float S = x[q][0];
-#pragma unroll
-      for (int l = 1; l < LIMBS; ++l) S = fmaf(x[q][l], c[l - 1], S);
-      const float qt = fmaf(S, inv, 12582912.0f) - 12582912.0f;
-      res[q] = fmaf(-qt, m, S);
+    for (int l = 1; l < LIMBS; ++l) {
+      const float cl = LIMBS == 4 ? c_mod.split_c14[j][l - 1] : c_mod.split_c13[j][l - 1];
+      c[l - 1] = make_float2(cl, cl);
     }
-    uint4 v;
-    v.x = bf16x2_of_digits(res[0], res[1]);
-    v.y = bf16x2_of_digits(res[2], res[3]);
-    v.z = bf16x2_of_digits(res[4], res[5]);
-    v.w = bf16x2_of_digits(res[6], res[7]);
-    *reinterpret_cast<uint4*>(out + j * plane) = v;
+    uint32_t w[4];
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+      float2 S = x[p][0];
+#pragma unroll
+      for (int l = 1; l < LIMBS; ++l) S = ffma2(x[p][l], c[l - 1], S);
+      const float2 qt = fadd2(ffma2(S, inv2, magic), unmagic);
+      const float2 res = ffma2(qt, negm, S);
+      w[p] = bf16x2_of_digits(res.x, res.y);
+    }
+    *reinterpret_cast<uint4*>(out + j * plane) = make_uint4(w[0], w[1], w[2], w[3]);
   }
 }
 
