@@ -296,14 +296,10 @@ __device__ __forceinline__ void write_residue_item(const long long (&D)[8], uint
   // constants would be held in registers)
 #pragma unroll 1
   for (int j = 0; j < K; ++j) {
-    const float m = c_mod.m_f[j], inv = c_mod.inv_f[j];
-    const float2 negm = make_float2(-m, -m), inv2 = make_float2(inv, inv);
+    const float2 negm = c_mod.pair_negm[j], inv2 = c_mod.pair_inv[j];
     float2 c[LIMBS - 1];
 #pragma unroll
-    for (int l = 1; l < LIMBS; ++l) {
-      const float cl = LIMBS == 4 ? c_mod.split_c14[j][l - 1] : c_mod.split_c13[j][l - 1];
-      c[l - 1] = make_float2(cl, cl);
-    }
+    for (int l = 1; l < LIMBS; ++l) c[l - 1] = LIMBS == 4 ? c_mod.pair_c14[j][l - 1] : c_mod.pair_c13[j][l - 1];
     uint32_t w[4];
 #pragma unroll
     for (int p = 0; p < 4; ++p) {
@@ -380,7 +376,7 @@ __device__ __forceinline__ void residue_tile(bool is_a, const uint64_t* src, int
   }
 }
 
-__global__ void __launch_bounds__(SP_THREADS) split_kernel(const __grid_constant__ SplitArgs args) {
+__global__ void __launch_bounds__(SP_THREADS, 3) split_kernel(const __grid_constant__ SplitArgs args) {
   __shared__ long long Ds[SP_TILE][SP_TILE + 1];
   __shared__ int ex_s[SP_TILE];  // exponent of each output row (A: row i; B^T: column k of B)
   __shared__ int any_nonfinite;

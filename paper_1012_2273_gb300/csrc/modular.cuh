@@ -109,6 +109,18 @@ __host__ __device__ constexpr float pow2f(int e) {
 __host__ __device__ constexpr int mod_groups(int k) { return (k + 1) / 2; }
 constexpr int MOD_GROUPS = MOD_COUNT / 2;
 
+// 32-bit limbs of the largest recombination weight W_g = M_k / M_g over the
+// groups of k moduli (3 for k = 11..14, 4 for k = 15, 16).
+__host__ __device__ constexpr int mod_weight_limbs(int k) {
+  int bits = 0;
+  for (int g = 0; g < mod_groups(k); ++g) {
+    const uint32_t Mg = mod_value(2 * g) * (2 * g + 1 < k ? mod_value(2 * g + 1) : 1u);
+    const int b = limbs_bit_length(limbs_div_small(mod_product(k), Mg));
+    bits = b > bits ? b : bits;
+  }
+  return (bits + 31) / 32;
+}
+
 struct ModTables {
   // split: the symmetric residue of 2^(13 l) (l = 1..4) and of 2^(14 l)
   // (l = 1..3) modulo m_j, m_j and RN(1/m_j) as floats
@@ -117,6 +129,12 @@ struct ModTables {
   uint32_t m_u[MOD_COUNT];
   float m_f[MOD_COUNT];
   float inv_f[MOD_COUNT];
+  // the same split constants as equal pairs, for packed f32x2 arithmetic:
+  // c_l, -m_j and RN(1/m_j) twice each
+  float2 pair_c13[MOD_COUNT][4];
+  float2 pair_c14[MOD_COUNT][3];
+  float2 pair_negm[MOD_COUNT];
+  float2 pair_inv[MOD_COUNT];
   // slice-product epilogue: ceil(2^39 / m_j) (so that floor(x / m_j) =
   // umulhi(x, magic) >> 7 for 0 <= x < 2^31 + 2^8), a multiple of m_j at least
   // 2^30 (added to make a sum of at most 2^30 in magnitude non-negative),
@@ -158,15 +176,20 @@ __host__ __device__ constexpr ModTables make_mod_tables() {
         uint64_t p = 1;
         for (int b = 0; b < bits * l; ++b) p = (p * 2) % m;
         const int64_t sym = (p > m / 2) ? static_cast<int64_t>(p) - m : static_cast<int64_t>(p);
-        if (bits == 13)
+        if (bits == 13) {
           t.split_c13[j][l - 1] = static_cast<float>(sym);
-        else
+          t.pair_c13[j][l - 1].x = t.pair_c13[j][l - 1].y = static_cast<float>(sym);
+        } else {
           t.split_c14[j][l - 1] = static_cast<float>(sym);
+          t.pair_c14[j][l - 1].x = t.pair_c14[j][l - 1].y = static_cast<float>(sym);
+        }
       }
     }
     t.m_u[j] = m;
     t.m_f[j] = static_cast<float>(m);
     t.inv_f[j] = 1.0f / static_cast<float>(m);
+    t.pair_negm[j].x = t.pair_negm[j].y = -static_cast<float>(m);
+    t.pair_inv[j].x = t.pair_inv[j].y = t.inv_f[j];
     t.magic[j] = static_cast<uint32_t>(((1ull << 39) + m - 1) / m);
     t.bias[j] = static_cast<uint32_t>(((1ull << 30) + m - 1) / m * m);
   }

@@ -79,8 +79,9 @@ __global__ void __launch_bounds__(256) slots_recombine_kernel(const __grid_const
 // Because |X| < M/2 - M/514 (the width rule), X = V - round(V/M) M, and
 // round(V/M) is found from a 24-bit estimate of V: its error, a few 2^-20,
 // is far inside the margin of 1/514.  V is summed in four 64-bit
-// accumulators of 32-bit limbs (each term below 2^48, at most 8 of them),
-// carried, and X is formed modulo 2^128, exact since |X| < 2^126.  Then one
+// accumulators of 32-bit limbs (each term below 2^48, at most 8 of them; the
+// limbs above W_g's highest nonzero one only receive carries), carried, and X
+// is formed modulo 2^128, exact since |X| < 2^126.  Then one
 // rounding: c = RN(X) 2^(e_i + f_k - 2 beta).  The four outputs' multiply-add
 // chains are interleaved.
 template <int K, int BN>
@@ -89,6 +90,7 @@ __device__ __forceinline__ void mod_recombine_tile(const EmuArgs& args, const Pr
   constexpr int NG = mod_groups(K);
   constexpr size_t SLOT = static_cast<size_t>(EM_BM) * BN;  // 16-bit entries per slot
   constexpr int QS = limbs_bit_length(mod_product(K)) - 31;  // V 2^-QS < 2^34
+  constexpr int LW = mod_weight_limbs(K);                      // nonzero limbs of every W_g
   // in_tile = ((c8 * 128 + r) * 2 + q): 8-column group c8, row r, half q of
   // the row's 16 bytes
   const int q = in_tile & 1, r = (in_tile >> 1) & (EM_BM - 1), c8 = in_tile >> 8;
@@ -109,7 +111,7 @@ __device__ __forceinline__ void mod_recombine_tile(const EmuArgs& args, const Pr
     for (int c = 0; c < 4; ++c) {
       const uint32_t T = ((c < 2 ? v[g].x : v[g].y) >> (16 * (c & 1))) & 0xFFFFu;
 #pragma unroll
-      for (int l = 0; l < 4; ++l) a[c][l] += static_cast<uint64_t>(T) * c_mod.wg[K][g][l];
+      for (int l = 0; l < LW; ++l) a[c][l] += static_cast<uint64_t>(T) * c_mod.wg[K][g][l];
     }
   }
   const uint64_t m_lo = (static_cast<uint64_t>(c_mod.mk[K][1]) << 32) | c_mod.mk[K][0];
