@@ -25,7 +25,11 @@
  *                   remainder theorem and rounded once to FP64 (after Ozaki,
  *                   Uchino and Imamura's "Ozaki scheme II", 2025): k products
  *                   instead of the s(s+1)/2 of the digit form.  Nothing in
- *                   the paper corresponds to it either.
+ *                   the paper corresponds to it either.  With the
+ *                   environment variable MM_PAIR_MMA=1, its tiles 256 columns
+ *                   wide run on CTA pairs (paired tcgen05.mma, 256 x 256
+ *                   tiles) instead of single CTAs: same results, measured
+ *                   slower on GB300, hence off by default.
  * MM_AUTO picks one per problem (see mm_config).
  *
  * Conventions for every call:

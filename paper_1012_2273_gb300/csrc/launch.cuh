@@ -129,6 +129,13 @@ cudaError_t split_launch(const Problem* table, const Problem* single, int count,
                          uint64_t* a_maxbits, uint64_t* b_maxbits, const int* max_offset, int* status,
                          cudaStream_t stream);
 
+// emu_gemm_pair.cu: the modular form's residue products on CTA pairs
+// (256 x 256 tiles; problems with m_pad a multiple of 256, B^T maps of
+// 128-row boxes; units index pair tiles; grid even)
+int mod_pair_smem_bytes();
+cudaError_t mod_pair_gemm_launch(const CUtensorMap* mapA, const CUtensorMap* mapB, const EmuArgs& args, int grid,
+                                 cudaStream_t stream);
+
 // emu_gemm.cu
 int emu_smem_bytes(int bn);
 cudaError_t emu_gemm_launch(int bn, bool modular, const CUtensorMap* mapA, const CUtensorMap* mapB,

@@ -292,6 +292,7 @@ struct EmuGroup {
   bool tabled = false;  // launched with a device problem/unit table (grouped calls)
   int groups = 0;       // forced pair groups per tile (0 = automatic)
   int bn = 256, grid = 1, max_pairs = 1;
+  bool pair = false;    // modular form at bn 256: CTA pairs (cta_group::2) on 256 x 256 tiles
   std::vector<Problem> ps;
   std::vector<int> max_off;        // offset of problem p in the maxbits arrays
   std::vector<CUtensorMap> maps;   // 2 per problem
@@ -332,9 +333,19 @@ int choose_groups_single(int tiles, int s, bool modular, int kb, int sms, int ma
 
 // Sizes the group's workspace and work units; with `base` set, also points
 // the problems into it and encodes the tensor maps.
+// CTA pairs (cta_group::2) for the modular form at bn 256 only with
+// MM_PAIR_MMA=1: on GB300 the paired kernel measured slower than the
+// single-CTA one over the paper's size sweep (0.309 against 0.278 ms of
+// residue products per step), so it is opt-in.
+bool pair_mma_enabled() {
+  const char* e = std::getenv("MM_PAIR_MMA");
+  return e && e[0] == '1';
+}
+
 mm_status layout_group(mm_handle h, EmuGroup& g, char* base) {
   Arena ar;
   g.total_tiles = g.total_split = g.total_absmax = g.max_rows = 0;
+  g.pair = g.form == 2 && g.bn == 256 && pair_mma_enabled() && h->num_sms >= 2;
   int maxn = 0;
   g.max_off.assign(g.ps.size(), 0);
   for (Problem& p : g.ps) maxn = std::max(maxn, p.n);
@@ -343,7 +354,7 @@ mm_status layout_group(mm_handle h, EmuGroup& g, char* base) {
   for (size_t i = 0; i < g.ps.size(); ++i) {
     Problem& p = g.ps[i];
     const int n = p.n;
-    p.m_pad = round_up(n, 128);
+    p.m_pad = round_up(n, g.pair ? 256 : 128);  // a pair covers two 128-row tiles
     p.n_pad = round_up(n, g.bn);
     p.k_pad = round_up(n, 64);
     p.tiles_m = p.m_pad / 128;
@@ -383,13 +394,15 @@ mm_status layout_group(mm_handle h, EmuGroup& g, char* base) {
   for (size_t i = 0; i < g.ps.size(); ++i) {
     Problem& p = g.ps[i];
     const int tiles = p.tiles_m * p.tiles_n;
+    // work-unit tiles: 256 x 256 pair tiles (two CTAs each) or 128-row tiles
+    const int unit_tiles = g.pair ? tiles / 2 : tiles;
     const int kb = p.k_pad / 64;
     const int P = mmk::problem_pairs(p);
     int G;
     if (g.groups > 0) {
       G = std::min(g.groups, P);
     } else if (g.ps.size() == 1) {
-      G = choose_groups_single(tiles, p.s, modular, kb, h->num_sms, g.max_pairs);
+      G = choose_groups_single(unit_tiles, p.s, modular, kb, g.pair ? h->num_sms / 2 : h->num_sms, g.max_pairs);
     } else {
       G = static_cast<int>(std::lround(P * kb / std::max(target, 1.0)));
       G = std::max(1, std::min(G, P));
@@ -413,7 +426,7 @@ mm_status layout_group(mm_handle h, EmuGroup& g, char* base) {
           int p0, p1;
           mmk::mod_group_range(p.s, G, gi, &p0, &p1);
           const int cost = (p1 - p0) * kb;
-          for (int t = 0; t < tiles; ++t) g.units.push_back(make_int4(static_cast<int>(i), t, gi, cost));
+          for (int t = 0; t < unit_tiles; ++t) g.units.push_back(make_int4(static_cast<int>(i), t, gi, cost));
         }
       }
       continue;
@@ -463,9 +476,9 @@ mm_status layout_group(mm_handle h, EmuGroup& g, char* base) {
     });
     g.total_units = static_cast<int>(g.units.size());
   } else {
-    g.total_units = g.ps[0].tiles_m * g.ps[0].tiles_n * g.ps[0].groups;
+    g.total_units = g.ps[0].tiles_m * g.ps[0].tiles_n / (g.pair ? 2 : 1) * g.ps[0].groups;
   }
-  g.grid = emu_grid(h, g.total_units);
+  g.grid = g.pair ? 2 * emu_grid(h, std::min(g.total_units, h->num_sms / 2)) : emu_grid(h, g.total_units);
   g.amax = ar.take(sizeof(uint64_t) * g.max_rows);
   g.bmax = ar.take(sizeof(uint64_t) * g.max_rows);
   g.scratch = ar.take(static_cast<size_t>(g.grid) * g.scratch_slots * slot * sizeof(int32_t));
@@ -478,7 +491,8 @@ mm_status layout_group(mm_handle h, EmuGroup& g, char* base) {
     for (size_t i = 0; i < g.ps.size(); ++i) {
       const Problem& p = g.ps[i];
       if (!make_plane_map(&g.maps[2 * i], p.a_slices, p.k_pad, static_cast<long>(p.s) * p.m_pad, 128) ||
-          !make_plane_map(&g.maps[2 * i + 1], p.b_slices, p.k_pad, static_cast<long>(p.s) * p.n_pad, g.bn))
+          !make_plane_map(&g.maps[2 * i + 1], p.b_slices, p.k_pad, static_cast<long>(p.s) * p.n_pad,
+                          g.pair ? g.bn / 2 : g.bn))
         return fail(h, MM_ERR_CUDA, "cuTensorMapEncodeTiled failed");
     }
   }
@@ -522,7 +536,8 @@ mm_status run_group(mm_handle h, const EmuGroup& g, const Problem* d_table, cons
   a.status = h->d_status;
   a.timeout_ns = h->timeout_ns;
   const long m_gemm = prof_start(h, stream, KIND_SLICE_GEMM);
-  const cudaError_t le = mmk::emu_gemm_launch(g.bn, g.form == 2, &g.maps[0], &g.maps[1], a, g.grid, stream);
+  const cudaError_t le = g.pair ? mmk::mod_pair_gemm_launch(&g.maps[0], &g.maps[1], a, g.grid, stream)
+                                : mmk::emu_gemm_launch(g.bn, g.form == 2, &g.maps[0], &g.maps[1], a, g.grid, stream);
   prof_end(h, stream, m_gemm);
   if (le != cudaSuccess) {
     char info[512];

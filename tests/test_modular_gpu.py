@@ -235,3 +235,35 @@ def test_grouped_call_mixing_native_digit_and_modular_forms(tmp_path, use_graph)
                 else:
                     assert_bits(C, oracle.fixed_gemm(A, B, beta_of(k, n)))
     assert {f for f, _ in plans.values()} == {0, 1, 2}
+
+
+@pytest.mark.parametrize("use_graph", [True, False])
+def test_modular_cta_pair_kernel_bit_exact(tmp_path, monkeypatch, use_graph):
+    # The opt-in paired kernel (two CTAs per 256 x 256 tile) computes the same
+    # residue products: single problems (rows padded to 256) and a grouped
+    # call with uneven sizes and moduli counts, bit for bit.
+    import paper_1012_2273_gb300 as mm
+    monkeypatch.setenv("MM_PAIR_MMA", "1")
+    tune = tmp_path / "tune.txt"
+    tune.write_text("300 2 14 256 0\n700 2 15 256 0\n100000 2 16 256 0\n")
+    flags = 0 if use_graph else mm.FLAG_NO_GRAPH
+    sizes = [1, 129, 257, 300, 385, 640, 1000]
+    pairs = [workload.pair("loguniform20", 60 + i, n) for i, n in enumerate(sizes)]
+    with mm.Handle("auto", flags=flags, tune_path=str(tune)) as h:
+        plans = {n: h.plan(n) for n in sizes}
+        for (A, B), n in zip(pairs[:3], sizes[:3]):
+            C = host(h.gemm(dev(A), dev(B)))
+            h.check()
+            form, k = plans[n]
+            if form == 2:
+                assert_bits(C, oracle.fixed_gemm(A, B, beta_of(k, n)))
+        Cs = h.gemm_grouped([dev(a) for a, _ in pairs], [dev(b) for _, b in pairs])
+        h.check()
+    for (A, B), C, n in zip(pairs, Cs, sizes):
+        form, k = plans[n]
+        C = host(C)
+        if form == 2:
+            assert_bits(C, oracle.fixed_gemm(A, B, beta_of(k, n)))
+        else:
+            assert_within_bound(C, oracle.gemm(A, B), oracle.absgemm(A, B), n)
+    assert plans[1000] == (2, 16) and plans[300] == (2, 14)
