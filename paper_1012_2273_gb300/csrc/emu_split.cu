@@ -415,9 +415,9 @@ __global__ void __launch_bounds__(SP_THREADS, 3) split_kernel(const __grid_const
     // Phase 1: source element (x, y) of the tile, x fastest (coalesced).
     //   A:   source row i = r0 + y, column j = c0 + x -> Ds[y][x]  (output row y)
     //   B^T: source row j = c0 + y, column k = r0 + x -> Ds[x][y]  (output row x)
-    // Each thread's 16 elements, 4 loads in flight at a time.
+    // Each thread's 16 elements, all 16 loads in flight at once.
     constexpr int PER = SP_TILE * SP_TILE / SP_THREADS;
-    constexpr int BATCH = 4;
+    constexpr int BATCH = 16;
     const int x = threadIdx.x % SP_TILE;
 #pragma unroll
     for (int q0 = 0; q0 < PER; q0 += BATCH) {
