@@ -314,32 +314,10 @@ __device__ __forceinline__ void write_residue_item(const long long (&D)[8], uint
   }
 }
 
-// Modular form, A tile: the planes are row-major like A, so no transpose is
-// needed -- each item (output row r, columns c0 + 8 cg ..) loads its 8 values
-// straight from A (a warp: 4 rows x 512 contiguous bytes) and writes one
-// 16-byte vector per plane (4 rows x 128 contiguous bytes).
-template <int K, int LIMBS>
-__device__ __forceinline__ void residue_tile_a(const uint64_t* src, int n, int r0, int c0, const int* ex_s,
-                                               int width, uint16_t* dst, int k_pad, size_t plane,
-                                               bool* nonfinite) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-#pragma unroll 1
-  for (int pass = 0; pass < 2; ++pass) {
-    const int r = (lane >> 3) + 4 * warp + 32 * pass, cg = lane & 7;
-    const int i = r0 + r, j0 = c0 + 8 * cg;
-    long long D[8];
-    uint64_t bits[8];
-#pragma unroll
-    for (int q = 0; q < 8; ++q) bits[q] = (i < n && j0 + q < n) ? src[static_cast<size_t>(i) * n + j0 + q] : 0ull;
-#pragma unroll
-    for (int q = 0; q < 8; ++q) D[q] = (i < n && j0 + q < n) ? fixed_point(bits[q], ex_s[r], width, nonfinite) : 0;
-    write_residue_item<K, LIMBS>(D, dst + static_cast<size_t>(i) * k_pad + j0, plane);
-  }
-}
-
-// Modular form, B^T tile, after the transpose into Ds: item (r, cg) with two
-// lanes per row -- every 8-byte shared load of a half-warp hits 16 distinct
-// bank pairs, and each row's two vectors per plane fill one 32-byte sector.
+// Modular form, phase 2 (the tile's D in Ds, output row first -- transposed
+// for B^T): item (r, cg) with two lanes per row -- every 8-byte shared load
+// of a half-warp hits 16 distinct bank pairs, and each row's two vectors per
+// plane fill one 32-byte sector.
 template <int K, int LIMBS>
 __device__ __forceinline__ void residue_tile_from_smem(const long long (&Ds)[SP_TILE][SP_TILE + 1], uint16_t* dst,
                                                        int r0, int c0, int k_pad, size_t plane) {
@@ -354,26 +332,14 @@ __device__ __forceinline__ void residue_tile_from_smem(const long long (&Ds)[SP_
   }
 }
 
-// Writes the digit planes of one 64 x 64 tile (digit count from the problem).
-// Phase 1 reads the tile coalesced along the source rows and stores each
-// fixed-point value D in shared memory, transposed for B^T; phase 2 turns 8
-// consecutive D of an output row into one 16-byte vector per plane (8 threads
-// write a row's 128 contiguous bytes).
+// Writes the K residue planes of one 64 x 64 tile from its D in Ds.
 template <int K>
-__device__ __forceinline__ void residue_tile(bool is_a, const uint64_t* src, int n, int r0, int c0, const int* ex_s,
-                                             int width, const long long (&Ds)[SP_TILE][SP_TILE + 1], uint16_t* dst,
-                                             int k_pad, size_t plane, bool* nonfinite) {
-  if (width <= 55) {  // |D| <= 2^55 < 2^56: four 14-bit limbs
-    if (is_a)
-      residue_tile_a<K, 4>(src, n, r0, c0, ex_s, width, dst, k_pad, plane, nonfinite);
-    else
-      residue_tile_from_smem<K, 4>(Ds, dst, r0, c0, k_pad, plane);
-  } else {
-    if (is_a)
-      residue_tile_a<K, 5>(src, n, r0, c0, ex_s, width, dst, k_pad, plane, nonfinite);
-    else
-      residue_tile_from_smem<K, 5>(Ds, dst, r0, c0, k_pad, plane);
-  }
+__device__ __forceinline__ void residue_tile(int r0, int c0, int width, const long long (&Ds)[SP_TILE][SP_TILE + 1],
+                                             uint16_t* dst, int k_pad, size_t plane) {
+  if (width <= 55)  // |D| <= 2^55 < 2^56: four 14-bit limbs
+    residue_tile_from_smem<K, 4>(Ds, dst, r0, c0, k_pad, plane);
+  else
+    residue_tile_from_smem<K, 5>(Ds, dst, r0, c0, k_pad, plane);
 }
 
 __global__ void __launch_bounds__(SP_THREADS, 3) split_kernel(const __grid_constant__ SplitArgs args) {
@@ -409,9 +375,7 @@ __global__ void __launch_bounds__(SP_THREADS, 3) split_kernel(const __grid_const
   }
   __syncthreads();
   bool nonfinite = false;
-  const bool direct = beta > 0 && is_a;  // modular A tiles skip the shared-memory pass
-
-  if (!direct) {
+  {
     // Phase 1: source element (x, y) of the tile, x fastest (coalesced).
     //   A:   source row i = r0 + y, column j = c0 + x -> Ds[y][x]  (output row y)
     //   B^T: source row j = c0 + y, column k = r0 + x -> Ds[x][y]  (output row x)
@@ -445,11 +409,11 @@ __global__ void __launch_bounds__(SP_THREADS, 3) split_kernel(const __grid_const
   if (beta > 0) {
     switch (S) {
 #define MM_RESIDUE_CASE(K) \
-  case K: residue_tile<K>(is_a, src, n, r0, c0, ex_s, width, Ds, dst, P->k_pad, plane, &nonfinite); break;
+  case K: residue_tile<K>(r0, c0, width, Ds, dst, P->k_pad, plane); break;
       MM_RESIDUE_CASE(2) MM_RESIDUE_CASE(3) MM_RESIDUE_CASE(4) MM_RESIDUE_CASE(5) MM_RESIDUE_CASE(6)
       MM_RESIDUE_CASE(7) MM_RESIDUE_CASE(8) MM_RESIDUE_CASE(9) MM_RESIDUE_CASE(10) MM_RESIDUE_CASE(11)
       MM_RESIDUE_CASE(12) MM_RESIDUE_CASE(13) MM_RESIDUE_CASE(14) MM_RESIDUE_CASE(15)
-      default: residue_tile<16>(is_a, src, n, r0, c0, ex_s, width, Ds, dst, P->k_pad, plane, &nonfinite); break;
+      default: residue_tile<16>(r0, c0, width, Ds, dst, P->k_pad, plane); break;
 #undef MM_RESIDUE_CASE
     }
   } else {
