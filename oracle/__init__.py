@@ -101,6 +101,12 @@ def lib() -> ctypes.CDLL:
             L.or_fixed_gemm.restype = c_int
             L.or_fixed_gemm_rows.argtypes = [c_int, c_int, _D, _D, _I, c_int, _D, c_int]
             L.or_fixed_gemm_rows.restype = c_int
+            L.or_gemm_mnk.argtypes = [c_int, c_int, c_int, _D, _D, _I, c_int, _D, c_int]
+            L.or_absgemm_mnk.argtypes = [c_int, c_int, c_int, _D, _D, _D, c_int]
+            L.or_fixed_gemm_mnk.argtypes = [c_int, c_int, c_int, c_int, _D, _D, _I, c_int, _D, c_int]
+            L.or_fixed_gemm_mnk.restype = c_int
+            L.or_emu_gemm_mnk.argtypes = [c_int, c_int, c_int, c_int, _D, _D, _I, c_int, _D, c_int]
+            L.or_emu_gemm_mnk.restype = c_int
             _lib = L
     return _lib
 
@@ -316,3 +322,63 @@ def fixed_gemm_rows(A, B, beta: int, rows, nthreads: int | None = None) -> np.nd
     if rc != 0:
         raise ValueError(f"oracle: fixed_gemm_rows failed ({rc})")
     return out
+
+
+# ---------------------------------------------------------------------------
+# Rectangular products: C (m x n) = A (m x k) . B (k x n), section 5 of
+# oracle.c (the paper's NRA x NCA times NCA x NCB, Alg. 2).
+# ---------------------------------------------------------------------------
+def _rect(A, B):
+    A = _f64(A)
+    B = _f64(B)
+    if A.ndim != 2 or B.ndim != 2 or A.shape[1] != B.shape[0]:
+        raise ValueError(f"oracle: shapes {A.shape} and {B.shape} do not chain")
+    return A, B, A.shape[0], B.shape[1], A.shape[1]
+
+
+def _rows_arg(rows, m):
+    if rows is None:
+        return None, m
+    r = np.ascontiguousarray(rows, dtype=np.int32)
+    return r, len(r)
+
+
+def gemm_mnk(A, B, rows=None, nthreads: int | None = None) -> np.ndarray:
+    """Alg. 1's sum for rectangular operands (j increasing from 0.0)."""
+    A, B, m, n, k = _rect(A, B)
+    r, nr = _rows_arg(rows, m)
+    C = np.empty((nr, n), np.float64)
+    lib().or_gemm_mnk(m, n, k, _dp(A), _dp(B), r.ctypes.data_as(_I) if r is not None else None, nr, _dp(C),
+                      threads(nthreads))
+    return C
+
+
+def absgemm_mnk(A, B, nthreads: int | None = None) -> np.ndarray:
+    A, B, m, n, k = _rect(A, B)
+    C = np.empty((m, n), np.float64)
+    lib().or_absgemm_mnk(m, n, k, _dp(A), _dp(B), _dp(C), threads(nthreads))
+    return C
+
+
+def fixed_gemm_mnk(A, B, beta: int, rows=None, nthreads: int | None = None) -> np.ndarray:
+    """The modular form's result for rectangular operands (exponents over the k entries)."""
+    A, B, m, n, k = _rect(A, B)
+    r, nr = _rows_arg(rows, m)
+    C = np.empty((nr, n), np.float64)
+    rc = lib().or_fixed_gemm_mnk(m, n, k, int(beta), _dp(A), _dp(B), r.ctypes.data_as(_I) if r is not None else None,
+                                 nr, _dp(C), threads(nthreads))
+    if rc != 0:
+        raise ValueError(f"oracle: fixed_gemm_mnk failed ({rc})")
+    return C
+
+
+def emu_gemm_mnk(A, B, s: int, rows=None, nthreads: int | None = None) -> np.ndarray:
+    """The digit form's result for rectangular operands."""
+    A, B, m, n, k = _rect(A, B)
+    r, nr = _rows_arg(rows, m)
+    C = np.empty((nr, n), np.float64)
+    rc = lib().or_emu_gemm_mnk(m, n, k, int(s), _dp(A), _dp(B), r.ctypes.data_as(_I) if r is not None else None,
+                               nr, _dp(C), threads(nthreads))
+    if rc != 0:
+        raise ValueError(f"oracle: emu_gemm_mnk failed ({rc})")
+    return C

@@ -10,7 +10,8 @@
  * Contraction is off so that every a*b is rounded before it is added, as the
  * paper's C loops do on its 2010 x86 CPUs.
  *
- * Layout: every matrix is square, row-major, leading dimension n.
+ * Layout: row-major, dense.  Sections 1-4 take square n x n matrices;
+ * section 5 takes C (m x n) = A (m x k) . B (k x n).
  *
  * Contents
  *   1. The product as the paper defines it (Alg. 1, Sec. 3.1; the same
@@ -24,6 +25,10 @@
  *      only); it follows the error-free splitting of Ozaki, Ogita, Oishi and
  *      Rump (Numer. Algorithms 59, 2012) with a fixed-point reading that is
  *      spelled out at each function.
+ *   4. The exact product of fixed-point operands, rounded once (the model
+ *      of the library's modular form; no counterpart in the paper).
+ *   5. Sections 1, 2 (|A||B|), 3 and 4 for rectangular shapes (the paper's
+ *      NRA x NCA times NCA x NCB of Alg. 2).
  */
 #include <math.h>
 #include <stdint.h>
@@ -536,4 +541,154 @@ int or_fixed_gemm(int n, int beta, const double* A, const double* B, double* C, 
   const int r = or_fixed_gemm_rows(n, beta, A, B, rows, n, C, nthreads);
   free(rows);
   return r;
+}
+
+/* ------------------------------------------------------------------------ */
+/* 5. Rectangular products: C (m x n) = A (m x k) . B (k x n)                */
+/* ------------------------------------------------------------------------ */
+/*
+ * The paper's experiments are square, but its master/worker program names
+ * the three dimensions separately (NRA rows of A, NCA columns of A = rows
+ * of B, NCB columns of B; Alg. 2) and the product is defined for any of
+ * them.  The functions below are the sections above with the three
+ * dimensions kept apart; every matrix is row-major and dense (leading
+ * dimension = its column count).  `rows` selects output rows (NULL: all m,
+ * nrows = m); output row r goes to C[r * n ...].
+ */
+
+/* Section 1's product: c(i,l) = sum_j a(i,j) b(j,l), j increasing from 0.0. */
+void or_gemm_mnk(int m, int n, int k, const double* A, const double* B, const int* rows, int nrows,
+                 double* C, int nthreads) {
+  if (!rows) nrows = m;
+#ifdef _OPENMP
+  if (nthreads < 1) nthreads = 1;
+#pragma omp parallel for schedule(static) num_threads(nthreads)
+#endif
+  for (int r = 0; r < nrows; ++r) {
+    const int i = rows ? rows[r] : r;
+    double* c = C + (size_t)r * n;
+    for (int l = 0; l < n; ++l) c[l] = 0.0;
+    for (int j = 0; j < k; ++j) {
+      const double a = A[(size_t)i * k + j];
+      const double* b = B + (size_t)j * n;
+      for (int l = 0; l < n; ++l) c[l] = c[l] + a * b[l];
+    }
+  }
+  (void)nthreads;
+}
+
+/* |A||B| for the componentwise error measure. */
+void or_absgemm_mnk(int m, int n, int k, const double* A, const double* B, double* C, int nthreads) {
+#ifdef _OPENMP
+  if (nthreads < 1) nthreads = 1;
+#pragma omp parallel for schedule(static) num_threads(nthreads)
+#endif
+  for (int i = 0; i < m; ++i) {
+    double* c = C + (size_t)i * n;
+    for (int l = 0; l < n; ++l) c[l] = 0.0;
+    for (int j = 0; j < k; ++j) {
+      const double a = fabs(A[(size_t)i * k + j]);
+      const double* b = B + (size_t)j * n;
+      for (int l = 0; l < n; ++l) c[l] = c[l] + a * fabs(b[l]);
+    }
+  }
+  (void)nthreads;
+}
+
+/* Section 4's fixed-point product: e_i over the k entries of row i of A,
+ * f_l over the k entries of column l of B, X = sum_j A_int B_int exactly,
+ * c = RN(X) 2^(e_i + f_l - 2 beta).  |X| <= k 2^(2 beta).  0 on success. */
+int or_fixed_gemm_mnk(int m, int n, int k, int beta, const double* A, const double* B, const int* rows,
+                      int nrows, double* C, int nthreads) {
+  if (m < 0 || n < 0 || !fixed_args_ok(k, beta)) return -1;
+  if (!rows) nrows = m;
+  if (nrows == 0 || n == 0) return 0;
+  int* f = (int*)malloc(sizeof(int) * (size_t)n);
+  int64_t* Bi = (int64_t*)malloc(sizeof(int64_t) * (size_t)k * n + 1);
+  if (!f || !Bi) { free(f); free(Bi); return -2; }
+  for (int l = 0; l < n; ++l) f[l] = exponent_of_max(B + l, k, (size_t)n);
+  for (int j = 0; j < k; ++j)
+    for (int l = 0; l < n; ++l) Bi[(size_t)j * n + l] = or_fix(B[(size_t)j * n + l], f[l], beta);
+  int bad = 0;
+#ifdef _OPENMP
+  if (nthreads < 1) nthreads = 1;
+#pragma omp parallel for schedule(dynamic) num_threads(nthreads) reduction(+ : bad)
+#endif
+  for (int r = 0; r < nrows; ++r) {
+    const double* a = A + (size_t)(rows ? rows[r] : r) * k;
+    const int e = exponent_of_max(a, k, 1);
+    __int128* acc = (__int128*)malloc(sizeof(__int128) * (size_t)n);
+    if (!acc) { ++bad; continue; }
+    for (int l = 0; l < n; ++l) acc[l] = 0;
+    for (int j = 0; j < k; ++j) {
+      const __int128 aj = or_fix(a[j], e, beta);
+      const int64_t* b = Bi + (size_t)j * n;
+      for (int l = 0; l < n; ++l) acc[l] += aj * (__int128)b[l];
+    }
+    for (int l = 0; l < n; ++l) C[(size_t)r * n + l] = ldexp((double)acc[l], e + f[l] - 2 * beta);
+    free(acc);
+  }
+  (void)nthreads;
+  free(f);
+  free(Bi);
+  return bad ? -2 : 0;
+}
+
+/* Section 3's digit model with s digits: the same exponents as above, the
+ * digits d_t of D = round-half-even(v 2^(8s-1-e)), the exact level sums over
+ * the pairs t + u <= s + 1 (one int32 sum per pair: k 2^14 < 2^31), and one
+ * rounding per output (or_emu_combine).  0 on success. */
+int or_emu_gemm_mnk(int m, int n, int k, int s, const double* A, const double* B, const int* rows, int nrows,
+                    double* C, int nthreads) {
+  if (s < 1 || s > OR_EMU_MAX_SLICES || m < 0 || n < 0 || k < 0 || k >= (1 << 17)) return -1;
+  if (!rows) nrows = m;
+  if (nrows == 0 || n == 0) return 0;
+  int* f = (int*)malloc(sizeof(int) * (size_t)n);
+  int16_t* dB = (int16_t*)malloc(sizeof(int16_t) * (size_t)s * k * n + 1);
+  if (!f || !dB) { free(f); free(dB); return -2; }
+  int d[OR_EMU_MAX_SLICES];
+  for (int l = 0; l < n; ++l) f[l] = exponent_of_max(B + l, k, (size_t)n);
+  for (int j = 0; j < k; ++j)
+    for (int l = 0; l < n; ++l) {
+      or_emu_digits_of(or_emu_fixed(B[(size_t)j * n + l], f[l], s), s, d);
+      for (int u = 0; u < s; ++u) dB[((size_t)u * k + j) * n + l] = (int16_t)d[u];
+    }
+  int bad = 0;
+#ifdef _OPENMP
+  if (nthreads < 1) nthreads = 1;
+#pragma omp parallel for schedule(dynamic) num_threads(nthreads) reduction(+ : bad)
+#endif
+  for (int r = 0; r < nrows; ++r) {
+    const double* a = A + (size_t)(rows ? rows[r] : r) * k;
+    const int e = exponent_of_max(a, k, 1);
+    int16_t* da = (int16_t*)malloc(sizeof(int16_t) * (size_t)s * k + 1);
+    int64_t* S = (int64_t*)calloc((size_t)s * n, sizeof(int64_t));
+    int32_t* acc = (int32_t*)malloc(sizeof(int32_t) * (size_t)n);
+    if (!da || !S || !acc) { free(da); free(S); free(acc); ++bad; continue; }
+    int dd[OR_EMU_MAX_SLICES];
+    for (int j = 0; j < k; ++j) {
+      or_emu_digits_of(or_emu_fixed(a[j], e, s), s, dd);
+      for (int t = 0; t < s; ++t) da[(size_t)t * k + j] = (int16_t)dd[t];
+    }
+    for (int t = 1; t <= s; ++t)
+      for (int u = 1; t + u <= s + 1; ++u) {
+        for (int l = 0; l < n; ++l) acc[l] = 0;
+        for (int j = 0; j < k; ++j) {
+          const int32_t aj = da[(size_t)(t - 1) * k + j];
+          const int16_t* bj = dB + ((size_t)(u - 1) * k + j) * n;
+          for (int l = 0; l < n; ++l) acc[l] += aj * (int32_t)bj[l];
+        }
+        for (int l = 0; l < n; ++l) S[(size_t)(t + u - 2) * n + l] += acc[l];
+      }
+    int64_t lv[OR_EMU_MAX_SLICES];
+    for (int l = 0; l < n; ++l) {
+      for (int L = 0; L < s; ++L) lv[L] = S[(size_t)L * n + l];
+      C[(size_t)r * n + l] = or_emu_combine(lv, s, e, f[l]);
+    }
+    free(da); free(S); free(acc);
+  }
+  (void)nthreads;
+  free(f);
+  free(dB);
+  return bad ? -2 : 0;
 }

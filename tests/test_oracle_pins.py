@@ -438,3 +438,100 @@ def test_modular_width_rule():
     assert oracle.modular_beta(16, 2000) == 56 and oracle.modular_beta(16, 16384) == 55
     assert oracle.modular_beta(14, 8192) == 48 and oracle.modular_beta(14, 2000) == 49
     assert oracle.modular_beta(15, 2000) == 52
+
+
+# ---------------------------------------------------------------------------
+# Rectangular products (oracle section 5): C (m x n) = A (m x k) . B (k x n)
+# ---------------------------------------------------------------------------
+RECT_SHAPES = [(1, 1, 1), (1, 5, 3), (4, 1, 6), (3, 7, 1), (5, 3, 9), (9, 4, 2), (6, 6, 6)]
+
+
+def _py_left_to_right(A, B):
+    m, k = A.shape
+    n = B.shape[1]
+    C = np.empty((m, n))
+    for i in range(m):
+        for l in range(n):
+            c = 0.0
+            for j in range(k):
+                c = c + float(A[i, j]) * float(B[j, l])  # Python floats: rounded product, rounded sum
+            C[i, l] = c
+    return C
+
+
+def _py_fixed_product_mnk(A, B, beta):
+    """Every step with Python integers and fractions, for any m x k times k x n."""
+    m, k = A.shape
+    n = B.shape[1]
+    e = [_py_exponent(A[i, :]) for i in range(m)]
+    f = [_py_exponent(B[:, l]) for l in range(n)]
+    Ai = [[round(Fraction(float(A[i, j])) * Fraction(2) ** (beta - e[i])) for j in range(k)] for i in range(m)]
+    Bi = [[round(Fraction(float(B[j, l])) * Fraction(2) ** (beta - f[l])) for l in range(n)] for j in range(k)]
+    C = np.empty((m, n))
+    for i in range(m):
+        for l in range(n):
+            X = sum(Ai[i][j] * Bi[j][l] for j in range(k))
+            C[i, l] = float(Fraction(X) * Fraction(2) ** (e[i] + f[l] - 2 * beta))
+    return C
+
+
+@pytest.mark.parametrize("m,n,k", RECT_SHAPES)
+def test_rect_product_is_the_left_to_right_sum(m, n, k):
+    A, B = workload.rect_pair("uniform11", 7 * m + n + k, m, n, k)
+    want = _py_left_to_right(A, B)
+    np.testing.assert_array_equal(oracle.gemm_mnk(A, B), want)
+    np.testing.assert_array_equal(oracle.gemm_mnk(A, B, rows=[m - 1, 0]), want[[m - 1, 0]])
+    np.testing.assert_array_equal(oracle.absgemm_mnk(A, B), _py_left_to_right(np.abs(A), np.abs(B)))
+
+
+def test_rect_functions_reduce_to_the_square_ones():
+    n = 23
+    A, B = workload.pair("loguniform20", 5, n)
+    A2, B2 = workload.rect_pair("loguniform20", 5, n, n, n)
+    np.testing.assert_array_equal(A, A2)
+    np.testing.assert_array_equal(B, B2)
+    np.testing.assert_array_equal(oracle.gemm_mnk(A, B), oracle.gemm(A, B))
+    np.testing.assert_array_equal(oracle.fixed_gemm_mnk(A, B, 45), oracle.fixed_gemm(A, B, 45))
+    np.testing.assert_array_equal(oracle.emu_gemm_mnk(A, B, 7), oracle.emu_gemm(A, B, 7))
+
+
+@pytest.mark.parametrize("m,n,k", [(5, 3, 40), (2, 9, 17), (12, 1, 33)])
+def test_rect_integer_products_are_exact(m, n, k):
+    A, B = workload.rect_pair("int8", 3 + k, m, n, k)
+    want = (A.astype(np.int64) @ B.astype(np.int64)).astype(np.float64)
+    np.testing.assert_array_equal(oracle.gemm_mnk(A, B), want)
+    np.testing.assert_array_equal(oracle.fixed_gemm_mnk(A, B, 20), want)
+    np.testing.assert_array_equal(oracle.emu_gemm_mnk(A, B, 2), want)
+
+
+@pytest.mark.parametrize("m,n,k", RECT_SHAPES)
+@pytest.mark.parametrize("beta", [5, 33, 60])
+def test_rect_fixed_product_against_exact_integers(m, n, k, beta):
+    A, B = workload.rect_pair("loguniform20", 11 * m + k, m, n, k)
+    A[0, 0] = 0.0
+    np.testing.assert_array_equal(oracle.fixed_gemm_mnk(A, B, beta), _py_fixed_product_mnk(A, B, beta))
+
+
+@pytest.mark.parametrize("m,n,k", [(5, 3, 9), (9, 4, 2), (1, 7, 30), (13, 2, 5)])
+def test_rect_emulation_models_commute_with_transposition(m, n, k):
+    # (A B)^T = B^T A^T: a row exponent of A becomes a column exponent of
+    # A^T, the digit pairs (t, u) become (u, t) -- the kept set t + u <= s + 1
+    # is symmetric -- and every integer sum is the same, so both models give
+    # the transposed result bit for bit.  A swapped exponent, a row/column
+    # mix-up or an asymmetric pair set breaks it.
+    A, B = workload.rect_pair("loguniform20", 17 + m, m, n, k)
+    for s in (3, 7):
+        np.testing.assert_array_equal(oracle.emu_gemm_mnk(A, B, s), oracle.emu_gemm_mnk(B.T, A.T, s).T)
+    for beta in (21, 58):
+        np.testing.assert_array_equal(oracle.fixed_gemm_mnk(A, B, beta), oracle.fixed_gemm_mnk(B.T, A.T, beta).T)
+
+
+def test_rect_emulation_model_error_bound():
+    # With enough digits the digit model is within 2 k u |A||B| of the exact product.
+    m, n, k = 7, 5, 300
+    A, B = workload.rect_pair("uniform11", 2, m, n, k)
+    exact = np.array([[float(sum(Fraction(float(A[i, j])) * Fraction(float(B[j, l])) for j in range(k)))
+                       for l in range(n)] for i in range(m)])
+    absab = oracle.absgemm_mnk(A, B)
+    for C in (oracle.emu_gemm_mnk(A, B, 7), oracle.fixed_gemm_mnk(A, B, 55), oracle.gemm_mnk(A, B)):
+        assert np.all(np.abs(C - exact) <= 2 * k * 2.0 ** -53 * absab)

@@ -72,6 +72,14 @@ def pair(dist: str, seed: int, n: int) -> tuple[np.ndarray, np.ndarray]:
     return matrix(dist, seed, n, "A"), matrix(dist, seed, n, "B")
 
 
+def rect_pair(dist: str, seed: int, m: int, n: int, k: int) -> tuple[np.ndarray, np.ndarray]:
+    """Operands of a rectangular product: A (m x k) and B (k x n), row-major,
+    from the same streams as pair() (m = n = k gives pair()'s matrices)."""
+    A = np.ascontiguousarray(values(dist, seed, m * k).reshape(m, k))
+    B = np.ascontiguousarray(values(dist, seed + B_STREAM_OFFSET, k * n).reshape(k, n))
+    return A, B
+
+
 def loguniform_sizes(count: int, lo: int, hi: int, seed: int) -> list[int]:
     """``count`` sizes N log-uniform over the integers [lo, hi].
 
