@@ -52,7 +52,8 @@ class _Config(ctypes.Structure):
                 ("tune_path", ctypes.c_char_p)]
 
 
-SYMBOLS = ("mm_create", "mm_destroy", "mm_gemm", "mm_gemm_grouped", "mm_gemm_host", "mm_gemm_grouped_host",
+SYMBOLS = ("mm_create", "mm_destroy", "mm_gemm", "mm_gemm_grouped", "mm_gemm_ex", "mm_gemm_grouped_ex",
+           "mm_gemm_host", "mm_gemm_grouped_host",
            "mm_status_get",
            "mm_last_error", "mm_plan", "mm_profile_read", "mm_probe_fp64_peak", "mm_selftest_wait", "mm_split",
            "mm_split_noalloc",
@@ -80,6 +81,10 @@ def lib(build_if_needed: bool = True) -> ctypes.CDLL:
             L.mm_gemm.argtypes = [vp, ci, vp, vp, vp, vp]
             L.mm_gemm_grouped.argtypes = [vp, ci, ctypes.POINTER(ci), ctypes.POINTER(vp), ctypes.POINTER(vp),
                                           ctypes.POINTER(vp), vp]
+            L.mm_gemm_ex.argtypes = [vp, ci, ci, ci, vp, ci, vp, ci, vp, ci, vp]
+            pi_ = ctypes.POINTER(ci)
+            L.mm_gemm_grouped_ex.argtypes = [vp, ci, pi_, pi_, pi_, ctypes.POINTER(vp), pi_, ctypes.POINTER(vp), pi_,
+                                             ctypes.POINTER(vp), pi_, vp]
             L.mm_gemm_host.argtypes = [vp, ci, vp, vp, vp, vp]
             L.mm_gemm_grouped_host.argtypes = [vp, ci, ctypes.POINTER(ci), ctypes.POINTER(vp), ctypes.POINTER(vp),
                                                ctypes.POINTER(vp), vp]
@@ -120,6 +125,30 @@ def _check_tensor(t, name: str, n: int | None = None):
         raise ValueError(f"{name} must be contiguous (row-major)")
     if t.dim() != 2 or t.shape[0] != t.shape[1] or (n is not None and t.shape[0] != n):
         raise ValueError(f"{name} must be square" + (f" of size {n}" if n is not None else ""))
+
+
+def _matrix(t, name: str):
+    """(rows, cols, leading dimension) of a row-major float64 CUDA matrix view."""
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != torch.float64:
+        raise TypeError(f"{name} must be float64")
+    if t.dim() != 2:
+        raise ValueError(f"{name} must be 2-D")
+    rows, cols = int(t.shape[0]), int(t.shape[1])
+    if cols > 1 and t.stride(1) != 1:
+        raise ValueError(f"{name} must be row-major (unit column stride)")
+    ld = int(t.stride(0)) if rows > 1 and cols > 0 else cols
+    if ld < cols:
+        raise ValueError(f"{name}: row stride below the row length")
+    return rows, cols, max(ld, 1)
+
+
+def _square_contiguous(*ts) -> bool:
+    n = ts[0].shape[0]
+    return all(t.dim() == 2 and t.shape[0] == n and t.shape[1] == n and t.is_contiguous() and t.data_ptr() % 16 == 0
+               for t in ts)
 
 
 def split_noalloc(M, by_columns: bool, slices: int, exps, digits, status=None, stream=None) -> int:
@@ -190,15 +219,24 @@ class Handle:
 
     # -- the product -----------------------------------------------------------
     def gemm(self, A, B, C=None, stream=None):
-        """C = A.B on the device (asynchronous on `stream`)."""
+        """C = A.B on the device (asynchronous on `stream`).  A (M x K) and B
+        (K x N) are row-major float64 CUDA tensors, possibly views with a row
+        stride (mm_gemm_ex); square contiguous operands take mm_gemm."""
         import torch
-        _check_tensor(A, "A")
-        n = A.shape[0]
-        _check_tensor(B, "B", n)
+        m, k, lda = _matrix(A, "A")
+        k2, n, ldb = _matrix(B, "B")
+        if k2 != k:
+            raise ValueError(f"inner dimensions differ: A is {m} x {k}, B is {k2} x {n}")
         if C is None:
-            C = torch.empty_like(A)
-        _check_tensor(C, "C", n)
-        self._raise(self._lib.mm_gemm(self._h, n, A.data_ptr(), B.data_ptr(), C.data_ptr(), _stream_ptr(stream)))
+            C = torch.empty((m, n), dtype=torch.float64, device=A.device)
+        mc, nc, ldc = _matrix(C, "C")
+        if (mc, nc) != (m, n):
+            raise ValueError(f"C must be {m} x {n}")
+        if _square_contiguous(A, B, C):
+            self._raise(self._lib.mm_gemm(self._h, n, A.data_ptr(), B.data_ptr(), C.data_ptr(), _stream_ptr(stream)))
+        else:
+            self._raise(self._lib.mm_gemm_ex(self._h, m, n, k, A.data_ptr(), lda, B.data_ptr(), ldb, C.data_ptr(), ldc,
+                                             _stream_ptr(stream)))
         return C
 
     def gemm_grouped(self, As: Sequence, Bs: Sequence, Cs: Sequence | None = None, stream=None):
@@ -207,18 +245,25 @@ class Handle:
         if len(Bs) != count or (Cs is not None and len(Cs) != count):
             raise ValueError("As, Bs, Cs must have the same length")
         if Cs is None:
-            Cs = [torch.empty_like(a) for a in As]
-        ns = (ctypes.c_int * count)()
-        pa = (ctypes.c_void_p * count)()
-        pb = (ctypes.c_void_p * count)()
-        pc = (ctypes.c_void_p * count)()
+            Cs = [torch.empty((a.shape[0], b.shape[1]), dtype=torch.float64, device=a.device) for a, b in zip(As, Bs)]
+        dims = []
         for i, (a, b, c) in enumerate(zip(As, Bs, Cs)):
-            _check_tensor(a, f"As[{i}]")
-            n = a.shape[0]
-            _check_tensor(b, f"Bs[{i}]", n)
-            _check_tensor(c, f"Cs[{i}]", n)
-            ns[i], pa[i], pb[i], pc[i] = n, a.data_ptr(), b.data_ptr(), c.data_ptr()
-        self._raise(self._lib.mm_gemm_grouped(self._h, count, ns, pa, pb, pc, _stream_ptr(stream)))
+            m, k, lda = _matrix(a, f"As[{i}]")
+            k2, n, ldb = _matrix(b, f"Bs[{i}]")
+            mc, nc, ldc = _matrix(c, f"Cs[{i}]")
+            if k2 != k or (mc, nc) != (m, n):
+                raise ValueError(f"problem {i}: shapes {tuple(a.shape)} x {tuple(b.shape)} -> {tuple(c.shape)}")
+            dims.append((m, n, k, lda, ldb, ldc))
+        pa = (ctypes.c_void_p * count)(*[a.data_ptr() for a in As])
+        pb = (ctypes.c_void_p * count)(*[b.data_ptr() for b in Bs])
+        pc = (ctypes.c_void_p * count)(*[c.data_ptr() for c in Cs])
+        if all(_square_contiguous(a, b, c) for a, b, c in zip(As, Bs, Cs)):
+            ns = (ctypes.c_int * count)(*[d[1] for d in dims])
+            self._raise(self._lib.mm_gemm_grouped(self._h, count, ns, pa, pb, pc, _stream_ptr(stream)))
+        else:
+            col = [(ctypes.c_int * count)(*[d[j] for d in dims]) for j in range(6)]
+            self._raise(self._lib.mm_gemm_grouped_ex(self._h, count, col[0], col[1], col[2], pa, col[3], pb, col[4], pc,
+                                                     col[5], _stream_ptr(stream)))
         return Cs
 
     def gemm_host(self, A, B, C=None, stream=None):

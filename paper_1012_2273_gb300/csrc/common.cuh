@@ -19,10 +19,13 @@ namespace mmk {
 // Problem table (one entry per independent product of a grouped call)
 // ---------------------------------------------------------------------------
 struct Problem {
-  const double* A;  // n x n row-major, lda = n (device)
-  const double* B;  // n x n row-major, ldb = n (device)
-  double* C;        // n x n row-major, ldc = n (device)
-  int n;
+  const double* A;  // m x k row-major, leading dimension lda (device)
+  const double* B;  // k x n row-major, leading dimension ldb (device)
+  double* C;        // m x n row-major, leading dimension ldc (device)
+  int n;            // columns of B and C (the square problem's N)
+  int m;            // rows of A and C
+  int k;            // columns of A, rows of B
+  int lda, ldb, ldc;
   int tile_begin;   // first linear tile of this problem in the grouped grid
   int tiles_m;      // tiles along rows of C
   int tiles_n;      // tiles along columns of C

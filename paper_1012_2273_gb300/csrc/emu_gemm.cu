@@ -583,9 +583,9 @@ __global__ void __launch_bounds__(EM_THREADS, 1)
         mine = before == U.G - 1;
         if (mine) __threadfence();
       }
-      if (!mine || row >= n) continue;
+      if (!mine || row >= P->m) continue;
       const int base_scale = P->a_exp[row] - 8 * s - 6;
-      double* crow = P->C + static_cast<size_t>(row) * n;
+      double* crow = P->C + static_cast<size_t>(row) * P->ldc;
       if (U.G > 1)
         recombine_row<BN, true>(tile_slots, s, U.G, maxp, r_in_tile, h * HALF, n0, n, base_scale, P->b_exp, crow);
       else

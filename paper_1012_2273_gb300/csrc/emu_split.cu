@@ -151,22 +151,22 @@ __global__ void __launch_bounds__(SP_THREADS) absmax_kernel(const __grid_constan
   __shared__ unsigned long long part[SP_THREADS / AM_BCOLS][AM_BCOLS];
   const Problem* P;
   const int pi = absmax_find(args, blockIdx.x, &P);
-  const int n = P->n;
-  const int a_blocks = P->m_pad > 0 ? (n + AM_ROWS - 1) / AM_ROWS : 0;
+  const int n = P->n, mrows = P->m, kdim = P->k;
+  const int a_blocks = P->m_pad > 0 ? (mrows + AM_ROWS - 1) / AM_ROWS : 0;
   int local = blockIdx.x - (args.table ? P->absmax_begin : 0);
   const int off = args.max_offset ? args.max_offset[pi] : 0;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (local < a_blocks) {
     const int i = local * AM_ROWS + warp;
-    if (i >= n) return;
-    const uint64_t* row = reinterpret_cast<const uint64_t*>(P->A) + static_cast<size_t>(i) * n;
+    if (i >= mrows) return;
+    const uint64_t* row = reinterpret_cast<const uint64_t*>(P->A) + static_cast<size_t>(i) * P->lda;
     unsigned long long m = 0;
-    for (int j0 = 0; j0 < n; j0 += 32 * 8) {
+    for (int j0 = 0; j0 < kdim; j0 += 32 * 8) {
       unsigned long long v[8];
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
         const int j = j0 + 32 * q + lane;
-        v[q] = j < n ? row[j] & 0x7FFFFFFFFFFFFFFFull : 0ull;
+        v[q] = j < kdim ? row[j] & 0x7FFFFFFFFFFFFFFFull : 0ull;
       }
 #pragma unroll
       for (int q = 0; q < 8; ++q) m = v[q] > m ? v[q] : m;
@@ -184,17 +184,18 @@ __global__ void __launch_bounds__(SP_THREADS) absmax_kernel(const __grid_constan
   const int k0 = (local % nbc) * AM_BCOLS, j0 = (local / nbc) * AM_BROWS;
   const int c = threadIdx.x % AM_BCOLS, ph = threadIdx.x / AM_BCOLS;
   constexpr int PHASES = SP_THREADS / AM_BCOLS;
-  const int k = k0 + c;
+  const int k = k0 + c;  // column of B
   const uint64_t* src = reinterpret_cast<const uint64_t*>(P->B);
+  const size_t ldb = P->ldb;
   unsigned long long m = 0;
   if (k < n) {
     for (int jj = ph; jj < AM_BROWS; jj += PHASES * 8) {
       unsigned long long v[8];
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
-        const int j = j0 + jj + PHASES * q;
-        v[q] = (jj + PHASES * q < AM_BROWS && j < n) ? src[static_cast<size_t>(j) * n + k] & 0x7FFFFFFFFFFFFFFFull
-                                                      : 0ull;
+        const int j = j0 + jj + PHASES * q;  // row of B
+        v[q] = (jj + PHASES * q < AM_BROWS && j < kdim) ? src[static_cast<size_t>(j) * ldb + k] & 0x7FFFFFFFFFFFFFFFull
+                                                         : 0ull;
       }
 #pragma unroll
       for (int q = 0; q < 8; ++q) m = v[q] > m ? v[q] : m;
@@ -367,11 +368,14 @@ __global__ void __launch_bounds__(SP_THREADS, 3) split_kernel(const __grid_const
   const uint64_t* maxbits = is_a ? args.a_maxbits + off : args.b_maxbits + off;
   int* exps = is_a ? P->a_exp : P->b_exp;
   if (threadIdx.x == 0) any_nonfinite = 0;
+  const int out_rows = is_a ? P->m : n;  // A: rows of A; B^T: columns of B
+  const int kdim = P->k;
+  const size_t ld = is_a ? P->lda : P->ldb;
   if (threadIdx.x < SP_TILE) {
     const int er = r0 + threadIdx.x;
-    const int e = er < n ? exponent_from_maxbits(maxbits[er]) : 0;
+    const int e = er < out_rows ? exponent_from_maxbits(maxbits[er]) : 0;
     ex_s[threadIdx.x] = e;
-    if (exps && c0 == 0 && er < n) exps[er] = e;
+    if (exps && c0 == 0 && er < out_rows) exps[er] = e;
   }
   __syncthreads();
   bool nonfinite = false;
@@ -379,6 +383,7 @@ __global__ void __launch_bounds__(SP_THREADS, 3) split_kernel(const __grid_const
     // Phase 1: source element (x, y) of the tile, x fastest (coalesced).
     //   A:   source row i = r0 + y, column j = c0 + x -> Ds[y][x]  (output row y)
     //   B^T: source row j = c0 + y, column k = r0 + x -> Ds[x][y]  (output row x)
+    // (A is m x kdim with leading dimension lda, B kdim x n with ldb)
     // Each thread's 16 elements, all 16 loads in flight at once.
     constexpr int PER = SP_TILE * SP_TILE / SP_THREADS;
     constexpr int BATCH = 16;
@@ -391,15 +396,17 @@ __global__ void __launch_bounds__(SP_THREADS, 3) split_kernel(const __grid_const
         const int y = threadIdx.x / SP_TILE + (q0 + b) * (SP_THREADS / SP_TILE);
         const int i = is_a ? r0 + y : c0 + y;  // source row
         const int j = is_a ? c0 + x : r0 + x;  // source column
-        bits[b] = (i < n && j < n) ? src[static_cast<size_t>(i) * n + j] : 0ull;
+        const bool in = is_a ? (i < out_rows && j < kdim) : (i < kdim && j < out_rows);
+        bits[b] = in ? src[static_cast<size_t>(i) * ld + j] : 0ull;
       }
 #pragma unroll
       for (int b = 0; b < BATCH; ++b) {
         const int y = threadIdx.x / SP_TILE + (q0 + b) * (SP_THREADS / SP_TILE);
         const int i = is_a ? r0 + y : c0 + y;
         const int j = is_a ? c0 + x : r0 + x;
+        const bool in = is_a ? (i < out_rows && j < kdim) : (i < kdim && j < out_rows);
         long long D = 0;
-        if (i < n && j < n) D = fixed_point(bits[b], ex_s[is_a ? y : x], width, &nonfinite);
+        if (in) D = fixed_point(bits[b], ex_s[is_a ? y : x], width, &nonfinite);
         if (is_a) Ds[y][x] = D; else Ds[x][y] = D;
       }
     }
@@ -436,14 +443,14 @@ __global__ void __launch_bounds__(SP_THREADS, 3) split_kernel(const __grid_const
 // Host side -------------------------------------------------------------------
 
 int split_tiles(const Problem& p) {
-  if (p.n <= 0) return 0;
+  if (p.n <= 0 || p.m <= 0 || p.k <= 0) return 0;
   return (p.m_pad / SP_TILE + p.n_pad / SP_TILE) * (p.k_pad / SP_TILE);
 }
 
 int absmax_blocks(const Problem& p) {
-  if (p.n <= 0) return 0;
-  const int a = p.m_pad > 0 ? (p.n + AM_ROWS - 1) / AM_ROWS : 0;
-  const int b = p.n_pad > 0 ? ((p.n + AM_BCOLS - 1) / AM_BCOLS) * ((p.n + AM_BROWS - 1) / AM_BROWS) : 0;
+  if (p.n <= 0 || p.m <= 0 || p.k <= 0) return 0;
+  const int a = p.m_pad > 0 ? (p.m + AM_ROWS - 1) / AM_ROWS : 0;
+  const int b = p.n_pad > 0 ? ((p.n + AM_BCOLS - 1) / AM_BCOLS) * ((p.k + AM_BROWS - 1) / AM_BROWS) : 0;
   return a + b;
 }
 

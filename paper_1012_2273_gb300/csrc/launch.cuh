@@ -113,7 +113,7 @@ struct EmuArgs {
 };
 
 // native_fp64.cu
-bool native_is_small(int n);
+bool native_is_small(const Problem& p);
 void native_small_fill_tiles(Problem& p);
 cudaError_t native_small_launch(const Problem* table, const Problem* single, int count, int total_tiles,
                                 cudaStream_t stream);

@@ -30,6 +30,22 @@ constexpr size_t kAlign = 256;
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 int round_up(int x, int a) { return (x + a - 1) / a * a; }
 
+// The square N x N problem: every dimension and leading dimension N.
+Problem square_problem(const double* A, const double* B, double* C, int N) {
+  Problem p{};
+  p.A = A;
+  p.B = B;
+  p.C = C;
+  p.n = p.m = p.k = N;
+  p.lda = p.ldb = p.ldc = N;
+  return p;
+}
+
+// Size a problem is planned by: its largest dimension.  The accuracy of both
+// emulation forms depends on the inner dimension k alone, and a plan tuned
+// for size max(m, n, k) >= k is at least as accurate as one for k.
+int plan_size(const Problem& p) { return std::max(p.m, std::max(p.n, p.k)); }
+
 // ---- driver entry point for tensor-map encoding (no -lcuda link needed) ----
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
@@ -346,17 +362,16 @@ mm_status layout_group(mm_handle h, EmuGroup& g, char* base) {
   Arena ar;
   g.total_tiles = g.total_split = g.total_absmax = g.max_rows = 0;
   g.pair = g.form == 2 && g.bn == 256 && pair_mma_enabled() && h->num_sms >= 2;
-  int maxn = 0;
+  int maxk = 0;
   g.max_off.assign(g.ps.size(), 0);
-  for (Problem& p : g.ps) maxn = std::max(maxn, p.n);
-  g.max_pairs = max_pairs_for(maxn);
+  for (Problem& p : g.ps) maxk = std::max(maxk, p.k);
+  g.max_pairs = max_pairs_for(maxk);
   long long work = 0;
   for (size_t i = 0; i < g.ps.size(); ++i) {
     Problem& p = g.ps[i];
-    const int n = p.n;
-    p.m_pad = round_up(n, g.pair ? 256 : 128);  // a pair covers two 128-row tiles
-    p.n_pad = round_up(n, g.bn);
-    p.k_pad = round_up(n, 64);
+    p.m_pad = round_up(p.m, g.pair ? 256 : 128);  // a pair covers two 128-row tiles
+    p.n_pad = round_up(p.n, g.bn);
+    p.k_pad = round_up(p.k, 64);
     p.tiles_m = p.m_pad / 128;
     p.tiles_n = p.n_pad / g.bn;
     p.tile_begin = g.total_tiles;
@@ -365,20 +380,20 @@ mm_status layout_group(mm_handle h, EmuGroup& g, char* base) {
     g.total_split += mmk::split_tiles(p);
     p.absmax_begin = g.total_absmax;
     g.total_absmax += mmk::absmax_blocks(p);
-    p.beta = g.form == 2 ? mmk::mod_beta(p.s, n) : 0;
+    p.beta = g.form == 2 ? mmk::mod_beta(p.s, p.k) : 0;  // the bound involves the inner dimension
     work += static_cast<long long>(p.tiles_m) * p.tiles_n * mmk::problem_pairs(p) * (p.k_pad / 64);
     const size_t a_sl = ar.take(static_cast<size_t>(p.s) * p.m_pad * p.k_pad * 2);
     const size_t b_sl = ar.take(static_cast<size_t>(p.s) * p.n_pad * p.k_pad * 2);
-    const size_t ae = ar.take(sizeof(int) * n);
-    const size_t be = ar.take(sizeof(int) * n);
+    const size_t ae = ar.take(sizeof(int) * p.m);
+    const size_t be = ar.take(sizeof(int) * p.n);
     if (base) {
       p.a_slices = reinterpret_cast<uint16_t*>(base + a_sl);
       p.b_slices = reinterpret_cast<uint16_t*>(base + b_sl);
       p.a_exp = reinterpret_cast<int*>(base + ae);
       p.b_exp = reinterpret_cast<int*>(base + be);
     }
-    g.max_off[i] = g.max_rows;
-    g.max_rows += n;
+    g.max_off[i] = g.max_rows;  // row maxima of A (m) and column maxima of B (n) share the offset
+    g.max_rows += std::max(p.m, p.n);
   }
   // Work units: pair groups per tile, then slot storage.  Grouped calls aim at
   // about MM_UNITS_PER_SM units per SM (default 4) so the dynamic scheduler
@@ -449,7 +464,7 @@ mm_status layout_group(mm_handle h, EmuGroup& g, char* base) {
     }
     // Short tiles (small N) leave the recombination to a separate pass: done
     // in the epilogue it stalls the tensor pipe for a large share of the tile.
-    p.defer = p.n < kDeferBelowN ? 1 : 0;
+    p.defer = p.k < kDeferBelowN ? 1 : 0;  // short k loops: few k-blocks per tile
     if (G > 1 || p.defer) {
       p.slot_base = g.tilebuf_elems;
       g.tilebuf_elems += static_cast<long long>(tiles) * p.nslots * slot;
@@ -561,22 +576,24 @@ mm_status run_group(mm_handle h, const EmuGroup& g, const Problem* d_table, cons
   return MM_OK;
 }
 
-mm_status check_emu_size(mm_handle h, int n, int s, int form) {
+// k: the inner dimension (N of a square problem), which bounds the exact sums.
+mm_status check_emu_size(mm_handle h, int k, int s, int form) {
   if (form == 2) {
     if (s < 2 || s > mmk::MOD_COUNT) return fail(h, MM_ERR_UNSUPPORTED, "the modular form takes 2..16 moduli");
-    if (n > 65535) return fail(h, MM_ERR_UNSUPPORTED, "the modular form supports N <= 65535");
-    if (mmk::mod_beta(s, n) < 1)
+    if (k > 65535) return fail(h, MM_ERR_UNSUPPORTED, "the modular form supports N (inner dimension K) <= 65535");
+    if (mmk::mod_beta(s, k) < 1)
       return fail(h, MM_ERR_UNSUPPORTED, "too few moduli for this N (the fixed-point width would be 0)");
     return MM_OK;
   }
   if (s < 1 || s > 8) return fail(h, MM_ERR_UNSUPPORTED, "slices must be in 1..8");
-  if (n > 131071) return fail(h, MM_ERR_UNSUPPORTED, "emulation supports N <= 131071 (one pair per int32 sum)");
+  if (k > 131071)
+    return fail(h, MM_ERR_UNSUPPORTED, "emulation supports N (inner dimension K) <= 131071 (one pair per int32 sum)");
   return MM_OK;
 }
 
 // Single emulated problem: workspace, maps, launches (no device table).
 mm_status emu_single(mm_handle h, const Problem& p, int form, int s, int bn, int groups, cudaStream_t stream) {
-  mm_status st = check_emu_size(h, p.n, s, form);
+  mm_status st = check_emu_size(h, p.k, s, form);
   if (st != MM_OK) return st;
   EmuGroup g;
   g.form = form;
@@ -594,7 +611,7 @@ mm_status emu_single(mm_handle h, const Problem& p, int form, int s, int bn, int
 }
 
 mm_status native_single(mm_handle h, Problem p, cudaStream_t stream) {
-  const bool small = mmk::native_is_small(p.n);
+  const bool small = mmk::native_is_small(p);
   if (small) mmk::native_small_fill_tiles(p); else mmk::native_fill_tiles(p);
   p.tile_begin = 0;
   const long m = prof_start(h, stream, KIND_NATIVE);
@@ -604,6 +621,313 @@ mm_status native_single(mm_handle h, Problem p, cudaStream_t stream) {
     MM_CUDA(h, mmk::native_launch(nullptr, &p, 1, p.tiles_m * p.tiles_n, stream));
   prof_end(h, stream, m);
   return MM_OK;
+}
+
+// The grouped product over a list of validated problems (any shapes; m or n
+// zero: skipped; k zero: C = 0).
+mm_status grouped_impl(mm_handle h, const std::vector<Problem>& probs, cudaStream_t user) {
+  prof_reset(h);
+  const bool use_graph = (h->cfg.flags & (MM_FLAG_NO_GRAPH | MM_FLAG_PROFILE)) == 0;
+
+  // A call identical to an earlier one replays its graph without redoing the
+  // host-side planning.  (Graphs are dropped whenever the arena is regrown.)
+  std::vector<long long> key;
+  key.reserve(9 * probs.size() + 3);
+  key.push_back(static_cast<long long>(probs.size()));
+  key.push_back(h->cfg.mode);
+  key.push_back(h->cfg.slices);
+  for (const Problem& q : probs) {
+    for (int v : {q.m, q.n, q.k, q.lda, q.ldb, q.ldc}) key.push_back(v);
+    key.push_back(static_cast<long long>(reinterpret_cast<uintptr_t>(q.A)));
+    key.push_back(static_cast<long long>(reinterpret_cast<uintptr_t>(q.B)));
+    key.push_back(static_cast<long long>(reinterpret_cast<uintptr_t>(q.C)));
+  }
+  auto it = h->graphs.end();
+  if (use_graph) {
+    it = h->graphs.find(key);
+    if (it != h->graphs.end()) {
+      MM_CUDA(h, cudaGraphLaunch(it->second.exec, user));
+      return MM_OK;
+    }
+  }
+
+  // Partition: native problems, and emulated problems by (slices, bn).
+  std::vector<Problem> nat;
+  std::map<std::tuple<int, int, int>, std::vector<Problem>> emu;  // (form, bn, groups)
+  std::vector<std::pair<Problem, Plan>> emu_plans;
+  for (const Problem& q : probs) {
+    if (q.m == 0 || q.n == 0) continue;
+    Problem p = q;
+    Plan pl = plan_for(h, plan_size(p));
+    if (p.k == 0) pl.form = 0;  // C = 0: the native kernel writes it
+    if (pl.form == 0) {
+      nat.push_back(p);
+    } else {
+      mm_status st = check_emu_size(h, p.k, pl.slices, pl.form);
+      if (st != MM_OK) return st;
+      p.s = pl.slices;
+      emu_plans.push_back({p, pl});
+    }
+  }
+  // All emulated problems of the call share one slice-product launch: the
+  // tile width is the one planned for the largest problem (digit counts may
+  // differ per problem).
+  if (!emu_plans.empty()) {
+    size_t big = 0;
+    for (size_t i = 1; i < emu_plans.size(); ++i)
+      if (plan_size(emu_plans[i].first) > plan_size(emu_plans[big].first)) big = i;
+    const int bn = emu_plans[big].second.bn;
+    for (auto& ep : emu_plans) emu[{ep.second.form, bn, ep.second.groups}].push_back(ep.first);
+  }
+  // Native problems: 64 x 64 tiles, or 16 x 16 tiles below 512 (two launches).
+  std::vector<Problem> nat_small;
+  {
+    std::vector<Problem> big;
+    for (const Problem& p : nat) (mmk::native_is_small(p) ? nat_small : big).push_back(p);
+    nat.swap(big);
+  }
+  int nat_tiles = 0, nat_small_tiles = 0;
+  for (Problem& p : nat) {
+    mmk::native_fill_tiles(p);
+    p.tile_begin = nat_tiles;
+    nat_tiles += p.tiles_m * p.tiles_n;
+  }
+  for (Problem& p : nat_small) {
+    mmk::native_small_fill_tiles(p);
+    p.tile_begin = nat_small_tiles;
+    nat_small_tiles += p.tiles_m * p.tiles_n;
+  }
+
+  // Workspace.  Emulation groups run one after another on the same stream, so
+  // they all start at offset 0 of the arena; a group whose workspace exceeds
+  // the limit is cut into waves (largest problems first), each run in turn.
+  size_t limit = 0;
+  {
+    size_t free_b = 0, total_b = 0;
+    if (const char* e = std::getenv("MM_WORKSPACE_LIMIT_MB")) limit = static_cast<size_t>(std::atoll(e)) << 20;
+    if (!limit && cudaMemGetInfo(&free_b, &total_b) == cudaSuccess) {
+      const size_t reserve = size_t(1) << 30;
+      limit = h->arena_cap + (free_b > reserve ? (free_b - reserve) / 10 * 9 : 0);
+    }
+    cudaGetLastError();
+    if (!limit) limit = size_t(64) << 30;
+  }
+  std::vector<EmuGroup> groups;
+  size_t arena_need = 0;
+  for (auto& kv : emu) {
+    std::vector<Problem> rest = kv.second;
+    std::stable_sort(rest.begin(), rest.end(), [](const Problem& a, const Problem& b) {
+      return static_cast<double>(a.m) * a.n * a.k > static_cast<double>(b.m) * b.n * b.k;
+    });
+    size_t at = 0;
+    while (at < rest.size()) {
+      // Largest prefix of the remaining problems whose workspace fits the
+      // limit (binary search; at least one problem).
+      auto make = [&](size_t end) {
+        EmuGroup t;
+        t.tabled = true;
+        t.form = std::get<0>(kv.first);
+        t.bn = std::get<1>(kv.first);
+        t.groups = std::get<2>(kv.first);
+        t.ps.assign(rest.begin() + at, rest.begin() + end);
+        return t;
+      };
+      EmuGroup g = make(rest.size());
+      mm_status st = layout_group(h, g, nullptr);
+      if (st != MM_OK) return st;
+      size_t end = rest.size();
+      if (g.bytes > limit && rest.size() - at > 1) {
+        size_t lo = at + 1, hi = rest.size() - 1;  // lo always fits or is the single-problem floor
+        while (lo < hi) {
+          const size_t mid = (lo + hi + 1) / 2;
+          EmuGroup t = make(mid);
+          st = layout_group(h, t, nullptr);
+          if (st != MM_OK) return st;
+          if (t.bytes <= limit) lo = mid; else hi = mid - 1;
+        }
+        end = lo;
+        g = make(end);
+        st = layout_group(h, g, nullptr);
+        if (st != MM_OK) return st;
+      }
+      at = end;
+      arena_need = std::max(arena_need, g.bytes);
+      groups.push_back(std::move(g));
+    }
+  }
+  if (arena_need) {
+    mm_status st = ensure_arena(h, arena_need);
+    if (st != MM_OK) return st;
+  }
+  for (size_t gi = 0; gi < groups.size(); ++gi) {
+    mm_status st = layout_group(h, groups[gi], static_cast<char*>(h->arena));
+    if (st != MM_OK) return st;
+  }
+
+  // Device-side tables: [native problems][per group: problems, maps, max offsets].
+  Arena tab;
+  const size_t off_nat = tab.take(sizeof(Problem) * std::max<size_t>(nat.size(), 1));
+  const size_t off_nat_small = tab.take(sizeof(Problem) * std::max<size_t>(nat_small.size(), 1));
+  std::vector<size_t> off_tab, off_maps, off_mo, off_units;
+  for (const EmuGroup& g : groups) {
+    off_tab.push_back(tab.take(sizeof(Problem) * g.ps.size()));
+    off_maps.push_back(tab.take(sizeof(CUtensorMap) * g.maps.size()));
+    off_mo.push_back(tab.take(sizeof(int) * g.max_off.size()));
+    off_units.push_back(tab.take(sizeof(int4) * std::max<size_t>(g.units.size(), 1)));
+  }
+  const size_t tab_bytes = tab.off;
+  std::vector<char> host_tab(tab_bytes, 0);
+  if (!nat.empty()) std::memcpy(host_tab.data() + off_nat, nat.data(), sizeof(Problem) * nat.size());
+  if (!nat_small.empty())
+    std::memcpy(host_tab.data() + off_nat_small, nat_small.data(), sizeof(Problem) * nat_small.size());
+  for (size_t gi = 0; gi < groups.size(); ++gi) {
+    const EmuGroup& g = groups[gi];
+    std::memcpy(host_tab.data() + off_tab[gi], g.ps.data(), sizeof(Problem) * g.ps.size());
+    std::memcpy(host_tab.data() + off_maps[gi], g.maps.data(), sizeof(CUtensorMap) * g.maps.size());
+    std::memcpy(host_tab.data() + off_mo[gi], g.max_off.data(), sizeof(int) * g.max_off.size());
+    if (!g.units.empty()) std::memcpy(host_tab.data() + off_units[gi], g.units.data(), sizeof(int4) * g.units.size());
+  }
+
+  auto launch_all = [&](char* dtab, cudaStream_t s) -> mm_status {
+    // Native problems do not depend on the emulation's kernels: unless
+    // profiling (which wants one kernel at a time), they run on a side stream.
+    const bool fork = !h->profile && (!nat.empty() || !nat_small.empty()) && !groups.empty();
+    if (fork) {
+      MM_CUDA(h, cudaEventRecord(h->fork_ev, s));
+      MM_CUDA(h, cudaStreamWaitEvent(h->side_stream, h->fork_ev, 0));
+      if (!nat_small.empty())
+        MM_CUDA(h, mmk::native_small_launch(reinterpret_cast<Problem*>(dtab + off_nat_small), nullptr,
+                                            static_cast<int>(nat_small.size()), nat_small_tiles, h->side_stream));
+      if (!nat.empty())
+        MM_CUDA(h, mmk::native_launch(reinterpret_cast<Problem*>(dtab + off_nat), nullptr,
+                                      static_cast<int>(nat.size()), nat_tiles, h->side_stream));
+      MM_CUDA(h, cudaEventRecord(h->join_ev, h->side_stream));
+    } else if (!nat.empty() || !nat_small.empty()) {
+      const long m = prof_start(h, s, KIND_NATIVE);
+      if (!nat_small.empty())
+        MM_CUDA(h, mmk::native_small_launch(reinterpret_cast<Problem*>(dtab + off_nat_small), nullptr,
+                                            static_cast<int>(nat_small.size()), nat_small_tiles, s));
+      if (!nat.empty())
+        MM_CUDA(h, mmk::native_launch(reinterpret_cast<Problem*>(dtab + off_nat), nullptr,
+                                      static_cast<int>(nat.size()), nat_tiles, s));
+      prof_end(h, s, m);
+    }
+    for (size_t gi = 0; gi < groups.size(); ++gi) {
+      mm_status st = run_group(h, groups[gi], reinterpret_cast<Problem*>(dtab + off_tab[gi]),
+                               reinterpret_cast<CUtensorMap*>(dtab + off_maps[gi]),
+                               reinterpret_cast<int*>(dtab + off_mo[gi]),
+                               reinterpret_cast<int4*>(dtab + off_units[gi]), s);
+      if (st != MM_OK) return st;
+    }
+    if (fork) MM_CUDA(h, cudaStreamWaitEvent(s, h->join_ev, 0));
+    return MM_OK;
+  };
+
+  if (!use_graph) {
+    if (tab_bytes > h->grp_table_cap) {
+      if (h->grp_table) cudaFree(h->grp_table);
+      if (h->grp_pinned) cudaFreeHost(h->grp_pinned);
+      h->grp_table = nullptr;
+      h->grp_pinned = nullptr;
+      h->grp_table_cap = 0;
+      if (cudaMalloc(&h->grp_table, tab_bytes) != cudaSuccess ||
+          cudaMallocHost(&h->grp_pinned, tab_bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(h, MM_ERR_NOMEM, "grouped table buffers");
+      }
+      h->grp_table_cap = tab_bytes;
+    }
+    MM_CUDA(h, cudaEventSynchronize(h->grp_event));  // previous upload done with the staging buffer
+    std::memcpy(h->grp_pinned, host_tab.data(), tab_bytes);
+    MM_CUDA(h, cudaMemcpyAsync(h->grp_table, h->grp_pinned, tab_bytes, cudaMemcpyHostToDevice, user));
+    MM_CUDA(h, cudaEventRecord(h->grp_event, user));
+    return launch_all(static_cast<char*>(h->grp_table), user);
+  }
+
+  it = h->graphs.find(key);  // the arena may have been regrown above (cache cleared)
+  if (it == h->graphs.end()) {
+    if (h->graphs.size() >= 32) {
+      for (auto& kv : h->graphs) {
+        if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+        if (kv.second.table_mem) cudaFree(kv.second.table_mem);
+      }
+      h->graphs.clear();
+    }
+    GraphEntry ge;
+    if (cudaMalloc(&ge.table_mem, std::max<size_t>(tab_bytes, 256)) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(h, MM_ERR_NOMEM, "grouped table");
+    }
+    if (cudaMemcpy(ge.table_mem, host_tab.data(), tab_bytes, cudaMemcpyHostToDevice) != cudaSuccess) {
+      cudaFree(ge.table_mem);
+      return fail(h, MM_ERR_CUDA, "grouped table upload");
+    }
+    cudaGraph_t graph = nullptr;
+    MM_CUDA(h, cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+    mm_status st = launch_all(static_cast<char*>(ge.table_mem), h->cap_stream);
+    cudaError_t ce = cudaStreamEndCapture(h->cap_stream, &graph);
+    if (st != MM_OK || ce != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      cudaFree(ge.table_mem);
+      cudaGetLastError();
+      return st != MM_OK ? st : cuda_fail(h, ce, "graph capture");
+    }
+    ce = cudaGraphInstantiate(&ge.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ce != cudaSuccess) {
+      cudaFree(ge.table_mem);
+      return cuda_fail(h, ce, "graph instantiate");
+    }
+    it = h->graphs.emplace(key, ge).first;
+  }
+  MM_CUDA(h, cudaGraphLaunch(it->second.exec, user));
+  return MM_OK;
+}
+
+// Validates one rectangular problem of the _ex entry points and fills *p.
+// m or n zero (or k zero with a valid C) is accepted; pointers need only be
+// 8-byte aligned (no kernel reads A, B or C with wider accesses).
+mm_status make_rect_problem(mm_handle h, int m, int n, int k, const double* A, int lda, const double* B, int ldb,
+                            double* C, int ldc, Problem* p) {
+  if (m < 0 || n < 0 || k < 0) return fail(h, MM_ERR_INVALID, "M, N, K must be >= 0");
+  *p = Problem{};
+  p->m = m;
+  p->n = n;
+  p->k = k;
+  if (m == 0 || n == 0) return MM_OK;
+  if (!C || (k > 0 && (!A || !B))) return fail(h, MM_ERR_INVALID, "null matrix pointer");
+  if (lda < std::max(k, 1) || ldb < n || ldc < n)
+    return fail(h, MM_ERR_INVALID, "leading dimensions must be at least the row lengths (lda >= K, ldb >= N, ldc >= N)");
+  auto al8 = [](const void* q) { return (reinterpret_cast<uintptr_t>(q) & 7u) == 0; };
+  if (!al8(C) || (k > 0 && (!al8(A) || !al8(B)))) return fail(h, MM_ERR_INVALID, "pointers must be 8-byte aligned");
+  // C's span must not meet A's or B's
+  auto span = [](const void* base, int rows, int cols, int ld) {
+    const char* b = static_cast<const char*>(base);
+    return std::make_pair(b, b + (static_cast<size_t>(rows - 1) * ld + cols) * sizeof(double));
+  };
+  const auto c = span(C, m, n, ldc);
+  if (k > 0) {
+    const auto a = span(A, m, k, lda), b = span(B, k, n, ldb);
+    if ((c.first < a.second && a.first < c.second) || (c.first < b.second && b.first < c.second))
+      return fail(h, MM_ERR_INVALID, "C must not overlap A or B");
+  }
+  p->A = A;
+  p->B = B;
+  p->C = C;
+  p->lda = lda;
+  p->ldb = ldb;
+  p->ldc = ldc;
+  return MM_OK;
+}
+
+// One problem, alone: the native or emulated path of its plan.
+mm_status single_impl(mm_handle h, const Problem& p, cudaStream_t s) {
+  if (p.m == 0 || p.n == 0) return MM_OK;
+  prof_reset(h);
+  Plan plan = plan_for(h, plan_size(p));
+  if (p.k == 0) plan.form = 0;  // C = 0: the native kernel writes it
+  if (plan.form == 0) return native_single(h, p, s);
+  return emu_single(h, p, plan.form, plan.slices, plan.bn, plan.groups, s);
 }
 
 }  // namespace
@@ -769,16 +1093,16 @@ mm_status mm_gemm(mm_handle h, int N, const double* A, const double* B, double* 
     return a < b + bytes && b < a + bytes;
   };
   if (overlap(C, A) || overlap(C, B)) return fail(h, MM_ERR_INVALID, "C must not overlap A or B");
-  prof_reset(h);
+  return single_impl(h, square_problem(A, B, C, N), static_cast<cudaStream_t>(stream));
+}
+
+mm_status mm_gemm_ex(mm_handle h, int M, int N, int K, const double* A, int lda, const double* B, int ldb, double* C,
+                     int ldc, void* stream) {
+  if (!h) return MM_ERR_INVALID;
   Problem p{};
-  p.A = A;
-  p.B = B;
-  p.C = C;
-  p.n = N;
-  const Plan plan = plan_for(h, N);
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
-  if (plan.form == 0) return native_single(h, p, s);
-  return emu_single(h, p, plan.form, plan.slices, plan.bn, plan.groups, s);
+  const mm_status st = make_rect_problem(h, M, N, K, A, lda, B, ldb, C, ldc, &p);
+  if (st != MM_OK) return st;
+  return single_impl(h, p, static_cast<cudaStream_t>(stream));
 }
 
 mm_status mm_gemm_host(mm_handle h, int N, const double* A_host, const double* B_host, double* C_host,
@@ -947,270 +1271,34 @@ mm_status mm_gemm_grouped(mm_handle h, int count, const int* Ns, const double* c
   if (count < 0) return fail(h, MM_ERR_INVALID, "count must be >= 0");
   if (count == 0) return MM_OK;
   if (!Ns || !As || !Bs || !Cs) return fail(h, MM_ERR_INVALID, "null array");
+  std::vector<Problem> probs;
+  probs.reserve(count);
   for (int i = 0; i < count; ++i) {
     if (Ns[i] < 0) return fail(h, MM_ERR_INVALID, "negative N in group");
     if (Ns[i] > 0 && (!As[i] || !Bs[i] || !Cs[i])) return fail(h, MM_ERR_INVALID, "null matrix in group");
     if (Ns[i] > 0 && (!aligned16(As[i]) || !aligned16(Bs[i]) || !aligned16(Cs[i])))
       return fail(h, MM_ERR_INVALID, "group pointers must be 16-byte aligned");
+    probs.push_back(square_problem(As[i], Bs[i], Cs[i], Ns[i]));
   }
-  cudaStream_t user = static_cast<cudaStream_t>(stream);
-  prof_reset(h);
-  const bool use_graph = (h->cfg.flags & (MM_FLAG_NO_GRAPH | MM_FLAG_PROFILE)) == 0;
+  return grouped_impl(h, probs, static_cast<cudaStream_t>(stream));
+}
 
-  // A call identical to an earlier one replays its graph without redoing the
-  // host-side planning.  (Graphs are dropped whenever the arena is regrown.)
-  std::vector<long long> key;
-  key.reserve(4 * static_cast<size_t>(count) + 3);
-  key.push_back(count);
-  key.push_back(h->cfg.mode);
-  key.push_back(h->cfg.slices);
+mm_status mm_gemm_grouped_ex(mm_handle h, int count, const int* Ms, const int* Ns, const int* Ks,
+                             const double* const* As, const int* ldas, const double* const* Bs, const int* ldbs,
+                             double* const* Cs, const int* ldcs, void* stream) {
+  if (!h) return MM_ERR_INVALID;
+  if (count < 0) return fail(h, MM_ERR_INVALID, "count must be >= 0");
+  if (count == 0) return MM_OK;
+  if (!Ms || !Ns || !Ks || !As || !ldas || !Bs || !ldbs || !Cs || !ldcs) return fail(h, MM_ERR_INVALID, "null array");
+  std::vector<Problem> probs;
+  probs.reserve(count);
   for (int i = 0; i < count; ++i) {
-    key.push_back(Ns[i]);
-    key.push_back(static_cast<long long>(reinterpret_cast<uintptr_t>(As[i])));
-    key.push_back(static_cast<long long>(reinterpret_cast<uintptr_t>(Bs[i])));
-    key.push_back(static_cast<long long>(reinterpret_cast<uintptr_t>(Cs[i])));
-  }
-  auto it = h->graphs.end();
-  if (use_graph) {
-    it = h->graphs.find(key);
-    if (it != h->graphs.end()) {
-      MM_CUDA(h, cudaGraphLaunch(it->second.exec, user));
-      return MM_OK;
-    }
-  }
-
-  // Partition: native problems, and emulated problems by (slices, bn).
-  std::vector<Problem> nat;
-  std::map<std::tuple<int, int, int>, std::vector<Problem>> emu;  // (form, bn, groups)
-  std::vector<std::pair<Problem, Plan>> emu_plans;
-  for (int i = 0; i < count; ++i) {
-    if (Ns[i] == 0) continue;
     Problem p{};
-    p.A = As[i];
-    p.B = Bs[i];
-    p.C = Cs[i];
-    p.n = Ns[i];
-    const Plan pl = plan_for(h, p.n);
-    if (pl.form == 0) {
-      nat.push_back(p);
-    } else {
-      mm_status st = check_emu_size(h, p.n, pl.slices, pl.form);
-      if (st != MM_OK) return st;
-      p.s = pl.slices;
-      emu_plans.push_back({p, pl});
-    }
-  }
-  // All emulated problems of the call share one slice-product launch: the
-  // tile width is the one planned for the largest problem (digit counts may
-  // differ per problem).
-  if (!emu_plans.empty()) {
-    size_t big = 0;
-    for (size_t i = 1; i < emu_plans.size(); ++i)
-      if (emu_plans[i].first.n > emu_plans[big].first.n) big = i;
-    const int bn = emu_plans[big].second.bn;
-    for (auto& ep : emu_plans) emu[{ep.second.form, bn, ep.second.groups}].push_back(ep.first);
-  }
-  // Native problems: 64 x 64 tiles, or 16 x 16 tiles below 512 (two launches).
-  std::vector<Problem> nat_small;
-  {
-    std::vector<Problem> big;
-    for (const Problem& p : nat) (mmk::native_is_small(p.n) ? nat_small : big).push_back(p);
-    nat.swap(big);
-  }
-  int nat_tiles = 0, nat_small_tiles = 0;
-  for (Problem& p : nat) {
-    mmk::native_fill_tiles(p);
-    p.tile_begin = nat_tiles;
-    nat_tiles += p.tiles_m * p.tiles_n;
-  }
-  for (Problem& p : nat_small) {
-    mmk::native_small_fill_tiles(p);
-    p.tile_begin = nat_small_tiles;
-    nat_small_tiles += p.tiles_m * p.tiles_n;
-  }
-
-  // Workspace.  Emulation groups run one after another on the same stream, so
-  // they all start at offset 0 of the arena; a group whose workspace exceeds
-  // the limit is cut into waves (largest problems first), each run in turn.
-  size_t limit = 0;
-  {
-    size_t free_b = 0, total_b = 0;
-    if (const char* e = std::getenv("MM_WORKSPACE_LIMIT_MB")) limit = static_cast<size_t>(std::atoll(e)) << 20;
-    if (!limit && cudaMemGetInfo(&free_b, &total_b) == cudaSuccess) {
-      const size_t reserve = size_t(1) << 30;
-      limit = h->arena_cap + (free_b > reserve ? (free_b - reserve) / 10 * 9 : 0);
-    }
-    cudaGetLastError();
-    if (!limit) limit = size_t(64) << 30;
-  }
-  std::vector<EmuGroup> groups;
-  size_t arena_need = 0;
-  for (auto& kv : emu) {
-    std::vector<Problem> rest = kv.second;
-    std::stable_sort(rest.begin(), rest.end(), [](const Problem& a, const Problem& b) { return a.n > b.n; });
-    size_t at = 0;
-    while (at < rest.size()) {
-      // Largest prefix of the remaining problems whose workspace fits the
-      // limit (binary search; at least one problem).
-      auto make = [&](size_t end) {
-        EmuGroup t;
-        t.tabled = true;
-        t.form = std::get<0>(kv.first);
-        t.bn = std::get<1>(kv.first);
-        t.groups = std::get<2>(kv.first);
-        t.ps.assign(rest.begin() + at, rest.begin() + end);
-        return t;
-      };
-      EmuGroup g = make(rest.size());
-      mm_status st = layout_group(h, g, nullptr);
-      if (st != MM_OK) return st;
-      size_t end = rest.size();
-      if (g.bytes > limit && rest.size() - at > 1) {
-        size_t lo = at + 1, hi = rest.size() - 1;  // lo always fits or is the single-problem floor
-        while (lo < hi) {
-          const size_t mid = (lo + hi + 1) / 2;
-          EmuGroup t = make(mid);
-          st = layout_group(h, t, nullptr);
-          if (st != MM_OK) return st;
-          if (t.bytes <= limit) lo = mid; else hi = mid - 1;
-        }
-        end = lo;
-        g = make(end);
-        st = layout_group(h, g, nullptr);
-        if (st != MM_OK) return st;
-      }
-      at = end;
-      arena_need = std::max(arena_need, g.bytes);
-      groups.push_back(std::move(g));
-    }
-  }
-  if (arena_need) {
-    mm_status st = ensure_arena(h, arena_need);
+    mm_status st = make_rect_problem(h, Ms[i], Ns[i], Ks[i], As[i], ldas[i], Bs[i], ldbs[i], Cs[i], ldcs[i], &p);
     if (st != MM_OK) return st;
+    probs.push_back(p);
   }
-  for (size_t gi = 0; gi < groups.size(); ++gi) {
-    mm_status st = layout_group(h, groups[gi], static_cast<char*>(h->arena));
-    if (st != MM_OK) return st;
-  }
-
-  // Device-side tables: [native problems][per group: problems, maps, max offsets].
-  Arena tab;
-  const size_t off_nat = tab.take(sizeof(Problem) * std::max<size_t>(nat.size(), 1));
-  const size_t off_nat_small = tab.take(sizeof(Problem) * std::max<size_t>(nat_small.size(), 1));
-  std::vector<size_t> off_tab, off_maps, off_mo, off_units;
-  for (const EmuGroup& g : groups) {
-    off_tab.push_back(tab.take(sizeof(Problem) * g.ps.size()));
-    off_maps.push_back(tab.take(sizeof(CUtensorMap) * g.maps.size()));
-    off_mo.push_back(tab.take(sizeof(int) * g.max_off.size()));
-    off_units.push_back(tab.take(sizeof(int4) * std::max<size_t>(g.units.size(), 1)));
-  }
-  const size_t tab_bytes = tab.off;
-  std::vector<char> host_tab(tab_bytes, 0);
-  if (!nat.empty()) std::memcpy(host_tab.data() + off_nat, nat.data(), sizeof(Problem) * nat.size());
-  if (!nat_small.empty())
-    std::memcpy(host_tab.data() + off_nat_small, nat_small.data(), sizeof(Problem) * nat_small.size());
-  for (size_t gi = 0; gi < groups.size(); ++gi) {
-    const EmuGroup& g = groups[gi];
-    std::memcpy(host_tab.data() + off_tab[gi], g.ps.data(), sizeof(Problem) * g.ps.size());
-    std::memcpy(host_tab.data() + off_maps[gi], g.maps.data(), sizeof(CUtensorMap) * g.maps.size());
-    std::memcpy(host_tab.data() + off_mo[gi], g.max_off.data(), sizeof(int) * g.max_off.size());
-    if (!g.units.empty()) std::memcpy(host_tab.data() + off_units[gi], g.units.data(), sizeof(int4) * g.units.size());
-  }
-
-  auto launch_all = [&](char* dtab, cudaStream_t s) -> mm_status {
-    // Native problems do not depend on the emulation's kernels: unless
-    // profiling (which wants one kernel at a time), they run on a side stream.
-    const bool fork = !h->profile && (!nat.empty() || !nat_small.empty()) && !groups.empty();
-    if (fork) {
-      MM_CUDA(h, cudaEventRecord(h->fork_ev, s));
-      MM_CUDA(h, cudaStreamWaitEvent(h->side_stream, h->fork_ev, 0));
-      if (!nat_small.empty())
-        MM_CUDA(h, mmk::native_small_launch(reinterpret_cast<Problem*>(dtab + off_nat_small), nullptr,
-                                            static_cast<int>(nat_small.size()), nat_small_tiles, h->side_stream));
-      if (!nat.empty())
-        MM_CUDA(h, mmk::native_launch(reinterpret_cast<Problem*>(dtab + off_nat), nullptr,
-                                      static_cast<int>(nat.size()), nat_tiles, h->side_stream));
-      MM_CUDA(h, cudaEventRecord(h->join_ev, h->side_stream));
-    } else if (!nat.empty() || !nat_small.empty()) {
-      const long m = prof_start(h, s, KIND_NATIVE);
-      if (!nat_small.empty())
-        MM_CUDA(h, mmk::native_small_launch(reinterpret_cast<Problem*>(dtab + off_nat_small), nullptr,
-                                            static_cast<int>(nat_small.size()), nat_small_tiles, s));
-      if (!nat.empty())
-        MM_CUDA(h, mmk::native_launch(reinterpret_cast<Problem*>(dtab + off_nat), nullptr,
-                                      static_cast<int>(nat.size()), nat_tiles, s));
-      prof_end(h, s, m);
-    }
-    for (size_t gi = 0; gi < groups.size(); ++gi) {
-      mm_status st = run_group(h, groups[gi], reinterpret_cast<Problem*>(dtab + off_tab[gi]),
-                               reinterpret_cast<CUtensorMap*>(dtab + off_maps[gi]),
-                               reinterpret_cast<int*>(dtab + off_mo[gi]),
-                               reinterpret_cast<int4*>(dtab + off_units[gi]), s);
-      if (st != MM_OK) return st;
-    }
-    if (fork) MM_CUDA(h, cudaStreamWaitEvent(s, h->join_ev, 0));
-    return MM_OK;
-  };
-
-  if (!use_graph) {
-    if (tab_bytes > h->grp_table_cap) {
-      if (h->grp_table) cudaFree(h->grp_table);
-      if (h->grp_pinned) cudaFreeHost(h->grp_pinned);
-      h->grp_table = nullptr;
-      h->grp_pinned = nullptr;
-      h->grp_table_cap = 0;
-      if (cudaMalloc(&h->grp_table, tab_bytes) != cudaSuccess ||
-          cudaMallocHost(&h->grp_pinned, tab_bytes) != cudaSuccess) {
-        cudaGetLastError();
-        return fail(h, MM_ERR_NOMEM, "grouped table buffers");
-      }
-      h->grp_table_cap = tab_bytes;
-    }
-    MM_CUDA(h, cudaEventSynchronize(h->grp_event));  // previous upload done with the staging buffer
-    std::memcpy(h->grp_pinned, host_tab.data(), tab_bytes);
-    MM_CUDA(h, cudaMemcpyAsync(h->grp_table, h->grp_pinned, tab_bytes, cudaMemcpyHostToDevice, user));
-    MM_CUDA(h, cudaEventRecord(h->grp_event, user));
-    return launch_all(static_cast<char*>(h->grp_table), user);
-  }
-
-  it = h->graphs.find(key);  // the arena may have been regrown above (cache cleared)
-  if (it == h->graphs.end()) {
-    if (h->graphs.size() >= 32) {
-      for (auto& kv : h->graphs) {
-        if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
-        if (kv.second.table_mem) cudaFree(kv.second.table_mem);
-      }
-      h->graphs.clear();
-    }
-    GraphEntry ge;
-    if (cudaMalloc(&ge.table_mem, std::max<size_t>(tab_bytes, 256)) != cudaSuccess) {
-      cudaGetLastError();
-      return fail(h, MM_ERR_NOMEM, "grouped table");
-    }
-    if (cudaMemcpy(ge.table_mem, host_tab.data(), tab_bytes, cudaMemcpyHostToDevice) != cudaSuccess) {
-      cudaFree(ge.table_mem);
-      return fail(h, MM_ERR_CUDA, "grouped table upload");
-    }
-    cudaGraph_t graph = nullptr;
-    MM_CUDA(h, cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
-    mm_status st = launch_all(static_cast<char*>(ge.table_mem), h->cap_stream);
-    cudaError_t ce = cudaStreamEndCapture(h->cap_stream, &graph);
-    if (st != MM_OK || ce != cudaSuccess) {
-      if (graph) cudaGraphDestroy(graph);
-      cudaFree(ge.table_mem);
-      cudaGetLastError();
-      return st != MM_OK ? st : cuda_fail(h, ce, "graph capture");
-    }
-    ce = cudaGraphInstantiate(&ge.exec, graph, 0);
-    cudaGraphDestroy(graph);
-    if (ce != cudaSuccess) {
-      cudaFree(ge.table_mem);
-      return cuda_fail(h, ce, "graph instantiate");
-    }
-    it = h->graphs.emplace(key, ge).first;
-  }
-  MM_CUDA(h, cudaGraphLaunch(it->second.exec, user));
-  return MM_OK;
+  return grouped_impl(h, probs, static_cast<cudaStream_t>(stream));
 }
 
 mm_status mm_split(mm_handle h, int N, const double* M, int by_columns, int slices, int* exps, uint16_t* digits,
@@ -1219,8 +1307,7 @@ mm_status mm_split(mm_handle h, int N, const double* M, int by_columns, int slic
   if (N <= 0 || !M || !exps || !digits || rows < N || ld < N || rows % 128 || ld % 64 || !aligned16(digits))
     return fail(h, MM_ERR_INVALID, "mm_split: bad arguments (rows % 128, ld % 64, 16-byte aligned digits)");
   if (slices < 1 || slices > 8) return fail(h, MM_ERR_UNSUPPORTED, "slices must be in 1..8");
-  Problem p{};
-  p.n = N;
+  Problem p = square_problem(nullptr, nullptr, nullptr, N);
   p.s = slices;
   p.k_pad = ld;
   if (by_columns) {
@@ -1256,8 +1343,7 @@ mm_status mm_level_sums(mm_handle h, int N, int slices, const uint16_t* a_digits
   if (static_cast<long long>(slices) * N * (1 << 14) >= (1LL << 31))
     return fail(h, MM_ERR_UNSUPPORTED, "level sums would not fit int32");
   const int bn = (b_rows % 256 == 0 && N > 128) ? 256 : 128;
-  Problem p{};
-  p.n = N;
+  Problem p = square_problem(nullptr, nullptr, nullptr, N);
   p.s = slices;
   p.a_slices = const_cast<uint16_t*>(a_digits);
   p.b_slices = const_cast<uint16_t*>(b_digits);

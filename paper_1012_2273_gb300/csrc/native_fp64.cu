@@ -5,8 +5,10 @@
 // here the split is into 64 x 64 tiles of C, one CTA each, over all problems
 // of a grouped call.  Each CTA streams 64 x 16 panels of A and 16 x 64 panels
 // of B through a double-buffered shared-memory ring (cp.async, 8-byte copies,
-// so any N works: rows of an odd-N matrix are not 16-byte aligned, which rules
-// out TMA tiles), and four warps run mma.sync m16n8k4 f64 on 32 x 32 sub-tiles.
+// so any shape and leading dimension works: rows of an odd-N matrix are not
+// 16-byte aligned, which rules out TMA tiles), and four warps run mma.sync
+// m16n8k4 f64 on 32 x 32 sub-tiles.  C (m x n) = A (m x k) . B (k x n), each
+// row-major with its own leading dimension; the square product is m = n = k.
 // Each output is a chain of FP64 fused multiply-adds; the order differs from
 // the paper's left-to-right sum, so results agree with it to within
 // gamma_N |A||B| rather than bit for bit (exactly, when all partial sums are
@@ -56,9 +58,10 @@ __global__ void __launch_bounds__(NT_THREADS) native_fp64_kernel(const __grid_co
   } else {
     P = &args.single;
   }
-  const int n = P->n;
+  const int n = P->n, m = P->m, kdim = P->k;
+  const size_t lda = P->lda, ldb = P->ldb, ldc = P->ldc;
   const int local = tile - P->tile_begin;
-  if (n <= 0 || local < 0 || local >= P->tiles_m * P->tiles_n) return;
+  if (n <= 0 || m <= 0 || local < 0 || local >= P->tiles_m * P->tiles_n) return;
   const int m0 = (local / P->tiles_n) * NT_BM;
   const int n0 = (local % P->tiles_n) * NT_BN;
   const double* __restrict__ A = P->A;
@@ -76,16 +79,16 @@ __global__ void __launch_bounds__(NT_THREADS) native_fp64_kernel(const __grid_co
       const int idx = tid + it * NT_THREADS;
       const int r = idx / NT_BK, c = idx % NT_BK;  // A: row r of the tile, column c
       const int gi = m0 + r, gk = k0 + c;
-      const bool ok = gi < n && gk < n;
-      cp_async_8(&As[buf][c][r], ok ? A + (size_t)gi * n + gk : A, ok);
+      const bool ok = gi < m && gk < kdim;
+      cp_async_8(&As[buf][c][r], ok ? A + (size_t)gi * lda + gk : A, ok);
     }
 #pragma unroll
     for (int it = 0; it < (NT_BK * NT_BN) / NT_THREADS; ++it) {
       const int idx = tid + it * NT_THREADS;
       const int r = idx / NT_BN, c = idx % NT_BN;  // B: row r (k), column c
       const int gk = k0 + r, gj = n0 + c;
-      const bool ok = gk < n && gj < n;
-      cp_async_8(&Bs[buf][r][c], ok ? B + (size_t)gk * n + gj : B, ok);
+      const bool ok = gk < kdim && gj < n;
+      cp_async_8(&Bs[buf][r][c], ok ? B + (size_t)gk * ldb + gj : B, ok);
     }
     cp_async_commit();
   };
@@ -98,8 +101,8 @@ __global__ void __launch_bounds__(NT_THREADS) native_fp64_kernel(const __grid_co
 #pragma unroll
       for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.0;
 
-  const int ktiles = (n + NT_BK - 1) / NT_BK;
-  load_stage(0, 0);
+  const int ktiles = (kdim + NT_BK - 1) / NT_BK;
+  if (ktiles > 0) load_stage(0, 0);
   for (int kt = 0; kt < ktiles; ++kt) {
     const int buf = kt & 1;
     if (kt + 1 < ktiles) {
@@ -136,9 +139,9 @@ __global__ void __launch_bounds__(NT_THREADS) native_fp64_kernel(const __grid_co
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         const int r = r0 + 8 * h;
-        if (r < n) {
-          if (c0 < n) C[(size_t)r * n + c0] = acc[mi][ni][2 * h];
-          if (c0 + 1 < n) C[(size_t)r * n + c0 + 1] = acc[mi][ni][2 * h + 1];
+        if (r < m) {
+          if (c0 < n) C[(size_t)r * ldc + c0] = acc[mi][ni][2 * h];
+          if (c0 + 1 < n) C[(size_t)r * ldc + c0 + 1] = acc[mi][ni][2 * h + 1];
         }
       }
     }
@@ -153,9 +156,10 @@ constexpr int NS_TILE = 16;
 __global__ void __launch_bounds__(32) native_fp64_small_kernel(const __grid_constant__ NativeArgs args) {
   const int tile = blockIdx.x;
   const Problem* P = args.table ? &args.table[find_problem(args.table, args.count, tile)] : &args.single;
-  const int n = P->n;
+  const int n = P->n, m = P->m, kdim = P->k;
+  const size_t lda = P->lda, ldb = P->ldb, ldc = P->ldc;
   const int local = tile - P->tile_begin;
-  if (n <= 0 || local < 0 || local >= P->tiles_m * P->tiles_n) return;
+  if (n <= 0 || m <= 0 || local < 0 || local >= P->tiles_m * P->tiles_n) return;
   const int m0 = (local / P->tiles_n) * NS_TILE;
   const int n0 = (local % P->tiles_n) * NS_TILE;
   const double* __restrict__ A = P->A;
@@ -163,18 +167,18 @@ __global__ void __launch_bounds__(32) native_fp64_small_kernel(const __grid_cons
   const int lane = threadIdx.x, g = lane >> 2, t = lane & 3;
   const int ra = m0 + g, rb = m0 + g + 8;  // rows of the A fragment
   double acc[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}};
-  for (int k0 = 0; k0 < n; k0 += 16) {
+  for (int k0 = 0; k0 < kdim; k0 += 16) {
     double a[4][2], b[4][2];
 #pragma unroll
     for (int kk = 0; kk < 4; ++kk) {
       const int k = k0 + 4 * kk + t;
-      const bool kin = k < n;
-      a[kk][0] = (kin && ra < n) ? A[static_cast<size_t>(ra) * n + k] : 0.0;
-      a[kk][1] = (kin && rb < n) ? A[static_cast<size_t>(rb) * n + k] : 0.0;
+      const bool kin = k < kdim;
+      a[kk][0] = (kin && ra < m) ? A[static_cast<size_t>(ra) * lda + k] : 0.0;
+      a[kk][1] = (kin && rb < m) ? A[static_cast<size_t>(rb) * lda + k] : 0.0;
 #pragma unroll
       for (int ni = 0; ni < 2; ++ni) {
         const int col = n0 + ni * 8 + g;
-        b[kk][ni] = (kin && col < n) ? B[static_cast<size_t>(k) * n + col] : 0.0;
+        b[kk][ni] = (kin && col < n) ? B[static_cast<size_t>(k) * ldb + col] : 0.0;
       }
     }
 #pragma unroll
@@ -189,9 +193,9 @@ __global__ void __launch_bounds__(32) native_fp64_small_kernel(const __grid_cons
 #pragma unroll
     for (int hh = 0; hh < 2; ++hh) {
       const int r = m0 + g + 8 * hh;
-      if (r < n) {
-        if (c0 < n) C[static_cast<size_t>(r) * n + c0] = acc[ni][2 * hh];
-        if (c0 + 1 < n) C[static_cast<size_t>(r) * n + c0 + 1] = acc[ni][2 * hh + 1];
+      if (r < m) {
+        if (c0 < n) C[static_cast<size_t>(r) * ldc + c0] = acc[ni][2 * hh];
+        if (c0 + 1 < n) C[static_cast<size_t>(r) * ldc + c0 + 1] = acc[ni][2 * hh + 1];
       }
     }
   }
@@ -202,12 +206,11 @@ __global__ void __launch_bounds__(32) native_fp64_small_kernel(const __grid_cons
 // Problems below this size use the 16 x 16 kernel.
 constexpr int NATIVE_SMALL_MAX_N = 511;
 
-bool native_is_small(int n) { return n <= NATIVE_SMALL_MAX_N; }
+bool native_is_small(const Problem& p) { return p.m <= NATIVE_SMALL_MAX_N && p.n <= NATIVE_SMALL_MAX_N; }
 
 void native_small_fill_tiles(Problem& p) {
-  const int tm = p.n > 0 ? (p.n + NS_TILE - 1) / NS_TILE : 0;
-  p.tiles_m = tm;
-  p.tiles_n = tm;
+  p.tiles_m = p.m > 0 && p.n > 0 ? (p.m + NS_TILE - 1) / NS_TILE : 0;
+  p.tiles_n = p.m > 0 && p.n > 0 ? (p.n + NS_TILE - 1) / NS_TILE : 0;
 }
 
 cudaError_t native_small_launch(const Problem* table, const Problem* single, int count, int total_tiles,
@@ -221,16 +224,9 @@ cudaError_t native_small_launch(const Problem* table, const Problem* single, int
   return cudaGetLastError();
 }
 
-int native_tiles(int n) {
-  if (n <= 0) return 0;
-  const int tm = (n + NT_BM - 1) / NT_BM;
-  return tm * tm;
-}
-
 void native_fill_tiles(Problem& p) {
-  const int tm = p.n > 0 ? (p.n + NT_BM - 1) / NT_BM : 0;
-  p.tiles_m = tm;
-  p.tiles_n = tm;
+  p.tiles_m = p.m > 0 && p.n > 0 ? (p.m + NT_BM - 1) / NT_BM : 0;
+  p.tiles_n = p.m > 0 && p.n > 0 ? (p.n + NT_BN - 1) / NT_BN : 0;
 }
 
 cudaError_t native_launch(const Problem* table, const Problem* single, int count, int total_tiles,

@@ -28,7 +28,7 @@ __global__ void __launch_bounds__(256) slots_recombine_kernel(const __grid_const
   int tm, tn;
   emu_tile_coords(tile_local, P->tiles_m, P->tiles_n, &tm, &tn);
   const int n = P->n, row = tm * EM_BM + r, col = tn * BN + 4 * c4;
-  if (row >= n || col >= n) return;
+  if (row >= P->m || col >= n) return;
   const int s = P->s;
   const int32_t* at = args.tilebuf + P->slot_base + static_cast<long long>(tile_local) * P->nslots * SLOT +
                       slot_index(r, 4 * c4);
@@ -60,7 +60,7 @@ __global__ void __launch_bounds__(256) slots_recombine_kernel(const __grid_const
   for (int k = 0; k < 4; ++k) i128_shift_add64(th[k], tl[k], 0, lv[k]);
   const int tail = 8 * (s + 1 - curL);
   const int base_scale = P->a_exp[row] - 8 * s - 6;
-  double* crow = P->C + static_cast<size_t>(row) * n;
+  double* crow = P->C + static_cast<size_t>(row) * P->ldc;
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
     if (col + j < n) {
@@ -97,7 +97,7 @@ __device__ __forceinline__ void mod_recombine_tile(const EmuArgs& args, const Pr
   int tm, tn;
   emu_tile_coords(tile_local, P->tiles_m, P->tiles_n, &tm, &tn);
   const int n = P->n, row = tm * EM_BM + r, col0 = tn * BN + 8 * c8 + 4 * q;
-  if (row >= n || col0 >= n) return;
+  if (row >= P->m || col0 >= n) return;
   const uint16_t* at = reinterpret_cast<const uint16_t*>(args.tilebuf + P->slot_base) +
                        static_cast<size_t>(tile_local) * NG * SLOT + static_cast<size_t>(c8) * (EM_BM * 8) + r * 8 +
                        q * 4;
@@ -117,7 +117,7 @@ __device__ __forceinline__ void mod_recombine_tile(const EmuArgs& args, const Pr
   const uint64_t m_lo = (static_cast<uint64_t>(c_mod.mk[K][1]) << 32) | c_mod.mk[K][0];
   const uint64_t m_hi = (static_cast<uint64_t>(c_mod.mk[K][3]) << 32) | c_mod.mk[K][2];
   const int base_scale = P->a_exp[row] - 2 * P->beta;
-  double* crow = P->C + static_cast<size_t>(row) * n;
+  double* crow = P->C + static_cast<size_t>(row) * P->ldc;
 #pragma unroll
   for (int c = 0; c < 4; ++c) {
     if (col0 + c < n) {

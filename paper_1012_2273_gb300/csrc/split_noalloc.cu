@@ -71,7 +71,8 @@ extern "C" mm_status mm_split_noalloc(int N, const double* M, int by_columns, in
     return MM_ERR_CUDA;
   }
   mmk::Problem p{};
-  p.n = N;
+  p.n = p.m = p.k = N;
+  p.lda = p.ldb = p.ldc = N;
   p.s = slices;
   p.k_pad = ld;
   if (by_columns) {
