@@ -106,31 +106,36 @@ mm_status mm_gemm(mm_handle h, int N, const double* A, const double* B, double* 
 mm_status mm_gemm_grouped(mm_handle h, int count, const int* Ns, const double* const* As,
                           const double* const* Bs, double* const* Cs, void* stream);
 
-/* Rectangular product C (M x N) = A (M x K) . B (K x N): the sum of Alg. 1
- * over the three dimensions the master/worker program of Alg. 2 names
+/* Rectangular product C (M x N) = op(A) (M x K) . op(B) (K x N): the sum of
+ * Alg. 1 over the three dimensions the master/worker program of Alg. 2 names
  * separately (NRA = M, NCA = K, NCB = N; the paper's experiments are square).
- *   - A, B, C: device pointers, row-major; element (i,j) of A at A[i*lda + j],
- *     of B at B[i*ldb + j], of C at C[i*ldc + j].  lda >= K, ldb >= N,
- *     ldc >= N: sub-matrices of larger arrays are passed with their parents'
- *     row strides.  Pointers must be 8-byte aligned (not 16).
- *   - M = 0 or N = 0: no-op.  K = 0: C = 0.  Negative sizes, leading
- *     dimensions below the row length, null or misaligned pointers, and a C
- *     whose span overlaps A's or B's: MM_ERR_INVALID, nothing launched.
+ *   - transa = 0: A is stored M x K, op(A)(i,j) = A[i*lda + j], lda >= K;
+ *     transa = 1: A is stored K x M (op(A) = A^T), op(A)(i,j) = A[j*lda + i],
+ *     lda >= M.  Likewise transb = 0: B stored K x N, ldb >= N; transb = 1:
+ *     B stored N x K, ldb >= K.  C is always M x N, C[i*ldc + j], ldc >= N.
+ *     Sub-matrices of larger arrays are passed with their parents' row
+ *     strides.  All device pointers, 8-byte aligned (not 16).
+ *   - M = 0 or N = 0: no-op.  K = 0: C = 0.  Negative sizes, flags other than
+ *     0 and 1, leading dimensions below the stored row length, null or
+ *     misaligned pointers, and a C whose span overlaps A's or B's:
+ *     MM_ERR_INVALID, nothing launched.
  *   - The plan (form, slice or moduli count, tile width) is the one for size
  *     max(M, N, K); the emulated forms' exponents run over the K entries of
- *     each row of A and column of B, and the modular form's fixed-point width
- *     follows the rule of mm_modular_params with N = K.
+ *     each row of op(A) and column of op(B), and the modular form's
+ *     fixed-point width follows the rule of mm_modular_params with N = K.
  *   - Asynchronous on `stream`; device-side errors via mm_status_get. */
-mm_status mm_gemm_ex(mm_handle h, int M, int N, int K, const double* A, int lda, const double* B, int ldb,
-                     double* C, int ldc, void* stream);
+mm_status mm_gemm_ex(mm_handle h, int transa, int transb, int M, int N, int K, const double* A, int lda,
+                     const double* B, int ldb, double* C, int ldc, void* stream);
 
-/* `count` rectangular products in one grouped launch per kernel, as
- * mm_gemm_grouped: Ms, Ns, Ks, As, ldas, Bs, ldbs, Cs, ldcs are HOST arrays of
- * length count with each problem's arguments as in mm_gemm_ex.  The graph
- * signature covers every size, leading dimension and pointer. */
-mm_status mm_gemm_grouped_ex(mm_handle h, int count, const int* Ms, const int* Ns, const int* Ks,
-                             const double* const* As, const int* ldas, const double* const* Bs,
-                             const int* ldbs, double* const* Cs, const int* ldcs, void* stream);
+/* `count` such products in one grouped launch per kernel, as
+ * mm_gemm_grouped: every argument array is a HOST array of length count with
+ * each problem's arguments as in mm_gemm_ex; transas / transbs may be NULL
+ * (no transposes).  The graph signature covers every size, flag, leading
+ * dimension and pointer. */
+mm_status mm_gemm_grouped_ex(mm_handle h, int count, const int* transas, const int* transbs, const int* Ms,
+                             const int* Ns, const int* Ks, const double* const* As, const int* ldas,
+                             const double* const* Bs, const int* ldbs, double* const* Cs, const int* ldcs,
+                             void* stream);
 
 /* End-to-end form of mm_gemm on HOST buffers: copies A and B to the device,
  * computes, copies C back, and returns when C is on the host (the span the

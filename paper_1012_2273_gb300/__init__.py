@@ -81,10 +81,10 @@ def lib(build_if_needed: bool = True) -> ctypes.CDLL:
             L.mm_gemm.argtypes = [vp, ci, vp, vp, vp, vp]
             L.mm_gemm_grouped.argtypes = [vp, ci, ctypes.POINTER(ci), ctypes.POINTER(vp), ctypes.POINTER(vp),
                                           ctypes.POINTER(vp), vp]
-            L.mm_gemm_ex.argtypes = [vp, ci, ci, ci, vp, ci, vp, ci, vp, ci, vp]
+            L.mm_gemm_ex.argtypes = [vp, ci, ci, ci, ci, ci, vp, ci, vp, ci, vp, ci, vp]
             pi_ = ctypes.POINTER(ci)
-            L.mm_gemm_grouped_ex.argtypes = [vp, ci, pi_, pi_, pi_, ctypes.POINTER(vp), pi_, ctypes.POINTER(vp), pi_,
-                                             ctypes.POINTER(vp), pi_, vp]
+            L.mm_gemm_grouped_ex.argtypes = [vp, ci, pi_, pi_, pi_, pi_, pi_, ctypes.POINTER(vp), pi_,
+                                             ctypes.POINTER(vp), pi_, ctypes.POINTER(vp), pi_, vp]
             L.mm_gemm_host.argtypes = [vp, ci, vp, vp, vp, vp]
             L.mm_gemm_grouped_host.argtypes = [vp, ci, ctypes.POINTER(ci), ctypes.POINTER(vp), ctypes.POINTER(vp),
                                                ctypes.POINTER(vp), vp]
@@ -127,8 +127,10 @@ def _check_tensor(t, name: str, n: int | None = None):
         raise ValueError(f"{name} must be square" + (f" of size {n}" if n is not None else ""))
 
 
-def _matrix(t, name: str):
-    """(rows, cols, leading dimension) of a row-major float64 CUDA matrix view."""
+def _matrix(t, name: str, allow_transposed: bool = False):
+    """(rows, cols, leading dimension, transposed) of a float64 CUDA matrix view:
+    row-major (unit column stride), or -- where allowed -- the transpose of a
+    row-major matrix (unit row stride, e.g. ``X.T``)."""
     import torch
     if not isinstance(t, torch.Tensor) or not t.is_cuda:
         raise TypeError(f"{name} must be a CUDA tensor")
@@ -137,12 +139,16 @@ def _matrix(t, name: str):
     if t.dim() != 2:
         raise ValueError(f"{name} must be 2-D")
     rows, cols = int(t.shape[0]), int(t.shape[1])
-    if cols > 1 and t.stride(1) != 1:
-        raise ValueError(f"{name} must be row-major (unit column stride)")
-    ld = int(t.stride(0)) if rows > 1 and cols > 0 else cols
-    if ld < cols:
-        raise ValueError(f"{name}: row stride below the row length")
-    return rows, cols, max(ld, 1)
+    if cols <= 1 or t.stride(1) == 1:
+        ld = int(t.stride(0)) if rows > 1 and cols > 0 else cols
+        if ld >= cols:
+            return rows, cols, max(ld, 1), 0
+    if allow_transposed and (rows <= 1 or t.stride(0) == 1):
+        ld = int(t.stride(1)) if cols > 1 and rows > 0 else rows
+        if ld >= rows:
+            return rows, cols, max(ld, 1), 1
+    raise ValueError(f"{name} must be row-major with a row stride >= its row length"
+                     + (" (or the transpose of such a matrix)" if allow_transposed else ""))
 
 
 def _square_contiguous(*ts) -> bool:
@@ -223,20 +229,20 @@ class Handle:
         (K x N) are row-major float64 CUDA tensors, possibly views with a row
         stride (mm_gemm_ex); square contiguous operands take mm_gemm."""
         import torch
-        m, k, lda = _matrix(A, "A")
-        k2, n, ldb = _matrix(B, "B")
+        m, k, lda, ta = _matrix(A, "A", True)
+        k2, n, ldb, tb = _matrix(B, "B", True)
         if k2 != k:
             raise ValueError(f"inner dimensions differ: A is {m} x {k}, B is {k2} x {n}")
         if C is None:
             C = torch.empty((m, n), dtype=torch.float64, device=A.device)
-        mc, nc, ldc = _matrix(C, "C")
+        mc, nc, ldc, _ = _matrix(C, "C")
         if (mc, nc) != (m, n):
             raise ValueError(f"C must be {m} x {n}")
         if _square_contiguous(A, B, C):
             self._raise(self._lib.mm_gemm(self._h, n, A.data_ptr(), B.data_ptr(), C.data_ptr(), _stream_ptr(stream)))
         else:
-            self._raise(self._lib.mm_gemm_ex(self._h, m, n, k, A.data_ptr(), lda, B.data_ptr(), ldb, C.data_ptr(), ldc,
-                                             _stream_ptr(stream)))
+            self._raise(self._lib.mm_gemm_ex(self._h, ta, tb, m, n, k, A.data_ptr(), lda, B.data_ptr(), ldb,
+                                             C.data_ptr(), ldc, _stream_ptr(stream)))
         return C
 
     def gemm_grouped(self, As: Sequence, Bs: Sequence, Cs: Sequence | None = None, stream=None):
@@ -248,12 +254,12 @@ class Handle:
             Cs = [torch.empty((a.shape[0], b.shape[1]), dtype=torch.float64, device=a.device) for a, b in zip(As, Bs)]
         dims = []
         for i, (a, b, c) in enumerate(zip(As, Bs, Cs)):
-            m, k, lda = _matrix(a, f"As[{i}]")
-            k2, n, ldb = _matrix(b, f"Bs[{i}]")
-            mc, nc, ldc = _matrix(c, f"Cs[{i}]")
+            m, k, lda, ta = _matrix(a, f"As[{i}]", True)
+            k2, n, ldb, tb = _matrix(b, f"Bs[{i}]", True)
+            mc, nc, ldc, _ = _matrix(c, f"Cs[{i}]")
             if k2 != k or (mc, nc) != (m, n):
                 raise ValueError(f"problem {i}: shapes {tuple(a.shape)} x {tuple(b.shape)} -> {tuple(c.shape)}")
-            dims.append((m, n, k, lda, ldb, ldc))
+            dims.append((m, n, k, lda, ldb, ldc, ta, tb))
         pa = (ctypes.c_void_p * count)(*[a.data_ptr() for a in As])
         pb = (ctypes.c_void_p * count)(*[b.data_ptr() for b in Bs])
         pc = (ctypes.c_void_p * count)(*[c.data_ptr() for c in Cs])
@@ -261,9 +267,9 @@ class Handle:
             ns = (ctypes.c_int * count)(*[d[1] for d in dims])
             self._raise(self._lib.mm_gemm_grouped(self._h, count, ns, pa, pb, pc, _stream_ptr(stream)))
         else:
-            col = [(ctypes.c_int * count)(*[d[j] for d in dims]) for j in range(6)]
-            self._raise(self._lib.mm_gemm_grouped_ex(self._h, count, col[0], col[1], col[2], pa, col[3], pb, col[4], pc,
-                                                     col[5], _stream_ptr(stream)))
+            col = [(ctypes.c_int * count)(*[d[j] for d in dims]) for j in range(8)]
+            self._raise(self._lib.mm_gemm_grouped_ex(self._h, count, col[6], col[7], col[0], col[1], col[2], pa, col[3],
+                                                     pb, col[4], pc, col[5], _stream_ptr(stream)))
         return Cs
 
     def gemm_host(self, A, B, C=None, stream=None):

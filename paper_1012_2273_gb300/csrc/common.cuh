@@ -19,13 +19,14 @@ namespace mmk {
 // Problem table (one entry per independent product of a grouped call)
 // ---------------------------------------------------------------------------
 struct Problem {
-  const double* A;  // m x k row-major, leading dimension lda (device)
-  const double* B;  // k x n row-major, leading dimension ldb (device)
+  const double* A;  // op(A) is m x k: A[i*lda + j] (ta = 0) or A[j*lda + i] (ta = 1) (device)
+  const double* B;  // op(B) is k x n: B[j*ldb + l] (tb = 0) or B[l*ldb + j] (tb = 1) (device)
   double* C;        // m x n row-major, leading dimension ldc (device)
-  int n;            // columns of B and C (the square problem's N)
-  int m;            // rows of A and C
-  int k;            // columns of A, rows of B
+  int n;            // columns of op(B) and C (the square problem's N)
+  int m;            // rows of op(A) and C
+  int k;            // columns of op(A), rows of op(B)
   int lda, ldb, ldc;
+  int ta, tb;       // 1: the stored matrix is the transpose of op(A) / op(B)
   int tile_begin;   // first linear tile of this problem in the grouped grid
   int tiles_m;      // tiles along rows of C
   int tiles_n;      // tiles along columns of C

@@ -120,15 +120,16 @@ __device__ __forceinline__ void digits_of(int64_t D, float (&out)[S]) {
   out[0] = static_cast<float>(d1);
 }
 
-// Row maxima of |A| and column maxima of |B| (as bit patterns; for finite
-// values the unsigned order of |v|'s pattern is the order of |v|).
-//   A: one warp per row, AM_ROWS rows per block; the lanes stride along the
-//      row (coalesced), 8 loads in flight each, and lane 0 stores the row's
-//      maximum (no atomics; every row of the problem is written).
-//   B: one block per AM_BCOLS columns x AM_BROWS rows; 4 row phases of 64
-//      columns (a warp reads 256 contiguous bytes of a row), reduced through
-//      shared memory, one atomicMax per column per block (the column maxima
-//      start at zero).
+// Row maxima of |op(A)| and column maxima of |op(B)| (as bit patterns; for
+// finite values the unsigned order of |v|'s pattern is the order of |v|).
+// Maxima that run along the stored rows (A, or a transposed B): one warp per
+// row, AM_ROWS rows per block; the lanes stride along the row (coalesced), 8
+// loads in flight each, and lane 0 stores the row's maximum (no atomics;
+// every row is written).  Maxima along the stored columns (B, or a
+// transposed A): one block per AM_BCOLS columns x AM_BROWS rows; 4 row phases
+// of 64 columns (a warp reads 256 contiguous bytes of a row), reduced
+// through shared memory, one atomicMax per column per block (the maxima
+// start at zero).
 constexpr int AM_ROWS = SP_THREADS / 32;
 constexpr int AM_BCOLS = 64;
 constexpr int AM_BROWS = 128;
@@ -147,19 +148,39 @@ __device__ __forceinline__ int absmax_find(const SplitArgs& a, int block, const 
   return lo;
 }
 
+// Blocks of the maxima kernel for one operand of p: a warp per stored row
+// (maxima along stored rows) or 64-column x AM_BROWS-row bands.
+__host__ __device__ inline int absmax_operand_blocks(int outs, int kdim, bool by_rows) {
+  if (outs <= 0 || kdim <= 0) return 0;
+  return by_rows ? (outs + AM_ROWS - 1) / AM_ROWS : ((outs + AM_BCOLS - 1) / AM_BCOLS) * ((kdim + AM_BROWS - 1) / AM_BROWS);
+}
+__host__ __device__ inline int absmax_a_blocks(const Problem& p) {
+  return p.m_pad > 0 && p.n > 0 ? absmax_operand_blocks(p.m, p.k, !p.ta) : 0;
+}
+
 __global__ void __launch_bounds__(SP_THREADS) absmax_kernel(const __grid_constant__ SplitArgs args) {
   __shared__ unsigned long long part[SP_THREADS / AM_BCOLS][AM_BCOLS];
   const Problem* P;
   const int pi = absmax_find(args, blockIdx.x, &P);
-  const int n = P->n, mrows = P->m, kdim = P->k;
-  const int a_blocks = P->m_pad > 0 ? (mrows + AM_ROWS - 1) / AM_ROWS : 0;
+  const int kdim = P->k;
   int local = blockIdx.x - (args.table ? P->absmax_begin : 0);
+  const int a_blocks = absmax_a_blocks(*P);
+  const bool is_a = local < a_blocks;
+  if (!is_a) local -= a_blocks;
+  // The maxima run over the k entries of each row of op(A) / column of op(B):
+  // along the stored rows for A and a transposed B, along the stored columns
+  // for B and a transposed A.
+  const bool by_rows = is_a ? !P->ta : P->tb;
+  const uint64_t* src = reinterpret_cast<const uint64_t*>(is_a ? P->A : P->B);
+  const size_t ld = is_a ? P->lda : P->ldb;
+  const int outs = is_a ? P->m : P->n;  // number of maxima
   const int off = args.max_offset ? args.max_offset[pi] : 0;
+  uint64_t* dst = (is_a ? args.a_maxbits : args.b_maxbits) + off;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  if (local < a_blocks) {
+  if (by_rows) {
     const int i = local * AM_ROWS + warp;
-    if (i >= mrows) return;
-    const uint64_t* row = reinterpret_cast<const uint64_t*>(P->A) + static_cast<size_t>(i) * P->lda;
+    if (i >= outs) return;
+    const uint64_t* row = src + static_cast<size_t>(i) * ld;
     unsigned long long m = 0;
     for (int j0 = 0; j0 < kdim; j0 += 32 * 8) {
       unsigned long long v[8];
@@ -176,25 +197,22 @@ __global__ void __launch_bounds__(SP_THREADS) absmax_kernel(const __grid_constan
       const unsigned long long v = __shfl_xor_sync(0xffffffffu, m, o);
       m = v > m ? v : m;
     }
-    if (lane == 0) args.a_maxbits[off + i] = m;
+    if (lane == 0) dst[i] = m;
     return;
   }
-  local -= a_blocks;
-  const int nbc = (n + AM_BCOLS - 1) / AM_BCOLS;
+  const int nbc = (outs + AM_BCOLS - 1) / AM_BCOLS;
   const int k0 = (local % nbc) * AM_BCOLS, j0 = (local / nbc) * AM_BROWS;
   const int c = threadIdx.x % AM_BCOLS, ph = threadIdx.x / AM_BCOLS;
   constexpr int PHASES = SP_THREADS / AM_BCOLS;
-  const int k = k0 + c;  // column of B
-  const uint64_t* src = reinterpret_cast<const uint64_t*>(P->B);
-  const size_t ldb = P->ldb;
+  const int k = k0 + c;  // stored column
   unsigned long long m = 0;
-  if (k < n) {
+  if (k < outs) {
     for (int jj = ph; jj < AM_BROWS; jj += PHASES * 8) {
       unsigned long long v[8];
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
-        const int j = j0 + jj + PHASES * q;  // row of B
-        v[q] = (jj + PHASES * q < AM_BROWS && j < kdim) ? src[static_cast<size_t>(j) * ldb + k] & 0x7FFFFFFFFFFFFFFFull
+        const int j = j0 + jj + PHASES * q;  // stored row
+        v[q] = (jj + PHASES * q < AM_BROWS && j < kdim) ? src[static_cast<size_t>(j) * ld + k] & 0x7FFFFFFFFFFFFFFFull
                                                          : 0ull;
       }
 #pragma unroll
@@ -203,11 +221,11 @@ __global__ void __launch_bounds__(SP_THREADS) absmax_kernel(const __grid_constan
   }
   part[ph][c] = m;
   __syncthreads();
-  if (threadIdx.x < AM_BCOLS && k0 + threadIdx.x < n) {
+  if (threadIdx.x < AM_BCOLS && k0 + threadIdx.x < outs) {
     unsigned long long mm = 0;
 #pragma unroll
     for (int w = 0; w < PHASES; ++w) mm = part[w][threadIdx.x] > mm ? part[w][threadIdx.x] : mm;
-    if (mm) atomicMax(reinterpret_cast<unsigned long long*>(&args.b_maxbits[off + k0 + threadIdx.x]), mm);
+    if (mm) atomicMax(reinterpret_cast<unsigned long long*>(&dst[k0 + threadIdx.x]), mm);
   }
 }
 
@@ -368,9 +386,12 @@ __global__ void __launch_bounds__(SP_THREADS, 3) split_kernel(const __grid_const
   const uint64_t* maxbits = is_a ? args.a_maxbits + off : args.b_maxbits + off;
   int* exps = is_a ? P->a_exp : P->b_exp;
   if (threadIdx.x == 0) any_nonfinite = 0;
-  const int out_rows = is_a ? P->m : n;  // A: rows of A; B^T: columns of B
+  const int out_rows = is_a ? P->m : n;  // A: rows of op(A); B^T: columns of op(B)
   const int kdim = P->k;
   const size_t ld = is_a ? P->lda : P->ldb;
+  // the stored matrix's rows are the output rows (A, transposed B) or the
+  // k index (B, transposed A)
+  const bool rows_out = is_a ? !P->ta : P->tb;
   if (threadIdx.x < SP_TILE) {
     const int er = r0 + threadIdx.x;
     const int e = er < out_rows ? exponent_from_maxbits(maxbits[er]) : 0;
@@ -380,35 +401,29 @@ __global__ void __launch_bounds__(SP_THREADS, 3) split_kernel(const __grid_const
   __syncthreads();
   bool nonfinite = false;
   {
-    // Phase 1: source element (x, y) of the tile, x fastest (coalesced).
-    //   A:   source row i = r0 + y, column j = c0 + x -> Ds[y][x]  (output row y)
-    //   B^T: source row j = c0 + y, column k = r0 + x -> Ds[x][y]  (output row x)
-    // (A is m x kdim with leading dimension lda, B kdim x n with ldb)
+    // Phase 1: stored element (x, y) of the tile, x fastest (coalesced).
+    //   stored rows = output rows (A, B^T given):  row r0 + y, column c0 + x -> Ds[y][x]
+    //   stored rows = k index (B, A^T given):      row c0 + y, column r0 + x -> Ds[x][y]
+    // (leading dimension lda or ldb)
     // Each thread's 16 elements, all 16 loads in flight at once.
     constexpr int PER = SP_TILE * SP_TILE / SP_THREADS;
-    constexpr int BATCH = 16;
-    const int x = threadIdx.x % SP_TILE;
+    const int x = threadIdx.x % SP_TILE, y0 = threadIdx.x / SP_TILE;
+    const int bi = rows_out ? r0 : c0, bj = rows_out ? c0 : r0;  // stored origin of the tile
+    const int lim_i = (rows_out ? out_rows : kdim) - bi, lim_j = (rows_out ? kdim : out_rows) - bj;
+    const uint64_t* p = src + static_cast<size_t>(bi) * ld + bj + x;
+    const bool xin = x < lim_j;
+    uint64_t bits[PER];
 #pragma unroll
-    for (int q0 = 0; q0 < PER; q0 += BATCH) {
-      uint64_t bits[BATCH];
+    for (int b = 0; b < PER; ++b) {
+      const int y = y0 + b * (SP_THREADS / SP_TILE);
+      bits[b] = (xin && y < lim_i) ? p[static_cast<size_t>(y) * ld] : 0ull;
+    }
 #pragma unroll
-      for (int b = 0; b < BATCH; ++b) {
-        const int y = threadIdx.x / SP_TILE + (q0 + b) * (SP_THREADS / SP_TILE);
-        const int i = is_a ? r0 + y : c0 + y;  // source row
-        const int j = is_a ? c0 + x : r0 + x;  // source column
-        const bool in = is_a ? (i < out_rows && j < kdim) : (i < kdim && j < out_rows);
-        bits[b] = in ? src[static_cast<size_t>(i) * ld + j] : 0ull;
-      }
-#pragma unroll
-      for (int b = 0; b < BATCH; ++b) {
-        const int y = threadIdx.x / SP_TILE + (q0 + b) * (SP_THREADS / SP_TILE);
-        const int i = is_a ? r0 + y : c0 + y;
-        const int j = is_a ? c0 + x : r0 + x;
-        const bool in = is_a ? (i < out_rows && j < kdim) : (i < kdim && j < out_rows);
-        long long D = 0;
-        if (in) D = fixed_point(bits[b], ex_s[is_a ? y : x], width, &nonfinite);
-        if (is_a) Ds[y][x] = D; else Ds[x][y] = D;
-      }
+    for (int b = 0; b < PER; ++b) {
+      const int y = y0 + b * (SP_THREADS / SP_TILE);
+      long long D = 0;
+      if (xin && y < lim_i) D = fixed_point(bits[b], ex_s[rows_out ? y : x], width, &nonfinite);
+      if (rows_out) Ds[y][x] = D; else Ds[x][y] = D;
     }
     __syncthreads();
   }
@@ -448,10 +463,8 @@ int split_tiles(const Problem& p) {
 }
 
 int absmax_blocks(const Problem& p) {
-  if (p.n <= 0 || p.m <= 0 || p.k <= 0) return 0;
-  const int a = p.m_pad > 0 ? (p.m + AM_ROWS - 1) / AM_ROWS : 0;
-  const int b = p.n_pad > 0 ? ((p.n + AM_BCOLS - 1) / AM_BCOLS) * ((p.k + AM_BROWS - 1) / AM_BROWS) : 0;
-  return a + b;
+  const int b = p.n_pad > 0 && p.m > 0 ? absmax_operand_blocks(p.n, p.k, p.tb != 0) : 0;
+  return absmax_a_blocks(p) + b;
 }
 
 cudaError_t split_launch(const Problem* table, const Problem* single, int count, int total_tiles, int total_absmax,

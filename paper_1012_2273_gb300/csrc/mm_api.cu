@@ -632,12 +632,12 @@ mm_status grouped_impl(mm_handle h, const std::vector<Problem>& probs, cudaStrea
   // A call identical to an earlier one replays its graph without redoing the
   // host-side planning.  (Graphs are dropped whenever the arena is regrown.)
   std::vector<long long> key;
-  key.reserve(9 * probs.size() + 3);
+  key.reserve(11 * probs.size() + 3);
   key.push_back(static_cast<long long>(probs.size()));
   key.push_back(h->cfg.mode);
   key.push_back(h->cfg.slices);
   for (const Problem& q : probs) {
-    for (int v : {q.m, q.n, q.k, q.lda, q.ldb, q.ldc}) key.push_back(v);
+    for (int v : {q.m, q.n, q.k, q.lda, q.ldb, q.ldc, q.ta, q.tb}) key.push_back(v);
     key.push_back(static_cast<long long>(reinterpret_cast<uintptr_t>(q.A)));
     key.push_back(static_cast<long long>(reinterpret_cast<uintptr_t>(q.B)));
     key.push_back(static_cast<long long>(reinterpret_cast<uintptr_t>(q.C)));
@@ -884,20 +884,25 @@ mm_status grouped_impl(mm_handle h, const std::vector<Problem>& probs, cudaStrea
   return MM_OK;
 }
 
-// Validates one rectangular problem of the _ex entry points and fills *p.
-// m or n zero (or k zero with a valid C) is accepted; pointers need only be
-// 8-byte aligned (no kernel reads A, B or C with wider accesses).
-mm_status make_rect_problem(mm_handle h, int m, int n, int k, const double* A, int lda, const double* B, int ldb,
-                            double* C, int ldc, Problem* p) {
+// Validates one problem of the _ex entry points and fills *p.  op(A) is
+// m x k and op(B) k x n; ta / tb: A / B is stored as the transpose (k x m,
+// n x k).  m or n zero (or k zero with a valid C) is accepted; pointers need
+// only be 8-byte aligned (no kernel reads A, B or C with wider accesses).
+mm_status make_rect_problem(mm_handle h, int ta, int tb, int m, int n, int k, const double* A, int lda, const double* B,
+                            int ldb, double* C, int ldc, Problem* p) {
   if (m < 0 || n < 0 || k < 0) return fail(h, MM_ERR_INVALID, "M, N, K must be >= 0");
+  if ((ta != 0 && ta != 1) || (tb != 0 && tb != 1)) return fail(h, MM_ERR_INVALID, "transa, transb must be 0 or 1");
   *p = Problem{};
   p->m = m;
   p->n = n;
   p->k = k;
   if (m == 0 || n == 0) return MM_OK;
   if (!C || (k > 0 && (!A || !B))) return fail(h, MM_ERR_INVALID, "null matrix pointer");
-  if (lda < std::max(k, 1) || ldb < n || ldc < n)
-    return fail(h, MM_ERR_INVALID, "leading dimensions must be at least the row lengths (lda >= K, ldb >= N, ldc >= N)");
+  // stored shapes (rows x columns)
+  const int a_rows = ta ? k : m, a_cols = ta ? m : k;
+  const int b_rows = tb ? n : k, b_cols = tb ? k : n;
+  if (ldc < n || (k > 0 && (lda < a_cols || ldb < b_cols)))
+    return fail(h, MM_ERR_INVALID, "leading dimensions must be at least the stored row lengths");
   auto al8 = [](const void* q) { return (reinterpret_cast<uintptr_t>(q) & 7u) == 0; };
   if (!al8(C) || (k > 0 && (!al8(A) || !al8(B)))) return fail(h, MM_ERR_INVALID, "pointers must be 8-byte aligned");
   // C's span must not meet A's or B's
@@ -907,16 +912,18 @@ mm_status make_rect_problem(mm_handle h, int m, int n, int k, const double* A, i
   };
   const auto c = span(C, m, n, ldc);
   if (k > 0) {
-    const auto a = span(A, m, k, lda), b = span(B, k, n, ldb);
+    const auto a = span(A, a_rows, a_cols, lda), b = span(B, b_rows, b_cols, ldb);
     if ((c.first < a.second && a.first < c.second) || (c.first < b.second && b.first < c.second))
       return fail(h, MM_ERR_INVALID, "C must not overlap A or B");
   }
   p->A = A;
   p->B = B;
   p->C = C;
-  p->lda = lda;
-  p->ldb = ldb;
+  p->lda = k > 0 ? lda : 1;
+  p->ldb = k > 0 ? ldb : 1;
   p->ldc = ldc;
+  p->ta = ta;
+  p->tb = tb;
   return MM_OK;
 }
 
@@ -1096,11 +1103,11 @@ mm_status mm_gemm(mm_handle h, int N, const double* A, const double* B, double* 
   return single_impl(h, square_problem(A, B, C, N), static_cast<cudaStream_t>(stream));
 }
 
-mm_status mm_gemm_ex(mm_handle h, int M, int N, int K, const double* A, int lda, const double* B, int ldb, double* C,
-                     int ldc, void* stream) {
+mm_status mm_gemm_ex(mm_handle h, int transa, int transb, int M, int N, int K, const double* A, int lda,
+                     const double* B, int ldb, double* C, int ldc, void* stream) {
   if (!h) return MM_ERR_INVALID;
   Problem p{};
-  const mm_status st = make_rect_problem(h, M, N, K, A, lda, B, ldb, C, ldc, &p);
+  const mm_status st = make_rect_problem(h, transa, transb, M, N, K, A, lda, B, ldb, C, ldc, &p);
   if (st != MM_OK) return st;
   return single_impl(h, p, static_cast<cudaStream_t>(stream));
 }
@@ -1283,9 +1290,10 @@ mm_status mm_gemm_grouped(mm_handle h, int count, const int* Ns, const double* c
   return grouped_impl(h, probs, static_cast<cudaStream_t>(stream));
 }
 
-mm_status mm_gemm_grouped_ex(mm_handle h, int count, const int* Ms, const int* Ns, const int* Ks,
-                             const double* const* As, const int* ldas, const double* const* Bs, const int* ldbs,
-                             double* const* Cs, const int* ldcs, void* stream) {
+mm_status mm_gemm_grouped_ex(mm_handle h, int count, const int* transas, const int* transbs, const int* Ms,
+                             const int* Ns, const int* Ks, const double* const* As, const int* ldas,
+                             const double* const* Bs, const int* ldbs, double* const* Cs, const int* ldcs,
+                             void* stream) {
   if (!h) return MM_ERR_INVALID;
   if (count < 0) return fail(h, MM_ERR_INVALID, "count must be >= 0");
   if (count == 0) return MM_OK;
@@ -1294,7 +1302,8 @@ mm_status mm_gemm_grouped_ex(mm_handle h, int count, const int* Ms, const int* N
   probs.reserve(count);
   for (int i = 0; i < count; ++i) {
     Problem p{};
-    mm_status st = make_rect_problem(h, Ms[i], Ns[i], Ks[i], As[i], ldas[i], Bs[i], ldbs[i], Cs[i], ldcs[i], &p);
+    mm_status st = make_rect_problem(h, transas ? transas[i] : 0, transbs ? transbs[i] : 0, Ms[i], Ns[i], Ks[i], As[i],
+                                     ldas[i], Bs[i], ldbs[i], Cs[i], ldcs[i], &p);
     if (st != MM_OK) return st;
     probs.push_back(p);
   }

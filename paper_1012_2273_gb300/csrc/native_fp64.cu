@@ -7,8 +7,9 @@
 // of B through a double-buffered shared-memory ring (cp.async, 8-byte copies,
 // so any shape and leading dimension works: rows of an odd-N matrix are not
 // 16-byte aligned, which rules out TMA tiles), and four warps run mma.sync
-// m16n8k4 f64 on 32 x 32 sub-tiles.  C (m x n) = A (m x k) . B (k x n), each
-// row-major with its own leading dimension; the square product is m = n = k.
+// m16n8k4 f64 on 32 x 32 sub-tiles.  C (m x n) = op(A) (m x k) . op(B)
+// (k x n), each stored row-major with its own leading dimension, op() the
+// identity or the transpose; the square product is m = n = k.
 // Each output is a chain of FP64 fused multiply-adds; the order differs from
 // the paper's left-to-right sum, so results agree with it to within
 // gamma_N |A||B| rather than bit for bit (exactly, when all partial sums are
@@ -47,21 +48,12 @@ __device__ __forceinline__ void dmma_16x8x4(double (&c)[4], double a0, double a1
       : "d"(a0), "d"(a1), "d"(b0));
 }
 
-__global__ void __launch_bounds__(NT_THREADS) native_fp64_kernel(const __grid_constant__ NativeArgs args) {
-  __shared__ __align__(16) double As[2][NT_BK][NT_LD];  // [k][m]
-  __shared__ __align__(16) double Bs[2][NT_BK][NT_LD];  // [k][n]
-
-  const int tile = blockIdx.x;
-  const Problem* P;
-  if (args.table) {
-    P = &args.table[find_problem(args.table, args.count, tile)];
-  } else {
-    P = &args.single;
-  }
+// One 64 x 64 tile of C; TA / TB: the stored A / B is the transpose of op(A) / op(B).
+template <bool ta, bool tb>
+__device__ __forceinline__ void native_tile(const Problem* P, int local, double (&As)[2][NT_BK][NT_LD],
+                                            double (&Bs)[2][NT_BK][NT_LD]) {
   const int n = P->n, m = P->m, kdim = P->k;
   const size_t lda = P->lda, ldb = P->ldb, ldc = P->ldc;
-  const int local = tile - P->tile_begin;
-  if (n <= 0 || m <= 0 || local < 0 || local >= P->tiles_m * P->tiles_n) return;
   const int m0 = (local / P->tiles_n) * NT_BM;
   const int n0 = (local % P->tiles_n) * NT_BN;
   const double* __restrict__ A = P->A;
@@ -77,18 +69,23 @@ __global__ void __launch_bounds__(NT_THREADS) native_fp64_kernel(const __grid_co
 #pragma unroll
     for (int it = 0; it < (NT_BM * NT_BK) / NT_THREADS; ++it) {
       const int idx = tid + it * NT_THREADS;
-      const int r = idx / NT_BK, c = idx % NT_BK;  // A: row r of the tile, column c
+      // row r (m) and column c (k) of the op(A) tile; consecutive threads
+      // follow the stored matrix's rows (k for A, m for a transposed A)
+      const int r = ta ? idx % NT_BM : idx / NT_BK, c = ta ? idx / NT_BM : idx % NT_BK;
       const int gi = m0 + r, gk = k0 + c;
       const bool ok = gi < m && gk < kdim;
-      cp_async_8(&As[buf][c][r], ok ? A + (size_t)gi * lda + gk : A, ok);
+      const size_t off = ta ? (size_t)gk * lda + gi : (size_t)gi * lda + gk;
+      cp_async_8(&As[buf][c][r], ok ? A + off : A, ok);
     }
 #pragma unroll
     for (int it = 0; it < (NT_BK * NT_BN) / NT_THREADS; ++it) {
       const int idx = tid + it * NT_THREADS;
-      const int r = idx / NT_BN, c = idx % NT_BN;  // B: row r (k), column c
+      // row r (k) and column c (n) of the op(B) tile, coalesced likewise
+      const int r = tb ? idx % NT_BK : idx / NT_BN, c = tb ? idx / NT_BK : idx % NT_BN;
       const int gk = k0 + r, gj = n0 + c;
       const bool ok = gk < kdim && gj < n;
-      cp_async_8(&Bs[buf][r][c], ok ? B + (size_t)gk * ldb + gj : B, ok);
+      const size_t off = tb ? (size_t)gj * ldb + gk : (size_t)gk * ldb + gj;
+      cp_async_8(&Bs[buf][r][c], ok ? B + off : B, ok);
     }
     cp_async_commit();
   };
@@ -147,6 +144,21 @@ __global__ void __launch_bounds__(NT_THREADS) native_fp64_kernel(const __grid_co
     }
 }
 
+__global__ void __launch_bounds__(NT_THREADS, 4) native_fp64_kernel(const __grid_constant__ NativeArgs args) {
+  __shared__ __align__(16) double As[2][NT_BK][NT_LD];  // [k][m]
+  __shared__ __align__(16) double Bs[2][NT_BK][NT_LD];  // [k][n]
+  const int tile = blockIdx.x;
+  const Problem* P = args.table ? &args.table[find_problem(args.table, args.count, tile)] : &args.single;
+  const int local = tile - P->tile_begin;
+  if (P->n <= 0 || P->m <= 0 || local < 0 || local >= P->tiles_m * P->tiles_n) return;
+  // one code path per storage order (uniform over the CTA)
+  if (P->ta) {
+    if (P->tb) native_tile<true, true>(P, local, As, Bs); else native_tile<true, false>(P, local, As, Bs);
+  } else {
+    if (P->tb) native_tile<false, true>(P, local, As, Bs); else native_tile<false, false>(P, local, As, Bs);
+  }
+}
+
 // Small problems: one warp per 16 x 16 tile of C, so that N ~ 100 still spreads
 // over many SMs (a 64 x 64 tile would leave all but a few idle, and the FP64
 // MMA rate of one SM is small).  Fragments are loaded straight from global
@@ -158,6 +170,7 @@ __global__ void __launch_bounds__(32) native_fp64_small_kernel(const __grid_cons
   const Problem* P = args.table ? &args.table[find_problem(args.table, args.count, tile)] : &args.single;
   const int n = P->n, m = P->m, kdim = P->k;
   const size_t lda = P->lda, ldb = P->ldb, ldc = P->ldc;
+  const bool ta = P->ta != 0, tb = P->tb != 0;
   const int local = tile - P->tile_begin;
   if (n <= 0 || m <= 0 || local < 0 || local >= P->tiles_m * P->tiles_n) return;
   const int m0 = (local / P->tiles_n) * NS_TILE;
@@ -173,12 +186,13 @@ __global__ void __launch_bounds__(32) native_fp64_small_kernel(const __grid_cons
     for (int kk = 0; kk < 4; ++kk) {
       const int k = k0 + 4 * kk + t;
       const bool kin = k < kdim;
-      a[kk][0] = (kin && ra < m) ? A[static_cast<size_t>(ra) * lda + k] : 0.0;
-      a[kk][1] = (kin && rb < m) ? A[static_cast<size_t>(rb) * lda + k] : 0.0;
+      a[kk][0] = (kin && ra < m) ? A[ta ? static_cast<size_t>(k) * lda + ra : static_cast<size_t>(ra) * lda + k] : 0.0;
+      a[kk][1] = (kin && rb < m) ? A[ta ? static_cast<size_t>(k) * lda + rb : static_cast<size_t>(rb) * lda + k] : 0.0;
 #pragma unroll
       for (int ni = 0; ni < 2; ++ni) {
         const int col = n0 + ni * 8 + g;
-        b[kk][ni] = (kin && col < n) ? B[static_cast<size_t>(k) * ldb + col] : 0.0;
+        b[kk][ni] = (kin && col < n) ? B[tb ? static_cast<size_t>(col) * ldb + k : static_cast<size_t>(k) * ldb + col]
+                                     : 0.0;
       }
     }
 #pragma unroll

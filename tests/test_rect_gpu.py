@@ -166,13 +166,13 @@ def test_rect_argument_checks():
     with handle("native") as h:
         hp = h._h
         a, b, c = A.data_ptr(), B.data_ptr(), C.data_ptr()
-        assert L.mm_gemm_ex(hp, 8, 5, 6, a, 5, b, 5, c, 5, None) == 1  # lda < K
-        assert L.mm_gemm_ex(hp, 8, 5, 6, a, 6, b, 4, c, 5, None) == 1  # ldb < N
-        assert L.mm_gemm_ex(hp, 8, 5, 6, a, 6, b, 5, c, 4, None) == 1  # ldc < N
-        assert L.mm_gemm_ex(hp, -1, 5, 6, a, 6, b, 5, c, 5, None) == 1
-        assert L.mm_gemm_ex(hp, 8, 5, 6, a + 4, 6, b, 5, c, 5, None) == 1  # misaligned
-        assert L.mm_gemm_ex(hp, 8, 5, 6, a, 6, b, 5, a, 5, None) == 1  # C overlaps A
-        assert L.mm_gemm_ex(hp, 0, 5, 6, None, 6, None, 5, None, 5, None) == 0  # M = 0: no-op
+        assert L.mm_gemm_ex(hp, 0, 0, 8, 5, 6, a, 5, b, 5, c, 5, None) == 1  # lda < K
+        assert L.mm_gemm_ex(hp, 0, 0, 8, 5, 6, a, 6, b, 4, c, 5, None) == 1  # ldb < N
+        assert L.mm_gemm_ex(hp, 0, 0, 8, 5, 6, a, 6, b, 5, c, 4, None) == 1  # ldc < N
+        assert L.mm_gemm_ex(hp, 0, 0, -1, 5, 6, a, 6, b, 5, c, 5, None) == 1
+        assert L.mm_gemm_ex(hp, 0, 0, 8, 5, 6, a + 4, 6, b, 5, c, 5, None) == 1  # misaligned
+        assert L.mm_gemm_ex(hp, 0, 0, 8, 5, 6, a, 6, b, 5, a, 5, None) == 1  # C overlaps A
+        assert L.mm_gemm_ex(hp, 0, 0, 0, 5, 6, None, 6, None, 5, None, 5, None) == 0  # M = 0: no-op
         with pytest.raises(ValueError):
             h.gemm(A, torch.zeros((5, 5), dtype=torch.float64, device="cuda"))
         h.check()
@@ -204,3 +204,90 @@ def test_rect_cta_pair_kernel(monkeypatch):
         C = host(h.gemm(dev(A), dev(B)))
         h.check()
     np.testing.assert_array_equal(bits(C), bits(oracle.fixed_gemm_mnk(A, B, oracle.modular_beta(15, k))))
+
+
+def stored(X, transposed, pad_rows=0, pad_cols=0):
+    """Device operand for op() = X: X itself, or the transpose of a stored X^T
+    (passed as a .T view), optionally as a window of a larger array."""
+    import torch
+    S = np.ascontiguousarray(X.T) if transposed else X
+    big = torch.full((S.shape[0] + pad_rows, S.shape[1] + pad_cols), 11.0, dtype=torch.float64, device="cuda")
+    win = big[pad_rows:, pad_cols:]
+    win.copy_(torch.from_numpy(S))
+    return win.T if transposed else win
+
+
+@pytest.mark.parametrize("ta,tb", [(0, 1), (1, 0), (1, 1)])
+@pytest.mark.parametrize("mode,slices", [("native", 0), ("modular", 16), ("emulated", 7)])
+def test_rect_transposed_operands(mode, slices, ta, tb):
+    m, n, k = 300, 129, 257
+    A, B = workload.rect_pair("loguniform20" if mode == "modular" else "uniform11", 50 + 2 * ta + tb, m, n, k)
+    dA = stored(A, ta, pad_rows=1, pad_cols=3)
+    dB = stored(B, tb, pad_rows=2, pad_cols=1)
+    assert (dA.stride(0) == 1) == bool(ta) and (dB.stride(0) == 1) == bool(tb)
+    with handle(mode, slices) as h:
+        C = host(h.gemm(dA, dB))
+        h.check()
+    if mode == "modular":
+        np.testing.assert_array_equal(bits(C), bits(oracle.fixed_gemm_mnk(A, B, oracle.modular_beta(16, k))))
+    elif mode == "emulated":
+        np.testing.assert_array_equal(bits(C), bits(oracle.emu_gemm_mnk(A, B, 7)))
+    else:
+        assert_within_bound(C, oracle.gemm_mnk(A, B), oracle.absgemm_mnk(A, B), k)
+
+
+def test_native_transposes_give_the_same_bits():
+    # the native kernel sums each output in the same k order whatever the storage
+    m, n, k = 517, 300, 200
+    A, B = workload.rect_pair("uniform11", 8, m, n, k)
+    with handle("native") as h:
+        ref = host(h.gemm(dev(A), dev(B)))
+        for ta in (0, 1):
+            for tb in (0, 1):
+                C = host(h.gemm(stored(A, ta), stored(B, tb)))
+                np.testing.assert_array_equal(bits(C), bits(ref))
+        h.check()
+
+
+def test_grouped_with_transposed_operands(tmp_path):
+    tune = tmp_path / "tune.txt"
+    tune.write_text("60 0 7 256 0\n300 1 7 256 0\n100000 2 15 256 0\n")
+    import paper_1012_2273_gb300 as mm
+    shapes = [(700, 300, 513), (250, 250, 250), (30, 20, 50), (129, 257, 640), (64, 64, 1)]
+    pairs = [workload.rect_pair("uniform11", 70 + i, *s[:2], s[2]) for i, s in enumerate(shapes)]
+    As = [stored(A, i % 2) for i, (A, _) in enumerate(pairs)]
+    Bs = [stored(B, (i // 2) % 2) for i, (_, B) in enumerate(pairs)]
+    with mm.Handle("auto", tune_path=str(tune)) as h:
+        plans = {s: h.plan(max(s)) for s in shapes}
+        Cs = h.gemm_grouped(As, Bs)
+        h.check()
+    for (A, B), C, s in zip(pairs, Cs, shapes):
+        form, sl = plans[s]
+        C = host(C)
+        k = s[2]
+        if form == 0:
+            assert_within_bound(C, oracle.gemm_mnk(A, B), oracle.absgemm_mnk(A, B), k)
+        elif form == 1:
+            np.testing.assert_array_equal(bits(C), bits(oracle.emu_gemm_mnk(A, B, sl)))
+        else:
+            np.testing.assert_array_equal(bits(C), bits(oracle.fixed_gemm_mnk(A, B, oracle.modular_beta(sl, k))))
+
+
+def test_transposed_argument_checks():
+    import torch
+    import paper_1012_2273_gb300 as mm
+    L = mm.lib()
+    A = torch.zeros((6, 8), dtype=torch.float64, device="cuda")  # stored K x M for op(A) = A^T, M = 8, K = 6
+    B = torch.zeros((5, 6), dtype=torch.float64, device="cuda")  # stored N x K for op(B) = B^T
+    C = torch.zeros((8, 5), dtype=torch.float64, device="cuda")
+    with handle("native") as h:
+        hp = h._h
+        a, b, c = A.data_ptr(), B.data_ptr(), C.data_ptr()
+        assert L.mm_gemm_ex(hp, 1, 1, 8, 5, 6, a, 8, b, 6, c, 5, None) == 0
+        h.check()
+        assert L.mm_gemm_ex(hp, 2, 0, 8, 5, 6, a, 8, b, 6, c, 5, None) == 1  # flag not 0/1
+        assert L.mm_gemm_ex(hp, 1, 1, 8, 5, 6, a, 7, b, 6, c, 5, None) == 1  # lda < M for a stored K x M
+        assert L.mm_gemm_ex(hp, 1, 1, 8, 5, 6, a, 8, b, 5, c, 5, None) == 1  # ldb < K for a stored N x K
+        with pytest.raises(ValueError):
+            h.gemm(A.T, B.T, C[:, :4])
+        h.check()
