@@ -158,50 +158,39 @@ __host__ __device__ inline int absmax_a_blocks(const Problem& p) {
   return p.m_pad > 0 && p.n > 0 ? absmax_operand_blocks(p.m, p.k, !p.ta) : 0;
 }
 
-__global__ void __launch_bounds__(SP_THREADS) absmax_kernel(const __grid_constant__ SplitArgs args) {
-  __shared__ unsigned long long part[SP_THREADS / AM_BCOLS][AM_BCOLS];
-  const Problem* P;
-  const int pi = absmax_find(args, blockIdx.x, &P);
-  const int kdim = P->k;
-  int local = blockIdx.x - (args.table ? P->absmax_begin : 0);
-  const int a_blocks = absmax_a_blocks(*P);
-  const bool is_a = local < a_blocks;
-  if (!is_a) local -= a_blocks;
-  // The maxima run over the k entries of each row of op(A) / column of op(B):
-  // along the stored rows for A and a transposed B, along the stored columns
-  // for B and a transposed A.
-  const bool by_rows = is_a ? !P->ta : P->tb;
-  const uint64_t* src = reinterpret_cast<const uint64_t*>(is_a ? P->A : P->B);
-  const size_t ld = is_a ? P->lda : P->ldb;
-  const int outs = is_a ? P->m : P->n;  // number of maxima
-  const int off = args.max_offset ? args.max_offset[pi] : 0;
-  uint64_t* dst = (is_a ? args.a_maxbits : args.b_maxbits) + off;
+// Maxima along stored rows: warp `warp` of block `blk` takes row blk *
+// AM_ROWS + warp (< outs) of length kdim and stores its maximum.
+__device__ __forceinline__ void absmax_rows(const uint64_t* src, size_t ld, int outs, int kdim, uint64_t* dst,
+                                            int blk) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  if (by_rows) {
-    const int i = local * AM_ROWS + warp;
-    if (i >= outs) return;
-    const uint64_t* row = src + static_cast<size_t>(i) * ld;
-    unsigned long long m = 0;
-    for (int j0 = 0; j0 < kdim; j0 += 32 * 8) {
-      unsigned long long v[8];
+  const int i = blk * AM_ROWS + warp;
+  if (i >= outs) return;
+  const uint64_t* row = src + static_cast<size_t>(i) * ld;
+  unsigned long long m = 0;
+  for (int j0 = 0; j0 < kdim; j0 += 32 * 8) {
+    unsigned long long v[8];
 #pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        const int j = j0 + 32 * q + lane;
-        v[q] = j < kdim ? row[j] & 0x7FFFFFFFFFFFFFFFull : 0ull;
-      }
-#pragma unroll
-      for (int q = 0; q < 8; ++q) m = v[q] > m ? v[q] : m;
+    for (int q = 0; q < 8; ++q) {
+      const int j = j0 + 32 * q + lane;
+      v[q] = j < kdim ? row[j] & 0x7FFFFFFFFFFFFFFFull : 0ull;
     }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const unsigned long long v = __shfl_xor_sync(0xffffffffu, m, o);
-      m = v > m ? v : m;
-    }
-    if (lane == 0) dst[i] = m;
-    return;
+    for (int q = 0; q < 8; ++q) m = v[q] > m ? v[q] : m;
   }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long v = __shfl_xor_sync(0xffffffffu, m, o);
+    m = v > m ? v : m;
+  }
+  if (lane == 0) dst[i] = m;
+}
+
+// Maxima along stored columns: block `blk` takes a band of AM_BCOLS columns
+// (< outs) x AM_BROWS rows (< kdim) and raises the columns' maxima.
+__device__ __forceinline__ void absmax_cols(const uint64_t* src, size_t ld, int outs, int kdim, uint64_t* dst,
+                                            int blk, unsigned long long (&part)[SP_THREADS / AM_BCOLS][AM_BCOLS]) {
   const int nbc = (outs + AM_BCOLS - 1) / AM_BCOLS;
-  const int k0 = (local % nbc) * AM_BCOLS, j0 = (local / nbc) * AM_BROWS;
+  const int k0 = (blk % nbc) * AM_BCOLS, j0 = (blk / nbc) * AM_BROWS;
   const int c = threadIdx.x % AM_BCOLS, ph = threadIdx.x / AM_BCOLS;
   constexpr int PHASES = SP_THREADS / AM_BCOLS;
   const int k = k0 + c;  // stored column
@@ -227,6 +216,28 @@ __global__ void __launch_bounds__(SP_THREADS) absmax_kernel(const __grid_constan
     for (int w = 0; w < PHASES; ++w) mm = part[w][threadIdx.x] > mm ? part[w][threadIdx.x] : mm;
     if (mm) atomicMax(reinterpret_cast<unsigned long long*>(&dst[k0 + threadIdx.x]), mm);
   }
+}
+
+__global__ void __launch_bounds__(SP_THREADS) absmax_kernel(const __grid_constant__ SplitArgs args) {
+  __shared__ unsigned long long part[SP_THREADS / AM_BCOLS][AM_BCOLS];
+  const Problem* P;
+  const int pi = absmax_find(args, blockIdx.x, &P);
+  int local = blockIdx.x - (args.table ? P->absmax_begin : 0);
+  const int a_blocks = absmax_a_blocks(*P);
+  const bool is_a = local < a_blocks;
+  if (!is_a) local -= a_blocks;
+  const int off = args.max_offset ? args.max_offset[pi] : 0;
+  // The maxima run over the k entries of each row of op(A) / column of op(B):
+  // along the stored rows for A and a transposed B, along the stored columns
+  // for B and a transposed A.
+  const uint64_t* src = reinterpret_cast<const uint64_t*>(is_a ? P->A : P->B);
+  const size_t ld = is_a ? P->lda : P->ldb;
+  const int outs = is_a ? P->m : P->n, kdim = P->k;
+  uint64_t* dst = (is_a ? args.a_maxbits : args.b_maxbits) + off;
+  if (is_a ? !P->ta : P->tb)
+    absmax_rows(src, ld, outs, kdim, dst, local);
+  else
+    absmax_cols(src, ld, outs, kdim, dst, local, part);
 }
 
 // Writes the digit planes of one 64 x 64 tile.  Phase 1 reads the tile
