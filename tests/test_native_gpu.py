@@ -98,3 +98,27 @@ def test_host_entry_point(h):
     A, B = workload.pair("int8", 9, n)
     C = h.gemm_host(A, B)
     np.testing.assert_array_equal(C, oracle.gemm(A, B))
+
+
+def test_native_bitwise_reproducible_across_runs_tile_shapes_and_calls():
+    # Each output of the native form is one chain of mma.sync over k in
+    # increasing order in both tile shapes (16 x 16 below 512 rows and
+    # columns, 64 x 64 above), with no split-K and no atomics, so the result
+    # is bitwise reproducible: across runs, between the two kernels (a 500 x
+    # 500 product against the first 500 rows of a 600 x 500 one with the same
+    # rows of A) and between single and grouped calls.
+    import torch
+    import paper_1012_2273_gb300 as mm
+    n = 500
+    A, B = workload.pair("loguniform20", 19, n)
+    A2 = np.vstack([A, workload.matrix("uniform11", 20, n)[:100]])
+    with mm.Handle("native") as h:
+        C1 = host(h.gemm(dev(A), dev(B)))
+        C2 = host(h.gemm(dev(A), dev(B)))
+        big = host(h.gemm(dev(A2), dev(B)))            # 600 x 500: the 64 x 64 kernel
+        G = h.gemm_grouped([dev(A), dev(A2)], [dev(B), dev(B)])
+        h.check()
+    assert np.array_equal(C1.view(np.int64), C2.view(np.int64))
+    assert np.array_equal(C1.view(np.int64), big[:n].view(np.int64))
+    assert np.array_equal(host(G[0]).view(np.int64), C1.view(np.int64))
+    assert np.array_equal(host(G[1]).view(np.int64), big.view(np.int64))
