@@ -127,10 +127,26 @@ def _check_tensor(t, name: str, n: int | None = None):
         raise ValueError(f"{name} must be square" + (f" of size {n}" if n is not None else ""))
 
 
+def _layout(rows: int, cols: int, stride0: int, stride1: int, allow_transposed: bool, name: str = "matrix"):
+    """(rows, cols, leading dimension, transposed) of a matrix with element
+    strides (stride0, stride1): row-major (unit column stride, row stride >=
+    cols) or -- where allowed -- the transpose of a row-major matrix (unit row
+    stride, column stride >= rows, e.g. ``X.T``).  Single rows and columns
+    take the row-major reading; the leading dimension is at least 1."""
+    if cols <= 1 or stride1 == 1:
+        ld = stride0 if rows > 1 and cols > 0 else cols
+        if ld >= cols:
+            return rows, cols, max(ld, 1), 0
+    if allow_transposed and (rows <= 1 or stride0 == 1):
+        ld = stride1 if cols > 1 and rows > 0 else rows
+        if ld >= rows:
+            return rows, cols, max(ld, 1), 1
+    raise ValueError(f"{name} must be row-major with a row stride >= its row length"
+                     + (" (or the transpose of such a matrix)" if allow_transposed else ""))
+
+
 def _matrix(t, name: str, allow_transposed: bool = False):
-    """(rows, cols, leading dimension, transposed) of a float64 CUDA matrix view:
-    row-major (unit column stride), or -- where allowed -- the transpose of a
-    row-major matrix (unit row stride, e.g. ``X.T``)."""
+    """_layout of a float64 CUDA matrix view."""
     import torch
     if not isinstance(t, torch.Tensor) or not t.is_cuda:
         raise TypeError(f"{name} must be a CUDA tensor")
@@ -138,17 +154,7 @@ def _matrix(t, name: str, allow_transposed: bool = False):
         raise TypeError(f"{name} must be float64")
     if t.dim() != 2:
         raise ValueError(f"{name} must be 2-D")
-    rows, cols = int(t.shape[0]), int(t.shape[1])
-    if cols <= 1 or t.stride(1) == 1:
-        ld = int(t.stride(0)) if rows > 1 and cols > 0 else cols
-        if ld >= cols:
-            return rows, cols, max(ld, 1), 0
-    if allow_transposed and (rows <= 1 or t.stride(0) == 1):
-        ld = int(t.stride(1)) if cols > 1 and rows > 0 else rows
-        if ld >= rows:
-            return rows, cols, max(ld, 1), 1
-    raise ValueError(f"{name} must be row-major with a row stride >= its row length"
-                     + (" (or the transpose of such a matrix)" if allow_transposed else ""))
+    return _layout(int(t.shape[0]), int(t.shape[1]), int(t.stride(0)), int(t.stride(1)), allow_transposed, name)
 
 
 def _square_contiguous(*ts) -> bool:

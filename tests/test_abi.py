@@ -47,6 +47,34 @@ def test_argument_checks_without_gpu():
     assert L.mm_destroy(None) == 1
     assert L.mm_last_error(None) == b"invalid handle"
     assert L.mm_gemm_grouped(None, 1, None, None, None, None, None) == 1
+    assert L.mm_gemm_ex(None, 0, 0, 4, 4, 4, None, 4, None, 4, None, 4, None) == 1
+    assert L.mm_gemm_grouped_ex(None, 1, None, None, None, None, None, None, None, None, None, None, None,
+                                None) == 1
+
+
+@pytest.mark.parametrize("shape,strides,trans_ok,want", [
+    ((5, 7), (7, 1), False, (5, 7, 7, 0)),       # contiguous
+    ((5, 7), (10, 1), False, (5, 7, 10, 0)),     # window of a wider array
+    ((5, 7), (1, 5), True, (5, 7, 5, 1)),        # X.T of a contiguous 7 x 5 X
+    ((5, 7), (1, 9), True, (5, 7, 9, 1)),        # X.T of a window
+    ((1, 7), (3, 1), False, (1, 7, 7, 0)),       # one row: its stride is irrelevant
+    ((5, 1), (1, 1), False, (5, 1, 1, 0)),       # one column: row-major with ld 1
+    ((5, 0), (0, 1), False, (5, 0, 1, 0)),       # empty rows: ld clamped to 1
+    ((0, 4), (4, 1), False, (0, 4, 4, 0)),
+])
+def test_binding_layout_rule(shape, strides, trans_ok, want):
+    assert mm._layout(shape[0], shape[1], strides[0], strides[1], trans_ok) == want
+
+
+@pytest.mark.parametrize("shape,strides,trans_ok", [
+    ((5, 7), (1, 5), False),   # transposed where only row-major is accepted (C)
+    ((5, 7), (7, 2), True),    # neither unit column nor unit row stride
+    ((5, 7), (6, 1), False),   # row stride below the row length
+    ((5, 7), (1, 4), True),    # transposed, column stride below the column length
+])
+def test_binding_layout_rule_rejects(shape, strides, trans_ok):
+    with pytest.raises(ValueError):
+        mm._layout(shape[0], shape[1], strides[0], strides[1], trans_ok)
 
 
 def test_header_cites_the_paper_and_states_conventions():
