@@ -34,8 +34,12 @@
  *
  * Conventions for every call:
  *   - Matrices are square, row-major, leading dimension N, FP64, 16-byte
- *     aligned device pointers, owned by the caller.  C is overwritten
+ *     aligned device pointers, owned by the caller -- except in mm_gemm_ex
+ *     and mm_gemm_grouped_ex, which take rectangular shapes, leading
+ *     dimensions, transposed storage and 8-byte alignment.  C is overwritten
  *     (beta = 0) and must not overlap A or B.
+ *   - A handle's workspace serves one call at a time: concurrent calls on
+ *     different streams need one handle each.
  *   - Calls are asynchronous on `stream` (a cudaStream_t passed as void*;
  *     NULL is the legacy default stream).  The return value covers argument
  *     checks and launch errors only; errors found on the device (a timed-out
