@@ -22,16 +22,12 @@ import json
 
 
 def row_ranges(n_rows: int, workers: int) -> list[tuple[int, int]]:
-    """Row blocks of the paper's split: n // W rows each, one more for the first n % W."""
+    """Row blocks [r0, r1) of the paper's split (shard.rows_of_worker): n // W
+    rows each, one more for each of the first n % W workers."""
+    from paper_1012_2273_gb300.shard import rows_of_worker
     if workers < 1:
         raise ValueError("workers must be >= 1")
-    base, extra = divmod(n_rows, workers)
-    out, r0 = [], 0
-    for w in range(workers):
-        r1 = r0 + base + (1 if w < extra else 0)
-        out.append((r0, r1))
-        r0 = r1
-    return out
+    return [(o, o + c) for o, c in (rows_of_worker(n_rows, workers, w) for w in range(workers))]
 
 
 class RowBlockGemm:
