@@ -14,11 +14,20 @@
 //    W_g = M_k / M_g read back from the recombination table: the Chinese
 //    remainder theorem's reconstruction of X, for every k = 2..16.
 // 4. The limbs of every W_g above mod_weight_limbs(k) are zero.
+// 5. The split's residue arithmetic replayed with IEEE fmaf in the kernel's
+//    order (what each lane of fma.rn.f32x2 computes): limbs of |D| as exact
+//    floats carrying D's sign, S = x_0 + sum_l x_l c_l, r = S - m rint(S
+//    RN(1/m)) with rint the add-and-subtract of 1.5 2^23, for |D| up to 2^55
+//    (four 14-bit limbs) and 2^62 (five 13-bit limbs), edge values included:
+//    every r is an integer with r == D (mod m) and |r| <= m / 2.
 #include <vector_types.h>
+
+#include <cmath>
 
 #include <cstdint>
 #include <cstdio>
 #include <cstdlib>
+#include <cstring>
 
 #include "../paper_1012_2273_gb300/csrc/modular.cuh"
 
@@ -140,6 +149,46 @@ int main() {
           v = (v + static_cast<uint64_t>(Tg[g] % m) * w) % m;
         }
         CHECK(v == mod_i128(X, m), "sum_g T_g W_g != X mod m_%d (k=%d, trial %d)", j, k, trial);
+      }
+    }
+  }
+  // 5. residues of the split
+  for (int limbs = 4; limbs <= 5; ++limbs) {
+    const int lb = mod_limb_bits(limbs);
+    const int maxbits = limbs == 4 ? 55 : 62;
+    for (int trial = 0; trial < 200000; ++trial) {
+      int64_t D;
+      const uint64_t top = 1ull << maxbits;
+      if (trial < 8) {
+        const int64_t edge[8] = {0, 1, -1, static_cast<int64_t>(top), -static_cast<int64_t>(top),
+                                 static_cast<int64_t>(top - 1), -static_cast<int64_t>(top - 1), 12345};
+        D = edge[trial];
+      } else {
+        const uint64_t mag = next_u64() >> (64 - 1 - maxbits + (trial % 40));  // magnitudes across the range
+        D = (next_u64() & 1) ? -static_cast<int64_t>(mag % (top + 1)) : static_cast<int64_t>(mag % (top + 1));
+      }
+      const uint64_t X = D < 0 ? 0ull - static_cast<uint64_t>(D) : static_cast<uint64_t>(D);
+      const float sg = D < 0 ? -1.0f : 1.0f, bias = D < 0 ? 8388608.0f : -8388608.0f;
+      float x[5];
+      for (int l = 0; l < limbs; ++l) {
+        const uint32_t limb = static_cast<uint32_t>(X >> (lb * l)) & ((1u << lb) - 1);
+        uint32_t pat = 0x4B000000u | limb;
+        float f;
+        std::memcpy(&f, &pat, 4);
+        x[l] = std::fmaf(sg, f, bias);
+      }
+      for (int j = 0; j < MOD_COUNT; ++j) {
+        const uint32_t m = T.m_u[j];
+        float S = x[0];
+        for (int l = 1; l < limbs; ++l)
+          S = std::fmaf(x[l], limbs == 4 ? T.pair_c14[j][l - 1].x : T.pair_c13[j][l - 1].x, S);
+        const float qt = std::fmaf(S, T.pair_inv[j].x, 12582912.0f) - 12582912.0f;
+        const float r = std::fmaf(qt, T.pair_negm[j].x, S);
+        const bool integral = r == std::nearbyint(r);
+        const int64_t ri = static_cast<int64_t>(r);
+        const int64_t dm = ((D % static_cast<int64_t>(m)) + m) % m;
+        CHECK(integral && std::fabs(r) <= m / 2.0f && ((ri % static_cast<int64_t>(m)) + m) % m == dm,
+              "split residue of D=%lld mod %u (limbs %d): r=%f", static_cast<long long>(D), m, limbs, r);
       }
     }
   }

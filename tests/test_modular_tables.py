@@ -1,7 +1,8 @@
 """The modular form's constant tables, checked on the host against exact
 integer arithmetic (tests/modular_tables_check.cpp): split constants, the
-epilogue's divisions by the moduli, and the epilogue's group residues
-recombined by the Chinese remainder theorem for every moduli count."""
+epilogue's divisions by the moduli, the epilogue's group residues recombined
+by the Chinese remainder theorem for every moduli count, and the split's FP32
+residue arithmetic replayed with IEEE fmaf over the whole fixed-point range."""
 import os
 import shutil
 import subprocess
