@@ -20,6 +20,11 @@
 //    RN(1/m)) with rint the add-and-subtract of 1.5 2^23, for |D| up to 2^55
 //    (four 14-bit limbs) and 2^62 (five 13-bit limbs), edge values included:
 //    every r is an integer with r == D (mod m) and |r| <= m / 2.
+// 6. The recombination replayed (32-bit limbs of W_g into 64-bit
+//    accumulators, carries, the FP32 estimate of round(V / M) from V's top
+//    limbs, X = V - q M modulo 2^128) from the group residues of step 3, for
+//    |X| up to the width rule's bound M/2 - M/514 and at it: X is recovered
+//    exactly for every k = 2..16.
 #include <vector_types.h>
 
 #include <cmath>
@@ -150,6 +155,55 @@ int main() {
         }
         CHECK(v == mod_i128(X, m), "sum_g T_g W_g != X mod m_%d (k=%d, trial %d)", j, k, trial);
       }
+    }
+  }
+  // 6. recombination from the group residues
+  for (int k = 2; k <= MOD_COUNT; ++k) {
+    const int ng = mod_groups(k);
+    unsigned __int128 M = 0;
+    for (int l = 3; l >= 0; --l) M = (M << 32) | T.mk[k][l];
+    const __int128 lim = static_cast<__int128>(M / 2 - M / 514);
+    const int QS = limbs_bit_length(mod_product(k)) - 31;
+    for (int trial = 0; trial < 3000; ++trial) {
+      __int128 X;
+      if (trial < 6) {
+        const __int128 e[6] = {lim, -lim, lim - 1, -lim + 1, 0, -1};
+        X = e[trial];
+      } else {
+        const unsigned __int128 r = (static_cast<unsigned __int128>(next_u64()) << 64) | next_u64();
+        X = static_cast<__int128>(r % (2 * static_cast<unsigned __int128>(lim) + 1)) - lim;
+      }
+      // group residues as the epilogue forms them (step 3's arithmetic, S = X mod m)
+      uint32_t Tg[MOD_GROUPS] = {};
+      uint32_t ta = 0;
+      for (int j = 0; j < k; ++j) {
+        const uint32_t m = T.m_u[j];
+        const uint32_t r = mod_i128(X, m);
+        if ((j & 1) == 0 && j + 1 < k) {
+          ta = r * T.cy[k][j] - umulhi(r, T.cyq[k][j]) * m;
+          continue;
+        }
+        const bool paired = (j & 1) != 0;
+        const uint32_t Mg = paired ? T.m_u[j - 1] * m : m;
+        const uint32_t Tp = (paired ? ta * m : 0u) + r * T.cym[k][j];
+        Tg[j >> 1] = Tp - (umulhi(Tp, T.gmagic[k][j >> 1]) >> (paired ? 9 : 7)) * Mg;
+      }
+      // the recombination's arithmetic
+      uint64_t a[4] = {0, 0, 0, 0};
+      for (int g = 0; g < ng; ++g)
+        for (int l = 0; l < mod_weight_limbs(k); ++l) a[l] += static_cast<uint64_t>(Tg[g]) * T.wg[k][g][l];
+      const uint64_t a1 = a[1] + (a[0] >> 32), a2 = a[2] + (a1 >> 32), a3 = a[3] + (a2 >> 32);
+      const uint32_t w0 = static_cast<uint32_t>(a[0]), w1 = static_cast<uint32_t>(a1), w2 = static_cast<uint32_t>(a2);
+      float vf = static_cast<float>(a3) * pow2f(96 - QS) + static_cast<float>(w2) * pow2f(64 - QS);
+      if (QS < 100 - 31) vf += static_cast<float>(w1) * pow2f(32 - QS) + static_cast<float>(w0) * pow2f(-QS);
+      const uint64_t qt = static_cast<uint64_t>(std::lrintf(vf * T.qscale[k]));
+      const uint64_t m_lo = (static_cast<uint64_t>(T.mk[k][1]) << 32) | T.mk[k][0];
+      const uint64_t m_hi = (static_cast<uint64_t>(T.mk[k][3]) << 32) | T.mk[k][2];
+      const uint64_t lo = (static_cast<uint64_t>(w1) << 32) | w0, hi = (a3 << 32) | w2;
+      const unsigned __int128 qm = static_cast<unsigned __int128>(qt) * ((static_cast<unsigned __int128>(m_hi) << 64) | m_lo);
+      const unsigned __int128 V = (static_cast<unsigned __int128>(hi) << 64) | lo;
+      const __int128 Xr = static_cast<__int128>(V - qm);
+      CHECK(Xr == X, "recombination k=%d trial %d", k, trial);
     }
   }
   // 5. residues of the split

@@ -1,8 +1,10 @@
 """The modular form's constant tables, checked on the host against exact
 integer arithmetic (tests/modular_tables_check.cpp): split constants, the
 epilogue's divisions by the moduli, the epilogue's group residues recombined
-by the Chinese remainder theorem for every moduli count, and the split's FP32
-residue arithmetic replayed with IEEE fmaf over the whole fixed-point range."""
+by the Chinese remainder theorem for every moduli count, the recombination's
+quotient estimate and 128-bit reconstruction at the width rule's extremes,
+and the split's FP32 residue arithmetic replayed with IEEE fmaf over the whole
+fixed-point range."""
 import os
 import shutil
 import subprocess
@@ -27,7 +29,7 @@ def test_modular_tables_against_exact_arithmetic(tmp_path):
         pytest.skip("needs g++ and the CUDA headers")
     exe = str(tmp_path / "modular_tables_check")
     src = os.path.join(ROOT, "tests", "modular_tables_check.cpp")
-    subprocess.run([gxx, "-std=c++17", "-O2", "-I", inc, "-I", os.path.join(ROOT, "include"), src, "-o", exe],
+    subprocess.run([gxx, "-std=c++17", "-O2", "-ffp-contract=off", "-I", inc, "-I", os.path.join(ROOT, "include"), src, "-o", exe],
                    check=True, capture_output=True, text=True)
     r = subprocess.run([exe], capture_output=True, text=True, timeout=300)
     assert r.returncode == 0, r.stdout + r.stderr
