@@ -20,6 +20,7 @@
 // problem p owns split tiles [split_begin_p, split_begin_p + (m_pad/64 +
 // n_pad/64) * (k_pad/64)), first the A tiles (rows i, columns j), then the
 // B^T tiles (rows k, columns j).
+#include "fixed_point.cuh"
 #include "launch.cuh"
 #include "modular.cuh"
 
@@ -53,34 +54,6 @@ __device__ __forceinline__ int split_find(const SplitArgs& a, int tile, const Pr
   }
   *P = &a.table[lo];
   return lo;
-}
-
-// Smallest e with m < 2^e for the magnitude whose bit pattern is mb (0 if m = 0).
-__device__ __forceinline__ int exponent_from_maxbits(uint64_t mb) {
-  if (mb == 0) return 0;
-  const int E = static_cast<int>(mb >> 52);
-  if (E == 0) return (64 - __clzll(static_cast<long long>(mb))) - 1074;  // subnormal maximum
-  return E - 1022;
-}
-
-// D = round-half-even(v * 2^(width-e)) computed on the bit pattern of v
-// (width = 8s - 1 for s digits, beta for the modular form), without
-// branches.  Requires |v| < 2^e (true for every entry of a row/column scaled
-// by its max), so a left shift never exceeds width bits.  A right shift by
-// n >= 1 rounds half to even as floor((x + 2^(n-1) - 1 + lsb) / 2^n) with
-// lsb the lowest kept bit of x; for n >= 54 (x < 2^53 <= 2^(n-1)) that is 0.
-__device__ __forceinline__ int64_t fixed_point(uint64_t bits, int e, int width, bool* nonfinite) {
-  const bool neg = (bits >> 63) != 0;
-  const int E = static_cast<int>((bits >> 52) & 0x7FF);
-  const uint64_t frac = bits & ((1ull << 52) - 1);
-  const uint64_t x = E != 0 ? (frac | (1ull << 52)) : frac;  // subnormal: v = frac 2^(1 - 1075)
-  const int sh = ((E != 0 ? E : 1) - 1075) - e + width;
-  const int n = min(max(-sh, 1), 63);
-  const uint64_t right = (x + ((1ull << (n - 1)) - 1) + ((x >> n) & 1)) >> n;
-  uint64_t D = sh >= 0 ? (x << min(sh, 63)) : right;
-  if (E == 0x7FF) *nonfinite = true;
-  D = E == 0x7FF ? 0ull : D;
-  return neg ? -static_cast<int64_t>(D) : static_cast<int64_t>(D);
 }
 
 // Digits d_1..d_s of D (balanced base 256: d_2..d_s in [-128, 127]).  With
