@@ -1,10 +1,13 @@
-"""The recombination's final rounding (round_i128_scaled, recombine.cuh):
+"""The recombinations' 128-bit helpers (recombine.cuh), compiled for the host.
+The final rounding (round_i128_scaled):
 one round-to-nearest-even of a two's-complement 128-bit integer to FP64, then
 the power-of-two scaling, compiled for the host and compared bit for bit with
 the oracle's model of the same step (or_int128_to_double, the C conversion of
 a 128-bit integer, then ldexp) on ties, carries into the next binade, every
 bit length, signs, and results that overflow, land in the subnormal range or
-underflow to zero."""
+underflow to zero.  The digit form's level combination (i128_shift_add and
+its 64-bit variant: T = T 2^shift + v, two's complement modulo 2^128) against
+Python integers for random level sequences."""
 import math
 import os
 import random
@@ -65,7 +68,7 @@ def test_round_i128_scaled_matches_the_oracle(tmp_path):
         u = v & ((1 << 128) - 1)
         hi = u >> 64
         hi = hi - (1 << 64) if hi >= 1 << 63 else hi
-        lines.append(f"{hi} {u & ((1 << 64) - 1)} {scale}")
+        lines.append(f"R {hi} {u & ((1 << 64) - 1)} {scale}")
     r = subprocess.run([exe], input="\n".join(lines) + "\n", capture_output=True, text=True, timeout=120, check=True)
     got = [int(x) for x in r.stdout.split()]
     assert len(got) == len(cs)
@@ -79,3 +82,34 @@ def test_round_i128_scaled_matches_the_oracle(tmp_path):
         if g != wbits:
             bad.append((v, scale, g, wbits))
     assert not bad, bad[:5]
+
+
+def test_shift_add_matches_python_integers(tmp_path):
+    gxx, inc = shutil.which("g++"), cuda_include()
+    if not gxx or not inc:
+        pytest.skip("needs g++ and the CUDA headers")
+    exe = str(tmp_path / "round_i128_check")
+    subprocess.run([gxx, "-std=c++17", "-O2", "-I", inc, os.path.join(ROOT, "tests", "round_i128_check.cpp"), "-o", exe],
+                   check=True, capture_output=True, text=True)
+    rnd = random.Random(11)
+    seqs = []
+    for t in range(3000):
+        wide = t % 2 == 1
+        count = rnd.randrange(1, 9)
+        seq = []
+        for i in range(count):
+            shift = 0 if i == 0 else 8 * rnd.randrange(0, 8)  # level gaps of 0..7 bytes
+            bound = 1 << (62 if wide else 31)
+            v = rnd.choice([rnd.randrange(-bound, bound), bound - 1, -bound, 0, -1])
+            seq.append((shift, v))
+        seqs.append(("B" if wide else "A", seq))
+    lines = [f"{op} {len(seq)} " + " ".join(f"{sh} {v}" for sh, v in seq) for op, seq in seqs]
+    r = subprocess.run([exe], input="\n".join(lines) + "\n", capture_output=True, text=True, timeout=60, check=True)
+    got = [tuple(int(x) for x in line.split()) for line in r.stdout.strip().splitlines()]
+    assert len(got) == len(seqs)
+    for (op, seq), (hi, lo) in zip(seqs, got):
+        T = 0
+        for sh, v in seq:
+            T = (T << sh) + v
+        T &= (1 << 128) - 1
+        assert ((hi & ((1 << 64) - 1)) << 64) | lo == T, (op, seq)
