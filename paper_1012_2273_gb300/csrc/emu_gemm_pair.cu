@@ -32,6 +32,7 @@
 #include "launch.cuh"
 #include "modular.cuh"
 #include "recombine.cuh"
+#include "tile_index.cuh"
 
 namespace mmk {
 
@@ -149,13 +150,6 @@ __device__ __forceinline__ void tc_commit_pair(uint64_t* bar, uint16_t mask) {
           smem_u32(bar)),
       "h"(mask)
       : "memory");
-}
-
-// Index of 128-row tile (tm, tn) in the tile order of emu_tile_coords.
-__device__ __forceinline__ int emu_tile_index(int tm, int tn, int tiles_m, int tiles_n) {
-  const int band = tn / EMU_BAND;
-  const int width = (tiles_n - band * EMU_BAND) < EMU_BAND ? (tiles_n - band * EMU_BAND) : EMU_BAND;
-  return band * tiles_m * EMU_BAND + tm * width + (tn - band * EMU_BAND);
 }
 
 struct PairUnit {

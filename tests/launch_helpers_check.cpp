@@ -9,10 +9,14 @@
 //     pairs, and emu_tile_slots counts them.
 //  4. mod_group_range cuts the moduli [0, k) into G contiguous ranges that
 //     start at residue-pair boundaries (even indices), covering every modulus.
+//  5. emu_tile_index (tile_index.cuh) inverts emu_tile_coords, and the two
+//     128-row halves of every 256-row pair tile (the CTA-pair kernel's units)
+//     land on distinct tiles that cover the grid once.
 #include <cstdio>
 #include <vector>
 
 #include "../paper_1012_2273_gb300/csrc/launch.cuh"
+#include "../paper_1012_2273_gb300/csrc/tile_index.cuh"
 
 using namespace mmk;
 
@@ -93,6 +97,27 @@ int main() {
         next = p1;
       }
       CHECK(next == k, "moduli ranges cover k=%d G=%d", k, G);
+    }
+  // 5. tile index and pair tiles
+  for (int tm = 1; tm <= 40; ++tm)
+    for (int tn = 1; tn <= 40; ++tn) {
+      for (int t = 0; t < tm * tn; ++t) {
+        int a, b;
+        emu_tile_coords(t, tm, tn, &a, &b);
+        CHECK(emu_tile_index(a, b, tm, tn) == t, "index of tile %d in %dx%d", t, tm, tn);
+      }
+      if (tm % 2) continue;
+      std::vector<int> seen(tm * tn, 0);
+      for (int pt = 0; pt < (tm / 2) * tn; ++pt) {
+        int a, b;
+        emu_tile_coords(pt, tm / 2, tn, &a, &b);
+        for (int r = 0; r < 2; ++r) {
+          const int t = emu_tile_index(2 * a + r, b, tm, tn);
+          CHECK(t >= 0 && t < tm * tn, "pair tile half out of range");
+          if (t >= 0 && t < tm * tn) ++seen[t];
+        }
+      }
+      for (int i = 0; i < tm * tn; ++i) CHECK(seen[i] == 1, "pair tiles of %dx%d: tile %d hit %d times", tm, tn, i, seen[i]);
     }
   std::printf("%s (%d failures)\n", failures ? "FAILED" : "ok", failures);
   return failures ? 1 : 0;
