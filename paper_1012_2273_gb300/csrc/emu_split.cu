@@ -56,41 +56,13 @@ __device__ __forceinline__ int split_find(const SplitArgs& a, int tile, const Pr
   return lo;
 }
 
-// Digits d_1..d_s of D (balanced base 256: d_2..d_s in [-128, 127]).  With
-// M = sum_{k=0}^{s-2} 128 * 256^k, the low s-1 bytes of D + M are exactly
-// d_t + 128 (t = s, s-1, ..., 2, least significant first) and (D + M) >> 8(s-1)
-// is d_1: adding 128 to every lower position turns the balanced digits into
-// plain bytes.  D + M itself can exceed the int64 range at s = 8, so M is
-// added to the low 8(s-1) bits alone and their carry is added to d_1.  Each digit d
-// becomes a float exactly (0x4B400000 | (d + 128) is 2^23 + 2^22 + d + 128)
-// and pairs of them become bf16x2 with one round-to-nearest conversion, exact
-// for integers of at most 8 significant bits.  Output: packed bf16x2 words,
-// word w of element q holds digit planes (2w, 2w+1).
+// Pairs of exact digit floats become bf16x2 with one round-to-nearest
+// conversion, exact for integers of at most 8 significant bits.  Output:
+// packed bf16x2 words, word w of element q holds digit planes (2w, 2w+1).
 __device__ __forceinline__ uint32_t bf16x2_of_digits(float lo, float hi) {
   uint32_t r;
   asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
   return r;
-}
-
-__device__ __forceinline__ float digit_float(uint32_t biased_byte) {
-  return __uint_as_float(0x4B400000u | biased_byte) - 12583040.0f;  // (2^23 + 2^22 + 128) -> d
-}
-
-template <int S>
-__device__ __forceinline__ void digits_of(int64_t D, float (&out)[S]) {
-  constexpr int SH = 8 * (S - 1);
-  constexpr uint64_t M = (S > 1) ? (0x8080808080808080ull >> (8 * (9 - S))) : 0ull;
-  constexpr uint64_t MASK = (S > 1) ? ((1ull << SH) - 1) : 0ull;
-  // Lower digits from the low SH bits only: (D mod 2^SH) + M < 2^(SH+1), no overflow.
-  const uint64_t low = (static_cast<uint64_t>(D) & MASK) + M;
-#pragma unroll
-  for (int t = S - 1; t >= 1; --t) {
-    const uint32_t b = static_cast<uint32_t>(low >> (8 * (S - 1 - t))) & 255u;
-    out[t] = digit_float(b);
-  }
-  // d_1 = floor(D / 2^SH) plus the carry out of the low part; |d_1| <= 128.
-  const int d1 = static_cast<int>(D >> SH) + static_cast<int>(low >> SH);
-  out[0] = static_cast<float>(d1);
 }
 
 // Row maxima of |op(A)| and column maxima of |op(B)| (as bit patterns; for

@@ -1,9 +1,11 @@
 // fixed_point.cuh -- the fixed-point reading of an FP64 value shared by both
-// emulation forms' split (emu_split.cu), compiled for the host as well so that
-// tests can check it against the oracle without a GPU.
+// emulation forms' split (emu_split.cu) and the digit form's balanced base-256
+// digits, compiled for the host as well so that tests can check them against
+// the oracle without a GPU.
 #pragma once
 
 #include <cstdint>
+#include <cstring>
 
 namespace mmk {
 
@@ -42,6 +44,46 @@ __host__ __device__ __forceinline__ int64_t fixed_point(uint64_t bits, int e, in
   if (E == 0x7FF) *nonfinite = true;
   D = E == 0x7FF ? 0ull : D;
   return neg ? -static_cast<int64_t>(D) : static_cast<int64_t>(D);
+}
+
+__host__ __device__ __forceinline__ float float_of_bits(uint32_t b) {
+#ifdef __CUDA_ARCH__
+  return __uint_as_float(b);
+#else
+  float f;
+  std::memcpy(&f, &b, sizeof f);
+  return f;
+#endif
+}
+
+// Digit d from its biased byte d + 128, exactly: 0x4B400000 | (d + 128) is the
+// float 2^23 + 2^22 + d + 128.
+__host__ __device__ __forceinline__ float digit_float(uint32_t biased_byte) {
+  return float_of_bits(0x4B400000u | biased_byte) - 12583040.0f;  // (2^23 + 2^22 + 128) -> d
+}
+
+// Digits d_1..d_s of D (balanced base 256: d_2..d_s in [-128, 127]) as exact
+// floats.  With M = sum_{k=0}^{s-2} 128 * 256^k, the low s-1 bytes of D + M
+// are exactly d_t + 128 (t = s, s-1, ..., 2, least significant first) and
+// (D + M) >> 8(s-1) is d_1: adding 128 to every lower position turns the
+// balanced digits into plain bytes.  D + M itself can exceed the int64 range
+// at s = 8, so M is added to the low 8(s-1) bits alone and their carry is
+// added to d_1.
+template <int S>
+__host__ __device__ __forceinline__ void digits_of(int64_t D, float (&out)[S]) {
+  constexpr int SH = 8 * (S - 1);
+  constexpr uint64_t M = (S > 1) ? (0x8080808080808080ull >> (8 * (9 - S))) : 0ull;
+  constexpr uint64_t MASK = (S > 1) ? ((1ull << SH) - 1) : 0ull;
+  // Lower digits from the low SH bits only: (D mod 2^SH) + M < 2^(SH+1), no overflow.
+  const uint64_t low = (static_cast<uint64_t>(D) & MASK) + M;
+#pragma unroll
+  for (int t = S - 1; t >= 1; --t) {
+    const uint32_t b = static_cast<uint32_t>(low >> (8 * (S - 1 - t))) & 255u;
+    out[t] = digit_float(b);
+  }
+  // d_1 = floor(D / 2^SH) plus the carry out of the low part; |d_1| <= 128.
+  const int d1 = static_cast<int>(D >> SH) + static_cast<int>(low >> SH);
+  out[0] = static_cast<float>(d1);
 }
 
 }  // namespace mmk

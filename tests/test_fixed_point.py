@@ -2,7 +2,9 @@
 both emulation forms), compiled for the host: D = round-half-even(v 2^(width -
 e)) against the oracle's or_fix on exact ties at every shift, subnormal
 inputs, values just below 2^e, widths 1..62 and both signs; the exponent of a
-maximum (frexp's exponent) against Python's; and the non-finite flag."""
+maximum (frexp's exponent) against Python's; the non-finite flag; and the
+digit form's balanced base-256 digits against the oracle's at every digit
+count, up to the largest fixed-point values."""
 import math
 import os
 import random
@@ -62,7 +64,7 @@ def test_fixed_point_matches_the_oracle(tmp_path):
     cs = cases()
     special = [(math.inf, 1, 40), (-math.inf, 1, 40), (math.nan, 1, 40)]
     maxima = [abs(v) for v, _, _ in cs[:400]]
-    lines = [f"{bits_of(v)} {e} {w}" for v, e, w in cs + special] + [f"{bits_of(m)} 0 0" for m in maxima]
+    lines = [f"F {bits_of(v)} {e} {w}" for v, e, w in cs + special] + [f"F {bits_of(m)} 0 0" for m in maxima]
     r = subprocess.run([exe], input="\n".join(lines) + "\n", capture_output=True, text=True, timeout=120, check=True)
     got = [tuple(int(x) for x in line.split()) for line in r.stdout.strip().splitlines()]
     assert len(got) == len(lines)
@@ -70,3 +72,27 @@ def test_fixed_point_matches_the_oracle(tmp_path):
     assert not bad, bad[:5]
     assert all(g == (0, 1) for g in got[len(cs):len(cs) + 3])  # Inf, NaN: D = 0, flagged
     assert [g[0] for g in got[len(cs) + 3:]] == [e_of(m) for m in maxima]
+
+
+def test_digits_match_the_oracle(tmp_path):
+    gxx, inc = shutil.which("g++"), cuda_include()
+    if not gxx or not inc:
+        pytest.skip("needs g++ and the CUDA headers")
+    exe = str(tmp_path / "fixed_point_check")
+    subprocess.run([gxx, "-std=c++17", "-O2", "-I", inc, os.path.join(ROOT, "tests", "fixed_point_check.cpp"), "-o", exe],
+                   check=True, capture_output=True, text=True)
+    rnd = random.Random(13)
+    cases = []
+    for s in range(1, 9):
+        top = 1 << (8 * s - 1)  # |D| <= 2^(8s-1), as the split's fixed point gives
+        if s == 8:
+            top -= 1 << 10  # s = 8: |x| <= 1 - 2^-53 keeps |D| <= 2^63 - 2^10
+        vals = [0, 1, -1, top, -top, top - 1, -(top - 1), 127, 128, -128, -129, 255, 256]
+        vals += [rnd.randrange(-top, top + 1) for _ in range(2000)]
+        cases += [(d, s) for d in vals if -top <= d <= top]
+    lines = [f"G {d} {s}" for d, s in cases]
+    r = subprocess.run([exe], input="\n".join(lines) + "\n", capture_output=True, text=True, timeout=60, check=True)
+    got = [[int(x) for x in line.split()] for line in r.stdout.strip().splitlines()]
+    assert len(got) == len(cases)
+    bad = [(d, s, g) for (d, s), g in zip(cases, got) if g != oracle.emu_digits_of(d, s)]
+    assert not bad, bad[:5]
