@@ -231,12 +231,16 @@ mm_status mm_split(mm_handle h, int N, const double* M, int by_columns, int slic
  * counterpart; this is an interface convenience of the library.
  *   - Its only scratch (one 64-bit maximum per row or column) is a static
  *     device array of MM_SPLIT_NOALLOC_MAX_N entries (512 KiB) that exists on
- *     every GPU that loads the library, until the process exits.
+ *     every GPU that loads the library, until the process exits or the
+ *     device is reset.
  *   - N > MM_SPLIT_NOALLOC_MAX_N returns MM_ERR_UNSUPPORTED; bad arguments
  *     return MM_ERR_INVALID; nothing is launched in either case.
- *   - The first call on each device looks up the array's device address
- *     (cudaGetSymbolAddress) with that device current; make that first call
- *     before any stream capture.
+ *   - Every call made while `stream` is not being captured looks up the
+ *     array's device address (cudaGetSymbolAddress) with the calling device
+ *     current, so a device reset, which may move the array, is picked up by
+ *     the next such call.  A call made during stream capture reuses the
+ *     address found by the last uncaptured call on that device: make one
+ *     call on the device before capturing (MM_ERR_CUDA otherwise).
  *   - Every call uses the same array: calls that overlap on the GPU (on
  *     different streams, or from several threads) race and corrupt each
  *     other's exponents.  Serialise them on one stream.

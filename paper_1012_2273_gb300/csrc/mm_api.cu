@@ -1134,16 +1134,22 @@ mm_status mm_gemm_host(mm_handle h, int N, const double* A_host, const double* B
   double* dB = h->e2e + stride;
   double* dC = h->e2e + 2 * stride;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  MM_CUDA(h, cudaMemcpyAsync(dA, A_host, elems * sizeof(double), cudaMemcpyHostToDevice, s));
-  MM_CUDA(h, cudaMemcpyAsync(dB, B_host, elems * sizeof(double), cudaMemcpyHostToDevice, s));
-  mm_status st = mm_gemm(h, N, dA, dB, dC, stream);
-  if (st != MM_OK) {
-    cudaStreamSynchronize(s);  // the uploads read the caller's buffers: let them finish
+  // Once a copy is enqueued it may still be reading or writing the caller's
+  // host buffers: every way out from here waits for the stream first.
+  auto drain = [&](mm_status st) {
+    cudaStreamSynchronize(s);
     cudaGetLastError();
     return st;
-  }
-  MM_CUDA(h, cudaMemcpyAsync(C_host, dC, elems * sizeof(double), cudaMemcpyDeviceToHost, s));
-  MM_CUDA(h, cudaStreamSynchronize(s));
+  };
+  cudaError_t e = cudaMemcpyAsync(dA, A_host, elems * sizeof(double), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dB, B_host, elems * sizeof(double), cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return drain(cuda_fail(h, e, "upload of A or B"));
+  const mm_status st = mm_gemm(h, N, dA, dB, dC, stream);
+  if (st != MM_OK) return drain(st);
+  e = cudaMemcpyAsync(C_host, dC, elems * sizeof(double), cudaMemcpyDeviceToHost, s);
+  if (e != cudaSuccess) return drain(cuda_fail(h, e, "download of C"));
+  e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return drain(cuda_fail(h, e, "cudaStreamSynchronize"));
   return MM_OK;
 }
 

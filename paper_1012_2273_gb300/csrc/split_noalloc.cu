@@ -13,9 +13,13 @@
 // library's module is loaded on a device and keeps until the process exits.
 //
 // The host cannot use the array's name as a device address (in host code the
-// symbol is only a host-side stand-in), so the first call on each device looks
-// the address up with cudaGetSymbolAddress, with that device current, and
-// caches it; later calls on that device reuse it.
+// symbol is only a host-side stand-in), so every call made outside stream
+// capture looks the address up with cudaGetSymbolAddress, with the calling
+// device current (the runtime answers from its own table), and records it
+// for that device.  A device reset unloads the module and may place the
+// array elsewhere; the next uncaptured call then finds the new address.  A
+// call made while its stream is being captured cannot look anything up, so
+// it reuses the address recorded by the last uncaptured call on the device.
 #include <mutex>
 
 #include "launch.cuh"
@@ -32,19 +36,25 @@ constexpr int kMaxDevices = 64;
 std::mutex g_addr_mutex;
 unsigned long long* g_addr[kMaxDevices] = {};
 
-// Device address of g_split_maxbits on the current device (looked up once per device).
-cudaError_t scratch_address(unsigned long long** out) {
+// Device address of g_split_maxbits on the current device: looked up afresh
+// unless `stream` is capturing, in which case the last address recorded for
+// the device is used (cudaErrorNotReady if there is none yet).
+cudaError_t scratch_address(cudaStream_t stream, unsigned long long** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  e = cudaStreamIsCapturing(stream, &cap);
+  if (e != cudaSuccess) return e;
   std::lock_guard<std::mutex> lock(g_addr_mutex);
-  if (!g_addr[dev]) {
+  if (cap == cudaStreamCaptureStatusNone) {
     void* p = nullptr;
     e = cudaGetSymbolAddress(&p, g_split_maxbits);
     if (e != cudaSuccess) return e;
     g_addr[dev] = static_cast<unsigned long long*>(p);
   }
+  if (!g_addr[dev]) return cudaErrorNotReady;
   *out = g_addr[dev];
   return cudaSuccess;
 }
@@ -59,11 +69,11 @@ extern "C" mm_status mm_split_noalloc(int N, const double* M, int by_columns, in
     return MM_ERR_INVALID;
   if (N > MM_SPLIT_NOALLOC_MAX_N || slices < 1 || slices > 8) return MM_ERR_UNSUPPORTED;
   unsigned long long* maxbits = nullptr;
-  if (scratch_address(&maxbits) != cudaSuccess) {
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (scratch_address(s, &maxbits) != cudaSuccess) {
     cudaGetLastError();
     return MM_ERR_CUDA;
   }
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
   // The maxima are built with atomicMax, so they must start at zero; the
   // previous call's values are still in the array.
   if (cudaMemsetAsync(maxbits, 0, sizeof(unsigned long long) * N, s) != cudaSuccess) {
