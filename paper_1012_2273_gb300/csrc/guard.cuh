@@ -1,0 +1,94 @@
+// guard.cuh -- the accuracy certificate of the emulated forms, shared by the
+// split, the slice-product kernel and the host planner, and compiled for the
+// host as well so that tests can check it against exact rational arithmetic.
+//
+// The product being guaranteed is Alg. 1's c_ik = sum_j a_ij b_jk (Sec. 3.1).
+// An emulated form computes, with a' = a 2^-e_i and b' = b 2^-f_k in (-1, 1)
+// and D = RNE(v' 2^w) their w-bit fixed-point integers,
+//     c^ = RN( sum_j D_A D_B  [minus the digit pairs the digit form drops] ) 2^(e_i + f_k - 2w).
+// With R = sum_j |a'_ij| |b'_jk| = (|A||B|)_ik 2^-(e_i + f_k) and |D - v' 2^w| <= 1/2,
+//     |c^ 2^-(e_i + f_k) - sum_j a' b'| <= u R + (1 + u) E',
+//     E' = 2^(-w-1) (SA_i + SB_k) + n 2^(-2w-2) + n kappa,
+// where SA_i = sum_j |a'_ij|, SB_k = sum_j |b'_jk|, n is the inner dimension,
+// u = 2^-53 and kappa bounds, per term, the digit pairs of weight t + u >= s + 2
+// that the digit form leaves out (0 for the modular form).  The result is
+// therefore within gamma_n (|A||B|)_ik of the exact product -- the bound the
+// recursive sum of Alg. 1 itself obeys -- whenever
+//     (1 + u) E' <= (n - 1) u R.                                     (*)
+// R is bounded below by 2^-14 S with S = sum_j M_A M_B, M = floor-ish(|v'| 2^7)
+// in [0, 127] (the "magnitude plane", multiplied exactly on the tensor cores
+// like any other plane); SA_i and SB_k are bounded above by integer sums of
+// ceil-ish(|v'| 2^24).  Scaling (*) by 2^(w + 25) gives the test
+//     (SA24_i + SB24_k) + K1 <= K2 S,
+//     K1 = n 2^(23 - w) + n kappa 2^(w + 25),   K2 = (n - 1) 2^(w - 42) / (1 + u),
+// evaluated in FP32 with margins that make it sufficient (see cert_ok).  An
+// element that fails it is recomputed in native FP64 afterwards.  A zero row
+// of op(A) or column of op(B) gives an exact zero in every form and is exempt.
+#pragma once
+
+#include <cmath>
+#include <cstdint>
+
+namespace mmk {
+
+// Lower bound of |v'| 2^7 from the fixed-point integer D of width w (|v' 2^w -
+// D| <= 1/2): floor((|D| - 1/2) 2^(7-w)) for |D| >= 1, else 0; in [0, 127]
+// because |D| <= 2^w.
+__host__ __device__ __forceinline__ uint32_t mag7_of(int64_t D, int w) {
+  const uint64_t a = D < 0 ? 0ull - static_cast<uint64_t>(D) : static_cast<uint64_t>(D);
+  if (a == 0) return 0u;
+  const uint64_t t = 2 * a - 1;  // (|D| - 1/2) 2^1
+  return static_cast<uint32_t>(w >= 6 ? t >> (w - 6) : t << (6 - w));
+}
+
+// Upper bound of |v'| 2^24 from D (|v'| 2^w <= |D| + 1/2): ceil((2|D| + 1)
+// 2^(23-w)); 0 when v itself is zero (then D = 0 and v' = 0).
+__host__ __device__ __forceinline__ uint64_t sum24_of(int64_t D, int w, bool v_nonzero) {
+  if (!v_nonzero) return 0ull;
+  const uint64_t a = D < 0 ? 0ull - static_cast<uint64_t>(D) : static_cast<uint64_t>(D);
+  const uint64_t t = 2 * a + 1;
+  if (w >= 23) {
+    const int sh = w - 23;
+    return (t >> sh) + ((t & ((1ull << sh) - 1)) != 0 ? 1ull : 0ull);
+  }
+  return t << (23 - w);
+}
+
+// The certificate test for one element: true when (*) holds for sure.  sa, sb
+// are the row and column sums of sum24_of, S the exact magnitude product,
+// k1 >= K1 and k2 <= K2 (1 - 2^-20) the constants of cert_constants.  Each
+// side is rounded at most twice by FP32 (relative error 2^-24 each), which
+// the 2^-20 margin in k2 absorbs, so the FP32 comparison implies the exact one.
+__host__ __device__ __forceinline__ bool cert_ok(uint64_t sa, uint64_t sb, uint32_t S, float k1, float k2) {
+  if (sa == 0 || sb == 0) return true;  // zero row or column: exact zero
+  const float lhs = static_cast<float>(sa + sb) + k1;
+  const float rhs = k2 * static_cast<float>(S);
+  return lhs <= rhs;
+}
+
+// kappa of the digit form with s digits: the digit pairs (t, u), 1 <= t, u <= s,
+// of level L = t + u >= s + 2 are left out; each |d_t d_u| <= 2^14 and weighs
+// 2^(2 - 8L) once scaled by 2^-2w (w = 8s - 1), with 2s + 1 - L pairs per level.
+inline double digit_kappa(int s) {
+  double k = 0.0;
+  for (int L = s + 2; L <= 2 * s; ++L) k += (2.0 * s + 1.0 - L) * std::ldexp(1.0, 16 - 8 * L);
+  return k;
+}
+
+// Host side: K1 rounded up and K2 (1 - 2^-20) rounded down to FP32, for inner
+// dimension n, fixed-point width w and kappa (0 for the modular form).
+// (The FP64 evaluation's own few roundings, relative 2^-53 each, are covered
+// by the extra factors 1 +- 2^-40.)
+inline void cert_constants(int n, int w, double kappa, float* k1, float* k2) {
+  const double K1 = (n * std::ldexp(1.0, 23 - w) + n * kappa * std::ldexp(1.0, w + 25)) * (1.0 + std::ldexp(1.0, -40));
+  const double K2 = (n - 1) * std::ldexp(1.0, w - 42) / (1.0 + std::ldexp(1.0, -53)) * (1.0 - std::ldexp(1.0, -20)) *
+                    (1.0 - std::ldexp(1.0, -40));
+  float a = static_cast<float>(K1);
+  if (static_cast<double>(a) < K1) a = std::nextafter(a, INFINITY);
+  float b = static_cast<float>(K2);
+  if (static_cast<double>(b) > K2) b = std::nextafter(b, 0.0f);
+  *k1 = a;
+  *k2 = b;
+}
+
+}  // namespace mmk
