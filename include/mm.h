@@ -81,6 +81,7 @@ typedef enum {
 /* Flags of mm_config.flags. */
 #define MM_FLAG_NO_GRAPH 1u /* grouped calls launch directly instead of replaying a CUDA graph */
 #define MM_FLAG_PROFILE 2u  /* bracket every kernel with CUDA events (implies MM_FLAG_NO_GRAPH) */
+#define MM_FLAG_NO_GUARD 4u /* emulated forms skip the accuracy certificate (see mm_guard_read) */
 
 typedef struct {
   mm_mode mode;          /* default MM_AUTO */
@@ -165,6 +166,33 @@ mm_status mm_status_get(mm_handle h, void* stream);
 /* Message of the last failed call on this handle (never NULL). */
 const char* mm_last_error(mm_handle h);
 
+/* Accuracy certificate of the emulated forms.  The product guaranteed is
+ * Alg. 1's c(i,k) (Sec. 3.1); the guarantee is that every element is within
+ * gamma_K (|A||B|)(i,k) of the exact product, gamma_K = K u / (1 - K u),
+ * u = 2^-53, K the inner dimension -- the bound the paper's own recursive sum
+ * obeys -- so that any two such results differ by at most 2 gamma_K |A||B|.
+ * Unless the handle has MM_FLAG_NO_GUARD, every emulated launch also
+ *   - writes one more plane per operand: the magnitude digits
+ *     M = floor-ish(|v| 2^(7 - e)) in [0, 127] of every entry,
+ *   - multiplies the two magnitude planes exactly on the tensor cores
+ *     (S = sum_j M_A M_B, so (|A||B|)(i,k) >= S 2^(e_i + f_k - 14)),
+ *   - tests for each element a bound of its own error (fixed-point rounding
+ *     of both operands, the digit pairs the digit form leaves out, the final
+ *     rounding) against gamma_K times that lower bound, and
+ *   - recomputes every element that fails in native FP64 (fused
+ *     multiply-adds, within gamma_K |A||B|); when more than a quarter of a
+ *     problem's elements fail, the whole problem is recomputed natively.
+ * Zero rows of A and columns of B are exact in every form and never fail.
+ * On typical inputs nothing fails (uniform entries) or a few elements in
+ * 10^4 (entries of magnitude 2^U(-20,20)); inputs whose rows mix magnitudes
+ * far apart fail more and cost more.  Results in the subnormal range are not
+ * covered (nor is the paper's loop there).
+ * mm_guard_read synchronises `stream` and returns how many elements
+ * (*elements) and whole problems (*problems, their elements included in
+ * *elements) were recomputed natively since the last read, then clears the
+ * counts.  Either pointer may be NULL. */
+mm_status mm_guard_read(mm_handle h, void* stream, long long* elements, long long* problems);
+
 /* Form and slice count the handle would use for an N x N problem (after
  * AUTO): form 0 = native FP64, 1 = digit emulation (slices = digits s),
  * 2 = modular emulation (slices = moduli k). */
@@ -184,7 +212,7 @@ mm_status mm_modular_params(int k, int N, int* beta, int* moduli);
  * in milliseconds, by kernel kind (events recorded on the call's stream):
  *   out_ms[0] scale and split (including zeroing of the row/column maxima)
  *   out_ms[1] slice products with fused recombination
- *   out_ms[2] native FP64 kernel
+ *   out_ms[2] native FP64 kernels (including the certificate's recomputation)
  *   out_ms[3] recombination run as its own pass (small problems, mm_recombine)
  * and launches[0..3] the number of kernel launches of each kind (may be
  * NULL).  Synchronises on the recorded events.  MM_ERR_INVALID without the flag. */

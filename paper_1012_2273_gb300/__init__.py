@@ -26,6 +26,7 @@ AUTO = 3
 EMU_MODULAR = 4
 FLAG_NO_GRAPH = 1
 FLAG_PROFILE = 2
+FLAG_NO_GUARD = 4
 
 STATUS_NAMES = {
     0: "MM_OK", 1: "MM_ERR_INVALID", 2: "MM_ERR_CUDA", 3: "MM_ERR_NOMEM",
@@ -54,7 +55,7 @@ class _Config(ctypes.Structure):
 
 SYMBOLS = ("mm_create", "mm_destroy", "mm_gemm", "mm_gemm_grouped", "mm_gemm_ex", "mm_gemm_grouped_ex",
            "mm_gemm_host", "mm_gemm_grouped_host",
-           "mm_status_get",
+           "mm_status_get", "mm_guard_read",
            "mm_last_error", "mm_plan", "mm_profile_read", "mm_probe_fp64_peak", "mm_selftest_wait", "mm_split",
            "mm_split_noalloc",
            "mm_level_sums", "mm_recombine", "mm_modular_params")
@@ -89,6 +90,7 @@ def lib(build_if_needed: bool = True) -> ctypes.CDLL:
             L.mm_gemm_grouped_host.argtypes = [vp, ci, ctypes.POINTER(ci), ctypes.POINTER(vp), ctypes.POINTER(vp),
                                                ctypes.POINTER(vp), vp]
             L.mm_status_get.argtypes = [vp, vp]
+            L.mm_guard_read.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]
             L.mm_last_error.argtypes = [vp]
             L.mm_last_error.restype = ctypes.c_char_p
             L.mm_plan.argtypes = [vp, ci, ctypes.POINTER(ci), ctypes.POINTER(ci)]
@@ -325,6 +327,13 @@ class Handle:
     def check(self, stream=None):
         """Synchronises and raises MMError for any device-side error."""
         self._raise(self._lib.mm_status_get(self._h, _stream_ptr(stream)))
+
+    def guard_read(self, stream=None) -> tuple[int, int]:
+        """mm_guard_read: (elements, whole problems) the accuracy certificate
+        sent to native FP64 since the last read (synchronises)."""
+        e, p = ctypes.c_longlong(), ctypes.c_longlong()
+        self._raise(self._lib.mm_guard_read(self._h, _stream_ptr(stream), ctypes.byref(e), ctypes.byref(p)))
+        return e.value, p.value
 
     def profile(self) -> dict:
         """Per-kernel-kind device time (ms) and launch counts of the last call (MM_FLAG_PROFILE)."""

@@ -8,7 +8,11 @@ k in 13..16, each at tile widths 128 and 256 (pair groups chosen
 automatically), at one representative size, and keeps the fastest plan whose
 result stays close to native FP64 -- at the representative size and at the
 bucket's smallest size -- on two input classes: uniform [-1, 1) and log-uniform
-magnitudes 2^U(-20,20).  "Close" means
+magnitudes 2^U(-20,20).  The handles run with the accuracy certificate on (the
+library's default), so a plan's time is the slower of its two input classes,
+native recomputation of the elements its certificate cannot vouch for
+included: a plan too narrow for log-uniform inputs pays for it there.  "Close"
+means
 max |C_plan - C_native| / (|A||B|) <= N 2^-53 / 2; the native result is itself
 within gamma_N |A||B| of the exact product, so an accepted plan is within
 (N/2 + N + small) 2^-53 |A||B| < 2 N 2^-53 |A||B|, the library's accuracy
@@ -103,7 +107,9 @@ def tune(buckets=BUCKETS, slices=(6, 7, 8), moduli=(13, 14, 15, 16), widths=(128
                 worst = max(worst, d / (size * U / 2))
             h.check()
             ok = worst <= 1.0
-            ms = _time_ms(lambda: h.gemm(classes[0][0], classes[0][1]), flush, reps)
+            # both input classes at the representative size (classes[0:2])
+            ms = max(_time_ms(lambda c=c: h.gemm(c[0], c[1]), flush, reps) for c in classes[:2])
+            h.guard_read()
             h.close()
             log(f"N={n:5d} {form} {'k' if form == 'modular' else 's'}={s} bn={bn} {ms:.3f} ms  "
                 f"max dev / allowance {worst:.3g} ({'ok' if ok else 'too far'})")

@@ -47,6 +47,20 @@ struct Problem {
   int defer;           // 1: slots go to the per-tile buffer and a separate pass recombines them
   long long slot_base; // int32 offset of this problem's tile 0 in the per-tile slot buffer (groups > 1)
   int8_t slot_level[64];  // level L of each segment slot of a tile, in slot order (nslots <= 64)
+  // Accuracy certificate (guard.cuh); guard = 0: off.  With it on, the split
+  // writes one more plane (index s: the magnitude digits of |v'|) and the
+  // row/column sums below, every tile gets one more work unit (group index
+  // `groups`) that multiplies the two magnitude planes and tests each
+  // element, and the guard kernel recomputes the failures in native FP64.
+  int guard;
+  float cert_k1, cert_k2;       // constants of cert_ok for this problem
+  unsigned long long* a_sum;    // [m] sums of sum24_of over each row of op(A) (zero at launch)
+  unsigned long long* b_sum;    // [n] sums over each column of op(B) (zero at launch)
+  int* guard_count;             // elements that failed the certificate (zero at launch)
+  int* guard_total;             // the same, summed over the problems of the launch (zero at launch)
+  int2* guard_list;             // their (row, column), the first guard_limit of them
+  int guard_limit;              // more failures than this: the whole problem is redone natively
+  int guard_tile_begin;         // first 64 x 64 tile of this problem in the guard kernel's grid
 };
 
 // Device status word.  0 = fine; otherwise the first mm_status recorded.

@@ -47,6 +47,7 @@
 // MM_ERR_TIMEOUT, lets its copies and MMAs finish, frees TMEM and returns.
 #include <cstdio>
 
+#include "guard.cuh"
 #include "launch.cuh"
 #include "modular.cuh"
 #include "recombine.cuh"
@@ -82,6 +83,7 @@ struct UnitRef {
   int tile_local;  // tile within the problem
   int g;           // pair group
   int G;           // pair groups of this problem
+  bool cert;       // the tile's certificate unit (g == G): the magnitude planes' product
 };
 
 __device__ __forceinline__ UnitRef emu_unit(const EmuArgs& a, int u) {
@@ -101,7 +103,20 @@ __device__ __forceinline__ UnitRef emu_unit(const EmuArgs& a, int u) {
     r.g = e.z;
     r.G = r.P->groups;
   }
+  r.cert = r.g >= r.G;
   return r;
+}
+
+// Products of a unit: [p0, p1) of the tile's digit pairs or moduli, or the
+// single magnitude product of a certificate unit.
+template <bool kMod>
+__device__ __forceinline__ void unit_products(const UnitRef& U, int* p0, int* p1) {
+  if (U.cert) {
+    *p0 = 0;
+    *p1 = 1;
+  } else {
+    unit_group_range<kMod>(U.P->s, U.G, U.g, p0, p1);
+  }
 }
 
 // Slots written by other CTAs are read from L2 (bypassing L1, which is not
@@ -263,10 +278,12 @@ __global__ void __launch_bounds__(EM_THREADS, 1)
         const CUtensorMap* ma = args.units ? &args.maps[2 * U.pi] : &mapA;
         const CUtensorMap* mb = args.units ? &args.maps[2 * U.pi + 1] : &mapB;
         int p0, p1;
-        unit_group_range<kMod>(P->s, U.G, U.g, &p0, &p1);
+        unit_products<kMod>(U, &p0, &p1);
         for (int p = p0; p < p1 && ok; ++p) {
           int ta = p, tb = p;  // modular form: residue planes p of A and of B^T
-          if (!kMod) {         // digit pair (t, L - t): planes t - 1 and L - t - 1
+          if (U.cert) {        // the magnitude planes follow the s digit or residue planes
+            ta = tb = P->s;
+          } else if (!kMod) {  // digit pair (t, L - t): planes t - 1 and L - t - 1
             int L, t;
             emu_pair_of(p, &L, &t);
             ta = t - 1;
@@ -328,10 +345,10 @@ __global__ void __launch_bounds__(EM_THREADS, 1)
         const UnitRef U = emu_unit(args, u);
         const int KB = U.P->k_pad / EM_BK;
         int p0, p1;
-        unit_group_range<kMod>(U.P->s, U.G, U.g, &p0, &p1);
+        unit_products<kMod>(U, &p0, &p1);
         int L, t0;
         for (int p = p0; p < p1 && ok;) {
-          const int np = kMod ? 1 : emu_segment(p, p1, maxp, &L, &t0);
+          const int np = (kMod || U.cert) ? 1 : emu_segment(p, p1, maxp, &L, &t0);
           p += np;
           const int nb = np * KB;
           for (int c0 = 0; c0 < nb && ok; c0 += EM_CHUNK_KB) {
@@ -431,10 +448,10 @@ __global__ void __launch_bounds__(EM_THREADS, 1)
       const int row = m0 + r_in_tile;
       const int s = P->s;
       int p0, p1;
-      unit_group_range<kMod>(s, U.G, U.g, &p0, &p1);
+      unit_products<kMod>(U, &p0, &p1);
       // slot of this unit's first segment, and where the tile's slots live
       int slot = kMod ? p0 : 0;
-      if (!kMod) {
+      if (!kMod && !U.cert) {
         for (int g = 0; g < U.g; ++g) {
           int q0, q1;
           emu_group_range(s, U.G, g, &q0, &q1);
@@ -447,7 +464,7 @@ __global__ void __launch_bounds__(EM_THREADS, 1)
       int L, t0;
       uint32_t pend[kMod ? HALF / 4 : 1] = {};  // modular form: residues of a pair's first modulus
       for (int p = p0; p < p1 && ok; ++slot) {
-        const int np = kMod ? 1 : emu_segment(p, p1, maxp, &L, &t0);
+        const int np = (kMod || U.cert) ? 1 : emu_segment(p, p1, maxp, &L, &t0);
         p += np;
         const int nb = np * KB;
         const int nchunks = (nb + EM_CHUNK_KB - 1) / EM_CHUNK_KB;
@@ -481,6 +498,45 @@ __global__ void __launch_bounds__(EM_THREADS, 1)
         }
         if (!ok) break;
         const uint32_t bias = static_cast<uint32_t>(nchunks) * EM_MAGIC;
+        if (U.cert) {
+          // Certificate (guard.cuh): S = sum_j M_A M_B, exact, bounds (|A||B|)
+          // from below; elements whose error bound it cannot certify are
+          // listed for the guard kernel.  Lanes are rows, so a warp tests 32
+          // rows of one column at a time; nothing is written when all pass.
+          const bool in_row = row < P->m;
+          const unsigned long long sa = in_row ? P->a_sum[row] : 0ull;
+          const float k1 = P->cert_k1, k2 = P->cert_k2;
+          uint32_t bad[HALF / 32];
+#pragma unroll
+          for (int w = 0; w < HALF / 32; ++w) bad[w] = 0u;
+#pragma unroll
+          for (int i = 0; i < HALF; ++i) {
+            const int col = n0 + h * HALF + i;
+            if (in_row && col < n && !cert_ok(sa, P->b_sum[col], acc[i] - bias, k1, k2)) bad[i / 32] |= 1u << (i % 32);
+          }
+          uint32_t any = 0u;
+#pragma unroll
+          for (int w = 0; w < HALF / 32; ++w) any |= bad[w];
+          if (__any_sync(0xffffffffu, any != 0u)) {
+#pragma unroll
+            for (int w = 0; w < HALF / 32; ++w) {
+              for (int b = 0; b < 32; ++b) {
+                const bool mine = (bad[w] >> b) & 1u;
+                const unsigned m = __ballot_sync(0xffffffffu, mine);
+                if (!m) continue;
+                int base = 0;
+                if (lane == 0) {
+                  base = atomicAdd(P->guard_count, __popc(m));
+                  atomicAdd(P->guard_total, __popc(m));
+                }
+                base = __shfl_sync(0xffffffffu, base, 0);
+                const int at = base + __popc(m & ((1u << lane) - 1u));
+                if (mine && at < P->guard_limit) P->guard_list[at] = make_int2(row, n0 + h * HALF + 32 * w + b);
+              }
+            }
+          }
+          continue;
+        }
         if (kMod) {
           // The exact sum S = sum_j r_a r_b of modulus m_j (|S| <= n 2^14 <=
           // 2^30) becomes r = S mod m in [0, m): x = S + (a multiple of m, at
@@ -568,7 +624,7 @@ __global__ void __launch_bounds__(EM_THREADS, 1)
         }
       }
       // deferred (and every modular problem): recombined by a separate pass
-      if (!ok || args.levels_out || P->defer || kMod) continue;
+      if (!ok || args.levels_out || P->defer || kMod || U.cert) continue;
       bool mine = true;
       if (U.G > 1) {
         // Each epilogue warp owns the same 32 x BN/2 region in every unit of

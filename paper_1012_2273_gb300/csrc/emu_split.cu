@@ -21,6 +21,7 @@
 // n_pad/64) * (k_pad/64)), first the A tiles (rows i, columns j), then the
 // B^T tiles (rows k, columns j).
 #include "fixed_point.cuh"
+#include "guard.cuh"
 #include "launch.cuh"
 #include "modular.cuh"
 
@@ -63,6 +64,28 @@ __device__ __forceinline__ uint32_t bf16x2_of_digits(float lo, float hi) {
   uint32_t r;
   asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
   return r;
+}
+
+// Accuracy certificate (guard.cuh), for the 8 fixed-point values D of one
+// output row that a thread has in hand: writes their magnitude digits (lower
+// bounds of |v'| 2^7, exact small integers in bf16) to the magnitude plane as
+// one 16-byte vector and adds the upper bounds of |v'| 2^24 to the row's sum
+// in shared memory.  (A zero row's sum is discarded later, from its maximum.)
+__device__ __forceinline__ void guard_item(const long long (&D)[8], int width, uint16_t* mag_out,
+                                           unsigned long long* row_sum, bool lead, unsigned pair_mask) {
+  uint32_t w[4];
+  unsigned long long sum = 0;
+#pragma unroll
+  for (int p = 0; p < 4; ++p) {
+    w[p] = bf16x2_of_digits(static_cast<float>(mag7_of(D[2 * p], width)),
+                            static_cast<float>(mag7_of(D[2 * p + 1], width)));
+    sum += sum24_of(D[2 * p], width, true) + sum24_of(D[2 * p + 1], width, true);
+  }
+  *reinterpret_cast<uint4*>(mag_out) = make_uint4(w[0], w[1], w[2], w[3]);
+  // the lanes of `pair_mask` hold the same row: add theirs first
+  for (int o = 1; o < 32; o <<= 1)
+    if (pair_mask & (1u << o)) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+  if (lead) atomicAdd(row_sum, sum);
 }
 
 // Row maxima of |op(A)| and column maxima of |op(B)| (as bit patterns; for
@@ -194,13 +217,20 @@ __global__ void __launch_bounds__(SP_THREADS) absmax_kernel(const __grid_constan
 // columns), 8 items per row; one 16-byte vector per digit plane.
 template <int S>
 __device__ __forceinline__ void write_digit_planes(const long long (&Ds)[SP_TILE][SP_TILE + 1], uint16_t* dst,
-                                                   int r0, int c0, int k_pad, size_t plane) {
+                                                   int r0, int c0, int k_pad, size_t plane, bool guard,
+                                                   unsigned long long* gsum) {
   for (int item = threadIdx.x; item < SP_TILE * (SP_TILE / 8); item += SP_THREADS) {
     const int r = item >> 3, cg = item & 7;
+    uint16_t* out = dst + static_cast<size_t>(r0 + r) * k_pad + c0 + cg * 8;
+    if (guard) {  // uniform over the CTA; the 8 lanes of a row are consecutive
+      long long D[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) D[q] = Ds[r][cg * 8 + q];
+      guard_item(D, 8 * S - 1, out + S * plane, &gsum[r], cg == 0, 0x7u);
+    }
     float dig[8][S];
 #pragma unroll
     for (int q = 0; q < 8; ++q) digits_of<S>(Ds[r][cg * 8 + q], dig[q]);
-    uint16_t* out = dst + static_cast<size_t>(r0 + r) * k_pad + c0 + cg * 8;
 #pragma unroll
     for (int t = 0; t < S; ++t) {
       uint4 v;
@@ -295,7 +325,8 @@ __device__ __forceinline__ void write_residue_item(const long long (&D)[8], uint
 // plane fill one 32-byte sector.
 template <int K, int LIMBS>
 __device__ __forceinline__ void residue_tile_from_smem(const long long (&Ds)[SP_TILE][SP_TILE + 1], uint16_t* dst,
-                                                       int r0, int c0, int k_pad, size_t plane) {
+                                                       int r0, int c0, int k_pad, size_t plane, int width, bool guard,
+                                                       unsigned long long* gsum) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll 1
   for (int pass = 0; pass < 2; ++pass) {
@@ -303,23 +334,28 @@ __device__ __forceinline__ void residue_tile_from_smem(const long long (&Ds)[SP_
     long long D[8];
 #pragma unroll
     for (int q = 0; q < 8; ++q) D[q] = Ds[r][8 * cg + q];
-    write_residue_item<K, LIMBS>(D, dst + static_cast<size_t>(r0 + r) * k_pad + c0 + 8 * cg, plane);
+    uint16_t* out = dst + static_cast<size_t>(r0 + r) * k_pad + c0 + 8 * cg;
+    // a row's 8 items: 2 lanes of each of 4 warps (uniform branch)
+    if (guard) guard_item(D, width, out + K * plane, &gsum[r], (lane & 1) == 0, 0x1u);
+    write_residue_item<K, LIMBS>(D, out, plane);
   }
 }
 
 // Writes the K residue planes of one 64 x 64 tile from its D in Ds.
 template <int K>
 __device__ __forceinline__ void residue_tile(int r0, int c0, int width, const long long (&Ds)[SP_TILE][SP_TILE + 1],
-                                             uint16_t* dst, int k_pad, size_t plane) {
+                                             uint16_t* dst, int k_pad, size_t plane, bool guard,
+                                             unsigned long long* gsum) {
   if (width <= 55)  // |D| <= 2^55 < 2^56: four 14-bit limbs
-    residue_tile_from_smem<K, 4>(Ds, dst, r0, c0, k_pad, plane);
+    residue_tile_from_smem<K, 4>(Ds, dst, r0, c0, k_pad, plane, width, guard, gsum);
   else
-    residue_tile_from_smem<K, 5>(Ds, dst, r0, c0, k_pad, plane);
+    residue_tile_from_smem<K, 5>(Ds, dst, r0, c0, k_pad, plane, width, guard, gsum);
 }
 
 __global__ void __launch_bounds__(SP_THREADS, 3) split_kernel(const __grid_constant__ SplitArgs args) {
   __shared__ long long Ds[SP_TILE][SP_TILE + 1];
   __shared__ int ex_s[SP_TILE];  // exponent of each output row (A: row i; B^T: column k of B)
+  __shared__ unsigned long long gsum[SP_TILE];  // certificate: this tile's part of each output row's sum
   __shared__ int any_nonfinite;
   const Problem* P;
   const int pi = split_find(args, blockIdx.x, &P);
@@ -348,10 +384,12 @@ __global__ void __launch_bounds__(SP_THREADS, 3) split_kernel(const __grid_const
   // the stored matrix's rows are the output rows (A, transposed B) or the
   // k index (B, transposed A)
   const bool rows_out = is_a ? !P->ta : P->tb;
+  const bool guard = P->guard != 0;
   if (threadIdx.x < SP_TILE) {
     const int er = r0 + threadIdx.x;
     const int e = er < out_rows ? exponent_from_maxbits(maxbits[er]) : 0;
     ex_s[threadIdx.x] = e;
+    gsum[threadIdx.x] = 0ull;
     if (exps && c0 == 0 && er < out_rows) exps[er] = e;
   }
   __syncthreads();
@@ -387,28 +425,35 @@ __global__ void __launch_bounds__(SP_THREADS, 3) split_kernel(const __grid_const
   if (beta > 0) {
     switch (S) {
 #define MM_RESIDUE_CASE(K) \
-  case K: residue_tile<K>(r0, c0, width, Ds, dst, P->k_pad, plane); break;
+  case K: residue_tile<K>(r0, c0, width, Ds, dst, P->k_pad, plane, guard, gsum); break;
       MM_RESIDUE_CASE(2) MM_RESIDUE_CASE(3) MM_RESIDUE_CASE(4) MM_RESIDUE_CASE(5) MM_RESIDUE_CASE(6)
       MM_RESIDUE_CASE(7) MM_RESIDUE_CASE(8) MM_RESIDUE_CASE(9) MM_RESIDUE_CASE(10) MM_RESIDUE_CASE(11)
       MM_RESIDUE_CASE(12) MM_RESIDUE_CASE(13) MM_RESIDUE_CASE(14) MM_RESIDUE_CASE(15)
-      default: residue_tile<16>(r0, c0, width, Ds, dst, P->k_pad, plane); break;
+      default: residue_tile<16>(r0, c0, width, Ds, dst, P->k_pad, plane, guard, gsum); break;
 #undef MM_RESIDUE_CASE
     }
   } else {
     switch (S) {
-      case 1: write_digit_planes<1>(Ds, dst, r0, c0, P->k_pad, plane); break;
-      case 2: write_digit_planes<2>(Ds, dst, r0, c0, P->k_pad, plane); break;
-      case 3: write_digit_planes<3>(Ds, dst, r0, c0, P->k_pad, plane); break;
-      case 4: write_digit_planes<4>(Ds, dst, r0, c0, P->k_pad, plane); break;
-      case 5: write_digit_planes<5>(Ds, dst, r0, c0, P->k_pad, plane); break;
-      case 6: write_digit_planes<6>(Ds, dst, r0, c0, P->k_pad, plane); break;
-      case 7: write_digit_planes<7>(Ds, dst, r0, c0, P->k_pad, plane); break;
-      default: write_digit_planes<8>(Ds, dst, r0, c0, P->k_pad, plane); break;
+      case 1: write_digit_planes<1>(Ds, dst, r0, c0, P->k_pad, plane, guard, gsum); break;
+      case 2: write_digit_planes<2>(Ds, dst, r0, c0, P->k_pad, plane, guard, gsum); break;
+      case 3: write_digit_planes<3>(Ds, dst, r0, c0, P->k_pad, plane, guard, gsum); break;
+      case 4: write_digit_planes<4>(Ds, dst, r0, c0, P->k_pad, plane, guard, gsum); break;
+      case 5: write_digit_planes<5>(Ds, dst, r0, c0, P->k_pad, plane, guard, gsum); break;
+      case 6: write_digit_planes<6>(Ds, dst, r0, c0, P->k_pad, plane, guard, gsum); break;
+      case 7: write_digit_planes<7>(Ds, dst, r0, c0, P->k_pad, plane, guard, gsum); break;
+      default: write_digit_planes<8>(Ds, dst, r0, c0, P->k_pad, plane, guard, gsum); break;
     }
   }
   if (nonfinite) any_nonfinite = 1;
   __syncthreads();
   if (threadIdx.x == 0 && any_nonfinite) set_status(args.status, MM_ERR_NONFINITE);
+  if (guard && threadIdx.x < SP_TILE) {
+    // the tile's part of each output row's certificate sum; a zero row keeps
+    // sum 0, which exempts it (its products are exactly zero in every form)
+    const int er = r0 + threadIdx.x;
+    unsigned long long* sums = is_a ? P->a_sum : P->b_sum;
+    if (er < out_rows && maxbits[er] != 0 && gsum[threadIdx.x] != 0) atomicAdd(&sums[er], gsum[threadIdx.x]);
+  }
 }
 
 // Host side -------------------------------------------------------------------

@@ -120,6 +120,12 @@ cudaError_t native_small_launch(const Problem* table, const Problem* single, int
 void native_fill_tiles(Problem& p);
 cudaError_t native_launch(const Problem* table, const Problem* single, int count, int total_tiles,
                           cudaStream_t stream);
+// 64 x 64 tiles of the guard kernel for one problem, and the guard kernel
+// itself over the problems of one emulated launch (guard_tile_begin set by
+// the caller, total_tiles their sum)
+int guard_tiles(const Problem& p);
+cudaError_t guard_launch(const Problem* table, const Problem* single, int count, int total_tiles, int num_sms,
+                         unsigned long long* stats, cudaStream_t stream);
 
 // emu_split.cu
 int split_tiles(const Problem& p);

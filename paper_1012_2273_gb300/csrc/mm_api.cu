@@ -19,6 +19,7 @@
 #include <tuple>
 #include <vector>
 
+#include "guard.cuh"
 #include "launch.cuh"
 #include "modular.cuh"
 
@@ -155,6 +156,12 @@ mm_status cuda_fail(mm_handle h, cudaError_t e, const char* what) {
 
 bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
+// The handle's certificate counters (64-bit, at byte 32 of its 128-byte
+// status block): [0] elements recomputed natively, [1] problems recomputed whole.
+unsigned long long* guard_stats(mm_handle h) { return reinterpret_cast<unsigned long long*>(h->d_status + 8); }
+
+bool guard_on(mm_handle h) { return (h->cfg.flags & MM_FLAG_NO_GUARD) == 0; }
+
 // ---- MM_FLAG_PROFILE --------------------------------------------------------
 enum { KIND_SPLIT = 0, KIND_SLICE_GEMM = 1, KIND_NATIVE = 2, KIND_RECOMBINE = 3 };
 
@@ -183,21 +190,21 @@ void prof_end(mm_handle h, cudaStream_t s, long mark) {
 }
 
 // Built-in plan table (a tune file overrides it): the output of
-// paper_1012_2273_gb300.autotune on a GB300 (tune/gb300.tune).  Below N = 256
-// native FP64 is as fast and is the only form that meets the componentwise
-// bound for wide-range inputs at the smallest N; from there the modular form
-// with the fewest moduli that stay within the bound on uniform and
-// log-uniform (2^+-20) inputs: 16 up to N = 511, 15 up to 1535, 14 up to
-// 6143, 13 above (the bound 2 N 2^-53 |A||B| grows with N).  Beyond the
-// modular form's size limit the digit form with 6 digits.
+// paper_1012_2273_gb300.autotune on a GB300 (tune/gb300.tune), which times
+// every plan with the accuracy certificate on, on uniform and log-uniform
+// (2^+-20) inputs, and keeps the fastest whose slower class stays within the
+// bound.  Below N = 256 native FP64 is as fast; from there the modular form
+// with the fewest moduli that rarely send elements back to native FP64: 16 up
+// to N = 511, 15 up to 1999, 14 above (13 moduli, narrower still, would
+// recompute nearly every log-uniform element natively).  Beyond the modular
+// form's size limit the digit form with 6 digits.
 void default_tune(mm_handle h) {
   h->tune.clear();
   h->tune.push_back({255, Plan{0, 7, 256, 0}});
   h->tune.push_back({511, Plan{2, 16, 128, 0}});
   h->tune.push_back({767, Plan{2, 15, 128, 0}});
-  h->tune.push_back({1535, Plan{2, 15, 256, 0}});
-  h->tune.push_back({6143, Plan{2, 14, 256, 0}});
-  h->tune.push_back({65535, Plan{2, 13, 256, 0}});
+  h->tune.push_back({1999, Plan{2, 15, 256, 0}});
+  h->tune.push_back({65535, Plan{2, 14, 256, 0}});
   h->tune.push_back({1 << 30, Plan{1, 6, 256, 0}});
 }
 
@@ -309,6 +316,8 @@ struct EmuGroup {
   int groups = 0;       // forced pair groups per tile (0 = automatic)
   int bn = 256, grid = 1, max_pairs = 1;
   bool pair = false;    // modular form at bn 256: CTA pairs (cta_group::2) on 256 x 256 tiles
+  bool guard = false;   // accuracy certificate and native recomputation of what it cannot vouch for
+  int guard_tiles = 0;  // blocks of the guard kernel's whole-problem part
   std::vector<Problem> ps;
   std::vector<int> max_off;        // offset of problem p in the maxbits arrays
   std::vector<CUtensorMap> maps;   // 2 per problem
@@ -317,6 +326,8 @@ struct EmuGroup {
   long long tilebuf_elems = 0;
   // byte offsets inside the group's region of the arena
   size_t amax = 0, bmax = 0, scratch = 0, tilebuf = 0, counters = 0, bytes = 0;
+  size_t gsum = 0;        // certificate sums and failure counts
+  size_t zero_bytes = 0;  // bytes from amax on that every launch zeroes first
   char* base = nullptr;
 };
 
@@ -361,7 +372,9 @@ bool pair_mma_enabled() {
 mm_status layout_group(mm_handle h, EmuGroup& g, char* base) {
   Arena ar;
   g.total_tiles = g.total_split = g.total_absmax = g.max_rows = 0;
-  g.pair = g.form == 2 && g.bn == 256 && pair_mma_enabled() && h->num_sms >= 2;
+  // (the CTA-pair kernel has no certificate unit: it runs only unguarded)
+  g.pair = g.form == 2 && g.bn == 256 && pair_mma_enabled() && h->num_sms >= 2 && !g.guard;
+  g.guard_tiles = 0;
   int maxk = 0;
   g.max_off.assign(g.ps.size(), 0);
   for (Problem& p : g.ps) maxk = std::max(maxk, p.k);
@@ -382,8 +395,22 @@ mm_status layout_group(mm_handle h, EmuGroup& g, char* base) {
     g.total_absmax += mmk::absmax_blocks(p);
     p.beta = g.form == 2 ? mmk::mod_beta(p.s, p.k) : 0;  // the bound involves the inner dimension
     work += static_cast<long long>(p.tiles_m) * p.tiles_n * mmk::problem_pairs(p) * (p.k_pad / 64);
-    const size_t a_sl = ar.take(static_cast<size_t>(p.s) * p.m_pad * p.k_pad * 2);
-    const size_t b_sl = ar.take(static_cast<size_t>(p.s) * p.n_pad * p.k_pad * 2);
+    // planes: s digits or residues, plus the magnitude plane when guarded
+    const int planes = p.s + (g.guard ? 1 : 0);
+    p.guard = g.guard ? 1 : 0;
+    const size_t a_sl = ar.take(static_cast<size_t>(planes) * p.m_pad * p.k_pad * 2);
+    const size_t b_sl = ar.take(static_cast<size_t>(planes) * p.n_pad * p.k_pad * 2);
+    if (g.guard) {
+      // certificate constants for inner dimension k and width w (guard.cuh)
+      const int w = g.form == 2 ? p.beta : 8 * p.s - 1;
+      mmk::cert_constants(p.k, w, g.form == 2 ? 0.0 : mmk::digit_kappa(p.s), &p.cert_k1, &p.cert_k2);
+      // more failures than a quarter of the outputs: recompute the whole
+      // problem natively (then the per-element list would cost about as much)
+      p.guard_limit = static_cast<int>(std::min<long long>(std::max<long long>(256, static_cast<long long>(p.m) * p.n / 4),
+                                                           1LL << 30));
+      p.guard_tile_begin = g.guard_tiles;
+      g.guard_tiles += mmk::guard_tiles(p);
+    }
     const size_t ae = ar.take(sizeof(int) * p.m);
     const size_t be = ar.take(sizeof(int) * p.n);
     if (base) {
@@ -443,6 +470,8 @@ mm_status layout_group(mm_handle h, EmuGroup& g, char* base) {
           const int cost = (p1 - p0) * kb;
           for (int t = 0; t < unit_tiles; ++t) g.units.push_back(make_int4(static_cast<int>(i), t, gi, cost));
         }
+        if (g.guard)  // the certificate unit of each tile: one product
+          for (int t = 0; t < unit_tiles; ++t) g.units.push_back(make_int4(static_cast<int>(i), t, G, kb));
       }
       continue;
     }
@@ -479,6 +508,8 @@ mm_status layout_group(mm_handle h, EmuGroup& g, char* base) {
         const int cost = (p1 - p0) * kb;
         for (int t = 0; t < tiles; ++t) g.units.push_back(make_int4(static_cast<int>(i), t, gi, cost));
       }
+      if (g.guard)
+        for (int t = 0; t < tiles; ++t) g.units.push_back(make_int4(static_cast<int>(i), t, G, kb));
     }
   }
   if (g.tabled) {
@@ -491,22 +522,53 @@ mm_status layout_group(mm_handle h, EmuGroup& g, char* base) {
     });
     g.total_units = static_cast<int>(g.units.size());
   } else {
-    g.total_units = g.ps[0].tiles_m * g.ps[0].tiles_n / (g.pair ? 2 : 1) * g.ps[0].groups;
+    g.total_units = g.ps[0].tiles_m * g.ps[0].tiles_n / (g.pair ? 2 : 1) * (g.ps[0].groups + (g.guard ? 1 : 0));
   }
   g.grid = g.pair ? 2 * emu_grid(h, std::min(g.total_units, h->num_sms / 2)) : emu_grid(h, g.total_units);
+  // Everything zeroed before a launch sits in one run (one memset): the
+  // row/column maxima, the tile and unit counters, and -- when guarded --
+  // per problem the certificate's row sums [m] and column sums [n], then the
+  // per-problem failure counts and their total.
   g.amax = ar.take(sizeof(uint64_t) * g.max_rows);
   g.bmax = ar.take(sizeof(uint64_t) * g.max_rows);
+  g.counters = ar.take(sizeof(int) * (8 * static_cast<size_t>(g.total_tiles) + 1));  // + unit counter
+  std::vector<size_t> sum_off(g.ps.size(), 0);
+  size_t counts_at = 0, gsum_len = 0;
+  if (g.guard) {
+    for (size_t i = 0; i < g.ps.size(); ++i) {
+      sum_off[i] = gsum_len;
+      gsum_len += sizeof(uint64_t) * (static_cast<size_t>(g.ps[i].m) + g.ps[i].n);
+    }
+    counts_at = gsum_len;
+    gsum_len += sizeof(int) * (g.ps.size() + 1);
+  }
+  g.gsum = ar.take(gsum_len);
+  g.zero_bytes = ar.off - g.amax;
   g.scratch = ar.take(static_cast<size_t>(g.grid) * g.scratch_slots * slot * sizeof(int32_t));
   g.tilebuf = ar.take(static_cast<size_t>(std::max<long long>(g.tilebuf_elems, 4)) * sizeof(int32_t));
-  g.counters = ar.take(sizeof(int) * (8 * static_cast<size_t>(g.total_tiles) + 1));  // + unit counter
+  if (g.guard) {
+    for (size_t i = 0; i < g.ps.size(); ++i) {
+      const size_t list_off = ar.take(sizeof(int2) * static_cast<size_t>(g.ps[i].guard_limit));
+      if (!base) continue;
+      Problem& p = g.ps[i];
+      char* gb = base + g.gsum;
+      int* counts = reinterpret_cast<int*>(gb + counts_at);
+      p.a_sum = reinterpret_cast<unsigned long long*>(gb + sum_off[i]);
+      p.b_sum = p.a_sum + p.m;
+      p.guard_count = counts + i;
+      p.guard_total = counts + g.ps.size();
+      p.guard_list = reinterpret_cast<int2*>(base + list_off);
+    }
+  }
   g.bytes = ar.off;
   g.base = base;
   if (base) {
     g.maps.resize(2 * g.ps.size());
     for (size_t i = 0; i < g.ps.size(); ++i) {
       const Problem& p = g.ps[i];
-      if (!make_plane_map(&g.maps[2 * i], p.a_slices, p.k_pad, static_cast<long>(p.s) * p.m_pad, 128) ||
-          !make_plane_map(&g.maps[2 * i + 1], p.b_slices, p.k_pad, static_cast<long>(p.s) * p.n_pad,
+      const long planes = p.s + (g.guard ? 1 : 0);
+      if (!make_plane_map(&g.maps[2 * i], p.a_slices, p.k_pad, planes * p.m_pad, 128) ||
+          !make_plane_map(&g.maps[2 * i + 1], p.b_slices, p.k_pad, planes * p.n_pad,
                           g.pair ? g.bn / 2 : g.bn))
         return fail(h, MM_ERR_CUDA, "cuTensorMapEncodeTiled failed");
     }
@@ -525,15 +587,14 @@ mm_status run_group(mm_handle h, const EmuGroup& g, const Problem* d_table, cons
   uint64_t* bmax = reinterpret_cast<uint64_t*>(g.base + g.bmax);
   const bool single = d_table == nullptr;
   const long m_split = prof_start(h, stream, KIND_SPLIT);
-  MM_CUDA(h, cudaMemsetAsync(amax, 0, sizeof(uint64_t) * g.max_rows, stream));
-  MM_CUDA(h, cudaMemsetAsync(bmax, 0, sizeof(uint64_t) * g.max_rows, stream));
+  // maxima, counters and certificate sums: one run of the workspace
+  MM_CUDA(h, cudaMemsetAsync(amax, 0, g.zero_bytes, stream));
   MM_CUDA(h, mmk::split_launch(d_table, single ? &g.ps[0] : nullptr, static_cast<int>(g.ps.size()), g.total_split,
                                g.total_absmax,
                                amax, bmax, single ? nullptr : d_max_off, h->d_status, stream));
   prof_end(h, stream, m_split);
   // Per-region completion counters (pair groups > 1) and the unit counter.
   int* counters = reinterpret_cast<int*>(g.base + g.counters);
-  MM_CUDA(h, cudaMemsetAsync(counters, 0, sizeof(int) * (8 * static_cast<size_t>(g.total_tiles) + 1), stream));
   mmk::EmuArgs a{};
   a.table = d_table;
   if (single) a.single = g.ps[0];
@@ -564,14 +625,22 @@ mm_status run_group(mm_handle h, const EmuGroup& g, const Problem* d_table, cons
     const long m_rec = prof_start(h, stream, KIND_RECOMBINE);
     MM_CUDA(h, mmk::mod_recombine_launch(g.bn, a, 0, g.total_tiles, stream));
     prof_end(h, stream, m_rec);
-    return MM_OK;
+  } else {
+    bool any_deferred = false;
+    for (const Problem& p : g.ps) any_deferred |= p.defer != 0;
+    if (any_deferred) {
+      const long m_rec = prof_start(h, stream, KIND_RECOMBINE);
+      MM_CUDA(h, mmk::slots_recombine_launch(g.bn, a, g.total_tiles, stream));
+      prof_end(h, stream, m_rec);
+    }
   }
-  bool any_deferred = false;
-  for (const Problem& p : g.ps) any_deferred |= p.defer != 0;
-  if (any_deferred) {
-    const long m_rec = prof_start(h, stream, KIND_RECOMBINE);
-    MM_CUDA(h, mmk::slots_recombine_launch(g.bn, a, g.total_tiles, stream));
-    prof_end(h, stream, m_rec);
+  if (g.guard) {
+    // native FP64 for what the certificate could not vouch for (returns at
+    // once when every element passed)
+    const long m_g = prof_start(h, stream, KIND_NATIVE);
+    MM_CUDA(h, mmk::guard_launch(d_table, single ? &g.ps[0] : nullptr, static_cast<int>(g.ps.size()), g.guard_tiles,
+                                 h->num_sms, guard_stats(h), stream));
+    prof_end(h, stream, m_g);
   }
   return MM_OK;
 }
@@ -597,6 +666,7 @@ mm_status emu_single(mm_handle h, const Problem& p, int form, int s, int bn, int
   if (st != MM_OK) return st;
   EmuGroup g;
   g.form = form;
+  g.guard = guard_on(h);
   g.bn = bn;
   g.groups = groups;
   g.ps.push_back(p);
@@ -726,6 +796,7 @@ mm_status grouped_impl(mm_handle h, const std::vector<Problem>& probs, cudaStrea
       auto make = [&](size_t end) {
         EmuGroup t;
         t.tabled = true;
+        t.guard = guard_on(h);
         t.form = std::get<0>(kv.first);
         t.bn = std::get<1>(kv.first);
         t.groups = std::get<2>(kv.first);
@@ -1084,6 +1155,17 @@ mm_status mm_status_get(mm_handle h, void* stream) {
                                              : st == MM_ERR_NONFINITE ? "non-finite input to the emulation"
                                                                       : "device error");
   }
+  return MM_OK;
+}
+
+mm_status mm_guard_read(mm_handle h, void* stream, long long* elements, long long* problems) {
+  if (!h) return MM_ERR_INVALID;
+  MM_CUDA(h, cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
+  unsigned long long v[2] = {0, 0};
+  MM_CUDA(h, cudaMemcpy(v, guard_stats(h), sizeof(v), cudaMemcpyDeviceToHost));
+  MM_CUDA(h, cudaMemset(guard_stats(h), 0, sizeof(v)));
+  if (elements) *elements = static_cast<long long>(v[0]);
+  if (problems) *problems = static_cast<long long>(v[1]);
   return MM_OK;
 }
 

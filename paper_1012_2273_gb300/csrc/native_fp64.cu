@@ -48,14 +48,13 @@ __device__ __forceinline__ void dmma_16x8x4(double (&c)[4], double a0, double a1
       : "d"(a0), "d"(a1), "d"(b0));
 }
 
-// One 64 x 64 tile of C; TA / TB: the stored A / B is the transpose of op(A) / op(B).
+// The 64 x 64 tile of C at (m0, n0); TA / TB: the stored A / B is the
+// transpose of op(A) / op(B).
 template <bool ta, bool tb>
-__device__ __forceinline__ void native_tile(const Problem* P, int local, double (&As)[2][NT_BK][NT_LD],
+__device__ __forceinline__ void native_tile(const Problem* P, int m0, int n0, double (&As)[2][NT_BK][NT_LD],
                                             double (&Bs)[2][NT_BK][NT_LD]) {
   const int n = P->n, m = P->m, kdim = P->k;
   const size_t lda = P->lda, ldb = P->ldb, ldc = P->ldc;
-  const int m0 = (local / P->tiles_n) * NT_BM;
-  const int n0 = (local % P->tiles_n) * NT_BN;
   const double* __restrict__ A = P->A;
   const double* __restrict__ B = P->B;
   double* __restrict__ C = P->C;
@@ -144,6 +143,16 @@ __device__ __forceinline__ void native_tile(const Problem* P, int local, double 
     }
 }
 
+// One code path per storage order (uniform over the CTA).
+__device__ __forceinline__ void native_tile_any(const Problem* P, int m0, int n0, double (&As)[2][NT_BK][NT_LD],
+                                                double (&Bs)[2][NT_BK][NT_LD]) {
+  if (P->ta) {
+    if (P->tb) native_tile<true, true>(P, m0, n0, As, Bs); else native_tile<true, false>(P, m0, n0, As, Bs);
+  } else {
+    if (P->tb) native_tile<false, true>(P, m0, n0, As, Bs); else native_tile<false, false>(P, m0, n0, As, Bs);
+  }
+}
+
 __global__ void __launch_bounds__(NT_THREADS, 4) native_fp64_kernel(const __grid_constant__ NativeArgs args) {
   __shared__ __align__(16) double As[2][NT_BK][NT_LD];  // [k][m]
   __shared__ __align__(16) double Bs[2][NT_BK][NT_LD];  // [k][n]
@@ -151,12 +160,7 @@ __global__ void __launch_bounds__(NT_THREADS, 4) native_fp64_kernel(const __grid
   const Problem* P = args.table ? &args.table[find_problem(args.table, args.count, tile)] : &args.single;
   const int local = tile - P->tile_begin;
   if (P->n <= 0 || P->m <= 0 || local < 0 || local >= P->tiles_m * P->tiles_n) return;
-  // one code path per storage order (uniform over the CTA)
-  if (P->ta) {
-    if (P->tb) native_tile<true, true>(P, local, As, Bs); else native_tile<true, false>(P, local, As, Bs);
-  } else {
-    if (P->tb) native_tile<false, true>(P, local, As, Bs); else native_tile<false, false>(P, local, As, Bs);
-  }
+  native_tile_any(P, (local / P->tiles_n) * NT_BM, (local % P->tiles_n) * NT_BN, As, Bs);
 }
 
 // Small problems: one warp per 16 x 16 tile of C, so that N ~ 100 still spreads
@@ -215,6 +219,95 @@ __global__ void __launch_bounds__(32) native_fp64_small_kernel(const __grid_cons
   }
 }
 
+// ---------------------------------------------------------------------------
+// Guard kernel: after an emulated launch, recomputes in native FP64 what its
+// accuracy certificate (guard.cuh) could not vouch for.  Blocks [0,
+// total_tiles) are the 64 x 64 tiles of every guarded problem: a problem with
+// more failures than its guard_limit is recomputed whole, by the tiles above
+// (each within gamma_k |A||B| of the exact product).  The remaining blocks
+// recompute the listed elements of the other problems one warp each: lanes
+// take every 32nd term in increasing order with fused multiply-adds, then a
+// butterfly sum -- at most ceil(k/32) + 5 <= k roundings on any path for k >=
+// 6 (and for k < 6 at most 1 + ceil(log2 k) <= k, the idle lanes adding exact
+// zeros), so within gamma_k |A||B| as well.  When nothing failed (the usual
+// case) every block returns after one load.
+// ---------------------------------------------------------------------------
+struct GuardArgs {
+  const Problem* table;  // device table (grouped) or nullptr
+  Problem single;
+  int count;
+  int total_tiles;
+  unsigned long long* stats;  // [0] elements recomputed, [1] problems recomputed whole
+};
+
+__device__ __forceinline__ const Problem* guard_problem(const GuardArgs& a, int p) {
+  return a.table ? &a.table[p] : &a.single;
+}
+
+__global__ void __launch_bounds__(NT_THREADS, 4) guard_kernel(const __grid_constant__ GuardArgs args) {
+  __shared__ __align__(16) double As[2][NT_BK][NT_LD];
+  __shared__ __align__(16) double Bs[2][NT_BK][NT_LD];
+  __shared__ int active[NT_THREADS];
+  __shared__ int nactive;
+  const Problem* P0 = guard_problem(args, 0);
+  if (*reinterpret_cast<volatile int*>(P0->guard_total) == 0) return;  // shared by the launch's problems
+  if (static_cast<int>(blockIdx.x) < args.total_tiles) {
+    int lo = 0, hi = args.count - 1;  // problem owning this tile
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (guard_problem(args, mid)->guard_tile_begin <= static_cast<int>(blockIdx.x)) lo = mid; else hi = mid - 1;
+    }
+    const Problem* P = guard_problem(args, lo);
+    const int tn = (P->n + NT_BN - 1) / NT_BN, tm = (P->m + NT_BM - 1) / NT_BM;
+    const int local = blockIdx.x - P->guard_tile_begin;
+    if (!P->guard || local < 0 || local >= tm * tn || *P->guard_count <= P->guard_limit) return;
+    if (local == 0 && threadIdx.x == 0) {
+      atomicAdd(&args.stats[0], static_cast<unsigned long long>(P->m) * P->n);
+      atomicAdd(&args.stats[1], 1ull);
+    }
+    native_tile_any(P, (local / tn) * NT_BM, (local % tn) * NT_BN, As, Bs);
+    return;
+  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long long wid = static_cast<long long>(blockIdx.x - args.total_tiles) * (NT_THREADS / 32) + warp;
+  const long long nw = static_cast<long long>(gridDim.x - args.total_tiles) * (NT_THREADS / 32);
+  unsigned long long done = 0;
+  for (int base = 0; base < args.count; base += NT_THREADS) {
+    // this round's problems with listed elements, found in parallel
+    if (threadIdx.x == 0) nactive = 0;
+    __syncthreads();
+    const int p = base + threadIdx.x;
+    if (p < args.count) {
+      const Problem* P = guard_problem(args, p);
+      const int c = P->guard ? *P->guard_count : 0;
+      if (c > 0 && c <= P->guard_limit) active[atomicAdd(&nactive, 1)] = p;
+    }
+    __syncthreads();
+    for (int a = 0; a < nactive; ++a) {
+      const Problem* P = guard_problem(args, active[a]);
+      const int cnt = *P->guard_count;
+      const double* A = P->A;
+      const double* B = P->B;
+      const size_t lda = P->lda, ldb = P->ldb;
+      for (long long e = wid; e < cnt; e += nw) {
+        const int2 ik = P->guard_list[e];
+        double acc = 0.0;
+        for (int j = lane; j < P->k; j += 32) {
+          const double x = P->ta ? A[static_cast<size_t>(j) * lda + ik.x] : A[static_cast<size_t>(ik.x) * lda + j];
+          const double y = P->tb ? B[static_cast<size_t>(ik.y) * ldb + j] : B[static_cast<size_t>(j) * ldb + ik.y];
+          acc = fma(x, y, acc);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) P->C[static_cast<size_t>(ik.x) * P->ldc + ik.y] = acc;
+        ++done;
+      }
+    }
+    __syncthreads();
+  }
+  if (lane == 0 && done) atomicAdd(&args.stats[0], done);
+}
+
 // Host-side helpers --------------------------------------------------------
 
 // Problems below this size use the 16 x 16 kernel.
@@ -251,6 +344,27 @@ cudaError_t native_launch(const Problem* table, const Problem* single, int count
   if (single) args.single = *single;
   args.count = count;
   native_fp64_kernel<<<total_tiles, NT_THREADS, 0, stream>>>(args);
+  return cudaGetLastError();
+}
+
+}  // namespace mmk
+
+namespace mmk {
+
+int guard_tiles(const Problem& p) {
+  return p.m > 0 && p.n > 0 ? ((p.m + NT_BM - 1) / NT_BM) * ((p.n + NT_BN - 1) / NT_BN) : 0;
+}
+
+cudaError_t guard_launch(const Problem* table, const Problem* single, int count, int total_tiles, int num_sms,
+                         unsigned long long* stats, cudaStream_t stream) {
+  GuardArgs args{};
+  args.table = table;
+  if (single) args.single = *single;
+  args.count = count;
+  args.total_tiles = total_tiles;
+  args.stats = stats;
+  const int fix_blocks = 2 * num_sms;
+  guard_kernel<<<total_tiles + fix_blocks, NT_THREADS, 0, stream>>>(args);
   return cudaGetLastError();
 }
 

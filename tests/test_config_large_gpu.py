@@ -55,12 +55,13 @@ def test_grouped_64_loguniform_1000_to_16384_and_single_16384():
             Bs.append(torch.from_numpy(B).cuda())
         Cs = h.gemm_grouped(As, Bs)
         h.check()
+        replaced, _ = h.guard_read()  # the models describe the result only where nothing was replaced
         plans = {n: h.plan(n) for n in set(sizes)}
         order = sorted(range(len(sizes)), key=lambda i: -sizes[i])
         for rank, p in enumerate(order):
             C = Cs[p].cpu().numpy()
             A, B = host[p]
-            worst = max(worst, verify(A, B, C, plans[sizes[p]], rng, exact_rows=1 if rank < 2 else 0)
+            worst = max(worst, verify(A, B, C, plans[sizes[p]], rng, exact_rows=1 if rank < 2 and not replaced else 0)
                         / (2 * sizes[p] * U))
         del As, Bs, Cs, host
         torch.cuda.empty_cache()
@@ -69,5 +70,7 @@ def test_grouped_64_loguniform_1000_to_16384_and_single_16384():
         A, B = workload.pair("loguniform20", 16384, n)
         C = h.gemm(torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda())
         h.check()
-        worst = max(worst, verify(A, B, C.cpu().numpy(), h.plan(n), rng, exact_rows=1) / (2 * n * U))
+        replaced, _ = h.guard_read()
+        worst = max(worst, verify(A, B, C.cpu().numpy(), h.plan(n), rng, exact_rows=0 if replaced else 1)
+                    / (2 * n * U))
     assert worst <= 1.0

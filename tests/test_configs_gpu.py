@@ -3,7 +3,10 @@
 Full products are compared with the oracle where the oracle finishes in
 seconds; larger ones are checked on rows the oracle computes one by one and
 with Freivalds' test on the whole result.  Errors are componentwise,
-|C - C_ref| / (|A||B|), against the bound 2 N 2^-53.
+|C - C_ref| / (|A||B|), against the bound 2 N 2^-53.  The precision study
+reports each slice or moduli count twice: the raw emulation
+(MM_FLAG_NO_GUARD) and the library's default, where the accuracy certificate
+sends what it cannot vouch for to native FP64 (with the share it sent).
 """
 import json
 import os
@@ -76,12 +79,21 @@ def test_precision_per_slice_count_n2000():
         with mm.Handle("native") as h:
             C = host(h.gemm(dev(A), dev(B)))
         errs["native"] = float(np.max(np.abs(C[r] - ref) / absab))
+        guarded = {}
         for s in range(2, 9):
-            with mm.Handle("emulated", slices=s) as h:
+            with mm.Handle("emulated", slices=s, flags=mm.FLAG_NO_GUARD) as h:
                 C = host(h.gemm(dev(A), dev(B)))
                 h.check()
             errs[f"s={s}"] = float(np.max(np.abs(C[r] - ref) / absab))
+            with mm.Handle("emulated", slices=s) as h:
+                C = host(h.gemm(dev(A), dev(B)))
+                h.check()
+                replaced, _ = h.guard_read()
+            e = float(np.max(np.abs(C[r] - ref) / absab))
+            guarded[f"s={s}"] = {"error": e, "replaced_fraction": replaced / (n * n)}
+            assert e <= 2 * n * U  # the certificate holds whatever s is
         out["rows"][dist] = errs
+        out.setdefault("guarded", {})[dist] = guarded
         # More slices never make the result worse by more than rounding.
         seq = [errs[f"s={s}"] for s in range(2, 9)]
         assert all(b <= a * 1.01 + 2 * n * U for a, b in zip(seq, seq[1:])), seq
@@ -105,9 +117,16 @@ def test_precision_per_moduli_count_n2000():
         r = rows_of(n, 10)
         ref = oracle.gemm_rows(A, B, r)
         absab = np.abs(A[r]) @ np.abs(B)
-        errs = {}
+        errs, guarded = {}, {}
         for k in range(8, 17):
             with mm.Handle("modular", slices=k) as h:
+                Cg = host(h.gemm(dev(A), dev(B)))
+                h.check()
+                replaced, _ = h.guard_read()
+            e = float(np.max(np.abs(Cg[r] - ref) / absab))
+            guarded[f"k={k}"] = {"error": e, "replaced_fraction": replaced / (n * n)}
+            assert e <= 2 * n * U
+            with mm.Handle("modular", slices=k, flags=mm.FLAG_NO_GUARD) as h:
                 C = host(h.gemm(dev(A), dev(B)))
                 h.check()
             errs[f"k={k} beta={oracle.modular_beta(k, n)}"] = float(np.max(np.abs(C[r] - ref) / absab))
@@ -115,6 +134,7 @@ def test_precision_per_moduli_count_n2000():
                 np.testing.assert_array_equal(C[r[:2]].view(np.int64),
                                               oracle.fixed_gemm_rows(A, B, oracle.modular_beta(k, n), r[:2]).view(np.int64))
         out["rows"][dist] = errs
+        out.setdefault("guarded", {})[dist] = guarded
         seq = list(errs.values())
         assert all(b <= a * 1.01 + 2 * n * U for a, b in zip(seq, seq[1:])), seq
         assert seq[-2] <= 2 * n * U and seq[-1] <= 2 * n * U  # 15 and 16 moduli
@@ -128,7 +148,7 @@ def test_precision_large_sizes_rows(n):
     out = {"N": n, "bound_2Nu": 2 * n * U, "rows": {}}
     for dist, s in (("uniform11", 7), ("loguniform20", 8)):
         A, B = workload.pair(dist, 5, n)
-        with mm.Handle("emulated", slices=s) as h:
+        with mm.Handle("emulated", slices=s, flags=mm.FLAG_NO_GUARD) as h:
             C = host(h.gemm(dev(A), dev(B)))
             h.check()
         r = rows_of(n, 4)
@@ -164,6 +184,7 @@ def test_grouped_batch_1024(batch_1024, form):
         Cs = h.gemm_grouped(As, Bs)
         Cs = h.gemm_grouped(As, Bs, Cs)  # graph replay
         h.check()
+        replaced, _ = h.guard_read()
         plans = {n: h.plan(n) for n in set(sizes)}
     torch.cuda.synchronize()
     rng = np.random.default_rng(11)
@@ -179,14 +200,17 @@ def test_grouped_batch_1024(batch_1024, form):
             worst = max(worst, float(np.max(np.abs(C - ref) / absab)) / (2 * n * U))
         elif p % 16 == 0:
             check_rows(C, A, B, n)
-        if plans[n][0] != 0 and p % 64 == 1:
+        if plans[n][0] != 0 and p % 64 == 1 and replaced == 0:  # the models describe unreplaced results
             r = rows_of(n, 2)[:3]
             if plans[n][0] == 1:
                 want = oracle.emu_gemm_rows(A, B, plans[n][1], r)
             else:
                 want = oracle.fixed_gemm_rows(A, B, oracle.modular_beta(plans[n][1], n), r)
             np.testing.assert_array_equal(C[r].view(np.int64), want.view(np.int64))
-    report(f"grouped_1024_{form}.json", {"worst_error_over_bound_small_problems": worst})
+    report(f"grouped_1024_{form}.json", {"worst_error_over_bound_small_problems": worst,
+                                          "elements_replaced_by_the_certificate_two_calls": replaced})
+    if form in ("modular", "auto"):
+        assert replaced == 0  # uniform inputs: the certificate vouches for every element
 
 
 def test_grouped_workspace_waves(monkeypatch):
@@ -195,7 +219,7 @@ def test_grouped_workspace_waves(monkeypatch):
     monkeypatch.setenv("MM_WORKSPACE_LIMIT_MB", "96")
     sizes = [700, 300, 1000, 64, 513, 1300]
     pairs = [workload.pair("uniform11", 40 + i, n) for i, n in enumerate(sizes)]
-    with mm.Handle("emulated", slices=7) as h:
+    with mm.Handle("emulated", slices=7, flags=mm.FLAG_NO_GUARD) as h:
         Cs = h.gemm_grouped([dev(a) for a, _ in pairs], [dev(b) for _, b in pairs])
         h.check()
     for (A, B), C, n in zip(pairs, Cs, sizes):

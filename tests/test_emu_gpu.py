@@ -4,6 +4,10 @@ Every step is compared through the C ABI with the oracle's model of the same
 step: exponents and digits (a3/a4) and level sums (a5) bit for bit, the
 recombination (a6) bit for bit, and the whole product bit for bit against
 the model and within 2 N 2^-53 |A||B| of the plain FP64 product.
+
+The emulated handles here run without the accuracy certificate
+(MM_FLAG_NO_GUARD): it may send elements to native FP64, which the models do
+not describe.  test_guard_gpu.py covers the guarded path.
 """
 import numpy as np
 import pytest
@@ -17,7 +21,7 @@ pytestmark = pytest.mark.gpu
 
 def handle(slices=7, mode="emulated", flags=0):
     import paper_1012_2273_gb300 as mm
-    return mm.Handle(mode, slices=slices, flags=flags)
+    return mm.Handle(mode, slices=slices, flags=flags | mm.FLAG_NO_GUARD)
 
 
 def bf16_planes_to_int(t):
@@ -229,7 +233,7 @@ def test_forced_pair_groups_are_bit_exact(tmp_path, groups):
     tune.write_text(f"# max_n form slices bn groups\n100000 1 7 256 {groups}\n")
     n = 300
     A, B = workload.pair("uniform11", 7, n)
-    with mm.Handle("emulated", slices=7, tune_path=str(tune)) as h:
+    with mm.Handle("emulated", slices=7, flags=mm.FLAG_NO_GUARD, tune_path=str(tune)) as h:
         C = host(h.gemm(dev(A), dev(B)))
         sizes = [300, 64, 513]
         pairs = [workload.pair("uniform01", 20 + i, m) for i, m in enumerate(sizes)]

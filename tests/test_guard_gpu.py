@@ -1,0 +1,146 @@
+"""The accuracy certificate on the GPU (guard.cuh; mm_guard_read in mm.h).
+
+The product is Alg. 1's c_ik (Sec. 3.1).  With the certificate on (the
+library's default) every element of an emulated product must be within the
+bound of the oracle's plain left-to-right sum, whatever the inputs: each
+element either carries a proof that its error is within gamma_N |A||B| or is
+recomputed in native FP64.  Checked here, through the C ABI:
+  - inputs whose rows and columns mix magnitudes far apart (one large entry
+    per row meeting small entries of B and the reverse; magnitudes over
+    2^+-60; an outlier column), in the automatic, modular and digit forms,
+    at N = 300 and 2000, element by element against the oracle, where the
+    same products without the certificate leave the bound;
+  - a grouped call mixing such problems with ordinary ones, replayed;
+  - transposed and rectangular operands;
+  - where nothing fails (uniform inputs) the guarded result equals the
+    unguarded one bit for bit and nothing is reported;
+  - where a few elements fail (log-uniform 2^+-20 inputs at N = 2000 with 14
+    moduli), only those change, each within the bound, and no problem is
+    recomputed whole.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workload
+from helpers import U, assert_within_bound, dev, host
+
+pytestmark = pytest.mark.gpu
+
+
+def run(mode, A, B, slices=0, flags=0):
+    import paper_1012_2273_gb300 as mm
+    with mm.Handle(mode, slices=slices, flags=flags) as h:
+        C = host(h.gemm(dev(A), dev(B)))
+        h.check()
+        replaced = h.guard_read()
+    return C, replaced
+
+
+def within(C, A, B, n):
+    """max |C - oracle| / (2 n u |A||B|) over entries with |A||B| > 0."""
+    ref, absab = oracle.gemm(A, B), oracle.absgemm(A, B)
+    mask = absab > 0
+    return float(np.max(np.abs(C - ref)[mask] / absab[mask])) / (2 * n * U), ref, absab
+
+
+@pytest.mark.parametrize("n", [300, 2000])
+@pytest.mark.parametrize("kind", workload.STRUCTURES)
+@pytest.mark.parametrize("mode,slices", [("auto", 0), ("modular", 0), ("emulated", 7)])
+def test_structured_inputs_stay_within_the_bound(mode, slices, kind, n):
+    A, B = workload.structured_pair(kind, 40 + n, n)
+    C, (elements, problems) = run(mode, A, B, slices)
+    ratio, ref, absab = within(C, A, B, n)
+    assert ratio <= 1.0, (mode, kind, n, ratio, elements, problems)
+    if n >= 256 or mode != "auto":  # emulated: these inputs defeat the certificate somewhere
+        assert elements > 0
+    if kind == "split_scales" and (n >= 256 or mode != "auto"):
+        assert problems == 1 and elements == n * n  # every element fails: recomputed whole
+
+
+@pytest.mark.parametrize("mode,slices", [("modular", 16), ("emulated", 7)])
+def test_without_the_certificate_the_same_products_leave_the_bound(mode, slices):
+    import paper_1012_2273_gb300 as mm
+    n = 300
+    A, B = workload.structured_pair("split_scales", 340, n)
+    C, replaced = run(mode, A, B, slices, flags=mm.FLAG_NO_GUARD)
+    assert replaced == (0, 0)
+    ratio, _, _ = within(C, A, B, n)
+    assert ratio > 1.0  # the raw emulation is far outside; the guarded call above is not
+
+
+@pytest.mark.parametrize("use_graph", [True, False])
+def test_grouped_call_mixing_structured_and_ordinary_problems(use_graph):
+    import paper_1012_2273_gb300 as mm
+    specs = [("uniform01", 500), ("split_scales", 300), ("wide60", 700), ("uniform11", 64),
+             ("loguniform20", 1000), ("outlier_column", 257), ("split_scales", 1)]
+    pairs = [(workload.structured_pair(k, 7 + i, n) if k in workload.STRUCTURES else workload.pair(k, 7 + i, n))
+             for i, (k, n) in enumerate(specs)]
+    flags = 0 if use_graph else mm.FLAG_NO_GRAPH
+    with mm.Handle("auto", flags=flags) as h:
+        for rep in range(2):
+            Cs = h.gemm_grouped([dev(a) for a, _ in pairs], [dev(b) for _, b in pairs])
+            h.check()
+            elements, problems = h.guard_read()
+            assert problems >= 1 and elements > 0, rep  # the split_scales problem of N = 300 at least
+            for (A, B), C, (k, n) in zip(pairs, Cs, specs):
+                ratio, _, _ = within(host(C), A, B, n)
+                assert ratio <= 1.0, (k, n, ratio)
+
+
+@pytest.mark.parametrize("ta,tb", [(0, 0), (1, 0), (0, 1), (1, 1)])
+def test_transposed_and_rectangular_structured_operands(ta, tb):
+    import torch
+    import paper_1012_2273_gb300 as mm
+    m, n, k = 300, 170, 520
+    A0, _ = workload.structured_pair("wide60", 91, max(m, k))
+    _, B0 = workload.structured_pair("wide60", 92, max(k, n))
+    A, B = np.ascontiguousarray(A0[:m, :k]), np.ascontiguousarray(B0[:k, :n])
+    dA = dev(A.T.copy()).T if ta else dev(A)
+    dB = dev(B.T.copy()).T if tb else dev(B)
+    with mm.Handle("modular") as h:
+        C = host(h.gemm(dA, dB))
+        h.check()
+        elements, _ = h.guard_read()
+    torch.cuda.synchronize()
+    assert elements > 0
+    ref = oracle.gemm_mnk(A, B)
+    assert_within_bound(C, ref, oracle.absgemm_mnk(A, B), k)
+
+
+@pytest.mark.parametrize("mode,slices,n", [("modular", 0, 300), ("modular", 0, 700), ("modular", 14, 2000),
+                                           ("emulated", 7, 300), ("auto", 0, 1500)])
+def test_nothing_fails_on_uniform_inputs_and_bits_are_unchanged(mode, slices, n):
+    import paper_1012_2273_gb300 as mm
+    A, B = workload.pair("uniform11", 60 + n, n)
+    C, replaced = run(mode, A, B, slices)
+    C0, _ = run(mode, A, B, slices, flags=mm.FLAG_NO_GUARD)
+    assert replaced == (0, 0)
+    np.testing.assert_array_equal(C.view(np.int64), C0.view(np.int64))
+
+
+def test_a_few_listed_elements_are_recomputed_one_by_one():
+    import paper_1012_2273_gb300 as mm
+    n, k = 2000, 14
+    A, B = workload.pair("loguniform20", 3, n)
+    C, (elements, problems) = run("modular", A, B, k)
+    C0, _ = run("modular", A, B, k, flags=mm.FLAG_NO_GUARD)
+    assert problems == 0 and 0 < elements < n * n // 100
+    changed = np.argwhere(C.view(np.int64) != C0.view(np.int64))
+    assert len(changed) <= elements
+    rows = sorted({int(i) for i, _ in changed[:40]} | {0, n - 1})
+    ref = oracle.gemm_rows(A, B, rows)
+    assert_within_bound(C[rows], ref, np.abs(A[rows]) @ np.abs(B), n)
+    # the unchanged elements are the model's, bit for bit
+    want = oracle.fixed_gemm_rows(A, B, oracle.modular_beta(k, n), rows)
+    np.testing.assert_array_equal(C0[rows].view(np.int64), want.view(np.int64))
+
+
+def test_zero_rows_and_columns_never_fail():
+    n = 400
+    A, B = workload.pair("uniform11", 12, n)
+    A[3, :] = 0.0
+    B[:, 7] = 0.0
+    C, (elements, problems) = run("modular", A, B)
+    assert (elements, problems) == (0, 0)
+    assert not C[3].any() and not C[:, 7].any()

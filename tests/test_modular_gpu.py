@@ -7,6 +7,10 @@ computes exactly that with 128-bit integers, so every comparison here is bit
 for bit (plus the FP64 tolerance against the plain product where the width
 allows it).  beta comes from the library's width rule, which the CPU tests
 pin against the oracle's own statement of it.
+
+The emulated handles here run without the accuracy certificate
+(MM_FLAG_NO_GUARD): it may send elements to native FP64, which the models do
+not describe.  test_guard_gpu.py covers the guarded path.
 """
 import numpy as np
 import pytest
@@ -20,7 +24,7 @@ pytestmark = pytest.mark.gpu
 
 def handle(k=16, flags=0, tune_path=None):
     import paper_1012_2273_gb300 as mm
-    return mm.Handle("modular", slices=k, flags=flags, tune_path=tune_path)
+    return mm.Handle("modular", slices=k, flags=flags | mm.FLAG_NO_GUARD, tune_path=tune_path)
 
 
 def beta_of(k, n):
@@ -121,7 +125,7 @@ def test_modular_grouped_uneven_sizes_and_moduli(tmp_path, use_graph):
     As = [dev(a) for a, _ in pairs]
     Bs = [dev(b) for _, b in pairs]
     flags = 0 if use_graph else mm.FLAG_NO_GRAPH
-    with mm.Handle("auto", flags=flags, tune_path=str(tune)) as h:
+    with mm.Handle("auto", flags=flags | mm.FLAG_NO_GUARD, tune_path=str(tune)) as h:
         plans = {n: h.plan(n) for n in sizes if n}
         for _ in range(2):
             Cs = h.gemm_grouped(As, Bs)
@@ -220,7 +224,7 @@ def test_grouped_call_mixing_native_digit_and_modular_forms(tmp_path, use_graph)
     sizes = [700, 40, 250, 1, 129, 513, 300, 64]
     pairs = [workload.pair("uniform11", 150 + i, n) for i, n in enumerate(sizes)]
     flags = 0 if use_graph else mm.FLAG_NO_GRAPH
-    with mm.Handle("auto", flags=flags, tune_path=str(tune)) as h:
+    with mm.Handle("auto", flags=flags | mm.FLAG_NO_GUARD, tune_path=str(tune)) as h:
         plans = {n: h.plan(n) for n in sizes}
         for _ in range(2):
             Cs = h.gemm_grouped([dev(a) for a, _ in pairs], [dev(b) for _, b in pairs])
@@ -249,7 +253,7 @@ def test_modular_cta_pair_kernel_bit_exact(tmp_path, monkeypatch, use_graph):
     flags = 0 if use_graph else mm.FLAG_NO_GRAPH
     sizes = [1, 129, 257, 300, 385, 640, 1000]
     pairs = [workload.pair("loguniform20", 60 + i, n) for i, n in enumerate(sizes)]
-    with mm.Handle("auto", flags=flags, tune_path=str(tune)) as h:
+    with mm.Handle("auto", flags=flags | mm.FLAG_NO_GUARD, tune_path=str(tune)) as h:
         plans = {n: h.plan(n) for n in sizes}
         for (A, B), n in zip(pairs[:3], sizes[:3]):
             C = host(h.gemm(dev(A), dev(B)))

@@ -80,6 +80,40 @@ def rect_pair(dist: str, seed: int, m: int, n: int, k: int) -> tuple[np.ndarray,
     return A, B
 
 
+STRUCTURES = ("split_scales", "wide60", "outlier_column")
+
+
+def structured_pair(kind: str, seed: int, n: int) -> tuple[np.ndarray, np.ndarray]:
+    """Operand pairs whose rows and columns mix magnitudes far apart: the
+    inputs on which an emulation that scales each row of A and column of B by
+    its maximum loses accuracy relative to |A||B|.
+
+    split_scales   a_i0 = u, a_ij = 2^-30 u (j > 0); b_0k = 2^-30 u, b_jk = u
+                   (j > 0): each row's large entry meets the small ones of B,
+                   and the reverse, so every c_ik is a sum of small terms
+    wide60         entries of magnitude 2^U(-60, 60), random signs
+    outlier_column uniform [-1, 1) with the first column of A scaled by 2^40
+    (u uniform [1/2, 1) from stream ``seed``; B from the offset stream.)"""
+    if kind == "wide60":
+        def draw(s):
+            u = uniform01(s, n * n)
+            sign = (splitmix64(s + SIGN_STREAM_OFFSET, n * n) >> np.uint64(63)).astype(np.int64)
+            mag = np.exp2(-60.0 + 120.0 * u)
+            return np.where(sign == 1, -mag, mag).reshape(n, n)
+        return np.ascontiguousarray(draw(seed)), np.ascontiguousarray(draw(seed + B_STREAM_OFFSET))
+    if kind == "split_scales":
+        A = (0.5 + 0.5 * uniform01(seed, n * n)).reshape(n, n) * 2.0 ** -30
+        B = (0.5 + 0.5 * uniform01(seed + B_STREAM_OFFSET, n * n)).reshape(n, n)
+        A[:, 0] *= 2.0 ** 30
+        B[0, :] *= 2.0 ** -30
+        return np.ascontiguousarray(A), np.ascontiguousarray(B)
+    if kind == "outlier_column":
+        A, B = pair("uniform11", seed, n)
+        A[:, 0] *= 2.0 ** 40
+        return A, B
+    raise ValueError(f"unknown structure {kind!r}; expected one of {STRUCTURES}")
+
+
 def loguniform_sizes(count: int, lo: int, hi: int, seed: int) -> list[int]:
     """``count`` sizes N log-uniform over the integers [lo, hi].
 
