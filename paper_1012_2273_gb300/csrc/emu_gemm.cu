@@ -74,7 +74,8 @@ struct EmuCfg {
   static constexpr int B_BYTES = BN * EM_BK * 2;
   static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
   static constexpr int TMEM_COLS = 2 * BN;
-  static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*align*/ + 512 /*barriers, unit ring*/;
+  static constexpr int CERT_BYTES = 8 * (BN / 2) * 4;  // certificate: column terms, per epilogue warp
+  static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*align*/ + 512 /*barriers, unit ring*/ + CERT_BYTES;
 };
 
 struct UnitRef {
@@ -503,16 +504,24 @@ __global__ void __launch_bounds__(EM_THREADS, 1)
           // from below; elements whose error bound it cannot certify are
           // listed for the guard kernel.  Lanes are rows, so a warp tests 32
           // rows of one column at a time; nothing is written when all pass.
+          // The warp's column terms go to its own slice of shared memory
+          // (each converted once, not once per row).
+          float* colt = reinterpret_cast<float*>(smem + Cfg::STAGES * Cfg::STAGE_BYTES + 512) + (warp - 4) * HALF;
+          const float k2 = P->cert_k2;
+          for (int c = lane; c < HALF; c += 32) {
+            const int col = n0 + h * HALF + c;
+            colt[c] = col < n ? cert_col_term(P->b_sum[col], P->cert_k1) : 0.0f;
+          }
+          __syncwarp();
           const bool in_row = row < P->m;
-          const unsigned long long sa = in_row ? P->a_sum[row] : 0ull;
-          const float k1 = P->cert_k1, k2 = P->cert_k2;
+          const float rowt = in_row ? cert_row_term(P->a_sum[row]) : 0.0f;
           uint32_t bad[HALF / 32];
 #pragma unroll
           for (int w = 0; w < HALF / 32; ++w) bad[w] = 0u;
 #pragma unroll
           for (int i = 0; i < HALF; ++i) {
-            const int col = n0 + h * HALF + i;
-            if (in_row && col < n && !cert_ok(sa, P->b_sum[col], acc[i] - bias, k1, k2)) bad[i / 32] |= 1u << (i % 32);
+            const bool fail = !cert_test(rowt, colt[i], acc[i] - bias, k2);
+            if (in_row && n0 + h * HALF + i < n && fail) bad[i / 32] |= 1u << (i % 32);
           }
           uint32_t any = 0u;
 #pragma unroll
@@ -535,6 +544,7 @@ __global__ void __launch_bounds__(EM_THREADS, 1)
               }
             }
           }
+          __syncwarp();  // every lane is done with colt before the warp's next certificate unit
           continue;
         }
         if (kMod) {

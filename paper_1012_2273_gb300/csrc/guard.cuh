@@ -56,14 +56,25 @@ __host__ __device__ __forceinline__ uint64_t sum24_of(int64_t D, int w, bool v_n
 
 // The certificate test for one element: true when (*) holds for sure.  sa, sb
 // are the row and column sums of sum24_of, S the exact magnitude product,
-// k1 >= K1 and k2 <= K2 (1 - 2^-20) the constants of cert_constants.  Each
-// side is rounded at most twice by FP32 (relative error 2^-24 each), which
-// the 2^-20 margin in k2 absorbs, so the FP32 comparison implies the exact one.
+// k1 >= K1 and k2 <= K2 (1 - 2^-20) the constants of cert_constants.  It is
+// cut in three so that a kernel converts each row and column sum once and
+// spends three FP32 operations per element:
+//   row = fl(sa),  col = fl(fl(sb) + k1),  test: fl(row + col) <= fl(k2 fl(S)).
+// The left side is rounded at most four times and the right side twice
+// (relative error 2^-24 each), which the 2^-20 margin in k2 absorbs, so the
+// FP32 comparison implies the exact one.  A zero row or column (sum 0) gives
+// an exact zero in every form: its term is -infinity, which always passes.
+__host__ __device__ __forceinline__ float cert_row_term(uint64_t sa) {
+  return sa == 0 ? -INFINITY : static_cast<float>(sa);
+}
+__host__ __device__ __forceinline__ float cert_col_term(uint64_t sb, float k1) {
+  return sb == 0 ? -INFINITY : static_cast<float>(sb) + k1;
+}
+__host__ __device__ __forceinline__ bool cert_test(float row, float col, uint32_t S, float k2) {
+  return row + col <= k2 * static_cast<float>(S);
+}
 __host__ __device__ __forceinline__ bool cert_ok(uint64_t sa, uint64_t sb, uint32_t S, float k1, float k2) {
-  if (sa == 0 || sb == 0) return true;  // zero row or column: exact zero
-  const float lhs = static_cast<float>(sa + sb) + k1;
-  const float rhs = k2 * static_cast<float>(S);
-  return lhs <= rhs;
+  return cert_test(cert_row_term(sa), cert_col_term(sb, k1), S, k2);
 }
 
 // kappa of the digit form with s digits: the digit pairs (t, u), 1 <= t, u <= s,
