@@ -21,6 +21,11 @@ Parity status of each function (what pins it, in ``tests/test_oracle_pins.py``):
       rounding), exact on small-integer inputs, within the fixed-point error
       bound of the exact product on random ones.
   modular_beta -- the fixed-point width rule, against Python big integers.
+  i8_* -- the INT8 slice model: D equals the exact rounding of
+      a 2^(8s-2-e) (Python fractions); its digits are signed bytes and
+      reconstruct D; the whole product equals a brute-force restatement in
+      Python integers on small cases, is exact on small-integer inputs, and
+      obeys the certificate's error bound (test_guard_rule.py).
   emu_* -- digits reconstruct D exactly; D equals the exact rounding of
       a 2^(8s-1-e) (Python fractions); level sums equal brute force with
       Python integers; RN of 128-bit integers equals Python's correctly
@@ -107,6 +112,13 @@ def lib() -> ctypes.CDLL:
             L.or_fixed_gemm_mnk.restype = c_int
             L.or_emu_gemm_mnk.argtypes = [c_int, c_int, c_int, c_int, _D, _D, _I, c_int, _D, c_int]
             L.or_emu_gemm_mnk.restype = c_int
+            L.or_i8_fixed.argtypes = [c_double, c_int, c_int]
+            L.or_i8_fixed.restype = ctypes.c_int64
+            L.or_i8_digits_of.argtypes = [ctypes.c_int64, c_int, _I]
+            L.or_i8_combine.argtypes = [_I64, c_int, c_int, c_int]
+            L.or_i8_combine.restype = c_double
+            L.or_i8_gemm_mnk.argtypes = [c_int, c_int, c_int, c_int, _D, _D, _I, c_int, _D, c_int]
+            L.or_i8_gemm_mnk.restype = c_int
             _lib = L
     return _lib
 
@@ -381,4 +393,37 @@ def emu_gemm_mnk(A, B, s: int, rows=None, nthreads: int | None = None) -> np.nda
                                nr, _dp(C), threads(nthreads))
     if rc != 0:
         raise ValueError(f"oracle: emu_gemm_mnk failed ({rc})")
+    return C
+
+
+# ---- section 6: the INT8 slice form -------------------------------------------
+
+def i8_fixed(v: float, e: int, s: int) -> int:
+    """round-half-even(v 2^(8s - 2 - e))."""
+    return int(lib().or_i8_fixed(float(v), int(e), int(s)))
+
+
+def i8_digits_of(D: int, s: int) -> list[int]:
+    """Digits d_1..d_s of D, |D| <= 2^(8s-2): d_2..d_s in [-128, 127], d_1 in [-64, 64]."""
+    d = (ctypes.c_int * s)()
+    lib().or_i8_digits_of(int(D), int(s), d)
+    return list(d)
+
+
+def i8_combine(levels, s: int, e: int, f: int) -> float:
+    """RN(sum_L S_L 2^(8(s+1-L))) 2^(e + f - 8s - 4) for levels S_2..S_{s+1}."""
+    lv = (ctypes.c_int64 * s)(*[int(x) for x in levels])
+    return float(lib().or_i8_combine(lv, int(s), int(e), int(f)))
+
+
+def i8_gemm(A, B, s: int, rows=None, nthreads: int | None = None) -> np.ndarray:
+    """The INT8 slice form's result (square or rectangular operands; the
+    listed rows of A only, if `rows` is given)."""
+    A, B, m, n, k = _rect(A, B)
+    r, nr = _rows_arg(rows, m)
+    C = np.empty((nr, n), np.float64)
+    rc = lib().or_i8_gemm_mnk(m, n, k, int(s), _dp(A), _dp(B), r.ctypes.data_as(_I) if r is not None else None,
+                              nr, _dp(C), threads(nthreads))
+    if rc != 0:
+        raise ValueError(f"oracle: i8_gemm failed ({rc})")
     return C

@@ -29,6 +29,8 @@
  *      of the library's modular form; no counterpart in the paper).
  *   5. Sections 1, 2 (|A||B|), 3 and 4 for rectangular shapes (the paper's
  *      NRA x NCA times NCA x NCB of Alg. 2).
+ *   6. A model of the INT8 slice form: section 3's splitting with a width
+ *      one bit narrower, so that every digit is a signed byte.
  */
 #include <math.h>
 #include <stdint.h>
@@ -684,6 +686,106 @@ int or_emu_gemm_mnk(int m, int n, int k, int s, const double* A, const double* B
     for (int l = 0; l < n; ++l) {
       for (int L = 0; L < s; ++L) lv[L] = S[(size_t)L * n + l];
       C[(size_t)r * n + l] = or_emu_combine(lv, s, e, f[l]);
+    }
+    free(da); free(S); free(acc);
+  }
+  (void)nthreads;
+  free(f);
+  free(dB);
+  return bad ? -2 : 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* 6. Model of the INT8 slice form                                           */
+/* ------------------------------------------------------------------------ */
+/*
+ * The library's third emulation form (no counterpart in the paper) is
+ * Ozaki's error-free splitting with int8 slices and int32 accumulation, as
+ * the integer tensor cores take it.  A signed byte holds -128..127, so the
+ * fixed-point width is one bit narrower than section 3's, which keeps the
+ * leading digit within [-64, 64]:
+ *   D      = round-half-even(v 2^(8s - 2 - e)),  e the row (A) or column (B)
+ *            exponent of section 3, so |D| <= 2^(8s - 2)
+ *   D      = sum_{t=1..s} d_t 2^(8(s - t)), d_2..d_s in [-128, 127] (the
+ *            balanced residues modulo 256, lowest first), d_1 the rest
+ *   S_L    = sum_j sum_{t+u=L} d_t(a_ij) d_u(b_jk), L = 2..s+1, exact
+ *   c_ik   = RN( sum_L S_L 2^(8(s+1-L)) ) 2^(e_i + f_k - 8s - 4)
+ * (D_A D_B 2^(e+f-2(8s-2)) is the product of the rounded operands; of its
+ * digit pairs only those with t + u <= s + 1 are kept, as in section 3.)
+ * Written apart from section 3 so that each model reads on its own.
+ */
+
+/* round-half-even(v 2^(8s - 2 - e)); exact as in or_emu_fixed. */
+int64_t or_i8_fixed(double v, int e, int s) { return (int64_t)nearbyint(ldexp(v, 8 * s - 2 - e)); }
+
+/* Digits d_1..d_s of D (|D| <= 2^(8s-2)) into d[0..s-1]. */
+void or_i8_digits_of(int64_t D, int s, int* d) {
+  for (int t = s; t >= 2; --t) {
+    const int r = (int)(D & 255);
+    const int dt = r >= 128 ? r - 256 : r;
+    d[t - 1] = dt;
+    D = (D - dt) / 256;
+  }
+  d[0] = (int)D;
+}
+
+/* RN(sum_L S_L 2^(8(s+1-L))) 2^(e + f - 8s - 4), levels S_2..S_{s+1}. */
+double or_i8_combine(const int64_t* S_levels, int s, int e, int f) {
+  __int128 T = 0;
+  for (int L = 2; L <= s + 1; ++L) T = T * 256 + (__int128)S_levels[L - 2];
+  return ldexp((double)T, e + f - 8 * s - 4);
+}
+
+/* C (rows of A listed in `rows`, or all m rows if rows is NULL) of the INT8
+ * slice model for A (m x k) and B (k x n), row-major.  Each digit pair's sum
+ * over j is formed in int32 (|d_t d_u| <= 2^14, k < 2^17) and added into the
+ * level in int64.  0 on success. */
+int or_i8_gemm_mnk(int m, int n, int k, int s, const double* A, const double* B, const int* rows, int nrows,
+                   double* C, int nthreads) {
+  if (s < 1 || s > OR_EMU_MAX_SLICES || m < 0 || n < 0 || k < 0 || k >= (1 << 17)) return -1;
+  if (!rows) nrows = m;
+  if (nrows == 0 || n == 0) return 0;
+  int* f = (int*)malloc(sizeof(int) * (size_t)n);
+  int8_t* dB = (int8_t*)malloc((size_t)s * k * n + 1);
+  if (!f || !dB) { free(f); free(dB); return -2; }
+  int d[OR_EMU_MAX_SLICES];
+  for (int l = 0; l < n; ++l) f[l] = exponent_of_max(B + l, k, (size_t)n);
+  for (int j = 0; j < k; ++j)
+    for (int l = 0; l < n; ++l) {
+      or_i8_digits_of(or_i8_fixed(B[(size_t)j * n + l], f[l], s), s, d);
+      for (int u = 0; u < s; ++u) dB[((size_t)u * k + j) * n + l] = (int8_t)d[u];
+    }
+  int bad = 0;
+#ifdef _OPENMP
+  if (nthreads < 1) nthreads = 1;
+#pragma omp parallel for schedule(dynamic) num_threads(nthreads) reduction(+ : bad)
+#endif
+  for (int r = 0; r < nrows; ++r) {
+    const double* a = A + (size_t)(rows ? rows[r] : r) * k;
+    const int e = exponent_of_max(a, k, 1);
+    int8_t* da = (int8_t*)malloc((size_t)s * k + 1);
+    int64_t* S = (int64_t*)calloc((size_t)s * n, sizeof(int64_t));
+    int32_t* acc = (int32_t*)malloc(sizeof(int32_t) * (size_t)n);
+    if (!da || !S || !acc) { free(da); free(S); free(acc); ++bad; continue; }
+    int dd[OR_EMU_MAX_SLICES];
+    for (int j = 0; j < k; ++j) {
+      or_i8_digits_of(or_i8_fixed(a[j], e, s), s, dd);
+      for (int t = 0; t < s; ++t) da[(size_t)t * k + j] = (int8_t)dd[t];
+    }
+    for (int t = 1; t <= s; ++t)
+      for (int u = 1; t + u <= s + 1; ++u) {
+        for (int l = 0; l < n; ++l) acc[l] = 0;
+        for (int j = 0; j < k; ++j) {
+          const int32_t aj = da[(size_t)(t - 1) * k + j];
+          const int8_t* bj = dB + ((size_t)(u - 1) * k + j) * n;
+          for (int l = 0; l < n; ++l) acc[l] += aj * (int32_t)bj[l];
+        }
+        for (int l = 0; l < n; ++l) S[(size_t)(t + u - 2) * n + l] += acc[l];
+      }
+    int64_t lv[OR_EMU_MAX_SLICES];
+    for (int l = 0; l < n; ++l) {
+      for (int L = 0; L < s; ++L) lv[L] = S[(size_t)L * n + l];
+      C[(size_t)r * n + l] = or_i8_combine(lv, s, e, f[l]);
     }
     free(da); free(S); free(acc);
   }

@@ -84,9 +84,11 @@ struct UnitRef {
   int tile_local;  // tile within the problem
   int g;           // pair group
   int G;           // pair groups of this problem
-  bool cert;       // the tile's certificate unit (g == G): the magnitude planes' product
 };
 
+// Unit u of a launch.  The certificate launch (kCert) has one unit per tile:
+// the product of the two magnitude planes.
+template <bool kCert>
 __device__ __forceinline__ UnitRef emu_unit(const EmuArgs& a, int u) {
   UnitRef r;
   if (!a.units) {
@@ -94,7 +96,7 @@ __device__ __forceinline__ UnitRef emu_unit(const EmuArgs& a, int u) {
     r.pi = 0;
     r.G = a.single.groups;
     const int tiles = a.single.tiles_m * a.single.tiles_n;
-    r.g = u / tiles;  // group-major: concurrent CTAs share the same digit slices
+    r.g = kCert ? 0 : u / tiles;  // group-major: concurrent CTAs share the same digit slices
     r.tile_local = u - r.g * tiles;
   } else {
     const int4 e = a.units[u];
@@ -104,15 +106,14 @@ __device__ __forceinline__ UnitRef emu_unit(const EmuArgs& a, int u) {
     r.g = e.z;
     r.G = r.P->groups;
   }
-  r.cert = r.g >= r.G;
   return r;
 }
 
 // Products of a unit: [p0, p1) of the tile's digit pairs or moduli, or the
 // single magnitude product of a certificate unit.
-template <bool kMod>
+template <bool kMod, bool kCert>
 __device__ __forceinline__ void unit_products(const UnitRef& U, int* p0, int* p1) {
-  if (U.cert) {
+  if (kCert) {
     *p0 = 0;
     *p1 = 1;
   } else {
@@ -181,7 +182,9 @@ __device__ __forceinline__ void recombine_row(const int32_t* tile_slots, int s, 
   }
 }
 
-template <int BN, bool kMod>
+// kCert: the certificate launch (units are tiles, each multiplying the two
+// magnitude planes and testing every element; see guard.cuh).
+template <int BN, bool kMod, bool kCert>
 __global__ void __launch_bounds__(EM_THREADS, 1)
     emu_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                     const __grid_constant__ EmuArgs args) {
@@ -269,7 +272,7 @@ __global__ void __launch_bounds__(EM_THREADS, 1)
           uphase ^= 1;
         }
         if (u < 0) break;
-        const UnitRef U = emu_unit(args, u);
+        const UnitRef U = emu_unit<kCert>(args, u);
         const Problem* P = U.P;
         int tm, tn;
         emu_tile_coords(U.tile_local, P->tiles_m, P->tiles_n, &tm, &tn);
@@ -279,10 +282,10 @@ __global__ void __launch_bounds__(EM_THREADS, 1)
         const CUtensorMap* ma = args.units ? &args.maps[2 * U.pi] : &mapA;
         const CUtensorMap* mb = args.units ? &args.maps[2 * U.pi + 1] : &mapB;
         int p0, p1;
-        unit_products<kMod>(U, &p0, &p1);
+        unit_products<kMod, kCert>(U, &p0, &p1);
         for (int p = p0; p < p1 && ok; ++p) {
           int ta = p, tb = p;  // modular form: residue planes p of A and of B^T
-          if (U.cert) {        // the magnitude planes follow the s digit or residue planes
+          if (kCert) {         // the magnitude planes follow the s digit or residue planes
             ta = tb = P->s;
           } else if (!kMod) {  // digit pair (t, L - t): planes t - 1 and L - t - 1
             int L, t;
@@ -343,13 +346,13 @@ __global__ void __launch_bounds__(EM_THREADS, 1)
           uphase ^= 1;
         }
         if (u < 0) break;
-        const UnitRef U = emu_unit(args, u);
+        const UnitRef U = emu_unit<kCert>(args, u);
         const int KB = U.P->k_pad / EM_BK;
         int p0, p1;
-        unit_products<kMod>(U, &p0, &p1);
+        unit_products<kMod, kCert>(U, &p0, &p1);
         int L, t0;
         for (int p = p0; p < p1 && ok;) {
-          const int np = (kMod || U.cert) ? 1 : emu_segment(p, p1, maxp, &L, &t0);
+          const int np = (kMod || kCert) ? 1 : emu_segment(p, p1, maxp, &L, &t0);
           p += np;
           const int nb = np * KB;
           for (int c0 = 0; c0 < nb && ok; c0 += EM_CHUNK_KB) {
@@ -438,7 +441,7 @@ __global__ void __launch_bounds__(EM_THREADS, 1)
         uphase ^= 1;
       }
       if (u < 0) break;
-      const UnitRef U = emu_unit(args, u);
+      const UnitRef U = emu_unit<kCert>(args, u);
       const Problem* P = U.P;
       const int n = P->n;
       int tm, tn;
@@ -449,10 +452,10 @@ __global__ void __launch_bounds__(EM_THREADS, 1)
       const int row = m0 + r_in_tile;
       const int s = P->s;
       int p0, p1;
-      unit_products<kMod>(U, &p0, &p1);
+      unit_products<kMod, kCert>(U, &p0, &p1);
       // slot of this unit's first segment, and where the tile's slots live
       int slot = kMod ? p0 : 0;
-      if (!kMod && !U.cert) {
+      if (!kMod && !kCert) {
         for (int g = 0; g < U.g; ++g) {
           int q0, q1;
           emu_group_range(s, U.G, g, &q0, &q1);
@@ -465,7 +468,7 @@ __global__ void __launch_bounds__(EM_THREADS, 1)
       int L, t0;
       uint32_t pend[kMod ? HALF / 4 : 1] = {};  // modular form: residues of a pair's first modulus
       for (int p = p0; p < p1 && ok; ++slot) {
-        const int np = (kMod || U.cert) ? 1 : emu_segment(p, p1, maxp, &L, &t0);
+        const int np = (kMod || kCert) ? 1 : emu_segment(p, p1, maxp, &L, &t0);
         p += np;
         const int nb = np * KB;
         const int nchunks = (nb + EM_CHUNK_KB - 1) / EM_CHUNK_KB;
@@ -499,7 +502,7 @@ __global__ void __launch_bounds__(EM_THREADS, 1)
         }
         if (!ok) break;
         const uint32_t bias = static_cast<uint32_t>(nchunks) * EM_MAGIC;
-        if (U.cert) {
+        if (kCert) {
           // Certificate (guard.cuh): S = sum_j M_A M_B, exact, bounds (|A||B|)
           // from below; elements whose error bound it cannot certify are
           // listed for the guard kernel.  Lanes are rows, so a warp tests 32
@@ -634,7 +637,7 @@ __global__ void __launch_bounds__(EM_THREADS, 1)
         }
       }
       // deferred (and every modular problem): recombined by a separate pass
-      if (!ok || args.levels_out || P->defer || kMod || U.cert) continue;
+      if (!ok || args.levels_out || P->defer || kMod || kCert) continue;
       bool mine = true;
       if (U.G > 1) {
         // Each epilogue warp owns the same 32 x BN/2 region in every unit of
@@ -673,13 +676,13 @@ __global__ void __launch_bounds__(EM_THREADS, 1)
 
 int emu_smem_bytes(int bn) { return bn == 256 ? EmuCfg<256>::SMEM_BYTES : EmuCfg<128>::SMEM_BYTES; }
 
-template <int BN, bool kMod>
+template <int BN, bool kMod, bool kCert>
 static cudaError_t launch_bn(const CUtensorMap* mapA, const CUtensorMap* mapB, const EmuArgs& args, int grid,
                              cudaStream_t stream) {
-  cudaError_t e = cudaFuncSetAttribute(emu_gemm_kernel<BN, kMod>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t e = cudaFuncSetAttribute(emu_gemm_kernel<BN, kMod, kCert>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        EmuCfg<BN>::SMEM_BYTES);
   if (e != cudaSuccess) return e;
-  emu_gemm_kernel<BN, kMod><<<grid, EM_THREADS, EmuCfg<BN>::SMEM_BYTES, stream>>>(*mapA, *mapB, args);
+  emu_gemm_kernel<BN, kMod, kCert><<<grid, EM_THREADS, EmuCfg<BN>::SMEM_BYTES, stream>>>(*mapA, *mapB, args);
   return cudaGetLastError();
 }
 
@@ -687,17 +690,24 @@ cudaError_t emu_gemm_launch(int bn, bool modular, const CUtensorMap* mapA, const
                             const EmuArgs& args, int grid, cudaStream_t stream) {
   if (args.total_units <= 0) return cudaSuccess;
   if (modular)
-    return bn == 256 ? launch_bn<256, true>(mapA, mapB, args, grid, stream)
-                     : launch_bn<128, true>(mapA, mapB, args, grid, stream);
-  return bn == 256 ? launch_bn<256, false>(mapA, mapB, args, grid, stream)
-                   : launch_bn<128, false>(mapA, mapB, args, grid, stream);
+    return bn == 256 ? launch_bn<256, true, false>(mapA, mapB, args, grid, stream)
+                     : launch_bn<128, true, false>(mapA, mapB, args, grid, stream);
+  return bn == 256 ? launch_bn<256, false, false>(mapA, mapB, args, grid, stream)
+                   : launch_bn<128, false, false>(mapA, mapB, args, grid, stream);
+}
+
+cudaError_t emu_cert_launch(int bn, const CUtensorMap* mapA, const CUtensorMap* mapB, const EmuArgs& args, int grid,
+                            cudaStream_t stream) {
+  if (args.total_units <= 0) return cudaSuccess;
+  return bn == 256 ? launch_bn<256, false, true>(mapA, mapB, args, grid, stream)
+                   : launch_bn<128, false, true>(mapA, mapB, args, grid, stream);
 }
 
 // Registers, threads and shared memory of the slice-product kernel, for error messages.
 void emu_kernel_info(int bn, char* buf, size_t len) {
   cudaFuncAttributes fa{};
-  const cudaError_t e = bn == 256 ? cudaFuncGetAttributes(&fa, emu_gemm_kernel<256, false>)
-                                  : cudaFuncGetAttributes(&fa, emu_gemm_kernel<128, false>);
+  const cudaError_t e = bn == 256 ? cudaFuncGetAttributes(&fa, emu_gemm_kernel<256, false, false>)
+                                  : cudaFuncGetAttributes(&fa, emu_gemm_kernel<128, false, false>);
   int dev = 0, optin = 0, regs_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);

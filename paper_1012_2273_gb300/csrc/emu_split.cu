@@ -71,8 +71,10 @@ __device__ __forceinline__ uint32_t bf16x2_of_digits(float lo, float hi) {
 // bounds of |v'| 2^7, exact small integers in bf16) to the magnitude plane as
 // one 16-byte vector and adds the upper bounds of |v'| 2^24 to the row's sum
 // in shared memory.  (A zero row's sum is discarded later, from its maximum.)
+// `xor_lanes`: the lane distances (bits 1, 2, 4, ...) to the other lanes that
+// hold the same row, whose partial sums are added in first.
 __device__ __forceinline__ void guard_item(const long long (&D)[8], int width, uint16_t* mag_out,
-                                           unsigned long long* row_sum, bool lead, unsigned pair_mask) {
+                                           unsigned long long* row_sum, bool lead, unsigned xor_lanes) {
   uint32_t w[4];
   unsigned long long sum = 0;
 #pragma unroll
@@ -82,9 +84,8 @@ __device__ __forceinline__ void guard_item(const long long (&D)[8], int width, u
     sum += sum24_of(D[2 * p], width, true) + sum24_of(D[2 * p + 1], width, true);
   }
   *reinterpret_cast<uint4*>(mag_out) = make_uint4(w[0], w[1], w[2], w[3]);
-  // the lanes of `pair_mask` hold the same row: add theirs first
   for (int o = 1; o < 32; o <<= 1)
-    if (pair_mask & (1u << o)) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    if (xor_lanes & static_cast<unsigned>(o)) sum += __shfl_xor_sync(0xffffffffu, sum, o);
   if (lead) atomicAdd(row_sum, sum);
 }
 

@@ -77,12 +77,13 @@ __host__ __device__ __forceinline__ bool cert_ok(uint64_t sa, uint64_t sb, uint3
   return cert_test(cert_row_term(sa), cert_col_term(sb, k1), S, k2);
 }
 
-// kappa of the digit form with s digits: the digit pairs (t, u), 1 <= t, u <= s,
+// kappa of a digit form with s digits of base 2^8 and width w (8s - 1 for
+// bf16 digits, 8s - 2 for int8 digits): the digit pairs (t, u), 1 <= t, u <= s,
 // of level L = t + u >= s + 2 are left out; each |d_t d_u| <= 2^14 and weighs
-// 2^(2 - 8L) once scaled by 2^-2w (w = 8s - 1), with 2s + 1 - L pairs per level.
-inline double digit_kappa(int s) {
+// 2^(8(2s - L) - 2w) once scaled by 2^-2w, with 2s + 1 - L pairs per level.
+inline double digit_kappa(int s, int w) {
   double k = 0.0;
-  for (int L = s + 2; L <= 2 * s; ++L) k += (2.0 * s + 1.0 - L) * std::ldexp(1.0, 16 - 8 * L);
+  for (int L = s + 2; L <= 2 * s; ++L) k += (2.0 * s + 1.0 - L) * std::ldexp(1.0, 14 + 16 * s - 8 * L - 2 * w);
   return k;
 }
 

@@ -146,6 +146,10 @@ cudaError_t mod_pair_gemm_launch(const CUtensorMap* mapA, const CUtensorMap* map
 int emu_smem_bytes(int bn);
 cudaError_t emu_gemm_launch(int bn, bool modular, const CUtensorMap* mapA, const CUtensorMap* mapB,
                             const EmuArgs& args, int grid, cudaStream_t stream);
+// the accuracy certificate's launch: one unit per tile (args.units lists
+// them for grouped calls; tile index = unit for a single problem)
+cudaError_t emu_cert_launch(int bn, const CUtensorMap* mapA, const CUtensorMap* mapB, const EmuArgs& args, int grid,
+                            cudaStream_t stream);
 void emu_kernel_info(int bn, char* buf, size_t len);
 
 // recombine.cu

@@ -127,6 +127,10 @@ struct mm_handle_s {
   // joined back into the call's stream (inside the captured graph)
   cudaStream_t side_stream = nullptr;
   cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
+  // the accuracy certificate's launches run on their own stream, forked from
+  // and joined back into the call's stream
+  cudaStream_t cert_stream = nullptr;
+  cudaEvent_t cert_fork = nullptr, cert_join = nullptr;
   // autotune table: N upper bound -> plan
   std::vector<std::pair<int, Plan>> tune;
   // MM_FLAG_PROFILE: events around every kernel of the last call
@@ -322,6 +326,8 @@ struct EmuGroup {
   std::vector<int> max_off;        // offset of problem p in the maxbits arrays
   std::vector<CUtensorMap> maps;   // 2 per problem
   std::vector<int4> units;         // grouped launches: {problem, tile, group, cost}
+  std::vector<int4> cert_units;    // grouped launches: the certificate's {problem, tile, 0, cost}
+  int cert_total = 0;              // units of the certificate's launch
   int total_tiles = 0, total_split = 0, total_absmax = 0, total_units = 0, max_rows = 0, scratch_slots = 1;
   long long tilebuf_elems = 0;
   // byte offsets inside the group's region of the arena
@@ -403,7 +409,7 @@ mm_status layout_group(mm_handle h, EmuGroup& g, char* base) {
     if (g.guard) {
       // certificate constants for inner dimension k and width w (guard.cuh)
       const int w = g.form == 2 ? p.beta : 8 * p.s - 1;
-      mmk::cert_constants(p.k, w, g.form == 2 ? 0.0 : mmk::digit_kappa(p.s), &p.cert_k1, &p.cert_k2);
+      mmk::cert_constants(p.k, w, g.form == 2 ? 0.0 : mmk::digit_kappa(p.s, w), &p.cert_k1, &p.cert_k2);
       // more failures than a quarter of the outputs: recompute the whole
       // problem natively (then the per-element list would cost about as much)
       p.guard_limit = static_cast<int>(std::min<long long>(std::max<long long>(256, static_cast<long long>(p.m) * p.n / 4),
@@ -470,8 +476,7 @@ mm_status layout_group(mm_handle h, EmuGroup& g, char* base) {
           const int cost = (p1 - p0) * kb;
           for (int t = 0; t < unit_tiles; ++t) g.units.push_back(make_int4(static_cast<int>(i), t, gi, cost));
         }
-        if (g.guard)  // the certificate unit of each tile: one product
-          for (int t = 0; t < unit_tiles; ++t) g.units.push_back(make_int4(static_cast<int>(i), t, G, kb));
+
       }
       continue;
     }
@@ -508,8 +513,7 @@ mm_status layout_group(mm_handle h, EmuGroup& g, char* base) {
         const int cost = (p1 - p0) * kb;
         for (int t = 0; t < tiles; ++t) g.units.push_back(make_int4(static_cast<int>(i), t, gi, cost));
       }
-      if (g.guard)
-        for (int t = 0; t < tiles; ++t) g.units.push_back(make_int4(static_cast<int>(i), t, G, kb));
+
     }
   }
   if (g.tabled) {
@@ -522,16 +526,31 @@ mm_status layout_group(mm_handle h, EmuGroup& g, char* base) {
     });
     g.total_units = static_cast<int>(g.units.size());
   } else {
-    g.total_units = g.ps[0].tiles_m * g.ps[0].tiles_n / (g.pair ? 2 : 1) * (g.ps[0].groups + (g.guard ? 1 : 0));
+    g.total_units = g.ps[0].tiles_m * g.ps[0].tiles_n / (g.pair ? 2 : 1) * g.ps[0].groups;
   }
   g.grid = g.pair ? 2 * emu_grid(h, std::min(g.total_units, h->num_sms / 2)) : emu_grid(h, g.total_units);
+  // The certificate's own launch: one unit per tile, k-blocks as the cost,
+  // longest first (grouped calls list them; a single problem numbers them).
+  g.cert_units.clear();
+  g.cert_total = 0;
+  if (g.guard) {
+    for (size_t i = 0; i < g.ps.size(); ++i) {
+      const Problem& p = g.ps[i];
+      const int tiles = p.tiles_m * p.tiles_n;
+      if (g.tabled)
+        for (int t = 0; t < tiles; ++t) g.cert_units.push_back(make_int4(static_cast<int>(i), t, 0, p.k_pad / 64));
+      g.cert_total += tiles;
+    }
+    std::stable_sort(g.cert_units.begin(), g.cert_units.end(),
+                     [](const int4& a, const int4& b) { return a.w > b.w; });
+  }
   // Everything zeroed before a launch sits in one run (one memset): the
   // row/column maxima, the tile and unit counters, and -- when guarded --
   // per problem the certificate's row sums [m] and column sums [n], then the
   // per-problem failure counts and their total.
   g.amax = ar.take(sizeof(uint64_t) * g.max_rows);
   g.bmax = ar.take(sizeof(uint64_t) * g.max_rows);
-  g.counters = ar.take(sizeof(int) * (8 * static_cast<size_t>(g.total_tiles) + 1));  // + unit counter
+  g.counters = ar.take(sizeof(int) * (8 * static_cast<size_t>(g.total_tiles) + 2));  // + unit counters (main, certificate)
   std::vector<size_t> sum_off(g.ps.size(), 0);
   size_t counts_at = 0, gsum_len = 0;
   if (g.guard) {
@@ -581,7 +600,7 @@ mm_status layout_group(mm_handle h, EmuGroup& g, char* base) {
 // hold one problem, passed by value; otherwise d_table/d_maps/d_max_off/d_units
 // are device copies of g.ps, g.maps, g.max_off and g.units.
 mm_status run_group(mm_handle h, const EmuGroup& g, const Problem* d_table, const CUtensorMap* d_maps,
-                    const int* d_max_off, const int4* d_units, cudaStream_t stream) {
+                    const int* d_max_off, const int4* d_units, const int4* d_cert_units, cudaStream_t stream) {
   if (g.total_units == 0) return MM_OK;
   uint64_t* amax = reinterpret_cast<uint64_t*>(g.base + g.amax);
   uint64_t* bmax = reinterpret_cast<uint64_t*>(g.base + g.bmax);
@@ -611,6 +630,28 @@ mm_status run_group(mm_handle h, const EmuGroup& g, const Problem* d_table, cons
   a.levels_out = nullptr;
   a.status = h->d_status;
   a.timeout_ns = h->timeout_ns;
+  // The certificate's launch needs only the split's planes and sums.  Unless
+  // profiling, it runs on its own stream, so that its units fill the SMs the
+  // slice products leave idle at their end; the guard kernel waits for it.
+  bool cert_forked = false;
+  if (g.guard) {
+    mmk::EmuArgs c = a;
+    c.units = single ? nullptr : d_cert_units;
+    c.total_units = g.cert_total;
+    c.unit_counter = a.unit_counter + 1;
+    cudaStream_t cs = stream;
+    if (!h->profile) {
+      MM_CUDA(h, cudaEventRecord(h->cert_fork, stream));
+      MM_CUDA(h, cudaStreamWaitEvent(h->cert_stream, h->cert_fork, 0));
+      cs = h->cert_stream;
+      cert_forked = true;
+    }
+    const long m_c = prof_start(h, cs, KIND_SLICE_GEMM);
+    const cudaError_t ce = mmk::emu_cert_launch(g.bn, &g.maps[0], &g.maps[1], c, emu_grid(h, g.cert_total), cs);
+    prof_end(h, cs, m_c);
+    if (ce != cudaSuccess) return cuda_fail(h, ce, "certificate launch");
+    if (cert_forked) MM_CUDA(h, cudaEventRecord(h->cert_join, cs));
+  }
   const long m_gemm = prof_start(h, stream, KIND_SLICE_GEMM);
   const cudaError_t le = g.pair ? mmk::mod_pair_gemm_launch(&g.maps[0], &g.maps[1], a, g.grid, stream)
                                 : mmk::emu_gemm_launch(g.bn, g.form == 2, &g.maps[0], &g.maps[1], a, g.grid, stream);
@@ -637,6 +678,7 @@ mm_status run_group(mm_handle h, const EmuGroup& g, const Problem* d_table, cons
   if (g.guard) {
     // native FP64 for what the certificate could not vouch for (returns at
     // once when every element passed)
+    if (cert_forked) MM_CUDA(h, cudaStreamWaitEvent(stream, h->cert_join, 0));
     const long m_g = prof_start(h, stream, KIND_NATIVE);
     MM_CUDA(h, mmk::guard_launch(d_table, single ? &g.ps[0] : nullptr, static_cast<int>(g.ps.size()), g.guard_tiles,
                                  h->num_sms, guard_stats(h), stream));
@@ -677,7 +719,7 @@ mm_status emu_single(mm_handle h, const Problem& p, int form, int s, int bn, int
   if (st != MM_OK) return st;
   st = layout_group(h, g, static_cast<char*>(h->arena));
   if (st != MM_OK) return st;
-  return run_group(h, g, nullptr, nullptr, nullptr, nullptr, stream);
+  return run_group(h, g, nullptr, nullptr, nullptr, nullptr, nullptr, stream);
 }
 
 mm_status native_single(mm_handle h, Problem p, cudaStream_t stream) {
@@ -839,12 +881,13 @@ mm_status grouped_impl(mm_handle h, const std::vector<Problem>& probs, cudaStrea
   Arena tab;
   const size_t off_nat = tab.take(sizeof(Problem) * std::max<size_t>(nat.size(), 1));
   const size_t off_nat_small = tab.take(sizeof(Problem) * std::max<size_t>(nat_small.size(), 1));
-  std::vector<size_t> off_tab, off_maps, off_mo, off_units;
+  std::vector<size_t> off_tab, off_maps, off_mo, off_units, off_cert;
   for (const EmuGroup& g : groups) {
     off_tab.push_back(tab.take(sizeof(Problem) * g.ps.size()));
     off_maps.push_back(tab.take(sizeof(CUtensorMap) * g.maps.size()));
     off_mo.push_back(tab.take(sizeof(int) * g.max_off.size()));
     off_units.push_back(tab.take(sizeof(int4) * std::max<size_t>(g.units.size(), 1)));
+    off_cert.push_back(tab.take(sizeof(int4) * std::max<size_t>(g.cert_units.size(), 1)));
   }
   const size_t tab_bytes = tab.off;
   std::vector<char> host_tab(tab_bytes, 0);
@@ -857,6 +900,8 @@ mm_status grouped_impl(mm_handle h, const std::vector<Problem>& probs, cudaStrea
     std::memcpy(host_tab.data() + off_maps[gi], g.maps.data(), sizeof(CUtensorMap) * g.maps.size());
     std::memcpy(host_tab.data() + off_mo[gi], g.max_off.data(), sizeof(int) * g.max_off.size());
     if (!g.units.empty()) std::memcpy(host_tab.data() + off_units[gi], g.units.data(), sizeof(int4) * g.units.size());
+    if (!g.cert_units.empty())
+      std::memcpy(host_tab.data() + off_cert[gi], g.cert_units.data(), sizeof(int4) * g.cert_units.size());
   }
 
   auto launch_all = [&](char* dtab, cudaStream_t s) -> mm_status {
@@ -887,7 +932,8 @@ mm_status grouped_impl(mm_handle h, const std::vector<Problem>& probs, cudaStrea
       mm_status st = run_group(h, groups[gi], reinterpret_cast<Problem*>(dtab + off_tab[gi]),
                                reinterpret_cast<CUtensorMap*>(dtab + off_maps[gi]),
                                reinterpret_cast<int*>(dtab + off_mo[gi]),
-                               reinterpret_cast<int4*>(dtab + off_units[gi]), s);
+                               reinterpret_cast<int4*>(dtab + off_units[gi]),
+                               reinterpret_cast<int4*>(dtab + off_cert[gi]), s);
       if (st != MM_OK) return st;
     }
     if (fork) MM_CUDA(h, cudaStreamWaitEvent(s, h->join_ev, 0));
@@ -1054,6 +1100,9 @@ mm_status mm_create(mm_handle* out, const mm_config* cfg) {
       cudaMalloc(&h->d_status, 128) != cudaSuccess || cudaMemset(h->d_status, 0, 128) != cudaSuccess ||
       cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
       cudaStreamCreateWithFlags(&h->side_stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&h->cert_stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->cert_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->cert_join, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&h->fork_ev, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&h->join_ev, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&h->grp_event, cudaEventDisableTiming) != cudaSuccess) {
@@ -1085,6 +1134,9 @@ mm_status mm_destroy(mm_handle h) {
   if (h->grp_event) cudaEventDestroy(h->grp_event);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   if (h->side_stream) cudaStreamDestroy(h->side_stream);
+  if (h->cert_stream) cudaStreamDestroy(h->cert_stream);
+  if (h->cert_fork) cudaEventDestroy(h->cert_fork);
+  if (h->cert_join) cudaEventDestroy(h->cert_join);
   if (h->fork_ev) cudaEventDestroy(h->fork_ev);
   if (h->join_ev) cudaEventDestroy(h->join_ev);
   if (h->d_status) cudaFree(h->d_status);

@@ -3,7 +3,7 @@
 //   M D w            mag7_of(D, w)
 //   U D w nz         sum24_of(D, w, nz != 0)
 //   K n w s          cert_constants for inner dimension n, width w and the
-//                    digit form's kappa with s digits (s = 0: modular form,
+//                    kappa of s digits at width w (s = 0: modular form,
 //                    kappa = 0): prints k1 and k2 as %a hex floats
 //   C sa sb S k1 k2  cert_ok (k1, k2 as hex floats): prints 1 or 0
 // Driven by tests/test_guard.py.
@@ -33,7 +33,7 @@ int main() {
       int n, w, s;
       if (std::scanf("%d %d %d", &n, &w, &s) != 3) return 1;
       float k1, k2;
-      mmk::cert_constants(n, w, s > 0 ? mmk::digit_kappa(s) : 0.0, &k1, &k2);
+      mmk::cert_constants(n, w, s > 0 ? mmk::digit_kappa(s, w) : 0.0, &k1, &k2);
       std::printf("%a %a\n", static_cast<double>(k1), static_cast<double>(k2));
     } else if (op == 'C') {
       unsigned long long sa, sb;

@@ -36,10 +36,10 @@ def harness(tmp_path_factory):
     return run
 
 
-def kappa(s: int) -> Fr:
+def kappa(s: int, w: int) -> Fr:
     """Digit pairs (t, u), 1 <= t, u <= s, t + u = L >= s + 2, each at most
-    2^14 in magnitude, weigh 2^(2 - 8L) after scaling by 2^-2w, w = 8s - 1."""
-    return sum((Fr(2 * s + 1 - L) * Fr(2) ** (16 - 8 * L) for L in range(s + 2, 2 * s + 1)), Fr(0))
+    2^14 in magnitude, weigh 2^(8(2s - L)) 2^-2w after scaling by 2^-2w."""
+    return sum((Fr(2 * s + 1 - L) * Fr(2) ** (14 + 16 * s - 8 * L - 2 * w) for L in range(s + 2, 2 * s + 1)), Fr(0))
 
 
 def d_cases(rnd):
@@ -71,13 +71,13 @@ def test_sum_term_is_the_ceiling_of_its_upper_bound(harness):
 
 
 def exact_constants(n, w, s):
-    K1 = n * Fr(2) ** (23 - w) + n * (kappa(s) if s else 0) * Fr(2) ** (w + 25)
+    K1 = n * Fr(2) ** (23 - w) + n * (kappa(s, w) if s else 0) * Fr(2) ** (w + 25)
     K2 = Fr(n - 1) * Fr(2) ** (w - 42) / (1 + U)
     return K1, K2
 
 
 CONST_CASES = [(n, w, 0) for n in (1, 2, 3, 300, 2000, 65535) for w in (1, 30, 45, 49, 56, 62)] + \
-              [(n, 8 * s - 1, s) for n in (2, 500, 131071) for s in range(1, 9)]
+              [(n, 8 * s - d, s) for n in (2, 500, 131071) for s in range(1, 9) for d in (1, 2)]
 
 
 def test_constants_bound_the_exact_ones(harness):

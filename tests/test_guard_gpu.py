@@ -144,3 +144,46 @@ def test_zero_rows_and_columns_never_fail():
     C, (elements, problems) = run("modular", A, B)
     assert (elements, problems) == (0, 0)
     assert not C[3].any() and not C[:, 7].any()
+
+
+def replica_failures(A, B, w, kappa, margin):
+    """Elements whose certificate fails, restated on the host in FP64 from the
+    definitions in guard.cuh: fixed point D = RNE(v 2^(w - e)), magnitude
+    digits floor((|D| - 1/2) 2^(7-w)), sums of ceil((2|D| + 1) 2^(23-w)),
+    and the test (SA + SB) + K1 <= K2 (1 - margin) S."""
+    n = A.shape[1]
+    e = np.frexp(np.max(np.abs(A), 1))[1]
+    f = np.frexp(np.max(np.abs(B), 0))[1]
+    aA = np.abs(np.rint(np.ldexp(A, (w - e)[:, None]))).astype(np.int64)
+    aB = np.abs(np.rint(np.ldexp(B, (w - f)[None, :]))).astype(np.int64)
+    MA = np.where(aA > 0, (2 * aA - 1) >> (w - 6), 0)
+    MB = np.where(aB > 0, (2 * aB - 1) >> (w - 6), 0)
+    sh = w - 23
+    tA = ((2 * aA + 1) >> sh) + (((2 * aA + 1) & ((1 << sh) - 1)) != 0)
+    tB = ((2 * aB + 1) >> sh) + (((2 * aB + 1) & ((1 << sh) - 1)) != 0)
+    SA, SB = tA.sum(1).astype(np.float64), tB.sum(0).astype(np.float64)
+    S = MA.astype(np.float64) @ MB.astype(np.float64)
+    K1 = n * 2.0 ** (23 - w) + n * kappa * 2.0 ** (w + 25)
+    K2 = (n - 1) * 2.0 ** (w - 42) / (1 + U) * (1 - margin)
+    fail = SA[:, None] + SB[None, :] + K1 > K2 * S
+    fail &= (SA[:, None] > 0) & (SB[None, :] > 0)
+    return int(fail.sum())
+
+
+@pytest.mark.parametrize("mode,slices,n,seed", [("modular", 14, 2000, 0), ("modular", 14, 2000, 7),
+                                                ("modular", 15, 1000, 1), ("emulated", 7, 1000, 2)])
+def test_replaced_count_matches_a_host_replica_of_the_certificate(mode, slices, n, seed):
+    # The device may only be stricter than the exact rule (its FP32 test has a
+    # 2^-20 margin), and by no more than that margin.
+    A, B = workload.pair("loguniform20", seed, n)
+    _, (elements, problems) = run(mode, A, B, slices)
+    if mode == "modular":
+        w, kap = oracle.modular_beta(slices, n), 0.0
+    else:
+        w = 8 * slices - 1
+        kap = sum((2 * slices + 1 - L) * 2.0 ** (14 + 16 * slices - 8 * L - 2 * w)
+                  for L in range(slices + 2, 2 * slices + 1))
+    lo = replica_failures(A, B, w, kap, 0.0)
+    hi = replica_failures(A, B, w, kap, 2.0 ** -18)
+    assert problems == 0
+    assert lo <= elements <= hi, (lo, elements, hi)

@@ -2,8 +2,9 @@
 against exact rational arithmetic on the oracle's models of both forms.
 
 The product is Alg. 1's c_ik = sum_j a_ij b_jk (Sec. 3.1).  For every element
-of the modular model (oracle.fixed_gemm, width beta) and of the digit model
-(oracle.emu_gemm, s digits, width 8s - 1) this checks
+of the modular model (oracle.fixed_gemm, width beta), of the digit model
+(oracle.emu_gemm, s digits, width 8s - 1) and of the INT8 slice model
+(oracle.i8_gemm, s digits, width 8s - 2) this checks
   (1) |c^ - c| <= 2^(e_i + f_k) (u (R + E') + E'),
       E' = 2^(-w-1) (SA_i + SB_k) + n 2^(-2w-2) + n kappa   (kappa = 0 for the modular form),
   (2) wherever (1 + u) E' <= (n - 1) u R, |c^ - c| <= n u (|A||B|)_ik,
@@ -26,8 +27,8 @@ import oracle
 U = Fr(1, 2 ** 53)
 
 
-def kappa(s: int) -> Fr:
-    return sum((Fr(2 * s + 1 - L) * Fr(2) ** (16 - 8 * L) for L in range(s + 2, 2 * s + 1)), Fr(0))
+def kappa(s: int, w: int) -> Fr:
+    return sum((Fr(2 * s + 1 - L) * Fr(2) ** (14 + 16 * s - 8 * L - 2 * w) for L in range(s + 2, 2 * s + 1)), Fr(0))
 
 
 def e_of(v: float) -> int:
@@ -82,12 +83,13 @@ def random_pair(rnd, n, kind):
 def coherent_pair(rnd, n, w, digits_s=0):
     """Entries x' = (D + 0.499...) 2^-w with D chosen so that every row and
     column maximum is just below a power of two (e = 0): every fixed-point
-    rounding error is close to -1/2, and for the digit form every digit is 127
-    or -128 alike, so the dropped pairs all add with the same sign."""
+    rounding error is close to -1/2, and for a digit form every low digit is
+    127, so the dropped pairs all add with the same sign."""
     top = (1 << w) - 2
+    hi = 1 << (w - 8 * (digits_s - 1)) if digits_s else 0  # the leading digit is below this
     def entry():
         if digits_s:
-            D = sum(127 << (8 * t) for t in range(digits_s - 1)) + (rnd.randrange(60, 127) << (8 * (digits_s - 1)))
+            D = sum(127 << (8 * t) for t in range(digits_s - 1)) + (rnd.randrange(hi // 2, hi - 1) << (8 * (digits_s - 1)))
         else:
             D = rnd.randrange(top // 2, top)
         return (D + 0.499) / 2.0 ** w
@@ -113,7 +115,16 @@ def test_digit_model_obeys_the_bound(kind):
         A, B = random_pair(rnd, n, kind)
         for s in (1, 2, 4, 7):
             model = oracle.emu_gemm(A, B, s, nthreads=1)
-            check(A, B, 8 * s - 1, kappa(s), model)
+            check(A, B, 8 * s - 1, kappa(s, 8 * s - 1), model)
+
+
+@pytest.mark.parametrize("kind", ["uniform", "wide", "split_scales"])
+def test_int8_slice_model_obeys_the_bound(kind):
+    rnd = random.Random(17 + (hash(kind) & 0xFFFF))
+    for n in (1, 3, 9):
+        A, B = random_pair(rnd, n, kind)
+        for s in (1, 2, 4, 7):
+            check(A, B, 8 * s - 2, kappa(s, 8 * s - 2), oracle.i8_gemm(A, B, s, nthreads=1))
 
 
 def test_bound_is_nearly_attained_by_coherent_rounding():
@@ -124,8 +135,11 @@ def test_bound_is_nearly_attained_by_coherent_rounding():
     assert worst > 0.9  # halving the rounding term would be violated
     s = 2
     A, B = coherent_pair(rnd, n, 8 * s - 1, digits_s=s)
-    worst, _ = check(A, B, 8 * s - 1, kappa(s), oracle.emu_gemm(A, B, s, nthreads=1))
+    worst, _ = check(A, B, 8 * s - 1, kappa(s, 8 * s - 1), oracle.emu_gemm(A, B, s, nthreads=1))
     assert worst > 0.5  # the dropped pairs (kappa) carry most of it
+    A, B = coherent_pair(rnd, n, 8 * s - 2, digits_s=s)
+    worst, _ = check(A, B, 8 * s - 2, kappa(s, 8 * s - 2), oracle.i8_gemm(A, B, s, nthreads=1))
+    assert worst > 0.5
 
 
 def test_certificate_holds_for_typical_inputs_and_fails_for_split_scales():
