@@ -18,7 +18,7 @@
 // R is bounded below by 2^-14 S with S = sum_j M_A M_B, M = floor-ish(|v'| 2^7)
 // in [0, 127] (the "magnitude plane", multiplied exactly on the tensor cores
 // like any other plane); SA_i and SB_k are bounded above by integer sums of
-// ceil-ish(|v'| 2^24).  Scaling (*) by 2^(w + 25) gives the test
+// |v'| 2^24 (plus at most 1).  Scaling (*) by 2^(w + 25) gives the test
 //     (SA24_i + SB24_k) + K1 <= K2 S,
 //     K1 = n 2^(23 - w) + n kappa 2^(w + 25),   K2 = (n - 1) 2^(w - 42) / (1 + u),
 // evaluated in FP32 with margins that make it sufficient (see cert_ok).  An
@@ -33,25 +33,23 @@ namespace mmk {
 
 // Lower bound of |v'| 2^7 from the fixed-point integer D of width w (|v' 2^w -
 // D| <= 1/2): floor((|D| - 1/2) 2^(7-w)) for |D| >= 1, else 0; in [0, 127]
-// because |D| <= 2^w.
+// because |D| <= 2^w.  For w >= 7 and |D| = q 2^(w-7) + r that floor is q
+// when r >= 1 and q - 1 when r = 0, which is (|D| - 1) >> (w - 7).
 __host__ __device__ __forceinline__ uint32_t mag7_of(int64_t D, int w) {
   const uint64_t a = D < 0 ? 0ull - static_cast<uint64_t>(D) : static_cast<uint64_t>(D);
   if (a == 0) return 0u;
-  const uint64_t t = 2 * a - 1;  // (|D| - 1/2) 2^1
-  return static_cast<uint32_t>(w >= 6 ? t >> (w - 6) : t << (6 - w));
+  return static_cast<uint32_t>(w >= 7 ? (a - 1) >> (w - 7) : (2 * a - 1) << (6 - w));
 }
 
-// Upper bound of |v'| 2^24 from D (|v'| 2^w <= |D| + 1/2): ceil((2|D| + 1)
-// 2^(23-w)); 0 when v itself is zero (then D = 0 and v' = 0).
+// Upper bound of |v'| 2^24 from D (|v'| 2^w <= |D| + 1/2), 0 when v itself is
+// zero (then D = 0 and v' = 0).  For w >= 24, with |D| 2^(24-w) = q + f, f a
+// multiple of 2^(24-w) below 1: (|D| + 1/2) 2^(24-w) = q + f + 2^(23-w) <= q + 1,
+// so q + 1 = (|D| >> (w - 24)) + 1 bounds it; below, (2|D| + 1) 2^(23-w) is an
+// integer and exact.
 __host__ __device__ __forceinline__ uint64_t sum24_of(int64_t D, int w, bool v_nonzero) {
   if (!v_nonzero) return 0ull;
   const uint64_t a = D < 0 ? 0ull - static_cast<uint64_t>(D) : static_cast<uint64_t>(D);
-  const uint64_t t = 2 * a + 1;
-  if (w >= 23) {
-    const int sh = w - 23;
-    return (t >> sh) + ((t & ((1ull << sh) - 1)) != 0 ? 1ull : 0ull);
-  }
-  return t << (23 - w);
+  return w >= 24 ? (a >> (w - 24)) + 1 : (2 * a + 1) << (23 - w);
 }
 
 // The certificate test for one element: true when (*) holds for sure.  sa, sb

@@ -221,11 +221,11 @@ __global__ void __launch_bounds__(32) native_fp64_small_kernel(const __grid_cons
 
 // ---------------------------------------------------------------------------
 // Guard kernel: after an emulated launch, recomputes in native FP64 what its
-// accuracy certificate (guard.cuh) could not vouch for.  Blocks [0,
-// total_tiles) are the 64 x 64 tiles of every guarded problem: a problem with
-// more failures than its guard_limit is recomputed whole, by the tiles above
-// (each within gamma_k |A||B| of the exact product).  The remaining blocks
-// recompute the listed elements of the other problems one warp each: lanes
+// accuracy certificate (guard.cuh) could not vouch for.  A problem with more
+// failures than its guard_limit is recomputed whole, its 64 x 64 tiles
+// (numbered from guard_tile_begin, total_tiles in all) strided over the
+// blocks, each tile within gamma_k |A||B| of the exact product.  Then the
+// blocks recompute the listed elements of the other problems one warp each: lanes
 // take every 32nd term in increasing order with fused multiply-adds, then a
 // butterfly sum -- at most ceil(k/32) + 5 <= k roundings on any path for k >=
 // 6 (and for k < 6 at most 1 + ceil(log2 k) <= k, the idle lanes adding exact
@@ -251,29 +251,31 @@ __global__ void __launch_bounds__(NT_THREADS, 4) guard_kernel(const __grid_const
   __shared__ int nactive;
   const Problem* P0 = guard_problem(args, 0);
   if (*reinterpret_cast<volatile int*>(P0->guard_total) == 0) return;  // shared by the launch's problems
-  if (static_cast<int>(blockIdx.x) < args.total_tiles) {
+  // Problems recomputed whole: their 64 x 64 tiles, strided over the blocks.
+  for (int tile = blockIdx.x; tile < args.total_tiles; tile += gridDim.x) {
     int lo = 0, hi = args.count - 1;  // problem owning this tile
     while (lo < hi) {
       const int mid = (lo + hi + 1) >> 1;
-      if (guard_problem(args, mid)->guard_tile_begin <= static_cast<int>(blockIdx.x)) lo = mid; else hi = mid - 1;
+      if (guard_problem(args, mid)->guard_tile_begin <= tile) lo = mid; else hi = mid - 1;
     }
     const Problem* P = guard_problem(args, lo);
     const int tn = (P->n + NT_BN - 1) / NT_BN, tm = (P->m + NT_BM - 1) / NT_BM;
-    const int local = blockIdx.x - P->guard_tile_begin;
-    if (!P->guard || local < 0 || local >= tm * tn || *P->guard_count <= P->guard_limit) return;
+    const int local = tile - P->guard_tile_begin;
+    if (!P->guard || local < 0 || local >= tm * tn || *P->guard_count <= P->guard_limit) continue;
     if (local == 0 && threadIdx.x == 0) {
       atomicAdd(&args.stats[0], static_cast<unsigned long long>(P->m) * P->n);
       atomicAdd(&args.stats[1], 1ull);
     }
-    native_tile_any(P, (local / tn) * NT_BM, (local % tn) * NT_BN, As, Bs);
-    return;
+    native_tile_any(P, (local / tn) * NT_BM, (local % tn) * NT_BN, As, Bs);  // uniform over the block
   }
+  // Listed elements of the other problems, one warp each.
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const long long wid = static_cast<long long>(blockIdx.x - args.total_tiles) * (NT_THREADS / 32) + warp;
-  const long long nw = static_cast<long long>(gridDim.x - args.total_tiles) * (NT_THREADS / 32);
+  const long long wid = static_cast<long long>(blockIdx.x) * (NT_THREADS / 32) + warp;
+  const long long nw = static_cast<long long>(gridDim.x) * (NT_THREADS / 32);
   unsigned long long done = 0;
   for (int base = 0; base < args.count; base += NT_THREADS) {
     // this round's problems with listed elements, found in parallel
+    __syncthreads();
     if (threadIdx.x == 0) nactive = 0;
     __syncthreads();
     const int p = base + threadIdx.x;
@@ -289,10 +291,13 @@ __global__ void __launch_bounds__(NT_THREADS, 4) guard_kernel(const __grid_const
       const double* A = P->A;
       const double* B = P->B;
       const size_t lda = P->lda, ldb = P->ldb;
+      const int kdim = P->k;
       for (long long e = wid; e < cnt; e += nw) {
         const int2 ik = P->guard_list[e];
         double acc = 0.0;
-        for (int j = lane; j < P->k; j += 32) {
+        // the loads of eight steps go out together; the sum stays one chain per lane
+#pragma unroll 8
+        for (int j = lane; j < kdim; j += 32) {
           const double x = P->ta ? A[static_cast<size_t>(j) * lda + ik.x] : A[static_cast<size_t>(ik.x) * lda + j];
           const double y = P->tb ? B[static_cast<size_t>(ik.y) * ldb + j] : B[static_cast<size_t>(j) * ldb + ik.y];
           acc = fma(x, y, acc);
@@ -303,7 +308,6 @@ __global__ void __launch_bounds__(NT_THREADS, 4) guard_kernel(const __grid_const
         ++done;
       }
     }
-    __syncthreads();
   }
   if (lane == 0 && done) atomicAdd(&args.stats[0], done);
 }
@@ -363,8 +367,7 @@ cudaError_t guard_launch(const Problem* table, const Problem* single, int count,
   args.count = count;
   args.total_tiles = total_tiles;
   args.stats = stats;
-  const int fix_blocks = 2 * num_sms;
-  guard_kernel<<<total_tiles + fix_blocks, NT_THREADS, 0, stream>>>(args);
+  guard_kernel<<<4 * num_sms, NT_THREADS, 0, stream>>>(args);
   return cudaGetLastError();
 }
 

@@ -149,8 +149,8 @@ def test_zero_rows_and_columns_never_fail():
 def replica_failures(A, B, w, kappa, margin):
     """Elements whose certificate fails, restated on the host in FP64 from the
     definitions in guard.cuh: fixed point D = RNE(v 2^(w - e)), magnitude
-    digits floor((|D| - 1/2) 2^(7-w)), sums of ceil((2|D| + 1) 2^(23-w)),
-    and the test (SA + SB) + K1 <= K2 (1 - margin) S."""
+    digits floor((|D| - 1/2) 2^(7-w)), sums of (|D| >> (w - 24)) + 1 (w >= 24
+    here), and the test (SA + SB) + K1 <= K2 (1 - margin) S."""
     n = A.shape[1]
     e = np.frexp(np.max(np.abs(A), 1))[1]
     f = np.frexp(np.max(np.abs(B), 0))[1]
@@ -158,10 +158,10 @@ def replica_failures(A, B, w, kappa, margin):
     aB = np.abs(np.rint(np.ldexp(B, (w - f)[None, :]))).astype(np.int64)
     MA = np.where(aA > 0, (2 * aA - 1) >> (w - 6), 0)
     MB = np.where(aB > 0, (2 * aB - 1) >> (w - 6), 0)
-    sh = w - 23
-    tA = ((2 * aA + 1) >> sh) + (((2 * aA + 1) & ((1 << sh) - 1)) != 0)
-    tB = ((2 * aB + 1) >> sh) + (((2 * aB + 1) & ((1 << sh) - 1)) != 0)
-    SA, SB = tA.sum(1).astype(np.float64), tB.sum(0).astype(np.float64)
+    SA = ((aA >> (w - 24)) + 1).sum(1).astype(np.float64)  # every entry of a nonzero row adds at least 1
+    SB = ((aB >> (w - 24)) + 1).sum(0).astype(np.float64)
+    SA[~np.any(A != 0, 1)] = 0.0  # a zero row or column is exempt
+    SB[~np.any(B != 0, 0)] = 0.0
     S = MA.astype(np.float64) @ MB.astype(np.float64)
     K1 = n * 2.0 ** (23 - w) + n * kappa * 2.0 ** (w + 25)
     K2 = (n - 1) * 2.0 ** (w - 42) / (1 + U) * (1 - margin)
