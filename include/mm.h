@@ -30,6 +30,13 @@
  *                   wide run on CTA pairs (paired tcgen05.mma, 256 x 256
  *                   tiles) instead of single CTAs: same results, measured
  *                   slower on GB300, hence off by default.
+ *   MM_EMU_INT8     INT8 slice emulation: as MM_EMU_BF16 with s digits of
+ *                   the (8s - 2)-bit fixed-point value, every digit a signed
+ *                   byte (Ozaki-style slices with int32 accumulation), the
+ *                   digit products on the integer tensor path (mma.sync
+ *                   m16n8k32 s8, the only 8-bit integer MMA of sm_103a) and
+ *                   recombined as the digit form is.  Far slower than the
+ *                   bf16 forms on GB300; never chosen by MM_AUTO.
  * MM_AUTO picks one per problem (see mm_config).
  *
  * Conventions for every call:
@@ -74,6 +81,7 @@ typedef enum {
 typedef enum {
   MM_NATIVE_FP64 = 0,
   MM_EMU_BF16 = 1,
+  MM_EMU_INT8 = 2,
   MM_AUTO = 3,
   MM_EMU_MODULAR = 4
 } mm_mode;
@@ -85,8 +93,8 @@ typedef enum {
 
 typedef struct {
   mm_mode mode;          /* default MM_AUTO */
-  int slices;            /* digit count s in 1..8 (MM_EMU_BF16), moduli k in 2..16
-                            (MM_EMU_MODULAR); 0 = chosen per problem */
+  int slices;            /* digit count s in 1..8 (MM_EMU_BF16, MM_EMU_INT8), moduli k in
+                            2..16 (MM_EMU_MODULAR); 0 = chosen per problem */
   unsigned flags;        /* MM_FLAG_* */
   const char* tune_path; /* optional autotune table (text file); NULL = built-in table */
 } mm_config;
@@ -195,7 +203,8 @@ mm_status mm_guard_read(mm_handle h, void* stream, long long* elements, long lon
 
 /* Form and slice count the handle would use for an N x N problem (after
  * AUTO): form 0 = native FP64, 1 = digit emulation (slices = digits s),
- * 2 = modular emulation (slices = moduli k). */
+ * 2 = modular emulation (slices = moduli k), 3 = INT8 slice emulation
+ * (slices = digits s). */
 mm_status mm_plan(mm_handle h, int N, int* form, int* slices);
 
 /* Parameters of the modular form with k moduli at size N, computed on the
@@ -222,6 +231,12 @@ mm_status mm_profile_read(mm_handle h, double out_ms[4], int launches[4]);
  * (independent chains of mma.sync m16n8k4 f64, and of scalar FP64 FMA),
  * in TFLOP/s: the roof of the native form.  Blocks for a few milliseconds. */
 mm_status mm_probe_fp64_peak(mm_handle h, double* dmma_tflops, double* dfma_tflops);
+
+/* Measures the 8-bit integer MMA throughput of this GPU with a calibration
+ * kernel (independent chains of mma.sync m16n8k32 s8, the instruction of the
+ * INT8 slice form), in tera-operations per second (2 per multiply-add): the
+ * roof of MM_EMU_INT8.  Blocks for a few milliseconds. */
+mm_status mm_probe_int8_peak(mm_handle h, double* tops);
 
 /* Failure-detection self-test: enqueues a kernel that waits on an mbarrier
  * nothing ever arrives on, through the same time-bounded wait every pipeline

@@ -22,6 +22,7 @@ from . import build as _build
 
 NATIVE_FP64 = 0
 EMU_BF16 = 1
+EMU_INT8 = 2
 AUTO = 3
 EMU_MODULAR = 4
 FLAG_NO_GRAPH = 1
@@ -34,9 +35,9 @@ STATUS_NAMES = {
 }
 
 _MODES = {"native": NATIVE_FP64, "emulated": EMU_BF16, "emu": EMU_BF16, "auto": AUTO,
-          "modular": EMU_MODULAR}
-# forms reported by plan(): native FP64, digit emulation, modular emulation
-FORMS = ("native", "emulated", "modular")
+          "modular": EMU_MODULAR, "int8": EMU_INT8}
+# forms reported by plan(): native FP64, digit emulation, modular emulation, INT8 slices
+FORMS = ("native", "emulated", "modular", "int8")
 
 _lock = threading.Lock()
 _lib = None
@@ -56,7 +57,7 @@ class _Config(ctypes.Structure):
 SYMBOLS = ("mm_create", "mm_destroy", "mm_gemm", "mm_gemm_grouped", "mm_gemm_ex", "mm_gemm_grouped_ex",
            "mm_gemm_host", "mm_gemm_grouped_host",
            "mm_status_get", "mm_guard_read",
-           "mm_last_error", "mm_plan", "mm_profile_read", "mm_probe_fp64_peak", "mm_selftest_wait", "mm_split",
+           "mm_last_error", "mm_plan", "mm_profile_read", "mm_probe_fp64_peak", "mm_probe_int8_peak", "mm_selftest_wait", "mm_split",
            "mm_split_noalloc",
            "mm_level_sums", "mm_recombine", "mm_modular_params")
 SPLIT_NOALLOC_MAX_N = 65536
@@ -100,6 +101,7 @@ def lib(build_if_needed: bool = True) -> ctypes.CDLL:
             L.mm_recombine.argtypes = [vp, ci, ci, vp, vp, vp, vp, vp]
             L.mm_profile_read.argtypes = [vp, ctypes.POINTER(cd), ctypes.POINTER(ci)]
             L.mm_probe_fp64_peak.argtypes = [vp, ctypes.POINTER(cd), ctypes.POINTER(cd)]
+            L.mm_probe_int8_peak.argtypes = [vp, ctypes.POINTER(cd)]
             L.mm_selftest_wait.argtypes = [vp, ci, vp]
             L.mm_modular_params.argtypes = [ci, ci, ctypes.POINTER(ci), ctypes.POINTER(ci)]
             for name in SYMBOLS:
@@ -347,6 +349,12 @@ class Handle:
         a, b = ctypes.c_double(), ctypes.c_double()
         self._raise(self._lib.mm_probe_fp64_peak(self._h, ctypes.byref(a), ctypes.byref(b)))
         return a.value, b.value
+
+    def probe_int8_peak(self) -> float:
+        """Measured 8-bit integer mma.sync roof of this GPU, tera-operations per second."""
+        a = ctypes.c_double()
+        self._raise(self._lib.mm_probe_int8_peak(self._h, ctypes.byref(a)))
+        return a.value
 
     def selftest_wait(self, timeout_ms: int = 200, stream=None):
         """Enqueues the bounded-wait self-test (see mm_selftest_wait)."""

@@ -31,8 +31,8 @@ struct Problem {
   int tiles_m;      // tiles along rows of C
   int tiles_n;      // tiles along columns of C
   // split-precision emulation only
-  uint16_t* a_slices;  // [s][m_pad][k_pad] bf16 digits of A (K-major)
-  uint16_t* b_slices;  // [s][n_pad][k_pad] bf16 digits of B^T (K-major)
+  uint16_t* a_slices;  // [s][m_pad][k_pad] bf16 digits of A (K-major; int8 digits when i8)
+  uint16_t* b_slices;  // [s][n_pad][k_pad] bf16 digits of B^T (K-major; int8 digits when i8)
   int* a_exp;          // [n] row exponents e_i
   int* b_exp;          // [n] column exponents f_k
   int m_pad;           // rows of an A plane (multiple of 128)
@@ -42,6 +42,7 @@ struct Problem {
   int absmax_begin;    // first block of this problem in the maxima kernel
   int s;               // digits per value (digit form, 1..8) or moduli (modular form, 2..16)
   int beta;            // modular form: fixed-point width of the operands; 0 = digit form
+  int i8;              // INT8 slice form: int8 digit planes of width 8s - 2 (a digit form with beta = 0)
   int groups;          // digit-pair groups per tile: work units per tile of the slice-product kernel
   int nslots;          // segment sums per tile (all groups together)
   int defer;           // 1: slots go to the per-tile buffer and a separate pass recombines them

@@ -72,18 +72,30 @@ __device__ __forceinline__ uint32_t bf16x2_of_digits(float lo, float hi) {
 // one 16-byte vector and adds the upper bounds of |v'| 2^24 to the row's sum
 // in shared memory.  (A zero row's sum is discarded later, from its maximum.)
 // `xor_lanes`: the lane distances (bits 1, 2, 4, ...) to the other lanes that
-// hold the same row, whose partial sums are added in first.
-__device__ __forceinline__ void guard_item(const long long (&D)[8], int width, uint16_t* mag_out,
+// hold the same row, whose partial sums are added in first.  kI8: the planes
+// hold signed bytes (the INT8 slice form) instead of bf16.
+template <bool kI8 = false>
+__device__ __forceinline__ void guard_item(const long long (&D)[8], int width, void* mag_out,
                                            unsigned long long* row_sum, bool lead, unsigned xor_lanes) {
-  uint32_t w[4];
   unsigned long long sum = 0;
+  if (kI8) {
+    uint32_t w[2] = {0u, 0u};
 #pragma unroll
-  for (int p = 0; p < 4; ++p) {
-    w[p] = bf16x2_of_digits(static_cast<float>(mag7_of(D[2 * p], width)),
-                            static_cast<float>(mag7_of(D[2 * p + 1], width)));
-    sum += sum24_of(D[2 * p], width, true) + sum24_of(D[2 * p + 1], width, true);
+    for (int q = 0; q < 8; ++q) {
+      w[q >> 2] |= mag7_of(D[q], width) << (8 * (q & 3));  // 0..127: the byte itself
+      sum += sum24_of(D[q], width, true);
+    }
+    *reinterpret_cast<uint2*>(mag_out) = make_uint2(w[0], w[1]);
+  } else {
+    uint32_t w[4];
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+      w[p] = bf16x2_of_digits(static_cast<float>(mag7_of(D[2 * p], width)),
+                              static_cast<float>(mag7_of(D[2 * p + 1], width)));
+      sum += sum24_of(D[2 * p], width, true) + sum24_of(D[2 * p + 1], width, true);
+    }
+    *reinterpret_cast<uint4*>(mag_out) = make_uint4(w[0], w[1], w[2], w[3]);
   }
-  *reinterpret_cast<uint4*>(mag_out) = make_uint4(w[0], w[1], w[2], w[3]);
   for (int o = 1; o < 32; o <<= 1)
     if (xor_lanes & static_cast<unsigned>(o)) sum += __shfl_xor_sync(0xffffffffu, sum, o);
   if (lead) atomicAdd(row_sum, sum);
@@ -244,6 +256,34 @@ __device__ __forceinline__ void write_digit_planes(const long long (&Ds)[SP_TILE
   }
 }
 
+// Phase 2 of the INT8 slice form: the same balanced base-256 digits of the
+// (8S - 2)-bit value, every one a signed byte (the leading one within
+// [-64, 64]); one 8-byte store per plane, 8 threads per 64-byte row.
+template <int S>
+__device__ __forceinline__ void write_digit_planes_i8(const long long (&Ds)[SP_TILE][SP_TILE + 1], uint8_t* dst,
+                                                      int r0, int c0, int k_pad, size_t plane, bool guard,
+                                                      unsigned long long* gsum) {
+  for (int item = threadIdx.x; item < SP_TILE * (SP_TILE / 8); item += SP_THREADS) {
+    const int r = item >> 3, cg = item & 7;
+    uint8_t* out = dst + static_cast<size_t>(r0 + r) * k_pad + c0 + cg * 8;
+    long long D[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) D[q] = Ds[r][cg * 8 + q];
+    if (guard) guard_item<true>(D, 8 * S - 2, out + S * plane, &gsum[r], cg == 0, 0x7u);
+    float dig[8][S];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) digits_of<S>(D[q], dig[q]);
+#pragma unroll
+    for (int t = 0; t < S; ++t) {
+      uint32_t w[2] = {0u, 0u};
+#pragma unroll
+      for (int q = 0; q < 8; ++q)
+        w[q >> 2] |= (static_cast<uint32_t>(static_cast<int>(dig[q][t])) & 0xFFu) << (8 * (q & 3));
+      *reinterpret_cast<uint2*>(out + t * plane) = make_uint2(w[0], w[1]);
+    }
+  }
+}
+
 // Phase 2 for the modular form with K moduli: the symmetric residues of D
 // modulo m_0..m_{K-1}, one 16-byte vector (8 values) per plane.  |D| <= 2^62
 // is cut into LIMBS limbs x_l of b bits carrying D's sign (five of 13 bits,
@@ -363,7 +403,7 @@ __global__ void __launch_bounds__(SP_THREADS, 3) split_kernel(const __grid_const
   const int n = P->n;
   const int S = P->s;
   const int beta = P->beta;
-  const int width = beta > 0 ? beta : 8 * S - 1;
+  const int width = beta > 0 ? beta : (P->i8 ? 8 * S - 2 : 8 * S - 1);
   const int kt = P->k_pad / SP_TILE;
   const int a_tiles = (P->m_pad / SP_TILE) * kt;
   int local = blockIdx.x - (args.table ? P->split_begin : 0);
@@ -432,6 +472,18 @@ __global__ void __launch_bounds__(SP_THREADS, 3) split_kernel(const __grid_const
       MM_RESIDUE_CASE(12) MM_RESIDUE_CASE(13) MM_RESIDUE_CASE(14) MM_RESIDUE_CASE(15)
       default: residue_tile<16>(r0, c0, width, Ds, dst, P->k_pad, plane, guard, gsum); break;
 #undef MM_RESIDUE_CASE
+    }
+  } else if (P->i8) {
+    uint8_t* d8 = reinterpret_cast<uint8_t*>(dst);
+    switch (S) {
+      case 1: write_digit_planes_i8<1>(Ds, d8, r0, c0, P->k_pad, plane, guard, gsum); break;
+      case 2: write_digit_planes_i8<2>(Ds, d8, r0, c0, P->k_pad, plane, guard, gsum); break;
+      case 3: write_digit_planes_i8<3>(Ds, d8, r0, c0, P->k_pad, plane, guard, gsum); break;
+      case 4: write_digit_planes_i8<4>(Ds, d8, r0, c0, P->k_pad, plane, guard, gsum); break;
+      case 5: write_digit_planes_i8<5>(Ds, d8, r0, c0, P->k_pad, plane, guard, gsum); break;
+      case 6: write_digit_planes_i8<6>(Ds, d8, r0, c0, P->k_pad, plane, guard, gsum); break;
+      case 7: write_digit_planes_i8<7>(Ds, d8, r0, c0, P->k_pad, plane, guard, gsum); break;
+      default: write_digit_planes_i8<8>(Ds, d8, r0, c0, P->k_pad, plane, guard, gsum); break;
     }
   } else {
     switch (S) {

@@ -152,6 +152,13 @@ cudaError_t emu_cert_launch(int bn, const CUtensorMap* mapA, const CUtensorMap* 
                             cudaStream_t stream);
 void emu_kernel_info(int bn, char* buf, size_t len);
 
+// emu_int8.cu: the INT8 slice form's digit-pair products (128 x 128 tiles,
+// slots always written for the separate recombination) and its certificate
+// launch; grids of up to i8_blocks_per_sm() blocks per SM
+int i8_blocks_per_sm();
+cudaError_t i8_gemm_launch(const EmuArgs& args, int grid, cudaStream_t stream);
+cudaError_t i8_cert_launch(const EmuArgs& args, int grid, cudaStream_t stream);
+
 // recombine.cu
 cudaError_t slots_recombine_launch(int bn, const EmuArgs& args, int total_tiles, cudaStream_t stream);
 cudaError_t mod_recombine_launch(int bn, const EmuArgs& args, int tile0, int ntiles, cudaStream_t stream);
@@ -160,6 +167,7 @@ cudaError_t recombine_launch(int n, int s, const int32_t* levels, const int* e, 
 
 // probe.cu
 cudaError_t probe_fp64(int num_sms, double* sink, cudaStream_t stream, double* dmma, double* dfma);
+cudaError_t probe_int8(int num_sms, int* sink, cudaStream_t stream, double* tops);
 cudaError_t selftest_wait(int* status, uint64_t timeout_ns, int* gave_up, cudaStream_t stream);
 
 }  // namespace mmk

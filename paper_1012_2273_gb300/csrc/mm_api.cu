@@ -228,7 +228,7 @@ bool load_tune(mm_handle h, const std::string& path) {
     if (!(ss >> maxn >> p.form >> p.slices >> p.bn)) continue;
     if (!(ss >> p.groups)) p.groups = 0;
     const int max_slices = p.form == 2 ? mmk::MOD_COUNT : 8;
-    if (p.form < 0 || p.form > 2 || p.slices < (p.form == 2 ? 2 : 1) || p.slices > max_slices ||
+    if (p.form < 0 || p.form > 3 || p.slices < (p.form == 2 ? 2 : 1) || p.slices > max_slices ||
         (p.bn != 128 && p.bn != 256) || p.groups < 0 || p.groups > 36)
       return false;
     rows.push_back({static_cast<int>(std::min<long>(maxn, 1 << 30)), p});
@@ -247,12 +247,12 @@ Plan plan_for(mm_handle h, int n) {
       break;
     }
   if (h->cfg.mode == MM_NATIVE_FP64) p.form = 0;
-  if (h->cfg.mode == MM_EMU_BF16 || h->cfg.mode == MM_EMU_MODULAR) {
-    const int want = h->cfg.mode == MM_EMU_BF16 ? 1 : 2;
+  if (h->cfg.mode == MM_EMU_BF16 || h->cfg.mode == MM_EMU_MODULAR || h->cfg.mode == MM_EMU_INT8) {
+    const int want = h->cfg.mode == MM_EMU_BF16 ? 1 : h->cfg.mode == MM_EMU_MODULAR ? 2 : 3;
     if (p.form != want) {
       // a table row of another form: keep its tile width, take this form's
       // default count
-      p.slices = want == 1 ? 7 : 16;
+      p.slices = want == 2 ? 16 : 7;
       p.groups = 0;
     }
     p.form = want;
@@ -260,6 +260,7 @@ Plan plan_for(mm_handle h, int n) {
   }
   if (h->cfg.slices > 0) p.slices = h->cfg.slices;
   if (p.form != 0 && n < 256) p.bn = 128;
+  if (p.form == 3) p.bn = 128;  // the INT8 kernel's tiles are 128 x 128
   return p;
 }
 
@@ -403,12 +404,14 @@ mm_status layout_group(mm_handle h, EmuGroup& g, char* base) {
     work += static_cast<long long>(p.tiles_m) * p.tiles_n * mmk::problem_pairs(p) * (p.k_pad / 64);
     // planes: s digits or residues, plus the magnitude plane when guarded
     const int planes = p.s + (g.guard ? 1 : 0);
+    const size_t elt = g.form == 3 ? 1 : 2;  // int8 or bf16 digits
     p.guard = g.guard ? 1 : 0;
-    const size_t a_sl = ar.take(static_cast<size_t>(planes) * p.m_pad * p.k_pad * 2);
-    const size_t b_sl = ar.take(static_cast<size_t>(planes) * p.n_pad * p.k_pad * 2);
+    p.i8 = g.form == 3 ? 1 : 0;
+    const size_t a_sl = ar.take(static_cast<size_t>(planes) * p.m_pad * p.k_pad * elt);
+    const size_t b_sl = ar.take(static_cast<size_t>(planes) * p.n_pad * p.k_pad * elt);
     if (g.guard) {
       // certificate constants for inner dimension k and width w (guard.cuh)
-      const int w = g.form == 2 ? p.beta : 8 * p.s - 1;
+      const int w = g.form == 2 ? p.beta : g.form == 3 ? 8 * p.s - 2 : 8 * p.s - 1;
       mmk::cert_constants(p.k, w, g.form == 2 ? 0.0 : mmk::digit_kappa(p.s, w), &p.cert_k1, &p.cert_k2);
       // more failures than a quarter of the outputs: recompute the whole
       // problem natively (then the per-element list would cost about as much)
@@ -498,7 +501,8 @@ mm_status layout_group(mm_handle h, EmuGroup& g, char* base) {
     }
     // Short tiles (small N) leave the recombination to a separate pass: done
     // in the epilogue it stalls the tensor pipe for a large share of the tile.
-    p.defer = p.k < kDeferBelowN ? 1 : 0;  // short k loops: few k-blocks per tile
+    // (the INT8 kernel always leaves the recombination to the separate pass)
+    p.defer = (p.k < kDeferBelowN || g.form == 3) ? 1 : 0;  // short k loops: few k-blocks per tile
     if (G > 1 || p.defer) {
       p.slot_base = g.tilebuf_elems;
       g.tilebuf_elems += static_cast<long long>(tiles) * p.nslots * slot;
@@ -529,6 +533,7 @@ mm_status layout_group(mm_handle h, EmuGroup& g, char* base) {
     g.total_units = g.ps[0].tiles_m * g.ps[0].tiles_n / (g.pair ? 2 : 1) * g.ps[0].groups;
   }
   g.grid = g.pair ? 2 * emu_grid(h, std::min(g.total_units, h->num_sms / 2)) : emu_grid(h, g.total_units);
+  if (g.form == 3) g.grid = std::max(1, std::min(g.total_units, mmk::i8_blocks_per_sm() * h->num_sms));
   // The certificate's own launch: one unit per tile, k-blocks as the cost,
   // longest first (grouped calls list them; a single problem numbers them).
   g.cert_units.clear();
@@ -582,8 +587,8 @@ mm_status layout_group(mm_handle h, EmuGroup& g, char* base) {
   g.bytes = ar.off;
   g.base = base;
   if (base) {
-    g.maps.resize(2 * g.ps.size());
-    for (size_t i = 0; i < g.ps.size(); ++i) {
+    g.maps.assign(2 * g.ps.size(), CUtensorMap{});
+    for (size_t i = 0; i < g.ps.size() && g.form != 3; ++i) {  // (the INT8 kernel copies with cp.async)
       const Problem& p = g.ps[i];
       const long planes = p.s + (g.guard ? 1 : 0);
       if (!make_plane_map(&g.maps[2 * i], p.a_slices, p.k_pad, planes * p.m_pad, 128) ||
@@ -647,14 +652,17 @@ mm_status run_group(mm_handle h, const EmuGroup& g, const Problem* d_table, cons
       cert_forked = true;
     }
     const long m_c = prof_start(h, cs, KIND_SLICE_GEMM);
-    const cudaError_t ce = mmk::emu_cert_launch(g.bn, &g.maps[0], &g.maps[1], c, emu_grid(h, g.cert_total), cs);
+    const cudaError_t ce =
+        g.form == 3 ? mmk::i8_cert_launch(c, std::min(g.cert_total, mmk::i8_blocks_per_sm() * h->num_sms), cs)
+                    : mmk::emu_cert_launch(g.bn, &g.maps[0], &g.maps[1], c, emu_grid(h, g.cert_total), cs);
     prof_end(h, cs, m_c);
     if (ce != cudaSuccess) return cuda_fail(h, ce, "certificate launch");
     if (cert_forked) MM_CUDA(h, cudaEventRecord(h->cert_join, cs));
   }
   const long m_gemm = prof_start(h, stream, KIND_SLICE_GEMM);
-  const cudaError_t le = g.pair ? mmk::mod_pair_gemm_launch(&g.maps[0], &g.maps[1], a, g.grid, stream)
-                                : mmk::emu_gemm_launch(g.bn, g.form == 2, &g.maps[0], &g.maps[1], a, g.grid, stream);
+  const cudaError_t le = g.form == 3 ? mmk::i8_gemm_launch(a, g.grid, stream)
+                        : g.pair    ? mmk::mod_pair_gemm_launch(&g.maps[0], &g.maps[1], a, g.grid, stream)
+                                    : mmk::emu_gemm_launch(g.bn, g.form == 2, &g.maps[0], &g.maps[1], a, g.grid, stream);
   prof_end(h, stream, m_gemm);
   if (le != cudaSuccess) {
     char info[512];
@@ -789,7 +797,7 @@ mm_status grouped_impl(mm_handle h, const std::vector<Problem>& probs, cudaStrea
     for (size_t i = 1; i < emu_plans.size(); ++i)
       if (plan_size(emu_plans[i].first) > plan_size(emu_plans[big].first)) big = i;
     const int bn = emu_plans[big].second.bn;
-    for (auto& ep : emu_plans) emu[{ep.second.form, bn, ep.second.groups}].push_back(ep.first);
+    for (auto& ep : emu_plans) emu[{ep.second.form, ep.second.form == 3 ? 128 : bn, ep.second.groups}].push_back(ep.first);
   }
   // Native problems: 64 x 64 tiles, or 16 x 16 tiles below 512 (two launches).
   std::vector<Problem> nat_small;
@@ -1076,7 +1084,7 @@ mm_status mm_create(mm_handle* out, const mm_config* cfg) {
     h->cfg.tune_path = nullptr;
   }
   if (h->cfg.mode != MM_NATIVE_FP64 && h->cfg.mode != MM_EMU_BF16 && h->cfg.mode != MM_AUTO &&
-      h->cfg.mode != MM_EMU_MODULAR) {
+      h->cfg.mode != MM_EMU_MODULAR && h->cfg.mode != MM_EMU_INT8) {
     delete h;
     return MM_ERR_INVALID;
   }
@@ -1175,6 +1183,13 @@ mm_status mm_probe_fp64_peak(mm_handle h, double* dmma_tflops, double* dfma_tflo
   if (!h || !dmma_tflops || !dfma_tflops) return MM_ERR_INVALID;
   if (!h->probe_sink) MM_CUDA(h, cudaMalloc(&h->probe_sink, 64));
   MM_CUDA(h, mmk::probe_fp64(h->num_sms, h->probe_sink, h->cap_stream, dmma_tflops, dfma_tflops));
+  return MM_OK;
+}
+
+mm_status mm_probe_int8_peak(mm_handle h, double* tops) {
+  if (!h || !tops) return MM_ERR_INVALID;
+  if (!h->probe_sink) MM_CUDA(h, cudaMalloc(&h->probe_sink, 64));
+  MM_CUDA(h, mmk::probe_int8(h->num_sms, reinterpret_cast<int*>(h->probe_sink), h->cap_stream, tops));
   return MM_OK;
 }
 

@@ -1,9 +1,11 @@
-// probe.cu -- calibration kernels for the FP64 roof of the native form.
+// probe.cu -- calibration kernels for the FP64 roof of the native form and
+// the 8-bit integer roof of the INT8 slice form.
 //
-// GB300 publishes no FP64 tensor rate that this library can rely on, so the
-// native path's roofline denominator is measured: many independent chains of
-// mma.sync m16n8k4 f64 (the instruction the native kernel issues) and of
-// scalar FP64 FMA, enough warps to fill every SM.
+// GB300 publishes no FP64 or warp-level INT8 tensor rate that this library
+// can rely on, so the roofline denominators of the native and INT8 paths are
+// measured: many independent chains of mma.sync m16n8k4 f64 (the instruction
+// the native kernel issues), of scalar FP64 FMA, and of mma.sync m16n8k32
+// s8 (the INT8 kernel's instruction), enough warps to fill every SM.
 #include "launch.cuh"
 
 namespace mmk {
@@ -39,6 +41,52 @@ __global__ void probe_dfma_kernel(double* sink, int iters) {
 #pragma unroll
   for (int j = 0; j < 8; ++j) s += x[j];
   if (s == 1234567.0) sink[0] = s;
+}
+
+__global__ void probe_imma_kernel(int* sink, int iters) {
+  int c[4][4] = {};
+  const uint32_t a0 = 0x01020304u ^ threadIdx.x, a1 = 0x7F7F7F7Fu, b0 = 0x01010101u, b1 = 0x02020202u;
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      asm volatile(
+          "mma.sync.aligned.m16n8k32.row.col.s32.s8.s8.s32 {%0,%1,%2,%3}, {%4,%5,%4,%5}, {%6,%7}, {%0,%1,%2,%3};"
+          : "+r"(c[j][0]), "+r"(c[j][1]), "+r"(c[j][2]), "+r"(c[j][3])
+          : "r"(a0), "r"(a1), "r"(b0), "r"(b1));
+  }
+  int s = 0;
+#pragma unroll
+  for (int j = 0; j < 4; ++j)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) s += c[j][q];
+  if (s == 1234567) sink[0] = s;
+}
+
+// Runs the 8-bit integer probe on `stream`; returns tera-operations per second
+// (2 per multiply-add) through tops.
+cudaError_t probe_int8(int num_sms, int* sink, cudaStream_t stream, double* tops) {
+  const int blocks = num_sms * 4, threads = 256, iters = 4000;
+  cudaEvent_t e0, e1;
+  cudaError_t err = cudaEventCreate(&e0);
+  if (err != cudaSuccess) return err;
+  err = cudaEventCreate(&e1);
+  if (err != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return err;
+  }
+  float ms = 0;
+  probe_imma_kernel<<<blocks, threads, 0, stream>>>(sink, iters / 10);  // warm-up
+  cudaEventRecord(e0, stream);
+  probe_imma_kernel<<<blocks, threads, 0, stream>>>(sink, iters);
+  cudaEventRecord(e1, stream);
+  cudaEventSynchronize(e1);
+  cudaEventElapsedTime(&ms, e0, e1);
+  // one m16n8k32 is 16 * 8 * 32 multiply-adds
+  *tops = static_cast<double>(blocks) * (threads / 32) * iters * 4 * (2.0 * 16 * 8 * 32) / (ms * 1e-3) / 1e12;
+  err = cudaGetLastError();
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return err;
 }
 
 // Failure-detection self-test: waits on an mbarrier that nothing ever arrives

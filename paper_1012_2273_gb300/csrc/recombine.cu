@@ -59,7 +59,8 @@ __global__ void __launch_bounds__(256) slots_recombine_kernel(const __grid_const
 #pragma unroll
   for (int k = 0; k < 4; ++k) i128_shift_add64(th[k], tl[k], 0, lv[k]);
   const int tail = 8 * (s + 1 - curL);
-  const int base_scale = P->a_exp[row] - 8 * s - 6;
+  // 2^(e + f - 2w + 8(s - 1)): w = 8s - 1 (bf16 digits) or 8s - 2 (int8 digits)
+  const int base_scale = P->a_exp[row] - 8 * s - (P->i8 ? 4 : 6);
   double* crow = P->C + static_cast<size_t>(row) * P->ldc;
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
