@@ -11,9 +11,14 @@ graph).  Flops are counted the paper's way, N^2 (2N - 1) per product.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
-Prints one JSON line on rank 0.  `--impl reference` times the CPU oracle (the
-plain triple loop of Alg. 1 on all host cores) on a bounded sample of the same
-workload instead.
+Prints one JSON line on rank 0.  Beside the headline it carries, untimed by
+the headline: each form on each size of the sweep and of the precision
+configuration (N = 4096, 8192), the 1024-problem batch (configuration 4) by
+size bucket, the large configuration (64 problems up to N = 16384 and one
+N = 16384), the accuracy certificate's cost, and the oracle's check of the
+step's output.  `--impl reference` times the CPU oracle (the plain triple
+loop of Alg. 1 on all host cores) on a bounded sample of the same workload
+instead.
 """
 from __future__ import annotations
 
@@ -194,7 +199,7 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
-KERNEL_SOURCES = ("emu_gemm.cu", "common.cuh", "launch.cuh", "modular.cuh", "recombine.cuh")
+KERNEL_SOURCES = ("emu_gemm.cu", "common.cuh", "launch.cuh", "modular.cuh", "recombine.cuh", "guard.cuh")
 
 
 def source_digest() -> str:
@@ -280,9 +285,11 @@ def run_ours(args, dist: Dist):
             launches_per_step = sum(v[1] for v in p.values())
     hp.check()
     emu_sizes = [n for n in SWEEP if plan[n][0] != 0]
-    # tensor products per size: s(s+1)/2 digit pairs, or k residue products
+    # tensor products per size: s(s+1)/2 digit pairs, or k residue products,
+    # plus the certificate's product of the magnitude planes (its own launch,
+    # timed with the slice products)
     pairs_of = {n: plan[n][1] * (plan[n][1] + 1) // 2 if plan[n][0] == 1 else plan[n][1] for n in emu_sizes}
-    tensor_flops = sum(pairs_of[n] * 2 * n ** 3 for n in emu_sizes)
+    tensor_flops = sum((pairs_of[n] + 1) * 2 * n ** 3 for n in emu_sizes)
     gemm_ms = statistics.mean(kinds["slice_products"]) if emu_sizes else None
     digest = source_digest()
     traffic, traffic_meta = profiled_traffic(digest)
@@ -291,7 +298,8 @@ def run_ours(args, dist: Dist):
         achieved = tensor_flops / (gemm_ms / 1e3) / 1e12
         peak = peaks["bf16_tflops"]
         roofline = {"kernel": "emu_gemm_kernel (tcgen05 bf16 digit or residue products with exact int32 "
-                              "accumulation; every instantiation the step launches)",
+                              "accumulation, and the certificate's magnitude product; every launch of it "
+                              "the step makes)",
                     "bound": "tensor", "achieved": round(achieved, 2), "peak": peak, "unit": "TFLOP/s",
                     "frac": round(achieved / peak, 4),
                     "peak_source": f"{peaks['source']} bf16 dense burst (MEASURED_PEAKS.json bf16_tflops)",
@@ -301,12 +309,26 @@ def run_ours(args, dist: Dist):
                     "note": "bf16 products of 2N^3 flops each: " + ", ".join(
                         f"N={n}: " + (f"digits s={plan[n][1]}, {pairs_of[n]} pairs" if plan[n][0] == 1
                                       else f"moduli k={plan[n][1]}, {pairs_of[n]} residue products")
+                        + " + 1 certificate product"
                         for n in emu_sizes)}
 
-    # per-N comparison of the two forms (single calls, L2 flushed)
-    per_n = per_size(mm, As, Bs, Cs, flush, stream)
+    # certificate: elements the step's calls sent to native FP64 (uniform
+    # inputs: none), and the step without it (MM_FLAG_NO_GUARD) for context
+    guard_replaced, guard_problems = h.guard_read()
+    hu = mm.Handle("auto", flags=mm.FLAG_NO_GUARD)
+    unguarded_ms = timed_calls(lambda: step(hu), flush, stream, 20)
+    hu.check()
+    hu.close()
+
+    # per-N comparison of the forms (single calls, L2 flushed), the paper's
+    # sweep and the precision configuration's larger sizes
+    big = [workload.pair_torch(DIST, rank_seed, n, dev) for n in workload.PRECISION_SIZES[1:]]
+    per_n = per_size(mm, As + [a for a, _ in big], Bs + [b for _, b in big],
+                     Cs + [torch.empty_like(a) for a, _ in big], flush, stream)
+    del big
     hn = mm.Handle("native")
     dmma_peak, dfma_peak = hn.probe_fp64_peak()
+    int8_peak = hn.probe_int8_peak()
     for n, d in per_n.items():
         N = int(n)
         d["native_frac_of_dmma_peak"] = round(d["native_tflops"] / dmma_peak, 4)
@@ -315,7 +337,14 @@ def run_ours(args, dist: Dist):
         if "modular_moduli" in d:  # bf16 tensor work of the whole call (split and recombination included)
             k = d["modular_moduli"]
             d["modular_tensor_frac_whole_call"] = round(
-                k * 2 * N ** 3 / (d["modular_ms"] / 1e3) / 1e12 / peaks["bf16_tflops"], 4)
+                (k + 1) * 2 * N ** 3 / (d["modular_ms"] / 1e3) / 1e12 / peaks["bf16_tflops"], 4)
+        if "int8_slices" in d:  # 8-bit integer MMA work of the whole call, digit pairs and the certificate's
+            s8 = d["int8_slices"]
+            d["int8_tops_whole_call"] = round((s8 * (s8 + 1) // 2 + 1) * 2 * N ** 3 / (d["int8_ms"] / 1e3) / 1e12, 2)
+            d["int8_frac_of_imma_probe"] = round(d["int8_tops_whole_call"] / int8_peak, 4)
+
+    batch = batch_block(mm, dev, flush, stream, peaks, dmma_peak)
+    large = large_block(mm, dev, flush, stream)
 
     # end to end through the public API on host buffers (pinned), per step:
     # H2D of A and B, compute, D2H of C for every problem of the sweep
@@ -326,6 +355,7 @@ def run_ours(args, dist: Dist):
     cpu = None
     if dist.world == 1 and dist.rank == 0 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args.cpu_seconds)
+        check["oracle"] = oracle_check(host, Cs)
 
     line = {
         "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": dist.world, "steps": args.steps,
@@ -349,8 +379,17 @@ def run_ours(args, dist: Dist):
         "clocks": clocks,
         "roofline": roofline,
         "kernel_times_ms_per_step": {k: round(statistics.mean(v), 4) for k, v in kinds.items() if v},
+        "certificate": {"elements_recomputed_per_step": guard_replaced / max(1, args.steps + max(args.warmup, 3)),
+                        "problems_recomputed_whole": guard_problems,
+                        "ms_per_step_without_certificate": round(unguarded_ms, 4),
+                        "value_without_certificate": round(flops_step / (unguarded_ms / 1e3) / 1e12, 3),
+                        "note": "the library's default checks every emulated element's error bound and "
+                                "recomputes what it cannot vouch for in native FP64 (MM_FLAG_NO_GUARD skips it)"},
         "per_n": per_n,
+        "batch_1024": batch,
+        "large": large,
         "fp64_peak_measured": {"dmma_tflops": round(dmma_peak, 4), "dfma_tflops": round(dfma_peak, 4)},
+        "int8_mma_peak_measured_tops": round(int8_peak, 2),
         "check": check,
         "cpu_baseline": cpu,
     }
@@ -372,23 +411,52 @@ def verify(As, Bs, Cs) -> dict:
     return {"freivalds_worst_ratio": round(worst, 4), "passed": worst <= 4.0}
 
 
+def oracle_check(host_pairs, Cs) -> dict:
+    """Part of the CPU-baseline leg (rank 0, one GPU): the benchmarked step's
+    output checked with the oracle on the host, outside the timed region: the
+    oracle's Freivalds test on every product and three rows of each computed
+    by the oracle (Alg. 1's left-to-right sums), componentwise error
+    |C - C_oracle| / (|A||B|) against 2 N 2^-53."""
+    import oracle
+    oracle.build()
+    rng = np.random.default_rng(2)
+    worst, fails = 0.0, 0
+    for (A, B), C in zip(host_pairs, Cs):
+        C = C.cpu().numpy()
+        n = A.shape[0]
+        bad, _, _ = oracle.freivalds(A, B, C, rng.choice([-1.0, 1.0], n))
+        fails += int(bad)
+        rows = sorted({0, n // 2, n - 1})
+        ref = oracle.gemm_rows(A, B, rows)
+        absab = oracle.absgemm_mnk(np.ascontiguousarray(A[rows]), B)
+        m = absab > 0
+        if m.any():
+            worst = max(worst, float(np.max(np.abs(C[rows] - ref)[m] / absab[m])) / (2 * n * 2.0 ** -53))
+    return {"oracle_rows_worst_error_over_2Nu": round(worst, 4), "freivalds_failures": fails,
+            "passed": worst <= 1.0 and fails == 0,
+            "how": "oracle.freivalds on every product, oracle.gemm_rows on rows 0, N/2, N-1"}
+
+
 def per_size(mm, As, Bs, Cs, flush, stream, reps: int = 5) -> dict:
+    """Each form on each problem alone (single calls, L2 flushed, median of
+    `reps`; native FP64 takes fewer repetitions above N = 2000)."""
     import torch
     out = {}
     hn = mm.Handle("native")
     he = mm.Handle("emulated")
     hm = mm.Handle("modular")
+    hi = mm.Handle("int8")
     ha = mm.Handle("auto")
     for A, B, C in zip(As, Bs, Cs):
         n = A.shape[0]
         row = {}
         forms = [("native", hn), ("emulated", he), ("auto", ha)]
         if n >= 256:
-            forms.insert(2, ("modular", hm))
+            forms[2:2] = [("modular", hm), ("int8", hi)]
         for name, hh in forms:
             hh.gemm(A, B, C)  # warm
             ts = []
-            for r in range(reps):
+            for r in range(reps if name != "native" or n <= 2000 else 2):
                 flush.fill_(float(r))
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 e0.record(stream)
@@ -402,13 +470,124 @@ def per_size(mm, As, Bs, Cs, flush, stream, reps: int = 5) -> dict:
         row["emulated_slices"] = he.plan(n)[1]
         if n >= 256:
             row["modular_moduli"] = hm.plan(n)[1]
+            row["int8_slices"] = hi.plan(n)[1]
         form, k = ha.plan(n)
-        row["auto_plan"] = ("native", f"digits s={k}", f"modular k={k}")[form]
+        row["auto_plan"] = ("native", f"digits s={k}", f"modular k={k}", f"int8 s={k}")[form]
         row["speedup_auto_over_native"] = round(row["native_ms"] / row["auto_ms"], 2)
         out[str(n)] = row
-    for hh in (hn, he, hm, ha):
+    for hh in (hn, he, hm, hi, ha):
+        hh.guard_read()  # (clears the certificate's counts)
         hh.check()
         hh.close()
+    return out
+
+
+def timed_calls(fn, flush, stream, reps: int) -> float:
+    """Median device time (ms) of fn() over `reps` calls, L2 flushed before each."""
+    import torch
+    fn()  # warm (builds a grouped call's graph)
+    ts = []
+    for r in range(reps):
+        flush.fill_(float(r))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return statistics.median(ts)
+
+
+def batch_block(mm, dev, flush, stream, peaks, dmma_peak, reps: int = 5) -> dict:
+    """Batching: one grouped call of 1024 independent products, N log-uniform
+    over the integers [10, 2000] (seed 1), entries uniform [0, 1), automatic
+    plan, replayed from its CUDA graph.  Then each size bucket of the plan
+    alone (same problems, its own grouped call): time, share, and the roof of
+    its form -- bf16 tensor work (residue products, certificate included) for
+    emulated buckets, the FP64 DMMA probe (and HBM for N <= 100) for native."""
+    sizes = workload.loguniform_sizes(1024, 10, 2000, seed=1)
+    pairs = [workload.pair_torch("uniform01", 1 * 1000003 + p, n, dev) for p, n in enumerate(sizes)]
+    As = [a for a, _ in pairs]
+    Bs = [b for _, b in pairs]
+    Cs = [a.new_empty(a.shape) for a in As]
+    del pairs
+    h = mm.Handle("auto")
+    ms = timed_calls(lambda: h.gemm_grouped(As, Bs, Cs), flush, stream, reps)
+    flops = sum(workload.flops(n) for n in sizes)
+    replaced, _ = h.guard_read()
+    plans = {n: h.plan(n) for n in set(sizes)}
+    buckets = {}
+    for i, n in enumerate(sizes):
+        buckets.setdefault(plans[n], []).append(i)
+    rows = {}
+    total_bucket_ms = 0.0
+    for (form, k), idx in sorted(buckets.items()):
+        sub = (lambda idx=idx: h.gemm_grouped([As[i] for i in idx], [Bs[i] for i in idx], [Cs[i] for i in idx]))
+        bms = timed_calls(sub, flush, stream, reps)
+        total_bucket_ms += bms
+        ns = [sizes[i] for i in idx]
+        bflops = sum(workload.flops(n) for n in ns)
+        name = ("native", f"digits s={k}", f"modular k={k}", f"int8 s={k}")[form]
+        r = {"problems": len(idx), "N_range": [min(ns), max(ns)], "ms": round(bms, 4),
+             "tflops": round(bflops / (bms / 1e3) / 1e12, 3)}
+        if form == 0:
+            r["frac_of_dmma_probe"] = round(bflops / (bms / 1e3) / 1e12 / dmma_peak, 4)
+            if max(ns) <= 100:
+                r["frac_of_hbm"] = round(sum(24 * n * n for n in ns) / (bms / 1e3) / 1e9 / peaks["hbm_gbs"], 5)
+        elif form == 2:
+            tensor = sum((k + 1) * 2 * n ** 3 for n in ns)  # k residue products + the certificate's
+            r["tensor_frac_whole_call"] = round(tensor / (bms / 1e3) / 1e12 / peaks["bf16_tflops"], 4)
+        rows[name] = r
+    for r in rows.values():
+        r["share_of_bucket_time"] = round(r["ms"] / total_bucket_ms, 4)
+    h.check()
+    h.close()
+    return {"workload": "1024 square FP64 products, N log-uniform over [10, 2000] (seed 1), uniform [0, 1), "
+                        "one grouped call (CUDA graph replay), automatic plan",
+            "flops": flops, "ms": round(ms, 4), "tflops": round(flops / (ms / 1e3) / 1e12, 3),
+            "elements_recomputed_by_the_certificate": replaced, "buckets": rows,
+            "timing": f"median of {reps} calls, L2 flushed before each"}
+
+
+def large_block(mm, dev, flush, stream, reps: int = 2) -> dict:
+    """The combined large configuration: a grouped call of 64 products, N
+    log-uniform over [1000, 16384] (seed 5), and a single N = 16384 product,
+    entries of magnitude 2^U(-20, 20) with random signs, automatic plan.
+    Inputs are generated on the device (the same SplitMix64 streams)."""
+    import torch
+    sizes = workload.loguniform_sizes(64, 1000, 16384, seed=5)
+    need = sum(24 * n * n for n in sizes) + 24 * 16384 ** 2
+    free, _ = torch.cuda.mem_get_info(dev)
+    if free < 1.6 * need:
+        return {"skipped": f"needs about {1.6 * need / 2**30:.0f} GiB free, {free / 2**30:.0f} GiB available"}
+    h = mm.Handle("auto")
+    out = {"workload": "64 square FP64 products, N log-uniform over [1000, 16384] (seed 5), and one N = 16384, "
+                       "entries 2^U(-20,20) with random signs, automatic plan"}
+    pairs = [workload.pair_torch("loguniform20", 5 * 1000003 + p, n, dev) for p, n in enumerate(sizes)]
+    As = [a for a, _ in pairs]
+    Bs = [b for _, b in pairs]
+    Cs = [a.new_empty(a.shape) for a in As]
+    del pairs
+    ms = timed_calls(lambda: h.gemm_grouped(As, Bs, Cs), flush, stream, reps)
+    flops = sum(workload.flops(n) for n in sizes)
+    out["grouped"] = {"N_range": [min(sizes), max(sizes)], "flops": flops, "ms": round(ms, 3),
+                      "tflops": round(flops / (ms / 1e3) / 1e12, 3),
+                      "elements_recomputed_by_the_certificate": h.guard_read()[0]}
+    del As, Bs, Cs
+    torch.cuda.empty_cache()
+    n = 16384
+    A, B = workload.pair_torch("loguniform20", 16384, n, dev)
+    C = torch.empty_like(A)
+    ms = timed_calls(lambda: h.gemm(A, B, C), flush, stream, reps)
+    form, k = h.plan(n)
+    out["single_16384"] = {"plan": ("native", f"digits s={k}", f"modular k={k}", f"int8 s={k}")[form],
+                           "ms": round(ms, 3), "tflops": round(workload.flops(n) / (ms / 1e3) / 1e12, 3),
+                           "elements_recomputed_by_the_certificate": h.guard_read()[0]}
+    out["timing"] = f"median of {reps} calls after a warm-up call, L2 flushed before each"
+    del A, B, C
+    torch.cuda.empty_cache()
+    h.check()
+    h.close()
     return out
 
 

@@ -1,5 +1,6 @@
 """The seeded input generators (shared by both sides; no product arithmetic)."""
 import numpy as np
+import pytest
 
 import workload
 
@@ -48,3 +49,21 @@ def test_loguniform_sizes():
     # about half of the problems are at most ~140 (median of log-uniform [10, 2001])
     med = float(np.median(sizes))
     assert 100 < med < 200
+
+
+def test_device_generator_matches_the_host_draws():
+    # bench.py generates its largest inputs with PyTorch (here on the CPU):
+    # uniform draws bit for bit, log-uniform magnitudes within the last bit of exp2
+    torch = pytest.importorskip("torch")
+    for seed in (0, 3, 5 * 1000003 + 9, workload.B_STREAM_OFFSET):
+        np.testing.assert_array_equal(workload.values_torch("uniform01", seed, 4096, "cpu").numpy(),
+                                      workload.values("uniform01", seed, 4096))
+        h = workload.values("loguniform20", seed, 4096)
+        d = workload.values_torch("loguniform20", seed, 4096, "cpu").numpy()
+        assert np.array_equal(np.sign(h), np.sign(d))
+        assert np.max(np.abs(d - h) / np.abs(h)) <= 2.0 ** -51
+    A, B = workload.pair_torch("uniform01", 7, 33, "cpu")
+    hA, hB = workload.pair("uniform01", 7, 33)
+    np.testing.assert_array_equal(A.numpy(), hA)
+    np.testing.assert_array_equal(B.numpy(), hB)
+    _ = torch

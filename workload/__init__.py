@@ -38,6 +38,43 @@ def splitmix64(seed: int, count: int, start: int = 0) -> np.ndarray:
     return z
 
 
+def splitmix64_torch(seed: int, count: int, device):
+    """The same draws as splitmix64 (start 0), generated by PyTorch on `device`
+    as int64 bit patterns (wrapping multiplication, logical right shifts)."""
+    import torch
+    def s64(v):  # a uint64 constant as the int64 with the same bits
+        v &= 0xFFFFFFFFFFFFFFFF
+        return v - (1 << 64) if v >= 1 << 63 else v
+    def srl(z, k):
+        return (z >> k) & ((1 << (64 - k)) - 1)
+    idx = torch.arange(1, count + 1, dtype=torch.int64, device=device)
+    z = idx * s64(int(GOLDEN_GAMMA)) + s64(seed)
+    z = (z ^ srl(z, 30)) * s64(int(_M1))
+    z = (z ^ srl(z, 27)) * s64(int(_M2))
+    return z ^ srl(z, 31)
+
+
+def values_torch(dist: str, seed: int, count: int, device):
+    """values() generated on a PyTorch device (uniform01 and loguniform20),
+    equal to the host's draws up to the last bit of exp2 (exact for uniform01)."""
+    import torch
+    u = (torch.bitwise_right_shift(splitmix64_torch(seed, count, device), 11) & ((1 << 53) - 1)).double() * 2.0 ** -53
+    if dist == "uniform01":
+        return u
+    if dist == "loguniform20":
+        mag = torch.exp2(-20.0 + 40.0 * u)
+        sign = splitmix64_torch(seed + SIGN_STREAM_OFFSET, count, device) < 0  # top bit set
+        return torch.where(sign, -mag, mag)
+    raise ValueError(f"values_torch supports uniform01 and loguniform20, not {dist!r}")
+
+
+def pair_torch(dist: str, seed: int, n: int, device):
+    """pair() generated on a PyTorch device (see values_torch)."""
+    A = values_torch(dist, seed, n * n, device).reshape(n, n)
+    B = values_torch(dist, seed + B_STREAM_OFFSET, n * n, device).reshape(n, n)
+    return A, B
+
+
 def uniform01(seed: int, count: int) -> np.ndarray:
     """Uniform doubles in [0, 1): the top 53 bits of each draw times 2^-53."""
     z = splitmix64(seed, count)
