@@ -163,59 +163,95 @@ __global__ void __launch_bounds__(NT_THREADS, 4) native_fp64_kernel(const __grid
   native_tile_any(P, (local / P->tiles_n) * NT_BM, (local % P->tiles_n) * NT_BN, As, Bs);
 }
 
-// Small problems: one warp per 16 x 16 tile of C, so that N ~ 100 still spreads
-// over many SMs (a 64 x 64 tile would leave all but a few idle, and the FP64
-// MMA rate of one SM is small).  Fragments are loaded straight from global
-// memory (L1/L2), 16 k at a time: two m16n8k4 per k step.
+// Small problems: 16 x 16 tiles of C, so that N ~ 100 still spreads over many
+// SMs (a 64 x 64 tile would leave all but a few idle, and the FP64 MMA rate
+// of one SM is small).  Such a tile's work is a few microseconds of
+// dependent MMAs; what bounds it is the latency of its loads.  So the CTA
+// (two warps, one 16 x 8 half each) streams k-chunks of 64 of its A panel
+// and B panel into shared memory with all of a 256-deep stretch in flight at
+// once (8-byte cp.async, zero fill; a 4-chunk ring), and each warp runs its
+// MMA chain from shared memory: k-groups of 4 in increasing order up to the
+// next multiple of 16 -- the same chain, bit for bit, as the 64 x 64 kernel's.
 constexpr int NS_TILE = 16;
+constexpr int NS_KC = 64;      // k per chunk
+constexpr int NS_STAGES = 4;   // chunks in flight
+constexpr int NS_LD = 20;      // padded row (doubles): a half-warp's fragment reads hit 16 distinct bank pairs
+constexpr int NS_THREADS = 64;
+constexpr int NS_CHUNK_DOUBLES = 2 * NS_KC * NS_LD;  // A chunk [k][m], then B chunk [k][n]
+constexpr int NS_SMEM_BYTES = NS_STAGES * NS_CHUNK_DOUBLES * 8;
 
-__global__ void __launch_bounds__(32) native_fp64_small_kernel(const __grid_constant__ NativeArgs args) {
-  const int tile = blockIdx.x;
-  const Problem* P = args.table ? &args.table[find_problem(args.table, args.count, tile)] : &args.single;
-  const int n = P->n, m = P->m, kdim = P->k;
-  const size_t lda = P->lda, ldb = P->ldb, ldc = P->ldc;
-  const bool ta = P->ta != 0, tb = P->tb != 0;
-  const int local = tile - P->tile_begin;
-  if (n <= 0 || m <= 0 || local < 0 || local >= P->tiles_m * P->tiles_n) return;
-  const int m0 = (local / P->tiles_n) * NS_TILE;
-  const int n0 = (local % P->tiles_n) * NS_TILE;
+template <bool ta, bool tb>
+__device__ __forceinline__ void small_load_chunk(const Problem* P, int m0, int n0, int k0, double* sA) {
+  double* sB = sA + NS_KC * NS_LD;
+  const int m = P->m, n = P->n, kdim = P->k;
   const double* __restrict__ A = P->A;
   const double* __restrict__ B = P->B;
-  const int lane = threadIdx.x, g = lane >> 2, t = lane & 3;
-  const int ra = m0 + g, rb = m0 + g + 8;  // rows of the A fragment
-  double acc[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}};
-  for (int k0 = 0; k0 < kdim; k0 += 16) {
-    double a[4][2], b[4][2];
-#pragma unroll
-    for (int kk = 0; kk < 4; ++kk) {
-      const int k = k0 + 4 * kk + t;
-      const bool kin = k < kdim;
-      a[kk][0] = (kin && ra < m) ? A[ta ? static_cast<size_t>(k) * lda + ra : static_cast<size_t>(ra) * lda + k] : 0.0;
-      a[kk][1] = (kin && rb < m) ? A[ta ? static_cast<size_t>(k) * lda + rb : static_cast<size_t>(rb) * lda + k] : 0.0;
-#pragma unroll
-      for (int ni = 0; ni < 2; ++ni) {
-        const int col = n0 + ni * 8 + g;
-        b[kk][ni] = (kin && col < n) ? B[tb ? static_cast<size_t>(col) * ldb + k : static_cast<size_t>(k) * ldb + col]
-                                     : 0.0;
-      }
-    }
-#pragma unroll
-    for (int kk = 0; kk < 4; ++kk)
-#pragma unroll
-      for (int ni = 0; ni < 2; ++ni) dmma_16x8x4(acc[ni], a[kk][0], a[kk][1], b[kk][ni]);
+  const size_t lda = P->lda, ldb = P->ldb;
+  for (int idx = threadIdx.x; idx < NS_TILE * NS_KC; idx += NS_THREADS) {
+    // consecutive threads follow the stored rows (k for A, m for a transposed A)
+    const int r = ta ? idx % NS_TILE : idx / NS_KC, kk = ta ? idx / NS_TILE : idx % NS_KC;
+    const int gi = m0 + r, gk = k0 + kk;
+    const bool ok = gi < m && gk < kdim;
+    const size_t off = ta ? static_cast<size_t>(gk) * lda + gi : static_cast<size_t>(gi) * lda + gk;
+    cp_async_8(&sA[kk * NS_LD + r], ok ? A + off : A, ok);
   }
+  for (int idx = threadIdx.x; idx < NS_TILE * NS_KC; idx += NS_THREADS) {
+    const int c = tb ? idx / NS_KC : idx % NS_TILE, kk = tb ? idx % NS_KC : idx / NS_TILE;
+    const int gj = n0 + c, gk = k0 + kk;
+    const bool ok = gk < kdim && gj < n;
+    const size_t off = tb ? static_cast<size_t>(gj) * ldb + gk : static_cast<size_t>(gk) * ldb + gj;
+    cp_async_8(&sB[kk * NS_LD + c], ok ? B + off : B, ok);
+  }
+}
+
+template <bool ta, bool tb>
+__device__ __forceinline__ void small_tile(const Problem* P, int m0, int n0, double* smem) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  const int ksteps = (P->k + 15) / 16 * 16;  // the chain runs to the next multiple of 16, as the 64 x 64 kernel's
+  const int chunks = (ksteps + NS_KC - 1) / NS_KC;
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+  for (int c = 0; c < NS_STAGES - 1; ++c) {
+    if (c < chunks) small_load_chunk<ta, tb>(P, m0, n0, c * NS_KC, smem + c * NS_CHUNK_DOUBLES);
+    cp_async_commit();
+  }
+  for (int c = 0; c < chunks; ++c) {
+    cp_async_wait<NS_STAGES - 2>();
+    __syncthreads();  // chunk c is in for every thread; chunk c - 1's slot is free
+    const int nx = c + NS_STAGES - 1;
+    if (nx < chunks) small_load_chunk<ta, tb>(P, m0, n0, nx * NS_KC, smem + (nx % NS_STAGES) * NS_CHUNK_DOUBLES);
+    cp_async_commit();
+    const double* sA = smem + (c % NS_STAGES) * NS_CHUNK_DOUBLES;
+    const double* sB = sA + NS_KC * NS_LD;
+    const int kend = ksteps - c * NS_KC < NS_KC ? ksteps - c * NS_KC : NS_KC;
+    for (int kq = 0; kq < kend; kq += 4)
+      dmma_16x8x4(acc, sA[(kq + t) * NS_LD + g], sA[(kq + t) * NS_LD + g + 8], sB[(kq + t) * NS_LD + warp * 8 + g]);
+  }
+  cp_async_wait<0>();
   double* __restrict__ C = P->C;
+  const int c0 = n0 + warp * 8 + 2 * t;
 #pragma unroll
-  for (int ni = 0; ni < 2; ++ni) {
-    const int c0 = n0 + ni * 8 + 2 * t;
-#pragma unroll
-    for (int hh = 0; hh < 2; ++hh) {
-      const int r = m0 + g + 8 * hh;
-      if (r < m) {
-        if (c0 < n) C[static_cast<size_t>(r) * ldc + c0] = acc[ni][2 * hh];
-        if (c0 + 1 < n) C[static_cast<size_t>(r) * ldc + c0 + 1] = acc[ni][2 * hh + 1];
-      }
+  for (int hh = 0; hh < 2; ++hh) {
+    const int r = m0 + g + 8 * hh;
+    if (r < P->m) {
+      if (c0 < P->n) C[static_cast<size_t>(r) * P->ldc + c0] = acc[2 * hh];
+      if (c0 + 1 < P->n) C[static_cast<size_t>(r) * P->ldc + c0 + 1] = acc[2 * hh + 1];
     }
+  }
+}
+
+__global__ void __launch_bounds__(NS_THREADS) native_fp64_small_kernel(const __grid_constant__ NativeArgs args) {
+  extern __shared__ __align__(16) double ns_smem[];
+  const int tile = blockIdx.x;
+  const Problem* P = args.table ? &args.table[find_problem(args.table, args.count, tile)] : &args.single;
+  const int local = tile - P->tile_begin;
+  if (P->n <= 0 || P->m <= 0 || local < 0 || local >= P->tiles_m * P->tiles_n) return;
+  const int m0 = (local / P->tiles_n) * NS_TILE;
+  const int n0 = (local % P->tiles_n) * NS_TILE;
+  if (P->ta) {
+    if (P->tb) small_tile<true, true>(P, m0, n0, ns_smem); else small_tile<true, false>(P, m0, n0, ns_smem);
+  } else {
+    if (P->tb) small_tile<false, true>(P, m0, n0, ns_smem); else small_tile<false, false>(P, m0, n0, ns_smem);
   }
 }
 
@@ -331,7 +367,10 @@ cudaError_t native_small_launch(const Problem* table, const Problem* single, int
   args.table = table;
   if (single) args.single = *single;
   args.count = count;
-  native_fp64_small_kernel<<<total_tiles, 32, 0, stream>>>(args);
+  const cudaError_t e = cudaFuncSetAttribute(native_fp64_small_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             NS_SMEM_BYTES);
+  if (e != cudaSuccess) return e;
+  native_fp64_small_kernel<<<total_tiles, NS_THREADS, NS_SMEM_BYTES, stream>>>(args);
   return cudaGetLastError();
 }
 
