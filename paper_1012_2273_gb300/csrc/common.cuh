@@ -121,6 +121,12 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 
+// Waits that only let work already issued finish -- copies in flight, MMAs
+// committed -- use this fixed limit however short the caller's limit is:
+// what they wait for completes on its own, and a CTA must not release its
+// shared or tensor memory before it has.
+constexpr uint64_t WIND_DOWN_NS = 2000000000ull;
+
 // Waits for phase `parity` of `bar` to complete, for at most `limit_ns`.
 // Returns false (and records MM_ERR_TIMEOUT) if the limit ran out.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint64_t limit_ns, int* status) {

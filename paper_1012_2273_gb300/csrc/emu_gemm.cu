@@ -319,7 +319,7 @@ __global__ void __launch_bounds__(EM_THREADS, 1)
           st += Cfg::STAGES;
           ph ^= 1;
         }
-        mbar_wait(&full[st], ph, tmo, args.status);
+        mbar_wait(&full[st], ph, WIND_DOWN_NS, args.status);
       }
     }
     __syncwarp();
@@ -393,7 +393,7 @@ __global__ void __launch_bounds__(EM_THREADS, 1)
       }
       // Every MMA issued so far must finish before TMEM is released.
       tc_commit(mma_done);
-      mbar_wait(mma_done, 0, tmo, args.status);
+      mbar_wait(mma_done, 0, WIND_DOWN_NS, args.status);
     }
     __syncwarp();
   }

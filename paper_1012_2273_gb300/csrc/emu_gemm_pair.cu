@@ -310,7 +310,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(PR_THREADS, 1)
             st += PR_STAGES;
             ph ^= 1;
           }
-          mbar_wait(&full[st], ph, tmo, args.status);
+          mbar_wait(&full[st], ph, WIND_DOWN_NS, args.status);
         }
       }
     } else if (warp == 1 && lane == 0 && leader) {
@@ -373,7 +373,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(PR_THREADS, 1)
         }
       }
       tc_commit_pair(mma_done, 0x1);
-      mbar_wait(mma_done, 0, tmo, args.status);
+      mbar_wait(mma_done, 0, WIND_DOWN_NS, args.status);
     }
     __syncwarp();
   } else {

@@ -1093,9 +1093,9 @@ mm_status mm_create(mm_handle* out, const mm_config* cfg) {
     delete h;
     return MM_ERR_UNSUPPORTED;
   }
-  if (const char* t = std::getenv("MM_TIMEOUT_MS")) {
-    const long ms = std::atol(t);
-    if (ms > 0) h->timeout_ns = static_cast<uint64_t>(ms) * 1000000ull;
+  if (const char* t = std::getenv("MM_TIMEOUT_MS")) {  // milliseconds, fractions allowed
+    const double ms = std::atof(t);
+    if (ms > 0) h->timeout_ns = std::max<uint64_t>(100, static_cast<uint64_t>(ms * 1e6));
   }
   h->profile = (h->cfg.flags & MM_FLAG_PROFILE) != 0;
   default_tune(h);

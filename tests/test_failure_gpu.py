@@ -48,3 +48,30 @@ def test_selftest_argument_checks():
         L = mm.lib()
         assert L.mm_selftest_wait(h._h, 0, None) == 1
         assert L.mm_selftest_wait(h._h, 60001, None) == 1
+
+
+def test_pipeline_waits_that_run_out_wind_down_and_later_calls_are_exact(monkeypatch):
+    # A limit of 100 ns on every wait of the slice-product pipeline (TMA
+    # stages, accumulators, the unit ring): a normal N = 2000 product's waits
+    # run out, the kernel records MM_ERR_TIMEOUT, lets its copies and MMAs
+    # finish (those waits keep their own 2 s limit), frees its tensor memory
+    # and returns.  Later calls on fresh handles with the default limit run
+    # (a leaked TMEM allocation would stall them) and are exact.
+    import paper_1012_2273_gb300 as mm
+    n, k = 2000, 14
+    A, B = workload.pair("uniform11", 14, n)
+    dA, dB = dev(A), dev(B)
+    monkeypatch.setenv("MM_TIMEOUT_MS", "0.0001")
+    with mm.Handle("modular", slices=k) as h:
+        h.gemm(dA, dB)
+        with pytest.raises(mm.MMError) as ei:
+            h.check()
+        assert ei.value.code == 5  # MM_ERR_TIMEOUT
+    monkeypatch.delenv("MM_TIMEOUT_MS")
+    rows = [0, 999, n - 1]
+    want = oracle.fixed_gemm_rows(A, B, oracle.modular_beta(k, n), rows)
+    for _ in range(2):
+        with mm.Handle("modular", slices=k, flags=mm.FLAG_NO_GUARD) as h:
+            C = host(h.gemm(dA, dB))
+            h.check()
+        np.testing.assert_array_equal(C[rows].view(np.int64), want.view(np.int64))
