@@ -329,6 +329,7 @@ struct EmuGroup {
   std::vector<int4> units;         // grouped launches: {problem, tile, group, cost}
   std::vector<int4> cert_units;    // grouped launches: the certificate's {problem, tile, 0, cost}
   int cert_total = 0;              // units of the certificate's launch
+  int cert_grid = 1;               // its CTAs
   int total_tiles = 0, total_split = 0, total_absmax = 0, total_units = 0, max_rows = 0, scratch_slots = 1;
   long long tilebuf_elems = 0;
   // byte offsets inside the group's region of the arena
@@ -548,6 +549,21 @@ mm_status layout_group(mm_handle h, EmuGroup& g, char* base) {
     }
     std::stable_sort(g.cert_units.begin(), g.cert_units.end(),
                      [](const int4& a, const int4& b) { return a.w > b.w; });
+    // The two launches run side by side (the certificate on a forked
+    // stream): the CTA slots are shared in proportion to their k-blocks, so
+    // that both finish together instead of the certificate running in the
+    // slice products' tail.  (Profiling runs them one after the other, each
+    // on every slot.)
+    const int slots = g.form == 3 ? mmk::i8_blocks_per_sm() * h->num_sms : h->num_sms;
+    double main_kb = 0.0, cert_kb = 0.0;
+    for (const Problem& p : g.ps) {
+      const double kb = p.k_pad / 64.0, tiles = static_cast<double>(p.tiles_m) * p.tiles_n;
+      main_kb += tiles * mmk::problem_pairs(p) * kb;
+      cert_kb += tiles * kb;
+    }
+    g.cert_grid = std::max(1, std::min(g.cert_total, static_cast<int>(std::lround(slots * cert_kb / (main_kb + cert_kb)))));
+    if (!h->profile && !g.pair && slots > g.cert_grid) g.grid = std::max(1, std::min(g.grid, slots - g.cert_grid));
+    if (h->profile) g.cert_grid = std::min(g.cert_total, slots);
   }
   // Everything zeroed before a launch sits in one run (one memset): the
   // row/column maxima, the tile and unit counters, and -- when guarded --
@@ -653,8 +669,8 @@ mm_status run_group(mm_handle h, const EmuGroup& g, const Problem* d_table, cons
     }
     const long m_c = prof_start(h, cs, KIND_SLICE_GEMM);
     const cudaError_t ce =
-        g.form == 3 ? mmk::i8_cert_launch(c, std::min(g.cert_total, mmk::i8_blocks_per_sm() * h->num_sms), cs)
-                    : mmk::emu_cert_launch(g.bn, &g.maps[0], &g.maps[1], c, emu_grid(h, g.cert_total), cs);
+        g.form == 3 ? mmk::i8_cert_launch(c, g.cert_grid, cs)
+                    : mmk::emu_cert_launch(g.bn, &g.maps[0], &g.maps[1], c, g.cert_grid, cs);
     prof_end(h, cs, m_c);
     if (ce != cudaSuccess) return cuda_fail(h, ce, "certificate launch");
     if (cert_forked) MM_CUDA(h, cudaEventRecord(h->cert_join, cs));
