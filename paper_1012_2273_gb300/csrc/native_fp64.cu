@@ -6,23 +6,31 @@
 // of a grouped call.  Each CTA streams 64 x 16 panels of A and 16 x 64 panels
 // of B through a double-buffered shared-memory ring (cp.async, 8-byte copies,
 // so any shape and leading dimension works: rows of an odd-N matrix are not
-// 16-byte aligned, which rules out TMA tiles), and four warps run mma.sync
-// m16n8k4 f64 on 32 x 32 sub-tiles.  C (m x n) = op(A) (m x k) . op(B)
+// 16-byte aligned, which rules out TMA tiles), and eight warps run mma.sync
+// m16n8k4 f64 on 32 x 16 sub-tiles (two CTAs per SM, 16 warps: enough
+// independent MMA chains to keep each sub-partition's FP64 pipe busy while
+// a chunk's partial sums are added into the total).  C (m x n) = op(A) (m x k) . op(B)
 // (k x n), each stored row-major with its own leading dimension, op() the
 // identity or the transpose; the square product is m = n = k.
-// Each output is a chain of FP64 fused multiply-adds; the order differs from
-// the paper's left-to-right sum, so results agree with it to within
-// gamma_N |A||B| rather than bit for bit (exactly, when all partial sums are
-// exact, e.g. for small-integer inputs).
+// The order of every output's sum is fixed, the same in both kernels here
+// and in every tile shape: k (zero-padded to a multiple of 16) is cut into
+// chunks of NT_KCHUNK = 32; each chunk is one chain of MMAs over its k-groups
+// of 4 in increasing order, starting from 0; the chunks' partial sums are
+// added left to right into a total that starts from 0.  So results are
+// bitwise reproducible across runs, kernels, tile shapes, storage orders and
+// single or grouped calls.  The order differs from the paper's left-to-right
+// sum, so results agree with it to within gamma_N |A||B| rather than bit for
+// bit (exactly, when all partial sums are exact, e.g. for small integers).
 #include "launch.cuh"
 
 namespace mmk {
 
+constexpr int NT_KCHUNK = 32;  // k per chain of MMAs (see above)
 constexpr int NT_BM = 64;
 constexpr int NT_BN = 64;
 constexpr int NT_BK = 16;
 constexpr int NT_LD = 68;  // padded stride (doubles): conflict-free fragment loads
-constexpr int NT_THREADS = 128;
+constexpr int NT_THREADS = 256;
 
 struct NativeArgs {
   const Problem* table;  // device problem table (grouped) or nullptr
@@ -62,7 +70,7 @@ __device__ __forceinline__ void native_tile(const Problem* P, int m0, int n0, do
   const int tid = threadIdx.x;
   const int warp = tid >> 5, lane = tid & 31;
   const int g = lane >> 2, t = lane & 3;
-  const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
+  const int wm = (warp >> 2) * 32, wn = (warp & 3) * 16;
 
   auto load_stage = [&](int buf, int k0) {
 #pragma unroll
@@ -89,13 +97,13 @@ __device__ __forceinline__ void native_tile(const Problem* P, int m0, int n0, do
     cp_async_commit();
   };
 
-  double acc[2][4][4];
+  double acc[2][2][4], tot[2][2][4];  // the current chunk's chains; the total of the chunks before it
 #pragma unroll
   for (int i = 0; i < 2; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j)
+    for (int j = 0; j < 2; ++j)
 #pragma unroll
-      for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.0;
+      for (int q = 0; q < 4; ++q) acc[i][j][q] = tot[i][j][q] = 0.0;
 
   const int ktiles = (kdim + NT_BK - 1) / NT_BK;
   if (ktiles > 0) load_stage(0, 0);
@@ -110,34 +118,45 @@ __device__ __forceinline__ void native_tile(const Problem* P, int m0, int n0, do
     __syncthreads();
 #pragma unroll
     for (int kk = 0; kk < NT_BK; kk += 4) {
-      double a[2][2], b[4];
+      double a[2][2], b[2];
 #pragma unroll
       for (int mi = 0; mi < 2; ++mi) {
         a[mi][0] = As[buf][kk + t][wm + mi * 16 + g];
         a[mi][1] = As[buf][kk + t][wm + mi * 16 + g + 8];
       }
 #pragma unroll
-      for (int ni = 0; ni < 4; ++ni) b[ni] = Bs[buf][kk + t][wn + ni * 8 + g];
+      for (int ni = 0; ni < 2; ++ni) b[ni] = Bs[buf][kk + t][wn + ni * 8 + g];
 #pragma unroll
       for (int mi = 0; mi < 2; ++mi)
 #pragma unroll
-        for (int ni = 0; ni < 4; ++ni) dmma_16x8x4(acc[mi][ni], a[mi][0], a[mi][1], b[ni]);
+        for (int ni = 0; ni < 2; ++ni) dmma_16x8x4(acc[mi][ni], a[mi][0], a[mi][1], b[ni]);
     }
     __syncthreads();
+    if ((kt + 1) % (NT_KCHUNK / NT_BK) == 0 || kt + 1 == ktiles) {  // a chunk ends: add it to the total
+#pragma unroll
+      for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+        for (int ni = 0; ni < 2; ++ni)
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            tot[mi][ni][q] = tot[mi][ni][q] + acc[mi][ni][q];
+            acc[mi][ni][q] = 0.0;
+          }
+    }
   }
 
 #pragma unroll
   for (int mi = 0; mi < 2; ++mi)
 #pragma unroll
-    for (int ni = 0; ni < 4; ++ni) {
+    for (int ni = 0; ni < 2; ++ni) {
       const int r0 = m0 + wm + mi * 16 + g;
       const int c0 = n0 + wn + ni * 8 + 2 * t;
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         const int r = r0 + 8 * h;
         if (r < m) {
-          if (c0 < n) C[(size_t)r * ldc + c0] = acc[mi][ni][2 * h];
-          if (c0 + 1 < n) C[(size_t)r * ldc + c0 + 1] = acc[mi][ni][2 * h + 1];
+          if (c0 < n) C[(size_t)r * ldc + c0] = tot[mi][ni][2 * h];
+          if (c0 + 1 < n) C[(size_t)r * ldc + c0 + 1] = tot[mi][ni][2 * h + 1];
         }
       }
     }
@@ -153,7 +172,7 @@ __device__ __forceinline__ void native_tile_any(const Problem* P, int m0, int n0
   }
 }
 
-__global__ void __launch_bounds__(NT_THREADS, 4) native_fp64_kernel(const __grid_constant__ NativeArgs args) {
+__global__ void __launch_bounds__(NT_THREADS, 2) native_fp64_kernel(const __grid_constant__ NativeArgs args) {
   __shared__ __align__(16) double As[2][NT_BK][NT_LD];  // [k][m]
   __shared__ __align__(16) double Bs[2][NT_BK][NT_LD];  // [k][n]
   const int tile = blockIdx.x;
@@ -163,81 +182,96 @@ __global__ void __launch_bounds__(NT_THREADS, 4) native_fp64_kernel(const __grid
   native_tile_any(P, (local / P->tiles_n) * NT_BM, (local % P->tiles_n) * NT_BN, As, Bs);
 }
 
-// Small problems: 16 x 16 tiles of C, so that N ~ 100 still spreads over many
-// SMs (a 64 x 64 tile would leave all but a few idle, and the FP64 MMA rate
-// of one SM is small).  Such a tile's work is a few microseconds of
-// dependent MMAs; what bounds it is the latency of its loads.  So the CTA
-// (two warps, one 16 x 8 half each) streams k-chunks of 64 of its A panel
-// and B panel into shared memory with all of a 256-deep stretch in flight at
-// once (8-byte cp.async, zero fill; a 4-chunk ring), and each warp runs its
-// MMA chain from shared memory: k-groups of 4 in increasing order up to the
-// next multiple of 16 -- the same chain, bit for bit, as the 64 x 64 kernel's.
-constexpr int NS_TILE = 16;
-constexpr int NS_KC = 64;      // k per chunk
-constexpr int NS_STAGES = 4;   // chunks in flight
-constexpr int NS_LD = 20;      // padded row (doubles): a half-warp's fragment reads hit 16 distinct bank pairs
-constexpr int NS_THREADS = 64;
-constexpr int NS_CHUNK_DOUBLES = 2 * NS_KC * NS_LD;  // A chunk [k][m], then B chunk [k][n]
-constexpr int NS_SMEM_BYTES = NS_STAGES * NS_CHUNK_DOUBLES * 8;
+// Small problems: 16 x 8 tiles of C, one CTA of four warps each, so that
+// N ~ 100 still spreads over most SMs (N = 100 is 91 tiles).  A chain of
+// dependent FP64 MMAs advances slowly on GB300 (the FP64 tensor rate of one
+// SM sub-partition is a few MMAs per microsecond), so the tile's 32-deep k
+// chunks are shared out over its warps -- warp w takes chunks w, w + 4, ... --
+// each warp streaming its chunks of the A panel (16 rows) and B panel (8
+// columns) through its own two-chunk shared-memory ring (8-byte cp.async,
+// zero fill) and running each chunk's chain from 0.  The partial sums are
+// then added in chunk order: the canonical order of this file, bit for bit
+// the 64 x 64 kernel's.
+constexpr int NS_TM = 16, NS_TN = 8;
+constexpr int NS_KC = NT_KCHUNK;  // k per chunk: the canonical chunk
+constexpr int NS_WARPS = 4;
+constexpr int NS_STAGES = 2;      // chunks in flight per warp
+constexpr int NS_LDA = 20;        // padded rows (doubles): a half-warp's fragment reads hit 16 distinct bank pairs
+constexpr int NS_LDB = 12;
+constexpr int NS_THREADS = 32 * NS_WARPS;
+constexpr int NS_MAX_CHUNKS = 16;  // k <= 511 (the small kernel's limit) pads to at most 512
+constexpr int NS_CHUNK_DOUBLES = NS_KC * (NS_LDA + NS_LDB);  // A chunk [k][m], then B chunk [k][n]
+constexpr int NS_RING_DOUBLES = NS_WARPS * NS_STAGES * NS_CHUNK_DOUBLES;
+constexpr int NS_SMEM_BYTES = (NS_RING_DOUBLES + NS_MAX_CHUNKS * 32 * 4) * 8;
 
-template <bool ta, bool tb>
-__device__ __forceinline__ void small_load_chunk(const Problem* P, int m0, int n0, int k0, double* sA) {
-  double* sB = sA + NS_KC * NS_LD;
+// One warp's copies of chunk k0 .. k0 + NS_KC - 1 of the tile's panels.
+// The storage order is a run-time choice here (one copy of the code: what
+// bounds this kernel is latency, and a cold instruction cache is part of it).
+__device__ __forceinline__ void small_load_chunk(const Problem* P, int m0, int n0, int k0, double* sA, int lane) {
+  double* sB = sA + NS_KC * NS_LDA;
   const int m = P->m, n = P->n, kdim = P->k;
+  const bool ta = P->ta != 0, tb = P->tb != 0;
   const double* __restrict__ A = P->A;
   const double* __restrict__ B = P->B;
-  const size_t lda = P->lda, ldb = P->ldb;
-  for (int idx = threadIdx.x; idx < NS_TILE * NS_KC; idx += NS_THREADS) {
-    // consecutive threads follow the stored rows (k for A, m for a transposed A)
-    const int r = ta ? idx % NS_TILE : idx / NS_KC, kk = ta ? idx / NS_TILE : idx % NS_KC;
+  // element (i, j) of op(A) is A[i * a_i + j * a_j]; element (j, l) of op(B) is B[j * b_j + l * b_l]
+  const size_t a_i = ta ? 1 : P->lda, a_j = ta ? P->lda : 1;
+  const size_t b_j = tb ? 1 : P->ldb, b_l = tb ? P->ldb : 1;
+#pragma unroll 4
+  for (int idx = lane; idx < NS_TM * NS_KC; idx += 32) {
+    // consecutive lanes follow the stored rows (k for A, m for a transposed A)
+    const int r = ta ? idx % NS_TM : idx / NS_KC, kk = ta ? idx / NS_TM : idx % NS_KC;
     const int gi = m0 + r, gk = k0 + kk;
     const bool ok = gi < m && gk < kdim;
-    const size_t off = ta ? static_cast<size_t>(gk) * lda + gi : static_cast<size_t>(gi) * lda + gk;
-    cp_async_8(&sA[kk * NS_LD + r], ok ? A + off : A, ok);
+    const size_t off = static_cast<size_t>(gi) * a_i + static_cast<size_t>(gk) * a_j;
+    cp_async_8(&sA[kk * NS_LDA + r], ok ? A + off : A, ok);
   }
-  for (int idx = threadIdx.x; idx < NS_TILE * NS_KC; idx += NS_THREADS) {
-    const int c = tb ? idx / NS_KC : idx % NS_TILE, kk = tb ? idx % NS_KC : idx / NS_TILE;
+#pragma unroll 4
+  for (int idx = lane; idx < NS_TN * NS_KC; idx += 32) {
+    const int c = tb ? idx / NS_KC : idx % NS_TN, kk = tb ? idx % NS_KC : idx / NS_TN;
     const int gj = n0 + c, gk = k0 + kk;
     const bool ok = gk < kdim && gj < n;
-    const size_t off = tb ? static_cast<size_t>(gj) * ldb + gk : static_cast<size_t>(gk) * ldb + gj;
-    cp_async_8(&sB[kk * NS_LD + c], ok ? B + off : B, ok);
+    const size_t off = static_cast<size_t>(gk) * b_j + static_cast<size_t>(gj) * b_l;
+    cp_async_8(&sB[kk * NS_LDB + c], ok ? B + off : B, ok);
   }
 }
 
-template <bool ta, bool tb>
 __device__ __forceinline__ void small_tile(const Problem* P, int m0, int n0, double* smem) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-  const int ksteps = (P->k + 15) / 16 * 16;  // the chain runs to the next multiple of 16, as the 64 x 64 kernel's
+  const int ksteps = (P->k + 15) / 16 * 16;  // zero-padded to a multiple of 16, as in the 64 x 64 kernel
   const int chunks = (ksteps + NS_KC - 1) / NS_KC;
-  double acc[4] = {0.0, 0.0, 0.0, 0.0};
-#pragma unroll
-  for (int c = 0; c < NS_STAGES - 1; ++c) {
-    if (c < chunks) small_load_chunk<ta, tb>(P, m0, n0, c * NS_KC, smem + c * NS_CHUNK_DOUBLES);
+  const int mine = chunks > warp ? (chunks - warp + NS_WARPS - 1) / NS_WARPS : 0;  // chunks warp, warp + 4, ...
+  double* ring = smem + warp * NS_STAGES * NS_CHUNK_DOUBLES;
+  double* part = smem + NS_RING_DOUBLES;  // [chunk][fragment value q][lane]
+  if (mine > 0) small_load_chunk(P, m0, n0, warp * NS_KC, ring, lane);
+  cp_async_commit();
+  for (int j = 0; j < mine; ++j) {
+    if (j + 1 < mine)
+      small_load_chunk(P, m0, n0, (warp + NS_WARPS * (j + 1)) * NS_KC, ring + ((j + 1) % NS_STAGES) * NS_CHUNK_DOUBLES,
+                       lane);
     cp_async_commit();
-  }
-  for (int c = 0; c < chunks; ++c) {
-    cp_async_wait<NS_STAGES - 2>();
-    __syncthreads();  // chunk c is in for every thread; chunk c - 1's slot is free
-    const int nx = c + NS_STAGES - 1;
-    if (nx < chunks) small_load_chunk<ta, tb>(P, m0, n0, nx * NS_KC, smem + (nx % NS_STAGES) * NS_CHUNK_DOUBLES);
-    cp_async_commit();
-    const double* sA = smem + (c % NS_STAGES) * NS_CHUNK_DOUBLES;
-    const double* sB = sA + NS_KC * NS_LD;
+    cp_async_wait<1>();
+    __syncwarp();  // chunk j is in for every lane
+    const int c = warp + NS_WARPS * j;
+    const double* sA = ring + (j % NS_STAGES) * NS_CHUNK_DOUBLES;
+    const double* sB = sA + NS_KC * NS_LDA;
     const int kend = ksteps - c * NS_KC < NS_KC ? ksteps - c * NS_KC : NS_KC;
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
     for (int kq = 0; kq < kend; kq += 4)
-      dmma_16x8x4(acc, sA[(kq + t) * NS_LD + g], sA[(kq + t) * NS_LD + g + 8], sB[(kq + t) * NS_LD + warp * 8 + g]);
+      dmma_16x8x4(acc, sA[(kq + t) * NS_LDA + g], sA[(kq + t) * NS_LDA + g + 8], sB[(kq + t) * NS_LDB + g]);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) part[(c * 4 + q) * 32 + lane] = acc[q];
+    __syncwarp();  // every lane is done with this slot before the next copy into it
   }
   cp_async_wait<0>();
-  double* __restrict__ C = P->C;
-  const int c0 = n0 + warp * 8 + 2 * t;
-#pragma unroll
-  for (int hh = 0; hh < 2; ++hh) {
-    const int r = m0 + g + 8 * hh;
-    if (r < P->m) {
-      if (c0 < P->n) C[static_cast<size_t>(r) * P->ldc + c0] = acc[2 * hh];
-      if (c0 + 1 < P->n) C[static_cast<size_t>(r) * P->ldc + c0 + 1] = acc[2 * hh + 1];
-    }
-  }
+  __syncthreads();
+  // Warp w adds up fragment value q = w (the FP64 adds of one warp are slow
+  // on GB300, so the four values are summed side by side), chunk by chunk.
+  static_assert(NS_WARPS == 4, "one warp per value of an m16n8 f64 fragment");
+  const int q = warp;
+  double tot = 0.0;
+  for (int c = 0; c < chunks; ++c) tot = tot + part[(c * 4 + q) * 32 + lane];
+  const int r = m0 + g + 8 * (q >> 1), col = n0 + 2 * t + (q & 1);
+  if (r < P->m && col < P->n) P->C[static_cast<size_t>(r) * P->ldc + col] = tot;
 }
 
 __global__ void __launch_bounds__(NS_THREADS) native_fp64_small_kernel(const __grid_constant__ NativeArgs args) {
@@ -246,13 +280,9 @@ __global__ void __launch_bounds__(NS_THREADS) native_fp64_small_kernel(const __g
   const Problem* P = args.table ? &args.table[find_problem(args.table, args.count, tile)] : &args.single;
   const int local = tile - P->tile_begin;
   if (P->n <= 0 || P->m <= 0 || local < 0 || local >= P->tiles_m * P->tiles_n) return;
-  const int m0 = (local / P->tiles_n) * NS_TILE;
-  const int n0 = (local % P->tiles_n) * NS_TILE;
-  if (P->ta) {
-    if (P->tb) small_tile<true, true>(P, m0, n0, ns_smem); else small_tile<true, false>(P, m0, n0, ns_smem);
-  } else {
-    if (P->tb) small_tile<false, true>(P, m0, n0, ns_smem); else small_tile<false, false>(P, m0, n0, ns_smem);
-  }
+  const int m0 = (local / P->tiles_n) * NS_TM;
+  const int n0 = (local % P->tiles_n) * NS_TN;
+  small_tile(P, m0, n0, ns_smem);
 }
 
 // ---------------------------------------------------------------------------
@@ -280,7 +310,7 @@ __device__ __forceinline__ const Problem* guard_problem(const GuardArgs& a, int 
   return a.table ? &a.table[p] : &a.single;
 }
 
-__global__ void __launch_bounds__(NT_THREADS, 4) guard_kernel(const __grid_constant__ GuardArgs args) {
+__global__ void __launch_bounds__(NT_THREADS, 2) guard_kernel(const __grid_constant__ GuardArgs args) {
   __shared__ __align__(16) double As[2][NT_BK][NT_LD];
   __shared__ __align__(16) double Bs[2][NT_BK][NT_LD];
   __shared__ int active[NT_THREADS];
@@ -350,14 +380,18 @@ __global__ void __launch_bounds__(NT_THREADS, 4) guard_kernel(const __grid_const
 
 // Host-side helpers --------------------------------------------------------
 
-// Problems below this size use the 16 x 16 kernel.
+// Problems with m, n and k at most this use the small kernel (16 x 8 tiles).
 constexpr int NATIVE_SMALL_MAX_N = 511;
 
-bool native_is_small(const Problem& p) { return p.m <= NATIVE_SMALL_MAX_N && p.n <= NATIVE_SMALL_MAX_N; }
+// (k too: the small kernel keeps one partial sum per 32-deep chunk, at most NS_MAX_CHUNKS)
+bool native_is_small(const Problem& p) {
+  return p.m <= NATIVE_SMALL_MAX_N && p.n <= NATIVE_SMALL_MAX_N && p.k <= NATIVE_SMALL_MAX_N;
+}
+static_assert((NATIVE_SMALL_MAX_N + 15) / 16 * 16 <= NS_MAX_CHUNKS * NS_KC, "small-kernel partial sums");
 
 void native_small_fill_tiles(Problem& p) {
-  p.tiles_m = p.m > 0 && p.n > 0 ? (p.m + NS_TILE - 1) / NS_TILE : 0;
-  p.tiles_n = p.m > 0 && p.n > 0 ? (p.n + NS_TILE - 1) / NS_TILE : 0;
+  p.tiles_m = p.m > 0 && p.n > 0 ? (p.m + NS_TM - 1) / NS_TM : 0;
+  p.tiles_n = p.m > 0 && p.n > 0 ? (p.n + NS_TN - 1) / NS_TN : 0;
 }
 
 cudaError_t native_small_launch(const Problem* table, const Problem* single, int count, int total_tiles,
@@ -367,9 +401,17 @@ cudaError_t native_small_launch(const Problem* table, const Problem* single, int
   args.table = table;
   if (single) args.single = *single;
   args.count = count;
-  const cudaError_t e = cudaFuncSetAttribute(native_fp64_small_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             NS_SMEM_BYTES);
+  // (the shared-memory opt-in is set once per device: a driver call per
+  // launch would weigh on the smallest products)
+  static bool opted[64] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64 || !opted[dev]) {
+    e = cudaFuncSetAttribute(native_fp64_small_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, NS_SMEM_BYTES);
+    if (e != cudaSuccess) return e;
+    if (dev >= 0 && dev < 64) opted[dev] = true;
+  }
   native_fp64_small_kernel<<<total_tiles, NS_THREADS, NS_SMEM_BYTES, stream>>>(args);
   return cudaGetLastError();
 }
@@ -406,7 +448,7 @@ cudaError_t guard_launch(const Problem* table, const Problem* single, int count,
   args.count = count;
   args.total_tiles = total_tiles;
   args.stats = stats;
-  guard_kernel<<<4 * num_sms, NT_THREADS, 0, stream>>>(args);
+  guard_kernel<<<2 * num_sms, NT_THREADS, 0, stream>>>(args);  // one wave: two blocks per SM
   return cudaGetLastError();
 }
 

@@ -6,7 +6,11 @@
 
 --sweep runs the benchmark's step instead: one grouped call over the paper's
 size sweep (N = 10, 100, 500, 1000, 1500, 2000, automatic plan), the exact
-launches bench.py times.
+launches bench.py times.  --profile creates the handle with MM_FLAG_PROFILE,
+as bench.py's per-kernel timing pass does: kernels one after another, each
+on every SM (without it, the accuracy certificate's launch is sized to run
+beside the slice products on its share of the SMs, which a profiler that
+serialises launches would show as a long launch on a few SMs).
 
 Generates seeded inputs (uniform [0, 1), seed 0), runs the product `reps`
 times through the C ABI and exits 0 if every call succeeded.  The operands of
@@ -30,6 +34,7 @@ def main() -> int:
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--dist", default="uniform01")
     ap.add_argument("--sweep", action="store_true", help="run the benchmark's grouped sweep step")
+    ap.add_argument("--profile", action="store_true", help="MM_FLAG_PROFILE: the bench's per-kernel timing pass")
     args = ap.parse_args()
 
     import torch
@@ -41,7 +46,7 @@ def main() -> int:
         pairs = [workload.pair("uniform01", 0, n) for n in workload.SWEEP_SIZES]
         As = [torch.from_numpy(a).cuda() for a, _ in pairs]
         Bs = [torch.from_numpy(b).cuda() for _, b in pairs]
-        with mm.Handle("auto") as h:
+        with mm.Handle("auto", flags=mm.FLAG_PROFILE if args.profile else 0) as h:
             for _ in range(args.reps):
                 h.gemm_grouped(As, Bs)
             h.check()

@@ -142,6 +142,41 @@ def test_precision_per_moduli_count_n2000():
     report("precision_modular_n2000.json", out)
 
 
+def test_precision_per_int8_slice_count_n2000():
+    # The INT8 slice form (signed-byte digits of the (8s - 2)-bit value,
+    # int32 accumulation): error against the plain product per digit count,
+    # raw and with the certificate (and the share it sent to native FP64).
+    import paper_1012_2273_gb300 as mm
+    n = 2000
+    out = {"N": n, "bound_2Nu": 2 * n * U, "rows": {}, "guarded": {}}
+    for dist in ("uniform11", "loguniform20"):
+        A, B = workload.pair(dist, 3, n)
+        r = rows_of(n, 10)
+        ref = oracle.gemm_rows(A, B, r)
+        absab = np.abs(A[r]) @ np.abs(B)
+        errs, guarded = {}, {}
+        for s in range(2, 9):
+            with mm.Handle("int8", slices=s, flags=mm.FLAG_NO_GUARD) as h:
+                C = host(h.gemm(dev(A), dev(B)))
+                h.check()
+            errs[f"s={s}"] = float(np.max(np.abs(C[r] - ref) / absab))
+            if s == 8:
+                np.testing.assert_array_equal(C[r[:2]].view(np.int64), oracle.i8_gemm(A, B, s, rows=r[:2]).view(np.int64))
+            with mm.Handle("int8", slices=s) as h:
+                Cg = host(h.gemm(dev(A), dev(B)))
+                h.check()
+                replaced, _ = h.guard_read()
+            e = float(np.max(np.abs(Cg[r] - ref) / absab))
+            guarded[f"s={s}"] = {"error": e, "replaced_fraction": replaced / (n * n)}
+            assert e <= 2 * n * U
+        out["rows"][dist] = errs
+        out["guarded"][dist] = guarded
+        seq = [errs[f"s={s}"] for s in range(2, 9)]
+        assert all(b <= a * 1.01 + 2 * n * U for a, b in zip(seq, seq[1:])), seq
+        assert errs["s=8"] <= 2 * n * U
+    report("precision_int8_n2000.json", out)
+
+
 @pytest.mark.parametrize("n", [4096, 8192])
 def test_precision_large_sizes_rows(n):
     import paper_1012_2273_gb300 as mm

@@ -101,12 +101,13 @@ def test_host_entry_point(h):
 
 
 def test_native_bitwise_reproducible_across_runs_tile_shapes_and_calls():
-    # Each output of the native form is one chain of mma.sync over k in
-    # increasing order in both tile shapes (16 x 16 below 512 rows and
-    # columns, 64 x 64 above), with no split-K and no atomics, so the result
-    # is bitwise reproducible: across runs, between the two kernels (a 500 x
-    # 500 product against the first 500 rows of a 600 x 500 one with the same
-    # rows of A) and between single and grouped calls.
+    # Each output of the native form is summed in one fixed order in both
+    # kernels (16 x 8 tiles with the k chunks shared over four warps below 512
+    # rows, columns and depth; 64 x 64 tiles above): chains of mma.sync over
+    # 32-deep chunks of k, the chunks' sums added left to right; no atomics.
+    # So the result is bitwise reproducible: across runs, between the two
+    # kernels (a 500 x 500 product against the first 500 rows of a 600 x 500
+    # one with the same rows of A) and between single and grouped calls.
     import torch
     import paper_1012_2273_gb300 as mm
     n = 500
