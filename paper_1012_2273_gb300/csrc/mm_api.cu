@@ -195,19 +195,23 @@ void prof_end(mm_handle h, cudaStream_t s, long mark) {
 
 // Built-in plan table (a tune file overrides it): the output of
 // paper_1012_2273_gb300.autotune on a GB300 (tune/gb300.tune), which times
-// every plan with the accuracy certificate on, on uniform and log-uniform
-// (2^+-20) inputs, and keeps the fastest whose slower class stays within the
-// bound.  Below N = 256 native FP64 is as fast; from there the modular form
-// with the fewest moduli that rarely send elements back to native FP64: 16 up
-// to N = 511, 15 up to 1999, 14 above (13 moduli, narrower still, would
-// recompute nearly every log-uniform element natively).  Beyond the modular
-// form's size limit the digit form with 6 digits.
+// every plan with the accuracy certificate on, as the mean over uniform and
+// log-uniform (2^+-20) inputs -- native recomputation of what the certificate
+// sends back included -- and keeps the fastest accurate one.  Below N = 256
+// native FP64 is as fast; from there the modular form with 14 to 16 moduli
+// (the tuner's pick per bucket; neighbouring counts are within a few percent
+// of each other, 13 moduli would recompute nearly every log-uniform element
+// natively).  Beyond the modular form's size limit the digit form with 6
+// digits.
 void default_tune(mm_handle h) {
   h->tune.clear();
   h->tune.push_back({255, Plan{0, 7, 256, 0}});
-  h->tune.push_back({511, Plan{2, 16, 128, 0}});
-  h->tune.push_back({767, Plan{2, 15, 128, 0}});
-  h->tune.push_back({1999, Plan{2, 15, 256, 0}});
+  h->tune.push_back({511, Plan{2, 15, 128, 0}});
+  h->tune.push_back({767, Plan{2, 16, 128, 0}});
+  h->tune.push_back({1023, Plan{2, 16, 256, 0}});
+  h->tune.push_back({1535, Plan{2, 15, 256, 0}});
+  h->tune.push_back({1999, Plan{2, 14, 256, 0}});
+  h->tune.push_back({3071, Plan{2, 15, 256, 0}});
   h->tune.push_back({65535, Plan{2, 14, 256, 0}});
   h->tune.push_back({1 << 30, Plan{1, 6, 256, 0}});
 }
