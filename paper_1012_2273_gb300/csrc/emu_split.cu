@@ -57,13 +57,19 @@ __device__ __forceinline__ int split_find(const SplitArgs& a, int tile, const Pr
   return lo;
 }
 
-// Pairs of exact digit floats become bf16x2 with one round-to-nearest
-// conversion, exact for integers of at most 8 significant bits.  Output:
-// packed bf16x2 words, word w of element q holds digit planes (2w, 2w+1).
+// Pairs of exact digit floats become bf16x2.  An integer of at most 8
+// significant bits (every digit, residue and magnitude digit here: |x| <=
+// 256) has zeros in the low 16 bits of its FP32 pattern, so the upper half
+// of that pattern is its bf16 pattern exactly: one byte permute per pair
+// (lo in the low half), no conversion.
 __device__ __forceinline__ uint32_t bf16x2_of_digits(float lo, float hi) {
-  uint32_t r;
-  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
-  return r;
+  return __byte_perm(__float_as_uint(lo), __float_as_uint(hi), 0x7632);
+}
+
+// The exact float of an integer 0 <= m < 2^23, without a conversion
+// instruction: 2^23 + m has m in its low mantissa bits.
+__device__ __forceinline__ float small_uint_float(uint32_t m) {
+  return __uint_as_float(0x4B000000u | m) - 8388608.0f;
 }
 
 // Accuracy certificate (guard.cuh), for the 8 fixed-point values D of one
@@ -90,8 +96,8 @@ __device__ __forceinline__ void guard_item(const long long (&D)[8], int width, v
     uint32_t w[4];
 #pragma unroll
     for (int p = 0; p < 4; ++p) {
-      w[p] = bf16x2_of_digits(static_cast<float>(mag7_of(D[2 * p], width)),
-                              static_cast<float>(mag7_of(D[2 * p + 1], width)));
+      w[p] = bf16x2_of_digits(small_uint_float(mag7_of(D[2 * p], width)),
+                              small_uint_float(mag7_of(D[2 * p + 1], width)));
       sum += sum24_of(D[2 * p], width, true) + sum24_of(D[2 * p + 1], width, true);
     }
     *reinterpret_cast<uint4*>(mag_out) = make_uint4(w[0], w[1], w[2], w[3]);

@@ -83,7 +83,7 @@ __host__ __device__ __forceinline__ void digits_of(int64_t D, float (&out)[S]) {
   }
   // d_1 = floor(D / 2^SH) plus the carry out of the low part; |d_1| <= 128.
   const int d1 = static_cast<int>(D >> SH) + static_cast<int>(low >> SH);
-  out[0] = static_cast<float>(d1);
+  out[0] = digit_float(static_cast<uint32_t>(d1 + 128));  // d1 + 128 in [0, 256]: exact as well
 }
 
 }  // namespace mmk

@@ -72,9 +72,10 @@ __global__ void __launch_bounds__(256) slots_recombine_kernel(const __grid_const
 }
 
 // Recombination of the modular form with K moduli, after the slice-product
-// kernel: one thread per 4 consecutive outputs of a tile row (one 8-byte
-// word per residue group; 2 lanes read a row's 16 contiguous bytes, a warp 16
-// rows).  With T_g = X w_g mod M_g from the epilogue (w_g = (M/M_g)^-1 mod
+// kernel: one thread per 2 consecutive outputs of a tile row (one 4-byte
+// word per residue group; 4 lanes read a row's 16 contiguous bytes, a warp 8
+// rows -- few enough registers that 6 blocks of 256 threads fit on an SM,
+// whose warps hide the latency of the loads and of the integer chains).  With T_g = X w_g mod M_g from the epilogue (w_g = (M/M_g)^-1 mod
 // M_g, M_g the product of group g's moduli), V = sum_g T_g (M/M_g) is
 // congruent to X modulo M = m_1...m_K and V / M = sum_g T_g / M_g < ceil(K/2).
 // Because |X| < M/2 - M/514 (the width rule), X = V - round(V/M) M, and
@@ -83,7 +84,7 @@ __global__ void __launch_bounds__(256) slots_recombine_kernel(const __grid_const
 // accumulators of 32-bit limbs (each term below 2^48, at most 8 of them; the
 // limbs above W_g's highest nonzero one only receive carries), carried, and X
 // is formed modulo 2^128, exact since |X| < 2^126.  Then one
-// rounding: c = RN(X) 2^(e_i + f_k - 2 beta).  The four outputs' multiply-add
+// rounding: c = RN(X) 2^(e_i + f_k - 2 beta).  The two outputs' multiply-add
 // chains are interleaved.
 template <int K, int BN>
 __device__ __forceinline__ void mod_recombine_tile(const EmuArgs& args, const Problem* P, int tile_local,
@@ -92,25 +93,25 @@ __device__ __forceinline__ void mod_recombine_tile(const EmuArgs& args, const Pr
   constexpr size_t SLOT = static_cast<size_t>(EM_BM) * BN;  // 16-bit entries per slot
   constexpr int QS = limbs_bit_length(mod_product(K)) - 31;  // V 2^-QS < 2^34
   constexpr int LW = mod_weight_limbs(K);                      // nonzero limbs of every W_g
-  // in_tile = ((c8 * 128 + r) * 2 + q): 8-column group c8, row r, half q of
-  // the row's 16 bytes
-  const int q = in_tile & 1, r = (in_tile >> 1) & (EM_BM - 1), c8 = in_tile >> 8;
+  // in_tile = ((c8 * 128 + r) * 4 + q): 8-column group c8, row r, quarter q
+  // of the row's 16 bytes
+  const int q = in_tile & 3, r = (in_tile >> 2) & (EM_BM - 1), c8 = in_tile >> 9;
   int tm, tn;
   emu_tile_coords(tile_local, P->tiles_m, P->tiles_n, &tm, &tn);
-  const int n = P->n, row = tm * EM_BM + r, col0 = tn * BN + 8 * c8 + 4 * q;
+  const int n = P->n, row = tm * EM_BM + r, col0 = tn * BN + 8 * c8 + 2 * q;
   if (row >= P->m || col0 >= n) return;
   const uint16_t* at = reinterpret_cast<const uint16_t*>(args.tilebuf + P->slot_base) +
                        static_cast<size_t>(tile_local) * NG * SLOT + static_cast<size_t>(c8) * (EM_BM * 8) + r * 8 +
-                       q * 4;
-  uint2 v[NG];
+                       q * 2;
+  uint32_t v[NG];
 #pragma unroll
-  for (int g = 0; g < NG; ++g) v[g] = __ldcs(reinterpret_cast<const uint2*>(at + g * SLOT));
-  uint64_t a[4][4] = {};
+  for (int g = 0; g < NG; ++g) v[g] = __ldcs(reinterpret_cast<const uint32_t*>(at + g * SLOT));
+  uint64_t a[2][4] = {};
 #pragma unroll
   for (int g = 0; g < NG; ++g) {
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      const uint32_t T = ((c < 2 ? v[g].x : v[g].y) >> (16 * (c & 1))) & 0xFFFFu;
+    for (int c = 0; c < 2; ++c) {
+      const uint32_t T = (v[g] >> (16 * c)) & 0xFFFFu;
 #pragma unroll
       for (int l = 0; l < LW; ++l) a[c][l] += static_cast<uint64_t>(T) * c_mod.wg[K][g][l];
     }
@@ -120,7 +121,7 @@ __device__ __forceinline__ void mod_recombine_tile(const EmuArgs& args, const Pr
   const int base_scale = P->a_exp[row] - 2 * P->beta;
   double* crow = P->C + static_cast<size_t>(row) * P->ldc;
 #pragma unroll
-  for (int c = 0; c < 4; ++c) {
+  for (int c = 0; c < 2; ++c) {
     if (col0 + c < n) {
       const uint64_t a1 = a[c][1] + (a[c][0] >> 32);
       const uint64_t a2 = a[c][2] + (a1 >> 32);
@@ -128,8 +129,12 @@ __device__ __forceinline__ void mod_recombine_tile(const EmuArgs& args, const Pr
       const uint32_t w0 = static_cast<uint32_t>(a[c][0]), w1 = static_cast<uint32_t>(a1),
                      w2 = static_cast<uint32_t>(a2);
       // qt = round(V / M) from V 2^-QS in FP32 (for M > 2^100 the low 64
-      // bits of V move V / M by less than 2^-36 and are left out)
-      float vf = __ull2float_rn(a3) * pow2f(96 - QS) + __uint2float_rn(w2) * pow2f(64 - QS);
+      // bits of V move V / M by less than 2^-36 and are left out).  Only
+      // 32-bit conversions: a 64-bit one runs on the FP64 pipe, a small
+      // fraction of the others on GB300.  V < 2^(QS + 34), so bits 128 and up
+      // of a3 exist only when QS > 94.
+      float vf = __uint2float_rn(static_cast<uint32_t>(a3)) * pow2f(96 - QS) + __uint2float_rn(w2) * pow2f(64 - QS);
+      if constexpr (QS > 128 - 34) vf += __uint2float_rn(static_cast<uint32_t>(a3 >> 32)) * pow2f(128 - QS);
       if (QS < 100 - 31) vf += __uint2float_rn(w1) * pow2f(32 - QS) + __uint2float_rn(w0) * pow2f(-QS);
       const uint64_t qt = static_cast<uint64_t>(__float2int_rn(vf * c_mod.qscale[K]));
       // X = V - qt M modulo 2^128
@@ -147,8 +152,8 @@ __device__ __forceinline__ void mod_recombine_tile(const EmuArgs& args, const Pr
 // One launch for every modular problem of a group: each tile dispatches on
 // its problem's moduli count (uniform across the tile's threads).
 template <int BN>
-__global__ void __launch_bounds__(256) mod_recombine_kernel(const __grid_constant__ EmuArgs args, int tile0) {
-  constexpr int PER_TILE = EM_BM * BN / 4;  // threads per tile
+__global__ void __launch_bounds__(256, 6) mod_recombine_kernel(const __grid_constant__ EmuArgs args, int tile0) {
+  constexpr int PER_TILE = EM_BM * BN / 2;  // threads per tile
   const long long item = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
   const int tile = tile0 + static_cast<int>(item / PER_TILE);
   const int in_tile = static_cast<int>(item % PER_TILE);
@@ -197,7 +202,7 @@ cudaError_t slots_recombine_launch(int bn, const EmuArgs& args, int total_tiles,
 
 cudaError_t mod_recombine_launch(int bn, const EmuArgs& args, int tile0, int ntiles, cudaStream_t stream) {
   if (ntiles <= 0) return cudaSuccess;
-  const long long threads = static_cast<long long>(ntiles) * (EM_BM * bn / 4);
+  const long long threads = static_cast<long long>(ntiles) * (EM_BM * bn / 2);
   const unsigned blocks = static_cast<unsigned>((threads + 255) / 256);
   if (bn == 256)
     mod_recombine_kernel<256><<<blocks, 256, 0, stream>>>(args, tile0);

@@ -12,8 +12,9 @@ namespace mmk {
 constexpr int EM_BM = 128;  // rows of a C tile (tcgen05 M)
 
 // ---------------------------------------------------------------------------
-// One rounding of (hi:lo) * 2^scale to FP64, round-half-even, integer ops only
-// in the normal range.  (hi:lo) is a two's-complement 128-bit integer.
+// One rounding of (hi:lo) * 2^scale to FP64, round-half-even, integer ops
+// only.  (hi:lo) is a two's-complement 128-bit integer.  (Below the normal
+// range the 53-bit rounded value is rounded again onto the subnormal grid.)
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ double round_i128_scaled(int64_t hi_s, uint64_t lo, int scale) {
   uint64_t hi = static_cast<uint64_t>(hi_s);
@@ -50,16 +51,20 @@ __device__ __forceinline__ double round_i128_scaled(int64_t hi_s, uint64_t lo, i
     if (neg) bits |= 1ull << 63;
     return __longlong_as_double(static_cast<long long>(bits));
   }
-  // Outside the normal range: overflow, or a subnormal/zero result.
-  if (e > 1023) return neg ? -__longlong_as_double(0x7FF0000000000000ll) : __longlong_as_double(0x7FF0000000000000ll);
-  if (e <= -1076) return neg ? -0.0 : 0.0;  // at most half the smallest subnormal
-  // -1076 < e < -1022: scale exactly into the normal range, then one rounding
-  // multiplication onto the subnormal grid (as ldexp does).
-  double d = __longlong_as_double(static_cast<long long>((static_cast<uint64_t>(ex + 1023) << 52) |
-                                                         (mant & ((1ull << 52) - 1))));
-  if (neg) d = -d;
-  d = d * __longlong_as_double(static_cast<long long>(static_cast<uint64_t>(scale + 1000 + 1023) << 52));
-  return d * 0x1p-1000;
+  // Outside the normal range: overflow, or a subnormal/zero result -- in
+  // integer arithmetic too (an FP64 instruction here, even predicated off,
+  // would occupy GB300's slow FP64 pipe on every call).
+  const uint64_t sign = neg ? (1ull << 63) : 0ull;
+  if (e > 1023) return __longlong_as_double(static_cast<long long>(sign | 0x7FF0000000000000ull));
+  if (e <= -1076) return __longlong_as_double(static_cast<long long>(sign));  // at most half the smallest subnormal
+  // -1076 < e < -1022: the 53-bit mant times 2^(e - 52) rounds, half to even,
+  // onto the subnormal grid of 2^-1074 -- the one rounding that multiplying
+  // the normal double mant 2^(e - 52) by a power of two would make.  In units
+  // of 2^-1074 that is mant / 2^t with t = -1022 - e in [1, 53]; a result of
+  // 2^52 units is the smallest normal number, whose pattern is the same.
+  const int t = -1022 - e;
+  const uint64_t units = (mant + ((1ull << (t - 1)) - 1) + ((mant >> t) & 1)) >> t;
+  return __longlong_as_double(static_cast<long long>(sign | units));
 }
 
 // T = T * 2^shift_bits + v for a signed 64-bit v, on (hi:lo).
