@@ -10,14 +10,12 @@
 // products of weight t + u <= s + 1; the fixed-point reading of the split is
 // this library's, the paper itself has no emulation).
 //
-// Exactness.  Digits satisfy |d| <= 128, so one digit product is at most 2^14
-// in magnitude and a sum of 256 of them at most 2^22.  Each chunk accumulates
-// onto 1.5 * 2^23 (the epilogue stores that constant into the TMEM buffer
-// before handing it back), so every partial sum is an integer in [2^23, 2^24],
-// held exactly by the tensor core's FP32 accumulator, and the FP32 bit
-// pattern of 1.5 * 2^23 + x is 0x4B400000 + x: adding the drained bit
-// patterns in int32 accumulates the chunk sums exactly (the bias is removed
-// once per segment).
+// Exactness.  Digits (and residues) satisfy |d| <= 128, so one product is at
+// most 2^14 in magnitude and a sum of 1024 of them at most 2^24.  Every
+// integer of magnitude up to 2^24 is an FP32 value, so the tensor core's FP32
+// accumulator holds each partial sum of a 1024-deep chunk exactly; the
+// chunk's first MMA starts from zero (no accumulate) and the epilogue converts
+// the chunk sums to int32 and adds them up, exactly.
 // An int32 segment sum stays below 2^31 because the host limits the pairs per
 // segment to floor((2^31 - 1) / (N 2^14)).  The recombination reads the
 // segment sums back in 128-bit integer arithmetic and rounds once -- no FP64
@@ -38,7 +36,7 @@
 //               into a STAGES-deep shared-memory ring (mbarrier full/empty)
 //   warp 1      allocates TMEM; one lane issues tcgen05.mma (M=128, N=BN,
 //               K=16, bf16 -> fp32) into one of two TMEM accumulators,
-//               switching after every 256-deep chunk
+//               switching after every 1024-deep chunk
 //   warps 2-3   idle (present so the register budget, kept per 4-warp group,
 //               is not wasted on a partial group)
 //   warps 4-11  drain accumulators (tcgen05.ld) into int32 registers, write
@@ -57,7 +55,7 @@ namespace mmk {
 static __constant__ ModTables c_mod = make_mod_tables();
 
 constexpr int EM_BK = 64;          // elements per k-block: one 128-byte swizzle row
-constexpr int EM_CHUNK_KB = 4;     // k-blocks per exact chunk: 256 digit products
+constexpr int EM_CHUNK_KB = 16;    // k-blocks per exact chunk: 1024 products, sums within 2^24
 constexpr int EM_UNIT_RING = 4;    // work units the producer may claim ahead of the consumers
 constexpr int EM_THREADS = 384;    // 12 warps: registers are budgeted per 4-warp group
 constexpr int EM_REGS_LAUNCH = 168;  // 65536 / 384, rounded down to a multiple of 8
@@ -65,7 +63,6 @@ constexpr int EM_REGS_CTRL = 56;     // warpgroup 0 after setmaxnreg.dec
 constexpr int EM_REGS_EPI = 224;     // warpgroups 1-2 after setmaxnreg.inc
 static_assert(128 * EM_REGS_CTRL + 256 * EM_REGS_EPI == EM_THREADS * EM_REGS_LAUNCH,
               "register split must add up to the launch allocation");
-constexpr uint32_t EM_MAGIC = 0x4B400000u;
 
 template <int BN>
 struct EmuCfg {
@@ -356,7 +353,7 @@ __global__ void __launch_bounds__(EM_THREADS, 1)
           p += np;
           const int nb = np * KB;
           for (int c0 = 0; c0 < nb && ok; c0 += EM_CHUNK_KB) {
-            // phase 0 of each buffer is the epilogue's first bias store
+            // phase 0 of each buffer is the epilogue's first arrival
             if (!mbar_wait(&acc_empty[abuf], aphase, tmo, args.status)) {
               ok = false;
               break;
@@ -375,9 +372,9 @@ __global__ void __launch_bounds__(EM_THREADS, 1)
               const uint64_t bdesc = smem_desc_k_sw128(sa + Cfg::A_BYTES);
 #pragma unroll
               for (int k = 0; k < EM_BK / 16; ++k) {
-                // advance 16 elements = 32 bytes = 2 units of the address field
-                // always accumulate: the buffer holds 1.5 * 2^23 at a chunk's start
-                tc_mma_bf16(d_tmem, adesc + 2 * k, bdesc + 2 * k, idesc, 1u);
+                // advance 16 elements = 32 bytes = 2 units of the address field;
+                // a chunk's first MMA overwrites the buffer
+                tc_mma_bf16(d_tmem, adesc + 2 * k, bdesc + 2 * k, idesc, (b != c0 || k != 0) ? 1u : 0u);
               }
               tc_commit(&empty[stage]);
               if (++stage == Cfg::STAGES) {
@@ -411,22 +408,10 @@ __global__ void __launch_bounds__(EM_THREADS, 1)
     bool ok = true;
     int uslot = 0;
     uint32_t uphase = 0;
-    // Both accumulators start every chunk at 1.5 * 2^23 (stored here, and again
-    // after each drain), so the MMAs' FP32 sums stay exact integers in [2^23,
-    // 2^24] whose bit patterns are 0x4B400000 + x: draining is one int32 add.
-    {
-      const uint32_t t0 = tmem_base + (static_cast<uint32_t>(32 * q) << 16) + static_cast<uint32_t>(h * HALF);
-#pragma unroll
-      for (int b = 0; b < 2; ++b)
-#pragma unroll
-        for (int c = 0; c < HALF; c += 4) tmem_st_32x32b_x4(t0 + b * BN + c, EM_MAGIC);
-      tmem_st_wait();
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) {
-        mbar_arrive(&acc_empty[0]);
-        mbar_arrive(&acc_empty[1]);
-      }
+    // Both accumulators start out free (a chunk's first MMA overwrites its buffer).
+    if (lane == 0) {
+      mbar_arrive(&acc_empty[0]);
+      mbar_arrive(&acc_empty[1]);
     }
     while (ok) {
       if (!mbar_wait(&ufull[uslot], uphase, tmo, args.status)) {
@@ -483,17 +468,15 @@ __global__ void __launch_bounds__(EM_THREADS, 1)
           tc_fence_after();
           const uint32_t taddr = tmem_base + (static_cast<uint32_t>(32 * q) << 16) +
                                  static_cast<uint32_t>(abuf * BN + h * HALF);
+          // the chunk sums are integers of magnitude <= 2^24: converted exactly
 #pragma unroll
           for (int part = 0; part < HALF / 32; ++part) {
             uint32_t r[32];
             tmem_ld_32x32b_x32(taddr + part * 32, r);
             tmem_ld_wait();
 #pragma unroll
-            for (int i = 0; i < 32; ++i) acc[part * 32 + i] += r[i];
+            for (int i = 0; i < 32; ++i) acc[part * 32 + i] += static_cast<uint32_t>(__float2int_rn(__uint_as_float(r[i])));
           }
-#pragma unroll
-          for (int c4 = 0; c4 < HALF; c4 += 4) tmem_st_32x32b_x4(taddr + c4, EM_MAGIC);
-          tmem_st_wait();
           tc_fence_before();
           __syncwarp();
           if (lane == 0) mbar_arrive(&acc_empty[abuf]);
@@ -501,7 +484,6 @@ __global__ void __launch_bounds__(EM_THREADS, 1)
           if (abuf == 0) aphase ^= 1;
         }
         if (!ok) break;
-        const uint32_t bias = static_cast<uint32_t>(nchunks) * EM_MAGIC;
         if (kCert) {
           // Certificate (guard.cuh): S = sum_j M_A M_B, exact, bounds (|A||B|)
           // from below; elements whose error bound it cannot certify are
@@ -523,7 +505,7 @@ __global__ void __launch_bounds__(EM_THREADS, 1)
           for (int w = 0; w < HALF / 32; ++w) bad[w] = 0u;
 #pragma unroll
           for (int i = 0; i < HALF; ++i) {
-            const bool fail = !cert_test(rowt, colt[i], acc[i] - bias, k2);
+            const bool fail = !cert_test(rowt, colt[i], acc[i], k2);
             if (in_row && n0 + h * HALF + i < n && fail) bad[i / 32] |= 1u << (i % 32);
           }
           uint32_t any = 0u;
@@ -563,7 +545,7 @@ __global__ void __launch_bounds__(EM_THREADS, 1)
           // warp's 32 rows contiguous.
           const int j = slot;
           const uint32_t m = c_mod.m_u[j], magic = c_mod.magic[j];
-          const uint32_t shift_in = c_mod.bias[j] - bias;  // x = acc - bias + bias_j
+          const uint32_t shift_in = c_mod.bias[j];  // x = S + bias_j
           if ((j & 1) == 0 && j + 1 < s) {  // first of a pair
             const uint32_t cy = c_mod.cy[s][j], cq = c_mod.cyq[s][j];
 #pragma unroll
@@ -618,7 +600,7 @@ __global__ void __launch_bounds__(EM_THREADS, 1)
             for (int i = 0; i < HALF; ++i) {
               const int col = n0 + h * HALF + i;
               if (col < n) {
-                const int32_t v = static_cast<int32_t>(acc[i] - bias);
+                const int32_t v = static_cast<int32_t>(acc[i]);
                 dst[col] = first ? v : dst[col] + v;
               }
             }
@@ -628,10 +610,10 @@ __global__ void __launch_bounds__(EM_THREADS, 1)
 #pragma unroll
           for (int i = 0; i < HALF; i += 4) {
             int4 v;
-            v.x = static_cast<int32_t>(acc[i] - bias);
-            v.y = static_cast<int32_t>(acc[i + 1] - bias);
-            v.z = static_cast<int32_t>(acc[i + 2] - bias);
-            v.w = static_cast<int32_t>(acc[i + 3] - bias);
+            v.x = static_cast<int32_t>(acc[i]);
+            v.y = static_cast<int32_t>(acc[i + 1]);
+            v.z = static_cast<int32_t>(acc[i + 2]);
+            v.w = static_cast<int32_t>(acc[i + 3]);
             __stcs(reinterpret_cast<int4*>(dst + (i >> 2) * (EM_BM * 4)), v);  // read once, by the recombination
           }
         }

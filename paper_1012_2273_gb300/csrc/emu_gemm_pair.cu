@@ -42,7 +42,7 @@ namespace {
 
 constexpr int PR_BN = 256;                              // columns of a pair tile
 constexpr int PR_BK = 64;                               // elements per k-block (one 128-byte swizzle row)
-constexpr int PR_CHUNK_KB = 4;                          // k-blocks per exact chunk (256 products)
+constexpr int PR_CHUNK_KB = 16;                         // k-blocks per exact chunk (1024 products)
 constexpr int PR_STAGES = 6;
 constexpr int PR_A_BYTES = EM_BM * PR_BK * 2;           // this CTA's 128 rows of A
 constexpr int PR_B_BYTES = (PR_BN / 2) * PR_BK * 2;     // this CTA's 128 rows of B^T
@@ -58,7 +58,6 @@ static_assert(128 * PR_REGS_CTRL + 256 * PR_REGS_EPI == PR_THREADS * 168, "regis
 constexpr int PR_PEND_BYTES = 8 * (PR_BN / 8) * 32 * 4;
 constexpr int PR_SMEM_BYTES = PR_STAGES * PR_STAGE_BYTES + 1024 /*align*/ + 512 /*barriers, ring*/ + PR_PEND_BYTES;
 static_assert(PR_SMEM_BYTES <= 227 * 1024, "shared memory of one CTA");
-constexpr uint32_t PR_MAGIC = 0x4B400000u;
 constexpr uint16_t PR_BOTH = 0x3;                       // multicast mask: both CTAs of the pair
 
 // ---- cluster and paired-tcgen05 wrappers ------------------------------------
@@ -134,12 +133,13 @@ __device__ __forceinline__ void tmem_dealloc_pair(uint32_t taddr, uint32_t ncols
   asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
 }
 // D[tmem of both CTAs] (+)= A[smem of both] * B[smem of both]; M = 256.
-__device__ __forceinline__ void tc_mma_pair(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc) {
+__device__ __forceinline__ void tc_mma_pair(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
+                                            uint32_t accumulate) {
   asm volatile(
       "{\n\t.reg .pred p;\n\t"
-      "setp.ne.b32 p, 1, 0;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
       "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-      "l"(a_desc), "l"(b_desc), "r"(idesc)
+      "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
       : "memory");
 }
 // Arrives on the mbarrier at bar's offset in every CTA of `mask` once the
@@ -341,7 +341,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(PR_THREADS, 1)
         mod_group_range(U.P->s, U.G, U.g, &p0, &p1);
         for (int p = p0; p < p1 && ok; ++p) {
           for (int c0 = 0; c0 < KB && ok; c0 += PR_CHUNK_KB) {
-            // phase 0 of each buffer is the epilogues' first bias store
+            // phase 0 of each buffer is the epilogues' first arrival
             if (!mbar_wait(&acc_empty[abuf], aphase, tmo, args.status)) {
               ok = false;
               break;
@@ -359,7 +359,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(PR_THREADS, 1)
               const uint64_t adesc = smem_desc_k_sw128(sa);
               const uint64_t bdesc = smem_desc_k_sw128(sa + PR_A_BYTES);
 #pragma unroll
-              for (int k = 0; k < PR_BK / 16; ++k) tc_mma_pair(d_tmem, adesc + 2 * k, bdesc + 2 * k, idesc);
+              for (int k = 0; k < PR_BK / 16; ++k)  // a chunk's first MMA overwrites the buffer
+                tc_mma_pair(d_tmem, adesc + 2 * k, bdesc + 2 * k, idesc, (b != c0 || k != 0) ? 1u : 0u);
               tc_commit_pair(&empty[stage], PR_BOTH);
               if (++stage == PR_STAGES) {
                 stage = 0;
@@ -389,20 +390,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(PR_THREADS, 1)
     bool ok = true;
     int uslot = 0;
     uint32_t uphase = 0;
-    // Both accumulators start every chunk at 1.5 * 2^23 (see emu_gemm.cu).
-    {
-      const uint32_t t0 = tmem_base + (static_cast<uint32_t>(32 * q) << 16) + static_cast<uint32_t>(h * HALF);
-#pragma unroll
-      for (int b = 0; b < 2; ++b)
-#pragma unroll
-        for (int c = 0; c < HALF; c += 4) tmem_st_32x32b_x4(t0 + b * PR_BN + c, PR_MAGIC);
-      tmem_st_wait();
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) {
-        mbar_arrive_remote(peer_addr(&acc_empty[0], 0));
-        mbar_arrive_remote(peer_addr(&acc_empty[1], 0));
-      }
+    // Both accumulators start out free (a chunk's first MMA overwrites its buffer).
+    if (lane == 0) {
+      mbar_arrive_remote(peer_addr(&acc_empty[0], 0));
+      mbar_arrive_remote(peer_addr(&acc_empty[1], 0));
     }
     while (ok) {
       if (!mbar_wait_cl(&ufull[uslot], uphase, tmo, args.status)) {
@@ -441,6 +432,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(PR_THREADS, 1)
           const uint32_t taddr = tmem_base + (static_cast<uint32_t>(32 * q) << 16) +
                                  static_cast<uint32_t>(abuf * PR_BN + h * HALF);
           // two loads in flight per wait: the drain is bound by load round trips
+          // chunk sums: integers of magnitude <= 2^24, converted exactly
 #pragma unroll
           for (int part = 0; part < HALF / 32; part += 2) {
             uint32_t r0[32], r1[32];
@@ -449,13 +441,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(PR_THREADS, 1)
             tmem_ld_wait();
 #pragma unroll
             for (int i = 0; i < 32; ++i) {
-              acc[part * 32 + i] += r0[i];
-              acc[(part + 1) * 32 + i] += r1[i];
+              acc[part * 32 + i] += static_cast<uint32_t>(__float2int_rn(__uint_as_float(r0[i])));
+              acc[(part + 1) * 32 + i] += static_cast<uint32_t>(__float2int_rn(__uint_as_float(r1[i])));
             }
           }
-#pragma unroll
-          for (int c4 = 0; c4 < HALF; c4 += 4) tmem_st_32x32b_x4(taddr + c4, PR_MAGIC);
-          tmem_st_wait();
           tc_fence_before();
           __syncwarp();
           if (lane == 0) mbar_arrive_remote(peer_addr(&acc_empty[abuf], 0));
@@ -464,9 +453,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(PR_THREADS, 1)
         }
         if (!ok) break;
         // Residue reduction exactly as in emu_gemm.cu's modular epilogue.
-        const uint32_t bias = static_cast<uint32_t>(nchunks) * PR_MAGIC;
         const uint32_t m = c_mod.m_u[j], magic = c_mod.magic[j];
-        const uint32_t shift_in = c_mod.bias[j] - bias;  // x = acc - bias + bias_j
+        const uint32_t shift_in = c_mod.bias[j];  // x = S + bias_j
         if ((j & 1) == 0 && j + 1 < s) {  // first of a pair
           const uint32_t cy = c_mod.cy[s][j], cq = c_mod.cyq[s][j];
 #pragma unroll

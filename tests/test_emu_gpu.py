@@ -76,12 +76,20 @@ def test_level_sums_match_model(n, s):
 
 
 def test_tensor_core_accumulation_is_exact_at_the_chunk_bound():
-    # Top digits of magnitude up to 128 with aligned signs drive 256-long chunk
-    # sums to about 2^22; any rounding inside the tensor core shows up here.
+    # One 1024-deep chunk (n = 1024): top digits of magnitude up to 128 with
+    # aligned signs drive its FP32 sums towards 2^24, the largest magnitude at
+    # which every integer is an FP32 value; any rounding inside the tensor core
+    # shows up here.  Row/column pairs 0-3 reach the bound exactly: 1024
+    # products of 128 * 128 (+2^24 and -2^24), and 127 * 127 (every partial
+    # sum after an odd number of products is odd and above 2^23).
     n, s = 1024, 1
     rng = np.random.default_rng(77)
     da = rng.integers(120, 129, (n, n)) * np.where(rng.random((n, n)) < 0.9, 1, -1)
     db = rng.integers(120, 129, (n, n)) * np.where(rng.random((n, n)) < 0.9, 1, -1)
+    da[0, :], db[:, 0] = 128, 128
+    da[1, :], db[:, 1] = -128, 128
+    da[2, :], db[:, 2] = 127, 127
+    da[3, :], db[:, 3] = -127, 127
     # x = d/128 (1 - 2^-40): every row and column maximum is below 1, so e = f = 0
     # and the single digit of x is d itself.
     A = da / 128.0 * (1 - 2.0 ** -40)
@@ -94,7 +102,9 @@ def test_tensor_core_accumulation_is_exact_at_the_chunk_bound():
     want = oracle.emu_level_sums(oracle.emu_digit_planes(A, oracle.emu_row_exponents(A), s, False),
                                  oracle.emu_digit_planes(B, oracle.emu_col_exponents(B), s, True))
     got = S.cpu().numpy().astype(np.int64)
-    assert np.abs(want).max() > 2 ** 23  # four chunks, each near the 2^22 bound
+    assert want[0, 0, 0] == 2 ** 24 and want[0, 1, 1] == -2 ** 24 and want[0, 2, 2] == 1024 * 127 * 127
+    assert np.abs(want).max() == 2 ** 24
+    assert (np.abs(want) > 2 ** 23).mean() > 0.5  # most sums near the bound
     np.testing.assert_array_equal(got, want)
 
 
