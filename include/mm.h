@@ -25,11 +25,11 @@
  *                   remainder theorem and rounded once to FP64 (after Ozaki,
  *                   Uchino and Imamura's "Ozaki scheme II", 2025): k products
  *                   instead of the s(s+1)/2 of the digit form.  Nothing in
- *                   the paper corresponds to it either.  With the
- *                   environment variable MM_PAIR_MMA=1, its tiles 256 columns
- *                   wide run on CTA pairs (paired tcgen05.mma, 256 x 256
- *                   tiles) instead of single CTAs: same results, measured
- *                   slower on GB300, hence off by default.
+ *                   the paper corresponds to it either.  Its tiles 256
+ *                   columns wide run on CTA pairs (paired tcgen05.mma, 256 x
+ *                   256 tiles), measured faster on GB300; the environment
+ *                   variable MM_PAIR_MMA=0 runs them on single CTAs instead
+ *                   (same results, bit for bit).
  *   MM_EMU_INT8     INT8 slice emulation: as MM_EMU_BF16 with s digits of
  *                   the (8s - 2)-bit fixed-point value, every digit a signed
  *                   byte (Ozaki-style slices with int32 accumulation), the

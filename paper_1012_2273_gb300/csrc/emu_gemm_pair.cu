@@ -26,9 +26,10 @@
 // the copies and MMAs they wait for order themselves through the mbarrier
 // (complete_tx, tcgen05.commit) and the tcgen05 fences; only the unit ring,
 // which carries a value stored by the other CTA, waits with cluster scope.
-// Every wait is bounded; on a timeout the roles stop and every thread meets
-// the final cluster barrier, so no CTA leaves while its peer may still touch
-// its shared memory, and the pair frees its tensor memory.
+// Every wait is bounded; on a timeout the roles stop, both CTAs meet at a
+// cluster barrier, stay resident long enough for every copy either of them
+// issued to land, and meet again before the pair frees its tensor memory, so
+// no CTA leaves while its peer, a copy or an MMA may still touch its memory.
 #include "launch.cuh"
 #include "modular.cuh"
 #include "recombine.cuh"
@@ -59,6 +60,7 @@ constexpr int PR_PEND_BYTES = 8 * (PR_BN / 8) * 32 * 4;
 constexpr int PR_SMEM_BYTES = PR_STAGES * PR_STAGE_BYTES + 1024 /*align*/ + 512 /*barriers, ring*/ + PR_PEND_BYTES;
 static_assert(PR_SMEM_BYTES <= 227 * 1024, "shared memory of one CTA");
 constexpr uint16_t PR_BOTH = 0x3;                       // multicast mask: both CTAs of the pair
+constexpr uint64_t PR_HOLD_NS = 1000000;                 // after a timeout: 1 ms for copies in flight to land
 
 // ---- cluster and paired-tcgen05 wrappers ------------------------------------
 __device__ __forceinline__ uint32_t cta_rank() {
@@ -299,9 +301,12 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(PR_THREADS, 1)
           }
         }
       }
-      // The leader waits until the copies still in flight (its own and the
-      // peer's) have landed; the final cluster barrier holds the peer until then.
-      if (leader) {
+      // After a normal end, the leader waits until the last copies (its own
+      // and the peer's) have landed.  After a timeout it does not: the peer
+      // may have stopped before its half of a stage, or gone one stage ahead
+      // of the leader, so the leader's barriers no longer say which copies
+      // are in flight; the hold before the final cluster barrier covers them.
+      if (leader && ok) {
         const int pending = issued < PR_STAGES ? static_cast<int>(issued) : PR_STAGES;
         for (int i = 1; i <= pending; ++i) {
           int st = stage - i;
@@ -310,7 +315,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(PR_THREADS, 1)
             st += PR_STAGES;
             ph ^= 1;
           }
-          mbar_wait(&full[st], ph, WIND_DOWN_NS, args.status);
+          if (!mbar_wait(&full[st], ph, tmo, args.status)) break;
         }
       }
     } else if (warp == 1 && lane == 0 && leader) {
@@ -504,6 +509,19 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(PR_THREADS, 1)
   }
 
   tc_fence_before();
+  __syncthreads();
+  // Every role of both CTAs has stopped issuing copies and MMAs (and the MMAs
+  // issued are done).
+  cluster_sync_all();
+  // If a wait ran out (the status word is set, here or anywhere), copies that
+  // either CTA issued may still be landing in its shared memory and on the
+  // leader's barriers: both CTAs stay resident for PR_HOLD_NS, far longer
+  // than any copy takes, before either leaves.
+  if (threadIdx.x == 0 && args.status && *reinterpret_cast<volatile int*>(args.status) != 0) {
+    const uint64_t t0 = globaltimer_ns();
+    while (globaltimer_ns() - t0 < PR_HOLD_NS) {
+    }
+  }
   __syncthreads();
   // No CTA leaves (or frees tensor memory) while its peer may still read its
   // shared memory, signal its barriers or write its tensor memory.

@@ -329,7 +329,7 @@ struct EmuGroup {
   int guard_tiles = 0;  // blocks of the guard kernel's whole-problem part
   std::vector<Problem> ps;
   std::vector<int> max_off;        // offset of problem p in the maxbits arrays
-  std::vector<CUtensorMap> maps;   // 2 per problem
+  std::vector<CUtensorMap> maps;   // 2 per problem; CTA pairs with the certificate: 2 more per problem after those
   std::vector<int4> units;         // grouped launches: {problem, tile, group, cost}
   std::vector<int4> cert_units;    // grouped launches: the certificate's {problem, tile, 0, cost}
   int cert_total = 0;              // units of the certificate's launch
@@ -373,19 +373,21 @@ int choose_groups_single(int tiles, int s, bool modular, int kb, int sms, int ma
 // Sizes the group's workspace and work units; with `base` set, also points
 // the problems into it and encodes the tensor maps.
 // CTA pairs (cta_group::2) for the modular form at bn 256 only with
-// MM_PAIR_MMA=1: on GB300 the paired kernel measured slower than the
-// single-CTA one over the paper's size sweep (0.309 against 0.278 ms of
-// residue products per step), so it is opt-in.
+// The modular form at tile width 256 runs its residue products on CTA pairs
+// (cta_group::2): on GB300 they measured faster than single CTAs at every
+// size (the paper's sweep: 0.267 against 0.274 ms; N = 8192: 1874 against
+// 1727 TFLOP/s of residue products).  MM_PAIR_MMA=0 selects the single-CTA
+// kernel.
 bool pair_mma_enabled() {
   const char* e = std::getenv("MM_PAIR_MMA");
-  return e && e[0] == '1';
+  return !(e && e[0] == '0');
 }
 
 mm_status layout_group(mm_handle h, EmuGroup& g, char* base) {
   Arena ar;
   g.total_tiles = g.total_split = g.total_absmax = g.max_rows = 0;
-  // (the CTA-pair kernel has no certificate unit: it runs only unguarded)
-  g.pair = g.form == 2 && g.bn == 256 && pair_mma_enabled() && h->num_sms >= 2 && !g.guard;
+  // (with CTA pairs the certificate's launch still runs on single CTAs, with tensor maps of its own)
+  g.pair = g.form == 2 && g.bn == 256 && pair_mma_enabled() && h->num_sms >= 2;
   g.guard_tiles = 0;
   int maxk = 0;
   g.max_off.assign(g.ps.size(), 0);
@@ -566,7 +568,14 @@ mm_status layout_group(mm_handle h, EmuGroup& g, char* base) {
       cert_kb += tiles * kb;
     }
     g.cert_grid = std::max(1, std::min(g.cert_total, static_cast<int>(std::lround(slots * cert_kb / (main_kb + cert_kb)))));
-    if (!h->profile && !g.pair && slots > g.cert_grid) g.grid = std::max(1, std::min(g.grid, slots - g.cert_grid));
+    if (!h->profile && slots > g.cert_grid) {
+      if (g.pair) {  // whole clusters of two; an SM left over goes to the certificate
+        g.grid = 2 * std::max(1, std::min(g.grid / 2, (slots - g.cert_grid) / 2));
+        g.cert_grid = std::max(g.cert_grid, std::min(g.cert_total, slots - g.grid));
+      } else {
+        g.grid = std::max(1, std::min(g.grid, slots - g.cert_grid));
+      }
+    }
     if (h->profile) g.cert_grid = std::min(g.cert_total, slots);
   }
   // Everything zeroed before a launch sits in one run (one memset): the
@@ -607,13 +616,19 @@ mm_status layout_group(mm_handle h, EmuGroup& g, char* base) {
   g.bytes = ar.off;
   g.base = base;
   if (base) {
-    g.maps.assign(2 * g.ps.size(), CUtensorMap{});
-    for (size_t i = 0; i < g.ps.size() && g.form != 3; ++i) {  // (the INT8 kernel copies with cp.async)
+    // CTA pairs stage half of a B^T tile per CTA; the certificate's launch
+    // (single CTAs) then gets maps of its own with whole tiles.
+    const bool cert_maps = g.pair && g.guard;
+    const size_t np = g.ps.size();
+    g.maps.assign((cert_maps ? 4 : 2) * np, CUtensorMap{});
+    for (size_t i = 0; i < np && g.form != 3; ++i) {  // (the INT8 kernel copies with cp.async)
       const Problem& p = g.ps[i];
       const long planes = p.s + (g.guard ? 1 : 0);
       if (!make_plane_map(&g.maps[2 * i], p.a_slices, p.k_pad, planes * p.m_pad, 128) ||
           !make_plane_map(&g.maps[2 * i + 1], p.b_slices, p.k_pad, planes * p.n_pad,
-                          g.pair ? g.bn / 2 : g.bn))
+                          g.pair ? g.bn / 2 : g.bn) ||
+          (cert_maps && (!make_plane_map(&g.maps[2 * np + 2 * i], p.a_slices, p.k_pad, planes * p.m_pad, 128) ||
+                         !make_plane_map(&g.maps[2 * np + 2 * i + 1], p.b_slices, p.k_pad, planes * p.n_pad, g.bn))))
         return fail(h, MM_ERR_CUDA, "cuTensorMapEncodeTiled failed");
     }
   }
@@ -671,10 +686,13 @@ mm_status run_group(mm_handle h, const EmuGroup& g, const Problem* d_table, cons
       cs = h->cert_stream;
       cert_forked = true;
     }
+    // maps of the certificate's single-CTA tiles (after the pairs' maps)
+    const size_t cm = g.pair ? 2 * g.ps.size() : 0;
+    if (d_maps) c.maps = d_maps + cm;
     const long m_c = prof_start(h, cs, KIND_SLICE_GEMM);
     const cudaError_t ce =
         g.form == 3 ? mmk::i8_cert_launch(c, g.cert_grid, cs)
-                    : mmk::emu_cert_launch(g.bn, &g.maps[0], &g.maps[1], c, g.cert_grid, cs);
+                    : mmk::emu_cert_launch(g.bn, &g.maps[cm], &g.maps[cm + 1], c, g.cert_grid, cs);
     prof_end(h, cs, m_c);
     if (ce != cudaSuccess) return cuda_fail(h, ce, "certificate launch");
     if (cert_forked) MM_CUDA(h, cudaEventRecord(h->cert_join, cs));

@@ -50,14 +50,19 @@ def test_selftest_argument_checks():
         assert L.mm_selftest_wait(h._h, 60001, None) == 1
 
 
-def test_pipeline_waits_that_run_out_wind_down_and_later_calls_are_exact(monkeypatch):
+@pytest.mark.parametrize("pair", ["1", "0"])
+def test_pipeline_waits_that_run_out_wind_down_and_later_calls_are_exact(monkeypatch, pair):
     # A limit of 100 ns on every wait of the slice-product pipeline (TMA
     # stages, accumulators, the unit ring): a normal N = 2000 product's waits
     # run out, the kernel records MM_ERR_TIMEOUT, lets its copies and MMAs
-    # finish (those waits keep their own 2 s limit), frees its tensor memory
-    # and returns.  Later calls on fresh handles with the default limit run
-    # (a leaked TMEM allocation would stall them) and are exact.
+    # finish (the waits for MMAs keep their own 2 s limit; CTA pairs hold
+    # both CTAs until every copy has landed), frees its tensor memory and
+    # returns.  Later calls on fresh handles with the default limit run (a
+    # leaked TMEM allocation would stall them) and are exact.  Both residue-
+    # product kernels: CTA pairs and single CTAs (with the certificate's
+    # single-CTA launch beside them).
     import paper_1012_2273_gb300 as mm
+    monkeypatch.setenv("MM_PAIR_MMA", pair)
     n, k = 2000, 14
     A, B = workload.pair("uniform11", 14, n)
     dA, dB = dev(A), dev(B)

@@ -241,13 +241,15 @@ def test_grouped_call_mixing_native_digit_and_modular_forms(tmp_path, use_graph)
     assert {f for f, _ in plans.values()} == {0, 1, 2}
 
 
+@pytest.mark.parametrize("pair", ["1", "0"])
 @pytest.mark.parametrize("use_graph", [True, False])
-def test_modular_cta_pair_kernel_bit_exact(tmp_path, monkeypatch, use_graph):
-    # The opt-in paired kernel (two CTAs per 256 x 256 tile) computes the same
-    # residue products: single problems (rows padded to 256) and a grouped
-    # call with uneven sizes and moduli counts, bit for bit.
+def test_modular_cta_pair_kernel_bit_exact(tmp_path, monkeypatch, use_graph, pair):
+    # The paired kernel (two CTAs per 256 x 256 tile, the default at tile
+    # width 256) and the single-CTA kernel (MM_PAIR_MMA=0) compute the same
+    # residue products: single problems (rows padded to 256 for pairs) and a
+    # grouped call with uneven sizes and moduli counts, bit for bit.
     import paper_1012_2273_gb300 as mm
-    monkeypatch.setenv("MM_PAIR_MMA", "1")
+    monkeypatch.setenv("MM_PAIR_MMA", pair)
     tune = tmp_path / "tune.txt"
     tune.write_text("300 2 14 256 0\n700 2 15 256 0\n100000 2 16 256 0\n")
     flags = 0 if use_graph else mm.FLAG_NO_GRAPH
@@ -271,3 +273,32 @@ def test_modular_cta_pair_kernel_bit_exact(tmp_path, monkeypatch, use_graph):
         else:
             assert_within_bound(C, oracle.gemm(A, B), oracle.absgemm(A, B), n)
     assert plans[1000] == (2, 16) and plans[300] == (2, 14)
+
+
+@pytest.mark.parametrize("pair", ["1", "0"])
+def test_modular_cta_pairs_beside_the_certificate(tmp_path, monkeypatch, pair):
+    # With the accuracy certificate on, the residue products (CTA pairs or
+    # single CTAs) run beside the certificate's own launch, which keeps
+    # single-CTA tiles with tensor maps of its own.  Uniform inputs pass the
+    # certificate everywhere, so the results are the model's bits and nothing
+    # is recomputed; grouped (graph and no graph) and single calls.
+    import paper_1012_2273_gb300 as mm
+    monkeypatch.setenv("MM_PAIR_MMA", pair)
+    tune = tmp_path / "tune.txt"
+    tune.write_text("300 2 15 256 0\n100000 2 16 256 0\n")
+    sizes = [129, 300, 385, 640, 1000, 1500]
+    pairs = [workload.pair("uniform11", 80 + i, n) for i, n in enumerate(sizes)]
+    for flags in (0, mm.FLAG_NO_GRAPH):
+        with mm.Handle("auto", flags=flags, tune_path=str(tune)) as h:
+            plans = {n: h.plan(n) for n in sizes}
+            A, B = pairs[3]
+            C1 = host(h.gemm(dev(A), dev(B)))
+            Cs = h.gemm_grouped([dev(a) for a, _ in pairs], [dev(b) for _, b in pairs])
+            h.check()
+            assert h.guard_read() == (0, 0)
+        k = plans[640][1]
+        assert_bits(C1, oracle.fixed_gemm(A, B, beta_of(k, 640)))
+        for (A, B), C, n in zip(pairs, Cs, sizes):
+            form, k = plans[n]
+            assert form == 2
+            assert_bits(host(C), oracle.fixed_gemm(A, B, beta_of(k, n)))

@@ -201,8 +201,9 @@ def test_rect_large_sampled_rows(tmp_path):
     assert np.all(np.abs(y) <= tol)
 
 
-def test_rect_cta_pair_kernel(monkeypatch):
-    monkeypatch.setenv("MM_PAIR_MMA", "1")
+@pytest.mark.parametrize("pair", ["1", "0"])
+def test_rect_cta_pair_kernel(monkeypatch, pair):
+    monkeypatch.setenv("MM_PAIR_MMA", pair)
     m, n, k = 700, 513, 900  # m padded to 768 rows (three 256-row pair tiles)
     A, B = workload.rect_pair("uniform11", 31, m, n, k)
     with handle("modular", 15) as h:
