@@ -199,7 +199,7 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
-KERNEL_SOURCES = ("emu_gemm.cu", "common.cuh", "launch.cuh", "modular.cuh", "recombine.cuh", "guard.cuh")
+KERNEL_SOURCES = ("emu_gemm_pair.cu", "common.cuh", "launch.cuh", "modular.cuh", "recombine.cuh", "tile_index.cuh")
 
 
 def source_digest() -> str:
@@ -285,21 +285,25 @@ def run_ours(args, dist: Dist):
             launches_per_step = sum(v[1] for v in p.values())
     hp.check()
     emu_sizes = [n for n in SWEEP if plan[n][0] != 0]
-    # tensor products per size: s(s+1)/2 digit pairs, or k residue products,
-    # plus the certificate's product of the magnitude planes (its own launch,
-    # timed with the slice products)
+    # tensor products per size: s(s+1)/2 digit pairs, or k residue products
+    # (the dominant kernel's launch); the certificate's product of the
+    # magnitude planes is a launch of its own, reported beside it
     pairs_of = {n: plan[n][1] * (plan[n][1] + 1) // 2 if plan[n][0] == 1 else plan[n][1] for n in emu_sizes}
-    tensor_flops = sum((pairs_of[n] + 1) * 2 * n ** 3 for n in emu_sizes)
+    tensor_flops = sum(pairs_of[n] * 2 * n ** 3 for n in emu_sizes)
+    cert_flops = sum(2 * n ** 3 for n in emu_sizes)
     gemm_ms = statistics.mean(kinds["slice_products"]) if emu_sizes else None
+    cert_ms = statistics.mean(kinds["certificate"]) if emu_sizes else None
+    all_modular = bool(emu_sizes) and all(plan[n][0] == 2 for n in emu_sizes)
     digest = source_digest()
     traffic, traffic_meta = profiled_traffic(digest)
     roofline = None
     if gemm_ms:
         achieved = tensor_flops / (gemm_ms / 1e3) / 1e12
         peak = peaks["bf16_tflops"]
-        roofline = {"kernel": "emu_gemm_kernel (tcgen05 bf16 digit or residue products with exact int32 "
-                              "accumulation, and the certificate's magnitude product; every launch of it "
-                              "the step makes)",
+        kernel = ("mod_gemm_pair_kernel (tcgen05.mma cta_group::2 bf16 residue products on CTA pairs, "
+                  "exact 1024-deep FP32 chunks, int32 sums reduced to paired residues in the epilogue)"
+                  if all_modular else "emu_gemm_kernel (tcgen05 bf16 slice products)")
+        roofline = {"kernel": kernel,
                     "bound": "tensor", "achieved": round(achieved, 2), "peak": peak, "unit": "TFLOP/s",
                     "frac": round(achieved / peak, 4),
                     "peak_source": f"{peaks['source']} bf16 dense burst (MEASURED_PEAKS.json bf16_tflops)",
@@ -309,8 +313,16 @@ def run_ours(args, dist: Dist):
                     "note": "bf16 products of 2N^3 flops each: " + ", ".join(
                         f"N={n}: " + (f"digits s={plan[n][1]}, {pairs_of[n]} pairs" if plan[n][0] == 1
                                       else f"moduli k={plan[n][1]}, {pairs_of[n]} residue products")
-                        + " + 1 certificate product"
-                        for n in emu_sizes)}
+                        for n in emu_sizes) + "; one launch per step, timed alone on every SM (profiling pass)"}
+        if cert_ms:
+            roofline["certificate_launch"] = {
+                "kernel": "emu_gemm_kernel<256, false, true> (the accuracy certificate's product of the "
+                          "magnitude planes, one per tile, single CTAs)",
+                "algorithmic_flops_per_launch": cert_flops, "avg_launch_ms": round(cert_ms, 4),
+                "achieved": round(cert_flops / (cert_ms / 1e3) / 1e12, 2),
+                "frac": round(cert_flops / (cert_ms / 1e3) / 1e12 / peak, 4),
+                "note": "timed alone on every SM in the profiling pass; in the timed step it runs beside the "
+                        "residue products on the SMs they leave"}
 
     # certificate: elements the step's calls sent to native FP64 (uniform
     # inputs: none), and the step without it (MM_FLAG_NO_GUARD) for context

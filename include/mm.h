@@ -220,12 +220,16 @@ mm_status mm_modular_params(int k, int N, int* beta, int* moduli);
 /* Device time of the last call made on this handle with MM_FLAG_PROFILE set,
  * in milliseconds, by kernel kind (events recorded on the call's stream):
  *   out_ms[0] scale and split (including zeroing of the row/column maxima)
- *   out_ms[1] slice products with fused recombination
+ *   out_ms[1] slice products (with the digit form's fused recombination)
  *   out_ms[2] native FP64 kernels (including the certificate's recomputation)
- *   out_ms[3] recombination run as its own pass (small problems, mm_recombine)
- * and launches[0..3] the number of kernel launches of each kind (may be
- * NULL).  Synchronises on the recorded events.  MM_ERR_INVALID without the flag. */
-mm_status mm_profile_read(mm_handle h, double out_ms[4], int launches[4]);
+ *   out_ms[3] recombination run as its own pass (small problems, the modular
+ *             form, mm_recombine)
+ *   out_ms[4] the accuracy certificate's product of the magnitude planes
+ * and launches[0..4] the number of kernel launches of each kind (may be
+ * NULL).  Both arrays hold MM_PROFILE_KINDS entries.  Synchronises on the
+ * recorded events.  MM_ERR_INVALID without the flag. */
+#define MM_PROFILE_KINDS 5
+mm_status mm_profile_read(mm_handle h, double out_ms[MM_PROFILE_KINDS], int launches[MM_PROFILE_KINDS]);
 
 /* Measures the FP64 throughput of this GPU with two calibration kernels
  * (independent chains of mma.sync m16n8k4 f64, and of scalar FP64 FMA),

@@ -61,7 +61,7 @@ SYMBOLS = ("mm_create", "mm_destroy", "mm_gemm", "mm_gemm_grouped", "mm_gemm_ex"
            "mm_split_noalloc",
            "mm_level_sums", "mm_recombine", "mm_modular_params")
 SPLIT_NOALLOC_MAX_N = 65536
-KERNEL_KINDS = ("split", "slice_products", "native_fp64", "recombine")
+KERNEL_KINDS = ("split", "slice_products", "native_fp64", "recombine", "certificate")
 
 
 def library_path() -> str:
@@ -339,8 +339,8 @@ class Handle:
 
     def profile(self) -> dict:
         """Per-kernel-kind device time (ms) and launch counts of the last call (MM_FLAG_PROFILE)."""
-        ms = (ctypes.c_double * 4)()
-        n = (ctypes.c_int * 4)()
+        ms = (ctypes.c_double * len(KERNEL_KINDS))()
+        n = (ctypes.c_int * len(KERNEL_KINDS))()
         self._raise(self._lib.mm_profile_read(self._h, ms, n))
         return {k: (ms[i], n[i]) for i, k in enumerate(KERNEL_KINDS)}
 

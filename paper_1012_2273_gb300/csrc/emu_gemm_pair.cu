@@ -7,9 +7,9 @@
 // m0 + 128 r .. of A and rows n0 + 128 r .. of B^T (half of the tile's
 // columns) in its shared memory, and its own tensor memory receives rows
 // m0 + 128 r .. of the tile, all 256 columns.  Per k-block a CTA stages 32 KB
-// instead of the single-CTA kernel's 48 KB, so six stages fit where four did,
-// and each SM's shared memory serves a third less operand traffic (A and its
-// half of B to the tensor core, TMA writes of the same).
+// instead of the single-CTA kernel's 48 KB, so seven stages fit where four
+// did, and each SM's shared memory serves a third less operand traffic (A and
+// its half of B to the tensor core, TMA writes of the same).
 //
 // Roles (both CTAs run the same code; rank 0 is the leader):
 //   warp 0      TMA producer of its own CTA's halves; both CTAs' copies
@@ -44,7 +44,7 @@ namespace {
 constexpr int PR_BN = 256;                              // columns of a pair tile
 constexpr int PR_BK = 64;                               // elements per k-block (one 128-byte swizzle row)
 constexpr int PR_CHUNK_KB = 16;                         // k-blocks per exact chunk (1024 products)
-constexpr int PR_STAGES = 6;
+constexpr int PR_STAGES = 7;
 constexpr int PR_A_BYTES = EM_BM * PR_BK * 2;           // this CTA's 128 rows of A
 constexpr int PR_B_BYTES = (PR_BN / 2) * PR_BK * 2;     // this CTA's 128 rows of B^T
 constexpr int PR_STAGE_BYTES = PR_A_BYTES + PR_B_BYTES;
@@ -54,10 +54,7 @@ constexpr int PR_THREADS = 384;
 constexpr int PR_REGS_CTRL = 56;
 constexpr int PR_REGS_EPI = 224;
 static_assert(128 * PR_REGS_CTRL + 256 * PR_REGS_EPI == PR_THREADS * 168, "register split");
-// residues of a pair's first modulus, per epilogue thread: 32 words (4 per
-// word) at [warp - 4][word][lane] -- each thread reads back only its own
-constexpr int PR_PEND_BYTES = 8 * (PR_BN / 8) * 32 * 4;
-constexpr int PR_SMEM_BYTES = PR_STAGES * PR_STAGE_BYTES + 1024 /*align*/ + 512 /*barriers, ring*/ + PR_PEND_BYTES;
+constexpr int PR_SMEM_BYTES = PR_STAGES * PR_STAGE_BYTES + 1024 /*align*/ + 512 /*barriers, ring*/;
 static_assert(PR_SMEM_BYTES <= 227 * 1024, "shared memory of one CTA");
 constexpr uint16_t PR_BOTH = 0x3;                       // multicast mask: both CTAs of the pair
 constexpr uint64_t PR_HOLD_NS = 1000000;                 // after a timeout: 1 ms for copies in flight to land
@@ -389,7 +386,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(PR_THREADS, 1)
     const int h = (warp - 4) >> 2;   // column half of the tile
     const int r_in_tile = 32 * q + lane;
     constexpr int HALF = PR_BN / 2;
-    uint32_t* pend = reinterpret_cast<uint32_t*>(smem + PR_STAGES * PR_STAGE_BYTES + 512) + (warp - 4) * (HALF / 4) * 32 + lane;
+    uint32_t pend[HALF / 4] = {};  // residues of a pair's first modulus, 4 per word
     int abuf = 0;
     uint32_t aphase = 0;
     bool ok = true;
@@ -439,16 +436,12 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(PR_THREADS, 1)
           // two loads in flight per wait: the drain is bound by load round trips
           // chunk sums: integers of magnitude <= 2^24, converted exactly
 #pragma unroll
-          for (int part = 0; part < HALF / 32; part += 2) {
-            uint32_t r0[32], r1[32];
+          for (int part = 0; part < HALF / 32; ++part) {
+            uint32_t r0[32];
             tmem_ld_32x32b_x32(taddr + part * 32, r0);
-            tmem_ld_32x32b_x32(taddr + (part + 1) * 32, r1);
             tmem_ld_wait();
 #pragma unroll
-            for (int i = 0; i < 32; ++i) {
-              acc[part * 32 + i] += static_cast<uint32_t>(__float2int_rn(__uint_as_float(r0[i])));
-              acc[(part + 1) * 32 + i] += static_cast<uint32_t>(__float2int_rn(__uint_as_float(r1[i])));
-            }
+            for (int i = 0; i < 32; ++i) acc[part * 32 + i] += static_cast<uint32_t>(__float2int_rn(__uint_as_float(r0[i])));
           }
           tc_fence_before();
           __syncwarp();
@@ -471,7 +464,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(PR_THREADS, 1)
               const uint32_t r = x - (__umulhi(x, magic) >> 7) * m;
               t[b] = r * cy - __umulhi(r, cq) * m;
             }
-            pend[(c / 4) * 32] = __byte_perm(__byte_perm(t[0], t[1], 0x0040), __byte_perm(t[2], t[3], 0x0040), 0x5410);
+            pend[c / 4] = __byte_perm(__byte_perm(t[0], t[1], 0x0040), __byte_perm(t[2], t[3], 0x0040), 0x5410);
           }
           continue;
         }
@@ -487,7 +480,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(PR_THREADS, 1)
 #pragma unroll
         for (int c = 0; c < HALF; c += 8) {
           uint32_t w[4];
-          const uint32_t pw0 = paired ? pend[(c / 4) * 32] : 0u, pw1 = paired ? pend[(c / 4 + 1) * 32] : 0u;
+          const uint32_t pw0 = paired ? pend[c / 4] : 0u, pw1 = paired ? pend[c / 4 + 1] : 0u;
 #pragma unroll
           for (int q2 = 0; q2 < 4; ++q2) {
             uint32_t T[2];

@@ -167,7 +167,8 @@ unsigned long long* guard_stats(mm_handle h) { return reinterpret_cast<unsigned 
 bool guard_on(mm_handle h) { return (h->cfg.flags & MM_FLAG_NO_GUARD) == 0; }
 
 // ---- MM_FLAG_PROFILE --------------------------------------------------------
-enum { KIND_SPLIT = 0, KIND_SLICE_GEMM = 1, KIND_NATIVE = 2, KIND_RECOMBINE = 3 };
+enum { KIND_SPLIT = 0, KIND_SLICE_GEMM = 1, KIND_NATIVE = 2, KIND_RECOMBINE = 3, KIND_CERT = 4 };
+static_assert(KIND_CERT + 1 == MM_PROFILE_KINDS, "profile kinds");
 
 void prof_reset(mm_handle h) {
   h->ev_used = 0;
@@ -689,7 +690,7 @@ mm_status run_group(mm_handle h, const EmuGroup& g, const Problem* d_table, cons
     // maps of the certificate's single-CTA tiles (after the pairs' maps)
     const size_t cm = g.pair ? 2 * g.ps.size() : 0;
     if (d_maps) c.maps = d_maps + cm;
-    const long m_c = prof_start(h, cs, KIND_SLICE_GEMM);
+    const long m_c = prof_start(h, cs, KIND_CERT);
     const cudaError_t ce =
         g.form == 3 ? mmk::i8_cert_launch(c, g.cert_grid, cs)
                     : mmk::emu_cert_launch(g.bn, &g.maps[cm], &g.maps[cm + 1], c, g.cert_grid, cs);
@@ -1192,10 +1193,10 @@ mm_status mm_destroy(mm_handle h) {
   return MM_OK;
 }
 
-mm_status mm_profile_read(mm_handle h, double out_ms[4], int launches[4]) {
+mm_status mm_profile_read(mm_handle h, double out_ms[MM_PROFILE_KINDS], int launches[MM_PROFILE_KINDS]) {
   if (!h || !out_ms) return MM_ERR_INVALID;
   if (!h->profile) return fail(h, MM_ERR_INVALID, "handle was created without MM_FLAG_PROFILE");
-  for (int k = 0; k < 4; ++k) {
+  for (int k = 0; k < MM_PROFILE_KINDS; ++k) {
     out_ms[k] = 0.0;
     if (launches) launches[k] = 0;
   }
