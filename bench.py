@@ -213,7 +213,7 @@ def source_digest() -> str:
 
 def profiled_traffic(kernel_digest: str):
     """DRAM bytes per launch of the slice-product kernel from a committed ncu summary, if current."""
-    path = os.path.join(ROOT, "profiles", "emu_gemm_traffic.json")
+    path = os.path.join(ROOT, "profiles", "mod_gemm_pair_traffic.json")
     if not os.path.exists(path):
         return None, None
     with open(path) as f:
