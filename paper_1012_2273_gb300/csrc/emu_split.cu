@@ -324,18 +324,45 @@ __device__ __forceinline__ float2 fadd2(float2 a, float2 b) {
   return d;
 }
 
+// guard_item for the modular split's magnitude-and-sign values (bf16
+// magnitude plane): the same digits and sums, from |D| with the 32-bit forms
+// of guard.cuh; the sums of a lane's 8 elements and its partner lanes' stay
+// below 2^29 and are added in 32 bits.
+__device__ __forceinline__ void guard_item_sm(const uint64_t (&V)[8], int width, void* mag_out,
+                                              unsigned long long* row_sum, bool lead, unsigned xor_lanes) {
+  uint32_t sum = 0, w[4];
+#pragma unroll
+  for (int p = 0; p < 4; ++p) {
+    const uint64_t a0 = V[2 * p] & ~(1ull << 63), a1 = V[2 * p + 1] & ~(1ull << 63);
+    const float2 f = fadd2(make_float2(__uint_as_float(0x4B000000u | mag7_of_abs(a0, width)),
+                                       __uint_as_float(0x4B000000u | mag7_of_abs(a1, width))),
+                           make_float2(-8388608.0f, -8388608.0f));
+    w[p] = bf16x2_of_digits(f.x, f.y);
+    sum += sum24_of_abs(a0, width) + sum24_of_abs(a1, width);
+  }
+  *reinterpret_cast<uint4*>(mag_out) = make_uint4(w[0], w[1], w[2], w[3]);
+  for (int o = 1; o < 32; o <<= 1)
+    if (xor_lanes & static_cast<unsigned>(o)) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+  if (lead) atomicAdd(row_sum, static_cast<unsigned long long>(sum));
+}
+
+// The modular split holds each D as |D| with the sign in bit 63
+// (fixed_point_sm): the magnitude is one mask, the sign one bit.
+constexpr uint64_t SM_MAG = ~(1ull << 63);
+
 template <int K, int LIMBS>
-__device__ __forceinline__ void write_residue_item(const long long (&D)[8], uint16_t* out, size_t plane) {
+__device__ __forceinline__ void write_residue_item(const uint64_t (&V)[8], uint16_t* out, size_t plane) {
   constexpr int LB = mod_limb_bits(LIMBS);
   float2 x[4][LIMBS];  // limbs of elements 2p (.x) and 2p + 1 (.y)
 #pragma unroll
   for (int p = 0; p < 4; ++p) {
-    const long long d0 = D[2 * p], d1 = D[2 * p + 1];
-    const uint64_t X0 = d0 < 0 ? 0ull - static_cast<uint64_t>(d0) : static_cast<uint64_t>(d0);
-    const uint64_t X1 = d1 < 0 ? 0ull - static_cast<uint64_t>(d1) : static_cast<uint64_t>(d1);
-    // sg (2^23 + limb) - sg 2^23 = sg limb, exactly, in one FMA
-    const float2 sg = make_float2(d0 < 0 ? -1.0f : 1.0f, d1 < 0 ? -1.0f : 1.0f);
-    const float2 bias = make_float2(d0 < 0 ? 8388608.0f : -8388608.0f, d1 < 0 ? 8388608.0f : -8388608.0f);
+    const uint64_t X0 = V[2 * p] & SM_MAG, X1 = V[2 * p + 1] & SM_MAG;
+    const uint32_t s0 = static_cast<uint32_t>(V[2 * p] >> 32) & 0x80000000u;
+    const uint32_t s1 = static_cast<uint32_t>(V[2 * p + 1] >> 32) & 0x80000000u;
+    // sg (2^23 + limb) - sg 2^23 = sg limb, exactly, in one FMA (sg = +-1
+    // and the bias -+2^23 take the sign bit directly)
+    const float2 sg = make_float2(__uint_as_float(0x3F800000u | s0), __uint_as_float(0x3F800000u | s1));
+    const float2 bias = make_float2(__uint_as_float(0xCB000000u ^ s0), __uint_as_float(0xCB000000u ^ s1));
 #pragma unroll
     for (int l = 0; l < LIMBS; ++l) {
       const uint32_t l0 = static_cast<uint32_t>(X0 >> (LB * l)) & ((1u << LB) - 1);
@@ -378,13 +405,13 @@ __device__ __forceinline__ void residue_tile_from_smem(const long long (&Ds)[SP_
 #pragma unroll 1
   for (int pass = 0; pass < 2; ++pass) {
     const int r = 16 * (warp >> 2) + (lane >> 1) + 32 * pass, cg = 2 * (warp & 3) + (lane & 1);
-    long long D[8];
+    uint64_t V[8];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) D[q] = Ds[r][8 * cg + q];
+    for (int q = 0; q < 8; ++q) V[q] = static_cast<uint64_t>(Ds[r][8 * cg + q]);
     uint16_t* out = dst + static_cast<size_t>(r0 + r) * k_pad + c0 + 8 * cg;
     // a row's 8 items: 2 lanes of each of 4 warps (uniform branch)
-    if (guard) guard_item(D, width, out + K * plane, &gsum[r], (lane & 1) == 0, 0x1u);
-    write_residue_item<K, LIMBS>(D, out, plane);
+    if (guard) guard_item_sm(V, width, out + K * plane, &gsum[r], (lane & 1) == 0, 0x1u);
+    write_residue_item<K, LIMBS>(V, out, plane);
   }
 }
 
@@ -463,7 +490,11 @@ __global__ void __launch_bounds__(SP_THREADS, 3) split_kernel(const __grid_const
     for (int b = 0; b < PER; ++b) {
       const int y = y0 + b * (SP_THREADS / SP_TILE);
       long long D = 0;
-      if (xin && y < lim_i) D = fixed_point(bits[b], ex_s[rows_out ? y : x], width, &nonfinite);
+      if (xin && y < lim_i) {
+        const int ex = ex_s[rows_out ? y : x];
+        D = beta > 0 ? static_cast<long long>(fixed_point_sm(bits[b], ex, width, &nonfinite))
+                     : fixed_point(bits[b], ex, width, &nonfinite);
+      }
       if (rows_out) Ds[y][x] = D; else Ds[x][y] = D;
     }
     __syncthreads();

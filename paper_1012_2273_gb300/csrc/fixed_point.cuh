@@ -25,14 +25,13 @@ __host__ __device__ __forceinline__ int exponent_from_maxbits(uint64_t mb) {
   return E - 1022;
 }
 
-// D = round-half-even(v * 2^(width-e)) computed on the bit pattern of v
-// (width = 8s - 1 for s digits, beta for the modular form), without
-// branches.  Requires |v| < 2^e (true for every entry of a row/column scaled
+// |D| for D = round-half-even(v * 2^(width-e)), computed on the bit pattern
+// of v (width = 8s - 1 for s digits, beta for the modular form), without
+// branches; fixed_point() below gives D itself.  Requires |v| < 2^e (true for every entry of a row/column scaled
 // by its max), so a left shift never exceeds width bits.  A right shift by
 // n >= 1 rounds half to even as floor((x + 2^(n-1) - 1 + lsb) / 2^n) with
 // lsb the lowest kept bit of x; for n >= 54 (x < 2^53 <= 2^(n-1)) that is 0.
-__host__ __device__ __forceinline__ int64_t fixed_point(uint64_t bits, int e, int width, bool* nonfinite) {
-  const bool neg = (bits >> 63) != 0;
+__host__ __device__ __forceinline__ uint64_t fixed_point_magnitude(uint64_t bits, int e, int width, bool* nonfinite) {
   const int E = static_cast<int>((bits >> 52) & 0x7FF);
   const uint64_t frac = bits & ((1ull << 52) - 1);
   const uint64_t x = E != 0 ? (frac | (1ull << 52)) : frac;  // subnormal: v = frac 2^(1 - 1075)
@@ -40,10 +39,26 @@ __host__ __device__ __forceinline__ int64_t fixed_point(uint64_t bits, int e, in
   const int n1 = -sh > 1 ? -sh : 1;
   const int n = n1 < 63 ? n1 : 63;
   const uint64_t right = (x + ((1ull << (n - 1)) - 1) + ((x >> n) & 1)) >> n;
-  uint64_t D = sh >= 0 ? (x << (sh < 63 ? sh : 63)) : right;
+  const uint64_t D = sh >= 0 ? (x << (sh < 63 ? sh : 63)) : right;
   if (E == 0x7FF) *nonfinite = true;
-  D = E == 0x7FF ? 0ull : D;
-  return neg ? -static_cast<int64_t>(D) : static_cast<int64_t>(D);
+  return E == 0x7FF ? 0ull : D;
+}
+
+__host__ __device__ __forceinline__ int64_t fixed_point(uint64_t bits, int e, int width, bool* nonfinite) {
+  const int64_t D = static_cast<int64_t>(fixed_point_magnitude(bits, e, width, nonfinite));
+  return (bits >> 63) ? -D : D;
+}
+
+// The same value as its magnitude |D| with the sign of v in bit 63: the
+// modular split's form (width <= 62, so |D| <= 2^62 leaves bit 63 free).
+__host__ __device__ __forceinline__ uint64_t fixed_point_sm(uint64_t bits, int e, int width, bool* nonfinite) {
+  return fixed_point_magnitude(bits, e, width, nonfinite) | (bits & (1ull << 63));
+}
+
+// Signed D from the magnitude-and-sign form.
+__host__ __device__ __forceinline__ int64_t sm_to_signed(uint64_t v) {
+  const int64_t a = static_cast<int64_t>(v & ~(1ull << 63));
+  return (v >> 63) ? -a : a;
 }
 
 __host__ __device__ __forceinline__ float float_of_bits(uint32_t b) {

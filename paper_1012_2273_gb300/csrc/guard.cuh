@@ -52,6 +52,32 @@ __host__ __device__ __forceinline__ uint64_t sum24_of(int64_t D, int w, bool v_n
   return w >= 24 ? (a >> (w - 24)) + 1 : (2 * a + 1) << (23 - w);
 }
 
+// The same two quantities from a = |D| (the modular split keeps D as its
+// magnitude and sign), with 32-bit operations when w >= 39: (a - 1) >> (w - 7)
+// is the high word of a - 1 shifted right by w - 39 (for a = 0 that word is
+// all ones, -1 as a signed shift, clamped to 0), and a >> (w - 24) < 2^24 is
+// one funnel shift of the two words (or the high word alone when w - 24 >=
+// 32).  Narrower widths take the 64-bit forms above; v is taken as nonzero
+// in sum24 (the split passes every element of a nonzero row, and a zero
+// row's sum is discarded).
+__host__ __device__ __forceinline__ uint32_t mag7_of_abs(uint64_t a, int w) {
+  if (w < 39) return mag7_of(static_cast<int64_t>(a), w);
+  const int32_t hi = static_cast<int32_t>(static_cast<uint32_t>((a - 1) >> 32));
+  const int32_t q = hi >> (w - 39);
+  return q > 0 ? static_cast<uint32_t>(q) : 0u;
+}
+__host__ __device__ __forceinline__ uint32_t sum24_of_abs(uint64_t a, int w) {
+  if (w < 39) return static_cast<uint32_t>(sum24_of(static_cast<int64_t>(a), w, true));
+  const uint32_t lo = static_cast<uint32_t>(a), hi = static_cast<uint32_t>(a >> 32);
+  const int sh = w - 24;  // 15 .. 38
+#ifdef __CUDA_ARCH__
+  const uint32_t q = sh >= 32 ? hi >> (sh - 32) : __funnelshift_r(lo, hi, sh);
+#else
+  const uint32_t q = sh >= 32 ? hi >> (sh - 32) : static_cast<uint32_t>(((static_cast<uint64_t>(hi) << 32) | lo) >> sh);
+#endif
+  return q + 1;
+}
+
 // The certificate test for one element: true when (*) holds for sure.  sa, sb
 // are the row and column sums of sum24_of, S the exact magnitude product,
 // k1 >= K1 and k2 <= K2 (1 - 2^-20) the constants of cert_constants.  It is

@@ -4,6 +4,7 @@
 //                    (as a signed 64-bit integer): prints "D nonfinite";
 //                    width 0: prints exponent_from_maxbits(bits & ~sign) and 0
 //   G D s            digits_of: prints the s digits d_1..d_s
+//   S bits e width   fixed_point_sm: prints "|D| sign nonfinite" (sign = bit 63)
 // Driven by tests/test_fixed_point.py.
 #include <vector_types.h>
 
@@ -37,6 +38,16 @@ int main() {
         case 7: print_digits<7>(D); break;
         default: print_digits<8>(D); break;
       }
+      continue;
+    }
+    if (op == 'S') {
+      long long bits;
+      int e, width;
+      if (std::scanf("%lld %d %d", &bits, &e, &width) != 3) return 1;
+      bool nonfinite = false;
+      const uint64_t v = mmk::fixed_point_sm(static_cast<uint64_t>(bits), e, width, &nonfinite);
+      std::printf("%llu %d %d\n", static_cast<unsigned long long>(v & ~(1ull << 63)), static_cast<int>(v >> 63),
+                  nonfinite ? 1 : 0);
       continue;
     }
     long long bits;

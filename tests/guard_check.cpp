@@ -2,6 +2,7 @@
 // csrc/guard.cuh).  Reads lines from stdin:
 //   M D w            mag7_of(D, w)
 //   U D w nz         sum24_of(D, w, nz != 0)
+//   A a w            mag7_of_abs(a, w) and sum24_of_abs(a, w) for a = |D|
 //   K n w s          cert_constants for inner dimension n, width w and the
 //                    kappa of s digits at width w (s = 0: modular form,
 //                    kappa = 0): prints k1 and k2 as %a hex floats
@@ -29,6 +30,11 @@ int main() {
       int w, nz;
       if (std::scanf("%lld %d %d", &D, &w, &nz) != 3) return 1;
       std::printf("%llu\n", static_cast<unsigned long long>(mmk::sum24_of(D, w, nz != 0)));
+    } else if (op == 'A') {
+      unsigned long long a;
+      int w;
+      if (std::scanf("%llu %d", &a, &w) != 2) return 1;
+      std::printf("%u %u\n", mmk::mag7_of_abs(a, w), mmk::sum24_of_abs(a, w));
     } else if (op == 'K') {
       int n, w, s;
       if (std::scanf("%d %d %d", &n, &w, &s) != 3) return 1;

@@ -96,3 +96,25 @@ def test_digits_match_the_oracle(tmp_path):
     assert len(got) == len(cases)
     bad = [(d, s, g) for (d, s), g in zip(cases, got) if g != oracle.emu_digits_of(d, s)]
     assert not bad, bad[:5]
+
+
+def test_magnitude_and_sign_form_matches_the_oracle(tmp_path):
+    # fixed_point_sm (the modular split's form: |D| with v's sign bit in bit
+    # 63) on the same cases: |D| is |or_fix|, the sign bit is v's, widths up
+    # to 62 leave bit 63 free; the non-finite flag as before.
+    gxx, inc = shutil.which("g++"), cuda_include()
+    if not gxx or not inc:
+        pytest.skip("needs g++ and the CUDA headers")
+    exe = str(tmp_path / "fixed_point_check")
+    subprocess.run([gxx, "-std=c++17", "-O2", "-I", inc, os.path.join(ROOT, "tests", "fixed_point_check.cpp"), "-o", exe],
+                   check=True, capture_output=True, text=True)
+    cs = cases()
+    lines = [f"S {bits_of(v)} {e} {w}" for v, e, w in cs] + [f"S {bits_of(v)} 1 40" for v in (math.inf, -math.nan)]
+    r = subprocess.run([exe], input="\n".join(lines) + "\n", capture_output=True, text=True, timeout=120, check=True)
+    got = [tuple(int(x) for x in line.split()) for line in r.stdout.strip().splitlines()]
+    assert len(got) == len(lines)
+    bad = [(v, e, w, g) for (v, e, w), g in zip(cs, got)
+           if g != (abs(oracle.fix(v, e, w)), 1 if math.copysign(1.0, v) < 0 else 0, 0)]
+    assert not bad, bad[:5]
+    assert all(g[0] < 2 ** 63 for g in got)
+    assert got[-2] == (0, 0, 1) and got[-1][0] == 0 and got[-1][2] == 1

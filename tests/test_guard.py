@@ -125,3 +125,23 @@ def test_fp32_test_implies_the_exact_inequality(harness):
             passed += 1
             assert Fr(sa + sb) + K1 <= K2 * S, m
     assert passed > len(meta) // 4  # the test is not vacuous
+
+
+def test_magnitude_forms_from_the_absolute_value_match(harness):
+    # mag7_of_abs / sum24_of_abs (the modular split's 32-bit forms for widths
+    # >= 39, the 64-bit ones below) give mag7_of(D, w) and sum24_of(D, w, true)
+    # for a = |D| at every width, including |D| = 0, 1, 2^w and values at the
+    # word boundary of the shifts.
+    rnd = random.Random(29)
+    cases = []
+    for w in range(1, 63):
+        top = 1 << w
+        vals = [0, 1, 2, top, top - 1, top // 2, (1 << 32) - 1, 1 << 32, (1 << 32) + 1]
+        vals += [rnd.randrange(0, top + 1) for _ in range(300)]
+        cases += [(a, w) for a in vals if a <= top]
+    got = harness([f"A {a} {w}" for a, w in cases])
+    want_m = harness([f"M {a} {w}" for a, w in cases])
+    want_u = harness([f"U {a} {w} 1" for a, w in cases])
+    assert len(got) == len(cases)
+    bad = [(a, w, g, m, u) for (a, w), g, m, u in zip(cases, got, want_m, want_u) if g.split() != [m.strip(), u.strip()]]
+    assert not bad, bad[:5]
