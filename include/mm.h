@@ -224,7 +224,9 @@ mm_status mm_modular_params(int k, int N, int* beta, int* moduli);
  *   out_ms[2] native FP64 kernels (including the certificate's recomputation)
  *   out_ms[3] recombination run as its own pass (small problems, the modular
  *             form, mm_recombine)
- *   out_ms[4] the accuracy certificate's product of the magnitude planes
+ *   out_ms[4] the accuracy certificate's product of the magnitude planes, when
+ *             it has a launch of its own (with CTA pairs its units run in the
+ *             slice-product launch, out_ms[1])
  * and launches[0..4] the number of kernel launches of each kind (may be
  * NULL).  Both arrays hold MM_PROFILE_KINDS entries.  Synchronises on the
  * recorded events.  MM_ERR_INVALID without the flag. */

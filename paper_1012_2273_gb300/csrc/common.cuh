@@ -50,9 +50,10 @@ struct Problem {
   int8_t slot_level[64];  // level L of each segment slot of a tile, in slot order (nslots <= 64)
   // Accuracy certificate (guard.cuh); guard = 0: off.  With it on, the split
   // writes one more plane (index s: the magnitude digits of |v'|) and the
-  // row/column sums below, every tile gets one more work unit (group index
-  // `groups`) that multiplies the two magnitude planes and tests each
-  // element, and the guard kernel recomputes the failures in native FP64.
+  // row/column sums below; the product of the two magnitude planes is tested
+  // element by element -- by the paired residue-product kernel as one more
+  // work unit per pair tile (group index `groups`), or else by a launch of
+  // its own -- and the guard kernel recomputes the failures in native FP64.
   int guard;
   float cert_k1, cert_k2;       // constants of cert_ok for this problem
   unsigned long long* a_sum;    // [m] sums of sum24_of over each row of op(A) (zero at launch)

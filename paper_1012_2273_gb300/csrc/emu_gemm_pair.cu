@@ -30,6 +30,7 @@
 // cluster barrier, stay resident long enough for every copy either of them
 // issued to land, and meet again before the pair frees its tensor memory, so
 // no CTA leaves while its peer, a copy or an MMA may still touch its memory.
+#include "guard.cuh"
 #include "launch.cuh"
 #include "modular.cuh"
 #include "recombine.cuh"
@@ -155,8 +156,20 @@ struct PairUnit {
   const Problem* P;
   int pi;         // problem index (tensor maps)
   int pair_tile;  // 256 x 256 tile within the problem, in emu_tile_coords order over (tiles_m / 2) x tiles_n
-  int g, G;       // residue-group range of the unit
+  int g, G;       // residue group g of G; g == G: the accuracy certificate's unit
+  bool cert;      // the product of the two magnitude planes (plane s), tested element by element
 };
+
+// Planes [p0, p1) that unit U multiplies: a residue group's moduli, or the
+// certificate's magnitude plane (index s, after the residue planes).
+__device__ __forceinline__ void pair_unit_planes(const PairUnit& U, int* p0, int* p1) {
+  if (U.cert) {
+    *p0 = U.P->s;
+    *p1 = U.P->s + 1;
+  } else {
+    mod_group_range(U.P->s, U.G, U.g, p0, p1);
+  }
+}
 
 __device__ __forceinline__ PairUnit pair_unit(const EmuArgs& a, int u) {
   PairUnit r;
@@ -175,6 +188,7 @@ __device__ __forceinline__ PairUnit pair_unit(const EmuArgs& a, int u) {
     r.g = e.z;
     r.G = r.P->groups;
   }
+  r.cert = r.g >= r.G;
   return r;
 }
 
@@ -278,7 +292,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(PR_THREADS, 1)
         const CUtensorMap* ma = args.units ? &args.maps[2 * U.pi] : &mapA;
         const CUtensorMap* mb = args.units ? &args.maps[2 * U.pi + 1] : &mapB;
         int p0, p1;
-        mod_group_range(P->s, U.G, U.g, &p0, &p1);
+        pair_unit_planes(U, &p0, &p1);
         for (int p = p0; p < p1 && ok; ++p) {
           for (int kb = 0; kb < KB; ++kb) {
             if (!mbar_wait(&empty[stage], phase ^ 1, tmo, args.status)) {
@@ -340,7 +354,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(PR_THREADS, 1)
         const PairUnit U = pair_unit(args, u);
         const int KB = U.P->k_pad / PR_BK;
         int p0, p1;
-        mod_group_range(U.P->s, U.G, U.g, &p0, &p1);
+        pair_unit_planes(U, &p0, &p1);
         for (int p = p0; p < p1 && ok; ++p) {
           for (int c0 = 0; c0 < KB && ok; c0 += PR_CHUNK_KB) {
             // phase 0 of each buffer is the epilogues' first arrival
@@ -419,7 +433,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(PR_THREADS, 1)
       const int KB = P->k_pad / PR_BK;
       const int s = P->s;
       int p0, p1;
-      mod_group_range(s, U.G, U.g, &p0, &p1);
+      pair_unit_planes(U, &p0, &p1);
       const int nchunks = (KB + PR_CHUNK_KB - 1) / PR_CHUNK_KB;
       for (int j = p0; j < p1 && ok; ++j) {
         uint32_t acc[HALF];
@@ -433,7 +447,6 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(PR_THREADS, 1)
           tc_fence_after();
           const uint32_t taddr = tmem_base + (static_cast<uint32_t>(32 * q) << 16) +
                                  static_cast<uint32_t>(abuf * PR_BN + h * HALF);
-          // two loads in flight per wait: the drain is bound by load round trips
           // chunk sums: integers of magnitude <= 2^24, converted exactly
 #pragma unroll
           for (int part = 0; part < HALF / 32; ++part) {
@@ -450,6 +463,57 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(PR_THREADS, 1)
           if (abuf == 0) aphase ^= 1;
         }
         if (!ok) break;
+        if (U.cert) {
+          // Accuracy certificate (guard.cuh): acc = S = sum_j M_A M_B, exact,
+          // bounds (|A||B|) from below; an element whose error bound it
+          // cannot certify is listed for the guard kernel.  Lanes are rows;
+          // each lane converts the terms of 4 of the warp's 128 columns once
+          // and the warp shares them by shuffles; nothing is written when
+          // every element passes.
+          const int row = (2 * tmp + static_cast<int>(rank)) * EM_BM + r_in_tile;
+          const int col0 = tn * PR_BN + h * HALF;
+          const bool in_row = row < P->m;
+          const float rowt = in_row ? cert_row_term(P->a_sum[row]) : 0.0f;
+          const float k2 = P->cert_k2;
+          const int ncols = P->n - col0 < HALF ? P->n - col0 : HALF;  // columns of this half inside the problem
+          float cts[HALF / 32];  // terms of columns (HALF / 32) lane + q
+#pragma unroll
+          for (int q2 = 0; q2 < HALF / 32; ++q2) {
+            const int c = (HALF / 32) * lane + q2;
+            cts[q2] = c < ncols ? cert_col_term(P->b_sum[col0 + c], P->cert_k1) : 0.0f;
+          }
+          uint32_t bad[HALF / 32];
+#pragma unroll
+          for (int w = 0; w < HALF / 32; ++w) bad[w] = 0u;
+#pragma unroll
+          for (int i = 0; i < HALF; ++i) {
+            const float colt = __shfl_sync(0xffffffffu, cts[i % (HALF / 32)], i / (HALF / 32));
+            const bool fail = !cert_test(rowt, colt, acc[i], k2);
+            if (in_row && i < ncols && fail) bad[i / 32] |= 1u << (i % 32);
+          }
+          uint32_t any = 0u;
+#pragma unroll
+          for (int w = 0; w < HALF / 32; ++w) any |= bad[w];
+          if (__any_sync(0xffffffffu, any != 0u)) {
+#pragma unroll
+            for (int w = 0; w < HALF / 32; ++w) {
+              for (int b = 0; b < 32; ++b) {
+                const bool mine = (bad[w] >> b) & 1u;
+                const unsigned msk = __ballot_sync(0xffffffffu, mine);
+                if (!msk) continue;
+                int base = 0;
+                if (lane == 0) {
+                  base = atomicAdd(P->guard_count, __popc(msk));
+                  atomicAdd(P->guard_total, __popc(msk));
+                }
+                base = __shfl_sync(0xffffffffu, base, 0);
+                const int at = base + __popc(msk & ((1u << lane) - 1u));
+                if (mine && at < P->guard_limit) P->guard_list[at] = make_int2(row, col0 + 32 * w + b);
+              }
+            }
+          }
+          continue;
+        }
         // Residue reduction exactly as in emu_gemm.cu's modular epilogue.
         const uint32_t m = c_mod.m_u[j], magic = c_mod.magic[j];
         const uint32_t shift_in = c_mod.bias[j];  // x = S + bias_j

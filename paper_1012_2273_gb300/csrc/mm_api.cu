@@ -328,9 +328,10 @@ struct EmuGroup {
   bool pair = false;    // modular form at bn 256: CTA pairs (cta_group::2) on 256 x 256 tiles
   bool guard = false;   // accuracy certificate and native recomputation of what it cannot vouch for
   int guard_tiles = 0;  // blocks of the guard kernel's whole-problem part
+  bool cert_folded = false;  // the certificate's products run as units of the paired kernel
   std::vector<Problem> ps;
   std::vector<int> max_off;        // offset of problem p in the maxbits arrays
-  std::vector<CUtensorMap> maps;   // 2 per problem; CTA pairs with the certificate: 2 more per problem after those
+  std::vector<CUtensorMap> maps;   // 2 per problem
   std::vector<int4> units;         // grouped launches: {problem, tile, group, cost}
   std::vector<int4> cert_units;    // grouped launches: the certificate's {problem, tile, 0, cost}
   int cert_total = 0;              // units of the certificate's launch
@@ -387,8 +388,10 @@ bool pair_mma_enabled() {
 mm_status layout_group(mm_handle h, EmuGroup& g, char* base) {
   Arena ar;
   g.total_tiles = g.total_split = g.total_absmax = g.max_rows = 0;
-  // (with CTA pairs the certificate's launch still runs on single CTAs, with tensor maps of its own)
   g.pair = g.form == 2 && g.bn == 256 && pair_mma_enabled() && h->num_sms >= 2;
+  // With CTA pairs the certificate's products are units of the paired kernel
+  // (one per pair tile, group index `groups`), tested in its epilogue.
+  g.cert_folded = g.pair && g.guard;
   g.guard_tiles = 0;
   int maxk = 0;
   g.max_off.assign(g.ps.size(), 0);
@@ -487,7 +490,8 @@ mm_status layout_group(mm_handle h, EmuGroup& g, char* base) {
           const int cost = (p1 - p0) * kb;
           for (int t = 0; t < unit_tiles; ++t) g.units.push_back(make_int4(static_cast<int>(i), t, gi, cost));
         }
-
+        if (g.cert_folded)
+          for (int t = 0; t < unit_tiles; ++t) g.units.push_back(make_int4(static_cast<int>(i), t, G, kb));
       }
       continue;
     }
@@ -538,7 +542,7 @@ mm_status layout_group(mm_handle h, EmuGroup& g, char* base) {
     });
     g.total_units = static_cast<int>(g.units.size());
   } else {
-    g.total_units = g.ps[0].tiles_m * g.ps[0].tiles_n / (g.pair ? 2 : 1) * g.ps[0].groups;
+    g.total_units = g.ps[0].tiles_m * g.ps[0].tiles_n / (g.pair ? 2 : 1) * (g.ps[0].groups + (g.cert_folded ? 1 : 0));
   }
   g.grid = g.pair ? 2 * emu_grid(h, std::min(g.total_units, h->num_sms / 2)) : emu_grid(h, g.total_units);
   if (g.form == 3) g.grid = std::max(1, std::min(g.total_units, mmk::i8_blocks_per_sm() * h->num_sms));
@@ -546,7 +550,7 @@ mm_status layout_group(mm_handle h, EmuGroup& g, char* base) {
   // longest first (grouped calls list them; a single problem numbers them).
   g.cert_units.clear();
   g.cert_total = 0;
-  if (g.guard) {
+  if (g.guard && !g.cert_folded) {
     for (size_t i = 0; i < g.ps.size(); ++i) {
       const Problem& p = g.ps[i];
       const int tiles = p.tiles_m * p.tiles_n;
@@ -569,14 +573,7 @@ mm_status layout_group(mm_handle h, EmuGroup& g, char* base) {
       cert_kb += tiles * kb;
     }
     g.cert_grid = std::max(1, std::min(g.cert_total, static_cast<int>(std::lround(slots * cert_kb / (main_kb + cert_kb)))));
-    if (!h->profile && slots > g.cert_grid) {
-      if (g.pair) {  // whole clusters of two; an SM left over goes to the certificate
-        g.grid = 2 * std::max(1, std::min(g.grid / 2, (slots - g.cert_grid) / 2));
-        g.cert_grid = std::max(g.cert_grid, std::min(g.cert_total, slots - g.grid));
-      } else {
-        g.grid = std::max(1, std::min(g.grid, slots - g.cert_grid));
-      }
-    }
+    if (!h->profile && slots > g.cert_grid) g.grid = std::max(1, std::min(g.grid, slots - g.cert_grid));
     if (h->profile) g.cert_grid = std::min(g.cert_total, slots);
   }
   // Everything zeroed before a launch sits in one run (one memset): the
@@ -617,19 +614,15 @@ mm_status layout_group(mm_handle h, EmuGroup& g, char* base) {
   g.bytes = ar.off;
   g.base = base;
   if (base) {
-    // CTA pairs stage half of a B^T tile per CTA; the certificate's launch
-    // (single CTAs) then gets maps of its own with whole tiles.
-    const bool cert_maps = g.pair && g.guard;
+    // (CTA pairs stage half of a B^T tile per CTA)
     const size_t np = g.ps.size();
-    g.maps.assign((cert_maps ? 4 : 2) * np, CUtensorMap{});
+    g.maps.assign(2 * np, CUtensorMap{});
     for (size_t i = 0; i < np && g.form != 3; ++i) {  // (the INT8 kernel copies with cp.async)
       const Problem& p = g.ps[i];
       const long planes = p.s + (g.guard ? 1 : 0);
       if (!make_plane_map(&g.maps[2 * i], p.a_slices, p.k_pad, planes * p.m_pad, 128) ||
           !make_plane_map(&g.maps[2 * i + 1], p.b_slices, p.k_pad, planes * p.n_pad,
-                          g.pair ? g.bn / 2 : g.bn) ||
-          (cert_maps && (!make_plane_map(&g.maps[2 * np + 2 * i], p.a_slices, p.k_pad, planes * p.m_pad, 128) ||
-                         !make_plane_map(&g.maps[2 * np + 2 * i + 1], p.b_slices, p.k_pad, planes * p.n_pad, g.bn))))
+                          g.pair ? g.bn / 2 : g.bn))
         return fail(h, MM_ERR_CUDA, "cuTensorMapEncodeTiled failed");
     }
   }
@@ -671,11 +664,12 @@ mm_status run_group(mm_handle h, const EmuGroup& g, const Problem* d_table, cons
   a.levels_out = nullptr;
   a.status = h->d_status;
   a.timeout_ns = h->timeout_ns;
-  // The certificate's launch needs only the split's planes and sums.  Unless
-  // profiling, it runs on its own stream, so that its units fill the SMs the
-  // slice products leave idle at their end; the guard kernel waits for it.
+  // Without CTA pairs the certificate has a launch of its own, which needs
+  // only the split's planes and sums.  Unless profiling, it runs on its own
+  // stream beside the slice products, on the SMs they leave; the guard kernel
+  // waits for it.
   bool cert_forked = false;
-  if (g.guard) {
+  if (g.guard && !g.cert_folded) {
     mmk::EmuArgs c = a;
     c.units = single ? nullptr : d_cert_units;
     c.total_units = g.cert_total;
@@ -687,13 +681,10 @@ mm_status run_group(mm_handle h, const EmuGroup& g, const Problem* d_table, cons
       cs = h->cert_stream;
       cert_forked = true;
     }
-    // maps of the certificate's single-CTA tiles (after the pairs' maps)
-    const size_t cm = g.pair ? 2 * g.ps.size() : 0;
-    if (d_maps) c.maps = d_maps + cm;
     const long m_c = prof_start(h, cs, KIND_CERT);
     const cudaError_t ce =
         g.form == 3 ? mmk::i8_cert_launch(c, g.cert_grid, cs)
-                    : mmk::emu_cert_launch(g.bn, &g.maps[cm], &g.maps[cm + 1], c, g.cert_grid, cs);
+                    : mmk::emu_cert_launch(g.bn, &g.maps[0], &g.maps[1], c, g.cert_grid, cs);
     prof_end(h, cs, m_c);
     if (ce != cudaSuccess) return cuda_fail(h, ce, "certificate launch");
     if (cert_forked) MM_CUDA(h, cudaEventRecord(h->cert_join, cs));

@@ -187,3 +187,31 @@ def test_replaced_count_matches_a_host_replica_of_the_certificate(mode, slices, 
     hi = replica_failures(A, B, w, kap, 2.0 ** -18)
     assert problems == 0
     assert lo <= elements <= hi, (lo, elements, hi)
+
+
+@pytest.mark.parametrize("n,seed", [(2000, 0), (1000, 3)])
+def test_folded_certificate_matches_its_own_launch(monkeypatch, n, seed):
+    # With CTA pairs (the default at tile width 256) the certificate's
+    # products are units of the paired kernel, tested in its epilogue; with
+    # single CTAs (MM_PAIR_MMA=0) they are a launch of their own.  Same
+    # arithmetic, so the same elements fail and the results are the same bits,
+    # on log-uniform inputs (some elements fail) and on a structured pair.
+    import paper_1012_2273_gb300 as mm
+    cases = [workload.pair("loguniform20", seed, n), workload.structured_pair("wide60", seed, n)]
+    got = {}
+    for pair in ("1", "0"):
+        monkeypatch.setenv("MM_PAIR_MMA", pair)
+        with mm.Handle("modular", slices=14) as h:
+            out = []
+            for A, B in cases:
+                C = host(h.gemm(dev(A), dev(B)))
+                h.check()
+                out.append((C, h.guard_read()))
+        got[pair] = out
+    for (C1, g1), (C0, g0), (A, B) in zip(got["1"], got["0"], cases):
+        assert g1 == g0
+        np.testing.assert_array_equal(C1.view(np.int64), C0.view(np.int64))
+        ratio, _, _ = within(C1, A, B, n)
+        assert ratio <= 1.0
+    if n == 2000:
+        assert got["1"][0][1][0] > 0  # log-uniform inputs at k = 14: some elements were recomputed
