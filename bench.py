@@ -199,7 +199,7 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
-KERNEL_SOURCES = ("emu_gemm_pair.cu", "common.cuh", "launch.cuh", "modular.cuh", "recombine.cuh", "tile_index.cuh")
+KERNEL_SOURCES = ("emu_gemm_pair.cu", "common.cuh", "launch.cuh", "modular.cuh", "recombine.cuh", "tile_index.cuh", "guard.cuh")
 
 
 def source_digest() -> str:
