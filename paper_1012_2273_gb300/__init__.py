@@ -196,6 +196,33 @@ def modular_params(k: int, n: int) -> tuple[int, tuple[int, ...]]:
     return beta.value, tuple(mods[:k])
 
 
+class _GroupedCall:
+    """See Handle.grouped_call."""
+
+    def __init__(self, handle, As, Bs, Cs, dims, square):
+        count = len(As)
+        self.handle, self.As, self.Bs, self.Cs = handle, As, Bs, Cs
+        self.count = count
+        self.pa = (ctypes.c_void_p * count)(*[a.data_ptr() for a in As])
+        self.pb = (ctypes.c_void_p * count)(*[b.data_ptr() for b in Bs])
+        self.pc = (ctypes.c_void_p * count)(*[c.data_ptr() for c in Cs])
+        self.square = square
+        if square:
+            self.ns = (ctypes.c_int * count)(*[d[1] for d in dims])
+        else:
+            self.col = [(ctypes.c_int * count)(*[d[j] for d in dims]) for j in range(8)]
+
+    def __call__(self, stream=None):
+        h = self.handle
+        if self.square:
+            h._raise(h._lib.mm_gemm_grouped(h._h, self.count, self.ns, self.pa, self.pb, self.pc, _stream_ptr(stream)))
+        else:
+            c = self.col
+            h._raise(h._lib.mm_gemm_grouped_ex(h._h, self.count, c[6], c[7], c[0], c[1], c[2], self.pa, c[3], self.pb,
+                                               c[4], self.pc, c[5], _stream_ptr(stream)))
+        return self.Cs
+
+
 class Handle:
     """One library handle (see mm_create).  Not thread safe."""
 
@@ -256,6 +283,37 @@ class Handle:
         return C
 
     def gemm_grouped(self, As: Sequence, Bs: Sequence, Cs: Sequence | None = None, stream=None):
+        return self.grouped_call(As, Bs, Cs)(stream)
+
+    def gemm_call(self, A, B, C):
+        """One product validated and marshalled once, for repeated use: the
+        returned callable runs mm_gemm (or mm_gemm_ex) on the stream it is
+        given.  The tensors must keep their storage and shapes meanwhile."""
+        m, k, lda, ta = _matrix(A, "A", True)
+        k2, n, ldb, tb = _matrix(B, "B", True)
+        if k2 != k:
+            raise ValueError(f"inner dimensions differ: A is {m} x {k}, B is {k2} x {n}")
+        mc, nc, ldc, _ = _matrix(C, "C")
+        if (mc, nc) != (m, n):
+            raise ValueError(f"C must be {m} x {n}")
+        lib, hh, pa, pb, pc = self._lib, self._h, A.data_ptr(), B.data_ptr(), C.data_ptr()
+        if _square_contiguous(A, B, C):
+            def call(stream=None):
+                self._raise(lib.mm_gemm(hh, n, pa, pb, pc, _stream_ptr(stream)))
+                return C
+        else:
+            def call(stream=None):
+                self._raise(lib.mm_gemm_ex(hh, ta, tb, m, n, k, pa, lda, pb, ldb, pc, ldc, _stream_ptr(stream)))
+                return C
+        call.tensors = (A, B, C)  # kept alive with the call
+        return call
+
+    def grouped_call(self, As: Sequence, Bs: Sequence, Cs: Sequence | None = None):
+        """A grouped call validated and marshalled once, for repeated use: the
+        returned object calls mm_gemm_grouped (or mm_gemm_grouped_ex) with the
+        pointer and size arrays built here, on the stream it is given, and
+        holds references to the tensors.  The tensors must keep their storage
+        and shapes while it is in use (their contents may change)."""
         import torch
         count = len(As)
         if len(Bs) != count or (Cs is not None and len(Cs) != count):
@@ -270,17 +328,8 @@ class Handle:
             if k2 != k or (mc, nc) != (m, n):
                 raise ValueError(f"problem {i}: shapes {tuple(a.shape)} x {tuple(b.shape)} -> {tuple(c.shape)}")
             dims.append((m, n, k, lda, ldb, ldc, ta, tb))
-        pa = (ctypes.c_void_p * count)(*[a.data_ptr() for a in As])
-        pb = (ctypes.c_void_p * count)(*[b.data_ptr() for b in Bs])
-        pc = (ctypes.c_void_p * count)(*[c.data_ptr() for c in Cs])
-        if all(_square_contiguous(a, b, c) for a, b, c in zip(As, Bs, Cs)):
-            ns = (ctypes.c_int * count)(*[d[1] for d in dims])
-            self._raise(self._lib.mm_gemm_grouped(self._h, count, ns, pa, pb, pc, _stream_ptr(stream)))
-        else:
-            col = [(ctypes.c_int * count)(*[d[j] for d in dims]) for j in range(8)]
-            self._raise(self._lib.mm_gemm_grouped_ex(self._h, count, col[6], col[7], col[0], col[1], col[2], pa, col[3],
-                                                     pb, col[4], pc, col[5], _stream_ptr(stream)))
-        return Cs
+        return _GroupedCall(self, list(As), list(Bs), list(Cs), dims,
+                            all(_square_contiguous(a, b, c) for a, b, c in zip(As, Bs, Cs)))
 
     def gemm_host(self, A, B, C=None, stream=None):
         """End-to-end product on host (numpy) arrays: copy in, compute, copy out."""

@@ -115,8 +115,11 @@ struct EmuArgs {
 // native_fp64.cu
 bool native_is_small(const Problem& p);
 void native_small_fill_tiles(Problem& p);
+// batch: one warp per 16 x 8 tile (many tiles) instead of one block per tile
+// (native_small_use_batch decides from the host's copies of the problems)
+bool native_small_use_batch(const Problem* ps, int count, int num_sms);
 cudaError_t native_small_launch(const Problem* table, const Problem* single, int count, int total_tiles,
-                                cudaStream_t stream);
+                                cudaStream_t stream, bool batch);
 void native_fill_tiles(Problem& p);
 cudaError_t native_launch(const Problem* table, const Problem* single, int count, int total_tiles,
                           cudaStream_t stream);

@@ -766,7 +766,8 @@ mm_status native_single(mm_handle h, Problem p, cudaStream_t stream) {
   p.tile_begin = 0;
   const long m = prof_start(h, stream, KIND_NATIVE);
   if (small)
-    MM_CUDA(h, mmk::native_small_launch(nullptr, &p, 1, p.tiles_m * p.tiles_n, stream));
+    MM_CUDA(h, mmk::native_small_launch(nullptr, &p, 1, p.tiles_m * p.tiles_n, stream,
+                                        mmk::native_small_use_batch(&p, 1, h->num_sms)));
   else
     MM_CUDA(h, mmk::native_launch(nullptr, &p, 1, p.tiles_m * p.tiles_n, stream));
   prof_end(h, stream, m);
@@ -942,6 +943,8 @@ mm_status grouped_impl(mm_handle h, const std::vector<Problem>& probs, cudaStrea
       std::memcpy(host_tab.data() + off_cert[gi], g.cert_units.data(), sizeof(int4) * g.cert_units.size());
   }
 
+  const bool nat_batch =
+      !nat_small.empty() && mmk::native_small_use_batch(nat_small.data(), static_cast<int>(nat_small.size()), h->num_sms);
   auto launch_all = [&](char* dtab, cudaStream_t s) -> mm_status {
     // Native problems do not depend on the emulation's kernels: unless
     // profiling (which wants one kernel at a time), they run on a side stream.
@@ -951,7 +954,8 @@ mm_status grouped_impl(mm_handle h, const std::vector<Problem>& probs, cudaStrea
       MM_CUDA(h, cudaStreamWaitEvent(h->side_stream, h->fork_ev, 0));
       if (!nat_small.empty())
         MM_CUDA(h, mmk::native_small_launch(reinterpret_cast<Problem*>(dtab + off_nat_small), nullptr,
-                                            static_cast<int>(nat_small.size()), nat_small_tiles, h->side_stream));
+                                            static_cast<int>(nat_small.size()), nat_small_tiles, h->side_stream,
+                                            nat_batch));
       if (!nat.empty())
         MM_CUDA(h, mmk::native_launch(reinterpret_cast<Problem*>(dtab + off_nat), nullptr,
                                       static_cast<int>(nat.size()), nat_tiles, h->side_stream));
@@ -960,7 +964,7 @@ mm_status grouped_impl(mm_handle h, const std::vector<Problem>& probs, cudaStrea
       const long m = prof_start(h, s, KIND_NATIVE);
       if (!nat_small.empty())
         MM_CUDA(h, mmk::native_small_launch(reinterpret_cast<Problem*>(dtab + off_nat_small), nullptr,
-                                            static_cast<int>(nat_small.size()), nat_small_tiles, s));
+                                            static_cast<int>(nat_small.size()), nat_small_tiles, s, nat_batch));
       if (!nat.empty())
         MM_CUDA(h, mmk::native_launch(reinterpret_cast<Problem*>(dtab + off_nat), nullptr,
                                       static_cast<int>(nat.size()), nat_tiles, s));

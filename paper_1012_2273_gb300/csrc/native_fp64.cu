@@ -21,6 +21,8 @@
 // single or grouped calls.  The order differs from the paper's left-to-right
 // sum, so results agree with it to within gamma_N |A||B| rather than bit for
 // bit (exactly, when all partial sums are exact, e.g. for small integers).
+#include <algorithm>
+
 #include "launch.cuh"
 
 namespace mmk {
@@ -285,6 +287,76 @@ __global__ void __launch_bounds__(NS_THREADS) native_fp64_small_kernel(const __g
   small_tile(P, m0, n0, ns_smem);
 }
 
+// Many small tiles at once (a batch of small problems): one warp per 16 x 8
+// tile, running up to NB_CHAINS of its 32-deep k chunks side by side as
+// independent chains (GB300's FP64 MMA pipe reaches its rate only with many
+// MMAs in flight per sub-partition), each chunk's chain from 0 and the chunk
+// sums added left to right from 0.0 -- the canonical order above, bit for
+// bit.  The operands of such problems are small and cached, so the fragments
+// come straight from global memory (zero outside the problem) and the
+// kernel needs no shared memory: four warps per block, four blocks per SM.
+constexpr int NB_WARPS = 4;
+constexpr int NB_CHAINS = 4;
+
+__device__ __forceinline__ void batch_tile(const Problem* P, int m0, int n0) {
+  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  const int m = P->m, n = P->n, kdim = P->k;
+  const double* __restrict__ A = P->A;
+  const double* __restrict__ B = P->B;
+  // element (i, j) of op(A) is A[i * a_i + j * a_j]; element (j, l) of op(B) is B[j * b_j + l * b_l]
+  const size_t a_i = P->ta ? 1 : P->lda, a_j = P->ta ? P->lda : 1;
+  const size_t b_j = P->tb ? 1 : P->ldb, b_l = P->tb ? P->ldb : 1;
+  const int ra = m0 + g, rb = m0 + g + 8, cb = n0 + g;
+  const int ksteps = (kdim + 15) / 16 * 16;  // zero-padded to a multiple of 16, as everywhere in this file
+  const int chunks = (ksteps + NS_KC - 1) / NS_KC;
+  double tot[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int c0 = 0; c0 < chunks; c0 += NB_CHAINS) {
+    double acc[NB_CHAINS][4];
+    int kend[NB_CHAINS];
+#pragma unroll
+    for (int j = 0; j < NB_CHAINS; ++j) {
+      acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.0;
+      const int left = ksteps - (c0 + j) * NS_KC;
+      kend[j] = c0 + j < chunks ? (left < NS_KC ? left : NS_KC) : 0;
+    }
+    for (int kq = 0; kq < NS_KC; kq += 4) {
+      double fa0[NB_CHAINS], fa1[NB_CHAINS], fb[NB_CHAINS];
+#pragma unroll
+      for (int j = 0; j < NB_CHAINS; ++j) {
+        const int k = (c0 + j) * NS_KC + kq + t;
+        const bool kin = kq < kend[j] && k < kdim;
+        fa0[j] = kin && ra < m ? A[static_cast<size_t>(ra) * a_i + static_cast<size_t>(k) * a_j] : 0.0;
+        fa1[j] = kin && rb < m ? A[static_cast<size_t>(rb) * a_i + static_cast<size_t>(k) * a_j] : 0.0;
+        fb[j] = kin && cb < n ? B[static_cast<size_t>(k) * b_j + static_cast<size_t>(cb) * b_l] : 0.0;
+      }
+#pragma unroll
+      for (int j = 0; j < NB_CHAINS; ++j)
+        if (kq < kend[j]) dmma_16x8x4(acc[j], fa0[j], fa1[j], fb[j]);  // (warp-uniform condition)
+    }
+#pragma unroll
+    for (int j = 0; j < NB_CHAINS; ++j)
+      if (kend[j] > 0) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) tot[q] = tot[q] + acc[j][q];
+      }
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int r = m0 + g + 8 * (q >> 1), col = n0 + 2 * t + (q & 1);
+    if (r < m && col < n) P->C[static_cast<size_t>(r) * P->ldc + col] = tot[q];
+  }
+}
+
+__global__ void __launch_bounds__(32 * NB_WARPS, 4) native_fp64_batch_kernel(const __grid_constant__ NativeArgs args,
+                                                                            int total_tiles) {
+  const int tile = blockIdx.x * NB_WARPS + (threadIdx.x >> 5);
+  if (tile >= total_tiles) return;
+  const Problem* P = args.table ? &args.table[find_problem(args.table, args.count, tile)] : &args.single;
+  const int local = tile - P->tile_begin;
+  if (P->n <= 0 || P->m <= 0 || local < 0 || local >= P->tiles_m * P->tiles_n) return;
+  batch_tile(P, (local / P->tiles_n) * NS_TM, (local % P->tiles_n) * NS_TN);
+}
+
 // ---------------------------------------------------------------------------
 // Guard kernel: after an emulated launch, recomputes in native FP64 what its
 // accuracy certificate (guard.cuh) could not vouch for.  A problem with more
@@ -394,9 +466,42 @@ void native_small_fill_tiles(Problem& p) {
   p.tiles_n = p.m > 0 && p.n > 0 ? (p.n + NS_TN - 1) / NS_TN : 0;
 }
 
+// Which small-tile kernel serves these problems: the estimated time of each,
+// in rounds of four side-by-side 32-deep chains, from the work and the tiles
+// the kernel holds at once (the latency kernel: 2 blocks of one tile per SM,
+// a tile's chunks over its 4 warps; the batch kernel: 4 blocks of 4 tiles per
+// SM, a tile's chunks 4 at a time in one warp), each at least its longest
+// tile.
+bool native_small_use_batch(const Problem* ps, int count, int num_sms) {
+  double lat = 0.0, bat = 0.0;
+  int lat_max = 0, bat_max = 0;
+  for (int i = 0; i < count; ++i) {
+    const Problem& p = ps[i];
+    if (p.m <= 0 || p.n <= 0) continue;
+    const int chunks = ((p.k + 15) / 16 * 16 + NS_KC - 1) / NS_KC;
+    const double tiles = static_cast<double>(p.tiles_m) * p.tiles_n;
+    const int rounds = (chunks + NB_CHAINS - 1) / NB_CHAINS;
+    lat += tiles * rounds;
+    bat += tiles * rounds;
+    lat_max = std::max(lat_max, rounds);
+    bat_max = std::max(bat_max, rounds);
+  }
+  const double t_lat = std::max(lat / (2.0 * num_sms), static_cast<double>(lat_max));
+  const double t_bat = std::max(bat / (4.0 * NB_WARPS * num_sms), static_cast<double>(bat_max));
+  return t_bat < t_lat;
+}
+
 cudaError_t native_small_launch(const Problem* table, const Problem* single, int count, int total_tiles,
-                                cudaStream_t stream) {
+                                cudaStream_t stream, bool batch) {
   if (total_tiles <= 0) return cudaSuccess;
+  if (batch) {
+    NativeArgs args{};
+    args.table = table;
+    if (single) args.single = *single;
+    args.count = count;
+    native_fp64_batch_kernel<<<(total_tiles + NB_WARPS - 1) / NB_WARPS, 32 * NB_WARPS, 0, stream>>>(args, total_tiles);
+    return cudaGetLastError();
+  }
   NativeArgs args{};
   args.table = table;
   if (single) args.single = *single;

@@ -253,3 +253,33 @@ def test_forced_pair_groups_are_bit_exact(tmp_path, groups):
     np.testing.assert_array_equal(C.view(np.int64), want.view(np.int64))
     for (a, b), c in zip(pairs, Cs):
         np.testing.assert_array_equal(host(c).view(np.int64), oracle.emu_gemm(a, b, 7).view(np.int64))
+
+
+def test_prepared_calls_give_the_same_bits():
+    # Handle.grouped_call / gemm_call validate and marshal once and then call
+    # the C ABI directly; repeated calls give the bits of the plain calls
+    # (mixed native and emulated problems, a strided view for the single one).
+    import torch
+    import paper_1012_2273_gb300 as mm
+    sizes = [10, 100, 300, 700]
+    pairs = [workload.pair("uniform11", 40 + i, n) for i, n in enumerate(sizes)]
+    with mm.Handle("auto") as h:
+        want = [host(c) for c in h.gemm_grouped([dev(a) for a, _ in pairs], [dev(b) for _, b in pairs])]
+        As, Bs = [dev(a) for a, _ in pairs], [dev(b) for _, b in pairs]
+        Cs = [torch.empty_like(a) for a in As]
+        call = h.grouped_call(As, Bs, Cs)
+        for _ in range(2):
+            call()
+            h.check()
+            for w, c in zip(want, Cs):
+                np.testing.assert_array_equal(host(c).view(np.int64), w.view(np.int64))
+        big = torch.zeros((310, 305), dtype=torch.float64, device="cuda")
+        A = big[5:, :300]  # a 305 x 300 view with leading dimension 305
+        A.copy_(dev(pairs[2][0][:305, :300] if pairs[2][0].shape[0] >= 305 else np.vstack([pairs[2][0], pairs[2][0][:5]])))
+        B = dev(pairs[2][1])
+        C = torch.empty((305, 300), dtype=torch.float64, device="cuda")
+        single = h.gemm_call(A, B, C)
+        for _ in range(2):
+            single()
+            h.check()
+            np.testing.assert_array_equal(host(C).view(np.int64), host(h.gemm(A, B)).view(np.int64))

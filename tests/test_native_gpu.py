@@ -123,3 +123,25 @@ def test_native_bitwise_reproducible_across_runs_tile_shapes_and_calls():
     assert np.array_equal(C1.view(np.int64), big[:n].view(np.int64))
     assert np.array_equal(host(G[0]).view(np.int64), C1.view(np.int64))
     assert np.array_equal(host(G[1]).view(np.int64), big.view(np.int64))
+
+
+def test_many_small_problems_one_warp_per_tile_same_bits():
+    # A grouped call of many small native problems runs one warp per 16 x 8
+    # tile (its chunks in order); single calls of the same problems run the
+    # latency kernel (a tile's chunks over four warps).  Both add the chunk
+    # sums in the canonical order, so the bits agree, and every result is
+    # within the bound of the oracle's.
+    import paper_1012_2273_gb300 as mm
+    sizes = workload.loguniform_sizes(300, 10, 250, seed=4)
+    pairs = [workload.pair("uniform11", 500 + i, n) for i, n in enumerate(sizes)]
+    with mm.Handle("native") as h:
+        Cs = [host(c) for c in h.gemm_grouped([dev(a) for a, _ in pairs], [dev(b) for _, b in pairs])]
+        h.check()
+        for i in range(0, len(sizes), 7):
+            A, B = pairs[i]
+            C1 = host(h.gemm(dev(A), dev(B)))
+            h.check()
+            np.testing.assert_array_equal(C1.view(np.int64), Cs[i].view(np.int64))
+    for i in range(0, len(sizes), 5):
+        A, B = pairs[i]
+        assert_within_bound(Cs[i], oracle.gemm(A, B), oracle.absgemm(A, B), sizes[i])
