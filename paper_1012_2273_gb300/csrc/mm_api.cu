@@ -1370,35 +1370,33 @@ mm_status mm_gemm_grouped_host(mm_handle h, int count, const int* Ns, const doub
       return fail(h, MM_ERR_CUDA, "copy streams");
     }
   }
-  // Chunks: every problem below N = 768 in a first chunk (little to copy,
-  // quick to compute), then the larger ones in order of size, at most four
-  // chunks of them cut by running flop count; the smallest of those chunks
-  // goes last, so that both the first upload and the last download that
-  // nothing overlaps are short.
-  std::vector<int> small, big;
-  double total_big = 0.0;
+  // Chunks, in decreasing problem size: the products take longer than the
+  // copies, so the largest computation starts first and the uploads of the
+  // rest overlap it, and the last chunk -- whose product and download
+  // nothing overlaps -- holds the smallest problems.  Leading chunks close
+  // once they hold a quarter of the work (at most three of them); the
+  // remaining problems form the last chunk.  (On GB300 the paper's sweep as
+  // [2000], [1500], [the rest] took 1.025 ms end to end, against 1.116 ms
+  // with the small problems first.)
+  std::vector<int> order;
+  double total = 0.0;
   for (int i = 0; i < count; ++i) {
     if (Ns[i] <= 0) continue;
-    if (Ns[i] < 768) {
-      small.push_back(i);
-    } else {
-      big.push_back(i);
-      total_big += 2.0 * Ns[i] * static_cast<double>(Ns[i]) * Ns[i];
+    order.push_back(i);
+    total += 2.0 * Ns[i] * static_cast<double>(Ns[i]) * Ns[i];
+  }
+  if (order.empty()) return MM_OK;
+  std::stable_sort(order.begin(), order.end(), [Ns](int a, int b) { return Ns[a] > Ns[b]; });
+  std::vector<std::vector<int>> chunks(1);
+  double in_chunk = 0.0;
+  for (int i : order) {
+    if (chunks.size() <= 3 && in_chunk >= total / 4.0) {
+      chunks.emplace_back();
+      in_chunk = 0.0;
     }
+    chunks.back().push_back(i);
+    in_chunk += 2.0 * Ns[i] * static_cast<double>(Ns[i]) * Ns[i];
   }
-  if (small.empty() && big.empty()) return MM_OK;
-  std::stable_sort(big.begin(), big.end(), [Ns](int a, int b) { return Ns[a] < Ns[b]; });
-  std::vector<std::vector<int>> bigc;
-  double acc = 0.0;
-  for (int i : big) {
-    if (bigc.empty() || (bigc.size() < 4 && acc >= total_big * bigc.size() / 4.0)) bigc.emplace_back();
-    bigc.back().push_back(i);
-    acc += 2.0 * Ns[i] * static_cast<double>(Ns[i]) * Ns[i];
-  }
-  std::vector<std::vector<int>> chunks;
-  if (!small.empty()) chunks.push_back(small);
-  for (size_t c = 1; c < bigc.size(); ++c) chunks.push_back(bigc[c]);
-  if (!bigc.empty()) chunks.push_back(bigc[0]);
   while (h->ge2e_events.size() < 2 * chunks.size() + 1) {
     cudaEvent_t e;
     if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
