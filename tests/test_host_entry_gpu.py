@@ -60,3 +60,23 @@ def test_grouped_host_rejects_bad_input():
             h.gemm_grouped_host([np.zeros((3, 4))], [np.zeros((3, 4))])
         with pytest.raises(TypeError):
             h.gemm_grouped_host([dev(np.zeros((4, 4)))], [dev(np.zeros((4, 4)))])
+
+
+def test_grouped_host_many_similar_problems_fill_every_chunk():
+    # 48 problems of similar size: the leading chunks close at a quarter of
+    # the work each (three of them) and the last takes the rest, so every
+    # chunk boundary falls inside a run of near-equal sizes; the results are
+    # the device-side grouped call's bits, on two calls in a row.
+    import paper_1012_2273_gb300 as mm
+    sizes = [int(x) for x in np.random.default_rng(7).integers(180, 260, size=48)]
+    pairs = [workload.pair("uniform11", 300 + i, n) for i, n in enumerate(sizes)]
+    with mm.Handle("auto") as h:
+        want = [host(c) for c in h.gemm_grouped([dev(a) for a, _ in pairs], [dev(b) for _, b in pairs])]
+        h.check()
+        for _ in range(2):
+            got = h.gemm_grouped_host([a for a, _ in pairs], [b for _, b in pairs])
+            h.check()
+            for n, g, w in zip(sizes, got, want):
+                np.testing.assert_array_equal(g.view(np.int64), w.view(np.int64), err_msg=f"N={n}")
+    A, B = pairs[0]
+    assert_within_bound(got[0], oracle.gemm(A, B), oracle.absgemm(A, B), sizes[0])
